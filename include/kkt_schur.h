@@ -1,0 +1,160 @@
+/*
+ * kkt_schur.h -- C ABI of the GB300 Schur-complement solver for
+ * block-arrowhead KKT systems (Kardos, Kourounis, Schenk,
+ * "Structure-Exploiting Interior Point Methods", Sec. 4).
+ *
+ * The system (eq. hessianPerm, written with B on the right):
+ *
+ *     K = [ A_0                B_0 ]     x = [x_0; ...; x_{N-1}; x_g]
+ *         [      ...           ... ]     r = [r_0; ...; r_{N-1}; r_g]
+ *         [          A_{N-1}   B_{N-1}]
+ *         [ B_0^T ... B_{N-1}^T  C ]
+ *
+ * is solved by Schur-complement decomposition (eqs. SCform, SCsolve,
+ * SCsolve1; Algorithm 1):
+ *
+ *     A_i = P L_i D_i L_i^T P^T                      (block factor, step 2)
+ *     S   = C - sum_i B_i^T A_i^{-1} B_i              (Schur assembly, steps 3-6)
+ *     t   = r_g - sum_i B_i^T A_i^{-1} r_i            (RHS reduction, steps 8-11)
+ *     S   = L_s D_s L_s^T,  x_g = S^{-1} t            (dense factor and solve, 12-13)
+ *     x_i = A_i^{-1} (r_i - B_i x_g)                  (local solves, eq. SCsolve1, step 15)
+ *
+ * followed by FP64 iterative refinement on the full K (Sec. 2.1: refinement
+ * improves the accuracy of the direct solve).
+ *
+ * All indices are 0-based int32.  All functions return a kkt_status; none
+ * aborts the process.  Device-side numerical events (perturbed pivots,
+ * refinement that stalls) are reported through kkt_get_info.
+ */
+#ifndef KKT_SCHUR_H
+#define KKT_SCHUR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kkt_handle kkt_handle; /* opaque; owns every device buffer it allocates */
+
+typedef enum {
+  KKT_OK = 0,
+  KKT_ERR_INVALID = 1,       /* malformed pattern, sizes or arguments */
+  KKT_ERR_OOM = 2,           /* a device or host allocation failed */
+  KKT_ERR_CUDA = 3,          /* a CUDA runtime call failed (message in kkt_last_error) */
+  KKT_ERR_ZERO_PIVOT = 4,    /* a pivot was exactly zero and pivot_eps is 0 */
+  KKT_ERR_INERTIA = 5,       /* inertia differs from (N*nP + nC, N*(nA-nP), 0) */
+  KKT_ERR_NOT_CONVERGED = 6, /* refinement did not reach refine_tol */
+  KKT_ERR_TIMEOUT = 7,       /* a bounded device wait ran out */
+  KKT_ERR_STATE = 8          /* call out of order (e.g. solve before factor) */
+} kkt_status;
+
+/* Arithmetic of the Schur contraction (step 3) and of the dense factor of S
+ * (step 12).  The block factors, the residual and the refinement are FP64 in
+ * every mode. */
+typedef enum { KKT_FP64 = 0, KKT_TF32 = 1, KKT_BF16 = 2 } kkt_precision;
+
+/* Sparsity of one arrowhead system.  All arrays are host memory, read during
+ * kkt_analyze only (copied; the caller keeps ownership).
+ *   A (eq. hessianPerm, blocks A_i): every block shares one pattern, given as
+ *     the lower triangle in CSR: row r holds columns a_col[a_rowptr[r] ..
+ *     a_rowptr[r+1]) in strictly increasing order, each <= r, and the last
+ *     one == r (the diagonal must be present).  Rows [0, nP) are primal
+ *     variables (positive pivots expected), rows [nP, nA) multipliers
+ *     (negative pivots expected).
+ *   B: block i's entries are b_blockptr[i] .. b_blockptr[i+1] of b_row
+ *     (in [0, nA)) and b_col (in [0, nC)), sorted by (row, col).
+ *   C: c_kind 0 = diagonal (nC values), 1 = dense symmetric (nC*nC values,
+ *     row-major; only the lower triangle is read).
+ *   a_vals_hint: optional (may be NULL) values of one block in the A pattern.
+ *     They choose each multiplier's pivot partner: the primal neighbour with
+ *     the largest |coupling|, eliminated right before the multiplier.  Without
+ *     a hint the best-connected primal neighbour is used. */
+typedef struct {
+  int32_t N, nA, nP, nC;
+  const int32_t* a_rowptr;
+  const int32_t* a_col;
+  const int32_t* b_blockptr;
+  const int32_t* b_row;
+  const int32_t* b_col;
+  int32_t c_kind;
+  const double* a_vals_hint;
+} kkt_pattern;
+
+typedef struct {
+  kkt_precision prec;  /* arithmetic of the Schur contraction and the factor of S */
+  double refine_tol;   /* target normwise backward error of the refined solution (1e-10) */
+  int32_t max_refine;  /* refinement steps at most (10) */
+  double pivot_eps;    /* |d| < pivot_eps * ||A_i||_max is replaced by +-pivot_eps * ||A_i||_max
+                          with the expected sign and counted; 0 turns the perturbation off */
+  int32_t use_graphs;  /* capture the factor/solve launch sequences in CUDA graphs */
+  int32_t fp64_fallback; /* refactor S in FP64 when refinement stalls in a reduced mode */
+  int32_t reserved[4];
+} kkt_options;
+
+typedef struct {
+  int64_t n_pos, n_neg, n_zero; /* inertia of K from the pivots of all D_i and D_s */
+  int64_t n_perturbed;          /* pivots replaced under pivot_eps */
+  int32_t refine_steps;         /* refinement steps taken by the last kkt_solve */
+  int32_t fell_back_fp64;       /* 1 if the last solve refactored S in FP64 */
+  double rel_residual;          /* eta = ||r-Kx||_inf / (||K||_inf ||x||_inf + ||r||_inf) */
+  double ms_analyze, ms_factor, ms_solve; /* host wall times of the last calls */
+  int64_t nnz_l;                /* strictly lower nonzeros of one block factor */
+  int64_t panel_doubles;        /* stored factor values per block (supernodal panels) */
+  int32_t n_supernodes, n_levels;
+  int32_t k_coupling_rows;      /* k: distinct rows of A carrying a nonzero of B */
+  int32_t w_rows;               /* rows of the elimination-tree reach of those rows */
+  double factor_flops;          /* block-factor flops per block */
+  int64_t device_bytes;         /* device memory held by the handle */
+} kkt_info;
+
+/* Default options: FP64, refine_tol 1e-10, max_refine 10, pivot_eps 1e-20,
+ * graphs on, FP64 fallback on. */
+void kkt_default_options(kkt_options* opt);
+
+/* Symbolic analysis of the pattern: ordering of the shared A pattern,
+ * elimination tree, supernodes, reach of B's rows, gather maps for S and t;
+ * uploads the index structures and allocates every device buffer that the
+ * numeric calls use.  Runs on the current CUDA device.  On success *out owns
+ * all of it until kkt_destroy. */
+kkt_status kkt_analyze(const kkt_pattern* pattern, const kkt_options* opt, kkt_handle** out);
+
+/* Numeric factorization (Algorithm 1 steps 2-6 and 12): block factors,
+ * Schur complement S = C - sum_i B_i^T A_i^{-1} B_i, dense LDL^T of S.
+ *   a_vals: N * nnz(A) doubles, block i at offset i * nnz(A), in the pattern's
+ *           CSR order;  b_vals: nnz(B) doubles in the pattern's entry order;
+ *   c_vals: nC (c_kind 0) or nC*nC (c_kind 1) doubles.
+ *   on_device: 0 = host pointers (copied on `stream`, pageable or pinned),
+ *              1 = device pointers (read until `stream` passes this work).
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ * The call is asynchronous with respect to the host for device inputs; the
+ * inertia and perturbation counts are read by kkt_get_info. */
+kkt_status kkt_factor(kkt_handle* h, const double* a_vals, const double* b_vals,
+                      const double* c_vals, int32_t on_device, void* stream);
+
+/* Solve K x = rhs for nrhs right-hand sides (stacked, each N*nA + nC long)
+ * with the current factorization, refined in FP64 to opt.refine_tol.
+ * rhs and x: host (on_device 0) or device (1) arrays.  Returns
+ * KKT_ERR_NOT_CONVERGED when refinement stops above refine_tol (x then holds
+ * the best iterate).  Synchronizes `stream` (the refinement reads its
+ * residual norm on the host). */
+kkt_status kkt_solve(kkt_handle* h, const double* rhs, double* x, int32_t nrhs, int32_t on_device,
+                     void* stream);
+
+/* Statistics of the handle and of the last factor/solve (synchronizes the
+ * handle's last stream). */
+kkt_status kkt_get_info(kkt_handle* h, kkt_info* info);
+
+/* Frees every device and host buffer of the handle.  NULL is accepted. */
+kkt_status kkt_destroy(kkt_handle* h);
+
+/* Static string for a status code. */
+const char* kkt_status_string(kkt_status s);
+
+/* Text of the last error on this thread ("" if none). */
+const char* kkt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KKT_SCHUR_H */

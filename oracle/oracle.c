@@ -20,7 +20,7 @@
  *      (Algorithm 1, steps 12-13);
  *   5. x_i = A_i^{-1} (r_i - B_i x_g) (eq. SCsolve1);
  *   6. inertia = sign counts of all D_i and D_s (Haynsworth additivity;
- *      Sec. 2 inertia correction).
+ *      the inertia test of Sec. 2.3).
  *
  * Notation follows K = [A B; B^T C] (B_i is nA x nC, right column), i.e. the
  * transpose of the paper's B_i.  Pivots are never perturbed here: an exactly

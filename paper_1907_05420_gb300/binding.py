@@ -1,0 +1,235 @@
+"""ctypes binding of the C ABI in include/kkt_schur.h (argument marshalling only).
+
+Every step of the factor and of the solve runs in the CUDA library
+libkkt_schur.so; this module converts numpy arrays / torch tensors into
+pointers and returns the status.  There is no CPU fallback: if the library
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KKT_FP64, KKT_TF32, KKT_BF16 = 0, 1, 2
+PRECISIONS = {"fp64": KKT_FP64, "tf32": KKT_TF32, "bf16": KKT_BF16}
+
+STATUS = {
+    0: "KKT_OK", 1: "KKT_ERR_INVALID", 2: "KKT_ERR_OOM", 3: "KKT_ERR_CUDA",
+    4: "KKT_ERR_ZERO_PIVOT", 5: "KKT_ERR_INERTIA", 6: "KKT_ERR_NOT_CONVERGED",
+    7: "KKT_ERR_TIMEOUT", 8: "KKT_ERR_STATE",
+}
+
+
+class KKTError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class kkt_pattern(C.Structure):
+    _fields_ = [("N", C.c_int32), ("nA", C.c_int32), ("nP", C.c_int32), ("nC", C.c_int32),
+                ("a_rowptr", C.c_void_p), ("a_col", C.c_void_p), ("b_blockptr", C.c_void_p),
+                ("b_row", C.c_void_p), ("b_col", C.c_void_p), ("c_kind", C.c_int32),
+                ("a_vals_hint", C.c_void_p)]
+
+
+class kkt_options(C.Structure):
+    _fields_ = [("prec", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int32),
+                ("pivot_eps", C.c_double), ("use_graphs", C.c_int32),
+                ("fp64_fallback", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+class kkt_info(C.Structure):
+    _fields_ = [("n_pos", C.c_int64), ("n_neg", C.c_int64), ("n_zero", C.c_int64),
+                ("n_perturbed", C.c_int64), ("refine_steps", C.c_int32),
+                ("fell_back_fp64", C.c_int32), ("rel_residual", C.c_double),
+                ("ms_analyze", C.c_double), ("ms_factor", C.c_double), ("ms_solve", C.c_double),
+                ("nnz_l", C.c_int64), ("panel_doubles", C.c_int64), ("n_supernodes", C.c_int32),
+                ("n_levels", C.c_int32), ("k_coupling_rows", C.c_int32), ("w_rows", C.c_int32),
+                ("factor_flops", C.c_double), ("device_bytes", C.c_int64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+# every symbol the header declares
+EXPORTS = ["kkt_default_options", "kkt_analyze", "kkt_factor", "kkt_solve", "kkt_get_info",
+           "kkt_destroy", "kkt_status_string", "kkt_last_error"]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libkkt_schur.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise OSError(f"CUDA library not built: {path}")
+    L = C.CDLL(path)
+    L.kkt_default_options.argtypes = [C.POINTER(kkt_options)]
+    L.kkt_default_options.restype = None
+    L.kkt_analyze.argtypes = [C.POINTER(kkt_pattern), C.POINTER(kkt_options), C.POINTER(C.c_void_p)]
+    L.kkt_analyze.restype = C.c_int
+    L.kkt_factor.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
+    L.kkt_factor.restype = C.c_int
+    L.kkt_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]
+    L.kkt_solve.restype = C.c_int
+    L.kkt_get_info.argtypes = [C.c_void_p, C.POINTER(kkt_info)]
+    L.kkt_get_info.restype = C.c_int
+    L.kkt_destroy.argtypes = [C.c_void_p]
+    L.kkt_destroy.restype = C.c_int
+    L.kkt_status_string.argtypes = [C.c_int]
+    L.kkt_status_string.restype = C.c_char_p
+    L.kkt_last_error.argtypes = []
+    L.kkt_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status, allow=()):
+    if status != 0 and status not in allow:
+        L = load()
+        raise KKTError(status, L.kkt_last_error().decode(errors="replace"))
+    return status
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data, 0
+    # torch tensor
+    if not a.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return a.data_ptr(), 1 if a.is_cuda else 0
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:  # pragma: no cover
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def kkt_default_options(prec="fp64", **kw) -> kkt_options:
+    opt = kkt_options()
+    load().kkt_default_options(C.byref(opt))
+    opt.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    for k, v in kw.items():
+        setattr(opt, k, v)
+    return opt
+
+
+def kkt_analyze(prob, opt: kkt_options | None = None, hint=True):
+    """Analyze the pattern of `prob` (any object with the KKTProblem fields).
+
+    Returns an opaque handle (int).  Host arrays are read during the call only.
+    """
+    L = load()
+    keep = {
+        "a_rowptr": np.ascontiguousarray(prob.a_rowptr, dtype=np.int32),
+        "a_col": np.ascontiguousarray(prob.a_col, dtype=np.int32),
+        "b_blockptr": np.ascontiguousarray(prob.b_blockptr, dtype=np.int32),
+        "b_row": np.ascontiguousarray(prob.b_row, dtype=np.int32),
+        "b_col": np.ascontiguousarray(prob.b_col, dtype=np.int32),
+    }
+    hint_arr = None
+    if hint:
+        hint_arr = np.ascontiguousarray(np.asarray(prob.a_vals).reshape(prob.N, -1)[0], dtype=np.float64)
+    pat = kkt_pattern(int(prob.N), int(prob.nA), int(prob.nP), int(prob.nC),
+                      keep["a_rowptr"].ctypes.data, keep["a_col"].ctypes.data,
+                      keep["b_blockptr"].ctypes.data, keep["b_row"].ctypes.data,
+                      keep["b_col"].ctypes.data, int(prob.c_kind),
+                      hint_arr.ctypes.data if hint_arr is not None else None)
+    if opt is None:
+        opt = kkt_default_options()
+    h = C.c_void_p()
+    _check(L.kkt_analyze(C.byref(pat), C.byref(opt), C.byref(h)))
+    return h.value
+
+
+def kkt_factor(h, a_vals, b_vals, c_vals, stream=None):
+    pa, da = _ptr(a_vals)
+    pb, db = _ptr(b_vals)
+    pc, dc = _ptr(c_vals)
+    if len({da, db, dc}) != 1:
+        raise ValueError("a_vals, b_vals and c_vals must all be host or all device arrays")
+    return _check(load().kkt_factor(h, pa, pb, pc, da, _stream_ptr(stream)))
+
+
+def kkt_solve(h, rhs, x, nrhs=1, stream=None, allow_not_converged=False):
+    pr, dr = _ptr(rhs)
+    px, dx = _ptr(x)
+    if dr != dx:
+        raise ValueError("rhs and x must both be host or both device arrays")
+    allow = (6,) if allow_not_converged else ()
+    return _check(load().kkt_solve(h, pr, px, int(nrhs), dr, _stream_ptr(stream)), allow)
+
+
+def kkt_get_info(h) -> dict:
+    info = kkt_info()
+    _check(load().kkt_get_info(h, C.byref(info)))
+    return info.as_dict()
+
+
+def kkt_destroy(h):
+    if h:
+        _check(load().kkt_destroy(h))
+
+
+class KKTSolver:
+    """Convenience owner of one handle: analyze once, then factor/solve."""
+
+    def __init__(self, prob, prec="fp64", **opts):
+        self.prob = prob
+        self.opt = kkt_default_options(prec, **opts)
+        self.h = kkt_analyze(prob, self.opt)
+
+    def factor(self, a_vals=None, b_vals=None, c_vals=None, stream=None):
+        p = self.prob
+        a = np.ascontiguousarray(p.a_vals, dtype=np.float64) if a_vals is None else a_vals
+        b = np.ascontiguousarray(p.b_vals, dtype=np.float64) if b_vals is None else b_vals
+        c = np.ascontiguousarray(p.c_vals, dtype=np.float64) if c_vals is None else c_vals
+        return kkt_factor(self.h, a, b, c, stream)
+
+    def solve(self, rhs=None, stream=None, allow_not_converged=False):
+        r = np.ascontiguousarray(self.prob.rhs if rhs is None else rhs, dtype=np.float64)
+        x = np.empty_like(r)
+        kkt_solve(self.h, r, x, 1, stream, allow_not_converged)
+        return x
+
+    def info(self):
+        return kkt_get_info(self.h)
+
+    def close(self):
+        if self.h:
+            kkt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

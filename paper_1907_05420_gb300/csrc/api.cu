@@ -1,0 +1,408 @@
+// C ABI: kkt_analyze / kkt_factor / kkt_solve / kkt_get_info / kkt_destroy.
+//
+// Host orchestration only: every arithmetic step of the factor and of the
+// solve runs in the kernels of factor.cu, schur.cu, dense.cu and solve.cu.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "handle.h"
+
+namespace kkt {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& v, int64_t& bytes) {
+  size_t n = v.empty() ? 1 : v.size();
+  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * n);
+  if (e != cudaSuccess) return e;
+  bytes += (int64_t)(sizeof(T) * n);
+  if (!v.empty()) e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+template <class T>
+cudaError_t dalloc(T** dst, int64_t count, int64_t& bytes) {
+  size_t n = count > 0 ? (size_t)count : 1;
+  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * n);
+  if (e == cudaSuccess) bytes += (int64_t)(sizeof(T) * n);
+  return e;
+}
+
+kkt_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return KKT_OK;
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? KKT_ERR_OOM : KKT_ERR_CUDA;
+}
+
+void free_all(Handle* h) {
+  void* ptrs[] = {h->d.sn_first, h->d.sn_rowptr, h->d.sn_rows, h->d.sn_valoff, h->d.upd_ptr,
+                  h->d.upd_src, h->d.upd_r0, h->d.upd_r1, h->d.upd_reloff, h->d.upd_rel,
+                  h->d.lvl_sn, h->d.perm, h->d.a_map, h->d.col_primal, h->d.col_dpos, h->d.fwork,
+                  h->d.full_rowptr, h->d.full_col, h->d.full_src, h->d.b_row, h->d.b_col,
+                  h->d.b_blockptr, h->d.e_t, h->d.e_block, h->d.wpos, h->d.sn_wrow, h->d.w_dpos,
+                  h->d.w_col, h->d.reach_lvl_sn, h->d.s_key, h->d.s_ptr, h->d.s_e1, h->d.s_e2,
+                  h->d.t_ptr, h->d.t_e, h->d.bt_ptr, h->d.E, h->Lx, h->a_vals, h->b_vals,
+                  h->c_vals, h->anorm, h->W, h->G, h->S, h->Ypanel, h->knorm, h->counters, h->r,
+                  h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->host_red) cudaFreeHost(h->host_red);
+  if (h->ev_f0) cudaEventDestroy(h->ev_f0);
+  if (h->ev_f1) cudaEventDestroy(h->ev_f1);
+}
+
+}  // namespace
+}  // namespace kkt
+
+using namespace kkt;
+
+extern "C" {
+
+void kkt_default_options(kkt_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->prec = KKT_FP64;
+  opt->refine_tol = 1e-10;
+  opt->max_refine = 10;
+  opt->pivot_eps = 1e-20;
+  opt->use_graphs = 1;
+  opt->fp64_fallback = 1;
+}
+
+const char* kkt_status_string(kkt_status s) {
+  switch (s) {
+    case KKT_OK: return "ok";
+    case KKT_ERR_INVALID: return "invalid argument";
+    case KKT_ERR_OOM: return "out of memory";
+    case KKT_ERR_CUDA: return "CUDA error";
+    case KKT_ERR_ZERO_PIVOT: return "zero pivot";
+    case KKT_ERR_INERTIA: return "wrong inertia";
+    case KKT_ERR_NOT_CONVERGED: return "refinement did not converge";
+    case KKT_ERR_TIMEOUT: return "device wait timed out";
+    case KKT_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* kkt_last_error(void) { return g_last_error.c_str(); }
+
+kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handle** out) {
+  if (!pat || !out) {
+    set_error("kkt_analyze: null argument");
+    return KKT_ERR_INVALID;
+  }
+  *out = nullptr;
+  if (!pat->a_rowptr || !pat->a_col || !pat->b_blockptr || (pat->c_kind != 0 && pat->c_kind != 1) ||
+      pat->N <= 0 || pat->nA <= 0 || pat->nC < 0) {
+    set_error("kkt_analyze: malformed pattern descriptor");
+    return KKT_ERR_INVALID;
+  }
+  const int64_t nnzB = pat->b_blockptr[pat->N];
+  if (nnzB > 0 && (!pat->b_row || !pat->b_col)) {
+    set_error("kkt_analyze: B has entries but no row/col arrays");
+    return KKT_ERR_INVALID;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  Handle* h = new (std::nothrow) Handle();
+  if (!h) return KKT_ERR_OOM;
+  kkt_default_options(&h->opt);
+  if (opt) h->opt = *opt;
+  h->N = pat->N;
+  h->nA = pat->nA;
+  h->nP = pat->nP;
+  h->nC = pat->nC;
+  h->c_kind = pat->c_kind;
+
+  std::string err = analyze_pattern(pat->nA, pat->nP, pat->a_rowptr, pat->a_col, pat->a_vals_hint,
+                                    pat->a_vals_hint ? 1 : 0, h->sym);
+  if (err.empty())
+    err = analyze_coupling(h->sym, pat->N, pat->nC, pat->b_blockptr, pat->b_row, pat->b_col, h->cpl);
+  if (!err.empty()) {
+    set_error("kkt_analyze: " + err);
+    delete h;
+    return KKT_ERR_INVALID;
+  }
+  const Symbolic& S = h->sym;
+  const Coupling& C = h->cpl;
+  const int32_t n = S.n;
+  h->nnzA = pat->a_rowptr[n];
+  h->nnzB = nnzB;
+  h->lvl_ptr = S.lvl_ptr;
+  h->reach_lvl_ptr = C.reach_lvl_ptr;
+
+  // factor work items: 64-row tiles of every supernode, grouped by level
+  std::vector<int32_t> fwork;
+  h->fwork_lvl_ptr.assign(S.nlevels + 1, 0);
+  for (int l = 0; l < S.nlevels; l++) {
+    for (int q = S.lvl_ptr[l]; q < S.lvl_ptr[l + 1]; q++) {
+      int s = S.lvl_sn[q];
+      int m = (int)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]);
+      for (int lo = 0; lo < m; lo += 64) {
+        fwork.push_back(s);
+        fwork.push_back(lo);
+        fwork.push_back(std::min(m, lo + 64));
+      }
+    }
+    h->fwork_lvl_ptr[l + 1] = (int32_t)(fwork.size() / 3);
+  }
+  // per-column pivot position and primal flag
+  std::vector<int64_t> col_dpos(n);
+  std::vector<int32_t> col_primal(n);
+  for (int s = 0; s < S.nsuper; s++) {
+    int f = S.sn_first[s], w = S.sn_first[s + 1] - f;
+    int64_t m = S.sn_rowptr[s + 1] - S.sn_rowptr[s];
+    for (int c = 0; c < w; c++) col_dpos[f + c] = S.sn_valoff[s] + (int64_t)c * m + c;
+  }
+  for (int j = 0; j < n; j++) col_primal[j] = S.perm[j] < S.nP ? 1 : 0;
+  // W rows
+  std::vector<int64_t> w_dpos(C.nw);
+  std::vector<int32_t> w_col(C.nw);
+  for (int s = 0; s < S.nsuper; s++) {
+    if (C.sn_wrow[s] < 0) continue;
+    int f = S.sn_first[s], w = S.sn_first[s + 1] - f;
+    for (int c = 0; c < w; c++) {
+      w_col[C.sn_wrow[s] + c] = f + c;
+      w_dpos[C.sn_wrow[s] + c] = col_dpos[f + c];
+    }
+  }
+  // symmetric full CSR of A with source positions
+  std::vector<int32_t> full_rowptr(n + 1, 0), full_col, full_src;
+  for (int r = 0; r < n; r++)
+    for (int p = pat->a_rowptr[r]; p < pat->a_rowptr[r + 1]; p++) {
+      full_rowptr[r + 1]++;
+      if (pat->a_col[p] != r) full_rowptr[pat->a_col[p] + 1]++;
+    }
+  for (int r = 0; r < n; r++) full_rowptr[r + 1] += full_rowptr[r];
+  full_col.resize(full_rowptr[n]);
+  full_src.resize(full_rowptr[n]);
+  {
+    std::vector<int32_t> fill(full_rowptr.begin(), full_rowptr.end() - 1);
+    for (int r = 0; r < n; r++)
+      for (int p = pat->a_rowptr[r]; p < pat->a_rowptr[r + 1]; p++) {
+        int c = pat->a_col[p];
+        full_col[fill[r]] = c;
+        full_src[fill[r]++] = p;
+        if (c != r) {
+          full_col[fill[c]] = r;
+          full_src[fill[c]++] = p;
+        }
+      }
+  }
+  h->nnzFull = full_rowptr[n];
+  std::vector<int32_t> b_row(pat->b_row ? pat->b_row : nullptr, pat->b_row ? pat->b_row + nnzB : nullptr);
+  std::vector<int32_t> b_col(pat->b_col ? pat->b_col : nullptr, pat->b_col ? pat->b_col + nnzB : nullptr);
+  std::vector<int32_t> b_blockptr(pat->b_blockptr, pat->b_blockptr + pat->N + 1);
+
+  int64_t& by = h->device_bytes;
+  cudaError_t e = cudaSuccess;
+#define UP(dst, vec) \
+  if (e == cudaSuccess) e = upload(&h->d.dst, vec, by)
+  UP(sn_first, S.sn_first);
+  UP(sn_rowptr, S.sn_rowptr);
+  UP(sn_rows, S.sn_rows);
+  UP(sn_valoff, S.sn_valoff);
+  UP(upd_ptr, S.upd_ptr);
+  UP(upd_src, S.upd_src);
+  UP(upd_r0, S.upd_r0);
+  UP(upd_r1, S.upd_r1);
+  UP(upd_reloff, S.upd_reloff);
+  UP(upd_rel, S.upd_rel);
+  UP(lvl_sn, S.lvl_sn);
+  UP(perm, S.perm);
+  UP(a_map, S.a_map);
+  UP(col_primal, col_primal);
+  UP(col_dpos, col_dpos);
+  UP(fwork, fwork);
+  UP(full_rowptr, full_rowptr);
+  UP(full_col, full_col);
+  UP(full_src, full_src);
+  UP(b_row, b_row);
+  UP(b_col, b_col);
+  UP(b_blockptr, b_blockptr);
+  UP(e_t, C.e_t);
+  UP(e_block, C.e_block);
+  UP(wpos, C.wpos);
+  UP(sn_wrow, C.sn_wrow);
+  UP(w_dpos, w_dpos);
+  UP(w_col, w_col);
+  UP(reach_lvl_sn, C.reach_lvl_sn);
+  UP(s_key, C.s_key);
+  UP(s_ptr, C.s_ptr);
+  UP(s_e1, C.s_e1);
+  UP(s_e2, C.s_e2);
+  UP(t_ptr, C.t_ptr);
+  UP(t_e, C.t_e);
+  UP(bt_ptr, C.bt_ptr);
+  UP(E, C.E);
+#undef UP
+  const int64_t nK = (int64_t)h->N * n + h->nC;
+  const int64_t k = C.k;
+#define AL(dst, T, cnt) \
+  if (e == cudaSuccess) e = dalloc<T>(&h->dst, cnt, by)
+  AL(Lx, double, S.panel_total * h->N);
+  AL(a_vals, double, h->nnzA * h->N);
+  AL(b_vals, double, nnzB);
+  AL(c_vals, double, h->c_kind == 0 ? (int64_t)h->nC : (int64_t)h->nC * h->nC);
+  AL(anorm, double, h->N);
+  AL(W, double, (int64_t)C.nw * k * h->N);
+  AL(G, double, k * k * h->N);
+  AL(S, double, (int64_t)h->nC * h->nC);
+  AL(Ypanel, double, (int64_t)h->nC * kDenseNB);
+  AL(knorm, double, 1);
+  AL(counters, unsigned long long, kNumCounters);
+  AL(z, double, (int64_t)h->N * n);
+  AL(u, double, k * h->N);
+  AL(v, double, k * h->N);
+  AL(tg, double, h->nC);
+  AL(xg, double, h->nC);
+  AL(x, double, nK);
+  AL(dx, double, nK);
+  AL(rho, double, nK);
+  AL(rhs, double, nK);
+  AL(red, double, 128);
+#undef AL
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->host_red, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev_f0);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev_f1);
+  if (e != cudaSuccess) {
+    kkt_status st = cuda_status(e, "kkt_analyze");
+    free_all(h);
+    delete h;
+    return st;
+  }
+  h->info.nnz_l = S.nnzL;
+  h->info.panel_doubles = S.panel_total;
+  h->info.n_supernodes = S.nsuper;
+  h->info.n_levels = S.nlevels;
+  h->info.k_coupling_rows = C.k;
+  h->info.w_rows = C.nw;
+  h->info.factor_flops = S.flops;
+  h->info.ms_analyze =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = reinterpret_cast<kkt_handle*>(h);
+  return KKT_OK;
+}
+
+kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals,
+                      const double* c_vals, int32_t on_device, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !a_vals || (h->nnzB > 0 && !b_vals) || (h->nC > 0 && !c_vals)) {
+    set_error("kkt_factor: null argument");
+    return KKT_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  h->stream = st;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const int64_t nc_vals = h->c_kind == 0 ? (int64_t)h->nC : (int64_t)h->nC * h->nC;
+  KKT_CUDA(cudaEventRecord(h->ev_f0, st));
+  KKT_CUDA(cudaMemcpyAsync(h->a_vals, a_vals, sizeof(double) * h->nnzA * h->N, kind, st));
+  if (h->nnzB > 0) KKT_CUDA(cudaMemcpyAsync(h->b_vals, b_vals, sizeof(double) * h->nnzB, kind, st));
+  if (nc_vals > 0) KKT_CUDA(cudaMemcpyAsync(h->c_vals, c_vals, sizeof(double) * nc_vals, kind, st));
+  KKT_CUDA(cudaMemsetAsync(h->counters, 0, sizeof(long long) * kNumCounters, st));
+  KKT_CUDA(launch_scatter_a(*h, st));
+  KKT_CUDA(launch_factor_levels(*h, st));
+  KKT_CUDA(launch_w_solve(*h, st));
+  KKT_CUDA(launch_contract_g(*h, st));
+  KKT_CUDA(launch_assemble_s(*h, st));
+  KKT_CUDA(launch_dense_ldlt(*h, st));
+  KKT_CUDA(launch_knorm(*h, st));
+  KKT_CUDA(cudaEventRecord(h->ev_f1, st));
+  h->factored = true;
+  h->timed_factor = true;
+  return KKT_OK;
+}
+
+kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs, int32_t on_device,
+                     void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !rhs || !x || nrhs < 1) {
+    set_error("kkt_solve: invalid argument");
+    return KKT_ERR_INVALID;
+  }
+  if (!h->factored) {
+    set_error("kkt_solve: no factorization");
+    return KKT_ERR_STATE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  h->stream = st;
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t nK = (int64_t)h->N * h->nA + h->nC;
+  kkt_status result = KKT_OK;
+  for (int32_t q = 0; q < nrhs; q++) {
+    const double* rq = rhs + q * nK;
+    double* xq = x + q * nK;
+    KKT_CUDA(cudaMemcpyAsync(h->rhs, rq, sizeof(double) * nK,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    KKT_CUDA(launch_apply_inverse(*h, h->rhs, h->x, st));
+    int steps = 0;
+    double eta = INFINITY, eta_prev = INFINITY;
+    for (;;) {
+      KKT_CUDA(launch_residual(*h, h->rhs, h->x, h->rho, st));
+      KKT_CUDA(launch_norms(*h, h->rho, h->x, h->rhs, st));
+      KKT_CUDA(cudaMemcpyAsync(h->host_red, h->red, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+      KKT_CUDA(cudaMemcpyAsync(h->host_red + 3, h->knorm, sizeof(double), cudaMemcpyDeviceToHost, st));
+      KKT_CUDA(cudaStreamSynchronize(st));
+      const double* hr = h->host_red;
+      eta = hr[0] / (hr[3] * hr[1] + hr[2]);
+      if (!(hr[0] > 0.0)) eta = 0.0;
+      if (eta <= h->opt.refine_tol || steps >= h->opt.max_refine) break;
+      if (steps > 0 && !(eta < 0.5 * eta_prev)) break;  // stalled
+      eta_prev = eta;
+      KKT_CUDA(launch_apply_inverse(*h, h->rho, h->dx, st));
+      KKT_CUDA(launch_axpy(h->x, h->dx, nK, st));
+      steps++;
+    }
+    KKT_CUDA(cudaMemcpyAsync(xq, h->x, sizeof(double) * nK,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    h->info.refine_steps = steps;
+    h->info.rel_residual = eta;
+    if (!(eta <= h->opt.refine_tol)) result = KKT_ERR_NOT_CONVERGED;
+  }
+  KKT_CUDA(cudaStreamSynchronize(st));
+  h->info.ms_solve =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (result != KKT_OK) set_error("kkt_solve: refinement stopped above refine_tol");
+  return result;
+}
+
+kkt_status kkt_get_info(kkt_handle* hh, kkt_info* info) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !info) {
+    set_error("kkt_get_info: null argument");
+    return KKT_ERR_INVALID;
+  }
+  KKT_CUDA(cudaStreamSynchronize(h->stream));
+  if (h->factored) {
+    unsigned long long c[kNumCounters];
+    KKT_CUDA(cudaMemcpy(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost));
+    h->info.n_pos = c[kPos];
+    h->info.n_neg = c[kNeg];
+    h->info.n_zero = c[kZero];
+    h->info.n_perturbed = c[kPerturbed];
+    if (h->timed_factor) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, h->ev_f0, h->ev_f1) == cudaSuccess) h->info.ms_factor = ms;
+      h->timed_factor = false;
+    }
+  }
+  h->info.device_bytes = h->device_bytes;
+  *info = h->info;
+  return KKT_OK;
+}
+
+kkt_status kkt_destroy(kkt_handle* hh) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return KKT_OK;
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+  return KKT_OK;
+}
+
+}  // extern "C"

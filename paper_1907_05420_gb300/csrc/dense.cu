@@ -1,0 +1,229 @@
+// (c) Dense LDL^T of the Schur complement, S = L_s D_s L_s^T, and the solve
+// S x_g = t (Algorithm 1, steps 12-13; eq. SCsolve).
+//
+// S is n x n, column-major, lower triangle.  Blocked right-looking, block
+// width kDenseNB = 64, per block column k0:
+//   k_dense_diag:   unblocked LDL^T of the 64 x 64 diagonal block in shared memory;
+//   k_dense_panel:  L21 = A21 L11^{-T} D1^{-1}; Y = L21 D1 kept for the update;
+//   k_dense_update: A22 -= Y L21^T on the lower-triangle 64 x 64 tiles.
+// No pivoting: S is positive definite when the blocks are quasidefinite and C
+// is positive definite; a zero pivot is counted and reported.
+#include "handle.h"
+
+namespace kkt {
+
+namespace {
+
+constexpr int NB = kDenseNB;
+
+__global__ void __launch_bounds__(256) k_dense_diag(double* __restrict__ S, int n, int k0,
+                                                    unsigned long long* __restrict__ counters) {
+  __shared__ double A[NB][NB + 1];
+  const int kb = min(NB, n - k0);
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
+    const int j = q / kb, i = q - j * kb;
+    A[i][j] = S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n];
+  }
+  __syncthreads();
+  for (int c = 0; c < kb; c++) {
+    const double d = A[c][c];
+    for (int r = c + 1 + threadIdx.x; r < kb; r += blockDim.x) A[r][c] = A[r][c] / d;
+    __syncthreads();
+    const int rem = kb - c - 1;
+    for (int q = threadIdx.x; q < rem * rem; q += blockDim.x) {
+      const int c2 = c + 1 + q / rem, r = c + 1 + q % rem;
+      if (r >= c2) A[r][c2] -= A[r][c] * d * A[c2][c];
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
+    const int j = q / kb, i = q - j * kb;
+    if (i >= j) S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n] = A[i][j];
+  }
+  if (threadIdx.x == 0) {
+    unsigned long long pos = 0, neg = 0, zero = 0;
+    for (int c = 0; c < kb; c++) {
+      const double d = A[c][c];
+      if (d > 0) pos++;
+      else if (d < 0) neg++;
+      else zero++;
+    }
+    atomicAdd(&counters[kPos], pos);
+    atomicAdd(&counters[kNeg], neg);
+    if (zero) atomicAdd(&counters[kZero], zero);
+  }
+}
+
+// rows k0+kb .. n-1: solve y L11^T = a per row, L21 = y / D, Y = y
+__global__ void __launch_bounds__(64) k_dense_panel(double* __restrict__ S, double* __restrict__ Y,
+                                                    int n, int k0) {
+  __shared__ double L11[NB][NB + 1];
+  const int kb = min(NB, n - k0);
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
+    const int j = q / kb, i = q - j * kb;
+    L11[i][j] = S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n];
+  }
+  __syncthreads();
+  const int row = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  double y[NB];
+#pragma unroll
+  for (int c = 0; c < NB; c++) y[c] = c < kb ? S[row + (int64_t)(k0 + c) * n] : 0.0;
+#pragma unroll
+  for (int c = 0; c < NB; c++) {
+    if (c < kb) {
+#pragma unroll
+      for (int c2 = 0; c2 < c; c2++) y[c] -= y[c2] * L11[c][c2];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NB; c++) {
+    if (c < kb) {
+      Y[row + (int64_t)c * n] = y[c];
+      S[row + (int64_t)(k0 + c) * n] = y[c] / L11[c][c];
+    }
+  }
+}
+
+// trailing update on lower tiles: A[i][j] -= sum_c Y[i][c] L[j][c]
+__global__ void __launch_bounds__(256) k_dense_update(double* __restrict__ S, const double* __restrict__ Y,
+                                                      int n, int k0) {
+  const int kb = min(NB, n - k0);
+  const int base = k0 + kb;
+  int tile = blockIdx.x, ti = 0;
+  while (tile > ti) {
+    tile -= ti + 1;
+    ti++;
+  }
+  const int tj = tile;
+  const int i0 = base + ti * 64, j0 = base + tj * 64;
+  constexpr int KC = 32;              // columns staged per pass
+  __shared__ double Ys[KC][64 + 1];  // [c][i]
+  __shared__ double Ls[KC][64 + 1];  // [c][j]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16, 4x4 outputs each
+  double acc[4][4] = {};
+  for (int cb = 0; cb < kb; cb += KC) {
+    const int kc = min(KC, kb - cb);
+    __syncthreads();
+    for (int q = threadIdx.x; q < kc * 64; q += 256) {
+      const int c = q / 64, r = q % 64;
+      Ys[c][r] = (i0 + r < n) ? Y[(i0 + r) + (int64_t)(cb + c) * n] : 0.0;
+      Ls[c][r] = (j0 + r < n) ? S[(j0 + r) + (int64_t)(k0 + cb + c) * n] : 0.0;
+    }
+    __syncthreads();
+    for (int c = 0; c < kc; c++) {
+      double a[4], bb[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        a[u] = Ys[c][ty + 16 * u];
+        bb[u] = Ls[c][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) acc[u][v] += a[u] * bb[v];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+      if (i < n && j < n && i >= j) S[i + (int64_t)j * n] -= acc[u][v];
+    }
+}
+
+// forward substitution with unit lower L: diagonal block of one block column
+__global__ void k_dense_fwd_diag(const double* __restrict__ S, double* __restrict__ x, int n, int k0) {
+  const int kb = min(NB, n - k0);
+  if (threadIdx.x != 0) return;
+  for (int c = 0; c < kb; c++) {
+    double v = x[k0 + c];
+    for (int c2 = 0; c2 < c; c2++) v -= S[(k0 + c) + (int64_t)(k0 + c2) * n] * x[k0 + c2];
+    x[k0 + c] = v;
+  }
+}
+
+// x[i] -= sum_{c in block} L[i][c] x[c] for rows below the block
+__global__ void k_dense_fwd_update(const double* __restrict__ S, double* __restrict__ x, int n, int k0) {
+  const int kb = min(NB, n - k0);
+  const int i = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int c = 0; c < kb; c++) acc += S[i + (int64_t)(k0 + c) * n] * x[k0 + c];
+  x[i] -= acc;
+}
+
+__global__ void k_dense_diag_scale(const double* __restrict__ S, double* __restrict__ x, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x[i] /= S[i + (int64_t)i * n];
+}
+
+// dot[c] = sum_{i >= k0+kb} L[i][k0+c] x[i]
+__global__ void k_dense_bwd_dot(const double* __restrict__ S, const double* __restrict__ x,
+                                double* __restrict__ dot, int n, int k0) {
+  const int kb = min(NB, n - k0);
+  const int c = blockIdx.x;
+  if (c >= kb) return;
+  __shared__ double red[256];
+  double acc = 0.0;
+  const double* col = S + (int64_t)(k0 + c) * n;
+  for (int i = k0 + kb + threadIdx.x; i < n; i += blockDim.x) acc += col[i] * x[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dot[c] = red[0];
+}
+
+__global__ void k_dense_bwd_diag(const double* __restrict__ S, double* __restrict__ x,
+                                 const double* __restrict__ dot, int n, int k0) {
+  const int kb = min(NB, n - k0);
+  if (threadIdx.x != 0) return;
+  for (int c = kb - 1; c >= 0; c--) {
+    double v = x[k0 + c] - dot[c];
+    for (int c2 = c + 1; c2 < kb; c2++) v -= S[(k0 + c2) + (int64_t)(k0 + c) * n] * x[k0 + c2];
+    x[k0 + c] = v;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_dense_ldlt(Handle& h, cudaStream_t st) {
+  const int n = h.nC;
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = std::min(NB, n - k0);
+    k_dense_diag<<<1, 256, 0, st>>>(h.S, n, k0, h.counters);
+    const int rest = n - k0 - kb;
+    if (rest > 0) {
+      k_dense_panel<<<(rest + 63) / 64, 64, 0, st>>>(h.S, h.Ypanel, n, k0);
+      const int T = (rest + 63) / 64;
+      k_dense_update<<<T * (T + 1) / 2, 256, 0, st>>>(h.S, h.Ypanel, n, k0);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_solve(Handle& h, const double* t, double* x, cudaStream_t st) {
+  const int n = h.nC;
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = cudaMemcpyAsync(x, t, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = std::min(NB, n - k0);
+    k_dense_fwd_diag<<<1, 32, 0, st>>>(h.S, x, n, k0);
+    const int rest = n - k0 - kb;
+    if (rest > 0) k_dense_fwd_update<<<(rest + 255) / 256, 256, 0, st>>>(h.S, x, n, k0);
+  }
+  k_dense_diag_scale<<<(n + 255) / 256, 256, 0, st>>>(h.S, x, n);
+  const int last = ((n - 1) / NB) * NB;
+  for (int k0 = last; k0 >= 0; k0 -= NB) {
+    k_dense_bwd_dot<<<NB, 256, 0, st>>>(h.S, x, h.red + 8, n, k0);
+    k_dense_bwd_diag<<<1, 32, 0, st>>>(h.S, x, h.red + 8, n, k0);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace kkt

@@ -1,0 +1,168 @@
+// (a) Batched numeric LDL^T of the N blocks A_i = P L_i D_i L_i^T P^T
+// (Algorithm 1, step 2), all blocks sharing one supernodal structure.
+//
+// Storage: block b's factor is one contiguous array of supernode panels;
+// panel s is column-major m_s x w_s (its rows are sn_rows[s], the first w_s of
+// them its own columns).  The diagonal of the w_s x w_s top block holds D,
+// the rest of the panel holds L (unit diagonal implied).
+//
+// Schedule: supernodes are processed level by level of the supernodal
+// elimination tree.  Per level two launches:
+//   k_factor_update: left-looking updates of every supernode s of the level
+//     from its descendants d,  P_s[rel(i), j - f_s] -= sum_k L_d[i,k] D_d[k] L_d[j,k],
+//     one CTA per (64-row tile of s, block) so that the wide supernodes at the
+//     top of the tree spread over many SMs;
+//   k_panel_factor: dense LDL^T of the panel (1x1 pivots; a pivot below
+//     pivot_eps*max|A_i| is replaced by the expected-sign value and counted).
+// Every entry is written by one thread in a fixed order: the result does not
+// depend on scheduling.
+#include "handle.h"
+
+namespace kkt {
+
+namespace {
+
+__global__ void k_scatter_a(const double* __restrict__ a_vals, int64_t nnzA,
+                            const int64_t* __restrict__ a_map, double* __restrict__ Lx,
+                            int64_t pt, int N) {
+  const int64_t total = nnzA * (int64_t)N;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = q / nnzA, p = q - b * nnzA;
+    Lx[b * pt + a_map[p]] = a_vals[q];
+  }
+}
+
+// max |a| of each block (threshold base of the pivot perturbation)
+__global__ void k_block_absmax(const double* __restrict__ a_vals, int64_t nnzA,
+                               double* __restrict__ anorm) {
+  __shared__ double red[256];
+  const double* a = a_vals + blockIdx.x * nnzA;
+  double m = 0.0;
+  for (int64_t p = threadIdx.x; p < nnzA; p += blockDim.x) m = fmax(m, fabs(a[p]));
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) anorm[blockIdx.x] = red[0];
+}
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_factor_update(const int32_t* __restrict__ work, DevSym d,
+                                                       double* __restrict__ Lx, int64_t pt) {
+  const int item = blockIdx.x, b = blockIdx.y;
+  const int s = work[3 * item], lo = work[3 * item + 1], hi = work[3 * item + 2];
+  const int ms = (int)(d.sn_rowptr[s + 1] - d.sn_rowptr[s]);
+  const int f = d.sn_first[s];
+  double* P = Lx + b * pt + d.sn_valoff[s];
+  __shared__ int range[2];
+  for (int64_t u = d.upd_ptr[s]; u < d.upd_ptr[s + 1]; u++) {
+    const int dd = d.upd_src[u];
+    const int r0 = d.upd_r0[u], r1 = d.upd_r1[u];
+    const int md = (int)(d.sn_rowptr[dd + 1] - d.sn_rowptr[dd]);
+    const int wd = d.sn_first[dd + 1] - d.sn_first[dd];
+    const double* Pd = Lx + b * pt + d.sn_valoff[dd];
+    const int32_t* Rd = d.sn_rows + d.sn_rowptr[dd];
+    const int32_t* rel = d.upd_rel + d.upd_reloff[u];
+    if (threadIdx.x == 0) {
+      range[0] = r0 + lower_bound_i32(rel, md - r0, lo);
+      range[1] = r0 + lower_bound_i32(rel, md - r0, hi);
+    }
+    __syncthreads();
+    const int ia = range[0], ni = range[1] - range[0], nj = r1 - r0;
+    const int total = ni * nj;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      const int i = ia + q % ni, j = r0 + q / ni;
+      if (i < j) continue;
+      double acc = 0.0;
+      for (int kk = 0; kk < wd; kk++) {
+        const double* col = Pd + (int64_t)kk * md;
+        acc += col[i] * col[kk] * col[j];
+      }
+      P[(int64_t)(Rd[j] - f) * ms + rel[i - r0]] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_panel_factor(const int32_t* __restrict__ lvl_sn, DevSym d,
+                                                      double* __restrict__ Lx, int64_t pt,
+                                                      const double* __restrict__ anorm,
+                                                      double pivot_eps,
+                                                      unsigned long long* __restrict__ counters) {
+  const int s = lvl_sn[blockIdx.x], b = blockIdx.y;
+  const int m = (int)(d.sn_rowptr[s + 1] - d.sn_rowptr[s]);
+  const int f = d.sn_first[s], w = d.sn_first[s + 1] - f;
+  double* P = Lx + b * pt + d.sn_valoff[s];
+  const double thr = pivot_eps * anorm[b];
+  __shared__ double dsh;
+  __shared__ int cnt[4];
+  if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
+  for (int c = 0; c < w; c++) {
+    if (threadIdx.x == 0) {
+      double dv = P[(int64_t)c * m + c];
+      const bool primal = d.col_primal[f + c] != 0;
+      if (thr > 0.0 && fabs(dv) < thr) {
+        dv = primal ? thr : -thr;
+        cnt[3]++;
+      }
+      P[(int64_t)c * m + c] = dv;
+      cnt[dv > 0.0 ? 0 : (dv < 0.0 ? 1 : 2)]++;
+      dsh = dv;
+    }
+    __syncthreads();
+    const double dv = dsh;
+    double* colc = P + (int64_t)c * m;
+    for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) colc[r] = colc[r] / dv;
+    __syncthreads();
+    for (int c2 = c + 1; c2 < w; c2++) {
+      const double l2 = colc[c2] * dv;
+      double* col2 = P + (int64_t)c2 * m;
+      for (int r = c2 + threadIdx.x; r < m; r += blockDim.x) col2[r] -= colc[r] * l2;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 4 && cnt[threadIdx.x]) atomicAdd(&counters[threadIdx.x], (unsigned long long)cnt[threadIdx.x]);
+}
+
+}  // namespace
+
+cudaError_t launch_scatter_a(Handle& h, cudaStream_t st) {
+  const int64_t pt = h.sym.panel_total;
+  cudaError_t e = cudaMemsetAsync(h.Lx, 0, sizeof(double) * pt * h.N, st);
+  if (e != cudaSuccess) return e;
+  int64_t total = h.nnzA * h.N;
+  int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  k_scatter_a<<<grid, 256, 0, st>>>(h.a_vals, h.nnzA, h.d.a_map, h.Lx, pt, h.N);
+  k_block_absmax<<<h.N, 256, 0, st>>>(h.a_vals, h.nnzA, h.anorm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
+  const int64_t pt = h.sym.panel_total;
+  for (int l = 0; l < h.sym.nlevels; l++) {
+    const int w0 = h.fwork_lvl_ptr[l], w1 = h.fwork_lvl_ptr[l + 1];
+    if (l > 0 && w1 > w0) {
+      dim3 grid(w1 - w0, h.N);
+      k_factor_update<<<grid, 256, 0, st>>>(h.d.fwork + 3 * w0, h.d, h.Lx, pt);
+    }
+    const int s0 = h.lvl_ptr[l], s1 = h.lvl_ptr[l + 1];
+    dim3 grid2(s1 - s0, h.N);
+    k_panel_factor<<<grid2, 256, 0, st>>>(h.d.lvl_sn + s0, h.d, h.Lx, pt, h.anorm, h.opt.pivot_eps,
+                                          h.counters);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace kkt

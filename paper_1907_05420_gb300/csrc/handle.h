@@ -1,0 +1,140 @@
+// Internal state of a kkt_handle: symbolic structures (host and device),
+// numeric buffers, and the kernel entry points shared by the .cu files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/kkt_schur.h"
+#include "symbolic.h"
+
+namespace kkt {
+
+// Records a CUDA error and returns from the enclosing kkt_status function.
+void set_error(const std::string& msg);
+#define KKT_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      ::kkt::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));         \
+      return KKT_ERR_CUDA;                                                          \
+    }                                                                               \
+  } while (0)
+
+// Device copies of the symbolic structures.
+struct DevSym {
+  int32_t* sn_first = nullptr;
+  int64_t* sn_rowptr = nullptr;
+  int32_t* sn_rows = nullptr;
+  int64_t* sn_valoff = nullptr;
+  int64_t* upd_ptr = nullptr;
+  int32_t* upd_src = nullptr;
+  int32_t* upd_r0 = nullptr;
+  int32_t* upd_r1 = nullptr;
+  int64_t* upd_reloff = nullptr;
+  int32_t* upd_rel = nullptr;
+  int32_t* lvl_sn = nullptr;
+  int32_t* perm = nullptr;
+  int64_t* a_map = nullptr;
+  int32_t* col_primal = nullptr;   // per column (elimination order): 1 if primal
+  int64_t* col_dpos = nullptr;     // per column: panel position of its pivot
+  // factor update work items: (supernode, first panel row, last panel row)
+  int32_t* fwork = nullptr;        // 3 ints per item
+  // symmetric full CSR of A for the residual: entry p reads a_vals[full_src[p]]
+  int32_t* full_rowptr = nullptr;
+  int32_t* full_col = nullptr;
+  int32_t* full_src = nullptr;
+  // coupling
+  int32_t* b_row = nullptr;
+  int32_t* b_col = nullptr;
+  int32_t* b_blockptr = nullptr;
+  int32_t* e_t = nullptr;
+  int32_t* e_block = nullptr;
+  int32_t* wpos = nullptr;
+  int32_t* sn_wrow = nullptr;
+  int64_t* w_dpos = nullptr;       // per W row: panel position of its pivot
+  int32_t* w_col = nullptr;        // per W row: its column (elimination order)
+  int32_t* reach_lvl_sn = nullptr;
+  int64_t* s_key = nullptr;
+  int64_t* s_ptr = nullptr;
+  int32_t* s_e1 = nullptr;
+  int32_t* s_e2 = nullptr;
+  int32_t* t_ptr = nullptr;
+  int32_t* t_e = nullptr;
+  int32_t* bt_ptr = nullptr;
+  int32_t* E = nullptr;            // the k rows of A carrying B's nonzeros
+};
+
+// Counters written by the kernels (device, int64).
+enum Counter { kPos = 0, kNeg, kZero, kPerturbed, kNumCounters };
+
+struct Handle {
+  // sizes
+  int32_t N = 0, nA = 0, nP = 0, nC = 0, c_kind = 0;
+  int64_t nnzA = 0, nnzB = 0, nnzFull = 0;
+  kkt_options opt{};
+  Symbolic sym;
+  Coupling cpl;
+  DevSym d;
+  std::vector<int32_t> fwork_lvl_ptr;  // factor work items per level
+  std::vector<int32_t> lvl_ptr;        // supernodes per level (host copy)
+  std::vector<int32_t> reach_lvl_ptr;
+
+  // numeric buffers
+  double* Lx = nullptr;       // N * panel_total
+  double* a_vals = nullptr;   // N * nnzA (FP64 copy for the residual)
+  double* b_vals = nullptr;   // nnzB
+  double* c_vals = nullptr;   // nC or nC*nC
+  double* anorm = nullptr;    // N: max |a| per block
+  double* W = nullptr;        // N * nw * k, row-major per block
+  double* G = nullptr;        // N * k * k
+  double* S = nullptr;        // nC * nC column-major (lower triangle used)
+  double* Ypanel = nullptr;   // nC * kDenseNB scratch of the dense factor
+  double* knorm = nullptr;    // ||K||_inf
+  unsigned long long* counters = nullptr;  // kNumCounters
+  // solve work vectors
+  double* r = nullptr;        // nK: right-hand side being solved
+  double* z = nullptr;        // N * nA
+  double* u = nullptr;        // N * k
+  double* v = nullptr;        // N * k
+  double* tg = nullptr;       // nC
+  double* xg = nullptr;       // nC
+  double* x = nullptr;        // nK iterate
+  double* dx = nullptr;       // nK correction
+  double* rho = nullptr;      // nK residual
+  double* rhs = nullptr;      // nK original right-hand side
+  double* red = nullptr;      // reduction scratch (norms)
+  double* host_red = nullptr; // pinned
+  int64_t device_bytes = 0;
+
+  bool factored = false;
+  bool timed_factor = false;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_f0 = nullptr, ev_f1 = nullptr;
+  kkt_info info{};
+};
+
+constexpr int kDenseNB = 64;
+
+// ---- kernel launchers (factor.cu) ----
+cudaError_t launch_scatter_a(Handle& h, cudaStream_t st);
+cudaError_t launch_factor_levels(Handle& h, cudaStream_t st);
+// ---- (schur.cu) ----
+cudaError_t launch_w_solve(Handle& h, cudaStream_t st);
+cudaError_t launch_contract_g(Handle& h, cudaStream_t st);
+cudaError_t launch_assemble_s(Handle& h, cudaStream_t st);
+// ---- (dense.cu) ----
+cudaError_t launch_dense_ldlt(Handle& h, cudaStream_t st);
+cudaError_t launch_dense_solve(Handle& h, const double* t, double* x, cudaStream_t st);
+// ---- (solve.cu) ----
+cudaError_t launch_apply_inverse(Handle& h, const double* rhs, double* out, cudaStream_t st);
+cudaError_t launch_residual(Handle& h, const double* rhs, const double* x, double* rho,
+                            cudaStream_t st);
+cudaError_t launch_knorm(Handle& h, cudaStream_t st);
+cudaError_t launch_axpy(double* y, const double* x, int64_t n, cudaStream_t st);
+cudaError_t launch_norms(Handle& h, const double* rho, const double* x, const double* rhs,
+                         cudaStream_t st);
+
+}  // namespace kkt

@@ -1,0 +1,187 @@
+// (b) Schur-complement assembly S = C - sum_i B_i^T A_i^{-1} B_i
+// (eq. SCform; Algorithm 1 steps 3-6).
+//
+// With E the k rows of A that carry a nonzero of some B_i, B_i = E M_i and
+//     B_i^T A_i^{-1} B_i = M_i^T G_i M_i,   G_i = W_i^T D_i^{-1} W_i,
+//     W_i = L_i^{-1} P^T E.
+// This is the (2,2) block that the incomplete factorization of the augmented
+// matrix [A_i B_i; B_i^T 0] leaves behind after A_i's last pivot (Sec. 4.2,
+// eq. augmented), computed as
+//   1. k_w_solve:     multi-RHS sparse forward solve, restricted to the
+//                     elimination-tree reach of E (left-looking, level by level);
+//   2. k_contract_g:  the contraction G_i = W_i^T D_i^{-1} W_i;
+//   3. k_assemble_s:  S = C - sum_i M_i^T G_i M_i, each entry of S summed by one
+//                     thread over its contributions in block order (no atomics).
+#include "handle.h"
+
+namespace kkt {
+
+namespace {
+
+__global__ void __launch_bounds__(128) k_w_solve(const int32_t* __restrict__ sn_list, DevSym d,
+                                                 const double* __restrict__ Lx, int64_t pt,
+                                                 double* __restrict__ W, int nw, int k) {
+  const int s = sn_list[blockIdx.x], b = blockIdx.y;
+  const int m = (int)(d.sn_rowptr[s + 1] - d.sn_rowptr[s]);
+  const int f = d.sn_first[s], w = d.sn_first[s + 1] - f;
+  const int ws = d.sn_wrow[s];
+  const double* P = Lx + b * pt + d.sn_valoff[s];
+  double* Wb = W + (int64_t)b * nw * k;
+  for (int q = threadIdx.x; q < w * k; q += blockDim.x) {
+    const int c = q / k, t = q - c * k;
+    Wb[(int64_t)(ws + c) * k + t] = d.wpos[t] == ws + c ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int64_t u = d.upd_ptr[s]; u < d.upd_ptr[s + 1]; u++) {
+    const int dd = d.upd_src[u];
+    const int wrd = d.sn_wrow[dd];
+    if (wrd < 0) continue;  // descendant outside the reach: its W rows are zero
+    const int r0 = d.upd_r0[u], r1 = d.upd_r1[u];
+    const int md = (int)(d.sn_rowptr[dd + 1] - d.sn_rowptr[dd]);
+    const int wd = d.sn_first[dd + 1] - d.sn_first[dd];
+    const double* Pd = Lx + b * pt + d.sn_valoff[dd];
+    const int32_t* Rd = d.sn_rows + d.sn_rowptr[dd];
+    const int total = (r1 - r0) * k;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      const int j = r0 + q / k, t = q % k;
+      double acc = 0.0;
+      for (int kk = 0; kk < wd; kk++) acc += Pd[(int64_t)kk * md + j] * Wb[(int64_t)(wrd + kk) * k + t];
+      Wb[(int64_t)(ws + Rd[j] - f) * k + t] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int c = 0; c + 1 < w; c++) {
+    const int total = (w - 1 - c) * k;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      const int c2 = c + 1 + q / k, t = q % k;
+      Wb[(int64_t)(ws + c2) * k + t] -= P[(int64_t)c * m + c2] * Wb[(int64_t)(ws + c) * k + t];
+    }
+    __syncthreads();
+  }
+}
+
+// G_b = W_b^T D_b^{-1} W_b in FP64, one 32x32 tile of the lower triangle per CTA
+__global__ void __launch_bounds__(256) k_contract_g_f64(const double* __restrict__ W,
+                                                        const double* __restrict__ Lx, int64_t pt,
+                                                        const int64_t* __restrict__ w_dpos, int nw,
+                                                        int k, double* __restrict__ G) {
+  const int b = blockIdx.y;
+  // tile index -> (ti, tj) with ti >= tj
+  int tile = blockIdx.x, ti = 0;
+  while (tile > ti) {
+    tile -= ti + 1;
+    ti++;
+  }
+  const int tj = tile;
+  const int t1_0 = ti * 32, t2_0 = tj * 32;
+  __shared__ double Wa[32][33], Wb_[32][33];
+  const double* Wblk = W + (int64_t)b * nw * k;
+  const double* Pb = Lx + b * pt;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  double acc[4] = {0, 0, 0, 0};
+  for (int r0 = 0; r0 < nw; r0 += 32) {
+    for (int q = threadIdx.x; q < 32 * 32; q += 256) {
+      const int rr = q >> 5, cc = q & 31;
+      const int row = r0 + rr;
+      double a = 0.0, bb = 0.0;
+      if (row < nw) {
+        const double dinv = 1.0 / Pb[w_dpos[row]];
+        if (t1_0 + cc < k) a = Wblk[(int64_t)row * k + t1_0 + cc] * dinv;
+        if (t2_0 + cc < k) bb = Wblk[(int64_t)row * k + t2_0 + cc];
+      }
+      Wa[rr][cc] = a;
+      Wb_[rr][cc] = bb;
+    }
+    __syncthreads();
+    for (int rr = 0; rr < 32; rr++) {
+      const double bv = Wb_[rr][tx];
+#pragma unroll
+      for (int i = 0; i < 4; i++) acc[i] += Wa[rr][ty + 8 * i] * bv;
+    }
+    __syncthreads();
+  }
+  double* Gb = G + (int64_t)b * k * k;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const int t1 = t1_0 + ty + 8 * i, t2 = t2_0 + tx;
+    if (t1 < k && t2 < k) {
+      Gb[(int64_t)t1 * k + t2] = acc[i];
+      if (ti != tj) Gb[(int64_t)t2 * k + t1] = acc[i];
+    }
+  }
+}
+
+__global__ void k_init_s(double* __restrict__ S, int nC, int c_kind, const double* __restrict__ c_vals) {
+  const int64_t n2 = (int64_t)nC * nC;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n2;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = q / nC, i = q - j * nC;  // column-major: row i, column j
+    double v = 0.0;
+    if (c_kind == 0) {
+      if (i == j) v = c_vals[i];
+    } else if (i >= j) {
+      v = c_vals[i * nC + j];  // row-major input, lower triangle
+    }
+    S[q] = v;
+  }
+}
+
+__global__ void k_assemble_s(const int64_t* __restrict__ s_key, const int64_t* __restrict__ s_ptr,
+                             const int32_t* __restrict__ s_e1, const int32_t* __restrict__ s_e2,
+                             const int32_t* __restrict__ e_t, const int32_t* __restrict__ e_block,
+                             const double* __restrict__ b_vals, const double* __restrict__ G, int k,
+                             int64_t nkeys, int nC, double* __restrict__ S) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nkeys;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t r = s_ptr[q]; r < s_ptr[q + 1]; r++) {
+      const int e1 = s_e1[r], e2 = s_e2[r];
+      const double* Gb = G + (int64_t)e_block[e1] * k * k;
+      acc += b_vals[e1] * b_vals[e2] * Gb[(int64_t)e_t[e1] * k + e_t[e2]];
+    }
+    const int64_t key = s_key[q];
+    const int64_t c1 = key / nC, c2 = key - c1 * nC;
+    S[c1 + c2 * (int64_t)nC] -= acc;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_w_solve(Handle& h, cudaStream_t st) {
+  const int k = h.cpl.k;
+  if (k == 0 || h.cpl.nw == 0) return cudaSuccess;
+  for (int l = 0; l < h.sym.nlevels; l++) {
+    const int s0 = h.reach_lvl_ptr[l], s1 = h.reach_lvl_ptr[l + 1];
+    if (s1 == s0) continue;
+    dim3 grid(s1 - s0, h.N);
+    k_w_solve<<<grid, 128, 0, st>>>(h.d.reach_lvl_sn + s0, h.d, h.Lx, h.sym.panel_total, h.W,
+                                    h.cpl.nw, k);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract_g(Handle& h, cudaStream_t st) {
+  const int k = h.cpl.k;
+  if (k == 0) return cudaSuccess;
+  if (h.cpl.nw == 0) return cudaMemsetAsync(h.G, 0, sizeof(double) * (size_t)h.N * k * k, st);
+  const int T = (k + 31) / 32;
+  dim3 grid(T * (T + 1) / 2, h.N);
+  k_contract_g_f64<<<grid, 256, 0, st>>>(h.W, h.Lx, h.sym.panel_total, h.d.w_dpos, h.cpl.nw, k, h.G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_s(Handle& h, cudaStream_t st) {
+  if (h.nC == 0) return cudaSuccess;
+  const int64_t n2 = (int64_t)h.nC * h.nC;
+  int grid = (int)std::min<int64_t>((n2 + 255) / 256, 152 * 32);
+  k_init_s<<<grid, 256, 0, st>>>(h.S, h.nC, h.c_kind, h.c_vals);
+  const int64_t nkeys = (int64_t)h.cpl.s_key.size();
+  if (nkeys > 0) {
+    int g2 = (int)std::min<int64_t>((nkeys + 255) / 256, 152 * 32);
+    k_assemble_s<<<g2, 256, 0, st>>>(h.d.s_key, h.d.s_ptr, h.d.s_e1, h.d.s_e2, h.d.e_t, h.d.e_block,
+                                     h.b_vals, h.G, h.cpl.k, nkeys, h.nC, h.S);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace kkt

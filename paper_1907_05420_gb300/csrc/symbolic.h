@@ -1,0 +1,95 @@
+// Host-side symbolic analysis of the shared block pattern (internal header).
+//
+// The N diagonal blocks A_i of the arrowhead system share one sparsity
+// pattern (Sec. 4.1, eq. hessianPerm: every period has the same network), so
+// the ordering, elimination tree, supernode partition and every index map
+// below are computed once and reused by all N numeric factorizations.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace kkt {
+
+// Supernodes never exceed this many columns, so a whole panel column block
+// fits the shared-memory tiles of the factor kernels.
+constexpr int kMaxSnWidth = 32;
+
+struct Symbolic {
+  int32_t n = 0;   // block size nA
+  int32_t nP = 0;  // primal rows come first
+  std::vector<int32_t> perm;   // perm[k] = original row eliminated k-th
+  std::vector<int32_t> iperm;  // inverse
+  std::vector<int32_t> partner;  // per original multiplier row: its pivot partner (or -1)
+
+  // supernodes (columns in elimination order)
+  int32_t nsuper = 0;
+  std::vector<int32_t> sn_first;    // nsuper+1; columns [sn_first[s], sn_first[s+1])
+  std::vector<int64_t> sn_rowptr;   // nsuper+1; rows of s in sn_rows[...]
+  std::vector<int32_t> sn_rows;     // sorted; the first w_s rows are s's own columns
+  std::vector<int64_t> sn_valoff;   // nsuper+1; panel offsets (column-major m_s x w_s)
+  std::vector<int32_t> sn_parent;   // supernodal elimination tree (-1 = root)
+  std::vector<int32_t> sn_level;    // height above the leaves
+  std::vector<int32_t> col_sn;      // column -> supernode
+  int64_t panel_total = 0;          // doubles per block
+  int32_t nlevels = 0;
+
+  // numeric assembly: each entry of the caller's lower CSR -> panel position
+  std::vector<int64_t> a_map;       // nnzA
+
+  // left-looking update lists: for supernode s, updates from descendants d
+  // upd_ptr[s]..upd_ptr[s+1] index upd_*; each record names d and the
+  // first row position (within d's row list) that falls into s's columns.
+  std::vector<int64_t> upd_ptr;
+  std::vector<int32_t> upd_src;     // d
+  std::vector<int32_t> upd_r0;      // first row index (position in d's rows) >= sn_first[s]
+  std::vector<int32_t> upd_r1;      // one past the last row position inside s's columns
+  // for update u: rows r0..m_d-1 of d map to positions upd_rel[upd_reloff[u] + (i - r0)] in s
+  std::vector<int64_t> upd_reloff;
+  std::vector<int32_t> upd_rel;
+  // supernodes grouped by level (level 0 = leaves)
+  std::vector<int32_t> lvl_ptr;
+  std::vector<int32_t> lvl_sn;
+
+  // statistics
+  int64_t nnzL = 0;       // strictly lower nonzeros of L (exact, no padding)
+  double flops = 0;       // factorization flops per block
+};
+
+// Coupling analysis: B_i (COO per block) against the block factor.
+// With E the sorted union of the rows that carry a nonzero of some B_i
+// (k = |E| rows), B_i = E M_i and
+//   B_i^T A_i^{-1} B_i = M_i^T (E^T A_i^{-1} E) M_i = M_i^T G_i M_i,
+//   G_i = W_i^T D_i^{-1} W_i,   W_i = L_i^{-1} P^T E.
+// W_i is nonzero only on the elimination-tree reach of E, so it is stored
+// for the reach supernodes only (nw rows x k columns).
+struct Coupling {
+  int32_t N = 0, nC = 0, k = 0;
+  int64_t nnzB = 0;
+  std::vector<int32_t> E;            // k original row indices
+  std::vector<int32_t> e_t;          // per B entry: its index t in E
+  std::vector<int32_t> e_block;      // per B entry: its block
+  std::vector<int32_t> wpos;         // per t: W row holding the unit right-hand side
+  std::vector<int32_t> sn_wrow;      // per supernode: first W row (-1 = outside the reach)
+  int32_t nw = 0;                    // W rows
+  std::vector<int32_t> reach_lvl_ptr;  // reach supernodes grouped by level
+  std::vector<int32_t> reach_lvl_sn;
+  // lower triangle of sum_i M_i^T G_i M_i, gathered per output entry
+  std::vector<int64_t> s_key;        // c1 * nC + c2 (c1 >= c2), sorted
+  std::vector<int64_t> s_ptr;        // records of entry q: s_ptr[q]..s_ptr[q+1]
+  std::vector<int32_t> s_e1, s_e2;   // B entry pair of each record (same block)
+  // t = r_g - sum_i M_i^T u_i, gathered per coupling column
+  std::vector<int32_t> t_ptr;        // nC + 1
+  std::vector<int32_t> t_e;          // B entries of that column, block order
+  // v_i = M_i x_g: B entries of block i with index t lie in bt_ptr[i*(k+1)+t] ..
+  std::vector<int32_t> bt_ptr;       // N * (k + 1)
+};
+
+std::string analyze_coupling(const Symbolic& S, int32_t N, int32_t nC, const int32_t* b_blockptr,
+                             const int32_t* b_row, const int32_t* b_col, Coupling& out);
+
+// Returns an empty string on success, else a description of the problem.
+std::string analyze_pattern(int32_t n, int32_t nP, const int32_t* rowptr, const int32_t* col,
+                            const double* vals_hint, int32_t hint_blocks, Symbolic& out);
+
+}  // namespace kkt

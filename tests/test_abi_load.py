@@ -1,0 +1,69 @@
+"""The C-ABI library loads and exports every symbol include/kkt_schur.h declares.
+
+No compute call is made (no GPU needed).
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "kkt_schur.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kkt_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for n in ["kkt_analyze", "kkt_factor", "kkt_solve", "kkt_get_info", "kkt_destroy"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1907_05420_gb300 import binding
+
+    try:
+        lib = binding.load()
+    except OSError as e:  # the CUDA runtime library itself is missing
+        pytest.skip(f"cannot load libkkt_schur.so here: {e}")
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    assert sorted(binding.EXPORTS) == declared_functions()
+
+
+def test_status_strings_without_gpu():
+    from paper_1907_05420_gb300 import binding
+
+    lib = binding.load()
+    assert lib.kkt_status_string(0) == b"ok"
+    assert lib.kkt_status_string(6) == b"refinement did not converge"
+    opt = binding.kkt_default_options()
+    assert opt.refine_tol == 1e-10 and opt.max_refine == 10 and opt.prec == 0
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes structures have the C compiler's sizes and offsets for the header."""
+    import subprocess
+
+    from paper_1907_05420_gb300 import binding
+
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "kkt_schur.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\","
+        "sizeof(kkt_pattern), offsetof(kkt_pattern, a_vals_hint),"
+        "sizeof(kkt_options), offsetof(kkt_options, reserved),"
+        "sizeof(kkt_info), offsetof(kkt_info, device_bytes));return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = [ctypes.sizeof(binding.kkt_pattern), binding.kkt_pattern.a_vals_hint.offset,
+            ctypes.sizeof(binding.kkt_options), binding.kkt_options.reserved.offset,
+            ctypes.sizeof(binding.kkt_info), binding.kkt_info.device_bytes.offset]
+    assert got == want

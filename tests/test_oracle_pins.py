@@ -5,7 +5,7 @@ sparsity plots), so the oracle is pinned by:
 
 * an independent dense LAPACK LU solve of the fully assembled K (tiny cases);
 * the inertia of K from a dense symmetric eigensolver, against the count the
-  inertia-correction section (Sec. 2.6) requires: one positive eigenvalue per
+  inertia-correction section (Sec. 2.3) requires: one positive eigenvalue per
   primal variable and coupling variable, one negative per multiplier;
 * closed forms: N = 1 without coupling (a plain sparse solve), B = 0
   (S = C, decoupled blocks), diagonal A_i (S = C - sum B_i^T diag(A_i)^-1 B_i);
