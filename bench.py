@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""KKT solves/s of the Schur-complement solve of a multiperiod storage OPF
+system on GB300.
+
+Workload: the synthetic 2,383-bus grid (2,900 lines, 327 generators, 100
+storage units) over 96 periods; blocks A_i of size 10,486, coupling S of
+size 9,600 (input recipe in gen/mpopf.py).  One step = one KKT solve: the
+numeric factorization (block factors, Schur assembly, dense factor of S) plus
+the solve with FP64 iterative refinement to eta <= 1e-10.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|tf32|bf16]
+    python bench.py --impl reference ...   # the CPU oracle, timed on the host
+
+Multi-GPU (torchrun, one rank per GPU): independent replicas, one system per
+rank, no data-path collective; value = solves of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "KKT solves/s & p50/p99 latency, mixed-prec vs plain FP64 GPU at resid≤1e-10"
+WORKLOAD = "grid2383_n96"
+WORKLOAD_DESC = ("grid2383_n96: synthetic 2,383-bus grid, 2,900 lines, 327 generators, "
+                 "100 storage units, N=96 periods; blocks nA=10,486; S 9,600 x 9,600")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [ln.strip().split(",") for ln in self.tmp.read().splitlines() if ln.strip()]
+        self.tmp.close()
+        os.unlink(self.tmp.name)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_reference_solve(prob, perm=None):
+    """One oracle solve of the workload on the host cores (the CPU baseline).
+
+    The ordering is analysis (once per pattern, like kkt_analyze on the GPU
+    side) and is computed outside the timed region when `perm` is None.
+    """
+    import oracle
+
+    if perm is None:
+        perm = oracle.min_degree(prob.nA, prob.a_rowptr, prob.a_col, prob.nP)
+    t0 = time.perf_counter()
+    out = oracle.kkt_solve(prob, perm)
+    dt = time.perf_counter() - t0
+    return out, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count()
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, timed as it stands on the host cores."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from gen import CONFIGS, make_problem
+
+    prob = make_problem(CONFIGS[args.workload])
+    small = make_problem(CONFIGS["grid30_n24"])
+    for _ in range(args.warmup):  # warm-up on the small instance (loads the library, threads)
+        oracle.kkt_solve(small)
+    perm = oracle.min_degree(prob.nA, prob.a_rowptr, prob.a_col, prob.nP)  # analysis, untimed
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_reference_solve(prob, perm)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps / total
+    threads = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "precision": "fp64", "parallelism": "none (host)"},
+        "latency_ms": {"p50": 1e3 * statistics.median(times),
+                       "p99": 1e3 * max(times) if len(times) < 100 else
+                       1e3 * sorted(times)[int(0.99 * len(times))]},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} full solves of {args.workload}, ordering computed once "
+                                   f"untimed (warm-up: {args.warmup} solves of grid30_n24)"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32", "bf16"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from gen import CONFIGS, make_problem
+    from paper_1907_05420_gb300 import binding as B
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    prob = make_problem(CONFIGS[args.workload])
+    stream = torch.cuda.current_stream()
+    opt = B.kkt_default_options(args.prec)
+    h = B.kkt_analyze(prob, opt)
+    info0 = B.kkt_get_info(h)
+
+    a = torch.from_numpy(np.ascontiguousarray(prob.a_vals)).to(dev)
+    b = torch.from_numpy(np.ascontiguousarray(prob.b_vals)).to(dev)
+    c = torch.from_numpy(np.ascontiguousarray(prob.c_vals)).to(dev)
+    r = torch.from_numpy(np.ascontiguousarray(prob.rhs)).to(dev)
+    x = torch.empty_like(r)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step_device():
+        B.kkt_factor(h, a, b, c, stream)
+        B.kkt_solve(h, r, x, 1, stream)
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    launches0 = B.kkt_get_info(h)["n_launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    phases = {"a_block_factor": [], "b_schur_assembly": [], "c_dense_factor": [], "d_solve": []}
+    etas, steps_ir = [], []
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step_device()
+        ev[i][1].record(stream)
+        inf = B.kkt_get_info(h)
+        phases["a_block_factor"].append(inf["ms_block_factor"])
+        phases["b_schur_assembly"].append(inf["ms_schur_assembly"])
+        phases["c_dense_factor"].append(inf["ms_dense_factor"])
+        phases["d_solve"].append(inf["ms_solve_device"])
+        etas.append(inf["rel_residual"])
+        steps_ir.append(inf["refine_steps"])
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    info = B.kkt_get_info(h)
+    launches = info["n_launches"] - launches0
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+    x_gpu = x.cpu().numpy()
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # inputs and D2H of the solution inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).pin_memory()  # noqa: E731
+        ha, hb, hc, hr = pin(prob.a_vals), pin(prob.b_vals), pin(prob.c_vals), pin(prob.rhs)
+        hx = torch.empty_like(hr).pin_memory()
+        for _ in range(max(1, args.warmup)):
+            B.kkt_factor(h, ha, hb, hc, stream)
+            B.kkt_solve(h, hr, hx, 1, stream)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            flush.zero_()
+            B.kkt_factor(h, ha, hb, hc, stream)
+            B.kkt_solve(h, hr, hx, 1, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = e0.elapsed_time(e1) / 1e3
+        if world > 1:
+            import torch.distributed as dist
+
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        h2d = sum(t.numel() * t.element_size() for t in (ha, hb, hc, hr))
+        e2e = {"value": world * args.steps / e2e_s, "unit": "solves/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hx.numel() * 8)}
+
+    # roofline of the dominant phase (algorithmic work / measured phase time)
+    peaks, peak_kind = _peaks()
+    fp64_gflops = B.kkt_measure_fp64_peak()
+    N, nA, nC = prob.N, prob.nA, prob.nC
+    k, nw = info["k_coupling_rows"], info["w_rows"]
+    mean = {kk: statistics.mean(v) for kk, v in phases.items()}
+    ir = statistics.mean(steps_ir)
+    work = {
+        "a_block_factor": {"flops": N * info["factor_flops"],
+                           "bytes": 8.0 * N * (prob.nnzA + info["nnz_l"] + nA)},
+        "b_schur_assembly": {"flops": N * nw * k * k, "bytes": 8.0 * N * 2 * nw * k},
+        "c_dense_factor": {"flops": nC ** 3 / 3.0, "bytes": 8.0 * nC * nC},
+        "d_solve": {"flops": 0.0,
+                    "bytes": (1 + ir) * (8.0 * N * (2 * info["panel_doubles"] + 2 * nA) + 8.0 * nC * nC)},
+    }
+    dom = max(mean, key=mean.get)
+    t_dom = mean[dom] / 1e3
+    if dom == "d_solve":
+        bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
+        achieved = work[dom]["bytes"] / t_dom / 1e9
+        peak_src = f"hbm_gbs of {peak_kind} peaks"
+    elif dom == "c_dense_factor" and args.prec != "fp64":
+        ratio = 0.5 if args.prec == "tf32" else 1.0
+        bound, peak, unit = "tensor", peaks["bf16_tflops"] * ratio, "TFLOP/s"
+        achieved = work[dom]["flops"] / t_dom / 1e12
+        peak_src = f"bf16_tflops of {peak_kind} peaks x {ratio} ({args.prec})"
+    else:
+        bound, peak, unit = "alu", fp64_gflops / 1e3, "TFLOP/s"
+        achieved = work[dom]["flops"] / t_dom / 1e12
+        peak_src = "FP64 FMA throughput measured by kkt_measure_fp64_peak in this run"
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "phase": dom, "peak_source": peak_src}
+    phase_report = {}
+    for kk, ms in mean.items():
+        s = ms / 1e3
+        phase_report[kk] = {"ms": ms, "gflops": work[kk]["flops"] / s / 1e9 if s > 0 else None,
+                            "gbs": work[kk]["bytes"] / s / 1e9 if s > 0 else None,
+                            "hbm_frac": work[kk]["bytes"] / s / 1e9 / peaks["hbm_gbs"] if s > 0 else None}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.prec == "fp64" else f"f64+{args.prec}", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "precision": args.prec,
+                   "l2": "256 MB buffer written before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "residual_eta_max": max(etas), "refine_steps_mean": ir,
+        "roofline": roofline, "phases": phase_report, "fp64_peak_gflops_measured": fp64_gflops,
+        "e2e": e2e, "clocks": clk, "gpu_launches": int(launches), "wall_s_timed": t_wall,
+        "analyze_ms": info0["ms_analyze"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out, dt = cpu_reference_solve(prob)
+        import oracle
+
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "solves/s", "cores": oracle.max_threads(),
+                                "host_cores": host_cores(), "kind": "oracle",
+                                "sample": f"1 full solve of {args.workload} (FP64 oracle, OpenMP; "
+                                          "ordering computed once, untimed)"}
+        xo = out["x"]
+        line["error_vs_oracle"] = float(np.max(np.abs(x_gpu - xo)) / np.max(np.abs(xo)))
+    B.kkt_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

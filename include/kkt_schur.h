@@ -106,6 +106,11 @@ typedef struct {
   int32_t w_rows;               /* rows of the elimination-tree reach of those rows */
   double factor_flops;          /* block-factor flops per block */
   int64_t device_bytes;         /* device memory held by the handle */
+  /* device times (CUDA events on the call's stream) of the last kkt_factor,
+   * per phase: (a) block factors, (b) Schur assembly, (c) dense factor of S */
+  double ms_block_factor, ms_schur_assembly, ms_dense_factor;
+  double ms_solve_device;       /* device time of the last kkt_solve, refinement included */
+  int64_t n_launches;           /* kernels launched by this handle since kkt_analyze */
 } kkt_info;
 
 /* Default options: FP64, refine_tol 1e-10, max_refine 10, pivot_eps 1e-20,
@@ -153,6 +158,11 @@ const char* kkt_status_string(kkt_status s);
 
 /* Text of the last error on this thread ("" if none). */
 const char* kkt_last_error(void);
+
+/* Measured FP64 FMA throughput of the current device in GFLOP/s (8
+ * independent FMA chains per thread, best of 5 launches).  The FP64-bound
+ * phases report their roofline fraction against it. */
+kkt_status kkt_measure_fp64_peak(double* gflops);
 
 #ifdef __cplusplus
 }

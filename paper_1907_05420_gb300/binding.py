@@ -50,7 +50,10 @@ class kkt_info(C.Structure):
                 ("ms_analyze", C.c_double), ("ms_factor", C.c_double), ("ms_solve", C.c_double),
                 ("nnz_l", C.c_int64), ("panel_doubles", C.c_int64), ("n_supernodes", C.c_int32),
                 ("n_levels", C.c_int32), ("k_coupling_rows", C.c_int32), ("w_rows", C.c_int32),
-                ("factor_flops", C.c_double), ("device_bytes", C.c_int64)]
+                ("factor_flops", C.c_double), ("device_bytes", C.c_int64),
+                ("ms_block_factor", C.c_double), ("ms_schur_assembly", C.c_double),
+                ("ms_dense_factor", C.c_double), ("ms_solve_device", C.c_double),
+                ("n_launches", C.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -58,7 +61,7 @@ class kkt_info(C.Structure):
 
 # every symbol the header declares
 EXPORTS = ["kkt_default_options", "kkt_analyze", "kkt_factor", "kkt_solve", "kkt_get_info",
-           "kkt_destroy", "kkt_status_string", "kkt_last_error"]
+           "kkt_destroy", "kkt_status_string", "kkt_last_error", "kkt_measure_fp64_peak"]
 
 _lib = None
 
@@ -94,6 +97,8 @@ def load(build_if_missing: bool = True):
     L.kkt_status_string.restype = C.c_char_p
     L.kkt_last_error.argtypes = []
     L.kkt_last_error.restype = C.c_char_p
+    L.kkt_measure_fp64_peak.argtypes = [C.POINTER(C.c_double)]
+    L.kkt_measure_fp64_peak.restype = C.c_int
     _lib = L
     return L
 
@@ -192,6 +197,13 @@ def kkt_get_info(h) -> dict:
     info = kkt_info()
     _check(load().kkt_get_info(h, C.byref(info)))
     return info.as_dict()
+
+
+def kkt_measure_fp64_peak() -> float:
+    """Measured FP64 FMA throughput of the current device, GFLOP/s."""
+    v = C.c_double()
+    _check(load().kkt_measure_fp64_peak(C.byref(v)))
+    return v.value
 
 
 def kkt_destroy(h):

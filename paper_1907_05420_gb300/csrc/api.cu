@@ -53,8 +53,9 @@ void free_all(Handle* h) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->host_red) cudaFreeHost(h->host_red);
-  if (h->ev_f0) cudaEventDestroy(h->ev_f0);
-  if (h->ev_f1) cudaEventDestroy(h->ev_f1);
+  cudaEvent_t evs[] = {h->ev_f0, h->ev_f1, h->ev_fa, h->ev_fb, h->ev_s0, h->ev_s1};
+  for (cudaEvent_t ev : evs)
+    if (ev) cudaEventDestroy(ev);
 }
 
 }  // namespace
@@ -268,8 +269,8 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   AL(red, double, 128);
 #undef AL
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->host_red, sizeof(double) * 8);
-  if (e == cudaSuccess) e = cudaEventCreate(&h->ev_f0);
-  if (e == cudaSuccess) e = cudaEventCreate(&h->ev_f1);
+  for (cudaEvent_t* ev : {&h->ev_f0, &h->ev_f1, &h->ev_fa, &h->ev_fb, &h->ev_s0, &h->ev_s1})
+    if (e == cudaSuccess) e = cudaEventCreate(ev);
   if (e != cudaSuccess) {
     kkt_status st = cuda_status(e, "kkt_analyze");
     free_all(h);
@@ -307,9 +308,11 @@ kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals
   KKT_CUDA(cudaMemsetAsync(h->counters, 0, sizeof(long long) * kNumCounters, st));
   KKT_CUDA(launch_scatter_a(*h, st));
   KKT_CUDA(launch_factor_levels(*h, st));
+  KKT_CUDA(cudaEventRecord(h->ev_fa, st));
   KKT_CUDA(launch_w_solve(*h, st));
   KKT_CUDA(launch_contract_g(*h, st));
   KKT_CUDA(launch_assemble_s(*h, st));
+  KKT_CUDA(cudaEventRecord(h->ev_fb, st));
   KKT_CUDA(launch_dense_ldlt(*h, st));
   KKT_CUDA(launch_knorm(*h, st));
   KKT_CUDA(cudaEventRecord(h->ev_f1, st));
@@ -334,6 +337,7 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
   auto t0 = std::chrono::steady_clock::now();
   const int64_t nK = (int64_t)h->N * h->nA + h->nC;
   kkt_status result = KKT_OK;
+  KKT_CUDA(cudaEventRecord(h->ev_s0, st));
   for (int32_t q = 0; q < nrhs; q++) {
     const double* rq = rhs + q * nK;
     double* xq = x + q * nK;
@@ -355,7 +359,7 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
       if (steps > 0 && !(eta < 0.5 * eta_prev)) break;  // stalled
       eta_prev = eta;
       KKT_CUDA(launch_apply_inverse(*h, h->rho, h->dx, st));
-      KKT_CUDA(launch_axpy(h->x, h->dx, nK, st));
+      KKT_CUDA(launch_axpy(*h, h->x, h->dx, nK, st));
       steps++;
     }
     KKT_CUDA(cudaMemcpyAsync(xq, h->x, sizeof(double) * nK,
@@ -364,7 +368,12 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
     h->info.rel_residual = eta;
     if (!(eta <= h->opt.refine_tol)) result = KKT_ERR_NOT_CONVERGED;
   }
+  KKT_CUDA(cudaEventRecord(h->ev_s1, st));
   KKT_CUDA(cudaStreamSynchronize(st));
+  {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_s0, h->ev_s1) == cudaSuccess) h->info.ms_solve_device = ms;
+  }
   h->info.ms_solve =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (result != KKT_OK) set_error("kkt_solve: refinement stopped above refine_tol");
@@ -388,10 +397,14 @@ kkt_status kkt_get_info(kkt_handle* hh, kkt_info* info) {
     if (h->timed_factor) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, h->ev_f0, h->ev_f1) == cudaSuccess) h->info.ms_factor = ms;
+      if (cudaEventElapsedTime(&ms, h->ev_f0, h->ev_fa) == cudaSuccess) h->info.ms_block_factor = ms;
+      if (cudaEventElapsedTime(&ms, h->ev_fa, h->ev_fb) == cudaSuccess) h->info.ms_schur_assembly = ms;
+      if (cudaEventElapsedTime(&ms, h->ev_fb, h->ev_f1) == cudaSuccess) h->info.ms_dense_factor = ms;
       h->timed_factor = false;
     }
   }
   h->info.device_bytes = h->device_bytes;
+  h->info.n_launches = h->launches;
   *info = h->info;
   return KKT_OK;
 }

@@ -195,12 +195,21 @@ cudaError_t launch_dense_ldlt(Handle& h, cudaStream_t st) {
   const int n = h.nC;
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = std::min(NB, n - k0);
+    {
     k_dense_diag<<<1, 256, 0, st>>>(h.S, n, k0, h.counters);
+    h.launches++;
+  }
     const int rest = n - k0 - kb;
     if (rest > 0) {
-      k_dense_panel<<<(rest + 63) / 64, 64, 0, st>>>(h.S, h.Ypanel, n, k0);
+      {
+    k_dense_panel<<<(rest + 63) / 64, 64, 0, st>>>(h.S, h.Ypanel, n, k0);
+    h.launches++;
+  }
       const int T = (rest + 63) / 64;
-      k_dense_update<<<T * (T + 1) / 2, 256, 0, st>>>(h.S, h.Ypanel, n, k0);
+      {
+    k_dense_update<<<T * (T + 1) / 2, 256, 0, st>>>(h.S, h.Ypanel, n, k0);
+    h.launches++;
+  }
     }
   }
   return cudaGetLastError();
@@ -213,15 +222,30 @@ cudaError_t launch_dense_solve(Handle& h, const double* t, double* x, cudaStream
   if (e != cudaSuccess) return e;
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = std::min(NB, n - k0);
+    {
     k_dense_fwd_diag<<<1, 32, 0, st>>>(h.S, x, n, k0);
-    const int rest = n - k0 - kb;
-    if (rest > 0) k_dense_fwd_update<<<(rest + 255) / 256, 256, 0, st>>>(h.S, x, n, k0);
+    h.launches++;
   }
-  k_dense_diag_scale<<<(n + 255) / 256, 256, 0, st>>>(h.S, x, n);
+    const int rest = n - k0 - kb;
+    if (rest > 0) {
+    k_dense_fwd_update<<<(rest + 255) / 256, 256, 0, st>>>(h.S, x, n, k0);
+    h.launches++;
+  }
+  }
+  {
+    k_dense_diag_scale<<<(n + 255) / 256, 256, 0, st>>>(h.S, x, n);
+    h.launches++;
+  }
   const int last = ((n - 1) / NB) * NB;
   for (int k0 = last; k0 >= 0; k0 -= NB) {
+    {
     k_dense_bwd_dot<<<NB, 256, 0, st>>>(h.S, x, h.red + 8, n, k0);
+    h.launches++;
+  }
+    {
     k_dense_bwd_diag<<<1, 32, 0, st>>>(h.S, x, h.red + 8, n, k0);
+    h.launches++;
+  }
   }
   return cudaGetLastError();
 }

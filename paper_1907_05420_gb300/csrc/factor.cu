@@ -144,8 +144,14 @@ cudaError_t launch_scatter_a(Handle& h, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   int64_t total = h.nnzA * h.N;
   int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-  k_scatter_a<<<grid, 256, 0, st>>>(h.a_vals, h.nnzA, h.d.a_map, h.Lx, pt, h.N);
-  k_block_absmax<<<h.N, 256, 0, st>>>(h.a_vals, h.nnzA, h.anorm);
+  {
+    k_scatter_a<<<grid, 256, 0, st>>>(h.a_vals, h.nnzA, h.d.a_map, h.Lx, pt, h.N);
+    h.launches++;
+  }
+  {
+    k_block_absmax<<<h.N, 256, 0, st>>>(h.a_vals, h.nnzA, h.anorm);
+    h.launches++;
+  }
   return cudaGetLastError();
 }
 
@@ -155,12 +161,18 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
     const int w0 = h.fwork_lvl_ptr[l], w1 = h.fwork_lvl_ptr[l + 1];
     if (l > 0 && w1 > w0) {
       dim3 grid(w1 - w0, h.N);
-      k_factor_update<<<grid, 256, 0, st>>>(h.d.fwork + 3 * w0, h.d, h.Lx, pt);
+      {
+    k_factor_update<<<grid, 256, 0, st>>>(h.d.fwork + 3 * w0, h.d, h.Lx, pt);
+    h.launches++;
+  }
     }
     const int s0 = h.lvl_ptr[l], s1 = h.lvl_ptr[l + 1];
     dim3 grid2(s1 - s0, h.N);
+    {
     k_panel_factor<<<grid2, 256, 0, st>>>(h.d.lvl_sn + s0, h.d, h.Lx, pt, h.anorm, h.opt.pivot_eps,
                                           h.counters);
+    h.launches++;
+  }
   }
   return cudaGetLastError();
 }

@@ -113,6 +113,9 @@ struct Handle {
   bool timed_factor = false;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_f0 = nullptr, ev_f1 = nullptr;
+  cudaEvent_t ev_fa = nullptr, ev_fb = nullptr;  // phase boundaries inside kkt_factor
+  cudaEvent_t ev_s0 = nullptr, ev_s1 = nullptr;  // around kkt_solve
+  int64_t launches = 0;                          // kernels launched since analyze
   kkt_info info{};
 };
 
@@ -133,7 +136,7 @@ cudaError_t launch_apply_inverse(Handle& h, const double* rhs, double* out, cuda
 cudaError_t launch_residual(Handle& h, const double* rhs, const double* x, double* rho,
                             cudaStream_t st);
 cudaError_t launch_knorm(Handle& h, cudaStream_t st);
-cudaError_t launch_axpy(double* y, const double* x, int64_t n, cudaStream_t st);
+cudaError_t launch_axpy(Handle& h, double* y, const double* x, int64_t n, cudaStream_t st);
 cudaError_t launch_norms(Handle& h, const double* rho, const double* x, const double* rhs,
                          cudaStream_t st);
 

@@ -154,8 +154,11 @@ cudaError_t launch_w_solve(Handle& h, cudaStream_t st) {
     const int s0 = h.reach_lvl_ptr[l], s1 = h.reach_lvl_ptr[l + 1];
     if (s1 == s0) continue;
     dim3 grid(s1 - s0, h.N);
+    {
     k_w_solve<<<grid, 128, 0, st>>>(h.d.reach_lvl_sn + s0, h.d, h.Lx, h.sym.panel_total, h.W,
                                     h.cpl.nw, k);
+    h.launches++;
+  }
   }
   return cudaGetLastError();
 }
@@ -166,7 +169,10 @@ cudaError_t launch_contract_g(Handle& h, cudaStream_t st) {
   if (h.cpl.nw == 0) return cudaMemsetAsync(h.G, 0, sizeof(double) * (size_t)h.N * k * k, st);
   const int T = (k + 31) / 32;
   dim3 grid(T * (T + 1) / 2, h.N);
-  k_contract_g_f64<<<grid, 256, 0, st>>>(h.W, h.Lx, h.sym.panel_total, h.d.w_dpos, h.cpl.nw, k, h.G);
+  {
+    k_contract_g_f64<<<grid, 256, 0, st>>>(h.W, h.Lx, h.sym.panel_total, h.d.w_dpos, h.cpl.nw, k, h.G);
+    h.launches++;
+  }
   return cudaGetLastError();
 }
 
@@ -174,12 +180,18 @@ cudaError_t launch_assemble_s(Handle& h, cudaStream_t st) {
   if (h.nC == 0) return cudaSuccess;
   const int64_t n2 = (int64_t)h.nC * h.nC;
   int grid = (int)std::min<int64_t>((n2 + 255) / 256, 152 * 32);
-  k_init_s<<<grid, 256, 0, st>>>(h.S, h.nC, h.c_kind, h.c_vals);
+  {
+    k_init_s<<<grid, 256, 0, st>>>(h.S, h.nC, h.c_kind, h.c_vals);
+    h.launches++;
+  }
   const int64_t nkeys = (int64_t)h.cpl.s_key.size();
   if (nkeys > 0) {
     int g2 = (int)std::min<int64_t>((nkeys + 255) / 256, 152 * 32);
+    {
     k_assemble_s<<<g2, 256, 0, st>>>(h.d.s_key, h.d.s_ptr, h.d.s_e1, h.d.s_e2, h.d.e_t, h.d.e_block,
                                      h.b_vals, h.G, h.cpl.k, nkeys, h.nC, h.S);
+    h.launches++;
+  }
   }
   return cudaGetLastError();
 }

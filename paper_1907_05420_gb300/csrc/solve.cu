@@ -327,35 +327,62 @@ cudaError_t launch_apply_inverse(Handle& h, const double* r, double* out, cudaSt
   const int nA = h.nA, N = h.N, k = h.cpl.k, nw = h.cpl.nw;
   const int64_t pt = h.sym.panel_total;
   const int64_t nb = (int64_t)nA * N;
-  k_permute_in<<<grid_for(nb), 256, 0, st>>>(r, h.d.perm, h.z, nA, N);
+  {
+    k_permute_in<<<grid_for(nb), 256, 0, st>>>(r, h.d.perm, h.z, nA, N);
+    h.launches++;
+  }
   for (int l = 0; l < h.sym.nlevels; l++) {
     const int s0 = h.lvl_ptr[l], nsn = h.lvl_ptr[l + 1] - s0;
     const int warps = nsn * N;
+    {
     k_fsolve_level<<<(warps + 3) / 4, 128, 0, st>>>(h.d.lvl_sn + s0, nsn, h.d, h.Lx, pt, h.z, nA, N);
+    h.launches++;
+  }
   }
   if (h.nC > 0) {
     if (k > 0 && nw > 0) {
       dim3 g((k + 127) / 128, N);
-      k_reduce_u<<<g, 128, 0, st>>>(h.W, h.z, h.Lx, pt, h.d.w_dpos, h.d.w_col, nw, k, nA, h.u);
+      {
+    k_reduce_u<<<g, 128, 0, st>>>(h.W, h.z, h.Lx, pt, h.d.w_dpos, h.d.w_col, nw, k, nA, h.u);
+    h.launches++;
+  }
     } else if (k > 0) {
       cudaMemsetAsync(h.u, 0, sizeof(double) * (size_t)k * N, st);
     }
+    {
     k_reduce_t<<<(h.nC + 255) / 256, 256, 0, st>>>(r + nb, h.d.t_ptr, h.d.t_e, h.d.e_t, h.d.e_block,
                                                    h.b_vals, h.u, k, h.nC, h.tg);
+    h.launches++;
+  }
     cudaError_t e = launch_dense_solve(h, h.tg, h.xg, st);
     if (e != cudaSuccess) return e;
     if (k > 0 && nw > 0) {
-      k_mx<<<(k * N + 255) / 256, 256, 0, st>>>(h.d.bt_ptr, h.d.b_col, h.b_vals, h.xg, k, N, h.v);
-      k_apply_xg<<<grid_for((int64_t)nw * N), 256, 0, st>>>(h.W, h.v, h.d.w_col, nw, k, nA, N, h.z);
+      {
+    k_mx<<<(k * N + 255) / 256, 256, 0, st>>>(h.d.bt_ptr, h.d.b_col, h.b_vals, h.xg, k, N, h.v);
+    h.launches++;
+  }
+      {
+    k_apply_xg<<<grid_for((int64_t)nw * N), 256, 0, st>>>(h.W, h.v, h.d.w_col, nw, k, nA, N, h.z);
+    h.launches++;
+  }
     }
   }
-  k_diag_scale<<<grid_for(nb), 256, 0, st>>>(h.d.col_dpos, h.Lx, pt, h.z, nA, N);
+  {
+    k_diag_scale<<<grid_for(nb), 256, 0, st>>>(h.d.col_dpos, h.Lx, pt, h.z, nA, N);
+    h.launches++;
+  }
   for (int l = h.sym.nlevels - 1; l >= 0; l--) {
     const int s0 = h.lvl_ptr[l], nsn = h.lvl_ptr[l + 1] - s0;
     const int warps = nsn * N;
+    {
     k_bsolve_level<<<(warps + 3) / 4, 128, 0, st>>>(h.d.lvl_sn + s0, nsn, h.d, h.Lx, pt, h.z, nA, N);
+    h.launches++;
   }
-  k_permute_out<<<grid_for(nb), 256, 0, st>>>(h.z, h.d.perm, out, nA, N);
+  }
+  {
+    k_permute_out<<<grid_for(nb), 256, 0, st>>>(h.z, h.d.perm, out, nA, N);
+    h.launches++;
+  }
   if (h.nC > 0)
     cudaMemcpyAsync(out + nb, h.xg, sizeof(double) * h.nC, cudaMemcpyDeviceToDevice, st);
   return cudaGetLastError();
@@ -364,14 +391,23 @@ cudaError_t launch_apply_inverse(Handle& h, const double* r, double* out, cudaSt
 cudaError_t launch_residual(Handle& h, const double* r, const double* x, double* rho, cudaStream_t st) {
   const int nA = h.nA, N = h.N, k = h.cpl.k;
   const int64_t nb = (int64_t)nA * N;
-  k_resid_blocks<<<grid_for(nb), 256, 0, st>>>(h.d.full_rowptr, h.d.full_col, h.d.full_src, h.a_vals,
+  {
+    k_resid_blocks<<<grid_for(nb), 256, 0, st>>>(h.d.full_rowptr, h.d.full_col, h.d.full_src, h.a_vals,
                                                h.nnzA, r, x, rho, nA, N);
+    h.launches++;
+  }
   if (h.nC > 0) {
     if (k > 0)
-      k_resid_b<<<(k * N + 255) / 256, 256, 0, st>>>(h.d.bt_ptr, h.d.b_row, h.d.b_col, h.b_vals,
+      {
+    k_resid_b<<<(k * N + 255) / 256, 256, 0, st>>>(h.d.bt_ptr, h.d.b_row, h.d.b_col, h.b_vals,
                                                      x + nb, k, nA, N, rho);
+    h.launches++;
+  }
+    {
     k_resid_g<<<(h.nC + 255) / 256, 256, 0, st>>>(h.d.t_ptr, h.d.t_e, h.d.e_block, h.d.b_row, h.b_vals,
                                                   h.c_vals, h.c_kind, r, x, nA, N, h.nC, rho);
+    h.launches++;
+  }
   }
   return cudaGetLastError();
 }
@@ -380,17 +416,26 @@ cudaError_t launch_knorm(Handle& h, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(h.knorm, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
   const int64_t nb = (int64_t)h.nA * h.N;
-  k_knorm_blocks<<<grid_for(nb), 256, 0, st>>>(h.d.full_rowptr, h.d.full_src, h.a_vals, h.nnzA,
+  {
+    k_knorm_blocks<<<grid_for(nb), 256, 0, st>>>(h.d.full_rowptr, h.d.full_src, h.a_vals, h.nnzA,
                                                h.d.bt_ptr, h.d.b_row, h.b_vals, h.d.E, h.cpl.k,
                                                h.nA, h.N, h.knorm);
+    h.launches++;
+  }
   if (h.nC > 0)
+    {
     k_knorm_g<<<(h.nC + 255) / 256, 256, 0, st>>>(h.d.t_ptr, h.d.t_e, h.b_vals, h.c_vals, h.c_kind,
                                                   h.nC, h.knorm);
+    h.launches++;
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_axpy(double* y, const double* x, int64_t n, cudaStream_t st) {
-  k_axpy<<<grid_for(n), 256, 0, st>>>(y, x, n);
+cudaError_t launch_axpy(Handle& h, double* y, const double* x, int64_t n, cudaStream_t st) {
+  {
+    k_axpy<<<grid_for(n), 256, 0, st>>>(y, x, n);
+    h.launches++;
+  }
   return cudaGetLastError();
 }
 
@@ -399,7 +444,10 @@ cudaError_t launch_norms(Handle& h, const double* rho, const double* x, const do
   cudaError_t e = cudaMemsetAsync(h.red, 0, sizeof(double) * 3, st);
   if (e != cudaSuccess) return e;
   const int64_t nK = (int64_t)h.nA * h.N + h.nC;
-  k_norms3<<<grid_for(nK), 256, 0, st>>>(rho, x, rhs, nK, h.red);
+  {
+    k_norms3<<<grid_for(nK), 256, 0, st>>>(rho, x, rhs, nK, h.red);
+    h.launches++;
+  }
   return cudaGetLastError();
 }
 

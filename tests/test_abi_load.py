@@ -15,7 +15,7 @@ HEADER = os.path.join(ROOT, "include", "kkt_schur.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(kkt_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(kkt_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_the_abi():
@@ -58,12 +58,12 @@ def test_struct_layouts_match_header(tmp_path):
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(kkt_pattern), offsetof(kkt_pattern, a_vals_hint),"
         "sizeof(kkt_options), offsetof(kkt_options, reserved),"
-        "sizeof(kkt_info), offsetof(kkt_info, device_bytes));return 0;}\n")
+        "sizeof(kkt_info), offsetof(kkt_info, n_launches));return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                           check=True).stdout.split()]
     want = [ctypes.sizeof(binding.kkt_pattern), binding.kkt_pattern.a_vals_hint.offset,
             ctypes.sizeof(binding.kkt_options), binding.kkt_options.reserved.offset,
-            ctypes.sizeof(binding.kkt_info), binding.kkt_info.device_bytes.offset]
+            ctypes.sizeof(binding.kkt_info), binding.kkt_info.n_launches.offset]
     assert got == want
