@@ -13,11 +13,11 @@
  * is solved by Schur-complement decomposition (eqs. SCform, SCsolve,
  * SCsolve1; Algorithm 1):
  *
- *     A_i = P L_i D_i L_i^T P^T                      (block factor, step 2)
- *     S   = C - sum_i B_i^T A_i^{-1} B_i              (Schur assembly, steps 3-6)
- *     t   = r_g - sum_i B_i^T A_i^{-1} r_i            (RHS reduction, steps 8-11)
- *     S   = L_s D_s L_s^T,  x_g = S^{-1} t            (dense factor and solve, 12-13)
- *     x_i = A_i^{-1} (r_i - B_i x_g)                  (local solves, eq. SCsolve1, step 15)
+ *     A_i = P L_i D_i L_i^T P^T                      (block factors)
+ *     S   = C - sum_i B_i^T A_i^{-1} B_i              (Schur assembly, eq. SCform)
+ *     t   = r_g - sum_i B_i^T A_i^{-1} r_i            (RHS reduction, eq. SCsolve)
+ *     S   = L_s D_s L_s^T,  x_g = S^{-1} t            (dense factor and solve of S)
+ *     x_i = A_i^{-1} (r_i - B_i x_g)                  (local solves, eq. SCsolve1)
  *
  * followed by FP64 iterative refinement on the full K (Sec. 2.1: refinement
  * improves the accuracy of the direct solve).
@@ -49,9 +49,8 @@ typedef enum {
   KKT_ERR_STATE = 8          /* call out of order (e.g. solve before factor) */
 } kkt_status;
 
-/* Arithmetic of the Schur contraction (step 3) and of the dense factor of S
- * (step 12).  The block factors, the residual and the refinement are FP64 in
- * every mode. */
+/* Arithmetic of the Schur contraction and of the dense factor of S.  The
+ * block factors, the residual and the refinement are FP64 in every mode. */
 typedef enum { KKT_FP64 = 0, KKT_TF32 = 1, KKT_BF16 = 2 } kkt_precision;
 
 /* Sparsity of one arrowhead system.  All arrays are host memory, read during
@@ -124,7 +123,7 @@ void kkt_default_options(kkt_options* opt);
  * all of it until kkt_destroy. */
 kkt_status kkt_analyze(const kkt_pattern* pattern, const kkt_options* opt, kkt_handle** out);
 
-/* Numeric factorization (Algorithm 1 steps 2-6 and 12): block factors,
+/* Numeric factorization (Algorithm 1 up to the factor of S): block factors,
  * Schur complement S = C - sum_i B_i^T A_i^{-1} B_i, dense LDL^T of S.
  *   a_vals: N * nnz(A) doubles, block i at offset i * nnz(A), in the pattern's
  *           CSR order;  b_vals: nnz(B) doubles in the pattern's entry order;

@@ -8,9 +8,9 @@ the paper defines:
 
 * ``min_degree``          -- fill-reducing ordering of A_i's pattern
                              (minimum degree on the explicit elimination graph);
-* ``ldlt_dense``          -- A = P L D L^T P^T, 1x1 pivots (Algorithm 1 step 2);
+* ``ldlt_dense``          -- A = P L D L^T P^T, 1x1 pivots (block factorization, Algorithm 1);
 * ``sparse_solve``        -- A^{-1} b from that factor;
-* ``dense_ldlt``          -- S = L_s D_s L_s^T, no pivoting (Algorithm 1 step 12);
+* ``dense_ldlt``          -- S = L_s D_s L_s^T, no pivoting (dense factor of S, Algorithm 1);
 * ``kkt_solve``           -- eqs. SCform, SCsolve, SCsolve1 in sequence,
                              S by one full solve per nonzero column of B_i
                              ("backsolve", Sec. 4.2);

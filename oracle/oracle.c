@@ -12,12 +12,12 @@
  *      elimination graph, smallest current degree first, ties to the
  *      smallest index);
  *   2. A_i = L_i D_i L_i^T by the up-looking sparse algorithm with 1x1
- *      pivots in that order (Algorithm 1, step 2);
+ *      pivots in that order (the block factorization of Algorithm 1);
  *   3. S = C - sum_i B_i^T A_i^{-1} B_i, one full solve per nonzero column
  *      of B_i ("backsolve" assembly, Sec. 4.2) and
  *      t = r_g - sum_i B_i^T A_i^{-1} r_i (eq. SCsolve);
  *   4. dense S = L_s D_s L_s^T (Crout form, no pivoting) and S x_g = t
- *      (Algorithm 1, steps 12-13);
+ *      (the dense factor and solve of Algorithm 1, eq. SCsolve);
  *   5. x_i = A_i^{-1} (r_i - B_i x_g) (eq. SCsolve1);
  *   6. inertia = sign counts of all D_i and D_s (Haynsworth additivity;
  *      the inertia test of Sec. 2.3).
@@ -623,7 +623,7 @@ int orc_kkt_solve(int32_t N, int32_t nA, int32_t nC, const int32_t *a_rowptr,
   int *brc = (int *)calloc((size_t)(N > 0 ? N : 1), sizeof(int));
   if (!F || !kcols || !S || !t || !Sloc || !tloc || !cols || !brc) return ORC_ERR_NOMEM;
 
-  /* steps 2 and 3: per block factor, local Schur contribution, local RHS term */
+  /* parts 2 and 3 above: per block factor, local Schur contribution, local RHS term */
 #pragma omp parallel
   {
     int32_t *mark = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nC > 0 ? nC : 1));
@@ -700,7 +700,7 @@ int orc_kkt_solve(int32_t N, int32_t nA, int32_t nC, const int32_t *a_rowptr,
   if (S_out) memcpy(S_out, S, sizeof(double) * (size_t)nC * (size_t)nC);
   if (t_out) memcpy(t_out, t, sizeof(double) * (size_t)nC);
 
-  /* step 4: S = L_s D_s L_s^T, x_g = S^{-1} t */
+  /* part 4 above: S = L_s D_s L_s^T, x_g = S^{-1} t */
   {
     int64_t in_s[3] = {0, 0, 0};
     rc = orc_dense_ldlt(nC, S, in_s);
@@ -715,7 +715,7 @@ int orc_kkt_solve(int32_t N, int32_t nA, int32_t nC, const int32_t *a_rowptr,
     }
   }
 
-  /* step 5: x_i = A_i^{-1} (r_i - B_i x_g) */
+  /* part 5 above: x_i = A_i^{-1} (r_i - B_i x_g) */
   {
     const double *xg = x + (int64_t)N * nA;
 #pragma omp parallel
@@ -734,7 +734,7 @@ int orc_kkt_solve(int32_t N, int32_t nA, int32_t nC, const int32_t *a_rowptr,
     }
   }
 
-  /* step 6: inertia of K = sum of block inertias + inertia of S */
+  /* part 6 above: inertia of K = sum of block inertias + inertia of S */
   if (inertia) {
     for (int32_t i = 0; i < N; i++)
       for (int32_t j = 0; j < nA; j++) {

@@ -1,5 +1,5 @@
 // (c) Dense LDL^T of the Schur complement, S = L_s D_s L_s^T, and the solve
-// S x_g = t (Algorithm 1, steps 12-13; eq. SCsolve).
+// S x_g = t (Algorithm 1; eqs. SCform and SCsolve).
 //
 // S is n x n, column-major, lower triangle.  Blocked right-looking, block
 // width kDenseNB = 64, per block column k0:

@@ -1,5 +1,6 @@
 // (a) Batched numeric LDL^T of the N blocks A_i = P L_i D_i L_i^T P^T
-// (Algorithm 1, step 2), all blocks sharing one supernodal structure.
+// (the block factorization of Algorithm 1), all blocks sharing one supernodal
+// structure.
 //
 // Storage: block b's factor is one contiguous array of supernode panels;
 // panel s is column-major m_s x w_s (its rows are sn_rows[s], the first w_s of

@@ -140,4 +140,5 @@ cudaError_t launch_axpy(Handle& h, double* y, const double* x, int64_t n, cudaSt
 cudaError_t launch_norms(Handle& h, const double* rho, const double* x, const double* rhs,
                          cudaStream_t st);
 
+
 }  // namespace kkt

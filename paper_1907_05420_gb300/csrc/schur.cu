@@ -1,5 +1,5 @@
 // (b) Schur-complement assembly S = C - sum_i B_i^T A_i^{-1} B_i
-// (eq. SCform; Algorithm 1 steps 3-6).
+// (eq. SCform; the Schur-complement accumulation of Algorithm 1).
 //
 // With E the k rows of A that carry a nonzero of some B_i, B_i = E M_i and
 //     B_i^T A_i^{-1} B_i = M_i^T G_i M_i,   G_i = W_i^T D_i^{-1} W_i,

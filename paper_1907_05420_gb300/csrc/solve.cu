@@ -1,5 +1,5 @@
 // (d) Local solves and the right-hand-side reduction (eqs. SCsolve and
-// SCsolve1; Algorithm 1 steps 8-11 and 15), plus the FP64 residual of the
+// SCsolve1; Algorithm 1), plus the FP64 residual of the
 // iterative refinement on the full K.
 //
 // One application of the factored K^{-1} to r = [r_0..r_{N-1}; r_g]:

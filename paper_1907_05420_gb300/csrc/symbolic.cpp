@@ -1,6 +1,6 @@
 // Symbolic analysis of the shared pattern of the blocks A_i.
 //
-// Every IPM iteration factors A_i = L_i D_i L_i^T (Algorithm 1, step 2) on
+// Every IPM iteration factors A_i = L_i D_i L_i^T (Algorithm 1) on
 // one unchanging pattern, so the ordering, elimination tree, supernodes and
 // every index map are built here once per pattern.
 //
