@@ -158,6 +158,28 @@ const char* kkt_status_string(kkt_status s);
 /* Text of the last error on this thread ("" if none). */
 const char* kkt_last_error(void);
 
+/* One application of the current factorization to a device right-hand side,
+ * allocating nothing.  The paper has no counterpart: this exists for callers
+ * that cannot call cudaMalloc while they solve (a serving process that gives
+ * all device memory to its own pool up front and must stay inside that
+ * budget, or a latency-critical loop that cannot take the device-wide
+ * synchronization an allocation may imply).
+ *   rhs, x: device arrays of N*nA + nC doubles (caller-owned; rhs is read,
+ *           x is written).  No refinement: x = (factored K)^{-1} rhs, computed
+ *           by the same kernels in the same order as kkt_solve's first step.
+ *   Work vectors come from one file-scope device array of 2^21 doubles
+ *   (16 MiB) that every GPU loading this library holds until process exit;
+ *   systems with N*nA + 2*N*k + 2*nC above that (k: rows of A carrying B's
+ *   nonzeros, see kkt_info) are rejected with KKT_ERR_INVALID.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any
+ *   stream capture.  All calls share the array and it keeps the last call's
+ *   contents: calls whose kernels overlap on the GPU (different streams,
+ *   different handles) race on it and must be serialized by the caller.
+ *   Asynchronous with respect to the host; errors of the launches are
+ *   returned as KKT_ERR_CUDA. */
+kkt_status kkt_solve_noalloc(kkt_handle* h, const double* rhs, double* x, void* stream);
+
 /* Measured FP64 FMA throughput of the current device in GFLOP/s (8
  * independent FMA chains per thread, best of 5 launches).  The FP64-bound
  * phases report their roofline fraction against it. */

@@ -61,7 +61,8 @@ class kkt_info(C.Structure):
 
 # every symbol the header declares
 EXPORTS = ["kkt_default_options", "kkt_analyze", "kkt_factor", "kkt_solve", "kkt_get_info",
-           "kkt_destroy", "kkt_status_string", "kkt_last_error", "kkt_measure_fp64_peak"]
+           "kkt_destroy", "kkt_status_string", "kkt_last_error", "kkt_measure_fp64_peak",
+           "kkt_solve_noalloc"]
 
 _lib = None
 
@@ -99,6 +100,8 @@ def load(build_if_missing: bool = True):
     L.kkt_last_error.restype = C.c_char_p
     L.kkt_measure_fp64_peak.argtypes = [C.POINTER(C.c_double)]
     L.kkt_measure_fp64_peak.restype = C.c_int
+    L.kkt_solve_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.kkt_solve_noalloc.restype = C.c_int
     _lib = L
     return L
 
@@ -197,6 +200,16 @@ def kkt_get_info(h) -> dict:
     info = kkt_info()
     _check(load().kkt_get_info(h, C.byref(info)))
     return info.as_dict()
+
+
+def kkt_solve_noalloc(h, rhs, x, stream=None):
+    """One application of the factorization to device arrays, without any
+    allocation (see include/kkt_schur.h); returns the status."""
+    pr, dr = _ptr(rhs)
+    px, dx = _ptr(x)
+    if not (dr and dx):
+        raise ValueError("kkt_solve_noalloc takes device arrays only")
+    return _check(load().kkt_solve_noalloc(h, pr, px, _stream_ptr(stream)))
 
 
 def kkt_measure_fp64_peak() -> float:

@@ -250,4 +250,31 @@ cudaError_t launch_dense_solve(Handle& h, const double* t, double* x, cudaStream
   return cudaGetLastError();
 }
 
+cudaError_t launch_dense_solve_ws(Handle& h, const double* t, double* x, double* dot,
+                                  cudaStream_t st) {
+  const int n = h.nC;
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = cudaMemcpyAsync(x, t, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = std::min(NB, n - k0);
+    k_dense_fwd_diag<<<1, 32, 0, st>>>(h.S, x, n, k0);
+    h.launches++;
+    const int rest = n - k0 - kb;
+    if (rest > 0) {
+      k_dense_fwd_update<<<(rest + 255) / 256, 256, 0, st>>>(h.S, x, n, k0);
+      h.launches++;
+    }
+  }
+  k_dense_diag_scale<<<(n + 255) / 256, 256, 0, st>>>(h.S, x, n);
+  h.launches++;
+  const int last = ((n - 1) / NB) * NB;
+  for (int k0 = last; k0 >= 0; k0 -= NB) {
+    k_dense_bwd_dot<<<NB, 256, 0, st>>>(h.S, x, dot, n, k0);
+    k_dense_bwd_diag<<<1, 32, 0, st>>>(h.S, x, dot, n, k0);
+    h.launches += 2;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace kkt

@@ -140,5 +140,18 @@ cudaError_t launch_axpy(Handle& h, double* y, const double* x, int64_t n, cudaSt
 cudaError_t launch_norms(Handle& h, const double* rho, const double* x, const double* rhs,
                          cudaStream_t st);
 
+// Solve work vectors supplied by the caller instead of the handle.
+struct SolveWorkspace {
+  double* z;    // N * nA
+  double* u;    // N * k
+  double* v;    // N * k
+  double* tg;   // nC
+  double* xg;   // nC
+  double* dot;  // kDenseNB
+};
+cudaError_t launch_apply_inverse_ws(Handle& h, const double* rhs, double* out,
+                                    const SolveWorkspace& ws, cudaStream_t st);
+cudaError_t launch_dense_solve_ws(Handle& h, const double* t, double* x, double* dot,
+                                  cudaStream_t st);
 
 }  // namespace kkt

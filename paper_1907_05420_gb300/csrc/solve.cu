@@ -451,4 +451,54 @@ cudaError_t launch_norms(Handle& h, const double* rho, const double* x, const do
   return cudaGetLastError();
 }
 
+cudaError_t launch_apply_inverse_ws(Handle& h, const double* r, double* out,
+                                    const SolveWorkspace& ws, cudaStream_t st) {
+  const int nA = h.nA, N = h.N, k = h.cpl.k, nw = h.cpl.nw;
+  const int64_t pt = h.sym.panel_total;
+  const int64_t nb = (int64_t)nA * N;
+  k_permute_in<<<grid_for(nb), 256, 0, st>>>(r, h.d.perm, ws.z, nA, N);
+  h.launches++;
+  for (int l = 0; l < h.sym.nlevels; l++) {
+    const int s0 = h.lvl_ptr[l], nsn = h.lvl_ptr[l + 1] - s0;
+    const int warps = nsn * N;
+    k_fsolve_level<<<(warps + 3) / 4, 128, 0, st>>>(h.d.lvl_sn + s0, nsn, h.d, h.Lx, pt, ws.z, nA, N);
+    h.launches++;
+  }
+  if (h.nC > 0) {
+    if (k > 0 && nw > 0) {
+      dim3 g((k + 127) / 128, N);
+      k_reduce_u<<<g, 128, 0, st>>>(h.W, ws.z, h.Lx, pt, h.d.w_dpos, h.d.w_col, nw, k, nA, ws.u);
+      h.launches++;
+    } else if (k > 0) {
+      cudaError_t e = cudaMemsetAsync(ws.u, 0, sizeof(double) * (size_t)k * N, st);
+      if (e != cudaSuccess) return e;
+    }
+    k_reduce_t<<<(h.nC + 255) / 256, 256, 0, st>>>(r + nb, h.d.t_ptr, h.d.t_e, h.d.e_t, h.d.e_block,
+                                                   h.b_vals, ws.u, k, h.nC, ws.tg);
+    h.launches++;
+    cudaError_t e = launch_dense_solve_ws(h, ws.tg, ws.xg, ws.dot, st);
+    if (e != cudaSuccess) return e;
+    if (k > 0 && nw > 0) {
+      k_mx<<<(k * N + 255) / 256, 256, 0, st>>>(h.d.bt_ptr, h.d.b_col, h.b_vals, ws.xg, k, N, ws.v);
+      k_apply_xg<<<grid_for((int64_t)nw * N), 256, 0, st>>>(h.W, ws.v, h.d.w_col, nw, k, nA, N, ws.z);
+      h.launches += 2;
+    }
+  }
+  k_diag_scale<<<grid_for(nb), 256, 0, st>>>(h.d.col_dpos, h.Lx, pt, ws.z, nA, N);
+  h.launches++;
+  for (int l = h.sym.nlevels - 1; l >= 0; l--) {
+    const int s0 = h.lvl_ptr[l], nsn = h.lvl_ptr[l + 1] - s0;
+    const int warps = nsn * N;
+    k_bsolve_level<<<(warps + 3) / 4, 128, 0, st>>>(h.d.lvl_sn + s0, nsn, h.d, h.Lx, pt, ws.z, nA, N);
+    h.launches++;
+  }
+  k_permute_out<<<grid_for(nb), 256, 0, st>>>(ws.z, h.d.perm, out, nA, N);
+  h.launches++;
+  if (h.nC > 0) {
+    cudaError_t e = cudaMemcpyAsync(out + nb, ws.xg, sizeof(double) * h.nC, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace kkt
