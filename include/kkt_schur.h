@@ -49,9 +49,18 @@ typedef enum {
   KKT_ERR_STATE = 8          /* call out of order (e.g. solve before factor) */
 } kkt_status;
 
-/* Arithmetic of the Schur contraction and of the dense factor of S.  The
- * block factors, the residual and the refinement are FP64 in every mode. */
-typedef enum { KKT_FP64 = 0, KKT_TF32 = 1, KKT_BF16 = 2 } kkt_precision;
+/* Arithmetic of the dense factor of S (and of the Schur contraction where
+ * noted).  The block factors, the residual and the refinement are FP64 in
+ * every mode.
+ *   KKT_FP64:          FP64 on the CUDA cores.
+ *   KKT_TF32/KKT_BF16: S factored in FP32 with the trailing update on the tensor
+ *                      cores (TF32 or BF16 operands, FP32 accumulation); FP64
+ *                      refinement on K, FP64-accurate refactor of S if it stalls.
+ *   KKT_F64_EMULATED:  FP64-accurate factor of S whose trailing update runs on
+ *                      the BF16 tensor cores: operands cut into exact 8-bit
+ *                      digit slices, digit products accumulated exactly in FP32
+ *                      and recombined in FP64. */
+typedef enum { KKT_FP64 = 0, KKT_TF32 = 1, KKT_BF16 = 2, KKT_F64_EMULATED = 3 } kkt_precision;
 
 /* Sparsity of one arrowhead system.  All arrays are host memory, read during
  * kkt_analyze only (copied; the caller keeps ownership).
@@ -92,7 +101,9 @@ typedef struct {
 } kkt_options;
 
 typedef struct {
-  int64_t n_pos, n_neg, n_zero; /* inertia of K from the pivots of all D_i and D_s */
+  int64_t n_pos, n_neg, n_zero; /* inertia of K from the pivots of all D_i and of the current
+                                   factor of S (in KKT_TF32/KKT_BF16 mode that factor is FP32 and
+                                   its pivot signs can be wrong for an ill-conditioned S) */
   int64_t n_perturbed;          /* pivots replaced under pivot_eps */
   int32_t refine_steps;         /* refinement steps taken by the last kkt_solve */
   int32_t fell_back_fp64;       /* 1 if the last solve refactored S in FP64 */
@@ -176,6 +187,8 @@ const char* kkt_last_error(void);
  *   stream capture.  All calls share the array and it keeps the last call's
  *   contents: calls whose kernels overlap on the GPU (different streams,
  *   different handles) race on it and must be serialized by the caller.
+ *   Needs an FP64-accurate factor of S (handles in KKT_FP64 or
+ *   KKT_F64_EMULATED mode); otherwise returns KKT_ERR_STATE.
  *   Asynchronous with respect to the host; errors of the launches are
  *   returned as KKT_ERR_CUDA. */
 kkt_status kkt_solve_noalloc(kkt_handle* h, const double* rhs, double* x, void* stream);

@@ -6,6 +6,7 @@ ctypes layer over it with the same function names.
 """
 from .binding import (  # noqa: F401
     KKT_BF16,
+    KKT_F64_EMULATED,
     KKT_FP64,
     KKT_TF32,
     KKTError,

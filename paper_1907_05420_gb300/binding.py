@@ -14,8 +14,8 @@ import numpy as np
 
 from . import build as _build
 
-KKT_FP64, KKT_TF32, KKT_BF16 = 0, 1, 2
-PRECISIONS = {"fp64": KKT_FP64, "tf32": KKT_TF32, "bf16": KKT_BF16}
+KKT_FP64, KKT_TF32, KKT_BF16, KKT_F64_EMULATED = 0, 1, 2, 3
+PRECISIONS = {"fp64": KKT_FP64, "tf32": KKT_TF32, "bf16": KKT_BF16, "f64emu": KKT_F64_EMULATED}
 
 STATUS = {
     0: "KKT_OK", 1: "KKT_ERR_INVALID", 2: "KKT_ERR_OOM", 3: "KKT_ERR_CUDA",

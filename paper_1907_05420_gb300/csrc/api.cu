@@ -49,7 +49,9 @@ void free_all(Handle* h) {
                   h->d.w_col, h->d.reach_lvl_sn, h->d.s_key, h->d.s_ptr, h->d.s_e1, h->d.s_e2,
                   h->d.t_ptr, h->d.t_e, h->d.bt_ptr, h->d.E, h->Lx, h->a_vals, h->b_vals,
                   h->c_vals, h->anorm, h->W, h->G, h->S, h->Ypanel, h->knorm, h->counters, h->r,
-                  h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red};
+                  h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red,
+                  h->trsv_flags, h->trsv_ticket, h->dev_err, h->S32, h->Y32, h->tc_imgA,
+                  h->tc_imgB, h->tc_scaleA, h->tc_scaleB};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->host_red) cudaFreeHost(h->host_red);
@@ -114,6 +116,11 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   if (!h) return KKT_ERR_OOM;
   kkt_default_options(&h->opt);
   if (opt) h->opt = *opt;
+  if (h->opt.prec < KKT_FP64 || h->opt.prec > KKT_F64_EMULATED) {
+    set_error("kkt_analyze: unknown precision mode");
+    delete h;
+    return KKT_ERR_INVALID;
+  }
   h->N = pat->N;
   h->nA = pat->nA;
   h->nP = pat->nP;
@@ -256,7 +263,7 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   AL(S, double, (int64_t)h->nC * h->nC);
   AL(Ypanel, double, (int64_t)h->nC * kDenseNB);
   AL(knorm, double, 1);
-  AL(counters, unsigned long long, kNumCounters);
+  AL(counters, unsigned long long, 2 * kNumCounters);  // second half: discarded counts
   AL(z, double, (int64_t)h->N * n);
   AL(u, double, k * h->N);
   AL(v, double, k * h->N);
@@ -267,7 +274,28 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   AL(rho, double, nK);
   AL(rhs, double, nK);
   AL(red, double, 128);
+  AL(trsv_flags, int, 2 * ((h->nC + kDenseNB - 1) / kDenseNB));
+  if (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) {
+    AL(S32, float, (int64_t)h->nC * h->nC);
+    AL(Y32, float, (int64_t)h->nC * kDenseNB);
+  }
+  if (h->opt.prec != KKT_FP64 && h->nC > 0) {
+    // operand images sized for the largest panel step; the FP64 fallback of the
+    // reduced modes uses the emulated path, so size for the larger of the two
+    const int mode_img = KKT_F64_EMULATED;
+    const int64_t ia = tc_image_bytes_a(h->nC, mode_img);
+    const int64_t itot = tc_image_bytes(h->nC, mode_img);
+    AL(tc_imgA, uint8_t, ia);
+    AL(tc_imgB, uint8_t, itot - ia);
+    AL(tc_scaleA, double, (int64_t)h->nC + 256);
+    AL(tc_scaleB, double, (int64_t)h->nC + 256);
+  }
+  AL(trsv_ticket, unsigned, 2);
+  AL(dev_err, int, 1);
 #undef AL
+  if (e == cudaSuccess)
+    e = cudaMemset(h->trsv_flags, 0, sizeof(int) * (size_t)std::max(1, 2 * ((h->nC + kDenseNB - 1) / kDenseNB)));
+  if (e == cudaSuccess) e = cudaMemset(h->dev_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->host_red, sizeof(double) * 8);
   for (cudaEvent_t* ev : {&h->ev_f0, &h->ev_f1, &h->ev_fa, &h->ev_fb, &h->ev_s0, &h->ev_s1})
     if (e == cudaSuccess) e = cudaEventCreate(ev);
@@ -305,7 +333,7 @@ kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals
   KKT_CUDA(cudaMemcpyAsync(h->a_vals, a_vals, sizeof(double) * h->nnzA * h->N, kind, st));
   if (h->nnzB > 0) KKT_CUDA(cudaMemcpyAsync(h->b_vals, b_vals, sizeof(double) * h->nnzB, kind, st));
   if (nc_vals > 0) KKT_CUDA(cudaMemcpyAsync(h->c_vals, c_vals, sizeof(double) * nc_vals, kind, st));
-  KKT_CUDA(cudaMemsetAsync(h->counters, 0, sizeof(long long) * kNumCounters, st));
+  KKT_CUDA(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * 2 * kNumCounters, st));
   KKT_CUDA(launch_scatter_a(*h, st));
   KKT_CUDA(launch_factor_levels(*h, st));
   KKT_CUDA(cudaEventRecord(h->ev_fa, st));
@@ -313,7 +341,14 @@ kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals
   KKT_CUDA(launch_contract_g(*h, st));
   KKT_CUDA(launch_assemble_s(*h, st));
   KKT_CUDA(cudaEventRecord(h->ev_fb, st));
-  KKT_CUDA(launch_dense_ldlt(*h, st));
+  if (h->opt.prec == KKT_FP64) {
+    KKT_CUDA(launch_dense_ldlt(*h, h->counters + kNumCounters, st));
+    h->s_factor = 0;
+  } else {
+    KKT_CUDA(launch_dense_ldlt_tc(*h, h->opt.prec, h->counters + kNumCounters, st));
+    h->s_factor = h->opt.prec == KKT_F64_EMULATED ? 0 : 1;
+  }
+  h->info.fell_back_fp64 = 0;
   KKT_CUDA(launch_knorm(*h, st));
   KKT_CUDA(cudaEventRecord(h->ev_f1, st));
   h->factored = true;
@@ -351,12 +386,32 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
       KKT_CUDA(launch_norms(*h, h->rho, h->x, h->rhs, st));
       KKT_CUDA(cudaMemcpyAsync(h->host_red, h->red, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
       KKT_CUDA(cudaMemcpyAsync(h->host_red + 3, h->knorm, sizeof(double), cudaMemcpyDeviceToHost, st));
+      KKT_CUDA(cudaMemcpyAsync(h->host_red + 4, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
       KKT_CUDA(cudaStreamSynchronize(st));
+      if (*reinterpret_cast<int*>(h->host_red + 4) != 0) {
+        set_error("kkt_solve: a bounded device wait ran out");
+        return KKT_ERR_TIMEOUT;
+      }
       const double* hr = h->host_red;
       eta = hr[0] / (hr[3] * hr[1] + hr[2]);
       if (!(hr[0] > 0.0)) eta = 0.0;
-      if (eta <= h->opt.refine_tol || steps >= h->opt.max_refine) break;
-      if (steps > 0 && !(eta < 0.5 * eta_prev)) break;  // stalled
+      if (eta <= h->opt.refine_tol) break;
+      const bool stalled = !(eta < 0.5 * eta_prev) || !std::isfinite(eta);
+      if (steps >= h->opt.max_refine || (steps > 0 && stalled)) {
+        if (h->s_factor == 1 && h->opt.fp64_fallback) {
+          // refinement with the FP32 factor of S stalls: refactor S (still the
+          // assembled FP64 matrix) FP64-accurately and restart from its solve
+          KKT_CUDA(cudaMemsetAsync(h->counters + kNumCounters, 0, sizeof(unsigned long long) * kNumCounters, st));
+          KKT_CUDA(launch_dense_ldlt_tc(*h, KKT_F64_EMULATED, h->counters + kNumCounters, st));
+          h->s_factor = 0;
+          h->info.fell_back_fp64 = 1;
+          KKT_CUDA(launch_apply_inverse(*h, h->rhs, h->x, st));
+          eta_prev = INFINITY;
+          steps++;
+          continue;
+        }
+        break;
+      }
       eta_prev = eta;
       KKT_CUDA(launch_apply_inverse(*h, h->rho, h->dx, st));
       KKT_CUDA(launch_axpy(*h, h->x, h->dx, nK, st));
@@ -388,12 +443,12 @@ kkt_status kkt_get_info(kkt_handle* hh, kkt_info* info) {
   }
   KKT_CUDA(cudaStreamSynchronize(h->stream));
   if (h->factored) {
-    unsigned long long c[kNumCounters];
+    unsigned long long c[2 * kNumCounters];
     KKT_CUDA(cudaMemcpy(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost));
-    h->info.n_pos = c[kPos];
-    h->info.n_neg = c[kNeg];
-    h->info.n_zero = c[kZero];
-    h->info.n_perturbed = c[kPerturbed];
+    h->info.n_pos = (int64_t)(c[kPos] + c[kNumCounters + kPos]);
+    h->info.n_neg = (int64_t)(c[kNeg] + c[kNumCounters + kNeg]);
+    h->info.n_zero = (int64_t)(c[kZero] + c[kNumCounters + kZero]);
+    h->info.n_perturbed = (int64_t)c[kPerturbed];
     if (h->timed_factor) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, h->ev_f0, h->ev_f1) == cudaSuccess) h->info.ms_factor = ms;

@@ -189,14 +189,157 @@ __global__ void k_dense_bwd_diag(const double* __restrict__ S, double* __restric
   }
 }
 
+// ---- pipelined triangular solves with the dense factor ----
+//
+// One launch per direction.  CTAs take 64-row blocks in the order of an atomic
+// ticket, so a CTA only ever waits for blocks owned by CTAs that started
+// before it.  A finished block publishes its solution, then its flag
+// (threadfence + volatile store); waiting CTAs poll the flag with a bounded
+// budget and record a timeout instead of spinning forever.
+
+constexpr long long kSpinBudgetCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+__device__ __forceinline__ bool wait_flag(const int* flag, int epoch, int* err) {
+  const long long t0 = clock64();
+  while (*((volatile const int*)flag) < epoch) {
+    __nanosleep(32);
+    if (clock64() - t0 > kSpinBudgetCycles) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+  __threadfence();
+  return true;
+}
+
+// L y = b in place (unit lower L, column-major n x n, leading dimension n)
+template <class T>
+__global__ void __launch_bounds__(256) k_trsv_lower(const T* __restrict__ L, int n, double* x,
+                                                    int* flags, unsigned* ticket, int epoch, int* err) {
+  __shared__ int s_blk, s_ok;
+  __shared__ double yj[64];
+  __shared__ double part[4][64];
+  __shared__ double Ld[64][65];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_blk = (int)atomicAdd(ticket, 1u);
+    s_ok = 1;
+  }
+  __syncthreads();
+  const int t = s_blk, r0 = t * 64, rows = min(64, n - r0);
+  const int r = tid & 63, pid = tid >> 6;
+  double acc = 0.0;
+  for (int j = 0; j < t; j++) {
+    if (tid == 0 && !wait_flag(flags + j, epoch, err)) s_ok = 0;
+    __syncthreads();
+    if (!s_ok) break;
+    if (tid < 64) yj[tid] = __ldcg(x + j * 64 + tid);
+    __syncthreads();
+    if (r < rows) {
+      const T* col = L + (int64_t)(r0 + r) + (int64_t)(j * 64 + pid * 16) * n;
+#pragma unroll 4
+      for (int c = 0; c < 16; c++) acc += (double)col[(int64_t)c * n] * yj[pid * 16 + c];
+    }
+    __syncthreads();
+  }
+  part[pid][r] = acc;
+  for (int q = tid; q < rows * rows; q += 256) {
+    const int c = q / rows, i = q - c * rows;
+    Ld[i][c] = (double)L[(int64_t)(r0 + i) + (int64_t)(r0 + c) * n];
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int lane = tid;
+    double a0 = 0.0, a1 = 0.0;
+    if (lane < rows) a0 = __ldcg(x + r0 + lane) - (part[0][lane] + part[1][lane] + part[2][lane] + part[3][lane]);
+    if (lane + 32 < rows)
+      a1 = __ldcg(x + r0 + lane + 32) -
+           (part[0][lane + 32] + part[1][lane + 32] + part[2][lane + 32] + part[3][lane + 32]);
+    for (int c = 0; c < rows; c++) {
+      const double yc = __shfl_sync(0xffffffffu, c < 32 ? a0 : a1, c & 31);
+      if (lane > c && lane < rows) a0 -= Ld[lane][c] * yc;
+      if (lane + 32 > c && lane + 32 < rows) a1 -= Ld[lane + 32][c] * yc;
+    }
+    if (lane < rows) x[r0 + lane] = a0;
+    if (lane + 32 < rows) x[r0 + lane + 32] = a1;
+    __threadfence();  // publish this block's solution before its flag
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    *((volatile int*)(flags + t)) = epoch;
+  }
+}
+
+// L^T x = y in place (blocks from the bottom up)
+template <class T>
+__global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ L, int n, double* x,
+                                                    int* flags, unsigned* ticket, int epoch, int* err) {
+  __shared__ int s_blk, s_ok;
+  __shared__ double xj[64];
+  __shared__ double accs[64];
+  __shared__ double Ld[64][65];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = (n + 63) / 64;
+  if (tid == 0) {
+    s_blk = nb - 1 - (int)atomicAdd(ticket, 1u);
+    s_ok = 1;
+  }
+  if (tid < 64) accs[tid] = 0.0;
+  __syncthreads();
+  const int b = s_blk, r0 = b * 64, rows = min(64, n - r0);
+  for (int j = nb - 1; j > b; j--) {
+    if (tid == 0 && !wait_flag(flags + j, epoch, err)) s_ok = 0;
+    __syncthreads();
+    if (!s_ok) break;
+    const int c0 = j * 64, cols = min(64, n - c0);
+    if (tid < 64) xj[tid] = tid < cols ? __ldcg(x + c0 + tid) : 0.0;
+    __syncthreads();
+    // warp w handles rows 8w..8w+7 of this block; lanes run along the column
+    for (int rr = warp * 8; rr < warp * 8 + 8; rr++) {
+      if (rr >= rows) break;
+      const T* col = L + (int64_t)(r0 + rr) * n + c0;
+      double v = 0.0;
+      if (lane < cols) v += (double)col[lane] * xj[lane];
+      if (lane + 32 < cols) v += (double)col[lane + 32] * xj[lane + 32];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) accs[rr] += v;
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < rows * rows; q += 256) {
+    const int c = q / rows, i = q - c * rows;
+    Ld[i][c] = (double)L[(int64_t)(r0 + i) + (int64_t)(r0 + c) * n];
+  }
+  __syncthreads();
+  if (tid < 32) {
+    double a0 = lane < rows ? __ldcg(x + r0 + lane) - accs[lane] : 0.0;
+    double a1 = lane + 32 < rows ? __ldcg(x + r0 + lane + 32) - accs[lane + 32] : 0.0;
+    for (int c = rows - 1; c >= 0; c--) {
+      const double xc = __shfl_sync(0xffffffffu, c < 32 ? a0 : a1, c & 31);
+      if (lane < c) a0 -= Ld[c][lane] * xc;
+      if (lane + 32 < c) a1 -= Ld[c][lane + 32] * xc;
+    }
+    if (lane < rows) x[r0 + lane] = a0;
+    if (lane + 32 < rows) x[r0 + lane + 32] = a1;
+    __threadfence();  // publish this block's solution before its flag
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    *((volatile int*)(flags + b)) = epoch;
+  }
+}
+
 }  // namespace
 
-cudaError_t launch_dense_ldlt(Handle& h, cudaStream_t st) {
+cudaError_t launch_dense_ldlt(Handle& h, unsigned long long* counters, cudaStream_t st) {
   const int n = h.nC;
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = std::min(NB, n - k0);
     {
-    k_dense_diag<<<1, 256, 0, st>>>(h.S, n, k0, h.counters);
+    k_dense_diag<<<1, 256, 0, st>>>(h.S, n, k0, counters);
     h.launches++;
   }
     const int rest = n - k0 - kb;
@@ -218,35 +361,17 @@ cudaError_t launch_dense_ldlt(Handle& h, cudaStream_t st) {
 cudaError_t launch_dense_solve(Handle& h, const double* t, double* x, cudaStream_t st) {
   const int n = h.nC;
   if (n == 0) return cudaSuccess;
+  const int nb = (n + NB - 1) / NB;
   cudaError_t e = cudaMemcpyAsync(x, t, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h.trsv_ticket, 0, sizeof(unsigned) * 2, st);
   if (e != cudaSuccess) return e;
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int kb = std::min(NB, n - k0);
-    {
-    k_dense_fwd_diag<<<1, 32, 0, st>>>(h.S, x, n, k0);
-    h.launches++;
-  }
-    const int rest = n - k0 - kb;
-    if (rest > 0) {
-    k_dense_fwd_update<<<(rest + 255) / 256, 256, 0, st>>>(h.S, x, n, k0);
-    h.launches++;
-  }
-  }
-  {
-    k_dense_diag_scale<<<(n + 255) / 256, 256, 0, st>>>(h.S, x, n);
-    h.launches++;
-  }
-  const int last = ((n - 1) / NB) * NB;
-  for (int k0 = last; k0 >= 0; k0 -= NB) {
-    {
-    k_dense_bwd_dot<<<NB, 256, 0, st>>>(h.S, x, h.red + 8, n, k0);
-    h.launches++;
-  }
-    {
-    k_dense_bwd_diag<<<1, 32, 0, st>>>(h.S, x, h.red + 8, n, k0);
-    h.launches++;
-  }
-  }
+  // flags hold the epoch of the last solve that finished each block; two per solve
+  const int ep_f = ++h.trsv_epoch, ep_b = ++h.trsv_epoch;
+  k_trsv_lower<double><<<nb, 256, 0, st>>>(h.S, n, x, h.trsv_flags, h.trsv_ticket, ep_f, h.dev_err);
+  k_dense_diag_scale<<<(n + 255) / 256, 256, 0, st>>>(h.S, x, n);
+  k_trsv_upper<double><<<nb, 256, 0, st>>>(h.S, n, x, h.trsv_flags + nb, h.trsv_ticket + 1, ep_b,
+                                           h.dev_err);
+  h.launches += 3;
   return cudaGetLastError();
 }
 
@@ -274,6 +399,30 @@ cudaError_t launch_dense_solve_ws(Handle& h, const double* t, double* x, double*
     k_dense_bwd_diag<<<1, 32, 0, st>>>(h.S, x, dot, n, k0);
     h.launches += 2;
   }
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_dense_diag_scale_f32(const float* __restrict__ S, double* __restrict__ x, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x[i] /= (double)S[i + (int64_t)i * n];
+}
+}  // namespace
+
+// x = S32^{-1} t with the FP32 factor of the TF32/BF16 modes (FP64 accumulation)
+cudaError_t launch_dense_solve_f32(Handle& h, const double* t, double* x, cudaStream_t st) {
+  const int n = h.nC;
+  if (n == 0) return cudaSuccess;
+  const int nb = (n + NB - 1) / NB;
+  cudaError_t e = cudaMemcpyAsync(x, t, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h.trsv_ticket, 0, sizeof(unsigned) * 2, st);
+  if (e != cudaSuccess) return e;
+  const int ep_f = ++h.trsv_epoch, ep_b = ++h.trsv_epoch;
+  k_trsv_lower<float><<<nb, 256, 0, st>>>(h.S32, n, x, h.trsv_flags, h.trsv_ticket, ep_f, h.dev_err);
+  k_dense_diag_scale_f32<<<(n + 255) / 256, 256, 0, st>>>(h.S32, x, n);
+  k_trsv_upper<float><<<nb, 256, 0, st>>>(h.S32, n, x, h.trsv_flags + nb, h.trsv_ticket + 1, ep_b,
+                                          h.dev_err);
+  h.launches += 3;
   return cudaGetLastError();
 }
 

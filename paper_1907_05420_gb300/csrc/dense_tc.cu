@@ -1,0 +1,494 @@
+// (c) Dense LDL^T of S with the trailing update on the tensor cores
+// (tcgen05 MMA into tensor memory), in three arithmetics:
+//
+//   TF32 / BF16:  S held in FP32; the update S22 -= Y L21^T takes Y = L21 D and
+//                 L21 rounded to TF32 or BF16 and accumulates in FP32.
+//   F64 (emulated): S held in FP64.  Each row of Y and of L21 is scaled by a
+//                 power of two 2^e and cut into 7 signed 8-bit digits,
+//                 v = 2^e sum_s d_s 2^{-8(s+1)}, |d_s| <= 255, so every digit is
+//                 an exact BF16 integer and every digit product is exact in
+//                 FP32.  The 28 digit pairs with s + t <= 6 are accumulated per
+//                 level d = s + t in 7 FP32 tensor-memory accumulators (levels
+//                 0-3 stay below 2^24 and are exact for a 64-wide panel; the
+//                 rounding of levels >= 4 is below 2^-56 of the product), and
+//                 the levels are recombined in FP64:
+//                   (Y L^T)_ij = 2^{e_i+f_j} sum_d 2^{-8(d+2)} acc_d[i][j].
+//                 This is the FP64 product to within ~2^-50 relative.
+//
+// The blocked right-looking factorization (panel width 64) is that of
+// dense.cu; only the trailing update and its operand preparation live here:
+//   k_tc_slice:  writes the tile images of the update operands (the exact
+//                shared-memory layout of one 128-row A block or 64-row B block,
+//                all digit slices contiguous) and the row scales;
+//   k_tc_update: one CTA per 128 x 64 lower tile of the trailing matrix; the
+//                images arrive by bulk copy, one thread issues the MMAs, four
+//                warps drain tensor memory and update S.
+//
+// Shared-memory operand layout (K-major, no swizzle): an 8-row x 16-byte core
+// matrix is 128 contiguous bytes; cores are ordered K-fastest, so the
+// descriptor's leading byte offset (along K) is 128 and its stride byte offset
+// (along M/N) is 128 * (cores per row group).
+#include <cuda_bf16.h>
+
+#include "handle.h"
+
+namespace kkt {
+
+namespace {
+
+constexpr int TM = 128;       // rows of an A block (MMA M)
+constexpr int TN = 64;        // rows of a B block (MMA N)
+constexpr int TK = kDenseNB;  // panel width = reduction length
+constexpr int kEmuSlices = 7;
+constexpr int kEmuLevels = 7;
+constexpr long long kWaitBudget = 4000000000LL;  // cycles (~2 s)
+
+struct ModeCfg {
+  int kind;     // 0 bf16 operands, 1 tf32 operands
+  int slices;   // digit slices per operand
+  int levels;   // accumulators in tensor memory
+  int esz;      // bytes per operand element
+};
+
+__host__ __device__ constexpr ModeCfg mode_cfg(int mode) {
+  // mode: 0 = TF32, 1 = BF16, 2 = FP64 emulated on BF16 digit slices
+  return mode == 0 ? ModeCfg{1, 1, 1, 4} : (mode == 1 ? ModeCfg{0, 1, 1, 2} : ModeCfg{0, kEmuSlices, kEmuLevels, 2});
+}
+
+__host__ __device__ constexpr int kgroups_of(int mode) { return TK * mode_cfg(mode).esz / 16; }
+__host__ __device__ constexpr int slice_bytes(int mode, int rows) { return rows / 8 * kgroups_of(mode) * 128; }
+__host__ __device__ constexpr int image_bytes(int mode, int rows) {
+  return mode_cfg(mode).slices * slice_bytes(mode, rows);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of the fifth-generation tensor core
+  return d;                // base offset 0, no swizzle
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitBudget) return false;
+  }
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
+      "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+// digits of v / 2^e in [-1, 1): 7 truncated base-256 digits, exact in FP64
+__device__ __forceinline__ void digits7(double u, float out[kEmuSlices]) {
+#pragma unroll
+  for (int s = 0; s < kEmuSlices; s++) {
+    u *= 256.0;
+    const double d = trunc(u);
+    u -= d;
+    out[s] = (float)d;
+  }
+}
+
+// Images of the operands of one panel step.  Rows rho in [0, m) are trailing
+// rows base + rho.  A = Y (rows of L21 D, from Y with leading dimension n),
+// B = L21 (columns k0..k0+63 of S).  Rows >= m are written as zeros.
+template <int MODE, class T>
+__global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S, const T* __restrict__ Y,
+                                                  int n, int k0, int m, uint8_t* __restrict__ imgA,
+                                                  uint8_t* __restrict__ imgB, double* __restrict__ scaleA,
+                                                  double* __restrict__ scaleB, int mpadA, int mpadB) {
+  constexpr ModeCfg cfg = mode_cfg(MODE);
+  constexpr int KG = kgroups_of(MODE);
+  constexpr int kpc = 16 / cfg.esz;  // elements per 16-byte core row
+  const int base = k0 + TK;
+  const int total = mpadA + mpadB;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const bool isA = q < mpadA;
+    const int rho = isA ? q : q - mpadA;
+    const int rows_blk = isA ? TM : TN;
+    uint8_t* img = isA ? imgA : imgB;
+    const T* src = isA ? Y : S;
+    const int64_t col0 = isA ? 0 : k0;  // Y columns are 0..63, L21 columns k0..k0+63
+    const int blk = rho / rows_blk, rr = rho % rows_blk, g = rr / 8, r8 = rr % 8;
+    uint8_t* blk_img = img + (int64_t)blk * image_bytes(MODE, rows_blk);
+    const bool live = rho < m;
+    double e_scale = 1.0;
+    if (MODE == 2) {
+      double amax = 0.0;
+      if (live)
+        for (int c = 0; c < TK; c++) amax = fmax(amax, fabs((double)src[(int64_t)(base + rho) + (col0 + c) * n]));
+      int e = 0;
+      if (amax > 0.0) e = ilogb(amax) + 1;  // |v| < 2^e
+      e_scale = ldexp(1.0, e);
+      if (isA) scaleA[rho] = e_scale;
+      else scaleB[rho] = e_scale;
+    }
+    for (int kq = 0; kq < KG; kq++) {
+      // one 16-byte core row: elements kq*kpc .. kq*kpc+kpc-1
+      if (MODE == 2) {
+        float dig[kpc][kEmuSlices];
+#pragma unroll
+        for (int e = 0; e < kpc; e++) {
+          double v = live ? (double)src[(int64_t)(base + rho) + (col0 + kq * kpc + e) * n] : 0.0;
+          digits7(v / e_scale, dig[e]);
+        }
+#pragma unroll
+        for (int s = 0; s < kEmuSlices; s++) {
+          __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+          for (int e = 0; e < 8; e++) h[e] = __float2bfloat16_rn(dig[e][s]);
+          uint8_t* dst = blk_img + (int64_t)s * slice_bytes(MODE, rows_blk) + (g * KG + kq) * 128 + r8 * 16;
+          *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+        }
+      } else if (MODE == 1) {
+        __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++)
+          h[e] = __float2bfloat16_rn(live ? (float)src[(int64_t)(base + rho) + (col0 + kq * kpc + e) * n] : 0.f);
+        *reinterpret_cast<uint4*>(blk_img + (g * KG + kq) * 128 + r8 * 16) = *reinterpret_cast<const uint4*>(h);
+      } else {
+        __align__(16) float f[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) f[e] = live ? (float)src[(int64_t)(base + rho) + (col0 + kq * kpc + e) * n] : 0.f;
+        *reinterpret_cast<uint4*>(blk_img + (g * KG + kq) * 128 + r8 * 16) = *reinterpret_cast<const uint4*>(f);
+      }
+    }
+  }
+}
+
+// tile list: (I, J) with J <= 2I + 1 (tiles that hold part of the lower triangle)
+__device__ __forceinline__ void tile_of(int t, int TJ, int& I, int& J) {
+  // rows of the list: I = 0 has min(2, TJ) tiles, I has min(2I+2, TJ)
+  int i = 0;
+  for (;;) {
+    const int cnt = min(2 * i + 2, TJ);
+    if (t < cnt) break;
+    t -= cnt;
+    i++;
+  }
+  I = i;
+  J = t;
+}
+
+template <int MODE, class T>
+__global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S, int n, int k0, int m, int TJ,
+                                                      const uint8_t* __restrict__ imgA,
+                                                      const uint8_t* __restrict__ imgB,
+                                                      const double* __restrict__ scaleA,
+                                                      const double* __restrict__ scaleB, int* err) {
+  constexpr ModeCfg cfg = mode_cfg(MODE);
+  constexpr int KG = kgroups_of(MODE);
+  constexpr int A_BYTES = image_bytes(MODE, TM), B_BYTES = image_bytes(MODE, TN);
+  constexpr int A_SLICE = slice_bytes(MODE, TM), B_SLICE = slice_bytes(MODE, TN);
+  constexpr uint32_t TMEM_COLS = cfg.levels * TN <= 32 ? 32 : (cfg.levels * TN <= 64 ? 64 : (cfg.levels * TN <= 128 ? 128 : (cfg.levels * TN <= 256 ? 256 : 512)));
+  constexpr int MMA_K_BYTES = 32;  // one MMA consumes 32 bytes of K (16 bf16 or 8 tf32)
+  constexpr int KSTEPS = TK * cfg.esz / MMA_K_BYTES;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + A_BYTES;
+  __shared__ __align__(8) uint64_t bar_load, bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int I, J;
+  tile_of(blockIdx.x, TJ, I, J);
+  const int base = k0 + TK;
+
+  if (tid == 0) {
+    s_ok = 1;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_load)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+
+  if (tid == 0) {
+    // bulk copies of the two images (16 KB pieces), completion on bar_load
+    const uint32_t bl = smem_u32(&bar_load);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bl), "r"((uint32_t)(A_BYTES + B_BYTES))
+                 : "memory");
+    const uint8_t* srcA = imgA + (int64_t)I * A_BYTES;
+    const uint8_t* srcB = imgB + (int64_t)J * B_BYTES;
+    for (int off = 0; off < A_BYTES; off += 16384) {
+      const uint32_t sz = (uint32_t)min(16384, A_BYTES - off);
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_u32(sA + off)),
+                   "l"(srcA + off), "r"(sz), "r"(bl)
+                   : "memory");
+    }
+    for (int off = 0; off < B_BYTES; off += 16384) {
+      const uint32_t sz = (uint32_t)min(16384, B_BYTES - off);
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_u32(sB + off)),
+                   "l"(srcB + off), "r"(sz), "r"(bl)
+                   : "memory");
+    }
+    if (!mbar_wait(bl, 0)) {
+      atomicExch(err, 2);
+      s_ok = 0;
+      mbar_wait(bl, 0);  // give copies still in flight a second bounded window before exit
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t idesc = (1u << 4) | ((uint32_t)(cfg.kind == 0 ? 1 : 2) << 7) |
+                             ((uint32_t)(cfg.kind == 0 ? 1 : 2) << 10) | ((uint32_t)(TN >> 3) << 17) |
+                             ((uint32_t)(TM >> 4) << 24);
+      for (int d = 0; d < cfg.levels; d++) {
+        const uint32_t dtm = tmem + (uint32_t)(d * TN);
+        bool first = true;
+        for (int sa = 0; sa < cfg.slices; sa++) {
+          const int sb = d - sa;
+          if (cfg.slices > 1 && (sb < 0 || sb >= cfg.slices)) continue;
+          const int sbb = cfg.slices > 1 ? sb : 0;
+          for (int ks = 0; ks < KSTEPS; ks++) {
+            const uint64_t ad = umma_desc(smem_u32(sA + sa * A_SLICE + ks * MMA_K_BYTES * 8), 128, KG * 128);
+            const uint64_t bd = umma_desc(smem_u32(sB + sbb * B_SLICE + ks * MMA_K_BYTES * 8), 128, KG * 128);
+            const uint32_t acc = first ? 0u : 1u;
+            first = false;
+            if (cfg.kind == 0)
+              asm volatile(
+                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                      dtm),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            else
+              asm volatile(
+                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+                      dtm),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          }
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&bar_mma))
+                   : "memory");
+    }
+  }
+  __syncthreads();
+  bool ok = s_ok != 0;
+  if (ok) {
+    if (!mbar_wait(smem_u32(&bar_mma), 0)) {
+      atomicExch(err, 3);
+      ok = false;
+      mbar_wait(smem_u32(&bar_mma), 0);  // second bounded window before tensor memory is freed
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    const int rho = I * TM + warp * 32 + lane;  // this thread's tile row
+    const int row = base + rho;
+    const double sa = (MODE == 2 && rho < m) ? scaleA[rho] : 1.0;
+    for (int cc = 0; cc < TN / 32; cc++) {
+      uint32_t r[32];
+      if (MODE == 2) {
+        double acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) acc[j] = 0.0;
+        for (int d = 0; d < cfg.levels; d++) {
+          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * TN + cc * 32), r);
+          const double wd = ldexp(1.0, -8 * (d + 2));
+#pragma unroll
+          for (int j = 0; j < 32; j++) acc[j] += wd * (double)__uint_as_float(r[j]);
+        }
+        if (rho < m) {
+#pragma unroll
+          for (int j = 0; j < 32; j++) {
+            const int cj = J * TN + cc * 32 + j;  // trailing column index
+            const int col = base + cj;
+            if (cj < m && row >= col) {
+              T* p = S + (int64_t)row + (int64_t)col * n;
+              *p = (T)((double)*p - sa * scaleB[cj] * acc[j]);
+            }
+          }
+        }
+      } else {
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), r);
+        if (rho < m) {
+#pragma unroll
+          for (int j = 0; j < 32; j++) {
+            const int cj = J * TN + cc * 32 + j;
+            const int col = base + cj;
+            if (cj < m && row >= col) {
+              T* p = S + (int64_t)row + (int64_t)col * n;
+              *p = *p - (T)__uint_as_float(r[j]);
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// ---- FP32 panel kernels for the TF32 / BF16 modes (same steps as the FP64 ones in dense.cu) ----
+
+template <class T>
+__global__ void __launch_bounds__(256) k_dense_diag_t(T* __restrict__ S, int n, int k0,
+                                                      unsigned long long* __restrict__ counters) {
+  __shared__ T A[TK][TK + 1];
+  const int kb = min(TK, n - k0);
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
+    const int j = q / kb, i = q - j * kb;
+    A[i][j] = S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n];
+  }
+  __syncthreads();
+  for (int c = 0; c < kb; c++) {
+    const T d = A[c][c];
+    for (int r = c + 1 + threadIdx.x; r < kb; r += blockDim.x) A[r][c] = A[r][c] / d;
+    __syncthreads();
+    const int rem = kb - c - 1;
+    for (int q = threadIdx.x; q < rem * rem; q += blockDim.x) {
+      const int c2 = c + 1 + q / rem, r = c + 1 + q % rem;
+      if (r >= c2) A[r][c2] -= A[r][c] * d * A[c2][c];
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
+    const int j = q / kb, i = q - j * kb;
+    if (i >= j) S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n] = A[i][j];
+  }
+  if (threadIdx.x == 0) {
+    unsigned long long pos = 0, neg = 0, zero = 0;
+    for (int c = 0; c < kb; c++) {
+      const T d = A[c][c];
+      if (d > 0) pos++;
+      else if (d < 0) neg++;
+      else zero++;
+    }
+    atomicAdd(&counters[kPos], pos);
+    atomicAdd(&counters[kNeg], neg);
+    if (zero) atomicAdd(&counters[kZero], zero);
+  }
+}
+
+// rows below the block: solve y L11^T = a (one warp per row, L11 in shared memory)
+template <class T>
+__global__ void __launch_bounds__(256) k_dense_panel_t(T* __restrict__ S, T* __restrict__ Y, int n, int k0) {
+  __shared__ T L11[TK][TK + 1];
+  const int kb = min(TK, n - k0);
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
+    const int j = q / kb, i = q - j * kb;
+    L11[i][j] = S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int row = k0 + kb + blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);  // one warp per row
+  if (row >= n) return;
+  // lane holds y[lane] and y[lane+32]
+  T y0 = lane < kb ? S[row + (int64_t)(k0 + lane) * n] : T(0);
+  T y1 = lane + 32 < kb ? S[row + (int64_t)(k0 + lane + 32) * n] : T(0);
+  for (int c = 0; c < kb; c++) {
+    const T yc = __shfl_sync(0xffffffffu, c < 32 ? y0 : y1, c & 31);
+    if (lane > c && lane < kb) y0 -= yc * L11[lane][c];
+    if (lane + 32 > c && lane + 32 < kb) y1 -= yc * L11[lane + 32][c];
+  }
+  if (lane < kb) {
+    Y[row + (int64_t)lane * n] = y0;
+    S[row + (int64_t)(k0 + lane) * n] = y0 / L11[lane][lane];
+  }
+  if (lane + 32 < kb) {
+    Y[row + (int64_t)(lane + 32) * n] = y1;
+    S[row + (int64_t)(k0 + lane + 32) * n] = y1 / L11[lane + 32][lane + 32];
+  }
+}
+
+__global__ void k_to_f32(const double* __restrict__ S, float* __restrict__ S32, int64_t n2) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n2; q += (int64_t)gridDim.x * blockDim.x)
+    S32[q] = (float)S[q];
+}
+
+__global__ void k_dense_diag_scale_f(const float* __restrict__ S, double* __restrict__ x, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x[i] /= (double)S[i + (int64_t)i * n];
+}
+
+template <int MODE, class T>
+cudaError_t factor_tc(Handle& h, T* S, T* Y, unsigned long long* counters, cudaStream_t st) {
+  const int n = h.nC;
+  constexpr int A_BYTES = image_bytes(MODE, TM), B_BYTES = image_bytes(MODE, TN);
+  const int smem = A_BYTES + B_BYTES;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_update<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  for (int k0 = 0; k0 < n; k0 += TK) {
+    const int kb = std::min(TK, n - k0);
+    k_dense_diag_t<T><<<1, 256, 0, st>>>(S, n, k0, counters);
+    h.launches++;
+    const int m = n - k0 - kb;
+    if (m <= 0) continue;
+    k_dense_panel_t<T><<<(m + 7) / 8, 256, 0, st>>>(S, Y, n, k0);
+    h.launches++;
+    if (kb < TK) continue;  // a ragged last panel leaves no trailing matrix
+    const int TI = (m + TM - 1) / TM, TJ = (m + TN - 1) / TN;
+    const int mpadA = TI * TM, mpadB = TJ * TN;
+    const int sgrid = std::min((mpadA + mpadB + 255) / 256, 152 * 8);
+    k_tc_slice<MODE, T><<<sgrid, 256, 0, st>>>(S, Y, n, k0, m, h.tc_imgA, h.tc_imgB, h.tc_scaleA, h.tc_scaleB,
+                                               mpadA, mpadB);
+    int tiles = 0;
+    for (int I = 0; I < TI; I++) tiles += std::min(2 * I + 2, TJ);
+    k_tc_update<MODE, T><<<tiles, 128, smem, st>>>(S, n, k0, m, TJ, h.tc_imgA, h.tc_imgB, h.tc_scaleA,
+                                                   h.tc_scaleB, h.dev_err);
+    h.launches += 2;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t tc_image_bytes(int n, int mode) {
+  const int TI = (n + TM - 1) / TM + 1, TJ = (n + TN - 1) / TN + 1;
+  const int m = mode == KKT_TF32 ? 0 : (mode == KKT_BF16 ? 1 : 2);
+  const int ia = m == 0 ? image_bytes(0, TM) : (m == 1 ? image_bytes(1, TM) : image_bytes(2, TM));
+  const int ib = m == 0 ? image_bytes(0, TN) : (m == 1 ? image_bytes(1, TN) : image_bytes(2, TN));
+  return (int64_t)TI * ia + (int64_t)TJ * ib;
+}
+
+int64_t tc_image_bytes_a(int n, int mode) {
+  const int TI = (n + TM - 1) / TM + 1;
+  const int ia = mode == KKT_TF32 ? image_bytes(0, TM) : (mode == KKT_BF16 ? image_bytes(1, TM) : image_bytes(2, TM));
+  return (int64_t)TI * ia;
+}
+
+// The dense factor of S in precision `mode`.  TF32/BF16 factor the FP32 copy
+// S32 (S itself is kept for the FP64 fallback); the emulated FP64 mode
+// factors S in place.  `counters` receives the pivot signs.
+cudaError_t launch_dense_ldlt_tc(Handle& h, int mode, unsigned long long* counters, cudaStream_t st) {
+  const int n = h.nC;
+  if (n == 0) return cudaSuccess;
+  if (mode == KKT_F64_EMULATED) return factor_tc<2, double>(h, h.S, h.Ypanel, counters, st);
+  const int64_t n2 = (int64_t)n * n;
+  k_to_f32<<<(int)std::min<int64_t>((n2 + 255) / 256, 152 * 32), 256, 0, st>>>(h.S, h.S32, n2);
+  h.launches++;
+  if (mode == KKT_TF32) return factor_tc<0, float>(h, h.S32, h.Y32, counters, st);
+  return factor_tc<1, float>(h, h.S32, h.Y32, counters, st);
+}
+
+}  // namespace kkt

@@ -69,6 +69,7 @@ struct DevSym {
 
 // Counters written by the kernels (device, int64).
 enum Counter { kPos = 0, kNeg, kZero, kPerturbed, kNumCounters };
+// counters[0..3]: block pivots; counters[4..7]: pivots of the current factor of S
 
 struct Handle {
   // sizes
@@ -92,6 +93,13 @@ struct Handle {
   double* G = nullptr;        // N * k * k
   double* S = nullptr;        // nC * nC column-major (lower triangle used)
   double* Ypanel = nullptr;   // nC * kDenseNB scratch of the dense factor
+  float* S32 = nullptr;       // nC * nC FP32 copy factored in the TF32/BF16 modes
+  float* Y32 = nullptr;       // nC * kDenseNB FP32 panel scratch
+  uint8_t* tc_imgA = nullptr; // tensor-core operand images of one panel step
+  uint8_t* tc_imgB = nullptr;
+  double* tc_scaleA = nullptr;  // row scales of the emulated FP64 update
+  double* tc_scaleB = nullptr;
+  int s_factor = 0;           // current factor of S: 0 FP64-accurate in S, 1 FP32 in S32
   double* knorm = nullptr;    // ||K||_inf
   unsigned long long* counters = nullptr;  // kNumCounters
   // solve work vectors
@@ -107,6 +115,10 @@ struct Handle {
   double* rhs = nullptr;      // nK original right-hand side
   double* red = nullptr;      // reduction scratch (norms)
   double* host_red = nullptr; // pinned
+  int* trsv_flags = nullptr;  // 2 * ceil(nC/64): block-ready epochs of the dense triangular solves
+  unsigned* trsv_ticket = nullptr;  // 2 tickets (forward, backward)
+  int* dev_err = nullptr;     // set when a bounded device wait runs out
+  int trsv_epoch = 0;
   int64_t device_bytes = 0;
 
   bool factored = false;
@@ -129,8 +141,13 @@ cudaError_t launch_w_solve(Handle& h, cudaStream_t st);
 cudaError_t launch_contract_g(Handle& h, cudaStream_t st);
 cudaError_t launch_assemble_s(Handle& h, cudaStream_t st);
 // ---- (dense.cu) ----
-cudaError_t launch_dense_ldlt(Handle& h, cudaStream_t st);
+cudaError_t launch_dense_ldlt(Handle& h, unsigned long long* counters, cudaStream_t st);
 cudaError_t launch_dense_solve(Handle& h, const double* t, double* x, cudaStream_t st);
+cudaError_t launch_dense_solve_f32(Handle& h, const double* t, double* x, cudaStream_t st);
+// ---- (dense_tc.cu) ----
+cudaError_t launch_dense_ldlt_tc(Handle& h, int mode, unsigned long long* counters, cudaStream_t st);
+int64_t tc_image_bytes_a(int n, int mode);
+int64_t tc_image_bytes(int n, int mode);
 // ---- (solve.cu) ----
 cudaError_t launch_apply_inverse(Handle& h, const double* rhs, double* out, cudaStream_t st);
 cudaError_t launch_residual(Handle& h, const double* rhs, const double* x, double* rho,

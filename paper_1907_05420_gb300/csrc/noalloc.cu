@@ -75,6 +75,10 @@ extern "C" kkt_status kkt_solve_noalloc(kkt_handle* hh, const double* rhs, doubl
     set_error("kkt_solve_noalloc: no factorization");
     return KKT_ERR_STATE;
   }
+  if (h->s_factor != 0) {
+    set_error("kkt_solve_noalloc: needs an FP64-accurate factor of S (KKT_FP64 or KKT_F64_EMULATED)");
+    return KKT_ERR_STATE;
+  }
   const int64_t nz = (int64_t)h->N * h->nA, nk = (int64_t)h->N * h->cpl.k;
   const int64_t need = round_up(nz) + 2 * round_up(nk) + 2 * round_up(h->nC) + round_up(kDenseNB);
   if (need > kNoAllocScratchDoubles) {

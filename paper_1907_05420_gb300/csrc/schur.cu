@@ -18,18 +18,24 @@ namespace kkt {
 
 namespace {
 
+// One CTA per (reach supernode, block, chunk of 32 right-hand sides): the
+// columns of W are independent, so chunks spread the narrow top levels of the
+// tree over more SMs.
+constexpr int kWChunk = 32;
+
 __global__ void __launch_bounds__(128) k_w_solve(const int32_t* __restrict__ sn_list, DevSym d,
                                                  const double* __restrict__ Lx, int64_t pt,
                                                  double* __restrict__ W, int nw, int k) {
   const int s = sn_list[blockIdx.x], b = blockIdx.y;
+  const int t0 = blockIdx.z * kWChunk, nt = min(kWChunk, k - t0);
   const int m = (int)(d.sn_rowptr[s + 1] - d.sn_rowptr[s]);
   const int f = d.sn_first[s], w = d.sn_first[s + 1] - f;
   const int ws = d.sn_wrow[s];
   const double* P = Lx + b * pt + d.sn_valoff[s];
-  double* Wb = W + (int64_t)b * nw * k;
-  for (int q = threadIdx.x; q < w * k; q += blockDim.x) {
-    const int c = q / k, t = q - c * k;
-    Wb[(int64_t)(ws + c) * k + t] = d.wpos[t] == ws + c ? 1.0 : 0.0;
+  double* Wb = W + (int64_t)b * nw * k + t0;
+  for (int q = threadIdx.x; q < w * nt; q += blockDim.x) {
+    const int c = q / nt, t = q - c * nt;
+    Wb[(int64_t)(ws + c) * k + t] = d.wpos[t0 + t] == ws + c ? 1.0 : 0.0;
   }
   __syncthreads();
   for (int64_t u = d.upd_ptr[s]; u < d.upd_ptr[s + 1]; u++) {
@@ -41,9 +47,9 @@ __global__ void __launch_bounds__(128) k_w_solve(const int32_t* __restrict__ sn_
     const int wd = d.sn_first[dd + 1] - d.sn_first[dd];
     const double* Pd = Lx + b * pt + d.sn_valoff[dd];
     const int32_t* Rd = d.sn_rows + d.sn_rowptr[dd];
-    const int total = (r1 - r0) * k;
+    const int total = (r1 - r0) * nt;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
-      const int j = r0 + q / k, t = q % k;
+      const int j = r0 + q / nt, t = q % nt;
       double acc = 0.0;
       for (int kk = 0; kk < wd; kk++) acc += Pd[(int64_t)kk * md + j] * Wb[(int64_t)(wrd + kk) * k + t];
       Wb[(int64_t)(ws + Rd[j] - f) * k + t] -= acc;
@@ -51,9 +57,9 @@ __global__ void __launch_bounds__(128) k_w_solve(const int32_t* __restrict__ sn_
     __syncthreads();
   }
   for (int c = 0; c + 1 < w; c++) {
-    const int total = (w - 1 - c) * k;
+    const int total = (w - 1 - c) * nt;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
-      const int c2 = c + 1 + q / k, t = q % k;
+      const int c2 = c + 1 + q / nt, t = q % nt;
       Wb[(int64_t)(ws + c2) * k + t] -= P[(int64_t)c * m + c2] * Wb[(int64_t)(ws + c) * k + t];
     }
     __syncthreads();
@@ -153,7 +159,7 @@ cudaError_t launch_w_solve(Handle& h, cudaStream_t st) {
   for (int l = 0; l < h.sym.nlevels; l++) {
     const int s0 = h.reach_lvl_ptr[l], s1 = h.reach_lvl_ptr[l + 1];
     if (s1 == s0) continue;
-    dim3 grid(s1 - s0, h.N);
+    dim3 grid(s1 - s0, h.N, (k + kWChunk - 1) / kWChunk);
     {
     k_w_solve<<<grid, 128, 0, st>>>(h.d.reach_lvl_sn + s0, h.d, h.Lx, h.sym.panel_total, h.W,
                                     h.cpl.nw, k);

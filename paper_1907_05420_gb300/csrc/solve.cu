@@ -74,6 +74,91 @@ __global__ void __launch_bounds__(128) k_fsolve_level(const int32_t* __restrict_
   if (lane < w) zb[f + lane] = zc;
 }
 
+// Narrow levels (few supernodes x blocks): one CTA of kSolveWarps warps per
+// (supernode, block).  Forward: warp w accumulates the updates u with
+// u % kSolveWarps == w into its own partial vector; the partials are summed in
+// warp order.  Backward: warp w owns the columns c with c % kSolveWarps == w.
+constexpr int kSolveWarps = 8;
+constexpr int kWideLevelWarps = 152 * 32;  // levels with fewer (supernode, block) pairs use a CTA per pair
+
+__global__ void __launch_bounds__(kSolveWarps * 32) k_fsolve_level_wide(
+    const int32_t* __restrict__ sn_list, DevSym d, const double* __restrict__ Lx, int64_t pt,
+    double* __restrict__ z, int nA) {
+  __shared__ double part[kSolveWarps][32];
+  const int s = sn_list[blockIdx.x], b = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = (int)(d.sn_rowptr[s + 1] - d.sn_rowptr[s]);
+  const int f = d.sn_first[s], w = d.sn_first[s + 1] - f;
+  const double* P = Lx + b * pt + d.sn_valoff[s];
+  double* zb = z + (int64_t)b * nA;
+  double mine = 0.0;  // partial for row f + lane of this warp's updates
+  for (int64_t u = d.upd_ptr[s] + warp; u < d.upd_ptr[s + 1]; u += kSolveWarps) {
+    const int dd = d.upd_src[u];
+    const int r0 = d.upd_r0[u], r1 = d.upd_r1[u];
+    const int md = (int)(d.sn_rowptr[dd + 1] - d.sn_rowptr[dd]);
+    const int fd = d.sn_first[dd], wd = d.sn_first[dd + 1] - fd;
+    const double* Pd = Lx + b * pt + d.sn_valoff[dd];
+    const int32_t* Rd = d.sn_rows + d.sn_rowptr[dd];
+    // lane j handles row r0 + j of d; its target is row Rd[r0 + j] - f of s
+    double acc = 0.0;
+    const int j = r0 + lane;
+    if (j < r1)
+      for (int kk = 0; kk < wd; kk++) acc += Pd[(int64_t)kk * md + j] * zb[fd + kk];
+    const int tgt = j < r1 ? Rd[j] - f : -1;
+    // route acc to the lane owning its target row (targets are distinct within an update)
+    for (int src = 0; src < r1 - r0; src++) {
+      const double v = __shfl_sync(0xffffffffu, acc, src);
+      const int tg = __shfl_sync(0xffffffffu, tgt, src);
+      if (lane == tg) mine += v;
+    }
+  }
+  part[warp][lane] = mine;
+  __syncthreads();
+  if (warp == 0) {
+    double zc = 0.0;
+    if (lane < w) {
+      double sum = 0.0;
+      for (int q = 0; q < kSolveWarps; q++) sum += part[q][lane];
+      zc = zb[f + lane] - sum;
+    }
+    for (int c = 0; c + 1 < w; c++) {
+      const double zcc = __shfl_sync(0xffffffffu, zc, c);
+      if (lane > c && lane < w) zc -= P[(int64_t)c * m + lane] * zcc;
+    }
+    if (lane < w) zb[f + lane] = zc;
+  }
+}
+
+__global__ void __launch_bounds__(kSolveWarps * 32) k_bsolve_level_wide(
+    const int32_t* __restrict__ sn_list, DevSym d, const double* __restrict__ Lx, int64_t pt,
+    double* __restrict__ z, int nA) {
+  __shared__ double dots[32];
+  const int s = sn_list[blockIdx.x], b = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = (int)(d.sn_rowptr[s + 1] - d.sn_rowptr[s]);
+  const int f = d.sn_first[s], w = d.sn_first[s + 1] - f;
+  const double* P = Lx + b * pt + d.sn_valoff[s];
+  const int32_t* R = d.sn_rows + d.sn_rowptr[s];
+  double* zb = z + (int64_t)b * nA;
+  for (int c = warp; c < w; c += kSolveWarps) {
+    const double* col = P + (int64_t)c * m;
+    double acc = 0.0;
+    for (int r = w + lane; r < m; r += 32) acc += col[r] * zb[R[r]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) dots[c] = acc;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double mine = lane < w ? zb[f + lane] - dots[lane] : 0.0;
+    for (int c = w - 1; c >= 0; c--) {
+      const double xc = __shfl_sync(0xffffffffu, mine, c);
+      if (lane < c) mine -= P[(int64_t)lane * m + c] * xc;
+    }
+    if (lane < w) zb[f + lane] = mine;
+  }
+}
+
 // z /= D (D from the panel diagonals)
 __global__ void k_diag_scale(const int64_t* __restrict__ col_dpos, const double* __restrict__ Lx,
                              int64_t pt, double* __restrict__ z, int nA, int N) {
@@ -334,10 +419,12 @@ cudaError_t launch_apply_inverse(Handle& h, const double* r, double* out, cudaSt
   for (int l = 0; l < h.sym.nlevels; l++) {
     const int s0 = h.lvl_ptr[l], nsn = h.lvl_ptr[l + 1] - s0;
     const int warps = nsn * N;
-    {
-    k_fsolve_level<<<(warps + 3) / 4, 128, 0, st>>>(h.d.lvl_sn + s0, nsn, h.d, h.Lx, pt, h.z, nA, N);
+    if (warps < kWideLevelWarps) {
+      k_fsolve_level_wide<<<dim3(nsn, N), kSolveWarps * 32, 0, st>>>(h.d.lvl_sn + s0, h.d, h.Lx, pt, h.z, nA);
+    } else {
+      k_fsolve_level<<<(warps + 3) / 4, 128, 0, st>>>(h.d.lvl_sn + s0, nsn, h.d, h.Lx, pt, h.z, nA, N);
+    }
     h.launches++;
-  }
   }
   if (h.nC > 0) {
     if (k > 0 && nw > 0) {
@@ -354,7 +441,8 @@ cudaError_t launch_apply_inverse(Handle& h, const double* r, double* out, cudaSt
                                                    h.b_vals, h.u, k, h.nC, h.tg);
     h.launches++;
   }
-    cudaError_t e = launch_dense_solve(h, h.tg, h.xg, st);
+    cudaError_t e = h.s_factor == 1 ? launch_dense_solve_f32(h, h.tg, h.xg, st)
+                                    : launch_dense_solve(h, h.tg, h.xg, st);
     if (e != cudaSuccess) return e;
     if (k > 0 && nw > 0) {
       {
@@ -374,10 +462,12 @@ cudaError_t launch_apply_inverse(Handle& h, const double* r, double* out, cudaSt
   for (int l = h.sym.nlevels - 1; l >= 0; l--) {
     const int s0 = h.lvl_ptr[l], nsn = h.lvl_ptr[l + 1] - s0;
     const int warps = nsn * N;
-    {
-    k_bsolve_level<<<(warps + 3) / 4, 128, 0, st>>>(h.d.lvl_sn + s0, nsn, h.d, h.Lx, pt, h.z, nA, N);
+    if (warps < kWideLevelWarps) {
+      k_bsolve_level_wide<<<dim3(nsn, N), kSolveWarps * 32, 0, st>>>(h.d.lvl_sn + s0, h.d, h.Lx, pt, h.z, nA);
+    } else {
+      k_bsolve_level<<<(warps + 3) / 4, 128, 0, st>>>(h.d.lvl_sn + s0, nsn, h.d, h.Lx, pt, h.z, nA, N);
+    }
     h.launches++;
-  }
   }
   {
     k_permute_out<<<grid_for(nb), 256, 0, st>>>(h.z, h.d.perm, out, nA, N);

@@ -1,0 +1,51 @@
+"""Precision modes of the dense factor of S against the oracle.
+
+KKT_F64_EMULATED factors S FP64-accurately with the trailing update on the BF16
+tensor cores (exact digit-slice products); it must meet the same parity bar as
+KKT_FP64.  KKT_TF32 / KKT_BF16 factor S in FP32 on the tensor cores; FP64
+refinement on K either converges or falls back to the FP64-accurate factor, so
+every mode must reach eta <= 1e-10.  The inertia must be exact whenever the
+factor of S in use is FP64-accurate (FP64, emulated FP64, or after the
+fallback); an FP32 factor of an ill-conditioned S may flip pivot signs.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle
+from gen import CONFIGS, make_problem
+from tests.kkt_dense import dense_K
+from tests.test_gpu_parity import check_against_oracle, gpu_solve
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", ["f64emu", "tf32", "bf16"])
+@pytest.mark.parametrize("name", ["small", "grid30_n24"])
+def test_precision_modes_small(name, prec):
+    p = make_problem(CONFIGS[name])
+    x, info = gpu_solve(p, prec)
+    exact_s = prec == "f64emu" or info["fell_back_fp64"]
+    check_against_oracle(p, x, info, np.linalg.cond(dense_K(p)), inertia=exact_s)
+    if prec == "f64emu":
+        assert info["refine_steps"] <= 1
+
+
+@pytest.mark.parametrize("prec", ["f64emu", "tf32", "bf16"])
+def test_precision_modes_2383_bus_short_horizon(prec):
+    p = make_problem(replace(CONFIGS["grid2383_n96"], n_per=6))
+    x, info = gpu_solve(p, prec)
+    exact_s = prec == "f64emu" or info["fell_back_fp64"]
+    eta, err = check_against_oracle(p, x, info, inertia=exact_s)
+    print(f"{prec}: eta={eta:.2e} err={err:.2e} steps={info['refine_steps']} "
+          f"fallback={info['fell_back_fp64']}")
+
+
+def test_emulated_factor_matches_fp64_factor_solution():
+    """The emulated FP64 update reproduces the FP64 path to near FP64 accuracy."""
+    p = make_problem(replace(CONFIGS["grid2383_n96"], n_per=8))
+    x64, _ = gpu_solve(p, "fp64")
+    xe, info = gpu_solve(p, "f64emu")
+    assert oracle.backward_error(p, xe) <= 1e-14
+    assert np.max(np.abs(xe - x64)) / np.max(np.abs(x64)) <= 1e-6
