@@ -2,6 +2,7 @@
 //
 // Host orchestration only: every arithmetic step of the factor and of the
 // solve runs in the kernels of factor.cu, schur.cu, dense.cu and solve.cu.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -43,7 +44,7 @@ kkt_status cuda_status(cudaError_t e, const char* what) {
 void free_all(Handle* h) {
   void* ptrs[] = {h->d.sn_first, h->d.sn_rowptr, h->d.sn_rows, h->d.sn_valoff, h->d.upd_ptr,
                   h->d.upd_src, h->d.upd_r0, h->d.upd_r1, h->d.upd_reloff, h->d.upd_rel,
-                  h->d.lvl_sn, h->d.perm, h->d.a_map, h->d.col_primal, h->d.col_dpos, h->d.fwork,
+                  h->d.lvl_sn, h->d.perm, h->d.a_map, h->d.col_primal, h->d.col_dpos, h->d.fwork, h->d.frange,
                   h->d.full_rowptr, h->d.full_col, h->d.full_src, h->d.b_row, h->d.b_col,
                   h->d.b_blockptr, h->d.e_t, h->d.e_block, h->d.wpos, h->d.sn_wrow, h->d.w_dpos,
                   h->d.w_col, h->d.reach_lvl_sn, h->d.s_key, h->d.s_ptr, h->d.s_e1, h->d.s_e2,
@@ -144,20 +145,31 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   h->lvl_ptr = S.lvl_ptr;
   h->reach_lvl_ptr = C.reach_lvl_ptr;
 
-  // factor work items: 64-row tiles of every supernode, grouped by level
-  std::vector<int32_t> fwork;
+  // factor work items: 64-row tiles of every supernode, grouped by level; for
+  // every (tile, update) the rows [ia, ib) of the descendant that land in the tile
+  std::vector<int32_t> fwork, frange;
   h->fwork_lvl_ptr.assign(S.nlevels + 1, 0);
   for (int l = 0; l < S.nlevels; l++) {
     for (int q = S.lvl_ptr[l]; q < S.lvl_ptr[l + 1]; q++) {
       int s = S.lvl_sn[q];
       int m = (int)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]);
       for (int lo = 0; lo < m; lo += 64) {
+        const int hi = std::min(m, lo + 64);
         fwork.push_back(s);
         fwork.push_back(lo);
-        fwork.push_back(std::min(m, lo + 64));
+        fwork.push_back(hi);
+        fwork.push_back((int32_t)(frange.size() / 2));
+        for (int64_t u = S.upd_ptr[s]; u < S.upd_ptr[s + 1]; u++) {
+          const int32_t* rel = S.upd_rel.data() + S.upd_reloff[u];
+          const int64_t nrel = S.upd_reloff[u + 1] - S.upd_reloff[u];
+          const int32_t ia = S.upd_r0[u] + (int32_t)(std::lower_bound(rel, rel + nrel, lo) - rel);
+          const int32_t ib = S.upd_r0[u] + (int32_t)(std::lower_bound(rel, rel + nrel, hi) - rel);
+          frange.push_back(ia);
+          frange.push_back(ib);
+        }
       }
     }
-    h->fwork_lvl_ptr[l + 1] = (int32_t)(fwork.size() / 3);
+    h->fwork_lvl_ptr[l + 1] = (int32_t)(fwork.size() / 4);
   }
   // per-column pivot position and primal flag
   std::vector<int64_t> col_dpos(n);
@@ -227,6 +239,7 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   UP(col_primal, col_primal);
   UP(col_dpos, col_dpos);
   UP(fwork, fwork);
+  UP(frange, frange);
   UP(full_rowptr, full_rowptr);
   UP(full_col, full_col);
   UP(full_src, full_src);

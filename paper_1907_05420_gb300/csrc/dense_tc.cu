@@ -351,42 +351,49 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S, int n, 
 
 // ---- FP32 panel kernels for the TF32 / BF16 modes (same steps as the FP64 ones in dense.cu) ----
 
+// LDL^T of the 64 x 64 diagonal block with rows in registers: thread r holds
+// row r.  Step c publishes the unscaled column c (u_r = a_r[c], u_c = d) in a
+// double-buffered shared array, one barrier per step; thread r then sets
+// l_r = u_r / d and updates a_r[c2] -= l_r u_c2 for c < c2 <= r (since
+// l_c2 d = u_c2).
 template <class T>
-__global__ void __launch_bounds__(256) k_dense_diag_t(T* __restrict__ S, int n, int k0,
-                                                      unsigned long long* __restrict__ counters) {
-  __shared__ T A[TK][TK + 1];
+__global__ void __launch_bounds__(64) k_dense_diag_t(T* __restrict__ S, int n, int k0,
+                                                     unsigned long long* __restrict__ counters) {
+  __shared__ T colbuf[2][TK];
+  const int r = threadIdx.x;
   const int kb = min(TK, n - k0);
-  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
-    const int j = q / kb, i = q - j * kb;
-    A[i][j] = S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n];
-  }
-  __syncthreads();
-  for (int c = 0; c < kb; c++) {
-    const T d = A[c][c];
-    for (int r = c + 1 + threadIdx.x; r < kb; r += blockDim.x) A[r][c] = A[r][c] / d;
-    __syncthreads();
-    const int rem = kb - c - 1;
-    for (int q = threadIdx.x; q < rem * rem; q += blockDim.x) {
-      const int c2 = c + 1 + q / rem, r = c + 1 + q % rem;
-      if (r >= c2) A[r][c2] -= A[r][c] * d * A[c2][c];
+  T a[TK];
+#pragma unroll
+  for (int j = 0; j < TK; j++) a[j] = (r < kb && j <= r) ? S[(int64_t)(k0 + r) + (int64_t)(k0 + j) * n] : T(0);
+  T mydiag = T(0);
+#pragma unroll
+  for (int c = 0; c < TK; c++) {
+    if (c < kb) {
+      T* u = colbuf[c & 1];
+      if (r >= c && r < kb) u[r] = a[c];
+      __syncthreads();
+      const T d = u[c];
+      if (r == c) mydiag = d;
+      if (r > c && r < kb) {
+        const T l = a[c] / d;
+        a[c] = l;
+#pragma unroll
+        for (int c2 = c + 1; c2 < TK; c2++)
+          if (c2 <= r) a[c2] -= l * u[c2];
+      }
     }
-    __syncthreads();
   }
-  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
-    const int j = q / kb, i = q - j * kb;
-    if (i >= j) S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n] = A[i][j];
+  if (r < kb) {
+#pragma unroll
+    for (int j = 0; j < TK; j++)
+      if (j <= r) S[(int64_t)(k0 + r) + (int64_t)(k0 + j) * n] = a[j];
   }
-  if (threadIdx.x == 0) {
-    unsigned long long pos = 0, neg = 0, zero = 0;
-    for (int c = 0; c < kb; c++) {
-      const T d = A[c][c];
-      if (d > 0) pos++;
-      else if (d < 0) neg++;
-      else zero++;
-    }
-    atomicAdd(&counters[kPos], pos);
-    atomicAdd(&counters[kNeg], neg);
-    if (zero) atomicAdd(&counters[kZero], zero);
+  const int pos = __syncthreads_count(r < kb && mydiag > T(0));
+  const int neg = __syncthreads_count(r < kb && mydiag < T(0));
+  if (r == 0) {
+    atomicAdd(&counters[kPos], (unsigned long long)pos);
+    atomicAdd(&counters[kNeg], (unsigned long long)neg);
+    if (kb - pos - neg) atomicAdd(&counters[kZero], (unsigned long long)(kb - pos - neg));
   }
 }
 
@@ -440,7 +447,7 @@ cudaError_t factor_tc(Handle& h, T* S, T* Y, unsigned long long* counters, cudaS
   if (e != cudaSuccess) return e;
   for (int k0 = 0; k0 < n; k0 += TK) {
     const int kb = std::min(TK, n - k0);
-    k_dense_diag_t<T><<<1, 256, 0, st>>>(S, n, k0, counters);
+    k_dense_diag_t<T><<<1, TK, 0, st>>>(S, n, k0, counters);
     h.launches++;
     const int m = n - k0 - kb;
     if (m <= 0) continue;

@@ -60,15 +60,32 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int v) {
   return lo;
 }
 
-__global__ void __launch_bounds__(256) k_factor_update(const int32_t* __restrict__ work, DevSym d,
+// One CTA per (64-row tile of supernode s, block).  The tile's update is
+// accumulated in shared memory over all descendants d (in update order) and
+// subtracted from the panel once.  For each update the rows of d that land in
+// the tile ([ia, ib), precomputed per tile) and the rows that land in s's
+// columns ([r0, r1)) are staged in shared memory, the latter pre-multiplied by D_d.
+constexpr int kTileRows = 64;
+
+__global__ void __launch_bounds__(256) k_factor_update(const int32_t* __restrict__ work,
+                                                       const int32_t* __restrict__ frange, DevSym d,
                                                        double* __restrict__ Lx, int64_t pt) {
-  const int item = blockIdx.x, b = blockIdx.y;
-  const int s = work[3 * item], lo = work[3 * item + 1], hi = work[3 * item + 2];
+  __shared__ double acc[kTileRows][kMaxSnWidth + 1];
+  __shared__ double Li[kTileRows][kMaxSnWidth + 1];
+  __shared__ double Lj[kMaxSnWidth][kMaxSnWidth + 1];
+  __shared__ int rs[kTileRows], tc[kMaxSnWidth];
+  const int item = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+  const int s = work[4 * item], lo = work[4 * item + 1], hi = work[4 * item + 2];
+  const int roff = work[4 * item + 3];
   const int ms = (int)(d.sn_rowptr[s + 1] - d.sn_rowptr[s]);
-  const int f = d.sn_first[s];
+  const int f = d.sn_first[s], ws = d.sn_first[s + 1] - f;
+  const int nrow = hi - lo;
   double* P = Lx + b * pt + d.sn_valoff[s];
-  __shared__ int range[2];
-  for (int64_t u = d.upd_ptr[s]; u < d.upd_ptr[s + 1]; u++) {
+  for (int q = tid; q < kTileRows * (kMaxSnWidth + 1); q += blockDim.x) (&acc[0][0])[q] = 0.0;
+  const int64_t u0 = d.upd_ptr[s], u1 = d.upd_ptr[s + 1];
+  for (int64_t u = u0; u < u1; u++) {
+    const int ia = frange[2 * (roff + (u - u0))], ib = frange[2 * (roff + (u - u0)) + 1];
+    if (ia >= ib) continue;  // no row of this descendant falls in the tile
     const int dd = d.upd_src[u];
     const int r0 = d.upd_r0[u], r1 = d.upd_r1[u];
     const int md = (int)(d.sn_rowptr[dd + 1] - d.sn_rowptr[dd]);
@@ -76,24 +93,31 @@ __global__ void __launch_bounds__(256) k_factor_update(const int32_t* __restrict
     const double* Pd = Lx + b * pt + d.sn_valoff[dd];
     const int32_t* Rd = d.sn_rows + d.sn_rowptr[dd];
     const int32_t* rel = d.upd_rel + d.upd_reloff[u];
-    if (threadIdx.x == 0) {
-      range[0] = r0 + lower_bound_i32(rel, md - r0, lo);
-      range[1] = r0 + lower_bound_i32(rel, md - r0, hi);
+    const int ni = ib - ia, nj = r1 - r0;
+    __syncthreads();  // the previous update's reads of Li/Lj are done
+    for (int q = tid; q < ni * wd; q += blockDim.x) {
+      const int i = q % ni, kk = q / ni;
+      Li[i][kk] = Pd[(int64_t)kk * md + ia + i];
     }
-    __syncthreads();
-    const int ia = range[0], ni = range[1] - range[0], nj = r1 - r0;
-    const int total = ni * nj;
-    for (int q = threadIdx.x; q < total; q += blockDim.x) {
-      const int i = ia + q % ni, j = r0 + q / ni;
-      if (i < j) continue;
-      double acc = 0.0;
-      for (int kk = 0; kk < wd; kk++) {
-        const double* col = Pd + (int64_t)kk * md;
-        acc += col[i] * col[kk] * col[j];
-      }
-      P[(int64_t)(Rd[j] - f) * ms + rel[i - r0]] -= acc;
+    for (int q = tid; q < nj * wd; q += blockDim.x) {
+      const int j = q % nj, kk = q / nj;
+      Lj[j][kk] = Pd[(int64_t)kk * md + r0 + j] * Pd[(int64_t)kk * md + kk];
     }
+    for (int q = tid; q < ni; q += blockDim.x) rs[q] = rel[ia + q - r0] - lo;
+    for (int q = tid; q < nj; q += blockDim.x) tc[q] = Rd[r0 + q] - f;
     __syncthreads();
+    for (int q = tid; q < ni * nj; q += blockDim.x) {
+      const int i = q % ni, j = q / ni;
+      if (ia + i < r0 + j) continue;  // above the diagonal of the target
+      double sum = 0.0;
+      for (int kk = 0; kk < wd; kk++) sum += Li[i][kk] * Lj[j][kk];
+      acc[rs[i]][tc[j]] += sum;
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < nrow * ws; q += blockDim.x) {
+    const int r = q % nrow, c = q / nrow;
+    P[(int64_t)c * ms + lo + r] -= acc[r][c];
   }
 }
 
@@ -163,7 +187,7 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
     if (l > 0 && w1 > w0) {
       dim3 grid(w1 - w0, h.N);
       {
-    k_factor_update<<<grid, 256, 0, st>>>(h.d.fwork + 3 * w0, h.d, h.Lx, pt);
+    k_factor_update<<<grid, 256, 0, st>>>(h.d.fwork + 4 * w0, h.d.frange, h.d, h.Lx, pt);
     h.launches++;
   }
     }

@@ -41,7 +41,8 @@ struct DevSym {
   int32_t* col_primal = nullptr;   // per column (elimination order): 1 if primal
   int64_t* col_dpos = nullptr;     // per column: panel position of its pivot
   // factor update work items: (supernode, first panel row, last panel row)
-  int32_t* fwork = nullptr;        // 3 ints per item
+  int32_t* fwork = nullptr;        // 4 ints per item: s, lo, hi, offset into frange
+  int32_t* frange = nullptr;       // per (item, update of s): rows [ia, ib) of d inside the tile
   // symmetric full CSR of A for the residual: entry p reads a_vals[full_src[p]]
   int32_t* full_rowptr = nullptr;
   int32_t* full_col = nullptr;

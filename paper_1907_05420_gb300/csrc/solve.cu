@@ -201,20 +201,30 @@ __global__ void __launch_bounds__(128) k_bsolve_level(const int32_t* __restrict_
   if (lane < w) zb[f + lane] = mine;
 }
 
-// u_b[t] = sum_rho W_b[rho][t] z_b[w_col[rho]] / D[rho]
-__global__ void k_reduce_u(const double* __restrict__ W, const double* __restrict__ z,
-                           const double* __restrict__ Lx, int64_t pt, const int64_t* __restrict__ w_dpos,
-                           const int32_t* __restrict__ w_col, int nw, int k, int nA,
-                           double* __restrict__ u) {
-  const int b = blockIdx.y;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= k) return;
+// u_b[t] = sum_rho W_b[rho][t] z_b[w_col[rho]] / D[rho]; one CTA per (block,
+// 32 columns): warp w sums the rows rho = w mod 8, the 8 partials are added in
+// warp order.
+__global__ void __launch_bounds__(256) k_reduce_u(const double* __restrict__ W, const double* __restrict__ z,
+                                                  const double* __restrict__ Lx, int64_t pt,
+                                                  const int64_t* __restrict__ w_dpos,
+                                                  const int32_t* __restrict__ w_col, int nw, int k, int nA,
+                                                  double* __restrict__ u) {
+  __shared__ double part[8][32];
+  const int b = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 32 + lane;
   const double* Wb = W + (int64_t)b * nw * k;
   const double* zb = z + (int64_t)b * nA;
   const double* Pb = Lx + b * pt;
   double acc = 0.0;
-  for (int rho = 0; rho < nw; rho++) acc += Wb[(int64_t)rho * k + t] * (zb[w_col[rho]] / Pb[w_dpos[rho]]);
-  u[(int64_t)b * k + t] = acc;
+  if (t < k)
+    for (int rho = warp; rho < nw; rho += 8) acc += Wb[(int64_t)rho * k + t] * (zb[w_col[rho]] / Pb[w_dpos[rho]]);
+  part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && t < k) {
+    double sum = 0.0;
+    for (int q = 0; q < 8; q++) sum += part[q][lane];
+    u[(int64_t)b * k + t] = sum;
+  }
 }
 
 // t[c] = r_g[c] - sum_{e in column c} b[e] u[block(e)][t(e)]
@@ -428,9 +438,9 @@ cudaError_t launch_apply_inverse(Handle& h, const double* r, double* out, cudaSt
   }
   if (h.nC > 0) {
     if (k > 0 && nw > 0) {
-      dim3 g((k + 127) / 128, N);
+      dim3 g((k + 31) / 32, N);
       {
-    k_reduce_u<<<g, 128, 0, st>>>(h.W, h.z, h.Lx, pt, h.d.w_dpos, h.d.w_col, nw, k, nA, h.u);
+    k_reduce_u<<<g, 256, 0, st>>>(h.W, h.z, h.Lx, pt, h.d.w_dpos, h.d.w_col, nw, k, nA, h.u);
     h.launches++;
   }
     } else if (k > 0) {
@@ -556,8 +566,8 @@ cudaError_t launch_apply_inverse_ws(Handle& h, const double* r, double* out,
   }
   if (h.nC > 0) {
     if (k > 0 && nw > 0) {
-      dim3 g((k + 127) / 128, N);
-      k_reduce_u<<<g, 128, 0, st>>>(h.W, ws.z, h.Lx, pt, h.d.w_dpos, h.d.w_col, nw, k, nA, ws.u);
+      dim3 g((k + 31) / 32, N);
+      k_reduce_u<<<g, 256, 0, st>>>(h.W, ws.z, h.Lx, pt, h.d.w_dpos, h.d.w_col, nw, k, nA, ws.u);
       h.launches++;
     } else if (k > 0) {
       cudaError_t e = cudaMemsetAsync(ws.u, 0, sizeof(double) * (size_t)k * N, st);
