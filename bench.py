@@ -176,7 +176,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32", "bf16"])
+    ap.add_argument("--prec", default="tf32", choices=["fp64", "tf32", "bf16", "f64emu"],
+                    help="arithmetic of the dense factor of S on the timed path (default: the "
+                         "mixed path, TF32 tensor cores with FP64 refinement)")
+    ap.add_argument("--legs", default="fp64,f64emu,bf16,tf32+tcg",
+                    help="other precision modes measured beside the timed path ('' for none)")
+    ap.add_argument("--leg-steps", type=int, default=4)
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -206,10 +211,6 @@ def main():
 
     prob = make_problem(CONFIGS[args.workload])
     stream = torch.cuda.current_stream()
-    opt = B.kkt_default_options(args.prec)
-    h = B.kkt_analyze(prob, opt)
-    info0 = B.kkt_get_info(h)
-
     a = torch.from_numpy(np.ascontiguousarray(prob.a_vals)).to(dev)
     b = torch.from_numpy(np.ascontiguousarray(prob.b_vals)).to(dev)
     c = torch.from_numpy(np.ascontiguousarray(prob.c_vals)).to(dev)
@@ -217,53 +218,73 @@ def main():
     x = torch.empty_like(r)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def step_device():
-        B.kkt_factor(h, a, b, c, stream)
-        B.kkt_solve(h, r, x, 1, stream)
+    def time_mode(mode, steps, warmup, sample_clocks=False):
+        """Factor + refined solve of the workload, `steps` timed repetitions.
 
-    for _ in range(args.warmup):
-        step_device()
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
+        mode: a precision name; a '+tcg' suffix also runs the Schur contraction on
+        the tensor cores in that precision."""
+        prec, _, extra = mode.partition("+")
+        h = B.kkt_analyze(prob, B.kkt_default_options(prec, reduced_contraction=int(extra == "tcg")))
+        info0 = B.kkt_get_info(h)
 
-    launches0 = B.kkt_get_info(h)["n_launches"]
-    clocks = ClockSampler(local)
-    clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    phases = {"a_block_factor": [], "b_schur_assembly": [], "c_dense_factor": [], "d_solve": []}
-    etas, steps_ir = [], []
-    t_wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        step_device()
-        ev[i][1].record(stream)
-        inf = B.kkt_get_info(h)
-        phases["a_block_factor"].append(inf["ms_block_factor"])
-        phases["b_schur_assembly"].append(inf["ms_schur_assembly"])
-        phases["c_dense_factor"].append(inf["ms_dense_factor"])
-        phases["d_solve"].append(inf["ms_solve_device"])
-        etas.append(inf["rel_residual"])
-        steps_ir.append(inf["refine_steps"])
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter() - t_wall0
-    clk = clocks.stop()
-    info = B.kkt_get_info(h)
-    launches = info["n_launches"] - launches0
-    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
+        def step_device():
+            B.kkt_factor(h, a, b, c, stream)
+            B.kkt_solve(h, r, x, 1, stream, allow_not_converged=True)
 
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * args.steps / total_s
-    x_gpu = x.cpu().numpy()
+        for _ in range(warmup):
+            step_device()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        launches0 = B.kkt_get_info(h)["n_launches"]
+        clocks = ClockSampler(local) if sample_clocks else None
+        if clocks:
+            clocks.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        phases = {"a_block_factor": [], "b_schur_assembly": [], "c_dense_factor": [], "d_solve": []}
+        etas, steps_ir, fallback = [], [], []
+        t_wall0 = time.perf_counter()
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step_device()
+            ev[i][1].record(stream)
+            inf = B.kkt_get_info(h)
+            phases["a_block_factor"].append(inf["ms_block_factor"])
+            phases["b_schur_assembly"].append(inf["ms_schur_assembly"])
+            phases["c_dense_factor"].append(inf["ms_dense_factor"])
+            phases["d_solve"].append(inf["ms_solve_device"])
+            etas.append(inf["rel_residual"])
+            steps_ir.append(inf["refine_steps"])
+            fallback.append(inf["fell_back_fp64"])
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+        clk = clocks.stop() if clocks else None
+        info = B.kkt_get_info(h)
+        step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+        total_s = sum(step_ms) / 1e3
+        if world > 1:
+            import torch.distributed as dist
+
+            t = torch.tensor([total_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_s = float(t.item())
+        return {"h": h, "info0": info0, "info": info, "step_ms": step_ms, "total_s": total_s,
+                "phases": phases, "etas": etas, "steps_ir": steps_ir, "fallback": fallback,
+                "clocks": clk, "launches": info["n_launches"] - launches0, "wall_s": t_wall,
+                "x": x.cpu().numpy()}
+
+    main_run = time_mode(args.prec, args.steps, args.warmup, sample_clocks=True)
+    h = main_run["h"]
+    info0, info = main_run["info0"], main_run["info"]
+    step_ms, phases = main_run["step_ms"], main_run["phases"]
+    etas, steps_ir = main_run["etas"], main_run["steps_ir"]
+    clk, launches, t_wall = main_run["clocks"], main_run["launches"], main_run["wall_s"]
+    value = world * args.steps / main_run["total_s"]
+    x_gpu = main_run["x"]
 
     # end to end through the public API with host buffers: H2D of the step's
     # inputs and D2H of the solution inside the timed region
@@ -274,7 +295,7 @@ def main():
         hx = torch.empty_like(hr).pin_memory()
         for _ in range(max(1, args.warmup)):
             B.kkt_factor(h, ha, hb, hc, stream)
-            B.kkt_solve(h, hr, hx, 1, stream)
+            B.kkt_solve(h, hr, hx, 1, stream, allow_not_converged=True)
         torch.cuda.synchronize()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -282,7 +303,7 @@ def main():
         for _ in range(args.steps):
             flush.zero_()
             B.kkt_factor(h, ha, hb, hc, stream)
-            B.kkt_solve(h, hr, hx, 1, stream)
+            B.kkt_solve(h, hr, hx, 1, stream, allow_not_converged=True)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -296,6 +317,19 @@ def main():
         h2d = sum(t.numel() * t.element_size() for t in (ha, hb, hc, hr))
         e2e = {"value": world * args.steps / e2e_s, "unit": "solves/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hx.numel() * 8)}
+
+    legs = {}
+    for leg in [m for m in args.legs.split(",") if m and m != args.prec]:
+        lr = time_mode(leg, args.leg_steps, 2)
+        B.kkt_destroy(lr["h"])
+        legs[leg] = {"value": world * args.leg_steps / lr["total_s"], "unit": "solves/s",
+                     "ms_per_step": statistics.mean(lr["step_ms"]),
+                     "latency_ms": {"p50": float(np.percentile(lr["step_ms"], 50)),
+                                    "p99": float(np.percentile(lr["step_ms"], 99))},
+                     "residual_eta_max": max(lr["etas"]), "refine_steps": lr["steps_ir"][-1],
+                     "fell_back_fp64": lr["fallback"][-1],
+                     "phases_ms": {kk: statistics.mean(v) for kk, v in lr["phases"].items()},
+                     "_x": lr["x"]}
 
     # roofline of the dominant phase (algorithmic work / measured phase time)
     peaks, peak_kind = _peaks()
@@ -319,10 +353,14 @@ def main():
         achieved = work[dom]["bytes"] / t_dom / 1e9
         peak_src = f"hbm_gbs of {peak_kind} peaks"
     elif dom == "c_dense_factor" and args.prec != "fp64":
-        ratio = 0.5 if args.prec == "tf32" else 1.0
+        # TF32 runs at half the BF16 rate (nominal 1.1 vs 2.25 PFLOP/s dense); the
+        # emulated FP64 update issues 28 BF16 digit products per FP64 product
+        ratio = {"tf32": 0.5, "bf16": 1.0, "f64emu": 1.0}[args.prec]
+        mult = 28.0 if args.prec == "f64emu" else 1.0
         bound, peak, unit = "tensor", peaks["bf16_tflops"] * ratio, "TFLOP/s"
-        achieved = work[dom]["flops"] / t_dom / 1e12
-        peak_src = f"bf16_tflops of {peak_kind} peaks x {ratio} ({args.prec})"
+        achieved = mult * work[dom]["flops"] / t_dom / 1e12
+        peak_src = (f"bf16_tflops of {peak_kind} peaks x {ratio} ({args.prec})" +
+                    (", achieved counts the 28 digit products" if mult > 1 else ""))
     else:
         bound, peak, unit = "alu", fp64_gflops / 1e3, "TFLOP/s"
         achieved = work[dom]["flops"] / t_dom / 1e12
@@ -340,7 +378,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.prec == "fp64" else f"f64+{args.prec}", "data": "synthetic",
+        "dtype": {"fp64": "f64", "tf32": "f64+tf32", "bf16": "f64+bf16", "f64emu": "f64+bf16x7"}[args.prec],
+        "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "precision": args.prec,
                    "l2": "256 MB buffer written before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -348,7 +387,8 @@ def main():
         "residual_eta_max": max(etas), "refine_steps_mean": ir,
         "roofline": roofline, "phases": phase_report, "fp64_peak_gflops_measured": fp64_gflops,
         "e2e": e2e, "clocks": clk, "gpu_launches": int(launches), "wall_s_timed": t_wall,
-        "analyze_ms": info0["ms_analyze"],
+        "analyze_ms": info0["ms_analyze"], "refine_steps_last": steps_ir[-1],
+        "fell_back_fp64": main_run["fallback"][-1], "other_precisions": legs,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out, dt = cpu_reference_solve(prob)
@@ -359,7 +399,12 @@ def main():
                                 "sample": f"1 full solve of {args.workload} (FP64 oracle, OpenMP; "
                                           "ordering computed once, untimed)"}
         xo = out["x"]
-        line["error_vs_oracle"] = float(np.max(np.abs(x_gpu - xo)) / np.max(np.abs(xo)))
+        err = lambda xv: float(np.max(np.abs(xv - xo)) / np.max(np.abs(xo)))  # noqa: E731
+        line["error_vs_oracle"] = err(x_gpu)
+        for leg in legs.values():
+            leg["error_vs_oracle"] = err(leg["_x"])
+    for leg in legs.values():
+        leg.pop("_x", None)
     B.kkt_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -97,7 +97,11 @@ typedef struct {
                           with the expected sign and counted; 0 turns the perturbation off */
   int32_t use_graphs;  /* capture the factor/solve launch sequences in CUDA graphs */
   int32_t fp64_fallback; /* refactor S in FP64 when refinement stalls in a reduced mode */
-  int32_t reserved[4];
+  int32_t reduced_contraction; /* KKT_TF32/KKT_BF16 only: also run the Schur contraction
+                                  G_i = W_i^T D_i^{-1} W_i on the tensor cores in that precision
+                                  (0, the default: FP64 contraction).  On a stall the fallback then
+                                  recomputes G in FP64 and reassembles S before refactoring it. */
+  int32_t reserved[3];
 } kkt_options;
 
 typedef struct {

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libkkt_schur.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["api.cu", "factor.cu", "schur.cu", "dense.cu", "solve.cu", "probe.cu", "noalloc.cu", "dense_tc.cu"]
+CU = ["api.cu", "factor.cu", "schur.cu", "dense.cu", "solve.cu", "probe.cu", "noalloc.cu", "dense_tc.cu", "schur_tc.cu"]
 CPP = ["symbolic.cpp"]
 HEADERS = ["handle.h", "symbolic.h"]
 

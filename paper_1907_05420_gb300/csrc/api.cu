@@ -48,7 +48,7 @@ void free_all(Handle* h) {
                   h->d.full_rowptr, h->d.full_col, h->d.full_src, h->d.b_row, h->d.b_col,
                   h->d.b_blockptr, h->d.e_t, h->d.e_block, h->d.wpos, h->d.sn_wrow, h->d.w_dpos,
                   h->d.w_col, h->d.reach_lvl_sn, h->d.s_key, h->d.s_ptr, h->d.s_e1, h->d.s_e2,
-                  h->d.t_ptr, h->d.t_e, h->d.bt_ptr, h->d.E, h->Lx, h->a_vals, h->b_vals,
+                  h->d.t_ptr, h->d.t_e, h->d.bt_ptr, h->d.E, h->d.g_rows, h->Lx, h->a_vals, h->b_vals,
                   h->c_vals, h->anorm, h->W, h->G, h->S, h->Ypanel, h->knorm, h->counters, h->r,
                   h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red,
                   h->trsv_flags, h->trsv_ticket, h->dev_err, h->S32, h->Y32, h->tc_imgA,
@@ -191,6 +191,22 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
       w_dpos[C.sn_wrow[s] + c] = col_dpos[f + c];
     }
   }
+  // W rows in contraction order: primal (positive pivot) rows, then multiplier
+  // rows, each group padded with -1 to whole 64-row chunks
+  std::vector<int32_t> g_rows;
+  {
+    std::vector<int32_t> pos_rows, neg_rows;
+    for (int r = 0; r < C.nw; r++) (col_primal[w_col[r]] ? pos_rows : neg_rows).push_back(r);
+    auto pad = [](std::vector<int32_t>& v) {
+      while (v.size() % 64) v.push_back(-1);
+    };
+    pad(pos_rows);
+    pad(neg_rows);
+    h->g_nchunks_pos = (int)(pos_rows.size() / 64);
+    h->g_nchunks = h->g_nchunks_pos + (int)(neg_rows.size() / 64);
+    g_rows = pos_rows;
+    g_rows.insert(g_rows.end(), neg_rows.begin(), neg_rows.end());
+  }
   // symmetric full CSR of A with source positions
   std::vector<int32_t> full_rowptr(n + 1, 0), full_col, full_src;
   for (int r = 0; r < n; r++)
@@ -261,6 +277,7 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   UP(t_e, C.t_e);
   UP(bt_ptr, C.bt_ptr);
   UP(E, C.E);
+  UP(g_rows, g_rows);
 #undef UP
   const int64_t nK = (int64_t)h->N * n + h->nC;
   const int64_t k = C.k;
@@ -351,7 +368,12 @@ kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals
   KKT_CUDA(launch_factor_levels(*h, st));
   KKT_CUDA(cudaEventRecord(h->ev_fa, st));
   KKT_CUDA(launch_w_solve(*h, st));
-  KKT_CUDA(launch_contract_g(*h, st));
+  h->g_reduced = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && h->opt.reduced_contraction &&
+                 contract_g_tc_supported(*h);
+  if (h->g_reduced)
+    KKT_CUDA(launch_contract_g_tc(*h, h->opt.prec == KKT_BF16 ? 1 : 0, st));
+  else
+    KKT_CUDA(launch_contract_g(*h, st));
   KKT_CUDA(launch_assemble_s(*h, st));
   KKT_CUDA(cudaEventRecord(h->ev_fb, st));
   if (h->opt.prec == KKT_FP64) {
@@ -415,6 +437,12 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
           // refinement with the FP32 factor of S stalls: refactor S (still the
           // assembled FP64 matrix) FP64-accurately and restart from its solve
           KKT_CUDA(cudaMemsetAsync(h->counters + kNumCounters, 0, sizeof(unsigned long long) * kNumCounters, st));
+          if (h->g_reduced) {
+            // S was assembled from a reduced-precision contraction: rebuild it in FP64
+            KKT_CUDA(launch_contract_g(*h, st));
+            KKT_CUDA(launch_assemble_s(*h, st));
+            h->g_reduced = false;
+          }
           KKT_CUDA(launch_dense_ldlt_tc(*h, KKT_F64_EMULATED, h->counters + kNumCounters, st));
           h->s_factor = 0;
           h->info.fell_back_fp64 = 1;

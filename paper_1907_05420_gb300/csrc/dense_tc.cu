@@ -99,15 +99,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
-// digits of v / 2^e in [-1, 1): 7 truncated base-256 digits, exact in FP64
-__device__ __forceinline__ void digits7(double u, float out[kEmuSlices]) {
+// The 7 base-256 digits of u = v / 2^e in (-1, 1), truncated toward zero:
+// q = trunc(u 2^56) is exact in int64 (|v| has 53 significant bits and the
+// scaling is a power of two), and digit s is byte 6 - s of |q| with the sign of v.
+__device__ __forceinline__ void digits7(double v, int e, float out[kEmuSlices]) {
+  const long long q = (long long)ldexp(v, 56 - e);  // conversion truncates toward zero
+  const unsigned long long a = (unsigned long long)(q < 0 ? -q : q);
+  const float sg = q < 0 ? -1.f : 1.f;
 #pragma unroll
-  for (int s = 0; s < kEmuSlices; s++) {
-    u *= 256.0;
-    const double d = trunc(u);
-    u -= d;
-    out[s] = (float)d;
-  }
+  for (int s = 0; s < kEmuSlices; s++) out[s] = sg * (float)((a >> (8 * (kEmuSlices - 1 - s))) & 0xFFull);
 }
 
 // Images of the operands of one panel step.  Rows rho in [0, m) are trailing
@@ -134,13 +134,13 @@ __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S, const
     uint8_t* blk_img = img + (int64_t)blk * image_bytes(MODE, rows_blk);
     const bool live = rho < m;
     double e_scale = 1.0;
+    int e_exp = 0;
     if (MODE == 2) {
       double amax = 0.0;
       if (live)
         for (int c = 0; c < TK; c++) amax = fmax(amax, fabs((double)src[(int64_t)(base + rho) + (col0 + c) * n]));
-      int e = 0;
-      if (amax > 0.0) e = ilogb(amax) + 1;  // |v| < 2^e
-      e_scale = ldexp(1.0, e);
+      e_exp = amax > 0.0 ? ilogb(amax) + 1 : 0;  // |v| < 2^e
+      e_scale = ldexp(1.0, e_exp);
       if (isA) scaleA[rho] = e_scale;
       else scaleB[rho] = e_scale;
     }
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S, const
 #pragma unroll
         for (int e = 0; e < kpc; e++) {
           double v = live ? (double)src[(int64_t)(base + rho) + (col0 + kq * kpc + e) * n] : 0.0;
-          digits7(v / e_scale, dig[e]);
+          digits7(v, e_exp, dig[e]);
         }
 #pragma unroll
         for (int s = 0; s < kEmuSlices; s++) {
@@ -308,37 +308,62 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S, int n, 
     for (int cc = 0; cc < TN / 32; cc++) {
       uint32_t r[32];
       if (MODE == 2) {
+        // levels 0-3 hold exact integers below 2^24: combine them exactly in
+        // int64, V = ((a0 256 + a1) 256 + a2) 256 + a3; levels 4-6 are below
+        // 2^-32 of the product and are combined in FP32, c = a4 + a5/256 + a6/65536.
+        // Then (Y L^T)_ij = 2^{e_i+f_j} 2^-40 (V + c / 256).
+        long long V[32];
+        float cf[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+          V[j] = 0;
+          cf[j] = 0.f;
+        }
+#pragma unroll
+        for (int d = 0; d < kEmuLevels; d++) {
+          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * TN + cc * 32), r);
+#pragma unroll
+          for (int j = 0; j < 32; j++) {
+            const float fv = __uint_as_float(r[j]);
+            if (d < 4) V[j] = V[j] * 256 + (long long)__float2int_rn(fv);
+            else cf[j] += fv * (d == 4 ? 1.f : (d == 5 ? 0.00390625f : 0.0000152587890625f));
+          }
+        }
         double acc[32];
 #pragma unroll
-        for (int j = 0; j < 32; j++) acc[j] = 0.0;
-        for (int d = 0; d < cfg.levels; d++) {
-          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * TN + cc * 32), r);
-          const double wd = ldexp(1.0, -8 * (d + 2));
-#pragma unroll
-          for (int j = 0; j < 32; j++) acc[j] += wd * (double)__uint_as_float(r[j]);
-        }
+        for (int j = 0; j < 32; j++) acc[j] = 0x1p-40 * ((double)V[j] + 0.00390625 * (double)cf[j]);
         if (rho < m) {
+          // all loads of the 32 columns first, then the stores: 32 loads in flight
+          T cur[32];
 #pragma unroll
           for (int j = 0; j < 32; j++) {
             const int cj = J * TN + cc * 32 + j;  // trailing column index
             const int col = base + cj;
-            if (cj < m && row >= col) {
-              T* p = S + (int64_t)row + (int64_t)col * n;
-              *p = (T)((double)*p - sa * scaleB[cj] * acc[j]);
-            }
+            cur[j] = (cj < m && row >= col) ? S[(int64_t)row + (int64_t)col * n] : T(0);
+          }
+#pragma unroll
+          for (int j = 0; j < 32; j++) {
+            const int cj = J * TN + cc * 32 + j;
+            const int col = base + cj;
+            if (cj < m && row >= col)
+              S[(int64_t)row + (int64_t)col * n] = (T)((double)cur[j] - sa * scaleB[cj] * acc[j]);
           }
         }
       } else {
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), r);
         if (rho < m) {
+          T cur[32];
 #pragma unroll
           for (int j = 0; j < 32; j++) {
             const int cj = J * TN + cc * 32 + j;
             const int col = base + cj;
-            if (cj < m && row >= col) {
-              T* p = S + (int64_t)row + (int64_t)col * n;
-              *p = *p - (T)__uint_as_float(r[j]);
-            }
+            cur[j] = (cj < m && row >= col) ? S[(int64_t)row + (int64_t)col * n] : T(0);
+          }
+#pragma unroll
+          for (int j = 0; j < 32; j++) {
+            const int cj = J * TN + cc * 32 + j;
+            const int col = base + cj;
+            if (cj < m && row >= col) S[(int64_t)row + (int64_t)col * n] = cur[j] - (T)__uint_as_float(r[j]);
           }
         }
       }
@@ -351,46 +376,56 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S, int n, 
 
 // ---- FP32 panel kernels for the TF32 / BF16 modes (same steps as the FP64 ones in dense.cu) ----
 
-// LDL^T of the 64 x 64 diagonal block with rows in registers: thread r holds
-// row r.  Step c publishes the unscaled column c (u_r = a_r[c], u_c = d) in a
-// double-buffered shared array, one barrier per step; thread r then sets
-// l_r = u_r / d and updates a_r[c2] -= l_r u_c2 for c < c2 <= r (since
-// l_c2 d = u_c2).
+// LDL^T of the 64 x 64 diagonal block with rows in registers.  Thread (r, h)
+// holds columns [32h, 32h + 32) of row r (two threads per row, 128 threads).
+// Step c publishes the unscaled column c (u_r = a_r[c], u_c = d) in a
+// double-buffered shared array, one barrier per step; each thread then forms
+// l_r = u_r / d and updates its columns c2 with c < c2 <= r: a_r[c2] -= l_r u_c2
+// (since l_c2 d = u_c2).
 template <class T>
-__global__ void __launch_bounds__(64) k_dense_diag_t(T* __restrict__ S, int n, int k0,
-                                                     unsigned long long* __restrict__ counters) {
+__global__ void __launch_bounds__(2 * TK) k_dense_diag_t(T* __restrict__ S, int n, int k0,
+                                                         unsigned long long* __restrict__ counters) {
+  constexpr int H = TK / 2;
   __shared__ T colbuf[2][TK];
-  const int r = threadIdx.x;
+  const int r = threadIdx.x & (TK - 1), h = threadIdx.x / TK;
   const int kb = min(TK, n - k0);
-  T a[TK];
+  T a[H];
 #pragma unroll
-  for (int j = 0; j < TK; j++) a[j] = (r < kb && j <= r) ? S[(int64_t)(k0 + r) + (int64_t)(k0 + j) * n] : T(0);
+  for (int j = 0; j < H; j++) {
+    const int col = h * H + j;
+    a[j] = (r < kb && col <= r) ? S[(int64_t)(k0 + r) + (int64_t)(k0 + col) * n] : T(0);
+  }
   T mydiag = T(0);
 #pragma unroll
   for (int c = 0; c < TK; c++) {
     if (c < kb) {
       T* u = colbuf[c & 1];
-      if (r >= c && r < kb) u[r] = a[c];
+      const bool mine = (c / H) == h;  // this thread holds column c of its row
+      if (mine && r >= c && r < kb) u[r] = a[c % H];
       __syncthreads();
       const T d = u[c];
-      if (r == c) mydiag = d;
+      if (r == c && mine) mydiag = d;
       if (r > c && r < kb) {
-        const T l = a[c] / d;
-        a[c] = l;
+        const T l = u[r] / d;
+        if (mine) a[c % H] = l;
 #pragma unroll
-        for (int c2 = c + 1; c2 < TK; c2++)
-          if (c2 <= r) a[c2] -= l * u[c2];
+        for (int j = 0; j < H; j++) {
+          const int c2 = h * H + j;
+          if (c2 > c && c2 <= r) a[j] -= l * u[c2];
+        }
       }
     }
   }
   if (r < kb) {
 #pragma unroll
-    for (int j = 0; j < TK; j++)
-      if (j <= r) S[(int64_t)(k0 + r) + (int64_t)(k0 + j) * n] = a[j];
+    for (int j = 0; j < H; j++) {
+      const int col = h * H + j;
+      if (col <= r) S[(int64_t)(k0 + r) + (int64_t)(k0 + col) * n] = a[j];
+    }
   }
   const int pos = __syncthreads_count(r < kb && mydiag > T(0));
   const int neg = __syncthreads_count(r < kb && mydiag < T(0));
-  if (r == 0) {
+  if (threadIdx.x == 0) {
     atomicAdd(&counters[kPos], (unsigned long long)pos);
     atomicAdd(&counters[kNeg], (unsigned long long)neg);
     if (kb - pos - neg) atomicAdd(&counters[kZero], (unsigned long long)(kb - pos - neg));
@@ -447,7 +482,7 @@ cudaError_t factor_tc(Handle& h, T* S, T* Y, unsigned long long* counters, cudaS
   if (e != cudaSuccess) return e;
   for (int k0 = 0; k0 < n; k0 += TK) {
     const int kb = std::min(TK, n - k0);
-    k_dense_diag_t<T><<<1, TK, 0, st>>>(S, n, k0, counters);
+    k_dense_diag_t<T><<<1, 2 * TK, 0, st>>>(S, n, k0, counters);
     h.launches++;
     const int m = n - k0 - kb;
     if (m <= 0) continue;

@@ -66,6 +66,7 @@ struct DevSym {
   int32_t* t_e = nullptr;
   int32_t* bt_ptr = nullptr;
   int32_t* E = nullptr;            // the k rows of A carrying B's nonzeros
+  int32_t* g_rows = nullptr;       // W rows in contraction order: primal chunks, then multiplier chunks
 };
 
 // Counters written by the kernels (device, int64).
@@ -100,7 +101,9 @@ struct Handle {
   uint8_t* tc_imgB = nullptr;
   double* tc_scaleA = nullptr;  // row scales of the emulated FP64 update
   double* tc_scaleB = nullptr;
-  int s_factor = 0;           // current factor of S: 0 FP64-accurate in S, 1 FP32 in S32
+  int s_factor = 0;
+  bool g_reduced = false;     // S assembled from a TF32/BF16 contraction
+  int g_nchunks = 0, g_nchunks_pos = 0;  // 64-row chunks of g_rows (positive-pivot chunks first)           // current factor of S: 0 FP64-accurate in S, 1 FP32 in S32
   double* knorm = nullptr;    // ||K||_inf
   unsigned long long* counters = nullptr;  // kNumCounters
   // solve work vectors
@@ -141,6 +144,9 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st);
 cudaError_t launch_w_solve(Handle& h, cudaStream_t st);
 cudaError_t launch_contract_g(Handle& h, cudaStream_t st);
 cudaError_t launch_assemble_s(Handle& h, cudaStream_t st);
+// ---- (schur_tc.cu) ----
+bool contract_g_tc_supported(const Handle& h);
+cudaError_t launch_contract_g_tc(Handle& h, int bf16, cudaStream_t st);
 // ---- (dense.cu) ----
 cudaError_t launch_dense_ldlt(Handle& h, unsigned long long* counters, cudaStream_t st);
 cudaError_t launch_dense_solve(Handle& h, const double* t, double* x, cudaStream_t st);

@@ -42,6 +42,20 @@ def test_precision_modes_2383_bus_short_horizon(prec):
           f"fallback={info['fell_back_fp64']}")
 
 
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_reduced_contraction_falls_back_to_fp64_schur(prec):
+    """TF32/BF16 contraction on the tensor cores: refinement either converges or
+    the fallback rebuilds S from an FP64 contraction; eta <= 1e-10 either way."""
+    p = make_problem(replace(CONFIGS["grid2383_n96"], n_per=6))
+    x, info = gpu_solve(p, prec, reduced_contraction=1)
+    exact_s = bool(info["fell_back_fp64"])
+    eta, err = check_against_oracle(p, x, info, inertia=exact_s)
+    print(f"{prec}+tc-contraction: eta={eta:.2e} steps={info['refine_steps']} fallback={info['fell_back_fp64']}")
+    g = make_problem(CONFIGS["grid30_n24"])
+    xg, ig = gpu_solve(g, prec, reduced_contraction=1)
+    check_against_oracle(g, xg, ig, np.linalg.cond(dense_K(g)), inertia=bool(ig["fell_back_fp64"]))
+
+
 def test_emulated_factor_matches_fp64_factor_solution():
     """The emulated FP64 update reproduces the FP64 path to near FP64 accuracy."""
     p = make_problem(replace(CONFIGS["grid2383_n96"], n_per=8))
