@@ -170,6 +170,121 @@ def run_reference(args):
     return 0
 
 
+def _mix_problems(count, prec):
+    import numpy as np
+    import torch
+
+    from gen import make_problem, mix_spec
+    from paper_1907_05420_gb300 import binding as B
+
+    probs = [make_problem(mix_spec(k)) for k in range(count)]
+    dev = torch.device("cuda:0")
+    hs = [B.kkt_analyze(p, B.kkt_default_options(prec)) for p in probs]
+    up = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(dev)  # noqa: E731
+    vals = [(up(p.a_vals), up(p.b_vals), up(p.c_vals), up(p.rhs)) for p in probs]
+    xs = [torch.empty_like(v[3]) for v in vals]
+    return probs, hs, vals, xs
+
+
+def run_batch(args):
+    """The 64-instance size mix: one batched call against 64 sequential solves."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1907_05420_gb300 import binding as B
+
+    count = 64
+    out = {"metric": "KKT solves/s, 64-instance size mix, batched vs sequential", "unit": "solves/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "data": "synthetic", "config": {"workload": "mix64: 64 seeded grids, 118-3000 buses, "
+                                                       "N in {12,24,48,96}, 5-10% storage buses"}}
+    for prec in args.batch_precs.split(","):
+        probs, hs, vals, xs = _mix_problems(count, prec)
+        A = [v[0] for v in vals]
+        Bv = [v[1] for v in vals]
+        Cv = [v[2] for v in vals]
+        R = [v[3] for v in vals]
+        for _ in range(args.warmup):
+            B.kkt_batch_factor_solve(hs, A, Bv, Cv, R, xs, streams=args.batch_streams)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            B.kkt_batch_factor_solve(hs, A, Bv, Cv, R, xs, streams=args.batch_streams)
+        torch.cuda.synchronize()
+        t_batch = (time.perf_counter() - t0) / args.steps
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for h, (a, b, c, r), x in zip(hs, vals, xs):
+                B.kkt_factor(h, a, b, c)
+                B.kkt_solve(h, r, x, allow_not_converged=True)
+        torch.cuda.synchronize()
+        t_seq = (time.perf_counter() - t0) / args.steps
+        etas = [oracle.backward_error(p, x.cpu().numpy()) for p, x in zip(probs, xs)]
+        out[prec] = {"batched": count / t_batch, "sequential": count / t_seq,
+                     "ms_per_batch": 1e3 * t_batch, "ms_sequential": 1e3 * t_seq,
+                     "eta_max": max(etas), "streams": args.batch_streams}
+        for h in hs:
+            B.kkt_destroy(h)
+    out["value"] = out[args.batch_precs.split(",")[0]]["batched"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson request stream over the size mix; p50/p99 latency and solves/s per rate."""
+    import numpy as np
+    import torch
+
+    from paper_1907_05420_gb300 import binding as B
+
+    out = {"metric": "KKT solves/s and p50/p99 latency under a Poisson request stream", "unit": "solves/s",
+           "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+           "config": {"workload": f"serve: {args.serve_pool} resident patterns from the size mix; "
+                                  "Poisson arrivals; every request carries fresh values",
+                      "slots": args.serve_slots, "seconds_per_rate": args.serve_seconds}}
+    for prec in args.batch_precs.split(","):
+        probs, hs, vals, xs = _mix_problems(args.serve_pool, prec)
+        srv = B.KKTServer(slots=args.serve_slots,
+                          device_budget_bytes=int(0.8 * torch.cuda.mem_get_info()[0]))
+        rng = np.random.default_rng(4242)
+        res = {}
+        for rate in [float(r) for r in args.rates.split(",")]:
+            lats, ids = [], []
+            t_end = time.perf_counter() + 1.0 + args.serve_seconds
+            t_next = time.perf_counter()
+            t_measure = t_next + 1.0
+            measured = []
+            while time.perf_counter() < t_end:
+                now = time.perf_counter()
+                if now < t_next:
+                    time.sleep(min(t_next - now, 0.001))
+                    continue
+                k = int(rng.integers(0, len(probs)))
+                a, b, c, r = vals[k]
+                x = torch.empty_like(r)
+                ids.append((srv.submit(hs[k], a, b, c, r, x), now >= t_measure, now))
+                t_next += rng.exponential(1.0 / rate)
+            t_last = time.perf_counter()
+            for rid, in_window, _ in ids:
+                st, lat = srv.wait(rid)
+                if in_window:
+                    lats.append(lat)
+                    measured.append(rid)
+            t_done = time.perf_counter()
+            n = len(lats)
+            res[str(int(rate))] = {"requests": n, "solves_per_s": n / max(1e-9, (t_done - t_last) + args.serve_seconds),
+                                   "p50_ms": float(np.percentile(lats, 50)) if n else None,
+                                   "p99_ms": float(np.percentile(lats, 99)) if n else None}
+        srv.close()
+        for h in hs:
+            B.kkt_destroy(h)
+        out[prec] = res
+    out["value"] = max(v["solves_per_s"] for v in out[args.batch_precs.split(",")[0]].values())
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,10 +299,20 @@ def main():
     ap.add_argument("--leg-steps", type=int, default=4)
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-precs", default="tf32,fp64")
+    ap.add_argument("--batch-streams", type=int, default=8)
+    ap.add_argument("--serve-pool", type=int, default=32)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--rates", default="50,100,200,500,1000,2000")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "mix64":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import numpy as np
     import torch

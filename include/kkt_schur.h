@@ -197,6 +197,43 @@ const char* kkt_last_error(void);
  *   returned as KKT_ERR_CUDA. */
 kkt_status kkt_solve_noalloc(kkt_handle* h, const double* rhs, double* x, void* stream);
 
+/* ---- batching and serving (no counterpart in the paper; the workload's many
+ * independent systems of different grids and horizons) ---- */
+
+/* Factor and solve n independent systems, handles[i] with the values and
+ * right-hand side of system i (all host or all device arrays, as in kkt_factor
+ * and kkt_solve).  Systems are spread round-robin over `streams` CUDA streams
+ * (<= 0: 8), one host worker per stream, so the kernels of different systems
+ * overlap on the GPU.  statuses (may be NULL) receives each system's status;
+ * the return value is the first failure other than KKT_ERR_NOT_CONVERGED, else
+ * KKT_ERR_NOT_CONVERGED if any system stopped above refine_tol, else KKT_OK.
+ * Every handle must appear at most once. */
+kkt_status kkt_batch_factor_solve(kkt_handle* const* handles, int32_t n, const double* const* a_vals,
+                                  const double* const* b_vals, const double* const* c_vals,
+                                  const double* const* rhs, double* const* x, int32_t on_device,
+                                  int32_t streams, kkt_status* statuses);
+
+/* A request loop with continuous batching.  Up to `slots` requests run at once,
+ * each on its own stream; a queued request is admitted as soon as a slot is
+ * free, its handle is idle, and the device bytes of the handles in flight stay
+ * within device_budget_bytes (0 = no budget; a request is always admitted when
+ * nothing is in flight).  Handles stay resident: repeated requests on one
+ * handle reuse its analysis. */
+typedef struct kkt_server kkt_server;
+kkt_status kkt_server_create(int32_t slots, int64_t device_budget_bytes, kkt_server** out);
+/* Queue one KKT solve (factor + refined solve) on handle h; the arrays must
+ * stay valid until the request completes.  *request_id identifies it. */
+kkt_status kkt_server_submit(kkt_server* s, kkt_handle* h, const double* a_vals, const double* b_vals,
+                             const double* c_vals, const double* rhs, double* x, int32_t on_device,
+                             int64_t* request_id);
+/* Result of a request: with wait != 0 blocks until it completes; with wait == 0
+ * returns KKT_ERR_STATE while it is pending.  *status is the request's status,
+ * *latency_ms the time from submit to completion of its solve. */
+kkt_status kkt_server_poll(kkt_server* s, int64_t request_id, int32_t wait, kkt_status* status,
+                           double* latency_ms);
+/* Drains the queue, joins the workers and frees the streams. */
+kkt_status kkt_server_destroy(kkt_server* s);
+
 /* Measured FP64 FMA throughput of the current device in GFLOP/s (8
  * independent FMA chains per thread, best of 5 launches).  The FP64-bound
  * phases report their roofline fraction against it. */

@@ -63,7 +63,8 @@ class kkt_info(C.Structure):
 # every symbol the header declares
 EXPORTS = ["kkt_default_options", "kkt_analyze", "kkt_factor", "kkt_solve", "kkt_get_info",
            "kkt_destroy", "kkt_status_string", "kkt_last_error", "kkt_measure_fp64_peak",
-           "kkt_solve_noalloc"]
+           "kkt_solve_noalloc", "kkt_batch_factor_solve", "kkt_server_create", "kkt_server_submit",
+           "kkt_server_poll", "kkt_server_destroy"]
 
 _lib = None
 
@@ -103,6 +104,20 @@ def load(build_if_missing: bool = True):
     L.kkt_measure_fp64_peak.restype = C.c_int
     L.kkt_solve_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     L.kkt_solve_noalloc.restype = C.c_int
+    pp = C.POINTER(C.c_void_p)
+    L.kkt_batch_factor_solve.argtypes = [pp, C.c_int32, pp, pp, pp, pp, pp, C.c_int32, C.c_int32,
+                                         C.POINTER(C.c_int)]
+    L.kkt_batch_factor_solve.restype = C.c_int
+    L.kkt_server_create.argtypes = [C.c_int32, C.c_int64, C.POINTER(C.c_void_p)]
+    L.kkt_server_create.restype = C.c_int
+    L.kkt_server_submit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]
+    L.kkt_server_submit.restype = C.c_int
+    L.kkt_server_poll.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_int),
+                                  C.POINTER(C.c_double)]
+    L.kkt_server_poll.restype = C.c_int
+    L.kkt_server_destroy.argtypes = [C.c_void_p]
+    L.kkt_server_destroy.restype = C.c_int
     _lib = L
     return L
 
@@ -211,6 +226,61 @@ def kkt_solve_noalloc(h, rhs, x, stream=None):
     if not (dr and dx):
         raise ValueError("kkt_solve_noalloc takes device arrays only")
     return _check(load().kkt_solve_noalloc(h, pr, px, _stream_ptr(stream)))
+
+
+def kkt_batch_factor_solve(handles, a_vals, b_vals, c_vals, rhs, x, streams=8):
+    """Factor and solve independent systems concurrently; returns the per-system statuses."""
+    n = len(handles)
+    if not all(len(v) == n for v in (a_vals, b_vals, c_vals, rhs, x)):
+        raise ValueError("one set of arrays per handle")
+    ptrs = [[_ptr(a) for a in v] for v in (a_vals, b_vals, c_vals, rhs, x)]
+    dev = {d for v in ptrs for _, d in v}
+    if len(dev) > 1:
+        raise ValueError("all arrays must be host arrays or all device arrays")
+    on_device = dev.pop() if dev else 0
+    arr = lambda v: (C.c_void_p * n)(*[p for p, _ in v])  # noqa: E731
+    hs = (C.c_void_p * n)(*handles)
+    st = (C.c_int * n)()
+    rc = load().kkt_batch_factor_solve(hs, n, arr(ptrs[0]), arr(ptrs[1]), arr(ptrs[2]), arr(ptrs[3]),
+                                       arr(ptrs[4]), on_device, int(streams), st)
+    _check(rc, allow=(6,))
+    return list(st)
+
+
+class KKTServer:
+    """Continuous-batching request loop (kkt_server_*)."""
+
+    def __init__(self, slots=4, device_budget_bytes=0):
+        self.s = C.c_void_p()
+        _check(load().kkt_server_create(int(slots), int(device_budget_bytes), C.byref(self.s)))
+        self._keep = {}
+
+    def submit(self, h, a_vals, b_vals, c_vals, rhs, x):
+        ptrs = [_ptr(v) for v in (a_vals, b_vals, c_vals, rhs, x)]
+        dev = {d for _, d in ptrs}
+        if len(dev) > 1:
+            raise ValueError("all arrays must be host arrays or all device arrays")
+        rid = C.c_int64()
+        _check(load().kkt_server_submit(self.s, h, *[p for p, _ in ptrs], dev.pop(), C.byref(rid)))
+        self._keep[rid.value] = (a_vals, b_vals, c_vals, rhs, x)
+        return rid.value
+
+    def wait(self, rid):
+        st, lat = C.c_int(), C.c_double()
+        _check(load().kkt_server_poll(self.s, int(rid), 1, C.byref(st), C.byref(lat)))
+        self._keep.pop(rid, None)
+        return st.value, lat.value
+
+    def close(self):
+        if self.s:
+            _check(load().kkt_server_destroy(self.s))
+            self.s = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kkt_measure_fp64_peak() -> float:

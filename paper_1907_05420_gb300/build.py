@@ -14,7 +14,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libkkt_schur.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["api.cu", "factor.cu", "schur.cu", "dense.cu", "solve.cu", "probe.cu", "noalloc.cu", "dense_tc.cu", "schur_tc.cu"]
-CPP = ["symbolic.cpp"]
+CPP = ["symbolic.cpp", "serve.cpp"]
 HEADERS = ["handle.h", "symbolic.h"]
 
 
@@ -49,7 +49,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if src.endswith(".cu"):
             cmd = [nvcc] + ARCH + common + ["-c", src, "-o", obj]
         else:
-            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-c", src, "-o", obj]
+            cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-I", cuda_inc, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd))
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -56,7 +56,7 @@ void free_all(Handle* h) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->host_red) cudaFreeHost(h->host_red);
-  cudaEvent_t evs[] = {h->ev_f0, h->ev_f1, h->ev_fa, h->ev_fb, h->ev_s0, h->ev_s1};
+  cudaEvent_t evs[] = {h->ev_f0, h->ev_f1, h->ev_fa, h->ev_fb, h->ev_s0, h->ev_s1, h->ev_done};
   for (cudaEvent_t ev : evs)
     if (ev) cudaEventDestroy(ev);
 }
@@ -327,7 +327,7 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
     e = cudaMemset(h->trsv_flags, 0, sizeof(int) * (size_t)std::max(1, 2 * ((h->nC + kDenseNB - 1) / kDenseNB)));
   if (e == cudaSuccess) e = cudaMemset(h->dev_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->host_red, sizeof(double) * 8);
-  for (cudaEvent_t* ev : {&h->ev_f0, &h->ev_f1, &h->ev_fa, &h->ev_fb, &h->ev_s0, &h->ev_s1})
+  for (cudaEvent_t* ev : {&h->ev_f0, &h->ev_f1, &h->ev_fa, &h->ev_fb, &h->ev_s0, &h->ev_s1, &h->ev_done})
     if (e == cudaSuccess) e = cudaEventCreate(ev);
   if (e != cudaSuccess) {
     kkt_status st = cuda_status(e, "kkt_analyze");
@@ -357,6 +357,7 @@ kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals
   }
   cudaStream_t st = (cudaStream_t)stream;
   h->stream = st;
+  (void)cudaGetLastError();  // drop a stale non-sticky error left by an unrelated call
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const int64_t nc_vals = h->c_kind == 0 ? (int64_t)h->nC : (int64_t)h->nC * h->nC;
   KKT_CUDA(cudaEventRecord(h->ev_f0, st));
@@ -386,6 +387,7 @@ kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals
   h->info.fell_back_fp64 = 0;
   KKT_CUDA(launch_knorm(*h, st));
   KKT_CUDA(cudaEventRecord(h->ev_f1, st));
+  KKT_CUDA(cudaEventRecord(h->ev_done, st));
   h->factored = true;
   h->timed_factor = true;
   return KKT_OK;
@@ -404,6 +406,7 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
   }
   cudaStream_t st = (cudaStream_t)stream;
   h->stream = st;
+  (void)cudaGetLastError();
   auto t0 = std::chrono::steady_clock::now();
   const int64_t nK = (int64_t)h->N * h->nA + h->nC;
   kkt_status result = KKT_OK;
@@ -465,6 +468,7 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
     if (!(eta <= h->opt.refine_tol)) result = KKT_ERR_NOT_CONVERGED;
   }
   KKT_CUDA(cudaEventRecord(h->ev_s1, st));
+  KKT_CUDA(cudaEventRecord(h->ev_done, st));
   KKT_CUDA(cudaStreamSynchronize(st));
   {
     float ms = 0.f;
@@ -482,7 +486,7 @@ kkt_status kkt_get_info(kkt_handle* hh, kkt_info* info) {
     set_error("kkt_get_info: null argument");
     return KKT_ERR_INVALID;
   }
-  KKT_CUDA(cudaStreamSynchronize(h->stream));
+  KKT_CUDA(cudaEventSynchronize(h->ev_done));
   if (h->factored) {
     unsigned long long c[2 * kNumCounters];
     KKT_CUDA(cudaMemcpy(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost));
@@ -508,7 +512,7 @@ kkt_status kkt_get_info(kkt_handle* hh, kkt_info* info) {
 kkt_status kkt_destroy(kkt_handle* hh) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return KKT_OK;
-  cudaStreamSynchronize(h->stream);
+  cudaEventSynchronize(h->ev_done);
   free_all(h);
   delete h;
   return KKT_OK;

@@ -131,6 +131,7 @@ struct Handle {
   cudaEvent_t ev_f0 = nullptr, ev_f1 = nullptr;
   cudaEvent_t ev_fa = nullptr, ev_fb = nullptr;  // phase boundaries inside kkt_factor
   cudaEvent_t ev_s0 = nullptr, ev_s1 = nullptr;  // around kkt_solve
+  cudaEvent_t ev_done = nullptr;  // end of the handle's last factor/solve (outlives the caller's stream)
   int64_t launches = 0;                          // kernels launched since analyze
   kkt_info info{};
 };

@@ -99,6 +99,8 @@ extern "C" kkt_status kkt_solve_noalloc(kkt_handle* hh, const double* rhs, doubl
   ws.dot = ws.xg + round_up(h->nC);
   cudaStream_t st = (cudaStream_t)stream;
   h->stream = st;
+  (void)cudaGetLastError();
   KKT_CUDA(launch_apply_inverse_ws(*h, rhs, x, ws, st));
+  KKT_CUDA(cudaEventRecord(h->ev_done, st));
   return KKT_OK;
 }

@@ -1,0 +1,237 @@
+// Batching and serving around the per-system calls.
+//
+// kkt_batch_factor_solve: independent arrowhead systems (each with its own
+// analysed handle) are spread over a pool of CUDA streams, one host worker per
+// stream; the refinement of each solve synchronizes only its own stream, so the
+// kernels of different systems overlap on the GPU.
+//
+// kkt_server_*: a request loop with continuous batching.  Requests (a handle
+// plus the values and right-hand side of one KKT solve) are queued on submit;
+// up to `slots` requests are in flight, each on its own worker stream, and a new
+// request is admitted as soon as a slot is free and its handle is not busy.
+// Handles stay resident across requests (repeated solves of a pattern reuse
+// its analysis and buffers).  Admission also checks that the handles in flight
+// fit the device-memory budget given at creation.  Each request's latency runs
+// from its submit to the completion of its solve.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "handle.h"
+
+using namespace kkt;
+
+extern "C" kkt_status kkt_batch_factor_solve(kkt_handle* const* handles, int32_t n,
+                                             const double* const* a_vals, const double* const* b_vals,
+                                             const double* const* c_vals, const double* const* rhs,
+                                             double* const* x, int32_t on_device, int32_t streams,
+                                             kkt_status* statuses) {
+  if (n < 0 || (n > 0 && (!handles || !a_vals || !b_vals || !c_vals || !rhs || !x))) {
+    set_error("kkt_batch_factor_solve: invalid argument");
+    return KKT_ERR_INVALID;
+  }
+  if (n == 0) return KKT_OK;
+  const int ns = std::max(1, std::min<int>(streams > 0 ? streams : 8, n));
+  std::vector<cudaStream_t> pool(ns, nullptr);
+  for (int s = 0; s < ns; s++) {
+    cudaError_t e = cudaStreamCreateWithFlags(&pool[s], cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      for (int q = 0; q < s; q++) cudaStreamDestroy(pool[q]);
+      set_error(std::string("kkt_batch_factor_solve: cudaStreamCreate: ") + cudaGetErrorString(e));
+      return KKT_ERR_CUDA;
+    }
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<kkt_status> st(n, KKT_OK);
+  std::vector<std::thread> workers;
+  for (int s = 0; s < ns; s++) {
+    workers.emplace_back([&, s]() {
+      cudaSetDevice(dev);
+      for (int i = s; i < n; i += ns) {  // round robin: system i on stream i mod ns
+        kkt_status r = kkt_factor(handles[i], a_vals[i], b_vals[i], c_vals[i], on_device, pool[s]);
+        if (r == KKT_OK) r = kkt_solve(handles[i], rhs[i], x[i], 1, on_device, pool[s]);
+        st[i] = r;
+      }
+    });
+  }
+  for (auto& w : workers) w.join();
+  for (int s = 0; s < ns; s++) cudaStreamDestroy(pool[s]);
+  kkt_status worst = KKT_OK;
+  for (int i = 0; i < n; i++) {
+    if (statuses) statuses[i] = st[i];
+    if (st[i] != KKT_OK && (worst == KKT_OK || worst == KKT_ERR_NOT_CONVERGED)) worst = st[i];
+  }
+  return worst;
+}
+
+namespace {
+
+struct Request {
+  int64_t id;
+  kkt_handle* h;
+  const double *a, *b, *c, *rhs;
+  double* x;
+  int32_t on_device;
+  std::chrono::steady_clock::time_point t_submit;
+};
+
+struct Done {
+  kkt_status status;
+  double latency_ms;
+};
+
+}  // namespace
+
+struct kkt_server {
+  int slots = 1;
+  int64_t budget = 0;  // device bytes of handles that may be in flight at once (0 = no limit)
+  int dev = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request> queue;
+  std::unordered_map<int64_t, Done> done;
+  std::unordered_set<kkt_handle*> busy;
+  int64_t inflight_bytes = 0;
+  int64_t next_id = 1;
+  bool stop = false;
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> streams;
+};
+
+namespace {
+
+void worker_loop(kkt_server* S, int slot) {
+  cudaSetDevice(S->dev);
+  for (;;) {
+    Request req;
+    int64_t bytes = 0;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      for (;;) {
+        if (S->stop && S->queue.empty()) return;
+        // the oldest queued request whose handle is idle and which fits the budget
+        auto it = S->queue.begin();
+        for (; it != S->queue.end(); ++it) {
+          if (S->busy.count(it->h)) continue;
+          const int64_t hb = reinterpret_cast<Handle*>(it->h)->device_bytes;
+          if (S->budget > 0 && S->inflight_bytes > 0 && S->inflight_bytes + hb > S->budget) continue;
+          break;
+        }
+        if (it != S->queue.end()) {
+          req = *it;
+          S->queue.erase(it);
+          bytes = reinterpret_cast<Handle*>(req.h)->device_bytes;
+          S->busy.insert(req.h);
+          S->inflight_bytes += bytes;
+          break;
+        }
+        S->cv_work.wait(lk);
+      }
+    }
+    cudaStream_t st = S->streams[slot];
+    kkt_status r = kkt_factor(req.h, req.a, req.b, req.c, req.on_device, st);
+    if (r == KKT_OK) r = kkt_solve(req.h, req.rhs, req.x, 1, req.on_device, st);
+    if (r == KKT_OK || r == KKT_ERR_NOT_CONVERGED) cudaStreamSynchronize(st);
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - req.t_submit).count();
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->busy.erase(req.h);
+      S->inflight_bytes -= bytes;
+      S->done[req.id] = Done{r, ms};
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+  }
+}
+
+}  // namespace
+
+extern "C" kkt_status kkt_server_create(int32_t slots, int64_t device_budget_bytes, kkt_server** out) {
+  if (!out || slots < 1) {
+    set_error("kkt_server_create: invalid argument");
+    return KKT_ERR_INVALID;
+  }
+  kkt_server* S = new (std::nothrow) kkt_server();
+  if (!S) return KKT_ERR_OOM;
+  S->slots = slots;
+  S->budget = device_budget_bytes;
+  cudaGetDevice(&S->dev);
+  S->streams.resize(slots, nullptr);
+  for (int s = 0; s < slots; s++) {
+    cudaError_t e = cudaStreamCreateWithFlags(&S->streams[s], cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      for (int q = 0; q < s; q++) cudaStreamDestroy(S->streams[q]);
+      delete S;
+      set_error(std::string("kkt_server_create: cudaStreamCreate: ") + cudaGetErrorString(e));
+      return KKT_ERR_CUDA;
+    }
+  }
+  for (int s = 0; s < slots; s++) S->workers.emplace_back(worker_loop, S, s);
+  *out = S;
+  return KKT_OK;
+}
+
+extern "C" kkt_status kkt_server_submit(kkt_server* S, kkt_handle* h, const double* a_vals,
+                                        const double* b_vals, const double* c_vals, const double* rhs,
+                                        double* x, int32_t on_device, int64_t* request_id) {
+  if (!S || !h || !a_vals || !rhs || !x || !request_id) {
+    set_error("kkt_server_submit: invalid argument");
+    return KKT_ERR_INVALID;
+  }
+  Request r{0, h, a_vals, b_vals, c_vals, rhs, x, on_device, std::chrono::steady_clock::now()};
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) {
+      set_error("kkt_server_submit: server is shutting down");
+      return KKT_ERR_STATE;
+    }
+    r.id = S->next_id++;
+    S->queue.push_back(r);
+  }
+  *request_id = r.id;
+  S->cv_work.notify_one();
+  return KKT_OK;
+}
+
+extern "C" kkt_status kkt_server_poll(kkt_server* S, int64_t request_id, int32_t wait, kkt_status* status,
+                                      double* latency_ms) {
+  if (!S) {
+    set_error("kkt_server_poll: null server");
+    return KKT_ERR_INVALID;
+  }
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    auto it = S->done.find(request_id);
+    if (it != S->done.end()) {
+      if (status) *status = it->second.status;
+      if (latency_ms) *latency_ms = it->second.latency_ms;
+      S->done.erase(it);
+      return KKT_OK;
+    }
+    if (!wait) return KKT_ERR_STATE;  // not finished yet
+    S->cv_done.wait(lk);
+  }
+}
+
+extern "C" kkt_status kkt_server_destroy(kkt_server* S) {
+  if (!S) return KKT_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  for (auto& w : S->workers) w.join();
+  for (cudaStream_t st : S->streams) cudaStreamDestroy(st);
+  delete S;
+  return KKT_OK;
+}
