@@ -294,7 +294,7 @@ def main():
     ap.add_argument("--prec", default="tf32", choices=["fp64", "tf32", "bf16", "f64emu"],
                     help="arithmetic of the dense factor of S on the timed path (default: the "
                          "mixed path, TF32 tensor cores with FP64 refinement)")
-    ap.add_argument("--legs", default="fp64,f64emu,bf16,tf32+tcg",
+    ap.add_argument("--legs", default="fp64,f64emu,bf16,tf32+tcg,fp64+band,tf32+band",
                     help="other precision modes measured beside the timed path ('' for none)")
     ap.add_argument("--leg-steps", type=int, default=4)
     ap.add_argument("--workload", default=WORKLOAD)
@@ -347,9 +347,11 @@ def main():
         """Factor + refined solve of the workload, `steps` timed repetitions.
 
         mode: a precision name; a '+tcg' suffix also runs the Schur contraction on
-        the tensor cores in that precision."""
+        the tensor cores in that precision, '+band' limits the factor of S to its
+        row envelope (the structured Schur factor)."""
         prec, _, extra = mode.partition("+")
-        h = B.kkt_analyze(prob, B.kkt_default_options(prec, reduced_contraction=int(extra == "tcg")))
+        h = B.kkt_analyze(prob, B.kkt_default_options(prec, reduced_contraction=int(extra == "tcg"),
+                                                     structured_s=int(extra == "band")))
         info0 = B.kkt_get_info(h)
 
         def step_device():

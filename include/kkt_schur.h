@@ -101,7 +101,12 @@ typedef struct {
                                   G_i = W_i^T D_i^{-1} W_i on the tensor cores in that precision
                                   (0, the default: FP64 contraction).  On a stall the fallback then
                                   recomputes G in FP64 and reassembles S before refactoring it. */
-  int32_t reserved[3];
+  int32_t structured_s; /* limit the dense factor of S and its solves to S's row envelope
+                           (LDL^T without pivoting creates no fill outside it): the same
+                           arithmetic on every entry that can be nonzero, the exact zeros outside
+                           skipped.  For the adjacent-period coupling S is block-tridiagonal and
+                           the cost drops from n_C^3/3 to ~ n_C (2 n_stor)^2.  Default 0. */
+  int32_t reserved[2];
 } kkt_options;
 
 typedef struct {

@@ -48,7 +48,7 @@ void free_all(Handle* h) {
                   h->d.full_rowptr, h->d.full_col, h->d.full_src, h->d.b_row, h->d.b_col,
                   h->d.b_blockptr, h->d.e_t, h->d.e_block, h->d.wpos, h->d.sn_wrow, h->d.w_dpos,
                   h->d.w_col, h->d.reach_lvl_sn, h->d.s_key, h->d.s_ptr, h->d.s_e1, h->d.s_e2,
-                  h->d.t_ptr, h->d.t_e, h->d.bt_ptr, h->d.E, h->d.g_rows, h->Lx, h->a_vals, h->b_vals,
+                  h->d.t_ptr, h->d.t_e, h->d.bt_ptr, h->d.E, h->d.g_rows, h->d.trsv_jlo, h->d.trsv_jhi, h->Lx, h->a_vals, h->b_vals,
                   h->c_vals, h->anorm, h->W, h->G, h->S, h->Ypanel, h->knorm, h->counters, h->r,
                   h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red,
                   h->trsv_flags, h->trsv_ticket, h->dev_err, h->S32, h->Y32, h->tc_imgA,
@@ -207,6 +207,38 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
     g_rows = pos_rows;
     g_rows.insert(g_rows.end(), neg_rows.begin(), neg_rows.end());
   }
+  // row envelope of S for the structured mode: first[r] = first structurally
+  // nonzero column of row r (C is diagonal or dense; B's entries give the rest)
+  std::vector<int32_t> trsv_jlo, trsv_jhi;
+  if (h->opt.structured_s && h->nC > 0) {
+    const int nC = h->nC, NBK = kDenseNB, nbk = (nC + NBK - 1) / NBK;
+    std::vector<int32_t> first(nC);
+    for (int r = 0; r < nC; r++) first[r] = h->c_kind == 0 ? r : 0;
+    for (int64_t key : C.s_key) {
+      const int c1 = (int)(key / nC), c2 = (int)(key % nC);
+      first[c1] = std::min(first[c1], c2);
+    }
+    // panel p (columns [64p, 64p+64)) touches rows r with first[r] < 64p + 64
+    h->panel_rend.assign(nbk, 0);
+    std::vector<int32_t> last_row_of_col(nC, -1);
+    int run = -1;
+    std::vector<int32_t> maxrow(nC, -1);  // max r with first[r] <= c
+    for (int r = 0; r < nC; r++) maxrow[first[r]] = std::max(maxrow[first[r]], r);
+    for (int c = 0; c < nC; c++) {
+      run = std::max(run, maxrow[c]);
+      last_row_of_col[c] = run;
+    }
+    trsv_jlo.assign(nbk, 0);
+    trsv_jhi.assign(nbk, 0);
+    for (int p = 0; p < nbk; p++) {
+      const int clast = std::min(nC, (p + 1) * NBK) - 1;
+      h->panel_rend[p] = std::max(std::min(nC, (p + 1) * NBK), last_row_of_col[clast] + 1);
+      trsv_jhi[p] = (h->panel_rend[p] + NBK - 1) / NBK;
+      int fmin = nC;
+      for (int r = p * NBK; r < std::min(nC, (p + 1) * NBK); r++) fmin = std::min(fmin, first[r]);
+      trsv_jlo[p] = fmin / NBK;
+    }
+  }
   // symmetric full CSR of A with source positions
   std::vector<int32_t> full_rowptr(n + 1, 0), full_col, full_src;
   for (int r = 0; r < n; r++)
@@ -278,6 +310,10 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   UP(bt_ptr, C.bt_ptr);
   UP(E, C.E);
   UP(g_rows, g_rows);
+  if (!trsv_jlo.empty()) {
+    UP(trsv_jlo, trsv_jlo);
+    UP(trsv_jhi, trsv_jhi);
+  }
 #undef UP
   const int64_t nK = (int64_t)h->N * n + h->nC;
   const int64_t k = C.k;

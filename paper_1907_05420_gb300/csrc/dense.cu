@@ -3,9 +3,10 @@
 //
 // S is n x n, column-major, lower triangle.  Blocked right-looking, block
 // width kDenseNB = 64, per block column k0:
-//   k_dense_diag:   unblocked LDL^T of the 64 x 64 diagonal block in shared memory;
-//   k_dense_panel:  L21 = A21 L11^{-T} D1^{-1}; Y = L21 D1 kept for the update;
-//   k_dense_update: A22 -= Y L21^T on the lower-triangle 64 x 64 tiles.
+//   diagonal block: LDL^T of the 64 x 64 block with rows in registers, and
+//   panel: L21 = A21 L11^{-T} D1^{-1}, Y = L21 D1 kept for the update
+//     (k_dense_diag_t / k_dense_panel_t, shared with the tensor-core modes);
+//   k_dense_update: A22 -= Y L21^T on the lower-triangle 64 x 64 tiles (FP64).
 // No pivoting: S is positive definite when the blocks are quasidefinite and C
 // is positive definite; a zero pivot is counted and reported.
 #include "handle.h"
@@ -16,78 +17,9 @@ namespace {
 
 constexpr int NB = kDenseNB;
 
-__global__ void __launch_bounds__(256) k_dense_diag(double* __restrict__ S, int n, int k0,
-                                                    unsigned long long* __restrict__ counters) {
-  __shared__ double A[NB][NB + 1];
-  const int kb = min(NB, n - k0);
-  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
-    const int j = q / kb, i = q - j * kb;
-    A[i][j] = S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n];
-  }
-  __syncthreads();
-  for (int c = 0; c < kb; c++) {
-    const double d = A[c][c];
-    for (int r = c + 1 + threadIdx.x; r < kb; r += blockDim.x) A[r][c] = A[r][c] / d;
-    __syncthreads();
-    const int rem = kb - c - 1;
-    for (int q = threadIdx.x; q < rem * rem; q += blockDim.x) {
-      const int c2 = c + 1 + q / rem, r = c + 1 + q % rem;
-      if (r >= c2) A[r][c2] -= A[r][c] * d * A[c2][c];
-    }
-    __syncthreads();
-  }
-  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
-    const int j = q / kb, i = q - j * kb;
-    if (i >= j) S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n] = A[i][j];
-  }
-  if (threadIdx.x == 0) {
-    unsigned long long pos = 0, neg = 0, zero = 0;
-    for (int c = 0; c < kb; c++) {
-      const double d = A[c][c];
-      if (d > 0) pos++;
-      else if (d < 0) neg++;
-      else zero++;
-    }
-    atomicAdd(&counters[kPos], pos);
-    atomicAdd(&counters[kNeg], neg);
-    if (zero) atomicAdd(&counters[kZero], zero);
-  }
-}
-
-// rows k0+kb .. n-1: solve y L11^T = a per row, L21 = y / D, Y = y
-__global__ void __launch_bounds__(64) k_dense_panel(double* __restrict__ S, double* __restrict__ Y,
-                                                    int n, int k0) {
-  __shared__ double L11[NB][NB + 1];
-  const int kb = min(NB, n - k0);
-  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
-    const int j = q / kb, i = q - j * kb;
-    L11[i][j] = S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n];
-  }
-  __syncthreads();
-  const int row = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= n) return;
-  double y[NB];
-#pragma unroll
-  for (int c = 0; c < NB; c++) y[c] = c < kb ? S[row + (int64_t)(k0 + c) * n] : 0.0;
-#pragma unroll
-  for (int c = 0; c < NB; c++) {
-    if (c < kb) {
-#pragma unroll
-      for (int c2 = 0; c2 < c; c2++) y[c] -= y[c2] * L11[c][c2];
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < NB; c++) {
-    if (c < kb) {
-      Y[row + (int64_t)c * n] = y[c];
-      S[row + (int64_t)(k0 + c) * n] = y[c] / L11[c][c];
-    }
-  }
-}
-
 // trailing update on lower tiles: A[i][j] -= sum_c Y[i][c] L[j][c]
 __global__ void __launch_bounds__(256) k_dense_update(double* __restrict__ S, const double* __restrict__ Y,
-                                                      int n, int k0) {
+                                                      int n, int k0, int rend) {
   const int kb = min(NB, n - k0);
   const int base = k0 + kb;
   int tile = blockIdx.x, ti = 0;
@@ -107,8 +39,8 @@ __global__ void __launch_bounds__(256) k_dense_update(double* __restrict__ S, co
     __syncthreads();
     for (int q = threadIdx.x; q < kc * 64; q += 256) {
       const int c = q / 64, r = q % 64;
-      Ys[c][r] = (i0 + r < n) ? Y[(i0 + r) + (int64_t)(cb + c) * n] : 0.0;
-      Ls[c][r] = (j0 + r < n) ? S[(j0 + r) + (int64_t)(k0 + cb + c) * n] : 0.0;
+      Ys[c][r] = (i0 + r < rend) ? Y[(i0 + r) + (int64_t)(cb + c) * n] : 0.0;
+      Ls[c][r] = (j0 + r < rend) ? S[(j0 + r) + (int64_t)(k0 + cb + c) * n] : 0.0;
     }
     __syncthreads();
     for (int c = 0; c < kc; c++) {
@@ -129,7 +61,7 @@ __global__ void __launch_bounds__(256) k_dense_update(double* __restrict__ S, co
 #pragma unroll
     for (int v = 0; v < 4; v++) {
       const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
-      if (i < n && j < n && i >= j) S[i + (int64_t)j * n] -= acc[u][v];
+      if (i < rend && j < rend && i >= j) S[i + (int64_t)j * n] -= acc[u][v];
     }
 }
 
@@ -215,7 +147,8 @@ __device__ __forceinline__ bool wait_flag(const int* flag, int epoch, int* err) 
 // L y = b in place (unit lower L, column-major n x n, leading dimension n)
 template <class T>
 __global__ void __launch_bounds__(256) k_trsv_lower(const T* __restrict__ L, int n, double* x,
-                                                    int* flags, unsigned* ticket, int epoch, int* err) {
+                                                    int* flags, unsigned* ticket, int epoch, int* err,
+                                                    const int* __restrict__ jlo) {
   __shared__ int s_blk, s_ok;
   __shared__ double yj[64];
   __shared__ double part[4][64];
@@ -229,7 +162,7 @@ __global__ void __launch_bounds__(256) k_trsv_lower(const T* __restrict__ L, int
   const int t = s_blk, r0 = t * 64, rows = min(64, n - r0);
   const int r = tid & 63, pid = tid >> 6;
   double acc = 0.0;
-  for (int j = 0; j < t; j++) {
+  for (int j = jlo ? jlo[t] : 0; j < t; j++) {  // blocks left of the row envelope are zero
     if (tid == 0 && !wait_flag(flags + j, epoch, err)) s_ok = 0;
     __syncthreads();
     if (!s_ok) break;
@@ -274,7 +207,8 @@ __global__ void __launch_bounds__(256) k_trsv_lower(const T* __restrict__ L, int
 // L^T x = y in place (blocks from the bottom up)
 template <class T>
 __global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ L, int n, double* x,
-                                                    int* flags, unsigned* ticket, int epoch, int* err) {
+                                                    int* flags, unsigned* ticket, int epoch, int* err,
+                                                    const int* __restrict__ jhi) {
   __shared__ int s_blk, s_ok;
   __shared__ double xj[64];
   __shared__ double accs[64];
@@ -288,7 +222,7 @@ __global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ L, int
   if (tid < 64) accs[tid] = 0.0;
   __syncthreads();
   const int b = s_blk, r0 = b * 64, rows = min(64, n - r0);
-  for (int j = nb - 1; j > b; j--) {
+  for (int j = (jhi ? jhi[b] : nb) - 1; j > b; j--) {  // blocks below the envelope are zero
     if (tid == 0 && !wait_flag(flags + j, epoch, err)) s_ok = 0;
     __syncthreads();
     if (!s_ok) break;
@@ -338,21 +272,15 @@ cudaError_t launch_dense_ldlt(Handle& h, unsigned long long* counters, cudaStrea
   const int n = h.nC;
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = std::min(NB, n - k0);
-    {
-    k_dense_diag<<<1, 256, 0, st>>>(h.S, n, k0, counters);
-    h.launches++;
-  }
-    const int rest = n - k0 - kb;
+    const int rend = h.panel_rend.empty() ? n : h.panel_rend[k0 / NB];
+    // diagonal block (rows in registers) and panel (warp per row), FP64
+    cudaError_t e = launch_dense_diag_panel_f64(h, k0, rend, counters, st);
+    if (e != cudaSuccess) return e;
+    const int rest = rend - k0 - kb;
     if (rest > 0) {
-      {
-    k_dense_panel<<<(rest + 63) / 64, 64, 0, st>>>(h.S, h.Ypanel, n, k0);
-    h.launches++;
-  }
       const int T = (rest + 63) / 64;
-      {
-    k_dense_update<<<T * (T + 1) / 2, 256, 0, st>>>(h.S, h.Ypanel, n, k0);
-    h.launches++;
-  }
+      k_dense_update<<<T * (T + 1) / 2, 256, 0, st>>>(h.S, h.Ypanel, n, k0, rend);
+      h.launches++;
     }
   }
   return cudaGetLastError();
@@ -367,10 +295,11 @@ cudaError_t launch_dense_solve(Handle& h, const double* t, double* x, cudaStream
   if (e != cudaSuccess) return e;
   // flags hold the epoch of the last solve that finished each block; two per solve
   const int ep_f = ++h.trsv_epoch, ep_b = ++h.trsv_epoch;
-  k_trsv_lower<double><<<nb, 256, 0, st>>>(h.S, n, x, h.trsv_flags, h.trsv_ticket, ep_f, h.dev_err);
+  k_trsv_lower<double><<<nb, 256, 0, st>>>(h.S, n, x, h.trsv_flags, h.trsv_ticket, ep_f, h.dev_err,
+                                           h.d.trsv_jlo);
   k_dense_diag_scale<<<(n + 255) / 256, 256, 0, st>>>(h.S, x, n);
   k_trsv_upper<double><<<nb, 256, 0, st>>>(h.S, n, x, h.trsv_flags + nb, h.trsv_ticket + 1, ep_b,
-                                           h.dev_err);
+                                           h.dev_err, h.d.trsv_jhi);
   h.launches += 3;
   return cudaGetLastError();
 }
@@ -418,10 +347,11 @@ cudaError_t launch_dense_solve_f32(Handle& h, const double* t, double* x, cudaSt
   if (e == cudaSuccess) e = cudaMemsetAsync(h.trsv_ticket, 0, sizeof(unsigned) * 2, st);
   if (e != cudaSuccess) return e;
   const int ep_f = ++h.trsv_epoch, ep_b = ++h.trsv_epoch;
-  k_trsv_lower<float><<<nb, 256, 0, st>>>(h.S32, n, x, h.trsv_flags, h.trsv_ticket, ep_f, h.dev_err);
+  k_trsv_lower<float><<<nb, 256, 0, st>>>(h.S32, n, x, h.trsv_flags, h.trsv_ticket, ep_f, h.dev_err,
+                                          h.d.trsv_jlo);
   k_dense_diag_scale_f32<<<(n + 255) / 256, 256, 0, st>>>(h.S32, x, n);
   k_trsv_upper<float><<<nb, 256, 0, st>>>(h.S32, n, x, h.trsv_flags + nb, h.trsv_ticket + 1, ep_b,
-                                          h.dev_err);
+                                          h.dev_err, h.d.trsv_jhi);
   h.launches += 3;
   return cudaGetLastError();
 }

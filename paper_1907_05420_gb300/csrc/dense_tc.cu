@@ -434,7 +434,8 @@ __global__ void __launch_bounds__(2 * TK) k_dense_diag_t(T* __restrict__ S, int 
 
 // rows below the block: solve y L11^T = a (one warp per row, L11 in shared memory)
 template <class T>
-__global__ void __launch_bounds__(256) k_dense_panel_t(T* __restrict__ S, T* __restrict__ Y, int n, int k0) {
+__global__ void __launch_bounds__(256) k_dense_panel_t(T* __restrict__ S, T* __restrict__ Y, int n, int k0,
+                                                       int rend) {
   __shared__ T L11[TK][TK + 1];
   const int kb = min(TK, n - k0);
   for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(256) k_dense_panel_t(T* __restrict__ S, T* __r
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int row = k0 + kb + blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);  // one warp per row
-  if (row >= n) return;
+  if (row >= rend) return;
   // lane holds y[lane] and y[lane+32]
   T y0 = lane < kb ? S[row + (int64_t)(k0 + lane) * n] : T(0);
   T y1 = lane + 32 < kb ? S[row + (int64_t)(k0 + lane + 32) * n] : T(0);
@@ -484,9 +485,11 @@ cudaError_t factor_tc(Handle& h, T* S, T* Y, unsigned long long* counters, cudaS
     const int kb = std::min(TK, n - k0);
     k_dense_diag_t<T><<<1, 2 * TK, 0, st>>>(S, n, k0, counters);
     h.launches++;
-    const int m = n - k0 - kb;
+    // rows below the envelope of the panel's columns stay zero (no pivoting)
+    const int rend = h.panel_rend.empty() ? n : h.panel_rend[k0 / TK];
+    const int m = rend - k0 - kb;
     if (m <= 0) continue;
-    k_dense_panel_t<T><<<(m + 7) / 8, 256, 0, st>>>(S, Y, n, k0);
+    k_dense_panel_t<T><<<(m + 7) / 8, 256, 0, st>>>(S, Y, n, k0, rend);
     h.launches++;
     if (kb < TK) continue;  // a ragged last panel leaves no trailing matrix
     const int TI = (m + TM - 1) / TM, TJ = (m + TN - 1) / TN;
@@ -531,6 +534,22 @@ cudaError_t launch_dense_ldlt_tc(Handle& h, int mode, unsigned long long* counte
   h.launches++;
   if (mode == KKT_TF32) return factor_tc<0, float>(h, h.S32, h.Y32, counters, st);
   return factor_tc<1, float>(h, h.S32, h.Y32, counters, st);
+}
+
+// Diagonal block and panel of one 64-wide step of the FP64 factor (shared by
+// the FP64 path, whose trailing update runs on the CUDA cores).
+cudaError_t launch_dense_diag_panel_f64(Handle& h, int k0, int rend, unsigned long long* counters,
+                                        cudaStream_t st) {
+  const int n = h.nC;
+  const int kb = std::min(TK, n - k0);
+  k_dense_diag_t<double><<<1, 2 * TK, 0, st>>>(h.S, n, k0, counters);
+  h.launches++;
+  const int m = rend - k0 - kb;
+  if (m > 0) {
+    k_dense_panel_t<double><<<(m + 7) / 8, 256, 0, st>>>(h.S, h.Ypanel, n, k0, rend);
+    h.launches++;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace kkt

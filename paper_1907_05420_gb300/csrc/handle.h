@@ -67,6 +67,8 @@ struct DevSym {
   int32_t* bt_ptr = nullptr;
   int32_t* E = nullptr;            // the k rows of A carrying B's nonzeros
   int32_t* g_rows = nullptr;       // W rows in contraction order: primal chunks, then multiplier chunks
+  int32_t* trsv_jlo = nullptr;     // envelope of S (structured mode): first column block of each row block
+  int32_t* trsv_jhi = nullptr;     // one past the last row block of each column block
 };
 
 // Counters written by the kernels (device, int64).
@@ -84,6 +86,7 @@ struct Handle {
   std::vector<int32_t> fwork_lvl_ptr;  // factor work items per level
   std::vector<int32_t> lvl_ptr;        // supernodes per level (host copy)
   std::vector<int32_t> reach_lvl_ptr;
+  std::vector<int32_t> panel_rend;     // structured mode: per 64-wide panel, one past its last nonzero row
 
   // numeric buffers
   double* Lx = nullptr;       // N * panel_total
@@ -155,6 +158,8 @@ cudaError_t launch_dense_solve_f32(Handle& h, const double* t, double* x, cudaSt
 // ---- (dense_tc.cu) ----
 cudaError_t launch_dense_ldlt_tc(Handle& h, int mode, unsigned long long* counters, cudaStream_t st);
 int64_t tc_image_bytes_a(int n, int mode);
+cudaError_t launch_dense_diag_panel_f64(Handle& h, int k0, int rend, unsigned long long* counters,
+                                        cudaStream_t st);
 int64_t tc_image_bytes(int n, int mode);
 // ---- (solve.cu) ----
 cudaError_t launch_apply_inverse(Handle& h, const double* rhs, double* out, cudaStream_t st);

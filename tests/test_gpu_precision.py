@@ -63,3 +63,14 @@ def test_emulated_factor_matches_fp64_factor_solution():
     xe, info = gpu_solve(p, "f64emu")
     assert oracle.backward_error(p, xe) <= 1e-14
     assert np.max(np.abs(xe - x64)) / np.max(np.abs(x64)) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32", "f64emu"])
+def test_structured_s_equals_dense(prec):
+    """The envelope-limited factor only skips exact zeros: bitwise the dense result."""
+    for p in (make_problem(CONFIGS["grid30_n24"]), make_problem(replace(CONFIGS["grid2383_n96"], n_per=6))):
+        xd, infd = gpu_solve(p, prec)
+        xs, infs = gpu_solve(p, prec, structured_s=1)
+        assert np.array_equal(xd, xs)
+        assert [infd["n_pos"], infd["n_neg"]] == [infs["n_pos"], infs["n_neg"]]
+        assert oracle.backward_error(p, xs) <= 1e-10
