@@ -12,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libkkt_schur.so")
+SYM_LIB = os.path.join(OUT_DIR, "libkkt_symbolic.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["api.cu", "factor.cu", "schur.cu", "dense.cu", "solve.cu", "probe.cu", "noalloc.cu", "dense_tc.cu", "schur_tc.cu"]
 CPP = ["symbolic.cpp", "serve.cpp"]
@@ -34,6 +35,21 @@ def _stale() -> bool:
     deps = _sources() + [os.path.join(CSRC, h) for h in HEADERS]
     deps.append(os.path.join(os.path.dirname(HERE), "include", "kkt_schur.h"))
     return any(os.path.getmtime(p) > t for p in deps)
+
+
+def build_symbolic(force: bool = False) -> str:
+    """Host-only inspection library of the symbolic analysis (g++, no CUDA)."""
+    srcs = [os.path.join(CSRC, f) for f in ("symbolic.cpp", "symbolic_capi.cpp")]
+    deps = srcs + [os.path.join(CSRC, "symbolic.h"),
+                   os.path.join(os.path.dirname(HERE), "include", "kkt_symbolic.h")]
+    if not force and os.path.exists(SYM_LIB) and all(os.path.getmtime(p) <= os.path.getmtime(SYM_LIB)
+                                                    for p in deps):
+        return SYM_LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    tmp = SYM_LIB + f".tmp{os.getpid()}"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp] + srcs, check=True)
+    os.replace(tmp, SYM_LIB)
+    return SYM_LIB
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -69,3 +85,4 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))
+    print(build_symbolic(force="--force" in sys.argv))

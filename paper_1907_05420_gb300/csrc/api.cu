@@ -207,38 +207,9 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
     g_rows = pos_rows;
     g_rows.insert(g_rows.end(), neg_rows.begin(), neg_rows.end());
   }
-  // row envelope of S for the structured mode: first[r] = first structurally
-  // nonzero column of row r (C is diagonal or dense; B's entries give the rest)
+  // row envelope of S for the structured mode
   std::vector<int32_t> trsv_jlo, trsv_jhi;
-  if (h->opt.structured_s && h->nC > 0) {
-    const int nC = h->nC, NBK = kDenseNB, nbk = (nC + NBK - 1) / NBK;
-    std::vector<int32_t> first(nC);
-    for (int r = 0; r < nC; r++) first[r] = h->c_kind == 0 ? r : 0;
-    for (int64_t key : C.s_key) {
-      const int c1 = (int)(key / nC), c2 = (int)(key % nC);
-      first[c1] = std::min(first[c1], c2);
-    }
-    // panel p (columns [64p, 64p+64)) touches rows r with first[r] < 64p + 64
-    h->panel_rend.assign(nbk, 0);
-    std::vector<int32_t> last_row_of_col(nC, -1);
-    int run = -1;
-    std::vector<int32_t> maxrow(nC, -1);  // max r with first[r] <= c
-    for (int r = 0; r < nC; r++) maxrow[first[r]] = std::max(maxrow[first[r]], r);
-    for (int c = 0; c < nC; c++) {
-      run = std::max(run, maxrow[c]);
-      last_row_of_col[c] = run;
-    }
-    trsv_jlo.assign(nbk, 0);
-    trsv_jhi.assign(nbk, 0);
-    for (int p = 0; p < nbk; p++) {
-      const int clast = std::min(nC, (p + 1) * NBK) - 1;
-      h->panel_rend[p] = std::max(std::min(nC, (p + 1) * NBK), last_row_of_col[clast] + 1);
-      trsv_jhi[p] = (h->panel_rend[p] + NBK - 1) / NBK;
-      int fmin = nC;
-      for (int r = p * NBK; r < std::min(nC, (p + 1) * NBK); r++) fmin = std::min(fmin, first[r]);
-      trsv_jlo[p] = fmin / NBK;
-    }
-  }
+  if (h->opt.structured_s && h->nC > 0) s_envelope(C, h->c_kind, kDenseNB, h->panel_rend, trsv_jlo, trsv_jhi);
   // symmetric full CSR of A with source positions
   std::vector<int32_t> full_rowptr(n + 1, 0), full_col, full_src;
   for (int r = 0; r < n; r++)

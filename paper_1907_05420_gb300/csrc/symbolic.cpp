@@ -558,4 +558,35 @@ std::string analyze_coupling(const Symbolic& S, int32_t N, int32_t nC, const int
   return std::string();
 }
 
+void s_envelope(const Coupling& C, int32_t c_kind, int32_t block, std::vector<int32_t>& panel_rend,
+                std::vector<int32_t>& jlo, std::vector<int32_t>& jhi) {
+  const int32_t nC = C.nC, nbk = (nC + block - 1) / block;
+  panel_rend.assign(nbk, 0);
+  jlo.assign(nbk, 0);
+  jhi.assign(nbk, 0);
+  if (nC == 0) return;
+  std::vector<int32_t> first(nC);
+  for (int32_t r = 0; r < nC; r++) first[r] = c_kind == 0 ? r : 0;
+  for (int64_t key : C.s_key) {
+    const int32_t c1 = (int32_t)(key / nC), c2 = (int32_t)(key % nC);
+    first[c1] = std::min(first[c1], c2);
+  }
+  // last_row[c] = max{r : first[r] <= c}
+  std::vector<int32_t> maxrow(nC, -1), last_row(nC, -1);
+  for (int32_t r = 0; r < nC; r++) maxrow[first[r]] = std::max(maxrow[first[r]], r);
+  int32_t run = -1;
+  for (int32_t c = 0; c < nC; c++) {
+    run = std::max(run, maxrow[c]);
+    last_row[c] = run;
+  }
+  for (int32_t p = 0; p < nbk; p++) {
+    const int32_t cend = std::min(nC, (p + 1) * block);
+    panel_rend[p] = std::max(cend, last_row[cend - 1] + 1);
+    jhi[p] = (panel_rend[p] + block - 1) / block;
+    int32_t fmin = nC;
+    for (int32_t r = p * block; r < cend; r++) fmin = std::min(fmin, first[r]);
+    jlo[p] = fmin / block;
+  }
+}
+
 }  // namespace kkt

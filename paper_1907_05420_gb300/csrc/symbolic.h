@@ -88,6 +88,13 @@ struct Coupling {
 std::string analyze_coupling(const Symbolic& S, int32_t N, int32_t nC, const int32_t* b_blockptr,
                              const int32_t* b_row, const int32_t* b_col, Coupling& out);
 
+// Row envelope of S = C - sum_i M_i^T G_i M_i (the structured factor): for each
+// 64-wide panel p, one past the last row that can be nonzero in its columns
+// (panel_rend), and per 64-row block the first / one-past-last block of the
+// triangular solves (jlo, jhi).  LDL^T without pivoting keeps the envelope.
+void s_envelope(const Coupling& C, int32_t c_kind, int32_t block, std::vector<int32_t>& panel_rend,
+                std::vector<int32_t>& jlo, std::vector<int32_t>& jhi);
+
 // Returns an empty string on success, else a description of the problem.
 std::string analyze_pattern(int32_t n, int32_t nP, const int32_t* rowptr, const int32_t* col,
                             const double* vals_hint, int32_t hint_blocks, Symbolic& out);

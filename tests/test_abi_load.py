@@ -1,4 +1,4 @@
-"""The C-ABI library loads and exports every symbol include/kkt_schur.h declares.
+"""The C-ABI libraries load and export every symbol include/*.h declares.
 
 No compute call is made (no GPU needed).
 """
@@ -12,8 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "kkt_schur.h")
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(header=HEADER):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(kkt_[a-z0-9_]+)\s*\(", text)))
 
@@ -34,6 +34,16 @@ def test_library_exports_every_declared_symbol():
     for n in declared_functions():
         assert hasattr(lib, n), n
     assert sorted(binding.EXPORTS) == declared_functions()
+
+
+def test_symbolic_library_exports_its_header():
+    from paper_1907_05420_gb300 import build as lib_build
+
+    lib = ctypes.CDLL(lib_build.build_symbolic())
+    names = declared_functions(os.path.join(ROOT, "include", "kkt_symbolic.h"))
+    assert names == ["kkt_symbolic_create", "kkt_symbolic_destroy", "kkt_symbolic_error", "kkt_symbolic_get"]
+    for n in names:
+        assert hasattr(lib, n), n
 
 
 def test_status_strings_without_gpu():

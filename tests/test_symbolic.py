@@ -1,0 +1,345 @@
+"""Host logic of the analysis phase (Sec. 4.1, 4.2): ordering, supernodes,
+update maps, coupling reach and the envelope of S, checked on the CPU.
+
+The analysis that kkt_analyze runs before it uploads anything is exposed by
+the host-only inspection library (include/kkt_symbolic.h).  Its outputs are
+pinned here against brute force (graph elimination on small blocks) and
+against the oracle's independent symbolic and numeric factorizations.
+"""
+import ctypes as C
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from gen import CONFIGS, GridSpec, make_problem
+
+
+@functools.lru_cache(maxsize=None)
+def _lib():
+    from paper_1907_05420_gb300 import build as lib_build
+
+    L = C.CDLL(lib_build.build_symbolic())
+    i32p, f64p = C.POINTER(C.c_int32), C.POINTER(C.c_double)
+    L.kkt_symbolic_create.argtypes = [C.c_int32, C.c_int32, i32p, i32p, f64p, C.c_int32, C.c_int32,
+                                      i32p, i32p, i32p, C.c_int32]
+    L.kkt_symbolic_create.restype = C.c_void_p
+    L.kkt_symbolic_get.argtypes = [C.c_void_p, C.c_char_p, C.POINTER(C.c_int64)]
+    L.kkt_symbolic_get.restype = C.c_int64
+    L.kkt_symbolic_destroy.argtypes = [C.c_void_p]
+    L.kkt_symbolic_destroy.restype = None
+    L.kkt_symbolic_error.argtypes = []
+    L.kkt_symbolic_error.restype = C.c_char_p
+    return L
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def analyze(p, hint=True):
+    """All arrays of the analysis of problem p, as a dict of int64 arrays."""
+    L = _lib()
+    rp = np.ascontiguousarray(p.a_rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(p.a_col, dtype=np.int32)
+    bbp = np.ascontiguousarray(p.b_blockptr, dtype=np.int32)
+    brow = np.ascontiguousarray(p.b_row, dtype=np.int32)
+    bcol = np.ascontiguousarray(p.b_col, dtype=np.int32)
+    hv = np.ascontiguousarray(np.asarray(p.a_vals).reshape(p.N, -1)[0], dtype=np.float64)
+    h = L.kkt_symbolic_create(p.nA, p.nP, _ptr(rp, C.c_int32), _ptr(col, C.c_int32),
+                              _ptr(hv, C.c_double) if hint else None, p.N, p.nC,
+                              _ptr(bbp, C.c_int32), _ptr(brow, C.c_int32), _ptr(bcol, C.c_int32),
+                              int(p.c_kind))
+    assert h, L.kkt_symbolic_error().decode()
+    out = {}
+    try:
+        for name in ("perm partner sn_first sn_rowptr sn_rows sn_valoff sn_parent sn_level a_map "
+                     "upd_ptr upd_src upd_r0 upd_r1 upd_reloff upd_rel E e_t wpos sn_wrow s_key "
+                     "panel_rend jlo jhi stats").split():
+            n = L.kkt_symbolic_get(h, name.encode(), None)
+            assert n >= 0, name
+            a = np.zeros(n, dtype=np.int64)
+            L.kkt_symbolic_get(h, name.encode(), _ptr(a, C.c_int64))
+            out[name] = a
+    finally:
+        L.kkt_symbolic_destroy(h)
+    st = out.pop("stats")
+    out.update(n=int(st[0]), nsuper=int(st[1]), nlevels=int(st[2]), panel_total=int(st[3]),
+               nnzL=int(st[4]), k=int(st[5]), nw=int(st[6]))
+    return out
+
+
+def _storage_spec(seed=5):
+    # a few storage units, so M_i couples neighbouring periods through B
+    return GridSpec(20, 26, 4, 3, 6, 1e-6, 1e6, seed, "st20")
+
+
+PROBLEMS = {
+    "tiny": lambda: make_problem(CONFIGS["tiny"]),
+    "small": lambda: make_problem(CONFIGS["small"]),
+    "grid30_n24": lambda: make_problem(CONFIGS["grid30_n24"]),
+    "storage20": lambda: make_problem(_storage_spec()),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def _case(name):
+    p = PROBLEMS[name]()
+    return p, analyze(p)
+
+
+def _sym_adj(n, rowptr, col):
+    adj = [set() for _ in range(n)]
+    for r in range(n):
+        for q in range(rowptr[r], rowptr[r + 1]):
+            c = int(col[q])
+            if c != r:
+                adj[r].add(c)
+                adj[c].add(r)
+    return adj
+
+
+def _fill_pattern(p, perm):
+    """Strictly-lower pattern of L, per column of the permuted matrix, by
+    eliminating vertices of the graph of A one at a time (brute force)."""
+    n = p.nA
+    iperm = np.empty(n, dtype=np.int64)
+    iperm[perm] = np.arange(n)
+    adj = _sym_adj(n, p.a_rowptr, p.a_col)
+    g = [set(int(iperm[v]) for v in adj[perm[k]]) for k in range(n)]
+    pat = []
+    for k in range(n):
+        later = {j for j in g[k] if j > k}
+        pat.append(later)
+        for a in later:
+            g[a] |= later - {a}
+    return pat
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_perm_is_permutation_with_partners_first(name):
+    p, s = _case(name)
+    perm = s["perm"]
+    assert sorted(perm.tolist()) == list(range(p.nA))
+    iperm = np.empty(p.nA, dtype=np.int64)
+    iperm[perm] = np.arange(p.nA)
+    partner = s["partner"]
+    assert len(partner) == p.nA and np.all(partner[:p.nP] == -1)
+    adj = _sym_adj(p.nA, p.a_rowptr, p.a_col)
+    paired = 0
+    for r in range(p.nP, p.nA):
+        q = int(partner[r])
+        if q < 0:
+            continue
+        paired += 1
+        assert q < p.nP and q in adj[r]           # a primal neighbour of the multiplier
+        assert iperm[q] < iperm[r]                 # the partner is eliminated first
+    assert paired > 0
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_nnz_l_matches_oracle_symbolic(name):
+    p, s = _case(name)
+    perm = s["perm"].astype(np.int32)
+    assert s["nnzL"] == oracle.nnz_l(p.nA, p.a_rowptr, p.a_col, perm)
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "grid30_n24", "storage20"])
+def test_supernode_rows_are_union_of_column_patterns(name):
+    p, s = _case(name)
+    pat = _fill_pattern(p, s["perm"])
+    assert s["nnzL"] == sum(len(x) for x in pat)
+    first, rp, rows = s["sn_first"], s["sn_rowptr"], s["sn_rows"]
+    assert first[0] == 0 and first[-1] == p.nA and np.all(np.diff(first) >= 1)
+    assert np.all(np.diff(first) <= 32)
+    for q in range(s["nsuper"]):
+        cols = set(range(first[q], first[q + 1]))
+        want = set(cols)
+        for j in cols:
+            want |= pat[j]
+        got = rows[rp[q]:rp[q + 1]].tolist()
+        assert got == sorted(want)
+        assert got[:len(cols)] == sorted(cols)
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_supernodal_tree_levels_and_panels(name):
+    p, s = _case(name)
+    first, rp, rows, par, lvl = s["sn_first"], s["sn_rowptr"], s["sn_rows"], s["sn_parent"], s["sn_level"]
+    col_sn = np.repeat(np.arange(s["nsuper"]), np.diff(first))
+    off = s["sn_valoff"]
+    for q in range(s["nsuper"]):
+        w = first[q + 1] - first[q]
+        m = rp[q + 1] - rp[q]
+        assert off[q + 1] - off[q] == m * w
+        # parent = supernode of the first row below the diagonal block
+        if m > w:
+            assert par[q] == col_sn[rows[rp[q] + w]]
+            assert lvl[par[q]] > lvl[q]
+        else:
+            assert par[q] == -1
+    assert off[-1] == s["panel_total"]
+    leaves = set(range(s["nsuper"])) - set(par[par >= 0].tolist())
+    assert all(lvl[q] == 0 for q in leaves)
+    assert s["nlevels"] == lvl.max() + 1
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_a_map_places_each_entry_in_its_panel(name):
+    p, s = _case(name)
+    n = p.nA
+    iperm = np.empty(n, dtype=np.int64)
+    iperm[s["perm"]] = np.arange(n)
+    first, rp, rows, off = s["sn_first"], s["sn_rowptr"], s["sn_rows"], s["sn_valoff"]
+    col_sn = np.repeat(np.arange(s["nsuper"]), np.diff(first))
+    amap = s["a_map"]
+    assert len(amap) == p.nnzA
+    for r in range(n):
+        for q in range(p.a_rowptr[r], p.a_rowptr[r + 1]):
+            a, b = iperm[r], iperm[p.a_col[q]]
+            row, c = max(a, b), min(a, b)
+            sn = col_sn[c]
+            pos = int(np.searchsorted(rows[rp[sn]:rp[sn + 1]], row))
+            assert rows[rp[sn] + pos] == row
+            m = rp[sn + 1] - rp[sn]
+            assert amap[q] == off[sn] + (c - first[sn]) * m + pos
+    assert len(np.unique(amap)) == len(amap)
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_update_lists_are_exact(name):
+    p, s = _case(name)
+    first, rp, rows = s["sn_first"], s["sn_rowptr"], s["sn_rows"]
+    up, src, r0, r1, roff, rel = (s[k] for k in ("upd_ptr", "upd_src", "upd_r0", "upd_r1",
+                                                  "upd_reloff", "upd_rel"))
+    for q in range(s["nsuper"]):
+        lo, hi = first[q], first[q + 1]
+        srows = rows[rp[q]:rp[q + 1]]
+        want = {}
+        for d in range(q):
+            drows = rows[rp[d]:rp[d + 1]]
+            w = first[d + 1] - first[d]
+            inside = [i for i in range(w, len(drows)) if lo <= drows[i] < hi]
+            if inside:
+                want[d] = (inside[0], inside[-1] + 1)
+        got = {}
+        for u in range(up[q], up[q + 1]):
+            d = int(src[u])
+            got[d] = (int(r0[u]), int(r1[u]))
+            drows = rows[rp[d]:rp[d + 1]]
+            for i in range(r0[u], len(drows)):
+                assert srows[rel[roff[u] + i - r0[u]]] == drows[i]
+        assert got == want
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_coupling_rows_and_reach(name):
+    p, s = _case(name)
+    E = s["E"]
+    assert E.tolist() == sorted(set(np.asarray(p.b_row).tolist()))
+    assert s["k"] == len(E)
+    assert np.array_equal(E[s["e_t"]], np.asarray(p.b_row))
+    iperm = np.empty(p.nA, dtype=np.int64)
+    iperm[s["perm"]] = np.arange(p.nA)
+    first, par = s["sn_first"], s["sn_parent"]
+    col_sn = np.repeat(np.arange(s["nsuper"]), np.diff(first))
+    reach = set()
+    for r in E.tolist():
+        q = int(col_sn[iperm[r]])
+        while q >= 0 and q not in reach:
+            reach.add(q)
+            q = int(par[q])
+    assert set(np.nonzero(s["sn_wrow"] >= 0)[0].tolist()) == reach
+    assert s["nw"] == sum(first[q + 1] - first[q] for q in reach)
+    # each unit right-hand side sits on E's own row inside W
+    for t, r in enumerate(E.tolist()):
+        q = int(col_sn[iperm[r]])
+        assert s["wpos"][t] == s["sn_wrow"][q] + iperm[r] - first[q]
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "grid30_n24", "storage20"])
+def test_s_keys_cover_oracle_schur_complement(name):
+    p, s = _case(name)
+    S = oracle.kkt_solve(p, want_S=True)["S"]
+    nC = p.nC
+    keys = set(s["s_key"].tolist())
+    assert np.all(np.diff(s["s_key"]) > 0)
+    for key in keys:
+        c1, c2 = divmod(key, nC)
+        assert c1 >= c2
+    nz = np.argwhere(np.tril(S, -1) != 0)
+    for c1, c2 in nz:
+        assert c1 * nC + c2 in keys
+    # every structural pair is a real term: with generic values none cancels
+    diag_off = {c * nC + c for c in range(nC)}
+    assert len(keys - diag_off) == len(nz)
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "grid30_n24", "storage20"])
+def test_envelope_bounds_the_factor_of_s(name):
+    p, s = _case(name)
+    S = oracle.kkt_solve(p, want_S=True)["S"]
+    nC, NB = p.nC, 64
+    F, _ = oracle.dense_ldlt(S)
+    Lnz = np.tril(F, -1) != 0
+    nbk = (nC + NB - 1) // NB
+    rend, jlo, jhi = s["panel_rend"], s["jlo"], s["jhi"]
+    assert len(rend) == len(jlo) == len(jhi) == nbk
+    for pb in range(nbk):
+        c0, c1 = pb * NB, min(nC, pb * NB + NB)
+        rr = np.nonzero(Lnz[:, c0:c1].any(axis=1))[0]
+        assert rr.size == 0 or rr.max() < rend[pb]
+        assert rend[pb] >= c1 and jhi[pb] == -(-rend[pb] // NB)
+        rows_nz = np.nonzero(Lnz[c0:c1].any(axis=0))[0]
+        assert rows_nz.size == 0 or rows_nz.min() // NB >= jlo[pb]
+        assert jlo[pb] <= pb < jhi[pb]
+
+
+def test_envelope_of_dense_c_is_full():
+    p = make_problem(CONFIGS["tiny"])
+    p.c_kind = 1
+    p.c_vals = np.diag(np.asarray(p.c_vals, dtype=np.float64))
+    s = analyze(p)
+    nbk = (p.nC + 63) // 64
+    assert s["jlo"].tolist() == [0] * nbk
+    assert s["panel_rend"].tolist() == [p.nC] * nbk
+
+
+def test_no_hint_still_orders_every_row():
+    p = make_problem(CONFIGS["small"])
+    s = analyze(p, hint=False)
+    assert sorted(s["perm"].tolist()) == list(range(p.nA))
+    assert s["nnzL"] == oracle.nnz_l(p.nA, p.a_rowptr, p.a_col, s["perm"].astype(np.int32))
+
+
+def test_malformed_pattern_is_rejected():
+    p = make_problem(CONFIGS["tiny"])
+    bad = np.array(p.a_col, dtype=np.int32).copy()
+    bad[0] = p.nA + 5
+    p.a_col = bad
+    L = _lib()
+    rp = np.ascontiguousarray(p.a_rowptr, dtype=np.int32)
+    bbp = np.ascontiguousarray(p.b_blockptr, dtype=np.int32)
+    brow = np.ascontiguousarray(p.b_row, dtype=np.int32)
+    bcol = np.ascontiguousarray(p.b_col, dtype=np.int32)
+    h = L.kkt_symbolic_create(p.nA, p.nP, _ptr(rp, C.c_int32), _ptr(bad, C.c_int32), None, p.N, p.nC,
+                              _ptr(bbp, C.c_int32), _ptr(brow, C.c_int32), _ptr(bcol, C.c_int32), 0)
+    assert not h
+    assert L.kkt_symbolic_error()
+
+
+def test_full_size_block_pattern():
+    # the 2383-bus block at two periods: the block pattern is that of the full workload
+    import dataclasses
+
+    p = make_problem(dataclasses.replace(CONFIGS["grid2383_n96"], n_per=2))
+    s = analyze(p)
+    assert s["nnzL"] == oracle.nnz_l(p.nA, p.a_rowptr, p.a_col, s["perm"].astype(np.int32))
+    first, par, lvl = s["sn_first"], s["sn_parent"], s["sn_level"]
+    assert np.all(np.diff(first) <= 32)
+    kids = par >= 0
+    assert np.all(lvl[par[kids]] > lvl[kids])
+    assert np.all(par[kids] > np.nonzero(kids)[0])
+    assert len(np.unique(s["a_map"])) == p.nnzA
+    assert s["E"].tolist() == sorted(set(np.asarray(p.b_row).tolist()))
