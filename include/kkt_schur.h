@@ -106,7 +106,18 @@ typedef struct {
                            arithmetic on every entry that can be nonzero, the exact zeros outside
                            skipped.  For the adjacent-period coupling S is block-tridiagonal and
                            the cost drops from n_C^3/3 to ~ n_C (2 n_stor)^2.  Default 0. */
-  int32_t reserved[2];
+  int32_t dense_tail;   /* factor the top of the elimination tree (a suffix of the supernodes,
+                           whose rows are all tail columns) as one dense lower triangle per block
+                           with the blocked dense kernels of the factor of S, instead of
+                           supernode by supernode.  Chosen at analysis: the longest suffix whose
+                           dense flops are at most twice its exact sparse flops and whose N
+                           triangles fit 24 GB.  The same static-pivot rule applies; the
+                           factor is scattered back into the supernodal panels.
+                           0: off; 1: trailing updates in FP64 on the CUDA cores; 2: trailing
+                           updates in emulated FP64 on the tensor cores (7 base-256 digit
+                           slices per operand, as in KKT_F64_EMULATED); -1 (default): 2 in the
+                           KKT_TF32, KKT_BF16 and KKT_F64_EMULATED modes, 0 in KKT_FP64. */
+  int32_t reserved;
 } kkt_options;
 
 typedef struct {
@@ -130,10 +141,12 @@ typedef struct {
   double ms_block_factor, ms_schur_assembly, ms_dense_factor;
   double ms_solve_device;       /* device time of the last kkt_solve, refinement included */
   int64_t n_launches;           /* kernels launched by this handle since kkt_analyze */
+  int32_t dense_tail_cols;      /* columns of the dense tail of each block factor (0 = none) */
+  int32_t reserved_info;
 } kkt_info;
 
 /* Default options: FP64, refine_tol 1e-10, max_refine 10, pivot_eps 1e-20,
- * graphs on, FP64 fallback on. */
+ * graphs on, FP64 fallback on, dense tail chosen by the mode (-1). */
 void kkt_default_options(kkt_options* opt);
 
 /* Symbolic analysis of the pattern: ordering of the shared A pattern,

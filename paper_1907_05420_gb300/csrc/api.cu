@@ -48,7 +48,9 @@ void free_all(Handle* h) {
                   h->d.full_rowptr, h->d.full_col, h->d.full_src, h->d.b_row, h->d.b_col,
                   h->d.b_blockptr, h->d.e_t, h->d.e_block, h->d.wpos, h->d.sn_wrow, h->d.w_dpos,
                   h->d.w_col, h->d.reach_lvl_sn, h->d.s_key, h->d.s_ptr, h->d.s_e1, h->d.s_e2,
-                  h->d.t_ptr, h->d.t_e, h->d.bt_ptr, h->d.E, h->d.g_rows, h->d.trsv_jlo, h->d.trsv_jhi, h->Lx, h->a_vals, h->b_vals,
+                  h->d.t_ptr, h->d.t_e, h->d.bt_ptr, h->d.E, h->d.g_rows, h->d.trsv_jlo, h->d.trsv_jhi,
+                  h->d.flvl_sn, h->d.twork, h->d.upd_ntail, h->Tt, h->TY, h->t_imgA, h->t_imgB,
+                  h->t_scaleA, h->t_scaleB, h->Lx, h->a_vals, h->b_vals,
                   h->c_vals, h->anorm, h->W, h->G, h->S, h->Ypanel, h->knorm, h->counters, h->r,
                   h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red,
                   h->trsv_flags, h->trsv_ticket, h->dev_err, h->S32, h->Y32, h->tc_imgA,
@@ -77,6 +79,7 @@ void kkt_default_options(kkt_options* opt) {
   opt->pivot_eps = 1e-20;
   opt->use_graphs = 1;
   opt->fp64_fallback = 1;
+  opt->dense_tail = -1;
 }
 
 const char* kkt_status_string(kkt_status s) {
@@ -137,40 +140,62 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
     delete h;
     return KKT_ERR_INVALID;
   }
+  // dense tail: -1 (default) picks the emulated tail in the reduced-precision
+  // modes and none in the plain FP64 mode
+  h->tail_mode = h->opt.dense_tail < 0 ? (h->opt.prec == KKT_FP64 ? 0 : 2) : h->opt.dense_tail;
+  if (h->tail_mode < 0 || h->tail_mode > 2) {
+    set_error("kkt_analyze: dense_tail must be -1, 0, 1 or 2");
+    delete h;
+    return KKT_ERR_INVALID;
+  }
+  if (h->tail_mode) choose_tail(h->sym, h->N, kTailMaxBytes, kTailMinCols);
+  else choose_tail(h->sym, h->N, 0, 0);  // no tail fits in 0 bytes
   const Symbolic& S = h->sym;
   const Coupling& C = h->cpl;
   const int32_t n = S.n;
+  h->nT = n - S.tail_col;
+  if (h->nT == 0) h->tail_mode = 0;
   h->nnzA = pat->a_rowptr[n];
   h->nnzB = nnzB;
   h->lvl_ptr = S.lvl_ptr;
   h->reach_lvl_ptr = C.reach_lvl_ptr;
 
-  // factor work items: 64-row tiles of every supernode, grouped by level; for
-  // every (tile, update) the rows [ia, ib) of the descendant that land in the tile
-  std::vector<int32_t> fwork, frange;
-  h->fwork_lvl_ptr.assign(S.nlevels + 1, 0);
-  for (int l = 0; l < S.nlevels; l++) {
-    for (int q = S.lvl_ptr[l]; q < S.lvl_ptr[l + 1]; q++) {
-      int s = S.lvl_sn[q];
-      int m = (int)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]);
-      for (int lo = 0; lo < m; lo += 64) {
-        const int hi = std::min(m, lo + 64);
-        fwork.push_back(s);
-        fwork.push_back(lo);
-        fwork.push_back(hi);
-        fwork.push_back((int32_t)(frange.size() / 2));
-        for (int64_t u = S.upd_ptr[s]; u < S.upd_ptr[s + 1]; u++) {
-          const int32_t* rel = S.upd_rel.data() + S.upd_reloff[u];
-          const int64_t nrel = S.upd_reloff[u + 1] - S.upd_reloff[u];
-          const int32_t ia = S.upd_r0[u] + (int32_t)(std::lower_bound(rel, rel + nrel, lo) - rel);
-          const int32_t ib = S.upd_r0[u] + (int32_t)(std::lower_bound(rel, rel + nrel, hi) - rel);
-          frange.push_back(ia);
-          frange.push_back(ib);
-        }
+  // factor work items: 64-row tiles of every supernode outside the dense tail,
+  // grouped by level, then those of the tail supernodes; for every (tile,
+  // update) the rows [ia, ib) of the descendant that land in the tile
+  std::vector<int32_t> fwork, twork, frange, flvl_sn;
+  auto add_items = [&](int s, std::vector<int32_t>& items) {
+    int m = (int)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]);
+    for (int lo = 0; lo < m; lo += 64) {
+      const int hi = std::min(m, lo + 64);
+      items.push_back(s);
+      items.push_back(lo);
+      items.push_back(hi);
+      items.push_back((int32_t)(frange.size() / 2));
+      for (int64_t u = S.upd_ptr[s]; u < S.upd_ptr[s + 1]; u++) {
+        const int32_t* rel = S.upd_rel.data() + S.upd_reloff[u];
+        const int64_t nrel = S.upd_reloff[u + 1] - S.upd_reloff[u];
+        const int32_t ia = S.upd_r0[u] + (int32_t)(std::lower_bound(rel, rel + nrel, lo) - rel);
+        const int32_t ib = S.upd_r0[u] + (int32_t)(std::lower_bound(rel, rel + nrel, hi) - rel);
+        frange.push_back(ia);
+        frange.push_back(ib);
       }
     }
+  };
+  h->fwork_lvl_ptr.assign(S.nlevels + 1, 0);
+  h->flvl_ptr.assign(S.nlevels + 1, 0);
+  for (int l = 0; l < S.nlevels; l++) {
+    for (int q = S.lvl_ptr[l]; q < S.lvl_ptr[l + 1]; q++) {
+      const int s = S.lvl_sn[q];
+      if (s >= S.tail_sn) continue;
+      flvl_sn.push_back(s);
+      add_items(s, fwork);
+    }
     h->fwork_lvl_ptr[l + 1] = (int32_t)(fwork.size() / 4);
+    h->flvl_ptr[l + 1] = (int32_t)flvl_sn.size();
   }
+  for (int s = S.tail_sn; s < S.nsuper; s++) add_items(s, twork);
+  h->tail_items = (int32_t)(twork.size() / 4);
   // per-column pivot position and primal flag
   std::vector<int64_t> col_dpos(n);
   std::vector<int32_t> col_primal(n);
@@ -259,6 +284,9 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   UP(col_dpos, col_dpos);
   UP(fwork, fwork);
   UP(frange, frange);
+  UP(flvl_sn, flvl_sn);
+  UP(twork, twork);
+  UP(upd_ntail, S.upd_ntail);
   UP(full_rowptr, full_rowptr);
   UP(full_col, full_col);
   UP(full_src, full_src);
@@ -299,6 +327,18 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   AL(G, double, k * k * h->N);
   AL(S, double, (int64_t)h->nC * h->nC);
   AL(Ypanel, double, (int64_t)h->nC * kDenseNB);
+  if (h->nT > 0) {
+    AL(Tt, double, (int64_t)h->nT * h->nT * h->N);
+    AL(TY, double, (int64_t)h->nT * kDenseNB * h->N);
+  }
+  if (h->tail_mode == 2) {
+    const int64_t ia = tc_image_bytes_a(h->nT, KKT_F64_EMULATED);
+    const int64_t ib = tc_image_bytes(h->nT, KKT_F64_EMULATED) - ia;
+    AL(t_imgA, uint8_t, ia * h->N);
+    AL(t_imgB, uint8_t, ib * h->N);
+    AL(t_scaleA, double, ((int64_t)h->nT + 256) * h->N);
+    AL(t_scaleB, double, ((int64_t)h->nT + 256) * h->N);
+  }
   AL(knorm, double, 1);
   AL(counters, unsigned long long, 2 * kNumCounters);  // second half: discarded counts
   AL(z, double, (int64_t)h->N * n);
@@ -512,6 +552,7 @@ kkt_status kkt_get_info(kkt_handle* hh, kkt_info* info) {
   }
   h->info.device_bytes = h->device_bytes;
   h->info.n_launches = h->launches;
+  h->info.dense_tail_cols = h->nT;
   *info = h->info;
   return KKT_OK;
 }

@@ -5,65 +5,18 @@
 // width kDenseNB = 64, per block column k0:
 //   diagonal block: LDL^T of the 64 x 64 block with rows in registers, and
 //   panel: L21 = A21 L11^{-T} D1^{-1}, Y = L21 D1 kept for the update
-//     (k_dense_diag_t / k_dense_panel_t, shared with the tensor-core modes);
+//     (k_dense_diag_t / k_dense_panel_t in dense_kernels.cuh, shared with the
+//     tensor-core modes and the dense tail of the block factors);
 //   k_dense_update: A22 -= Y L21^T on the lower-triangle 64 x 64 tiles (FP64).
 // No pivoting: S is positive definite when the blocks are quasidefinite and C
 // is positive definite; a zero pivot is counted and reported.
-#include "handle.h"
+#include "dense_kernels.cuh"
 
 namespace kkt {
 
 namespace {
 
 constexpr int NB = kDenseNB;
-
-// trailing update on lower tiles: A[i][j] -= sum_c Y[i][c] L[j][c]
-__global__ void __launch_bounds__(256) k_dense_update(double* __restrict__ S, const double* __restrict__ Y,
-                                                      int n, int k0, int rend) {
-  const int kb = min(NB, n - k0);
-  const int base = k0 + kb;
-  int tile = blockIdx.x, ti = 0;
-  while (tile > ti) {
-    tile -= ti + 1;
-    ti++;
-  }
-  const int tj = tile;
-  const int i0 = base + ti * 64, j0 = base + tj * 64;
-  constexpr int KC = 32;              // columns staged per pass
-  __shared__ double Ys[KC][64 + 1];  // [c][i]
-  __shared__ double Ls[KC][64 + 1];  // [c][j]
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16, 4x4 outputs each
-  double acc[4][4] = {};
-  for (int cb = 0; cb < kb; cb += KC) {
-    const int kc = min(KC, kb - cb);
-    __syncthreads();
-    for (int q = threadIdx.x; q < kc * 64; q += 256) {
-      const int c = q / 64, r = q % 64;
-      Ys[c][r] = (i0 + r < rend) ? Y[(i0 + r) + (int64_t)(cb + c) * n] : 0.0;
-      Ls[c][r] = (j0 + r < rend) ? S[(j0 + r) + (int64_t)(k0 + cb + c) * n] : 0.0;
-    }
-    __syncthreads();
-    for (int c = 0; c < kc; c++) {
-      double a[4], bb[4];
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        a[u] = Ys[c][ty + 16 * u];
-        bb[u] = Ls[c][tx + 16 * u];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; u++)
-#pragma unroll
-        for (int v = 0; v < 4; v++) acc[u][v] += a[u] * bb[v];
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < 4; u++)
-#pragma unroll
-    for (int v = 0; v < 4; v++) {
-      const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
-      if (i < rend && j < rend && i >= j) S[i + (int64_t)j * n] -= acc[u][v];
-    }
-}
 
 // forward substitution with unit lower L: diagonal block of one block column
 __global__ void k_dense_fwd_diag(const double* __restrict__ S, double* __restrict__ x, int n, int k0) {
@@ -279,7 +232,7 @@ cudaError_t launch_dense_ldlt(Handle& h, unsigned long long* counters, cudaStrea
     const int rest = rend - k0 - kb;
     if (rest > 0) {
       const int T = (rest + 63) / 64;
-      k_dense_update<<<T * (T + 1) / 2, 256, 0, st>>>(h.S, h.Ypanel, n, k0, rend);
+      k_dense_update<<<T * (T + 1) / 2, 256, 0, st>>>(h.S, h.Ypanel, n, k0, rend, 0, 0);
       h.launches++;
     }
   }

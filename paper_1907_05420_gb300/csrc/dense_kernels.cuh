@@ -1,0 +1,315 @@
+// Building blocks of the blocked right-looking dense LDL^T (panel width
+// kDenseNB = 64), shared by the factor of the Schur complement S (one matrix)
+// and by the dense tail of the block factors (one matrix per block, batched
+// over blockIdx with a stride).  Matrices are column-major with leading
+// dimension n; only the lower triangle is read or written.  Per panel k0:
+//   k_dense_diag_t:   LDL^T of the kb x kb diagonal block;
+//   k_dense_panel_t:  L21 = A21 L11^{-T} D1^{-1} and Y = L21 D1 (rows below);
+//   k_dense_update:   A22 -= Y L21^T on the lower 64 x 64 tiles (FP64).
+// A division by a pivot is a multiplication by its reciprocal.
+// Included by the translation units that launch them (internal linkage).
+#pragma once
+#include "handle.h"
+
+namespace kkt {
+
+namespace {
+
+constexpr int kPanelW = kDenseNB;
+
+// Static-pivot rule of the block factors: a pivot with |d| < pivot_eps *
+// max|A_b| is replaced by +-pivot_eps * max|A_b|, with the sign the inertia of
+// a quasidefinite block gives its column (+ primal, - multiplier).  A null
+// anorm turns the rule off (the factor of S).
+struct PivotRule {
+  const double* anorm = nullptr;   // per matrix of the batch
+  double pivot_eps = 0.0;
+  const int32_t* primal = nullptr; // per column of the matrix: 1 if primal
+};
+
+// Pairs (i, j) with 1 <= j <= i < 64 ordered by j descending, then i: the
+// pairs with j >= r0 are the first (64 - r0)(65 - r0) / 2 entries, so a
+// trailing triangle of the diagonal block spreads evenly over the threads.
+constexpr int kDiagPairs = (kPanelW - 1) * kPanelW / 2;
+
+__device__ __forceinline__ void diag_pair(int p, int& i, int& j) {
+  // group t = 64 - j holds pairs [t(t-1)/2, t(t+1)/2)
+  int t = (int)((sqrtf(8.0f * p + 1.0f) + 1.0f) * 0.5f);
+  while (t * (t - 1) / 2 > p) t--;
+  while (t * (t + 1) / 2 <= p) t++;
+  j = kPanelW - t;
+  i = j + (p - t * (t - 1) / 2);
+}
+
+// LDL^T of the diagonal block at (k0, k0) of matrix blockIdx.x, in shared
+// memory, in sub-panels of kSub = 16 columns (three barriers per sub-panel
+// instead of a barrier per column):
+//   (1) warp 0 factors the 16 x 16 diagonal sub-block in registers (lane i
+//       holds row i; column c's unscaled entries reach the other lanes by
+//       shuffle), applying the pivot rule to each pivot;
+//   (2) the rows below it in the block solve y L11^T = a, one thread per row
+//       (Y = y kept unscaled, L = y D^{-1});
+//   (3) the trailing triangle of the block takes A[i][j] -= sum_c L[i][c] Y[j][c]
+//       over the sub-panel, spread over all threads through the pair table.
+constexpr int kSub = 16;
+
+template <class T>
+__global__ void __launch_bounds__(256) k_dense_diag_t(T* __restrict__ S0, int n, int k0, int64_t bstride,
+                                                      PivotRule rule,
+                                                      unsigned long long* __restrict__ counters) {
+  __shared__ T A[kPanelW][kPanelW + 1];
+  __shared__ T Ys[kPanelW][kSub + 1];
+  __shared__ T Dinv[kSub];
+  __shared__ uint16_t pairs[kDiagPairs];
+  __shared__ int pert;
+  T* S = S0 + (int64_t)blockIdx.x * bstride;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int kb = min(kPanelW, n - k0);
+  for (int q = tid; q < kb * kb; q += blockDim.x) {
+    const int c = q / kb, r = q - c * kb;
+    if (r >= c) A[r][c] = S[(int64_t)(k0 + r) + (int64_t)(k0 + c) * n];
+  }
+  for (int p = tid; p < kDiagPairs; p += blockDim.x) {
+    int i, j;
+    diag_pair(p, i, j);
+    pairs[p] = (uint16_t)(i | (j << 8));
+  }
+  if (tid == 0) pert = 0;
+  __syncthreads();
+  const double thr = rule.anorm ? rule.pivot_eps * rule.anorm[blockIdx.x] : 0.0;
+  for (int c0 = 0; c0 < kb; c0 += kSub) {
+    const int cb = min(kSub, kb - c0);
+    if (warp == 0) {  // (1)
+      const int i = lane;
+      T r[kSub];
+#pragma unroll
+      for (int j = 0; j < kSub; j++) r[j] = (i < cb && j <= i) ? A[c0 + i][c0 + j] : T(0);
+      int np = 0;
+#pragma unroll
+      for (int c = 0; c < kSub; c++) {
+        if (c < cb) {
+          T d = __shfl_sync(0xffffffffu, r[c], c);
+          if (thr > 0.0 && fabs((double)d) < thr) {
+            d = (T)(rule.primal[k0 + c0 + c] ? thr : -thr);
+            np++;
+          }
+          const T dinv = T(1) / d;
+          const T u = r[c];  // unscaled entry of row i in column c (i > c)
+          if (i == c) r[c] = d;
+          else if (i > c) r[c] = u * dinv;
+          if (lane == 0) Dinv[c] = dinv;
+#pragma unroll
+          for (int j = c + 1; j < kSub; j++) {
+            const T uj = __shfl_sync(0xffffffffu, u, j);
+            if (i >= j) r[j] -= r[c] * uj;
+          }
+        }
+      }
+      if (i < cb) {
+#pragma unroll
+        for (int j = 0; j < kSub; j++)
+          if (j <= i) A[c0 + i][c0 + j] = r[j];
+      }
+      if (lane == 0) pert += np;
+    }
+    __syncthreads();
+    const int r0 = c0 + cb;
+    for (int row = r0 + tid; row < kb; row += blockDim.x) {  // (2)
+      T y[kSub];
+#pragma unroll
+      for (int c = 0; c < kSub; c++) {
+        if (c < cb) {
+          T acc = A[row][c0 + c];
+#pragma unroll
+          for (int c2 = 0; c2 < c; c2++) acc -= y[c2] * A[c0 + c][c0 + c2];
+          y[c] = acc;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < kSub; c++)
+        if (c < cb) {
+          Ys[row][c] = y[c];
+          A[row][c0 + c] = y[c] * Dinv[c];
+        }
+    }
+    __syncthreads();
+    if (r0 < kb) {  // (3): pairs with j >= r0
+      const int npairs = (kPanelW - r0) * (kPanelW - r0 + 1) / 2;
+      for (int p = tid; p < npairs; p += blockDim.x) {
+        const int ij = pairs[p], i = ij & 0xFF, j = ij >> 8;
+        if (i < kb) {
+          T acc = T(0);
+#pragma unroll
+          for (int c = 0; c < kSub; c++)
+            if (c < cb) acc += A[i][c0 + c] * Ys[j][c];
+          A[i][j] -= acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < kb * kb; q += blockDim.x) {
+    const int c = q / kb, r = q - c * kb;
+    if (r >= c) S[(int64_t)(k0 + r) + (int64_t)(k0 + c) * n] = A[r][c];
+  }
+  const T dd = tid < kb ? A[tid][tid] : T(0);
+  const int pos = __syncthreads_count(dd > T(0));
+  const int neg = __syncthreads_count(dd < T(0));
+  if (tid == 0) {
+    atomicAdd(&counters[kPos], (unsigned long long)pos);
+    atomicAdd(&counters[kNeg], (unsigned long long)neg);
+    if (kb - pos - neg) atomicAdd(&counters[kZero], (unsigned long long)(kb - pos - neg));
+    if (pert) atomicAdd(&counters[kPerturbed], (unsigned long long)pert);
+  }
+}
+
+// Rows k0+kb .. rend-1 of matrix blockIdx.y, one thread per row (ROWS rows
+// per CTA): solve y L11^T = a with y in registers and L11 in shared memory
+// (every thread of a warp reads the same L11 entry), then Y = y and
+// L21 = y D1^{-1}.  Y has the matrix's leading dimension n and its rows.
+template <class T, int ROWS>
+__global__ void __launch_bounds__(ROWS) k_dense_panel_t(T* __restrict__ S0, T* __restrict__ Y0, int n,
+                                                        int k0, int rend, int64_t bstride,
+                                                        int64_t ystride) {
+  __shared__ T L11[kPanelW][kPanelW];  // [j][c], zero outside the strict lower triangle
+  __shared__ T dinv[kPanelW];
+  T* S = S0 + (int64_t)blockIdx.y * bstride;
+  T* Y = Y0 + (int64_t)blockIdx.y * ystride;
+  const int kb = min(kPanelW, n - k0);
+  for (int q = threadIdx.x; q < kPanelW * kPanelW; q += blockDim.x) {
+    const int c = q / kPanelW, j = q - c * kPanelW;
+    L11[j][c] = (j > c && j < kb) ? S[(int64_t)(k0 + j) + (int64_t)(k0 + c) * n] : T(0);
+  }
+  for (int c = threadIdx.x; c < kPanelW; c += blockDim.x)
+    dinv[c] = c < kb ? T(1) / S[(int64_t)(k0 + c) + (int64_t)(k0 + c) * n] : T(0);
+  __syncthreads();
+  const int row = k0 + kb + blockIdx.x * ROWS + threadIdx.x;
+  if (row >= rend) return;
+  T y[kPanelW];
+#pragma unroll
+  for (int c = 0; c < kPanelW; c++) y[c] = c < kb ? S[row + (int64_t)(k0 + c) * n] : T(0);
+  // y_j = a_j - sum_{c<j} y_c L_jc, subtracted in increasing c
+#pragma unroll
+  for (int j = 1; j < kPanelW; j++) {
+    T acc = y[j];
+#pragma unroll
+    for (int c = 0; c < j; c++) acc -= y[c] * L11[j][c];
+    y[j] = acc;
+  }
+#pragma unroll
+  for (int c = 0; c < kPanelW; c++)
+    if (c < kb) {
+      Y[row + (int64_t)c * n] = y[c];
+      S[row + (int64_t)(k0 + c) * n] = y[c] * dinv[c];
+    }
+}
+
+// The same solve with one warp per row: lane l holds y_l and y_{l+32}, and
+// column c's value reaches the other lanes by shuffle.  The dependency chain
+// of a row is 64 steps long instead of 2016 multiply-adds, which is what counts
+// for few rows (and in FP64, whose dependent multiply-add latency is long).
+template <class T>
+__global__ void __launch_bounds__(256) k_dense_panel_w(T* __restrict__ S0, T* __restrict__ Y0, int n, int k0,
+                                                       int rend, int64_t bstride, int64_t ystride) {
+  __shared__ T L11[kPanelW][kPanelW + 1];
+  __shared__ T dinv[kPanelW];
+  T* S = S0 + (int64_t)blockIdx.y * bstride;
+  T* Y = Y0 + (int64_t)blockIdx.y * ystride;
+  const int kb = min(kPanelW, n - k0);
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
+    const int j = q / kb, i = q - j * kb;
+    L11[i][j] = S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n];
+  }
+  for (int c = threadIdx.x; c < kb; c += blockDim.x) dinv[c] = T(1) / S[(int64_t)(k0 + c) + (int64_t)(k0 + c) * n];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int row = k0 + kb + blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (row >= rend) return;
+  T y0 = lane < kb ? S[row + (int64_t)(k0 + lane) * n] : T(0);
+  T y1 = lane + 32 < kb ? S[row + (int64_t)(k0 + lane + 32) * n] : T(0);
+  for (int c = 0; c < kb; c++) {
+    const T yc = __shfl_sync(0xffffffffu, c < 32 ? y0 : y1, c & 31);
+    if (lane > c && lane < kb) y0 -= yc * L11[lane][c];
+    if (lane + 32 > c && lane + 32 < kb) y1 -= yc * L11[lane + 32][c];
+  }
+  if (lane < kb) {
+    Y[row + (int64_t)lane * n] = y0;
+    S[row + (int64_t)(k0 + lane) * n] = y0 * dinv[lane];
+  }
+  if (lane + 32 < kb) {
+    Y[row + (int64_t)(lane + 32) * n] = y1;
+    S[row + (int64_t)(k0 + lane + 32) * n] = y1 * dinv[lane + 32];
+  }
+}
+
+// Rows below the diagonal block of nb matrices: FP32 with many rows takes a
+// thread per row, everything else a warp per row.
+template <class T>
+inline void launch_dense_panel(T* S, T* Y, int n, int k0, int rend, int nb, int64_t bstride, int64_t ystride,
+                               cudaStream_t st) {
+  const int m = rend - k0 - min(kPanelW, n - k0);
+  if (m <= 0) return;
+  if constexpr (sizeof(T) == 4) {
+    if (m > 2048) {
+      k_dense_panel_t<T, 128><<<dim3((m + 127) / 128, nb), 128, 0, st>>>(S, Y, n, k0, rend, bstride, ystride);
+      return;
+    }
+  }
+  k_dense_panel_w<T><<<dim3((m + 7) / 8, nb), 256, 0, st>>>(S, Y, n, k0, rend, bstride, ystride);
+}
+
+// Trailing update of matrix blockIdx.y on the lower 64 x 64 tiles below the
+// panel: A[i][j] -= sum_c Y[i][c] L[j][c] for k0+kb <= j <= i < rend.
+__global__ void __launch_bounds__(256) k_dense_update(double* __restrict__ S0, const double* __restrict__ Y0,
+                                                      int n, int k0, int rend, int64_t bstride,
+                                                      int64_t ystride) {
+  double* S = S0 + (int64_t)blockIdx.y * bstride;
+  const double* Y = Y0 + (int64_t)blockIdx.y * ystride;
+  const int kb = min(kPanelW, n - k0);
+  const int base = k0 + kb;
+  int tile = blockIdx.x, ti = 0;
+  while (tile > ti) {
+    tile -= ti + 1;
+    ti++;
+  }
+  const int tj = tile;
+  const int i0 = base + ti * 64, j0 = base + tj * 64;
+  constexpr int KC = 32;              // columns staged per pass
+  __shared__ double Ys[KC][64 + 1];  // [c][i]
+  __shared__ double Ls[KC][64 + 1];  // [c][j]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16, 4x4 outputs each
+  double acc[4][4] = {};
+  for (int cb = 0; cb < kb; cb += KC) {
+    const int kc = min(KC, kb - cb);
+    __syncthreads();
+    for (int q = threadIdx.x; q < kc * 64; q += 256) {
+      const int c = q / 64, r = q % 64;
+      Ys[c][r] = (i0 + r < rend) ? Y[(i0 + r) + (int64_t)(cb + c) * n] : 0.0;
+      Ls[c][r] = (j0 + r < rend) ? S[(j0 + r) + (int64_t)(k0 + cb + c) * n] : 0.0;
+    }
+    __syncthreads();
+    for (int c = 0; c < kc; c++) {
+      double a[4], bb[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        a[u] = Ys[c][ty + 16 * u];
+        bb[u] = Ls[c][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) acc[u][v] += a[u] * bb[v];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+      if (i < rend && j < rend && i >= j) S[i + (int64_t)j * n] -= acc[u][v];
+    }
+}
+
+}  // namespace
+
+}  // namespace kkt

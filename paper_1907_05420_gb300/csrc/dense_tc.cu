@@ -30,7 +30,7 @@
 // (along M/N) is 128 * (cores per row group).
 #include <cuda_bf16.h>
 
-#include "handle.h"
+#include "dense_kernels.cuh"
 
 namespace kkt {
 
@@ -113,11 +113,25 @@ __device__ __forceinline__ void digits7(double v, int e, float out[kEmuSlices]) 
 // Images of the operands of one panel step.  Rows rho in [0, m) are trailing
 // rows base + rho.  A = Y (rows of L21 D, from Y with leading dimension n),
 // B = L21 (columns k0..k0+63 of S).  Rows >= m are written as zeros.
+// Batched over blockIdx.y (the dense tails of the block factors): matrix b
+// is S + b * ts.s, its Y, images and scales are offset by the other strides.
+struct TcStrides {
+  int64_t s = 0, y = 0, img_a = 0, img_b = 0, scale = 0;
+};
+
 template <int MODE, class T>
-__global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S, const T* __restrict__ Y,
-                                                  int n, int k0, int m, uint8_t* __restrict__ imgA,
-                                                  uint8_t* __restrict__ imgB, double* __restrict__ scaleA,
-                                                  double* __restrict__ scaleB, int mpadA, int mpadB) {
+__global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S0, const T* __restrict__ Y0,
+                                                  int n, int k0, int m, uint8_t* __restrict__ imgA0,
+                                                  uint8_t* __restrict__ imgB0, double* __restrict__ scaleA0,
+                                                  double* __restrict__ scaleB0, int mpadA, int mpadB,
+                                                  TcStrides ts) {
+  const int64_t bb = blockIdx.y;
+  const T* S = S0 + bb * ts.s;
+  const T* Y = Y0 + bb * ts.y;
+  uint8_t* imgA = imgA0 + bb * ts.img_a;
+  uint8_t* imgB = imgB0 + bb * ts.img_b;
+  double* scaleA = scaleA0 + bb * ts.scale;
+  double* scaleB = scaleB0 + bb * ts.scale;
   constexpr ModeCfg cfg = mode_cfg(MODE);
   constexpr int KG = kgroups_of(MODE);
   constexpr int kpc = 16 / cfg.esz;  // elements per 16-byte core row
@@ -192,11 +206,18 @@ __device__ __forceinline__ void tile_of(int t, int TJ, int& I, int& J) {
 }
 
 template <int MODE, class T>
-__global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S, int n, int k0, int m, int TJ,
-                                                      const uint8_t* __restrict__ imgA,
-                                                      const uint8_t* __restrict__ imgB,
-                                                      const double* __restrict__ scaleA,
-                                                      const double* __restrict__ scaleB, int* err) {
+__global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n, int k0, int m, int TJ,
+                                                      const uint8_t* __restrict__ imgA0,
+                                                      const uint8_t* __restrict__ imgB0,
+                                                      const double* __restrict__ scaleA0,
+                                                      const double* __restrict__ scaleB0, int* err,
+                                                      TcStrides ts) {
+  const int64_t bb = blockIdx.y;
+  T* S = S0 + bb * ts.s;
+  const uint8_t* imgA = imgA0 + bb * ts.img_a;
+  const uint8_t* imgB = imgB0 + bb * ts.img_b;
+  const double* scaleA = scaleA0 + bb * ts.scale;
+  const double* scaleB = scaleB0 + bb * ts.scale;
   constexpr ModeCfg cfg = mode_cfg(MODE);
   constexpr int KG = kgroups_of(MODE);
   constexpr int A_BYTES = image_bytes(MODE, TM), B_BYTES = image_bytes(MODE, TN);
@@ -376,94 +397,6 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S, int n, 
 
 // ---- FP32 panel kernels for the TF32 / BF16 modes (same steps as the FP64 ones in dense.cu) ----
 
-// LDL^T of the 64 x 64 diagonal block with rows in registers.  Thread (r, h)
-// holds columns [32h, 32h + 32) of row r (two threads per row, 128 threads).
-// Step c publishes the unscaled column c (u_r = a_r[c], u_c = d) in a
-// double-buffered shared array, one barrier per step; each thread then forms
-// l_r = u_r / d and updates its columns c2 with c < c2 <= r: a_r[c2] -= l_r u_c2
-// (since l_c2 d = u_c2).
-template <class T>
-__global__ void __launch_bounds__(2 * TK) k_dense_diag_t(T* __restrict__ S, int n, int k0,
-                                                         unsigned long long* __restrict__ counters) {
-  constexpr int H = TK / 2;
-  __shared__ T colbuf[2][TK];
-  const int r = threadIdx.x & (TK - 1), h = threadIdx.x / TK;
-  const int kb = min(TK, n - k0);
-  T a[H];
-#pragma unroll
-  for (int j = 0; j < H; j++) {
-    const int col = h * H + j;
-    a[j] = (r < kb && col <= r) ? S[(int64_t)(k0 + r) + (int64_t)(k0 + col) * n] : T(0);
-  }
-  T mydiag = T(0);
-#pragma unroll
-  for (int c = 0; c < TK; c++) {
-    if (c < kb) {
-      T* u = colbuf[c & 1];
-      const bool mine = (c / H) == h;  // this thread holds column c of its row
-      if (mine && r >= c && r < kb) u[r] = a[c % H];
-      __syncthreads();
-      const T d = u[c];
-      if (r == c && mine) mydiag = d;
-      if (r > c && r < kb) {
-        const T l = u[r] / d;
-        if (mine) a[c % H] = l;
-#pragma unroll
-        for (int j = 0; j < H; j++) {
-          const int c2 = h * H + j;
-          if (c2 > c && c2 <= r) a[j] -= l * u[c2];
-        }
-      }
-    }
-  }
-  if (r < kb) {
-#pragma unroll
-    for (int j = 0; j < H; j++) {
-      const int col = h * H + j;
-      if (col <= r) S[(int64_t)(k0 + r) + (int64_t)(k0 + col) * n] = a[j];
-    }
-  }
-  const int pos = __syncthreads_count(r < kb && mydiag > T(0));
-  const int neg = __syncthreads_count(r < kb && mydiag < T(0));
-  if (threadIdx.x == 0) {
-    atomicAdd(&counters[kPos], (unsigned long long)pos);
-    atomicAdd(&counters[kNeg], (unsigned long long)neg);
-    if (kb - pos - neg) atomicAdd(&counters[kZero], (unsigned long long)(kb - pos - neg));
-  }
-}
-
-// rows below the block: solve y L11^T = a (one warp per row, L11 in shared memory)
-template <class T>
-__global__ void __launch_bounds__(256) k_dense_panel_t(T* __restrict__ S, T* __restrict__ Y, int n, int k0,
-                                                       int rend) {
-  __shared__ T L11[TK][TK + 1];
-  const int kb = min(TK, n - k0);
-  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
-    const int j = q / kb, i = q - j * kb;
-    L11[i][j] = S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int row = k0 + kb + blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);  // one warp per row
-  if (row >= rend) return;
-  // lane holds y[lane] and y[lane+32]
-  T y0 = lane < kb ? S[row + (int64_t)(k0 + lane) * n] : T(0);
-  T y1 = lane + 32 < kb ? S[row + (int64_t)(k0 + lane + 32) * n] : T(0);
-  for (int c = 0; c < kb; c++) {
-    const T yc = __shfl_sync(0xffffffffu, c < 32 ? y0 : y1, c & 31);
-    if (lane > c && lane < kb) y0 -= yc * L11[lane][c];
-    if (lane + 32 > c && lane + 32 < kb) y1 -= yc * L11[lane + 32][c];
-  }
-  if (lane < kb) {
-    Y[row + (int64_t)lane * n] = y0;
-    S[row + (int64_t)(k0 + lane) * n] = y0 / L11[lane][lane];
-  }
-  if (lane + 32 < kb) {
-    Y[row + (int64_t)(lane + 32) * n] = y1;
-    S[row + (int64_t)(k0 + lane + 32) * n] = y1 / L11[lane + 32][lane + 32];
-  }
-}
-
 __global__ void k_to_f32(const double* __restrict__ S, float* __restrict__ S32, int64_t n2) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n2; q += (int64_t)gridDim.x * blockDim.x)
     S32[q] = (float)S[q];
@@ -474,33 +407,37 @@ __global__ void k_dense_diag_scale_f(const float* __restrict__ S, double* __rest
     x[i] /= (double)S[i + (int64_t)i * n];
 }
 
+// One blocked LDL^T of nb matrices of order n (matrix b at S + b * ts.s):
+// diagonal block and panel on the CUDA cores, trailing update on the tensor
+// cores.  rend: per 64-wide panel, one past its last nonzero row (or null).
 template <int MODE, class T>
-cudaError_t factor_tc(Handle& h, T* S, T* Y, unsigned long long* counters, cudaStream_t st) {
-  const int n = h.nC;
+cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int nb, const TcStrides& ts, const PivotRule& rule,
+                      const int32_t* rend_of_panel, unsigned long long* counters, uint8_t* imgA,
+                      uint8_t* imgB, double* scaleA, double* scaleB, cudaStream_t st) {
   constexpr int A_BYTES = image_bytes(MODE, TM), B_BYTES = image_bytes(MODE, TN);
   const int smem = A_BYTES + B_BYTES;
   cudaError_t e = cudaFuncSetAttribute(k_tc_update<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   for (int k0 = 0; k0 < n; k0 += TK) {
     const int kb = std::min(TK, n - k0);
-    k_dense_diag_t<T><<<1, 2 * TK, 0, st>>>(S, n, k0, counters);
+    k_dense_diag_t<T><<<nb, 256, 0, st>>>(S, n, k0, ts.s, rule, counters);
     h.launches++;
     // rows below the envelope of the panel's columns stay zero (no pivoting)
-    const int rend = h.panel_rend.empty() ? n : h.panel_rend[k0 / TK];
+    const int rend = rend_of_panel ? rend_of_panel[k0 / TK] : n;
     const int m = rend - k0 - kb;
     if (m <= 0) continue;
-    k_dense_panel_t<T><<<(m + 7) / 8, 256, 0, st>>>(S, Y, n, k0, rend);
+    launch_dense_panel<T>(S, Y, n, k0, rend, nb, ts.s, ts.y, st);
     h.launches++;
     if (kb < TK) continue;  // a ragged last panel leaves no trailing matrix
     const int TI = (m + TM - 1) / TM, TJ = (m + TN - 1) / TN;
     const int mpadA = TI * TM, mpadB = TJ * TN;
-    const int sgrid = std::min((mpadA + mpadB + 255) / 256, 152 * 8);
-    k_tc_slice<MODE, T><<<sgrid, 256, 0, st>>>(S, Y, n, k0, m, h.tc_imgA, h.tc_imgB, h.tc_scaleA, h.tc_scaleB,
-                                               mpadA, mpadB);
+    const int sgrid = std::max(1, std::min((mpadA + mpadB + 255) / 256, 152 * 8 / nb));
+    k_tc_slice<MODE, T><<<dim3(sgrid, nb), 256, 0, st>>>(S, Y, n, k0, m, imgA, imgB, scaleA, scaleB, mpadA,
+                                                         mpadB, ts);
     int tiles = 0;
     for (int I = 0; I < TI; I++) tiles += std::min(2 * I + 2, TJ);
-    k_tc_update<MODE, T><<<tiles, 128, smem, st>>>(S, n, k0, m, TJ, h.tc_imgA, h.tc_imgB, h.tc_scaleA,
-                                                   h.tc_scaleB, h.dev_err);
+    k_tc_update<MODE, T><<<dim3(tiles, nb), 128, smem, st>>>(S, n, k0, m, TJ, imgA, imgB, scaleA, scaleB,
+                                                             h.dev_err, ts);
     h.launches += 2;
   }
   return cudaGetLastError();
@@ -528,12 +465,34 @@ int64_t tc_image_bytes_a(int n, int mode) {
 cudaError_t launch_dense_ldlt_tc(Handle& h, int mode, unsigned long long* counters, cudaStream_t st) {
   const int n = h.nC;
   if (n == 0) return cudaSuccess;
-  if (mode == KKT_F64_EMULATED) return factor_tc<2, double>(h, h.S, h.Ypanel, counters, st);
+  const int32_t* rend = h.panel_rend.empty() ? nullptr : h.panel_rend.data();
+  const TcStrides one{};
+  if (mode == KKT_F64_EMULATED)
+    return factor_tc<2, double>(h, h.S, h.Ypanel, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
+                                h.tc_scaleA, h.tc_scaleB, st);
   const int64_t n2 = (int64_t)n * n;
   k_to_f32<<<(int)std::min<int64_t>((n2 + 255) / 256, 152 * 32), 256, 0, st>>>(h.S, h.S32, n2);
   h.launches++;
-  if (mode == KKT_TF32) return factor_tc<0, float>(h, h.S32, h.Y32, counters, st);
-  return factor_tc<1, float>(h, h.S32, h.Y32, counters, st);
+  if (mode == KKT_TF32)
+    return factor_tc<0, float>(h, h.S32, h.Y32, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
+                               h.tc_scaleA, h.tc_scaleB, st);
+  return factor_tc<1, float>(h, h.S32, h.Y32, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
+                             h.tc_scaleA, h.tc_scaleB, st);
+}
+
+// The dense tails of the N block factors in emulated FP64: the batched
+// blocked LDL^T above with the static-pivot rule of the block factors.
+cudaError_t launch_tail_factor_emulated(Handle& h, cudaStream_t st) {
+  const int nT = h.nT;
+  TcStrides ts;
+  ts.s = (int64_t)nT * nT;
+  ts.y = (int64_t)nT * TK;
+  ts.img_a = tc_image_bytes_a(nT, KKT_F64_EMULATED);
+  ts.img_b = tc_image_bytes(nT, KKT_F64_EMULATED) - ts.img_a;
+  ts.scale = (int64_t)nT + 256;
+  const PivotRule rule{h.anorm, h.opt.pivot_eps, h.d.col_primal + h.sym.tail_col};
+  return factor_tc<2, double>(h, h.Tt, h.TY, nT, h.N, ts, rule, nullptr, h.counters, h.t_imgA, h.t_imgB,
+                              h.t_scaleA, h.t_scaleB, st);
 }
 
 // Diagonal block and panel of one 64-wide step of the FP64 factor (shared by
@@ -542,11 +501,11 @@ cudaError_t launch_dense_diag_panel_f64(Handle& h, int k0, int rend, unsigned lo
                                         cudaStream_t st) {
   const int n = h.nC;
   const int kb = std::min(TK, n - k0);
-  k_dense_diag_t<double><<<1, 2 * TK, 0, st>>>(h.S, n, k0, counters);
+  k_dense_diag_t<double><<<1, 256, 0, st>>>(h.S, n, k0, 0, PivotRule{}, counters);
   h.launches++;
   const int m = rend - k0 - kb;
   if (m > 0) {
-    k_dense_panel_t<double><<<(m + 7) / 8, 256, 0, st>>>(h.S, h.Ypanel, n, k0, rend);
+    launch_dense_panel<double>(h.S, h.Ypanel, n, k0, rend, 1, 0, 0, st);
     h.launches++;
   }
   return cudaGetLastError();

@@ -15,6 +15,10 @@
 //     top of the tree spread over many SMs;
 //   k_panel_factor: dense LDL^T of the panel (1x1 pivots; a pivot below
 //     pivot_eps*max|A_i| is replaced by the expected-sign value and counted).
+// The top of the tree (the dense tail, a suffix of the supernodes) is left out
+// of the level loop: once the rest is factored, its updates from outside the
+// tail are applied (k_factor_update<true>) and the tail is factored as one
+// dense triangle per block (tail.cu).
 // Every entry is written by one thread in a fixed order: the result does not
 // depend on scheduling.
 #include "handle.h"
@@ -65,8 +69,12 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int v) {
 // subtracted from the panel once.  For each update the rows of d that land in
 // the tile ([ia, ib), precomputed per tile) and the rows that land in s's
 // columns ([r0, r1)) are staged in shared memory, the latter pre-multiplied by D_d.
+// NONTAIL: apply only the updates from descendants outside the dense tail
+// (the leading upd_ntail[s] entries of s's list); used for the tail supernodes,
+// whose updates among themselves the dense tail factor performs.
 constexpr int kTileRows = 64;
 
+template <bool NONTAIL>
 __global__ void __launch_bounds__(256) k_factor_update(const int32_t* __restrict__ work,
                                                        const int32_t* __restrict__ frange, DevSym d,
                                                        double* __restrict__ Lx, int64_t pt) {
@@ -82,7 +90,7 @@ __global__ void __launch_bounds__(256) k_factor_update(const int32_t* __restrict
   const int nrow = hi - lo;
   double* P = Lx + b * pt + d.sn_valoff[s];
   for (int q = tid; q < kTileRows * (kMaxSnWidth + 1); q += blockDim.x) (&acc[0][0])[q] = 0.0;
-  const int64_t u0 = d.upd_ptr[s], u1 = d.upd_ptr[s + 1];
+  const int64_t u0 = d.upd_ptr[s], u1 = NONTAIL ? u0 + d.upd_ntail[s] : d.upd_ptr[s + 1];
   for (int64_t u = u0; u < u1; u++) {
     const int ia = frange[2 * (roff + (u - u0))], ib = frange[2 * (roff + (u - u0)) + 1];
     if (ia >= ib) continue;  // no row of this descendant falls in the tile
@@ -182,22 +190,32 @@ cudaError_t launch_scatter_a(Handle& h, cudaStream_t st) {
 
 cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
   const int64_t pt = h.sym.panel_total;
+  // supernodes outside the dense tail, level by level
   for (int l = 0; l < h.sym.nlevels; l++) {
     const int w0 = h.fwork_lvl_ptr[l], w1 = h.fwork_lvl_ptr[l + 1];
     if (l > 0 && w1 > w0) {
       dim3 grid(w1 - w0, h.N);
-      {
-    k_factor_update<<<grid, 256, 0, st>>>(h.d.fwork + 4 * w0, h.d.frange, h.d, h.Lx, pt);
-    h.launches++;
-  }
+      k_factor_update<false><<<grid, 256, 0, st>>>(h.d.fwork + 4 * w0, h.d.frange, h.d, h.Lx, pt);
+      h.launches++;
     }
-    const int s0 = h.lvl_ptr[l], s1 = h.lvl_ptr[l + 1];
-    dim3 grid2(s1 - s0, h.N);
-    {
-    k_panel_factor<<<grid2, 256, 0, st>>>(h.d.lvl_sn + s0, h.d, h.Lx, pt, h.anorm, h.opt.pivot_eps,
-                                          h.counters);
-    h.launches++;
+    const int s0 = h.flvl_ptr[l], s1 = h.flvl_ptr[l + 1];
+    if (s1 > s0) {
+      dim3 grid2(s1 - s0, h.N);
+      k_panel_factor<<<grid2, 256, 0, st>>>(h.d.flvl_sn + s0, h.d, h.Lx, pt, h.anorm, h.opt.pivot_eps,
+                                            h.counters);
+      h.launches++;
+    }
   }
+  if (h.nT > 0) {
+    // updates of the tail from the rest of the tree (all factored by now), then
+    // the dense factor of the tail
+    if (h.tail_items > 0) {
+      dim3 grid(h.tail_items, h.N);
+      k_factor_update<true><<<grid, 256, 0, st>>>(h.d.twork, h.d.frange, h.d, h.Lx, pt);
+      h.launches++;
+    }
+    cudaError_t e = launch_dense_tail(h, st);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

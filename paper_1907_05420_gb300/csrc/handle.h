@@ -69,6 +69,9 @@ struct DevSym {
   int32_t* g_rows = nullptr;       // W rows in contraction order: primal chunks, then multiplier chunks
   int32_t* trsv_jlo = nullptr;     // envelope of S (structured mode): first column block of each row block
   int32_t* trsv_jhi = nullptr;     // one past the last row block of each column block
+  int32_t* flvl_sn = nullptr;      // supernodes outside the dense tail, by level (block factor)
+  int32_t* twork = nullptr;        // factor work items of the dense-tail supernodes
+  int32_t* upd_ntail = nullptr;    // per supernode: leading updates from outside the tail
 };
 
 // Counters written by the kernels (device, int64).
@@ -87,6 +90,9 @@ struct Handle {
   std::vector<int32_t> lvl_ptr;        // supernodes per level (host copy)
   std::vector<int32_t> reach_lvl_ptr;
   std::vector<int32_t> panel_rend;     // structured mode: per 64-wide panel, one past its last nonzero row
+  std::vector<int32_t> flvl_ptr;       // supernodes outside the dense tail per level (factor)
+  int32_t nT = 0;                      // columns of the dense tail (0 = none)
+  int32_t tail_items = 0;              // factor work items of the tail supernodes
 
   // numeric buffers
   double* Lx = nullptr;       // N * panel_total
@@ -98,15 +104,22 @@ struct Handle {
   double* G = nullptr;        // N * k * k
   double* S = nullptr;        // nC * nC column-major (lower triangle used)
   double* Ypanel = nullptr;   // nC * kDenseNB scratch of the dense factor
+  double* Tt = nullptr;       // N * nT * nT: dense tails of the block factors (column-major)
+  double* TY = nullptr;       // N * nT * kDenseNB: panel scratch of the tail factor
+  int tail_mode = 0;          // 0 none, 1 FP64 on the CUDA cores, 2 emulated FP64 on the tensor cores
+  uint8_t* t_imgA = nullptr;  // per block: tensor-core operand images of one tail panel step
+  uint8_t* t_imgB = nullptr;
+  double* t_scaleA = nullptr; // per block: row scales of the emulated update (nT + 256)
+  double* t_scaleB = nullptr;
   float* S32 = nullptr;       // nC * nC FP32 copy factored in the TF32/BF16 modes
   float* Y32 = nullptr;       // nC * kDenseNB FP32 panel scratch
   uint8_t* tc_imgA = nullptr; // tensor-core operand images of one panel step
   uint8_t* tc_imgB = nullptr;
   double* tc_scaleA = nullptr;  // row scales of the emulated FP64 update
   double* tc_scaleB = nullptr;
-  int s_factor = 0;
+  int s_factor = 0;           // current factor of S: 0 FP64-accurate in S, 1 FP32 in S32
   bool g_reduced = false;     // S assembled from a TF32/BF16 contraction
-  int g_nchunks = 0, g_nchunks_pos = 0;  // 64-row chunks of g_rows (positive-pivot chunks first)           // current factor of S: 0 FP64-accurate in S, 1 FP32 in S32
+  int g_nchunks = 0, g_nchunks_pos = 0;  // 64-row chunks of g_rows (positive-pivot chunks first)
   double* knorm = nullptr;    // ||K||_inf
   unsigned long long* counters = nullptr;  // kNumCounters
   // solve work vectors
@@ -144,6 +157,9 @@ constexpr int kDenseNB = 64;
 // ---- kernel launchers (factor.cu) ----
 cudaError_t launch_scatter_a(Handle& h, cudaStream_t st);
 cudaError_t launch_factor_levels(Handle& h, cudaStream_t st);
+// ---- (tail.cu) ----
+cudaError_t launch_dense_tail(Handle& h, cudaStream_t st);
+cudaError_t launch_tail_factor_emulated(Handle& h, cudaStream_t st);  // (dense_tc.cu)
 // ---- (schur.cu) ----
 cudaError_t launch_w_solve(Handle& h, cudaStream_t st);
 cudaError_t launch_contract_g(Handle& h, cudaStream_t st);

@@ -257,6 +257,7 @@ std::string analyze_pattern(int32_t n, int32_t nP, const int32_t* rowptr, const 
     if (parent[j] >= 0) nchild[parent[j]]++;
   S.nnzL = 0;
   S.flops = 0;
+  S.colcount.assign(cnt.begin(), cnt.begin() + n);
   for (int32_t j = 0; j < n; j++) {
     S.nnzL += cnt[j];
     S.flops += (double)cnt[j] * (cnt[j] + 3);  // scale column, rank-1 update of the rest
@@ -586,6 +587,31 @@ void s_envelope(const Coupling& C, int32_t c_kind, int32_t block, std::vector<in
     int32_t fmin = nC;
     for (int32_t r = p * block; r < cend; r++) fmin = std::min(fmin, first[r]);
     jlo[p] = fmin / block;
+  }
+}
+
+void choose_tail(Symbolic& S, int32_t N, int64_t max_bytes, int32_t min_cols) {
+  const int32_t n = S.n;
+  S.tail_sn = S.nsuper;
+  S.tail_col = n;
+  double suffix = 0.0;  // exact sparse flops of columns >= sn_first[t]
+  for (int32_t t = S.nsuper - 1; t >= 0; t--) {
+    for (int32_t j = S.sn_first[t]; j < S.sn_first[t + 1]; j++)
+      suffix += (double)S.colcount[j] * (S.colcount[j] + 3);
+    const double nT = (double)(n - S.sn_first[t]);
+    if (nT < min_cols) continue;
+    if ((double)N * nT * nT * 8.0 > (double)max_bytes) break;
+    if (nT * nT * nT / 3.0 <= 2.0 * suffix) {
+      S.tail_sn = t;
+      S.tail_col = S.sn_first[t];
+    }
+  }
+  S.upd_ntail.assign(S.nsuper, 0);
+  for (int32_t s = 0; s < S.nsuper; s++) {
+    int32_t c = 0;
+    for (int64_t u = S.upd_ptr[s]; u < S.upd_ptr[s + 1]; u++)
+      if (S.upd_src[u] < S.tail_sn) c++;  // update lists are in increasing descendant order
+    S.upd_ntail[s] = c;
   }
 }
 

@@ -15,6 +15,11 @@ namespace kkt {
 // fits the shared-memory tiles of the factor kernels.
 constexpr int kMaxSnWidth = 32;
 
+// Dense tail limits: at least this many columns, and at most this many bytes
+// for the N dense triangles held at once.
+constexpr int32_t kTailMinCols = 16;
+constexpr int64_t kTailMaxBytes = int64_t(24) << 30;
+
 struct Symbolic {
   int32_t n = 0;   // block size nA
   int32_t nP = 0;  // primal rows come first
@@ -54,7 +59,21 @@ struct Symbolic {
   // statistics
   int64_t nnzL = 0;       // strictly lower nonzeros of L (exact, no padding)
   double flops = 0;       // factorization flops per block
+  std::vector<int32_t> colcount;  // per column: strictly lower nonzeros of L
+
+  // dense tail: columns [tail_col, n), the supernodes tail_sn .. nsuper-1.  A
+  // suffix of the postorder is closed under the elimination-tree parent, so
+  // every row of a tail supernode is a tail column and the tail is one dense
+  // lower triangle per block.  tail_sn == nsuper when there is none.
+  int32_t tail_sn = 0, tail_col = 0;
+  std::vector<int32_t> upd_ntail;  // per supernode: its leading updates from non-tail descendants
 };
+
+// Picks the dense tail: the longest suffix of supernodes whose dense factor
+// costs at most twice the exact sparse flops of its columns, has at least
+// min_cols columns, and whose N dense triangles (nT^2 doubles each) fit
+// max_bytes.  Fills tail_sn, tail_col and upd_ntail.
+void choose_tail(Symbolic& S, int32_t N, int64_t max_bytes, int32_t min_cols);
 
 // Coupling analysis: B_i (COO per block) against the block factor.
 // With E the sorted union of the rows that carry a nonzero of some B_i

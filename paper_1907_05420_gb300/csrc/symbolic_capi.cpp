@@ -38,6 +38,7 @@ kkt_symbolic* kkt_symbolic_create(int32_t nA, int32_t nP, const int32_t* a_rowpt
     return nullptr;
   }
   kkt::s_envelope(in->C, c_kind, 64, in->panel_rend, in->jlo, in->jhi);
+  kkt::choose_tail(in->S, N, kkt::kTailMaxBytes, kkt::kTailMinCols);
   return reinterpret_cast<kkt_symbolic*>(in);
 }
 
@@ -70,8 +71,10 @@ int64_t kkt_symbolic_get(const kkt_symbolic* sym, const char* name, int64_t* out
   if (n == "panel_rend") return copy_out(in->panel_rend, out);
   if (n == "jlo") return copy_out(in->jlo, out);
   if (n == "jhi") return copy_out(in->jhi, out);
+  if (n == "colcount") return copy_out(S.colcount, out);
+  if (n == "upd_ntail") return copy_out(S.upd_ntail, out);
   if (n == "stats") {
-    std::vector<int64_t> st = {S.n, S.nsuper, S.nlevels, S.panel_total, S.nnzL, C.k, C.nw};
+    std::vector<int64_t> st = {S.n, S.nsuper, S.nlevels, S.panel_total, S.nnzL, C.k, C.nw, S.tail_sn, S.tail_col};
     return copy_out(st, out);
   }
   return -1;

@@ -1,0 +1,82 @@
+// (a) Dense tail of the block factors.
+//
+// The last supernodes of the postorder (the top of the elimination tree) have
+// row sets inside the tail columns [c_T, n) and are nearly dense there, so the
+// tail of every block is factored as one dense nT x nT lower triangle
+// (nT = n - c_T) instead of supernode by supernode: the work is the same
+// LDL^T (Algorithm 1's block factorization) with the explicit zeros of the
+// tail included, done by the blocked dense kernels that factor S
+// (dense_kernels.cuh), batched over the N blocks.
+//
+// Per factor: the tail panels (A's values plus the updates from outside the
+// tail, applied by the level loop) are gathered into the zeroed dense
+// triangles; each 64-wide panel step factors the diagonal blocks of all N
+// triangles (with the static-pivot rule and the inertia counts of the sparse
+// panels), forms L21 and Y = L21 D, and updates the trailing triangles, in
+// FP64 on the CUDA cores (tail mode 1) or in emulated FP64 on the tensor cores
+// (tail mode 2, the update of dense_tc.cu: 7 base-256 digit slices per
+// operand); the factor is scattered back into the supernodal panels, which
+// the solves use.
+// Entries of the triangles outside the supernodal structure stay exact zeros
+// (every product that reaches them has a zero factor).
+#include "dense_kernels.cuh"
+
+namespace kkt {
+
+namespace {
+
+// panels of the tail supernodes <-> dense triangles, lower part only
+template <bool TO_DENSE>
+__global__ void __launch_bounds__(256) k_tail_move(DevSym d, double* __restrict__ Lx, int64_t pt,
+                                                   double* __restrict__ T, int nT, int tail_col,
+                                                   int tail_sn) {
+  const int s = tail_sn + blockIdx.x, b = blockIdx.y;
+  const int m = (int)(d.sn_rowptr[s + 1] - d.sn_rowptr[s]);
+  const int f = d.sn_first[s], w = d.sn_first[s + 1] - f;
+  double* P = Lx + b * pt + d.sn_valoff[s];
+  const int32_t* R = d.sn_rows + d.sn_rowptr[s];
+  double* Tb = T + (int64_t)b * nT * nT;
+  for (int q = threadIdx.x; q < m * w; q += blockDim.x) {
+    const int c = q / m, i = q - c * m;
+    const int row = R[i], col = f + c;
+    if (row < col) continue;  // strictly upper part of the diagonal block: unused
+    double* t = Tb + (int64_t)(row - tail_col) + (int64_t)(col - tail_col) * nT;
+    if (TO_DENSE) *t = P[q];
+    else P[q] = *t;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_dense_tail(Handle& h, cudaStream_t st) {
+  const int nT = h.nT, N = h.N;
+  const int tail_sn = h.sym.tail_sn, tail_col = h.sym.tail_col;
+  const int nsn = h.sym.nsuper - tail_sn;
+  const int64_t pt = h.sym.panel_total, t2 = (int64_t)nT * nT, ys = (int64_t)nT * kPanelW;
+  cudaError_t e = cudaMemsetAsync(h.Tt, 0, sizeof(double) * t2 * N, st);
+  if (e != cudaSuccess) return e;
+  k_tail_move<true><<<dim3(nsn, N), 256, 0, st>>>(h.d, h.Lx, pt, h.Tt, nT, tail_col, tail_sn);
+  h.launches++;
+  if (h.tail_mode == 2) {
+    e = launch_tail_factor_emulated(h, st);
+    if (e != cudaSuccess) return e;
+  }
+  const PivotRule rule{h.anorm, h.opt.pivot_eps, h.d.col_primal + tail_col};
+  for (int k0 = 0; h.tail_mode == 1 && k0 < nT; k0 += kPanelW) {
+    const int kb = std::min(kPanelW, nT - k0);
+    k_dense_diag_t<double><<<N, 256, 0, st>>>(h.Tt, nT, k0, t2, rule, h.counters);
+    h.launches++;
+    const int rest = nT - k0 - kb;
+    if (rest > 0) {
+      launch_dense_panel<double>(h.Tt, h.TY, nT, k0, nT, N, t2, ys, st);
+      const int tiles = (rest + 63) / 64;
+      k_dense_update<<<dim3(tiles * (tiles + 1) / 2, N), 256, 0, st>>>(h.Tt, h.TY, nT, k0, nT, t2, ys);
+      h.launches += 2;
+    }
+  }
+  k_tail_move<false><<<dim3(nsn, N), 256, 0, st>>>(h.d, h.Lx, pt, h.Tt, nT, tail_col, tail_sn);
+  h.launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace kkt

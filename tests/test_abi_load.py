@@ -65,15 +65,19 @@ def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "kkt_schur.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(kkt_pattern), offsetof(kkt_pattern, a_vals_hint),"
         "sizeof(kkt_options), offsetof(kkt_options, reduced_contraction),"
-        "sizeof(kkt_info), offsetof(kkt_info, n_launches));return 0;}\n")
+        "offsetof(kkt_options, dense_tail),"
+        "sizeof(kkt_info), offsetof(kkt_info, n_launches), offsetof(kkt_info, dense_tail_cols));"
+        "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                           check=True).stdout.split()]
     want = [ctypes.sizeof(binding.kkt_pattern), binding.kkt_pattern.a_vals_hint.offset,
             ctypes.sizeof(binding.kkt_options), binding.kkt_options.reduced_contraction.offset,
-            ctypes.sizeof(binding.kkt_info), binding.kkt_info.n_launches.offset]
+            binding.kkt_options.dense_tail.offset,
+            ctypes.sizeof(binding.kkt_info), binding.kkt_info.n_launches.offset,
+            binding.kkt_info.dense_tail_cols.offset]
     assert got == want

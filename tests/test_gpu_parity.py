@@ -149,3 +149,33 @@ def test_full_size_2383_bus_96_periods_backward_error():
     x, info = gpu_solve(p)
     assert [info["n_pos"], info["n_neg"], info["n_zero"]] == expected_inertia(p)
     assert oracle.backward_error(p, x) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["tiny", "grid30_n24", "grid2383_n6"])
+def test_dense_tail_modes(name):
+    """The dense tail factors the top of the tree as one triangle per block
+    (mode 1: FP64 updates; mode 2: emulated-FP64 tensor-core updates); in every
+    mode the solution meets the oracle's criteria and the pivot signs
+    (inertia) are the expected ones."""
+    spec = (replace(CONFIGS["grid2383_n96"], n_per=6, name="grid2383_n6") if name == "grid2383_n6"
+            else CONFIGS[name])
+    p = make_problem(spec)
+    kappa = np.linalg.cond(dense_K(p)) if p.nK <= 4000 else None
+    for mode in (0, 1, 2):
+        x, info = gpu_solve(p, dense_tail=mode)
+        assert (info["dense_tail_cols"] > 0) == (mode > 0)
+        check_against_oracle(p, x, info, kappa)
+        assert info["n_perturbed"] == 0
+        if name == "grid2383_n6" and mode:
+            assert info["dense_tail_cols"] >= 400
+
+
+@pytest.mark.parametrize("prec", ["tf32", "f64emu"])
+def test_default_tail_in_reduced_modes(prec):
+    """The reduced-precision modes take the emulated tail by default."""
+    p = make_problem(replace(CONFIGS["grid2383_n96"], n_per=6, name="grid2383_n6"))
+    x, info = gpu_solve(p, prec)
+    assert info["dense_tail_cols"] >= 400
+    assert oracle.backward_error(p, x) <= 1e-10
+    _, info64 = gpu_solve(p, "fp64")
+    assert info64["dense_tail_cols"] == 0

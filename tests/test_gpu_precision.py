@@ -57,12 +57,17 @@ def test_reduced_contraction_falls_back_to_fp64_schur(prec):
 
 
 def test_emulated_factor_matches_fp64_factor_solution():
-    """The emulated FP64 update reproduces the FP64 path to near FP64 accuracy."""
+    """The emulated FP64 update of S reproduces the FP64 path to near FP64
+    accuracy (same block factors); with the emulated dense tail of the block
+    factors as well, the backward error stays at the FP64 level."""
     p = make_problem(replace(CONFIGS["grid2383_n96"], n_per=8))
     x64, _ = gpu_solve(p, "fp64")
-    xe, info = gpu_solve(p, "f64emu")
+    xe, info = gpu_solve(p, "f64emu", dense_tail=0)
     assert oracle.backward_error(p, xe) <= 1e-14
     assert np.max(np.abs(xe - x64)) / np.max(np.abs(x64)) <= 1e-6
+    xt, info_t = gpu_solve(p, "f64emu")
+    assert info_t["dense_tail_cols"] > 0
+    assert oracle.backward_error(p, xt) <= 1e-14
 
 
 @pytest.mark.parametrize("prec", ["fp64", "tf32", "f64emu"])

@@ -56,7 +56,7 @@ def analyze(p, hint=True):
     try:
         for name in ("perm partner sn_first sn_rowptr sn_rows sn_valoff sn_parent sn_level a_map "
                      "upd_ptr upd_src upd_r0 upd_r1 upd_reloff upd_rel E e_t wpos sn_wrow s_key "
-                     "panel_rend jlo jhi stats").split():
+                     "panel_rend jlo jhi colcount upd_ntail stats").split():
             n = L.kkt_symbolic_get(h, name.encode(), None)
             assert n >= 0, name
             a = np.zeros(n, dtype=np.int64)
@@ -66,7 +66,7 @@ def analyze(p, hint=True):
         L.kkt_symbolic_destroy(h)
     st = out.pop("stats")
     out.update(n=int(st[0]), nsuper=int(st[1]), nlevels=int(st[2]), panel_total=int(st[3]),
-               nnzL=int(st[4]), k=int(st[5]), nw=int(st[6]))
+               nnzL=int(st[4]), k=int(st[5]), nw=int(st[6]), tail_sn=int(st[7]), tail_col=int(st[8]))
     return out
 
 
@@ -161,6 +161,53 @@ def test_supernode_rows_are_union_of_column_patterns(name):
         got = rows[rp[q]:rp[q + 1]].tolist()
         assert got == sorted(want)
         assert got[:len(cols)] == sorted(cols)
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "grid30_n24", "storage20"])
+def test_column_counts_match_brute_force(name):
+    p, s = _case(name)
+    pat = _fill_pattern(p, s["perm"])
+    assert s["colcount"].tolist() == [len(x) for x in pat]
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_dense_tail_is_the_longest_cheap_suffix(name):
+    """The dense tail: a suffix of the supernodes closed under the parent, whose
+    dense flops nT^3/3 are at most twice the exact sparse flops of its columns;
+    the longest such suffix that fits the memory cap is taken."""
+    p, s = _case(name)
+    first, rp, rows, par = s["sn_first"], s["sn_rowptr"], s["sn_rows"], s["sn_parent"]
+    ns, n, t0, tc = s["nsuper"], p.nA, s["tail_sn"], s["tail_col"]
+    assert tc == (first[t0] if t0 < ns else n)
+    cc = s["colcount"].astype(float)
+    fl = cc * (cc + 3)
+
+    def ok(t):
+        nT = n - first[t]
+        return nT >= 16 and p.N * nT * nT * 8 <= 24 << 30 and nT ** 3 / 3.0 <= 2.0 * fl[first[t]:].sum()
+
+    cands = [t for t in range(ns) if ok(t)]
+    assert t0 == (min(cands) if cands else ns)
+    for q in range(t0, ns):
+        assert rows[rp[q]:rp[q + 1]].min() >= tc        # every row is a tail column
+        assert par[q] == -1 or par[q] >= t0               # closed under the parent
+    # update lists: the updates from outside the tail come first
+    up, src, nt = s["upd_ptr"], s["upd_src"], s["upd_ntail"]
+    for q in range(ns):
+        lst = src[up[q]:up[q + 1]]
+        assert np.all(lst[:nt[q]] < t0) and np.all(lst[nt[q]:] >= t0)
+
+
+def test_dense_tail_present_on_meshed_grids():
+    import dataclasses
+
+    p = make_problem(dataclasses.replace(CONFIGS["grid2383_n96"], n_per=2))
+    s = analyze(p)
+    nT = p.nA - s["tail_col"]
+    cc = s["colcount"].astype(float)
+    fl = cc * (cc + 3)
+    assert 400 <= nT <= 2000
+    assert fl[s["tail_col"]:].sum() >= 0.8 * fl.sum()   # the tail holds most of the work
 
 
 @pytest.mark.parametrize("name", list(PROBLEMS))
