@@ -142,7 +142,8 @@ typedef struct {
   double ms_solve_device;       /* device time of the last kkt_solve, refinement included */
   int64_t n_launches;           /* kernels launched by this handle since kkt_analyze */
   int32_t dense_tail_cols;      /* columns of the dense tail of each block factor (0 = none) */
-  int32_t reserved_info;
+  int32_t tail_augmented;       /* 1 if the tail factor also forms the tail's rows of W and its
+                                   share of G (the k coupling rows appended to it) */
 } kkt_info;
 
 /* Default options: FP64, refine_tol 1e-10, max_refine 10, pivot_eps 1e-20,

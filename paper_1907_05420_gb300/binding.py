@@ -54,7 +54,7 @@ class kkt_info(C.Structure):
                 ("factor_flops", C.c_double), ("device_bytes", C.c_int64),
                 ("ms_block_factor", C.c_double), ("ms_schur_assembly", C.c_double),
                 ("ms_dense_factor", C.c_double), ("ms_solve_device", C.c_double),
-                ("n_launches", C.c_int64), ("dense_tail_cols", C.c_int32), ("reserved_info", C.c_int32)]
+                ("n_launches", C.c_int64), ("dense_tail_cols", C.c_int32), ("tail_augmented", C.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

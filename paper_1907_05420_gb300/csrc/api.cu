@@ -49,7 +49,7 @@ void free_all(Handle* h) {
                   h->d.b_blockptr, h->d.e_t, h->d.e_block, h->d.wpos, h->d.sn_wrow, h->d.w_dpos,
                   h->d.w_col, h->d.reach_lvl_sn, h->d.s_key, h->d.s_ptr, h->d.s_e1, h->d.s_e2,
                   h->d.t_ptr, h->d.t_e, h->d.bt_ptr, h->d.E, h->d.g_rows, h->d.trsv_jlo, h->d.trsv_jhi,
-                  h->d.flvl_sn, h->d.twork, h->d.upd_ntail, h->Tt, h->TY, h->t_imgA, h->t_imgB,
+                  h->d.flvl_sn, h->d.twork, h->d.upd_ntail, h->d.reach_lvl_sn_nt, h->d.tail_sn_list, h->d.tail_wrow, h->Tt, h->TY, h->t_imgA, h->t_imgB,
                   h->t_scaleA, h->t_scaleB, h->Lx, h->a_vals, h->b_vals,
                   h->c_vals, h->anorm, h->W, h->G, h->S, h->Ypanel, h->knorm, h->counters, h->r,
                   h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red,
@@ -155,10 +155,30 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   const int32_t n = S.n;
   h->nT = n - S.tail_col;
   if (h->nT == 0) h->tail_mode = 0;
+  // Augmented tail: the k coupling rows are appended to each tail triangle, and
+  // its factorization also yields W's tail rows and the tail's share of G
+  // (Sec. 4.2, the incomplete factorization of the augmented matrix); the tail's
+  // W rows (those of its supernodes in the reach of E) come after all others.
+  std::vector<int32_t> tail_wrow;
+  h->nw_nt = tail_w_rows(S, C, tail_wrow);
+  h->tail_aug = h->tail_mode != 0 && h->nT > 0 && C.k > 0;
+  if (!h->tail_aug) h->nw_nt = C.nw;
+  h->nTa = h->nT + (h->tail_aug ? C.k : 0);
   h->nnzA = pat->a_rowptr[n];
   h->nnzB = nnzB;
   h->lvl_ptr = S.lvl_ptr;
   h->reach_lvl_ptr = C.reach_lvl_ptr;
+  // reach supernodes outside the tail, by level (the W solve before the tail)
+  std::vector<int32_t> reach_lvl_sn_nt, tail_sn_list;
+  h->reach_lvl_ptr_nt.assign(S.nlevels + 1, 0);
+  for (int l = 0; l < S.nlevels; l++) {
+    for (int q = C.reach_lvl_ptr[l]; q < C.reach_lvl_ptr[l + 1]; q++)
+      if (C.reach_lvl_sn[q] < S.tail_sn) reach_lvl_sn_nt.push_back(C.reach_lvl_sn[q]);
+    h->reach_lvl_ptr_nt[l + 1] = (int32_t)reach_lvl_sn_nt.size();
+  }
+  for (int s = S.tail_sn; s < S.nsuper; s++)
+    if (C.sn_wrow[s] >= 0) tail_sn_list.push_back(s);  // tail supernodes in the reach of E
+  h->tail_reach_sn = (int32_t)tail_sn_list.size();
 
   // factor work items: 64-row tiles of every supernode outside the dense tail,
   // grouped by level, then those of the tail supernodes; for every (tile,
@@ -221,7 +241,9 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   std::vector<int32_t> g_rows;
   {
     std::vector<int32_t> pos_rows, neg_rows;
-    for (int r = 0; r < C.nw; r++) (col_primal[w_col[r]] ? pos_rows : neg_rows).push_back(r);
+    // with the augmented tail, the tail rows' share of G comes from the tail factor
+    const int nw_contract = h->nw_nt;
+    for (int r = 0; r < nw_contract; r++) (col_primal[w_col[r]] ? pos_rows : neg_rows).push_back(r);
     auto pad = [](std::vector<int32_t>& v) {
       while (v.size() % 64) v.push_back(-1);
     };
@@ -300,6 +322,9 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   UP(w_dpos, w_dpos);
   UP(w_col, w_col);
   UP(reach_lvl_sn, C.reach_lvl_sn);
+  UP(reach_lvl_sn_nt, reach_lvl_sn_nt);
+  UP(tail_sn_list, tail_sn_list);
+  UP(tail_wrow, tail_wrow);
   UP(s_key, C.s_key);
   UP(s_ptr, C.s_ptr);
   UP(s_e1, C.s_e1);
@@ -328,16 +353,16 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   AL(S, double, (int64_t)h->nC * h->nC);
   AL(Ypanel, double, (int64_t)h->nC * kDenseNB);
   if (h->nT > 0) {
-    AL(Tt, double, (int64_t)h->nT * h->nT * h->N);
-    AL(TY, double, (int64_t)h->nT * kDenseNB * h->N);
+    AL(Tt, double, (int64_t)h->nTa * h->nTa * h->N);
+    AL(TY, double, (int64_t)h->nTa * kDenseNB * h->N);
   }
   if (h->tail_mode == 2) {
-    const int64_t ia = tc_image_bytes_a(h->nT, KKT_F64_EMULATED);
-    const int64_t ib = tc_image_bytes(h->nT, KKT_F64_EMULATED) - ia;
+    const int64_t ia = tc_image_bytes_a(h->nTa, KKT_F64_EMULATED);
+    const int64_t ib = tc_image_bytes(h->nTa, KKT_F64_EMULATED) - ia;
     AL(t_imgA, uint8_t, ia * h->N);
     AL(t_imgB, uint8_t, ib * h->N);
-    AL(t_scaleA, double, ((int64_t)h->nT + 256) * h->N);
-    AL(t_scaleB, double, ((int64_t)h->nT + 256) * h->N);
+    AL(t_scaleA, double, ((int64_t)h->nTa + 256) * h->N);
+    AL(t_scaleB, double, ((int64_t)h->nTa + 256) * h->N);
   }
   AL(knorm, double, 1);
   AL(counters, unsigned long long, 2 * kNumCounters);  // second half: discarded counts
@@ -553,6 +578,7 @@ kkt_status kkt_get_info(kkt_handle* hh, kkt_info* info) {
   h->info.device_bytes = h->device_bytes;
   h->info.n_launches = h->launches;
   h->info.dense_tail_cols = h->nT;
+  h->info.tail_augmented = h->tail_aug ? 1 : 0;
   *info = h->info;
   return KKT_OK;
 }

@@ -227,12 +227,12 @@ cudaError_t launch_dense_ldlt(Handle& h, unsigned long long* counters, cudaStrea
     const int kb = std::min(NB, n - k0);
     const int rend = h.panel_rend.empty() ? n : h.panel_rend[k0 / NB];
     // diagonal block (rows in registers) and panel (warp per row), FP64
-    cudaError_t e = launch_dense_diag_panel_f64(h, k0, rend, counters, st);
+    cudaError_t e = launch_dense_diag_panel_f64(h, k0, kb, rend, counters, st);
     if (e != cudaSuccess) return e;
     const int rest = rend - k0 - kb;
     if (rest > 0) {
       const int T = (rest + 63) / 64;
-      k_dense_update<<<T * (T + 1) / 2, 256, 0, st>>>(h.S, h.Ypanel, n, k0, rend, 0, 0);
+      k_dense_update<<<T * (T + 1) / 2, 256, 0, st>>>(h.S, h.Ypanel, n, k0, kb, rend, 0, 0);
       h.launches++;
     }
   }

@@ -2,7 +2,10 @@
 // kDenseNB = 64), shared by the factor of the Schur complement S (one matrix)
 // and by the dense tail of the block factors (one matrix per block, batched
 // over blockIdx with a stride).  Matrices are column-major with leading
-// dimension n; only the lower triangle is read or written.  Per panel k0:
+// dimension n; only the lower triangle is read or written.  A panel k0 has
+// kb pivot columns (kb < 64 for a last ragged panel; the rows below the
+// pivots may extend past the last pivot column: the tail's augmented rows).
+// Per panel:
 //   k_dense_diag_t:   LDL^T of the kb x kb diagonal block;
 //   k_dense_panel_t:  L21 = A21 L11^{-T} D1^{-1} and Y = L21 D1 (rows below);
 //   k_dense_update:   A22 -= Y L21^T on the lower 64 x 64 tiles (FP64).
@@ -54,8 +57,8 @@ __device__ __forceinline__ void diag_pair(int p, int& i, int& j) {
 constexpr int kSub = 16;
 
 template <class T>
-__global__ void __launch_bounds__(256) k_dense_diag_t(T* __restrict__ S0, int n, int k0, int64_t bstride,
-                                                      PivotRule rule,
+__global__ void __launch_bounds__(256) k_dense_diag_t(T* __restrict__ S0, int n, int k0, int kb,
+                                                      int64_t bstride, PivotRule rule,
                                                       unsigned long long* __restrict__ counters) {
   __shared__ T A[kPanelW][kPanelW + 1];
   __shared__ T Ys[kPanelW][kSub + 1];
@@ -64,7 +67,6 @@ __global__ void __launch_bounds__(256) k_dense_diag_t(T* __restrict__ S0, int n,
   __shared__ int pert;
   T* S = S0 + (int64_t)blockIdx.x * bstride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int kb = min(kPanelW, n - k0);
   for (int q = tid; q < kb * kb; q += blockDim.x) {
     const int c = q / kb, r = q - c * kb;
     if (r >= c) A[r][c] = S[(int64_t)(k0 + r) + (int64_t)(k0 + c) * n];
@@ -169,13 +171,12 @@ __global__ void __launch_bounds__(256) k_dense_diag_t(T* __restrict__ S0, int n,
 // L21 = y D1^{-1}.  Y has the matrix's leading dimension n and its rows.
 template <class T, int ROWS>
 __global__ void __launch_bounds__(ROWS) k_dense_panel_t(T* __restrict__ S0, T* __restrict__ Y0, int n,
-                                                        int k0, int rend, int64_t bstride,
+                                                        int k0, int kb, int rend, int64_t bstride,
                                                         int64_t ystride) {
   __shared__ T L11[kPanelW][kPanelW];  // [j][c], zero outside the strict lower triangle
   __shared__ T dinv[kPanelW];
   T* S = S0 + (int64_t)blockIdx.y * bstride;
   T* Y = Y0 + (int64_t)blockIdx.y * ystride;
-  const int kb = min(kPanelW, n - k0);
   for (int q = threadIdx.x; q < kPanelW * kPanelW; q += blockDim.x) {
     const int c = q / kPanelW, j = q - c * kPanelW;
     L11[j][c] = (j > c && j < kb) ? S[(int64_t)(k0 + j) + (int64_t)(k0 + c) * n] : T(0);
@@ -210,12 +211,11 @@ __global__ void __launch_bounds__(ROWS) k_dense_panel_t(T* __restrict__ S0, T* _
 // for few rows (and in FP64, whose dependent multiply-add latency is long).
 template <class T>
 __global__ void __launch_bounds__(256) k_dense_panel_w(T* __restrict__ S0, T* __restrict__ Y0, int n, int k0,
-                                                       int rend, int64_t bstride, int64_t ystride) {
+                                                       int kb, int rend, int64_t bstride, int64_t ystride) {
   __shared__ T L11[kPanelW][kPanelW + 1];
   __shared__ T dinv[kPanelW];
   T* S = S0 + (int64_t)blockIdx.y * bstride;
   T* Y = Y0 + (int64_t)blockIdx.y * ystride;
-  const int kb = min(kPanelW, n - k0);
   for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
     const int j = q / kb, i = q - j * kb;
     L11[i][j] = S[(int64_t)(k0 + i) + (int64_t)(k0 + j) * n];
@@ -242,30 +242,38 @@ __global__ void __launch_bounds__(256) k_dense_panel_w(T* __restrict__ S0, T* __
   }
 }
 
-// Rows below the diagonal block of nb matrices: FP32 with many rows takes a
-// thread per row, everything else a warp per row.
+// Rows below the diagonal block of nb matrices.  A thread per row issues the
+// fewest instructions (no idle lanes) but its dependency chain is long; a
+// warp per row has a 64-step chain.  FP32 takes a thread per row from 2048
+// rows on.  In FP64 a warp issues one multiply-add per 64 cycles, so a thread
+// per row pays off once there are enough rows (m * nb >= 32768, over 1000
+// warps) to keep every sub-partition's FP64 pipe busy.
 template <class T>
-inline void launch_dense_panel(T* S, T* Y, int n, int k0, int rend, int nb, int64_t bstride, int64_t ystride,
-                               cudaStream_t st) {
-  const int m = rend - k0 - min(kPanelW, n - k0);
+inline void launch_dense_panel(T* S, T* Y, int n, int k0, int kb, int rend, int nb, int64_t bstride,
+                               int64_t ystride, cudaStream_t st) {
+  const int m = rend - k0 - kb;
   if (m <= 0) return;
   if constexpr (sizeof(T) == 4) {
     if (m > 2048) {
-      k_dense_panel_t<T, 128><<<dim3((m + 127) / 128, nb), 128, 0, st>>>(S, Y, n, k0, rend, bstride, ystride);
+      k_dense_panel_t<T, 128><<<dim3((m + 127) / 128, nb), 128, 0, st>>>(S, Y, n, k0, kb, rend, bstride, ystride);
+      return;
+    }
+  } else {
+    if ((int64_t)m * nb >= 32768) {
+      k_dense_panel_t<T, 32><<<dim3((m + 31) / 32, nb), 32, 0, st>>>(S, Y, n, k0, kb, rend, bstride, ystride);
       return;
     }
   }
-  k_dense_panel_w<T><<<dim3((m + 7) / 8, nb), 256, 0, st>>>(S, Y, n, k0, rend, bstride, ystride);
+  k_dense_panel_w<T><<<dim3((m + 7) / 8, nb), 256, 0, st>>>(S, Y, n, k0, kb, rend, bstride, ystride);
 }
 
 // Trailing update of matrix blockIdx.y on the lower 64 x 64 tiles below the
 // panel: A[i][j] -= sum_c Y[i][c] L[j][c] for k0+kb <= j <= i < rend.
 __global__ void __launch_bounds__(256) k_dense_update(double* __restrict__ S0, const double* __restrict__ Y0,
-                                                      int n, int k0, int rend, int64_t bstride,
+                                                      int n, int k0, int kb, int rend, int64_t bstride,
                                                       int64_t ystride) {
   double* S = S0 + (int64_t)blockIdx.y * bstride;
   const double* Y = Y0 + (int64_t)blockIdx.y * ystride;
-  const int kb = min(kPanelW, n - k0);
   const int base = k0 + kb;
   int tile = blockIdx.x, ti = 0;
   while (tile > ti) {

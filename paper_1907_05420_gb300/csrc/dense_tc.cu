@@ -121,7 +121,7 @@ struct TcStrides {
 
 template <int MODE, class T>
 __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S0, const T* __restrict__ Y0,
-                                                  int n, int k0, int m, uint8_t* __restrict__ imgA0,
+                                                  int n, int k0, int kb, int m, uint8_t* __restrict__ imgA0,
                                                   uint8_t* __restrict__ imgB0, double* __restrict__ scaleA0,
                                                   double* __restrict__ scaleB0, int mpadA, int mpadB,
                                                   TcStrides ts) {
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S0, cons
   constexpr ModeCfg cfg = mode_cfg(MODE);
   constexpr int KG = kgroups_of(MODE);
   constexpr int kpc = 16 / cfg.esz;  // elements per 16-byte core row
-  const int base = k0 + TK;
+  const int base = k0 + kb;
   const int total = mpadA + mpadB;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
     const bool isA = q < mpadA;
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S0, cons
     if (MODE == 2) {
       double amax = 0.0;
       if (live)
-        for (int c = 0; c < TK; c++) amax = fmax(amax, fabs((double)src[(int64_t)(base + rho) + (col0 + c) * n]));
+        for (int c = 0; c < kb; c++) amax = fmax(amax, fabs((double)src[(int64_t)(base + rho) + (col0 + c) * n]));
       e_exp = amax > 0.0 ? ilogb(amax) + 1 : 0;  // |v| < 2^e
       e_scale = ldexp(1.0, e_exp);
       if (isA) scaleA[rho] = e_scale;
@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S0, cons
         float dig[kpc][kEmuSlices];
 #pragma unroll
         for (int e = 0; e < kpc; e++) {
-          double v = live ? (double)src[(int64_t)(base + rho) + (col0 + kq * kpc + e) * n] : 0.0;
+          const int c = kq * kpc + e;  // columns >= kb (a ragged panel) are zero
+          double v = (live && c < kb) ? (double)src[(int64_t)(base + rho) + (col0 + c) * n] : 0.0;
           digits7(v, e_exp, dig[e]);
         }
 #pragma unroll
@@ -179,12 +180,15 @@ __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S0, cons
         __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
         for (int e = 0; e < 8; e++)
-          h[e] = __float2bfloat16_rn(live ? (float)src[(int64_t)(base + rho) + (col0 + kq * kpc + e) * n] : 0.f);
+          h[e] = __float2bfloat16_rn((live && kq * kpc + e < kb)
+                                         ? (float)src[(int64_t)(base + rho) + (col0 + kq * kpc + e) * n]
+                                         : 0.f);
         *reinterpret_cast<uint4*>(blk_img + (g * KG + kq) * 128 + r8 * 16) = *reinterpret_cast<const uint4*>(h);
       } else {
         __align__(16) float f[4];
 #pragma unroll
-        for (int e = 0; e < 4; e++) f[e] = live ? (float)src[(int64_t)(base + rho) + (col0 + kq * kpc + e) * n] : 0.f;
+        for (int e = 0; e < 4; e++)
+          f[e] = (live && kq * kpc + e < kb) ? (float)src[(int64_t)(base + rho) + (col0 + kq * kpc + e) * n] : 0.f;
         *reinterpret_cast<uint4*>(blk_img + (g * KG + kq) * 128 + r8 * 16) = *reinterpret_cast<const uint4*>(f);
       }
     }
@@ -206,7 +210,7 @@ __device__ __forceinline__ void tile_of(int t, int TJ, int& I, int& J) {
 }
 
 template <int MODE, class T>
-__global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n, int k0, int m, int TJ,
+__global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n, int k0, int kb, int m, int TJ,
                                                       const uint8_t* __restrict__ imgA0,
                                                       const uint8_t* __restrict__ imgB0,
                                                       const double* __restrict__ scaleA0,
@@ -234,7 +238,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int I, J;
   tile_of(blockIdx.x, TJ, I, J);
-  const int base = k0 + TK;
+  const int base = k0 + kb;
 
   if (tid == 0) {
     s_ok = 1;
@@ -411,32 +415,31 @@ __global__ void k_dense_diag_scale_f(const float* __restrict__ S, double* __rest
 // diagonal block and panel on the CUDA cores, trailing update on the tensor
 // cores.  rend: per 64-wide panel, one past its last nonzero row (or null).
 template <int MODE, class T>
-cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int nb, const TcStrides& ts, const PivotRule& rule,
+cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int npiv, int nb, const TcStrides& ts, const PivotRule& rule,
                       const int32_t* rend_of_panel, unsigned long long* counters, uint8_t* imgA,
                       uint8_t* imgB, double* scaleA, double* scaleB, cudaStream_t st) {
   constexpr int A_BYTES = image_bytes(MODE, TM), B_BYTES = image_bytes(MODE, TN);
   const int smem = A_BYTES + B_BYTES;
   cudaError_t e = cudaFuncSetAttribute(k_tc_update<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  for (int k0 = 0; k0 < n; k0 += TK) {
-    const int kb = std::min(TK, n - k0);
-    k_dense_diag_t<T><<<nb, 256, 0, st>>>(S, n, k0, ts.s, rule, counters);
+  for (int k0 = 0; k0 < npiv; k0 += TK) {
+    const int kb = std::min(TK, npiv - k0);
+    k_dense_diag_t<T><<<nb, 256, 0, st>>>(S, n, k0, kb, ts.s, rule, counters);
     h.launches++;
     // rows below the envelope of the panel's columns stay zero (no pivoting)
     const int rend = rend_of_panel ? rend_of_panel[k0 / TK] : n;
     const int m = rend - k0 - kb;
     if (m <= 0) continue;
-    launch_dense_panel<T>(S, Y, n, k0, rend, nb, ts.s, ts.y, st);
+    launch_dense_panel<T>(S, Y, n, k0, kb, rend, nb, ts.s, ts.y, st);
     h.launches++;
-    if (kb < TK) continue;  // a ragged last panel leaves no trailing matrix
     const int TI = (m + TM - 1) / TM, TJ = (m + TN - 1) / TN;
     const int mpadA = TI * TM, mpadB = TJ * TN;
     const int sgrid = std::max(1, std::min((mpadA + mpadB + 255) / 256, 152 * 8 / nb));
-    k_tc_slice<MODE, T><<<dim3(sgrid, nb), 256, 0, st>>>(S, Y, n, k0, m, imgA, imgB, scaleA, scaleB, mpadA,
+    k_tc_slice<MODE, T><<<dim3(sgrid, nb), 256, 0, st>>>(S, Y, n, k0, kb, m, imgA, imgB, scaleA, scaleB, mpadA,
                                                          mpadB, ts);
     int tiles = 0;
     for (int I = 0; I < TI; I++) tiles += std::min(2 * I + 2, TJ);
-    k_tc_update<MODE, T><<<dim3(tiles, nb), 128, smem, st>>>(S, n, k0, m, TJ, imgA, imgB, scaleA, scaleB,
+    k_tc_update<MODE, T><<<dim3(tiles, nb), 128, smem, st>>>(S, n, k0, kb, m, TJ, imgA, imgB, scaleA, scaleB,
                                                              h.dev_err, ts);
     h.launches += 2;
   }
@@ -468,44 +471,42 @@ cudaError_t launch_dense_ldlt_tc(Handle& h, int mode, unsigned long long* counte
   const int32_t* rend = h.panel_rend.empty() ? nullptr : h.panel_rend.data();
   const TcStrides one{};
   if (mode == KKT_F64_EMULATED)
-    return factor_tc<2, double>(h, h.S, h.Ypanel, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
+    return factor_tc<2, double>(h, h.S, h.Ypanel, n, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
                                 h.tc_scaleA, h.tc_scaleB, st);
   const int64_t n2 = (int64_t)n * n;
   k_to_f32<<<(int)std::min<int64_t>((n2 + 255) / 256, 152 * 32), 256, 0, st>>>(h.S, h.S32, n2);
   h.launches++;
   if (mode == KKT_TF32)
-    return factor_tc<0, float>(h, h.S32, h.Y32, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
+    return factor_tc<0, float>(h, h.S32, h.Y32, n, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
                                h.tc_scaleA, h.tc_scaleB, st);
-  return factor_tc<1, float>(h, h.S32, h.Y32, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
+  return factor_tc<1, float>(h, h.S32, h.Y32, n, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
                              h.tc_scaleA, h.tc_scaleB, st);
 }
 
 // The dense tails of the N block factors in emulated FP64: the batched
 // blocked LDL^T above with the static-pivot rule of the block factors.
 cudaError_t launch_tail_factor_emulated(Handle& h, cudaStream_t st) {
-  const int nT = h.nT;
+  const int nTa = h.nTa;
   TcStrides ts;
-  ts.s = (int64_t)nT * nT;
-  ts.y = (int64_t)nT * TK;
-  ts.img_a = tc_image_bytes_a(nT, KKT_F64_EMULATED);
-  ts.img_b = tc_image_bytes(nT, KKT_F64_EMULATED) - ts.img_a;
-  ts.scale = (int64_t)nT + 256;
+  ts.s = (int64_t)nTa * nTa;
+  ts.y = (int64_t)nTa * TK;
+  ts.img_a = tc_image_bytes_a(nTa, KKT_F64_EMULATED);
+  ts.img_b = tc_image_bytes(nTa, KKT_F64_EMULATED) - ts.img_a;
+  ts.scale = (int64_t)nTa + 256;
   const PivotRule rule{h.anorm, h.opt.pivot_eps, h.d.col_primal + h.sym.tail_col};
-  return factor_tc<2, double>(h, h.Tt, h.TY, nT, h.N, ts, rule, nullptr, h.counters, h.t_imgA, h.t_imgB,
-                              h.t_scaleA, h.t_scaleB, st);
+  return factor_tc<2, double>(h, h.Tt, h.TY, nTa, h.nT, h.N, ts, rule, nullptr, h.counters, h.t_imgA,
+                              h.t_imgB, h.t_scaleA, h.t_scaleB, st);
 }
 
 // Diagonal block and panel of one 64-wide step of the FP64 factor (shared by
 // the FP64 path, whose trailing update runs on the CUDA cores).
-cudaError_t launch_dense_diag_panel_f64(Handle& h, int k0, int rend, unsigned long long* counters,
+cudaError_t launch_dense_diag_panel_f64(Handle& h, int k0, int kb, int rend, unsigned long long* counters,
                                         cudaStream_t st) {
   const int n = h.nC;
-  const int kb = std::min(TK, n - k0);
-  k_dense_diag_t<double><<<1, 256, 0, st>>>(h.S, n, k0, 0, PivotRule{}, counters);
+  k_dense_diag_t<double><<<1, 256, 0, st>>>(h.S, n, k0, kb, 0, PivotRule{}, counters);
   h.launches++;
-  const int m = rend - k0 - kb;
-  if (m > 0) {
-    launch_dense_panel<double>(h.S, h.Ypanel, n, k0, rend, 1, 0, 0, st);
+  if (rend - k0 - kb > 0) {
+    launch_dense_panel<double>(h.S, h.Ypanel, n, k0, kb, rend, 1, 0, 0, st);
     h.launches++;
   }
   return cudaGetLastError();

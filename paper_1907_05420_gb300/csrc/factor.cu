@@ -208,7 +208,12 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
   }
   if (h.nT > 0) {
     // updates of the tail from the rest of the tree (all factored by now), then
-    // the dense factor of the tail
+    // the dense factor of the tail; an augmented tail first takes the W rows
+    // outside the tail and its own rows Z
+    if (h.tail_aug) {
+      cudaError_t e = launch_w_solve_before_tail(h, st);
+      if (e != cudaSuccess) return e;
+    }
     if (h.tail_items > 0) {
       dim3 grid(h.tail_items, h.N);
       k_factor_update<true><<<grid, 256, 0, st>>>(h.d.twork, h.d.frange, h.d, h.Lx, pt);

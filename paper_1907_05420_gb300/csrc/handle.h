@@ -72,6 +72,9 @@ struct DevSym {
   int32_t* flvl_sn = nullptr;      // supernodes outside the dense tail, by level (block factor)
   int32_t* twork = nullptr;        // factor work items of the dense-tail supernodes
   int32_t* upd_ntail = nullptr;    // per supernode: leading updates from outside the tail
+  int32_t* reach_lvl_sn_nt = nullptr;  // reach supernodes outside the tail, by level
+  int32_t* tail_sn_list = nullptr;     // the tail supernodes in the reach of E
+  int32_t* tail_wrow = nullptr;        // per tail column: its W row (-1 outside the reach)
 };
 
 // Counters written by the kernels (device, int64).
@@ -92,6 +95,11 @@ struct Handle {
   std::vector<int32_t> panel_rend;     // structured mode: per 64-wide panel, one past its last nonzero row
   std::vector<int32_t> flvl_ptr;       // supernodes outside the dense tail per level (factor)
   int32_t nT = 0;                      // columns of the dense tail (0 = none)
+  int32_t nTa = 0;                     // order of the tail matrices: nT, plus k augmented rows
+  bool tail_aug = false;               // tail augmented by the k coupling rows (Sec. 4.2)
+  int32_t nw_nt = 0;                   // W rows outside the tail (the first ones)
+  int32_t tail_reach_sn = 0;           // tail supernodes in the reach of E
+  std::vector<int32_t> reach_lvl_ptr_nt;  // reach supernodes outside the tail per level
   int32_t tail_items = 0;              // factor work items of the tail supernodes
 
   // numeric buffers
@@ -162,6 +170,8 @@ cudaError_t launch_dense_tail(Handle& h, cudaStream_t st);
 cudaError_t launch_tail_factor_emulated(Handle& h, cudaStream_t st);  // (dense_tc.cu)
 // ---- (schur.cu) ----
 cudaError_t launch_w_solve(Handle& h, cudaStream_t st);
+cudaError_t launch_w_solve_before_tail(Handle& h, cudaStream_t st);
+cudaError_t launch_add_tail_g(Handle& h, cudaStream_t st);
 cudaError_t launch_contract_g(Handle& h, cudaStream_t st);
 cudaError_t launch_assemble_s(Handle& h, cudaStream_t st);
 // ---- (schur_tc.cu) ----
@@ -174,7 +184,7 @@ cudaError_t launch_dense_solve_f32(Handle& h, const double* t, double* x, cudaSt
 // ---- (dense_tc.cu) ----
 cudaError_t launch_dense_ldlt_tc(Handle& h, int mode, unsigned long long* counters, cudaStream_t st);
 int64_t tc_image_bytes_a(int n, int mode);
-cudaError_t launch_dense_diag_panel_f64(Handle& h, int k0, int rend, unsigned long long* counters,
+cudaError_t launch_dense_diag_panel_f64(Handle& h, int k0, int kb, int rend, unsigned long long* counters,
                                         cudaStream_t st);
 int64_t tc_image_bytes(int n, int mode);
 // ---- (solve.cu) ----

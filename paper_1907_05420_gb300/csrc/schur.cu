@@ -20,9 +20,12 @@ namespace {
 
 // One CTA per (reach supernode, block, chunk of 32 right-hand sides): the
 // columns of W are independent, so chunks spread the narrow top levels of the
-// tree over more SMs.
+// tree over more SMs.  TAIL_INIT: for a supernode of the augmented tail, only
+// the right-hand side minus the updates from outside the tail (the rows Z the
+// tail factor is augmented with); its triangular solve is the tail factor's.
 constexpr int kWChunk = 32;
 
+template <bool TAIL_INIT>
 __global__ void __launch_bounds__(128) k_w_solve(const int32_t* __restrict__ sn_list, DevSym d,
                                                  const double* __restrict__ Lx, int64_t pt,
                                                  double* __restrict__ W, int nw, int k) {
@@ -38,7 +41,8 @@ __global__ void __launch_bounds__(128) k_w_solve(const int32_t* __restrict__ sn_
     Wb[(int64_t)(ws + c) * k + t] = d.wpos[t0 + t] == ws + c ? 1.0 : 0.0;
   }
   __syncthreads();
-  for (int64_t u = d.upd_ptr[s]; u < d.upd_ptr[s + 1]; u++) {
+  const int64_t u_end = TAIL_INIT ? d.upd_ptr[s] + d.upd_ntail[s] : d.upd_ptr[s + 1];
+  for (int64_t u = d.upd_ptr[s]; u < u_end; u++) {
     const int dd = d.upd_src[u];
     const int wrd = d.sn_wrow[dd];
     if (wrd < 0) continue;  // descendant outside the reach: its W rows are zero
@@ -56,6 +60,7 @@ __global__ void __launch_bounds__(128) k_w_solve(const int32_t* __restrict__ sn_
     }
     __syncthreads();
   }
+  if (TAIL_INIT) return;
   for (int c = 0; c + 1 < w; c++) {
     const int total = (w - 1 - c) * nt;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
@@ -67,9 +72,10 @@ __global__ void __launch_bounds__(128) k_w_solve(const int32_t* __restrict__ sn_
 }
 
 // G_b = W_b^T D_b^{-1} W_b in FP64, one 32x32 tile of the lower triangle per CTA
+// (the first nrows rows of W; nw is its row count per block)
 __global__ void __launch_bounds__(256) k_contract_g_f64(const double* __restrict__ W,
                                                         const double* __restrict__ Lx, int64_t pt,
-                                                        const int64_t* __restrict__ w_dpos, int nw,
+                                                        const int64_t* __restrict__ w_dpos, int nw, int nrows,
                                                         int k, double* __restrict__ G) {
   const int b = blockIdx.y;
   // tile index -> (ti, tj) with ti >= tj
@@ -85,12 +91,12 @@ __global__ void __launch_bounds__(256) k_contract_g_f64(const double* __restrict
   const double* Pb = Lx + b * pt;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   double acc[4] = {0, 0, 0, 0};
-  for (int r0 = 0; r0 < nw; r0 += 32) {
+  for (int r0 = 0; r0 < nrows; r0 += 32) {
     for (int q = threadIdx.x; q < 32 * 32; q += 256) {
       const int rr = q >> 5, cc = q & 31;
       const int row = r0 + rr;
       double a = 0.0, bb = 0.0;
-      if (row < nw) {
+      if (row < nrows) {
         const double dinv = 1.0 / Pb[w_dpos[row]];
         if (t1_0 + cc < k) a = Wblk[(int64_t)row * k + t1_0 + cc] * dinv;
         if (t2_0 + cc < k) bb = Wblk[(int64_t)row * k + t2_0 + cc];
@@ -114,6 +120,19 @@ __global__ void __launch_bounds__(256) k_contract_g_f64(const double* __restrict
       Gb[(int64_t)t1 * k + t2] = acc[i];
       if (ti != tj) Gb[(int64_t)t2 * k + t1] = acc[i];
     }
+  }
+}
+
+// G_b -= T_b[nT:, nT:]: after the nT pivots of the augmented tail its trailing
+// k x k block holds -W_T^T D_T^{-1} W_T (lower triangle), the tail rows' share of G.
+__global__ void k_add_tail_g(const double* __restrict__ Ta, int nT, int nTa, int k, double* __restrict__ G) {
+  const int b = blockIdx.y;
+  const double* Tb = Ta + (int64_t)b * nTa * nTa;
+  double* Gb = G + (int64_t)b * k * k;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < k * k; q += gridDim.x * blockDim.x) {
+    const int t1 = q / k, t2 = q - t1 * k;
+    const int hi = max(t1, t2), lo = min(t1, t2);
+    Gb[q] -= Tb[(int64_t)(nT + hi) + (int64_t)(nT + lo) * nTa];
   }
 }
 
@@ -153,33 +172,68 @@ __global__ void k_assemble_s(const int64_t* __restrict__ s_key, const int64_t* _
 
 }  // namespace
 
-cudaError_t launch_w_solve(Handle& h, cudaStream_t st) {
+namespace {
+
+cudaError_t w_levels(Handle& h, const std::vector<int32_t>& lvl_ptr, const int32_t* lvl_sn, cudaStream_t st) {
   const int k = h.cpl.k;
-  if (k == 0 || h.cpl.nw == 0) return cudaSuccess;
   for (int l = 0; l < h.sym.nlevels; l++) {
-    const int s0 = h.reach_lvl_ptr[l], s1 = h.reach_lvl_ptr[l + 1];
+    const int s0 = lvl_ptr[l], s1 = lvl_ptr[l + 1];
     if (s1 == s0) continue;
     dim3 grid(s1 - s0, h.N, (k + kWChunk - 1) / kWChunk);
-    {
-    k_w_solve<<<grid, 128, 0, st>>>(h.d.reach_lvl_sn + s0, h.d, h.Lx, h.sym.panel_total, h.W,
-                                    h.cpl.nw, k);
+    k_w_solve<false><<<grid, 128, 0, st>>>(lvl_sn + s0, h.d, h.Lx, h.sym.panel_total, h.W, h.cpl.nw, k);
     h.launches++;
   }
-  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_w_solve(Handle& h, cudaStream_t st) {
+  const int k = h.cpl.k;
+  if (k == 0 || h.cpl.nw == 0 || h.tail_aug) return cudaSuccess;  // augmented: done before the tail
+  return w_levels(h, h.reach_lvl_ptr, h.d.reach_lvl_sn, st);
+}
+
+// Augmented tail: the W rows outside the tail, then the tail's rows Z (the
+// right-hand side minus the updates from outside the tail), before the tail
+// factor that completes them.
+cudaError_t launch_w_solve_before_tail(Handle& h, cudaStream_t st) {
+  const int k = h.cpl.k;
+  cudaError_t e = w_levels(h, h.reach_lvl_ptr_nt, h.d.reach_lvl_sn_nt, st);
+  if (e != cudaSuccess) return e;
+  const int nts = h.tail_reach_sn;
+  if (nts == 0) return cudaSuccess;
+  dim3 grid(nts, h.N, (k + kWChunk - 1) / kWChunk);
+  k_w_solve<true><<<grid, 128, 0, st>>>(h.d.tail_sn_list, h.d, h.Lx, h.sym.panel_total, h.W, h.cpl.nw, k);
+  h.launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_tail_g(Handle& h, cudaStream_t st) {
+  if (!h.tail_aug) return cudaSuccess;
+  const int k = h.cpl.k;
+  dim3 grid((k * k + 255) / 256, h.N);
+  k_add_tail_g<<<grid, 256, 0, st>>>(h.Tt, h.nT, h.nTa, k, h.G);
+  h.launches++;
   return cudaGetLastError();
 }
 
 cudaError_t launch_contract_g(Handle& h, cudaStream_t st) {
   const int k = h.cpl.k;
   if (k == 0) return cudaSuccess;
-  if (h.cpl.nw == 0) return cudaMemsetAsync(h.G, 0, sizeof(double) * (size_t)h.N * k * k, st);
-  const int T = (k + 31) / 32;
-  dim3 grid(T * (T + 1) / 2, h.N);
-  {
-    k_contract_g_f64<<<grid, 256, 0, st>>>(h.W, h.Lx, h.sym.panel_total, h.d.w_dpos, h.cpl.nw, k, h.G);
+  const int nrows = h.nw_nt;
+  cudaError_t e = cudaSuccess;
+  if (nrows == 0) {
+    e = cudaMemsetAsync(h.G, 0, sizeof(double) * (size_t)h.N * k * k, st);
+  } else {
+    const int T = (k + 31) / 32;
+    dim3 grid(T * (T + 1) / 2, h.N);
+    k_contract_g_f64<<<grid, 256, 0, st>>>(h.W, h.Lx, h.sym.panel_total, h.d.w_dpos, h.cpl.nw, nrows, k, h.G);
     h.launches++;
+    e = cudaGetLastError();
   }
-  return cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_add_tail_g(h, st);
 }
 
 cudaError_t launch_assemble_s(Handle& h, cudaStream_t st) {

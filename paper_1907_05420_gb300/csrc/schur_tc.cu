@@ -197,7 +197,9 @@ cudaError_t launch_contract_g_tc(Handle& h, int bf16, cudaStream_t st) {
     k_contract_g_tc<0><<<h.N, 128, smem, st>>>(h.W, h.Lx, h.sym.panel_total, h.d.w_dpos, h.d.g_rows, nchunks, npos,
                                            h.cpl.nw, h.cpl.k, h.G, h.dev_err);
   h.launches++;
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_add_tail_g(h, st);
 }
 
 }  // namespace kkt

@@ -615,4 +615,17 @@ void choose_tail(Symbolic& S, int32_t N, int64_t max_bytes, int32_t min_cols) {
   }
 }
 
+int32_t tail_w_rows(const Symbolic& S, const Coupling& C, std::vector<int32_t>& wrow_of_tail_col) {
+  const int32_t nT = S.n - S.tail_col;
+  wrow_of_tail_col.assign(nT, -1);
+  int32_t before = C.nw;
+  for (int32_t s = S.tail_sn; s < S.nsuper; s++) {
+    if (C.sn_wrow[s] < 0) continue;
+    before = std::min(before, C.sn_wrow[s]);
+    for (int32_t j = S.sn_first[s]; j < S.sn_first[s + 1]; j++)
+      wrow_of_tail_col[j - S.tail_col] = C.sn_wrow[s] + (j - S.sn_first[s]);
+  }
+  return before;
+}
+
 }  // namespace kkt

@@ -114,6 +114,11 @@ std::string analyze_coupling(const Symbolic& S, int32_t N, int32_t nC, const int
 void s_envelope(const Coupling& C, int32_t c_kind, int32_t block, std::vector<int32_t>& panel_rend,
                 std::vector<int32_t>& jlo, std::vector<int32_t>& jhi);
 
+// W rows of the tail: per tail column, its W row (-1 outside the reach of E).
+// W rows are numbered in supernode order, so the tail's come after all others;
+// returns the number of W rows outside the tail.
+int32_t tail_w_rows(const Symbolic& S, const Coupling& C, std::vector<int32_t>& wrow_of_tail_col);
+
 // Returns an empty string on success, else a description of the problem.
 std::string analyze_pattern(int32_t n, int32_t nP, const int32_t* rowptr, const int32_t* col,
                             const double* vals_hint, int32_t hint_blocks, Symbolic& out);

@@ -73,8 +73,16 @@ int64_t kkt_symbolic_get(const kkt_symbolic* sym, const char* name, int64_t* out
   if (n == "jhi") return copy_out(in->jhi, out);
   if (n == "colcount") return copy_out(S.colcount, out);
   if (n == "upd_ntail") return copy_out(S.upd_ntail, out);
+  if (n == "tail_wrow") {
+    std::vector<int32_t> tw;
+    kkt::tail_w_rows(S, C, tw);
+    return copy_out(tw, out);
+  }
   if (n == "stats") {
-    std::vector<int64_t> st = {S.n, S.nsuper, S.nlevels, S.panel_total, S.nnzL, C.k, C.nw, S.tail_sn, S.tail_col};
+    std::vector<int32_t> tw;
+    const int32_t nw_before = kkt::tail_w_rows(S, C, tw);
+    std::vector<int64_t> st = {S.n, S.nsuper, S.nlevels, S.panel_total, S.nnzL,
+                               C.k, C.nw,     S.tail_sn, S.tail_col,    nw_before};
     return copy_out(st, out);
   }
   return -1;

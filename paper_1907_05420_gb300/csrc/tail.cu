@@ -19,44 +19,80 @@
 // the solves use.
 // Entries of the triangles outside the supernodal structure stay exact zeros
 // (every product that reaches them has a zero factor).
+//
+// Augmented tail: each triangle gets k more rows, Z^T, where Z holds the
+// tail's rows of P^T E - L_{T,rest} W_rest (the right-hand sides of W after
+// the updates from outside the tail; zero rows for tail columns outside the
+// reach of E).  Factoring only the nT tail pivots of [T Z; Z^T 0] is the
+// incomplete factorization of Sec. 4.2 (eq. augmented) restricted to the tail:
+// the augmented rows become W_T^T D_T^{-1} with W_T = L_T^{-1} Z, and the
+// trailing k x k block becomes -W_T^T D_T^{-1} W_T, the tail's share of G.  So
+// the tail's W solve and contraction run inside the tail factor.
 #include "dense_kernels.cuh"
 
 namespace kkt {
 
 namespace {
 
-// panels of the tail supernodes <-> dense triangles, lower part only
+// panels of the tail supernodes <-> dense triangles (order nTa, the first nT
+// columns), lower part only
 template <bool TO_DENSE>
 __global__ void __launch_bounds__(256) k_tail_move(DevSym d, double* __restrict__ Lx, int64_t pt,
-                                                   double* __restrict__ T, int nT, int tail_col,
+                                                   double* __restrict__ T, int nTa, int tail_col,
                                                    int tail_sn) {
   const int s = tail_sn + blockIdx.x, b = blockIdx.y;
   const int m = (int)(d.sn_rowptr[s + 1] - d.sn_rowptr[s]);
   const int f = d.sn_first[s], w = d.sn_first[s + 1] - f;
   double* P = Lx + b * pt + d.sn_valoff[s];
   const int32_t* R = d.sn_rows + d.sn_rowptr[s];
-  double* Tb = T + (int64_t)b * nT * nT;
+  double* Tb = T + (int64_t)b * nTa * nTa;
   for (int q = threadIdx.x; q < m * w; q += blockDim.x) {
     const int c = q / m, i = q - c * m;
     const int row = R[i], col = f + c;
     if (row < col) continue;  // strictly upper part of the diagonal block: unused
-    double* t = Tb + (int64_t)(row - tail_col) + (int64_t)(col - tail_col) * nT;
+    double* t = Tb + (int64_t)(row - tail_col) + (int64_t)(col - tail_col) * nTa;
     if (TO_DENSE) *t = P[q];
     else P[q] = *t;
+  }
+}
+
+// Augmented rows: T_b[nT + t][j] = Z_b[j][t] (tail column j's W row before
+// the tail solve; zero for a column outside the reach of E), and after the
+// factor the tail's W rows from them: row nT + t of the factor holds
+// (W_T^T D_T^{-1})[t][j], so W_b[row(j)][t] = T_b[nT + t][j] * D_j.
+template <bool TO_DENSE>
+__global__ void k_tail_aug_rows(double* __restrict__ W, int nw, int k, double* __restrict__ T, int nT,
+                                int nTa, const int32_t* __restrict__ wrow) {
+  const int b = blockIdx.y;
+  double* Tb = T + (int64_t)b * nTa * nTa;
+  double* Wb = W + (int64_t)b * nw * k;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nT * k; q += gridDim.x * blockDim.x) {
+    const int j = q / k, t = q - j * k;
+    const int r = wrow[j];
+    if (r < 0) continue;
+    double* a = Tb + (int64_t)(nT + t) + (int64_t)j * nTa;
+    if (TO_DENSE) *a = Wb[(int64_t)r * k + t];
+    else Wb[(int64_t)r * k + t] = *a * Tb[(int64_t)j + (int64_t)j * nTa];
   }
 }
 
 }  // namespace
 
 cudaError_t launch_dense_tail(Handle& h, cudaStream_t st) {
-  const int nT = h.nT, N = h.N;
+  const int nT = h.nT, nTa = h.nTa, N = h.N;
   const int tail_sn = h.sym.tail_sn, tail_col = h.sym.tail_col;
   const int nsn = h.sym.nsuper - tail_sn;
-  const int64_t pt = h.sym.panel_total, t2 = (int64_t)nT * nT, ys = (int64_t)nT * kPanelW;
+  const int64_t pt = h.sym.panel_total, t2 = (int64_t)nTa * nTa, ys = (int64_t)nTa * kPanelW;
+  const int k = h.cpl.k, nw = h.cpl.nw;
+  const dim3 agrid((int)std::min<int64_t>(((int64_t)nT * k + 255) / 256, 64), N);
   cudaError_t e = cudaMemsetAsync(h.Tt, 0, sizeof(double) * t2 * N, st);
   if (e != cudaSuccess) return e;
-  k_tail_move<true><<<dim3(nsn, N), 256, 0, st>>>(h.d, h.Lx, pt, h.Tt, nT, tail_col, tail_sn);
+  k_tail_move<true><<<dim3(nsn, N), 256, 0, st>>>(h.d, h.Lx, pt, h.Tt, nTa, tail_col, tail_sn);
   h.launches++;
+  if (h.tail_aug) {
+    k_tail_aug_rows<true><<<agrid, 256, 0, st>>>(h.W, nw, k, h.Tt, nT, nTa, h.d.tail_wrow);
+    h.launches++;
+  }
   if (h.tail_mode == 2) {
     e = launch_tail_factor_emulated(h, st);
     if (e != cudaSuccess) return e;
@@ -64,18 +100,22 @@ cudaError_t launch_dense_tail(Handle& h, cudaStream_t st) {
   const PivotRule rule{h.anorm, h.opt.pivot_eps, h.d.col_primal + tail_col};
   for (int k0 = 0; h.tail_mode == 1 && k0 < nT; k0 += kPanelW) {
     const int kb = std::min(kPanelW, nT - k0);
-    k_dense_diag_t<double><<<N, 256, 0, st>>>(h.Tt, nT, k0, t2, rule, h.counters);
+    k_dense_diag_t<double><<<N, 256, 0, st>>>(h.Tt, nTa, k0, kb, t2, rule, h.counters);
     h.launches++;
-    const int rest = nT - k0 - kb;
+    const int rest = nTa - k0 - kb;
     if (rest > 0) {
-      launch_dense_panel<double>(h.Tt, h.TY, nT, k0, nT, N, t2, ys, st);
+      launch_dense_panel<double>(h.Tt, h.TY, nTa, k0, kb, nTa, N, t2, ys, st);
       const int tiles = (rest + 63) / 64;
-      k_dense_update<<<dim3(tiles * (tiles + 1) / 2, N), 256, 0, st>>>(h.Tt, h.TY, nT, k0, nT, t2, ys);
+      k_dense_update<<<dim3(tiles * (tiles + 1) / 2, N), 256, 0, st>>>(h.Tt, h.TY, nTa, k0, kb, nTa, t2, ys);
       h.launches += 2;
     }
   }
-  k_tail_move<false><<<dim3(nsn, N), 256, 0, st>>>(h.d, h.Lx, pt, h.Tt, nT, tail_col, tail_sn);
+  k_tail_move<false><<<dim3(nsn, N), 256, 0, st>>>(h.d, h.Lx, pt, h.Tt, nTa, tail_col, tail_sn);
   h.launches++;
+  if (h.tail_aug) {
+    k_tail_aug_rows<false><<<agrid, 256, 0, st>>>(h.W, nw, k, h.Tt, nT, nTa, h.d.tail_wrow);
+    h.launches++;
+  }
   return cudaGetLastError();
 }
 

@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gen import CONFIGS, make_problem, reseed_barrier
+from gen import CONFIGS, GridSpec, make_problem, reseed_barrier
 from tests.kkt_dense import dense_K
 
 pytestmark = pytest.mark.gpu
@@ -151,14 +151,20 @@ def test_full_size_2383_bus_96_periods_backward_error():
     assert oracle.backward_error(p, x) <= 1e-10
 
 
-@pytest.mark.parametrize("name", ["tiny", "grid30_n24", "grid2383_n6"])
+AUG_SPECS = {  # grids whose dense tail lies wholly inside the reach of the coupling rows
+    "aug14": GridSpec(14, 18, 3, 2, 4, 1e-6, 1e6, 102, "aug14"),
+    "aug15": GridSpec(15, 19, 3, 2, 4, 1e-6, 1e6, 103, "aug15"),
+}
+
+
+@pytest.mark.parametrize("name", ["tiny", "grid30_n24", "aug14", "aug15", "grid2383_n6"])
 def test_dense_tail_modes(name):
     """The dense tail factors the top of the tree as one triangle per block
     (mode 1: FP64 updates; mode 2: emulated-FP64 tensor-core updates); in every
     mode the solution meets the oracle's criteria and the pivot signs
     (inertia) are the expected ones."""
     spec = (replace(CONFIGS["grid2383_n96"], n_per=6, name="grid2383_n6") if name == "grid2383_n6"
-            else CONFIGS[name])
+            else AUG_SPECS.get(name) or CONFIGS[name])
     p = make_problem(spec)
     kappa = np.linalg.cond(dense_K(p)) if p.nK <= 4000 else None
     for mode in (0, 1, 2):
@@ -168,6 +174,7 @@ def test_dense_tail_modes(name):
         assert info["n_perturbed"] == 0
         if name == "grid2383_n6" and mode:
             assert info["dense_tail_cols"] >= 400
+        assert info["tail_augmented"] == (1 if mode else 0)
 
 
 @pytest.mark.parametrize("prec", ["tf32", "f64emu"])

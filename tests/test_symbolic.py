@@ -56,7 +56,7 @@ def analyze(p, hint=True):
     try:
         for name in ("perm partner sn_first sn_rowptr sn_rows sn_valoff sn_parent sn_level a_map "
                      "upd_ptr upd_src upd_r0 upd_r1 upd_reloff upd_rel E e_t wpos sn_wrow s_key "
-                     "panel_rend jlo jhi colcount upd_ntail stats").split():
+                     "panel_rend jlo jhi colcount upd_ntail tail_wrow stats").split():
             n = L.kkt_symbolic_get(h, name.encode(), None)
             assert n >= 0, name
             a = np.zeros(n, dtype=np.int64)
@@ -66,7 +66,8 @@ def analyze(p, hint=True):
         L.kkt_symbolic_destroy(h)
     st = out.pop("stats")
     out.update(n=int(st[0]), nsuper=int(st[1]), nlevels=int(st[2]), panel_total=int(st[3]),
-               nnzL=int(st[4]), k=int(st[5]), nw=int(st[6]), tail_sn=int(st[7]), tail_col=int(st[8]))
+               nnzL=int(st[4]), k=int(st[5]), nw=int(st[6]), tail_sn=int(st[7]), tail_col=int(st[8]),
+               nw_before_tail=int(st[9]))
     return out
 
 
@@ -75,7 +76,13 @@ def _storage_spec(seed=5):
     return GridSpec(20, 26, 4, 3, 6, 1e-6, 1e6, seed, "st20")
 
 
+def _aug_spec(seed=102, nb=14):
+    # a block whose dense tail lies in the reach of the coupling rows
+    return GridSpec(nb, nb + 4, 3, 2, 4, 1e-6, 1e6, seed, f"aug{seed}")
+
+
 PROBLEMS = {
+    "aug14": lambda: make_problem(_aug_spec()),
     "tiny": lambda: make_problem(CONFIGS["tiny"]),
     "small": lambda: make_problem(CONFIGS["small"]),
     "grid30_n24": lambda: make_problem(CONFIGS["grid30_n24"]),
@@ -390,3 +397,24 @@ def test_full_size_block_pattern():
     assert np.all(par[kids] > np.nonzero(kids)[0])
     assert len(np.unique(s["a_map"])) == p.nnzA
     assert s["E"].tolist() == sorted(set(np.asarray(p.b_row).tolist()))
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_tail_w_rows(name):
+    """The augmented tail needs the tail's W rows after all others: W rows are
+    numbered in supernode order over the reach of E, so the rows outside the
+    tail are the first nw_before_tail, and every tail column in the reach maps
+    to its own W row."""
+    p, s = _case(name)
+    t0, tc, n = s["tail_sn"], s["tail_col"], p.nA
+    first, wrow = s["sn_first"], s["sn_wrow"]
+    nT = n - tc
+    assert s["nw_before_tail"] == sum(first[q + 1] - first[q] for q in range(t0) if wrow[q] >= 0)
+    tw = s["tail_wrow"]
+    assert len(tw) == nT
+    for q in range(t0, s["nsuper"]):
+        for j in range(first[q], first[q + 1]):
+            assert tw[j - tc] == (wrow[q] + j - first[q] if wrow[q] >= 0 else -1)
+    rows = tw[tw >= 0]
+    assert np.all(rows >= s["nw_before_tail"]) and len(set(rows.tolist())) == len(rows)
+    assert len(rows) == s["nw"] - s["nw_before_tail"]
