@@ -97,15 +97,48 @@ __device__ __forceinline__ bool wait_flag(const int* flag, int epoch, int* err) 
   return true;
 }
 
-// L y = b in place (unit lower L, column-major n x n, leading dimension n)
+// Inverses X_t = L_tt^{-1} of the unit lower 64 x 64 diagonal blocks of a
+// factor (row-major per block, zero above the diagonal and outside the
+// matrix) and the reciprocal pivots 1 / D.  With them each step of the block
+// triangular solves applies its diagonal block as a product instead of a
+// 64-step substitution.  Row i of X is e_i - sum_{k<i} L_ik X_k (right-looking
+// over k, one barrier per k).
+template <class T>
+__global__ void __launch_bounds__(256) k_diag_inverse(const T* __restrict__ L, int n, double* __restrict__ X,
+                                                      double* __restrict__ dinv) {
+  extern __shared__ double dsm[];
+  double(*Ls)[65] = reinterpret_cast<double(*)[65]>(dsm);
+  double(*Xs)[65] = reinterpret_cast<double(*)[65]>(dsm + 64 * 65);
+  const int t = blockIdx.x, r0 = t * 64, rows = min(64, n - r0), tid = threadIdx.x;
+  for (int q = tid; q < 64 * 64; q += blockDim.x) {
+    const int c = q / 64, i = q - c * 64;
+    Ls[i][c] = (i > c && i < rows) ? (double)L[(int64_t)(r0 + i) + (int64_t)(r0 + c) * n] : 0.0;
+    Xs[i][c] = (i == c && i < rows) ? 1.0 : 0.0;
+  }
+  if (tid < rows) dinv[r0 + tid] = 1.0 / (double)L[(int64_t)(r0 + tid) * (n + 1)];
+  __syncthreads();
+  for (int k = 0; k + 1 < rows; k++) {
+    const int cnt = (rows - 1 - k) * (k + 1);
+    for (int q = tid; q < cnt; q += blockDim.x) {
+      const int i = k + 1 + q / (k + 1), j = q % (k + 1);
+      Xs[i][j] -= Ls[i][k] * Xs[k][j];
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < 64 * 64; q += blockDim.x) X[(int64_t)t * 4096 + q] = Xs[q / 64][q % 64];
+}
+
+// L y = b in place (unit lower L, column-major n x n, leading dimension n).
+// One CTA per 64-row block, taken in ticket order; block t adds the products
+// of the finished blocks j < t (each awaited on its flag), then applies X_t.
 template <class T>
 __global__ void __launch_bounds__(256) k_trsv_lower(const T* __restrict__ L, int n, double* x,
                                                     int* flags, unsigned* ticket, int epoch, int* err,
-                                                    const int* __restrict__ jlo) {
+                                                    const int* __restrict__ jlo, const double* __restrict__ X) {
   __shared__ int s_blk, s_ok;
   __shared__ double yj[64];
   __shared__ double part[4][64];
-  __shared__ double Ld[64][65];
+  __shared__ double Xs[64][65];
   const int tid = threadIdx.x;
   if (tid == 0) {
     s_blk = (int)atomicAdd(ticket, 1u);
@@ -114,6 +147,7 @@ __global__ void __launch_bounds__(256) k_trsv_lower(const T* __restrict__ L, int
   __syncthreads();
   const int t = s_blk, r0 = t * 64, rows = min(64, n - r0);
   const int r = tid & 63, pid = tid >> 6;
+  for (int q = tid; q < 64 * 64; q += 256) Xs[q / 64][q % 64] = X[(int64_t)t * 4096 + q];
   double acc = 0.0;
   for (int j = jlo ? jlo[t] : 0; j < t; j++) {  // blocks left of the row envelope are zero
     if (tid == 0 && !wait_flag(flags + j, epoch, err)) s_ok = 0;
@@ -129,25 +163,16 @@ __global__ void __launch_bounds__(256) k_trsv_lower(const T* __restrict__ L, int
     __syncthreads();
   }
   part[pid][r] = acc;
-  for (int q = tid; q < rows * rows; q += 256) {
-    const int c = q / rows, i = q - c * rows;
-    Ld[i][c] = (double)L[(int64_t)(r0 + i) + (int64_t)(r0 + c) * n];
-  }
   __syncthreads();
-  if (tid < 32) {
-    const int lane = tid;
-    double a0 = 0.0, a1 = 0.0;
-    if (lane < rows) a0 = __ldcg(x + r0 + lane) - (part[0][lane] + part[1][lane] + part[2][lane] + part[3][lane]);
-    if (lane + 32 < rows)
-      a1 = __ldcg(x + r0 + lane + 32) -
-           (part[0][lane + 32] + part[1][lane + 32] + part[2][lane + 32] + part[3][lane + 32]);
-    for (int c = 0; c < rows; c++) {
-      const double yc = __shfl_sync(0xffffffffu, c < 32 ? a0 : a1, c & 31);
-      if (lane > c && lane < rows) a0 -= Ld[lane][c] * yc;
-      if (lane + 32 > c && lane + 32 < rows) a1 -= Ld[lane + 32][c] * yc;
-    }
-    if (lane < rows) x[r0 + lane] = a0;
-    if (lane + 32 < rows) x[r0 + lane + 32] = a1;
+  if (tid < 64) yj[tid] = tid < rows ? __ldcg(x + r0 + tid) - (part[0][tid] + part[1][tid] + part[2][tid] + part[3][tid]) : 0.0;
+  __syncthreads();
+  double y = 0.0;
+#pragma unroll
+  for (int c = 0; c < 16; c++) y += Xs[r][pid * 16 + c] * yj[pid * 16 + c];
+  part[pid][r] = y;
+  __syncthreads();
+  if (tid < rows) {
+    x[r0 + tid] = part[0][tid] + part[1][tid] + part[2][tid] + part[3][tid];
     __threadfence();  // publish this block's solution before its flag
   }
   __syncthreads();
@@ -157,15 +182,18 @@ __global__ void __launch_bounds__(256) k_trsv_lower(const T* __restrict__ L, int
   }
 }
 
-// L^T x = y in place (blocks from the bottom up)
+// L^T x = D^{-1} y in place (blocks from the bottom up; the pivots' scaling
+// is applied to the block's own right-hand side), then X_t^T.
 template <class T>
 __global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ L, int n, double* x,
                                                     int* flags, unsigned* ticket, int epoch, int* err,
-                                                    const int* __restrict__ jhi) {
+                                                    const int* __restrict__ jhi, const double* __restrict__ X,
+                                                    const double* __restrict__ dinv) {
   __shared__ int s_blk, s_ok;
   __shared__ double xj[64];
   __shared__ double accs[64];
-  __shared__ double Ld[64][65];
+  __shared__ double part[4][64];
+  __shared__ double Xs[64][65];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb = (n + 63) / 64;
   if (tid == 0) {
@@ -175,6 +203,7 @@ __global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ L, int
   if (tid < 64) accs[tid] = 0.0;
   __syncthreads();
   const int b = s_blk, r0 = b * 64, rows = min(64, n - r0);
+  for (int q = tid; q < 64 * 64; q += 256) Xs[q / 64][q % 64] = X[(int64_t)b * 4096 + q];
   for (int j = (jhi ? jhi[b] : nb) - 1; j > b; j--) {  // blocks below the envelope are zero
     if (tid == 0 && !wait_flag(flags + j, epoch, err)) s_ok = 0;
     __syncthreads();
@@ -195,21 +224,16 @@ __global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ L, int
     }
     __syncthreads();
   }
-  for (int q = tid; q < rows * rows; q += 256) {
-    const int c = q / rows, i = q - c * rows;
-    Ld[i][c] = (double)L[(int64_t)(r0 + i) + (int64_t)(r0 + c) * n];
-  }
+  if (tid < 64) xj[tid] = tid < rows ? __ldcg(x + r0 + tid) * dinv[r0 + tid] - accs[tid] : 0.0;
   __syncthreads();
-  if (tid < 32) {
-    double a0 = lane < rows ? __ldcg(x + r0 + lane) - accs[lane] : 0.0;
-    double a1 = lane + 32 < rows ? __ldcg(x + r0 + lane + 32) - accs[lane + 32] : 0.0;
-    for (int c = rows - 1; c >= 0; c--) {
-      const double xc = __shfl_sync(0xffffffffu, c < 32 ? a0 : a1, c & 31);
-      if (lane < c) a0 -= Ld[c][lane] * xc;
-      if (lane + 32 < c) a1 -= Ld[c][lane + 32] * xc;
-    }
-    if (lane < rows) x[r0 + lane] = a0;
-    if (lane + 32 < rows) x[r0 + lane + 32] = a1;
+  const int c = tid & 63, pid = tid >> 6;
+  double v = 0.0;
+#pragma unroll
+  for (int q = 0; q < 16; q++) v += Xs[pid * 16 + q][c] * xj[pid * 16 + q];
+  part[pid][c] = v;
+  __syncthreads();
+  if (tid < rows) {
+    x[r0 + tid] = part[0][tid] + part[1][tid] + part[2][tid] + part[3][tid];
     __threadfence();  // publish this block's solution before its flag
   }
   __syncthreads();
@@ -236,7 +260,8 @@ cudaError_t launch_dense_ldlt(Handle& h, unsigned long long* counters, cudaStrea
       h.launches++;
     }
   }
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  return e != cudaSuccess ? e : launch_diag_inverse(h, false, st);
 }
 
 cudaError_t launch_dense_solve(Handle& h, const double* t, double* x, cudaStream_t st) {
@@ -249,11 +274,10 @@ cudaError_t launch_dense_solve(Handle& h, const double* t, double* x, cudaStream
   // flags hold the epoch of the last solve that finished each block; two per solve
   const int ep_f = ++h.trsv_epoch, ep_b = ++h.trsv_epoch;
   k_trsv_lower<double><<<nb, 256, 0, st>>>(h.S, n, x, h.trsv_flags, h.trsv_ticket, ep_f, h.dev_err,
-                                           h.d.trsv_jlo);
-  k_dense_diag_scale<<<(n + 255) / 256, 256, 0, st>>>(h.S, x, n);
+                                           h.d.trsv_jlo, h.Xinv);
   k_trsv_upper<double><<<nb, 256, 0, st>>>(h.S, n, x, h.trsv_flags + nb, h.trsv_ticket + 1, ep_b,
-                                           h.dev_err, h.d.trsv_jhi);
-  h.launches += 3;
+                                           h.dev_err, h.d.trsv_jhi, h.Xinv, h.Sdinv);
+  h.launches += 2;
   return cudaGetLastError();
 }
 
@@ -284,12 +308,21 @@ cudaError_t launch_dense_solve_ws(Handle& h, const double* t, double* x, double*
   return cudaGetLastError();
 }
 
-namespace {
-__global__ void k_dense_diag_scale_f32(const float* __restrict__ S, double* __restrict__ x, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    x[i] /= (double)S[i + (int64_t)i * n];
+// The diagonal-block inverses and reciprocal pivots of the current factor of S
+// (FP64 in S, or FP32 in S32), for the block triangular solves.
+cudaError_t launch_diag_inverse(Handle& h, bool f32, cudaStream_t st) {
+  const int n = h.nC;
+  if (n == 0) return cudaSuccess;
+  const int nb = (n + NB - 1) / NB;
+  const int smem = 2 * 64 * 65 * (int)sizeof(double);
+  cudaError_t e = f32 ? cudaFuncSetAttribute(k_diag_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                      : cudaFuncSetAttribute(k_diag_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (f32) k_diag_inverse<float><<<nb, 256, smem, st>>>(h.S32, n, h.Xinv, h.Sdinv);
+  else k_diag_inverse<double><<<nb, 256, smem, st>>>(h.S, n, h.Xinv, h.Sdinv);
+  h.launches++;
+  return cudaGetLastError();
 }
-}  // namespace
 
 // x = S32^{-1} t with the FP32 factor of the TF32/BF16 modes (FP64 accumulation)
 cudaError_t launch_dense_solve_f32(Handle& h, const double* t, double* x, cudaStream_t st) {
@@ -301,11 +334,10 @@ cudaError_t launch_dense_solve_f32(Handle& h, const double* t, double* x, cudaSt
   if (e != cudaSuccess) return e;
   const int ep_f = ++h.trsv_epoch, ep_b = ++h.trsv_epoch;
   k_trsv_lower<float><<<nb, 256, 0, st>>>(h.S32, n, x, h.trsv_flags, h.trsv_ticket, ep_f, h.dev_err,
-                                          h.d.trsv_jlo);
-  k_dense_diag_scale_f32<<<(n + 255) / 256, 256, 0, st>>>(h.S32, x, n);
+                                          h.d.trsv_jlo, h.Xinv);
   k_trsv_upper<float><<<nb, 256, 0, st>>>(h.S32, n, x, h.trsv_flags + nb, h.trsv_ticket + 1, ep_b,
-                                          h.dev_err, h.d.trsv_jhi);
-  h.launches += 3;
+                                          h.dev_err, h.d.trsv_jhi, h.Xinv, h.Sdinv);
+  h.launches += 2;
   return cudaGetLastError();
 }
 

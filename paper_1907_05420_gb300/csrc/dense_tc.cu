@@ -470,17 +470,22 @@ cudaError_t launch_dense_ldlt_tc(Handle& h, int mode, unsigned long long* counte
   if (n == 0) return cudaSuccess;
   const int32_t* rend = h.panel_rend.empty() ? nullptr : h.panel_rend.data();
   const TcStrides one{};
-  if (mode == KKT_F64_EMULATED)
-    return factor_tc<2, double>(h, h.S, h.Ypanel, n, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
-                                h.tc_scaleA, h.tc_scaleB, st);
+  cudaError_t e;
+  if (mode == KKT_F64_EMULATED) {
+    e = factor_tc<2, double>(h, h.S, h.Ypanel, n, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
+                             h.tc_scaleA, h.tc_scaleB, st);
+    return e != cudaSuccess ? e : launch_diag_inverse(h, false, st);
+  }
   const int64_t n2 = (int64_t)n * n;
   k_to_f32<<<(int)std::min<int64_t>((n2 + 255) / 256, 152 * 32), 256, 0, st>>>(h.S, h.S32, n2);
   h.launches++;
   if (mode == KKT_TF32)
-    return factor_tc<0, float>(h, h.S32, h.Y32, n, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
-                               h.tc_scaleA, h.tc_scaleB, st);
-  return factor_tc<1, float>(h, h.S32, h.Y32, n, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
-                             h.tc_scaleA, h.tc_scaleB, st);
+    e = factor_tc<0, float>(h, h.S32, h.Y32, n, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
+                            h.tc_scaleA, h.tc_scaleB, st);
+  else
+    e = factor_tc<1, float>(h, h.S32, h.Y32, n, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
+                            h.tc_scaleA, h.tc_scaleB, st);
+  return e != cudaSuccess ? e : launch_diag_inverse(h, true, st);
 }
 
 // The dense tails of the N block factors in emulated FP64: the batched

@@ -112,6 +112,8 @@ struct Handle {
   double* G = nullptr;        // N * k * k
   double* S = nullptr;        // nC * nC column-major (lower triangle used)
   double* Ypanel = nullptr;   // nC * kDenseNB scratch of the dense factor
+  double* Xinv = nullptr;     // ceil(nC/64) * 64 * 64: inverses of the diagonal blocks of the factor of S
+  double* Sdinv = nullptr;    // nC: reciprocal pivots of the factor of S
   double* Tt = nullptr;       // N * nT * nT: dense tails of the block factors (column-major)
   double* TY = nullptr;       // N * nT * kDenseNB: panel scratch of the tail factor
   int tail_mode = 0;          // 0 none, 1 FP64 on the CUDA cores, 2 emulated FP64 on the tensor cores
@@ -181,6 +183,7 @@ cudaError_t launch_contract_g_tc(Handle& h, int bf16, cudaStream_t st);
 cudaError_t launch_dense_ldlt(Handle& h, unsigned long long* counters, cudaStream_t st);
 cudaError_t launch_dense_solve(Handle& h, const double* t, double* x, cudaStream_t st);
 cudaError_t launch_dense_solve_f32(Handle& h, const double* t, double* x, cudaStream_t st);
+cudaError_t launch_diag_inverse(Handle& h, bool f32, cudaStream_t st);
 // ---- (dense_tc.cu) ----
 cudaError_t launch_dense_ldlt_tc(Handle& h, int mode, unsigned long long* counters, cudaStream_t st);
 int64_t tc_image_bytes_a(int n, int mode);
