@@ -44,12 +44,27 @@ __device__ __forceinline__ void diag_pair(int p, int& i, int& j) {
   i = j + (p - t * (t - 1) / 2);
 }
 
+// Reciprocal of a pivot.  FP64: the Newton-Raphson iteration for 1/d,
+// y <- y + y (1 - d y), twice from a single-precision seed (each step squares
+// the relative error: 2^-23 -> 2^-46 -> 2^-92, so the result is within an ulp
+// or so of 1/d), about half the latency of a double division on this GPU.
+// Pivots outside the single-precision normal range use the division.
+__device__ __forceinline__ double pivot_recip(double d) {
+  const double ad = fabs(d);
+  if (!(ad > 1e-36 && ad < 1e36)) return 1.0 / d;
+  double y = (double)__frcp_rn((float)d);
+  y = fma(y, fma(-d, y, 1.0), y);
+  y = fma(y, fma(-d, y, 1.0), y);
+  return y;
+}
+__device__ __forceinline__ float pivot_recip(float d) { return __frcp_rn(d); }
+
 // LDL^T of the diagonal block at (k0, k0) of matrix blockIdx.x, in shared
-// memory, in sub-panels of kSub = 16 columns (three barriers per sub-panel
-// instead of a barrier per column):
-//   (1) warp 0 factors the 16 x 16 diagonal sub-block in registers (lane i
-//       holds row i; column c's unscaled entries reach the other lanes by
-//       shuffle), applying the pivot rule to each pivot;
+// memory, in sub-panels of kSub = 16 columns:
+//   (1) the 16 x 16 diagonal sub-block, one thread per entry, a barrier pair
+//       per column (thread 0 applies the pivot rule and forms 1/d; the
+//       trailing entries take -l_i u_j; the column is scaled one step late,
+//       after its unscaled values have been used);
 //   (2) the rows below it in the block solve y L11^T = a, one thread per row
 //       (Y = y kept unscaled, L = y D^{-1});
 //   (3) the trailing triangle of the block takes A[i][j] -= sum_c L[i][c] Y[j][c]
@@ -57,7 +72,7 @@ __device__ __forceinline__ void diag_pair(int p, int& i, int& j) {
 constexpr int kSub = 16;
 
 template <class T>
-__global__ void __launch_bounds__(256) k_dense_diag_t(T* __restrict__ S0, int n, int k0, int kb,
+__global__ void __launch_bounds__(256, 1) k_dense_diag_t(T* __restrict__ S0, int n, int k0, int kb,
                                                       int64_t bstride, PivotRule rule,
                                                       unsigned long long* __restrict__ counters) {
   __shared__ T A[kPanelW][kPanelW + 1];
@@ -66,10 +81,20 @@ __global__ void __launch_bounds__(256) k_dense_diag_t(T* __restrict__ S0, int n,
   __shared__ uint16_t pairs[kDiagPairs];
   __shared__ int pert;
   T* S = S0 + (int64_t)blockIdx.x * bstride;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int q = tid; q < kb * kb; q += blockDim.x) {
-    const int c = q / kb, r = q - c * kb;
-    if (r >= c) A[r][c] = S[(int64_t)(k0 + r) + (int64_t)(k0 + c) * n];
+  const int tid = threadIdx.x;
+  {
+    // 16 loads per thread issued together, then stored
+    T v[16];
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      const int q = tid + u * 256, c = q >> 6, r = q & 63;
+      v[u] = (r >= c && r < kb && c < kb) ? S[(int64_t)(k0 + r) + (int64_t)(k0 + c) * n] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      const int q = tid + u * 256, c = q >> 6, r = q & 63;
+      A[r][c] = v[u];
+    }
   }
   for (int p = tid; p < kDiagPairs; p += blockDim.x) {
     int i, j;
@@ -79,41 +104,26 @@ __global__ void __launch_bounds__(256) k_dense_diag_t(T* __restrict__ S0, int n,
   if (tid == 0) pert = 0;
   __syncthreads();
   const double thr = rule.anorm ? rule.pivot_eps * rule.anorm[blockIdx.x] : 0.0;
+  const int si = tid >> 4, sj = tid & 15;  // this thread's entry of a 16 x 16 sub-block
   for (int c0 = 0; c0 < kb; c0 += kSub) {
     const int cb = min(kSub, kb - c0);
-    if (warp == 0) {  // (1)
-      const int i = lane;
-      T r[kSub];
-#pragma unroll
-      for (int j = 0; j < kSub; j++) r[j] = (i < cb && j <= i) ? A[c0 + i][c0 + j] : T(0);
-      int np = 0;
-#pragma unroll
-      for (int c = 0; c < kSub; c++) {
-        if (c < cb) {
-          T d = __shfl_sync(0xffffffffu, r[c], c);
-          if (thr > 0.0 && fabs((double)d) < thr) {
-            d = (T)(rule.primal[k0 + c0 + c] ? thr : -thr);
-            np++;
-          }
-          const T dinv = T(1) / d;
-          const T u = r[c];  // unscaled entry of row i in column c (i > c)
-          if (i == c) r[c] = d;
-          else if (i > c) r[c] = u * dinv;
-          if (lane == 0) Dinv[c] = dinv;
-#pragma unroll
-          for (int j = c + 1; j < kSub; j++) {
-            const T uj = __shfl_sync(0xffffffffu, u, j);
-            if (i >= j) r[j] -= r[c] * uj;
-          }
+    for (int c = 0; c < cb; c++) {  // (1)
+      if (tid == 0) {
+        T d = A[c0 + c][c0 + c];
+        if (thr > 0.0 && fabs((double)d) < thr) {
+          d = (T)(rule.primal[k0 + c0 + c] ? thr : -thr);
+          A[c0 + c][c0 + c] = d;
+          pert++;
         }
+        Dinv[c] = pivot_recip(d);
       }
-      if (i < cb) {
-#pragma unroll
-        for (int j = 0; j < kSub; j++)
-          if (j <= i) A[c0 + i][c0 + j] = r[j];
-      }
-      if (lane == 0) pert += np;
+      if (c > 0 && sj == c - 1 && si > c - 1 && si < cb) A[c0 + si][c0 + c - 1] *= Dinv[c - 1];
+      __syncthreads();
+      if (si > c && sj > c && sj <= si && si < cb)
+        A[c0 + si][c0 + sj] -= A[c0 + si][c0 + c] * Dinv[c] * A[c0 + sj][c0 + c];
+      __syncthreads();
     }
+    if (sj == cb - 1 && si > cb - 1 && si < cb) A[c0 + si][c0 + cb - 1] *= Dinv[cb - 1];
     __syncthreads();
     const int r0 = c0 + cb;
     for (int row = r0 + tid; row < kb; row += blockDim.x) {  // (2)
@@ -150,9 +160,12 @@ __global__ void __launch_bounds__(256) k_dense_diag_t(T* __restrict__ S0, int n,
     }
     __syncthreads();
   }
-  for (int q = tid; q < kb * kb; q += blockDim.x) {
-    const int c = q / kb, r = q - c * kb;
-    if (r >= c) S[(int64_t)(k0 + r) + (int64_t)(k0 + c) * n] = A[r][c];
+  {
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      const int q = tid + u * 256, c = q >> 6, r = q & 63;
+      if (r >= c && r < kb && c < kb) S[(int64_t)(k0 + r) + (int64_t)(k0 + c) * n] = A[r][c];
+    }
   }
   const T dd = tid < kb ? A[tid][tid] : T(0);
   const int pos = __syncthreads_count(dd > T(0));
