@@ -49,7 +49,7 @@ void free_all(Handle* h) {
                   h->d.b_blockptr, h->d.e_t, h->d.e_block, h->d.wpos, h->d.sn_wrow, h->d.w_dpos,
                   h->d.w_col, h->d.reach_lvl_sn, h->d.s_key, h->d.s_ptr, h->d.s_e1, h->d.s_e2,
                   h->d.t_ptr, h->d.t_e, h->d.bt_ptr, h->d.E, h->d.g_rows, h->d.trsv_jlo, h->d.trsv_jhi,
-                  h->d.flvl_sn, h->d.twork, h->d.upd_ntail, h->d.reach_lvl_sn_nt, h->d.tail_sn_list, h->d.tail_wrow, h->Xinv, h->Sdinv, h->Tt, h->TY, h->t_imgA, h->t_imgB,
+                  h->d.flvl_sn, h->d.twork, h->d.upd_ntail, h->d.reach_lvl_sn_nt, h->d.tail_sn_list, h->d.tail_wrow, h->Xinv, h->Sdinv, h->wdinv, h->Xtail, h->Tt, h->TY, h->t_imgA, h->t_imgB,
                   h->t_scaleA, h->t_scaleB, h->Lx, h->a_vals, h->b_vals,
                   h->c_vals, h->anorm, h->W, h->G, h->S, h->Ypanel, h->knorm, h->counters, h->r,
                   h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red,
@@ -350,11 +350,13 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   AL(anorm, double, h->N);
   AL(W, double, (int64_t)C.nw * k * h->N);
   AL(G, double, k * k * h->N);
+  AL(wdinv, double, (int64_t)C.nw * h->N);
   AL(S, double, (int64_t)h->nC * h->nC);
   AL(Ypanel, double, (int64_t)h->nC * kDenseNB);
   AL(Xinv, double, (int64_t)((h->nC + kDenseNB - 1) / kDenseNB) * kDenseNB * kDenseNB);
   AL(Sdinv, double, h->nC);
   if (h->nT > 0) {
+    AL(Xtail, double, (int64_t)((h->nT + kDenseNB - 1) / kDenseNB) * kDenseNB * kDenseNB * h->N);
     AL(Tt, double, (int64_t)h->nTa * h->nTa * h->N);
     AL(TY, double, (int64_t)h->nTa * kDenseNB * h->N);
   }
@@ -442,6 +444,7 @@ kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals
   KKT_CUDA(launch_scatter_a(*h, st));
   KKT_CUDA(launch_factor_levels(*h, st));
   KKT_CUDA(cudaEventRecord(h->ev_fa, st));
+  KKT_CUDA(launch_w_dinv(*h, st));
   KKT_CUDA(launch_w_solve(*h, st));
   h->g_reduced = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && h->opt.reduced_contraction &&
                  contract_g_tc_supported(*h);

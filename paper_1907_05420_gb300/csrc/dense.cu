@@ -103,19 +103,24 @@ __device__ __forceinline__ bool wait_flag(const int* flag, int epoch, int* err) 
 // triangular solves applies its diagonal block as a product instead of a
 // 64-step substitution.  Row i of X is e_i - sum_{k<i} L_ik X_k (right-looking
 // over k, one barrier per k).
+// Batched over blockIdx.y (matrix b at L0 + b * bstride with leading dimension
+// ld, its inverses at X0 + b * xstride); dinv may be null.
 template <class T>
-__global__ void __launch_bounds__(256) k_diag_inverse(const T* __restrict__ L, int n, double* __restrict__ X,
+__global__ void __launch_bounds__(256) k_diag_inverse(const T* __restrict__ L0, int n, int ld, int64_t bstride,
+                                                      double* __restrict__ X0, int64_t xstride,
                                                       double* __restrict__ dinv) {
   extern __shared__ double dsm[];
   double(*Ls)[65] = reinterpret_cast<double(*)[65]>(dsm);
   double(*Xs)[65] = reinterpret_cast<double(*)[65]>(dsm + 64 * 65);
+  const T* L = L0 + (int64_t)blockIdx.y * bstride;
+  double* X = X0 + (int64_t)blockIdx.y * xstride;
   const int t = blockIdx.x, r0 = t * 64, rows = min(64, n - r0), tid = threadIdx.x;
   for (int q = tid; q < 64 * 64; q += blockDim.x) {
     const int c = q / 64, i = q - c * 64;
-    Ls[i][c] = (i > c && i < rows) ? (double)L[(int64_t)(r0 + i) + (int64_t)(r0 + c) * n] : 0.0;
+    Ls[i][c] = (i > c && i < rows) ? (double)L[(int64_t)(r0 + i) + (int64_t)(r0 + c) * ld] : 0.0;
     Xs[i][c] = (i == c && i < rows) ? 1.0 : 0.0;
   }
-  if (tid < rows) dinv[r0 + tid] = 1.0 / (double)L[(int64_t)(r0 + tid) * (n + 1)];
+  if (dinv && tid < rows) dinv[r0 + tid] = 1.0 / (double)L[(int64_t)(r0 + tid) * (ld + 1)];
   __syncthreads();
   for (int k = 0; k + 1 < rows; k++) {
     const int cnt = (rows - 1 - k) * (k + 1);
@@ -318,8 +323,21 @@ cudaError_t launch_diag_inverse(Handle& h, bool f32, cudaStream_t st) {
   cudaError_t e = f32 ? cudaFuncSetAttribute(k_diag_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
                       : cudaFuncSetAttribute(k_diag_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  if (f32) k_diag_inverse<float><<<nb, 256, smem, st>>>(h.S32, n, h.Xinv, h.Sdinv);
-  else k_diag_inverse<double><<<nb, 256, smem, st>>>(h.S, n, h.Xinv, h.Sdinv);
+  if (f32) k_diag_inverse<float><<<nb, 256, smem, st>>>(h.S32, n, n, 0, h.Xinv, 0, h.Sdinv);
+  else k_diag_inverse<double><<<nb, 256, smem, st>>>(h.S, n, n, 0, h.Xinv, 0, h.Sdinv);
+  h.launches++;
+  return cudaGetLastError();
+}
+
+// The diagonal-block inverses of the N dense tails (order nT, leading
+// dimension nTa), for the tail's block triangular solves.
+cudaError_t launch_tail_inverse(Handle& h, cudaStream_t st) {
+  const int nbT = (h.nT + NB - 1) / NB;
+  const int smem = 2 * 64 * 65 * (int)sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_diag_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_diag_inverse<double><<<dim3(nbT, h.N), 256, smem, st>>>(h.Tt, h.nT, h.nTa, (int64_t)h.nTa * h.nTa, h.Xtail,
+                                                           (int64_t)nbT * 4096, nullptr);
   h.launches++;
   return cudaGetLastError();
 }

@@ -100,15 +100,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 // The 7 base-256 digits of u = v / 2^e in (-1, 1), truncated toward zero:
-// q = trunc(u 2^56) is exact in int64 (|v| has 53 significant bits and the
-// scaling is a power of two), and digit s is byte 6 - s of |q| with the sign of v.
+// q = trunc(|u| 2^56), and digit s is byte 6 - s of q with the sign of v.
+// Computed on the raw bits with integer operations only (FP64 instructions
+// are scarce on this GPU): |v| = m 2^(E - 1075) with m the 53-bit significand
+// and E the biased exponent (a subnormal has E = 0, no implicit bit and
+// exponent -1074), so q is m shifted by E - 1075 + 56 - e; |v| < 2^e bounds q
+// below 2^56.
 __device__ __forceinline__ void digits7(double v, int e, float out[kEmuSlices]) {
-  const long long q = (long long)ldexp(v, 56 - e);  // conversion truncates toward zero
-  const unsigned long long a = (unsigned long long)(q < 0 ? -q : q);
-  const float sg = q < 0 ? -1.f : 1.f;
+  const long long b = __double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7FF);
+  const unsigned long long m = (unsigned long long)(b & 0xFFFFFFFFFFFFFll) | (E ? (1ull << 52) : 0ull);
+  const int sh = (E ? E : 1) - 1075 + 56 - e;
+  const unsigned long long a = sh >= 0 ? (sh < 64 ? m << sh : 0ull) : (sh > -64 ? m >> (-sh) : 0ull);
+  const float sg = b < 0 ? -1.f : 1.f;
 #pragma unroll
   for (int s = 0; s < kEmuSlices; s++) out[s] = sg * (float)((a >> (8 * (kEmuSlices - 1 - s))) & 0xFFull);
 }
+
+// Biased exponent field of a double (0 for zero and subnormals).
+__device__ __forceinline__ int exp_field(double v) {
+  return (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+}
+
 
 // Images of the operands of one panel step.  Rows rho in [0, m) are trailing
 // rows base + rho.  A = Y (rows of L21 D, from Y with leading dimension n),
@@ -150,10 +163,19 @@ __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S0, cons
     double e_scale = 1.0;
     int e_exp = 0;
     if (MODE == 2) {
-      double amax = 0.0;
+      // e = ilogb(max |v|) + 1 from the largest exponent field; rows whose
+      // largest entry is subnormal (or zero) take the FP64 route
+      int emax = 0;
       if (live)
-        for (int c = 0; c < kb; c++) amax = fmax(amax, fabs((double)src[(int64_t)(base + rho) + (col0 + c) * n]));
-      e_exp = amax > 0.0 ? ilogb(amax) + 1 : 0;  // |v| < 2^e
+        for (int c = 0; c < kb; c++) emax = max(emax, exp_field((double)src[(int64_t)(base + rho) + (col0 + c) * n]));
+      if (emax > 0) {
+        e_exp = emax - 1023 + 1;  // |v| < 2^e
+      } else {
+        double amax = 0.0;
+        if (live)
+          for (int c = 0; c < kb; c++) amax = fmax(amax, fabs((double)src[(int64_t)(base + rho) + (col0 + c) * n]));
+        e_exp = amax > 0.0 ? ilogb(amax) + 1 : 0;
+      }
       e_scale = ldexp(1.0, e_exp);
       if (isA) scaleA[rho] = e_scale;
       else scaleB[rho] = e_scale;
@@ -334,9 +356,12 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n,
       uint32_t r[32];
       if (MODE == 2) {
         // levels 0-3 hold exact integers below 2^24: combine them exactly in
-        // int64, V = ((a0 256 + a1) 256 + a2) 256 + a3; levels 4-6 are below
-        // 2^-32 of the product and are combined in FP32, c = a4 + a5/256 + a6/65536.
-        // Then (Y L^T)_ij = 2^{e_i+f_j} 2^-40 (V + c / 256).
+        // int64, V = ((a0 256 + a1) 256 + a2) 256 + a3 (|V| < 2^47); levels 4-6
+        // are below 2^-32 of the product and are combined in FP32,
+        // c = a4 + a5/256 + a6/65536.  Then
+        //   (Y L^T)_ij = 2^{e_i+f_j} 2^-40 (V + c / 256) = 2^{e_i+f_j-56} W,
+        //   W = V 2^16 + round(256 c)   (|W| < 2^63),
+        // applied as cur - W p with p = 2^{e_i-56} 2^{f_j} (exact powers of two).
         long long V[32];
         float cf[32];
 #pragma unroll
@@ -354,10 +379,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n,
             else cf[j] += fv * (d == 4 ? 1.f : (d == 5 ? 0.00390625f : 0.0000152587890625f));
           }
         }
-        double acc[32];
-#pragma unroll
-        for (int j = 0; j < 32; j++) acc[j] = 0x1p-40 * ((double)V[j] + 0.00390625 * (double)cf[j]);
         if (rho < m) {
+          const double pa = sa * 0x1p-56;
           // all loads of the 32 columns first, then the stores: 32 loads in flight
           T cur[32];
 #pragma unroll
@@ -370,8 +393,10 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n,
           for (int j = 0; j < 32; j++) {
             const int cj = J * TN + cc * 32 + j;
             const int col = base + cj;
-            if (cj < m && row >= col)
-              S[(int64_t)row + (int64_t)col * n] = (T)((double)cur[j] - sa * scaleB[cj] * acc[j]);
+            if (cj < m && row >= col) {
+              const long long W = V[j] * 65536 + (long long)__float2int_rn(cf[j] * 256.f);
+              S[(int64_t)row + (int64_t)col * n] = (T)fma(-(double)W, pa * scaleB[cj], (double)cur[j]);
+            }
           }
         }
       } else {

@@ -110,12 +110,14 @@ struct Handle {
   double* anorm = nullptr;    // N: max |a| per block
   double* W = nullptr;        // N * nw * k, row-major per block
   double* G = nullptr;        // N * k * k
+  double* wdinv = nullptr;    // N * nw: reciprocal pivot of each W row
   double* S = nullptr;        // nC * nC column-major (lower triangle used)
   double* Ypanel = nullptr;   // nC * kDenseNB scratch of the dense factor
   double* Xinv = nullptr;     // ceil(nC/64) * 64 * 64: inverses of the diagonal blocks of the factor of S
   double* Sdinv = nullptr;    // nC: reciprocal pivots of the factor of S
   double* Tt = nullptr;       // N * nT * nT: dense tails of the block factors (column-major)
   double* TY = nullptr;       // N * nT * kDenseNB: panel scratch of the tail factor
+  double* Xtail = nullptr;    // N * ceil(nT/64) * 64 * 64: inverses of the tails' diagonal blocks
   int tail_mode = 0;          // 0 none, 1 FP64 on the CUDA cores, 2 emulated FP64 on the tensor cores
   uint8_t* t_imgA = nullptr;  // per block: tensor-core operand images of one tail panel step
   uint8_t* t_imgB = nullptr;
@@ -174,6 +176,7 @@ cudaError_t launch_tail_factor_emulated(Handle& h, cudaStream_t st);  // (dense_
 cudaError_t launch_w_solve(Handle& h, cudaStream_t st);
 cudaError_t launch_w_solve_before_tail(Handle& h, cudaStream_t st);
 cudaError_t launch_add_tail_g(Handle& h, cudaStream_t st);
+cudaError_t launch_w_dinv(Handle& h, cudaStream_t st);
 cudaError_t launch_contract_g(Handle& h, cudaStream_t st);
 cudaError_t launch_assemble_s(Handle& h, cudaStream_t st);
 // ---- (schur_tc.cu) ----
@@ -184,6 +187,9 @@ cudaError_t launch_dense_ldlt(Handle& h, unsigned long long* counters, cudaStrea
 cudaError_t launch_dense_solve(Handle& h, const double* t, double* x, cudaStream_t st);
 cudaError_t launch_dense_solve_f32(Handle& h, const double* t, double* x, cudaStream_t st);
 cudaError_t launch_diag_inverse(Handle& h, bool f32, cudaStream_t st);
+cudaError_t launch_tail_inverse(Handle& h, cudaStream_t st);
+cudaError_t launch_tail_fsolve(Handle& h, double* z, cudaStream_t st);  // (tail.cu)
+cudaError_t launch_tail_bsolve(Handle& h, double* z, cudaStream_t st);
 // ---- (dense_tc.cu) ----
 cudaError_t launch_dense_ldlt_tc(Handle& h, int mode, unsigned long long* counters, cudaStream_t st);
 int64_t tc_image_bytes_a(int n, int mode);

@@ -72,10 +72,10 @@ __global__ void __launch_bounds__(128) k_w_solve(const int32_t* __restrict__ sn_
 }
 
 // G_b = W_b^T D_b^{-1} W_b in FP64, one 32x32 tile of the lower triangle per CTA
-// (the first nrows rows of W; nw is its row count per block)
+// (the first nrows rows of W; nw is its row count per block; wdinv holds the
+// reciprocal pivot of every W row)
 __global__ void __launch_bounds__(256) k_contract_g_f64(const double* __restrict__ W,
-                                                        const double* __restrict__ Lx, int64_t pt,
-                                                        const int64_t* __restrict__ w_dpos, int nw, int nrows,
+                                                        const double* __restrict__ wdinv, int nw, int nrows,
                                                         int k, double* __restrict__ G) {
   const int b = blockIdx.y;
   // tile index -> (ti, tj) with ti >= tj
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) k_contract_g_f64(const double* __restrict
   const int t1_0 = ti * 32, t2_0 = tj * 32;
   __shared__ double Wa[32][33], Wb_[32][33];
   const double* Wblk = W + (int64_t)b * nw * k;
-  const double* Pb = Lx + b * pt;
+  const double* dinv_b = wdinv + (int64_t)b * nw;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   double acc[4] = {0, 0, 0, 0};
   for (int r0 = 0; r0 < nrows; r0 += 32) {
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_contract_g_f64(const double* __restrict
       const int row = r0 + rr;
       double a = 0.0, bb = 0.0;
       if (row < nrows) {
-        const double dinv = 1.0 / Pb[w_dpos[row]];
+        const double dinv = dinv_b[row];
         if (t1_0 + cc < k) a = Wblk[(int64_t)row * k + t1_0 + cc] * dinv;
         if (t2_0 + cc < k) bb = Wblk[(int64_t)row * k + t2_0 + cc];
       }
@@ -133,6 +133,17 @@ __global__ void k_add_tail_g(const double* __restrict__ Ta, int nT, int nTa, int
     const int t1 = q / k, t2 = q - t1 * k;
     const int hi = max(t1, t2), lo = min(t1, t2);
     Gb[q] -= Tb[(int64_t)(nT + hi) + (int64_t)(nT + lo) * nTa];
+  }
+}
+
+// reciprocal pivot of every W row of every block (used by the contraction and
+// by the right-hand-side reduction of the solves)
+__global__ void k_w_dinv(const double* __restrict__ Lx, int64_t pt, const int64_t* __restrict__ w_dpos, int nw,
+                         int N, double* __restrict__ wdinv) {
+  const int64_t total = (int64_t)nw * N;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = q / nw, row = q - b * nw;
+    wdinv[q] = 1.0 / Lx[b * pt + w_dpos[row]];
   }
 }
 
@@ -209,6 +220,15 @@ cudaError_t launch_w_solve_before_tail(Handle& h, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_w_dinv(Handle& h, cudaStream_t st) {
+  const int64_t total = (int64_t)h.cpl.nw * h.N;
+  if (total == 0) return cudaSuccess;
+  k_w_dinv<<<(int)std::min<int64_t>((total + 255) / 256, 152 * 8), 256, 0, st>>>(h.Lx, h.sym.panel_total, h.d.w_dpos,
+                                                                              h.cpl.nw, h.N, h.wdinv);
+  h.launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_add_tail_g(Handle& h, cudaStream_t st) {
   if (!h.tail_aug) return cudaSuccess;
   const int k = h.cpl.k;
@@ -228,7 +248,7 @@ cudaError_t launch_contract_g(Handle& h, cudaStream_t st) {
   } else {
     const int T = (k + 31) / 32;
     dim3 grid(T * (T + 1) / 2, h.N);
-    k_contract_g_f64<<<grid, 256, 0, st>>>(h.W, h.Lx, h.sym.panel_total, h.d.w_dpos, h.cpl.nw, nrows, k, h.G);
+    k_contract_g_f64<<<grid, 256, 0, st>>>(h.W, h.wdinv, h.cpl.nw, nrows, k, h.G);
     h.launches++;
     e = cudaGetLastError();
   }

@@ -205,8 +205,7 @@ __global__ void __launch_bounds__(128) k_bsolve_level(const int32_t* __restrict_
 // 32 columns): warp w sums the rows rho = w mod 8, the 8 partials are added in
 // warp order.
 __global__ void __launch_bounds__(256) k_reduce_u(const double* __restrict__ W, const double* __restrict__ z,
-                                                  const double* __restrict__ Lx, int64_t pt,
-                                                  const int64_t* __restrict__ w_dpos,
+                                                  const double* __restrict__ wdinv,
                                                   const int32_t* __restrict__ w_col, int nw, int k, int nA,
                                                   double* __restrict__ u) {
   __shared__ double part[8][32];
@@ -214,10 +213,10 @@ __global__ void __launch_bounds__(256) k_reduce_u(const double* __restrict__ W, 
   const int t = blockIdx.x * 32 + lane;
   const double* Wb = W + (int64_t)b * nw * k;
   const double* zb = z + (int64_t)b * nA;
-  const double* Pb = Lx + b * pt;
+  const double* db = wdinv + (int64_t)b * nw;
   double acc = 0.0;
   if (t < k)
-    for (int rho = warp; rho < nw; rho += 8) acc += Wb[(int64_t)rho * k + t] * (zb[w_col[rho]] / Pb[w_dpos[rho]]);
+    for (int rho = warp; rho < nw; rho += 8) acc += Wb[(int64_t)rho * k + t] * (zb[w_col[rho]] * db[rho]);
   part[warp][lane] = acc;
   __syncthreads();
   if (warp == 0 && t < k) {
@@ -426,21 +425,31 @@ cudaError_t launch_apply_inverse(Handle& h, const double* r, double* out, cudaSt
     k_permute_in<<<grid_for(nb), 256, 0, st>>>(r, h.d.perm, h.z, nA, N);
     h.launches++;
   }
+  // with a dense tail, the levels cover the supernodes outside it and the
+  // tail's triangular solves are dense (the tail factor's triangles)
+  const bool tail = h.nT > 0;
+  const std::vector<int32_t>& lptr = tail ? h.flvl_ptr : h.lvl_ptr;
+  const int32_t* lsn = tail ? h.d.flvl_sn : h.d.lvl_sn;
   for (int l = 0; l < h.sym.nlevels; l++) {
-    const int s0 = h.lvl_ptr[l], nsn = h.lvl_ptr[l + 1] - s0;
+    const int s0 = lptr[l], nsn = lptr[l + 1] - s0;
+    if (nsn == 0) continue;
     const int warps = nsn * N;
     if (warps < kWideLevelWarps) {
-      k_fsolve_level_wide<<<dim3(nsn, N), kSolveWarps * 32, 0, st>>>(h.d.lvl_sn + s0, h.d, h.Lx, pt, h.z, nA);
+      k_fsolve_level_wide<<<dim3(nsn, N), kSolveWarps * 32, 0, st>>>(lsn + s0, h.d, h.Lx, pt, h.z, nA);
     } else {
-      k_fsolve_level<<<(warps + 3) / 4, 128, 0, st>>>(h.d.lvl_sn + s0, nsn, h.d, h.Lx, pt, h.z, nA, N);
+      k_fsolve_level<<<(warps + 3) / 4, 128, 0, st>>>(lsn + s0, nsn, h.d, h.Lx, pt, h.z, nA, N);
     }
     h.launches++;
+  }
+  if (tail) {
+    cudaError_t e = launch_tail_fsolve(h, h.z, st);
+    if (e != cudaSuccess) return e;
   }
   if (h.nC > 0) {
     if (k > 0 && nw > 0) {
       dim3 g((k + 31) / 32, N);
       {
-    k_reduce_u<<<g, 256, 0, st>>>(h.W, h.z, h.Lx, pt, h.d.w_dpos, h.d.w_col, nw, k, nA, h.u);
+    k_reduce_u<<<g, 256, 0, st>>>(h.W, h.z, h.wdinv, h.d.w_col, nw, k, nA, h.u);
     h.launches++;
   }
     } else if (k > 0) {
@@ -469,13 +478,18 @@ cudaError_t launch_apply_inverse(Handle& h, const double* r, double* out, cudaSt
     k_diag_scale<<<grid_for(nb), 256, 0, st>>>(h.d.col_dpos, h.Lx, pt, h.z, nA, N);
     h.launches++;
   }
+  if (tail) {
+    cudaError_t e = launch_tail_bsolve(h, h.z, st);
+    if (e != cudaSuccess) return e;
+  }
   for (int l = h.sym.nlevels - 1; l >= 0; l--) {
-    const int s0 = h.lvl_ptr[l], nsn = h.lvl_ptr[l + 1] - s0;
+    const int s0 = lptr[l], nsn = lptr[l + 1] - s0;
+    if (nsn == 0) continue;
     const int warps = nsn * N;
     if (warps < kWideLevelWarps) {
-      k_bsolve_level_wide<<<dim3(nsn, N), kSolveWarps * 32, 0, st>>>(h.d.lvl_sn + s0, h.d, h.Lx, pt, h.z, nA);
+      k_bsolve_level_wide<<<dim3(nsn, N), kSolveWarps * 32, 0, st>>>(lsn + s0, h.d, h.Lx, pt, h.z, nA);
     } else {
-      k_bsolve_level<<<(warps + 3) / 4, 128, 0, st>>>(h.d.lvl_sn + s0, nsn, h.d, h.Lx, pt, h.z, nA, N);
+      k_bsolve_level<<<(warps + 3) / 4, 128, 0, st>>>(lsn + s0, nsn, h.d, h.Lx, pt, h.z, nA, N);
     }
     h.launches++;
   }
@@ -567,7 +581,7 @@ cudaError_t launch_apply_inverse_ws(Handle& h, const double* r, double* out,
   if (h.nC > 0) {
     if (k > 0 && nw > 0) {
       dim3 g((k + 31) / 32, N);
-      k_reduce_u<<<g, 256, 0, st>>>(h.W, ws.z, h.Lx, pt, h.d.w_dpos, h.d.w_col, nw, k, nA, ws.u);
+      k_reduce_u<<<g, 256, 0, st>>>(h.W, ws.z, h.wdinv, h.d.w_col, nw, k, nA, ws.u);
       h.launches++;
     } else if (k > 0) {
       cudaError_t e = cudaMemsetAsync(ws.u, 0, sizeof(double) * (size_t)k * N, st);

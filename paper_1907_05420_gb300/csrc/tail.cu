@@ -76,7 +76,113 @@ __global__ void k_tail_aug_rows(double* __restrict__ W, int nw, int k, double* _
   }
 }
 
+// Forward solve, the tail's share: z[cols(s)] -= sum over descendants d
+// outside the tail of L_d[rows in s] z[cols(d)], for every tail supernode s
+// (independent of one another; the triangular solve is the dense tail's).
+// One CTA of 8 warps per (tail supernode, block), warp w taking the updates
+// u = w mod 8, the partials added in warp order.
+__global__ void __launch_bounds__(256) k_tail_fgather(DevSym d, const double* __restrict__ Lx, int64_t pt,
+                                                      double* __restrict__ z, int nA, int tail_sn) {
+  __shared__ double part[8][32];
+  const int s = tail_sn + blockIdx.x, b = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = d.sn_first[s], w = d.sn_first[s + 1] - f;
+  double* zb = z + (int64_t)b * nA;
+  double mine = 0.0;
+  const int64_t u0 = d.upd_ptr[s], u1 = u0 + d.upd_ntail[s];
+  for (int64_t u = u0 + warp; u < u1; u += 8) {
+    const int dd = d.upd_src[u];
+    const int r0 = d.upd_r0[u], r1 = d.upd_r1[u];
+    const int md = (int)(d.sn_rowptr[dd + 1] - d.sn_rowptr[dd]);
+    const int fd = d.sn_first[dd], wd = d.sn_first[dd + 1] - fd;
+    const double* Pd = Lx + b * pt + d.sn_valoff[dd];
+    const int32_t* Rd = d.sn_rows + d.sn_rowptr[dd];
+    double acc = 0.0;
+    const int j = r0 + lane;
+    if (j < r1)
+      for (int kk = 0; kk < wd; kk++) acc += Pd[(int64_t)kk * md + j] * zb[fd + kk];
+    const int tgt = j < r1 ? Rd[j] - f : -1;
+    for (int src = 0; src < r1 - r0; src++) {  // targets are distinct within an update
+      const double v = __shfl_sync(0xffffffffu, acc, src);
+      const int tg = __shfl_sync(0xffffffffu, tgt, src);
+      if (lane == tg) mine += v;
+    }
+  }
+  part[warp][lane] = mine;
+  __syncthreads();
+  if (warp == 0 && lane < w) {
+    double sum = 0.0;
+    for (int q = 0; q < 8; q++) sum += part[q][lane];
+    zb[f + lane] -= sum;
+  }
+}
+
+// Dense triangular solves of the tails, one CTA per block, in 64-row steps
+// with the diagonal-block inverses X_t.  Forward (L_T y = z): y_t = X_t z_t,
+// then the rows below take z_i -= L_it y_t.  Backward (L_T^T x = y): x_t =
+// X_t^T y_t, then the rows above take y_i -= L_ti^T x_t.  zt points at the
+// tail's first entry of block 0 (blocks nA apart).
+template <bool FORWARD>
+__global__ void __launch_bounds__(256) k_tail_trsv(const double* __restrict__ T, int nT, int nTa,
+                                                   const double* __restrict__ X, double* __restrict__ zt, int nA) {
+  __shared__ double v[64];
+  __shared__ double part[4][64];
+  const int b = blockIdx.x, tid = threadIdx.x, r = tid & 63, pid = tid >> 6;
+  const int nbT = (nT + 63) / 64;
+  const double* Tb = T + (int64_t)b * nTa * nTa;
+  const double* Xb = X + (int64_t)b * nbT * 4096;
+  double* z = zt + (int64_t)b * nA;
+  for (int step = 0; step < nbT; step++) {
+    const int t = FORWARD ? step : nbT - 1 - step;
+    const int r0 = t * 64, rows = min(64, nT - r0);
+    if (tid < 64) v[tid] = tid < rows ? z[r0 + tid] : 0.0;
+    __syncthreads();
+    // X_t v (forward) or X_t^T v (backward), 4 partial sums per output
+    double acc = 0.0;
+    const double* Xt = Xb + (int64_t)t * 4096;
+#pragma unroll
+    for (int c = 0; c < 16; c++)
+      acc += (FORWARD ? Xt[r * 64 + pid * 16 + c] : Xt[(pid * 16 + c) * 64 + r]) * v[pid * 16 + c];
+    part[pid][r] = acc;
+    __syncthreads();
+    if (tid < 64) {
+      const double y = part[0][tid] + part[1][tid] + part[2][tid] + part[3][tid];
+      v[tid] = y;
+      if (tid < rows) z[r0 + tid] = y;
+    }
+    __syncthreads();
+    if (FORWARD) {
+      for (int i = r0 + 64 + tid; i < nT; i += blockDim.x) {
+        double a = 0.0;
+        for (int c = 0; c < rows; c++) a += Tb[(int64_t)i + (int64_t)(r0 + c) * nTa] * v[c];
+        z[i] -= a;
+      }
+    } else {
+      for (int i = tid; i < r0; i += blockDim.x) {
+        double a = 0.0;
+        for (int c = 0; c < rows; c++) a += Tb[(int64_t)(r0 + c) + (int64_t)i * nTa] * v[c];
+        z[i] -= a;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_tail_fsolve(Handle& h, double* z, cudaStream_t st) {
+  const int nts = h.sym.nsuper - h.sym.tail_sn;
+  k_tail_fgather<<<dim3(nts, h.N), 256, 0, st>>>(h.d, h.Lx, h.sym.panel_total, z, h.nA, h.sym.tail_sn);
+  k_tail_trsv<true><<<h.N, 256, 0, st>>>(h.Tt, h.nT, h.nTa, h.Xtail, z + h.sym.tail_col, h.nA);
+  h.launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tail_bsolve(Handle& h, double* z, cudaStream_t st) {
+  k_tail_trsv<false><<<h.N, 256, 0, st>>>(h.Tt, h.nT, h.nTa, h.Xtail, z + h.sym.tail_col, h.nA);
+  h.launches++;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_dense_tail(Handle& h, cudaStream_t st) {
   const int nT = h.nT, nTa = h.nTa, N = h.N;
@@ -116,7 +222,8 @@ cudaError_t launch_dense_tail(Handle& h, cudaStream_t st) {
     k_tail_aug_rows<false><<<agrid, 256, 0, st>>>(h.W, nw, k, h.Tt, nT, nTa, h.d.tail_wrow);
     h.launches++;
   }
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  return e != cudaSuccess ? e : launch_tail_inverse(h, st);
 }
 
 }  // namespace kkt
