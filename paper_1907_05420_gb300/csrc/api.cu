@@ -61,6 +61,66 @@ void free_all(Handle* h) {
   cudaEvent_t evs[] = {h->ev_f0, h->ev_f1, h->ev_fa, h->ev_fb, h->ev_s0, h->ev_s1, h->ev_done};
   for (cudaEvent_t ev : evs)
     if (ev) cudaEventDestroy(ev);
+  if (h->factor_exec) cudaGraphExecDestroy(h->factor_exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+}
+
+// An event record that becomes a node of the graph while the factor is captured.
+cudaError_t record(Handle& h, cudaEvent_t ev, cudaStream_t st) {
+  return cudaEventRecordWithFlags(ev, st, h.capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
+// The device work of kkt_factor after the input copies: every launch depends
+// only on the handle's buffers and options, so the sequence is captured once
+// as a CUDA graph and replayed.
+cudaError_t enqueue_factor(Handle& h, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(h.counters, 0, sizeof(unsigned long long) * 2 * kNumCounters, st);
+#define STEP(x) \
+  if (e == cudaSuccess) e = (x)
+  STEP(launch_scatter_a(h, st));
+  STEP(launch_factor_levels(h, st));
+  STEP(record(h, h.ev_fa, st));
+  STEP(launch_w_dinv(h, st));
+  STEP(launch_w_solve(h, st));
+  if (h.g_reduced) {
+    STEP(launch_contract_g_tc(h, h.opt.prec == KKT_BF16 ? 1 : 0, st));
+  } else {
+    STEP(launch_contract_g(h, st));
+  }
+  STEP(launch_assemble_s(h, st));
+  STEP(record(h, h.ev_fb, st));
+  if (h.opt.prec == KKT_FP64) {
+    STEP(launch_dense_ldlt(h, h.counters + kNumCounters, st));
+  } else {
+    STEP(launch_dense_ldlt_tc(h, h.opt.prec, h.counters + kNumCounters, st));
+  }
+  STEP(launch_knorm(h, st));
+#undef STEP
+  return e;
+}
+
+// Captures enqueue_factor into h.factor_exec; on any failure the handle keeps
+// launching directly.
+void capture_factor(Handle& h) {
+  const int64_t l0 = h.launches;
+  cudaGraph_t g = nullptr;
+  h.capturing = true;
+  cudaError_t e = cudaStreamBeginCapture(h.cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = enqueue_factor(h, h.cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(h.cap_stream, &g);
+    e = e1 != cudaSuccess ? e1 : e2;
+  }
+  h.capturing = false;
+  if (e == cudaSuccess && g) e = cudaGraphInstantiate(&h.factor_exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  h.graph_launches = h.launches - l0;
+  h.launches = l0;
+  if (e != cudaSuccess || !h.factor_exec) {
+    h.graph_failed = true;
+    h.factor_exec = nullptr;
+    (void)cudaGetLastError();
+  }
 }
 
 }  // namespace
@@ -405,6 +465,10 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->host_red, sizeof(double) * 8);
   for (cudaEvent_t* ev : {&h->ev_f0, &h->ev_f1, &h->ev_fa, &h->ev_fb, &h->ev_s0, &h->ev_s1, &h->ev_done})
     if (e == cudaSuccess) e = cudaEventCreate(ev);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = dense_prepare();
+  if (e == cudaSuccess) e = dense_tc_prepare();
+  if (e == cudaSuccess) e = schur_tc_prepare();
   if (e != cudaSuccess) {
     kkt_status st = cuda_status(e, "kkt_analyze");
     free_all(h);
@@ -440,29 +504,17 @@ kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals
   KKT_CUDA(cudaMemcpyAsync(h->a_vals, a_vals, sizeof(double) * h->nnzA * h->N, kind, st));
   if (h->nnzB > 0) KKT_CUDA(cudaMemcpyAsync(h->b_vals, b_vals, sizeof(double) * h->nnzB, kind, st));
   if (nc_vals > 0) KKT_CUDA(cudaMemcpyAsync(h->c_vals, c_vals, sizeof(double) * nc_vals, kind, st));
-  KKT_CUDA(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * 2 * kNumCounters, st));
-  KKT_CUDA(launch_scatter_a(*h, st));
-  KKT_CUDA(launch_factor_levels(*h, st));
-  KKT_CUDA(cudaEventRecord(h->ev_fa, st));
-  KKT_CUDA(launch_w_dinv(*h, st));
-  KKT_CUDA(launch_w_solve(*h, st));
   h->g_reduced = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && h->opt.reduced_contraction &&
                  contract_g_tc_supported(*h);
-  if (h->g_reduced)
-    KKT_CUDA(launch_contract_g_tc(*h, h->opt.prec == KKT_BF16 ? 1 : 0, st));
-  else
-    KKT_CUDA(launch_contract_g(*h, st));
-  KKT_CUDA(launch_assemble_s(*h, st));
-  KKT_CUDA(cudaEventRecord(h->ev_fb, st));
-  if (h->opt.prec == KKT_FP64) {
-    KKT_CUDA(launch_dense_ldlt(*h, h->counters + kNumCounters, st));
-    h->s_factor = 0;
+  h->s_factor = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) ? 1 : 0;
+  if (h->opt.use_graphs && !h->graph_failed && !h->factor_exec) capture_factor(*h);
+  if (h->factor_exec) {
+    KKT_CUDA(cudaGraphLaunch(h->factor_exec, st));
+    h->launches += h->graph_launches;
   } else {
-    KKT_CUDA(launch_dense_ldlt_tc(*h, h->opt.prec, h->counters + kNumCounters, st));
-    h->s_factor = h->opt.prec == KKT_F64_EMULATED ? 0 : 1;
+    KKT_CUDA(enqueue_factor(*h, st));
   }
   h->info.fell_back_fp64 = 0;
-  KKT_CUDA(launch_knorm(*h, st));
   KKT_CUDA(cudaEventRecord(h->ev_f1, st));
   KKT_CUDA(cudaEventRecord(h->ev_done, st));
   h->factored = true;

@@ -315,14 +315,21 @@ cudaError_t launch_dense_solve_ws(Handle& h, const double* t, double* x, double*
 
 // The diagonal-block inverses and reciprocal pivots of the current factor of S
 // (FP64 in S, or FP32 in S32), for the block triangular solves.
+constexpr int kInvSmem = 2 * 64 * 65 * (int)sizeof(double);
+
+// Kernel attributes set once (before any launch, outside stream capture).
+cudaError_t dense_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(k_diag_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_diag_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSmem);
+  return e;
+}
+
 cudaError_t launch_diag_inverse(Handle& h, bool f32, cudaStream_t st) {
   const int n = h.nC;
   if (n == 0) return cudaSuccess;
   const int nb = (n + NB - 1) / NB;
-  const int smem = 2 * 64 * 65 * (int)sizeof(double);
-  cudaError_t e = f32 ? cudaFuncSetAttribute(k_diag_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-                      : cudaFuncSetAttribute(k_diag_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  const int smem = kInvSmem;
   if (f32) k_diag_inverse<float><<<nb, 256, smem, st>>>(h.S32, n, n, 0, h.Xinv, 0, h.Sdinv);
   else k_diag_inverse<double><<<nb, 256, smem, st>>>(h.S, n, n, 0, h.Xinv, 0, h.Sdinv);
   h.launches++;
@@ -333,9 +340,7 @@ cudaError_t launch_diag_inverse(Handle& h, bool f32, cudaStream_t st) {
 // dimension nTa), for the tail's block triangular solves.
 cudaError_t launch_tail_inverse(Handle& h, cudaStream_t st) {
   const int nbT = (h.nT + NB - 1) / NB;
-  const int smem = 2 * 64 * 65 * (int)sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_diag_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  const int smem = kInvSmem;
   k_diag_inverse<double><<<dim3(nbT, h.N), 256, smem, st>>>(h.Tt, h.nT, h.nTa, (int64_t)h.nTa * h.nTa, h.Xtail,
                                                            (int64_t)nbT * 4096, nullptr);
   h.launches++;

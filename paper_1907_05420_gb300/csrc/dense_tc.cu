@@ -445,8 +445,6 @@ cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int npiv, int nb, const TcSt
                       uint8_t* imgB, double* scaleA, double* scaleB, cudaStream_t st) {
   constexpr int A_BYTES = image_bytes(MODE, TM), B_BYTES = image_bytes(MODE, TN);
   const int smem = A_BYTES + B_BYTES;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_update<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
   for (int k0 = 0; k0 < npiv; k0 += TK) {
     const int kb = std::min(TK, npiv - k0);
     k_dense_diag_t<T><<<nb, 256, 0, st>>>(S, n, k0, kb, ts.s, rule, counters);
@@ -472,6 +470,19 @@ cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int npiv, int nb, const TcSt
 }
 
 }  // namespace
+
+// Kernel attributes set once (before any launch, outside stream capture).
+cudaError_t dense_tc_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_update<0, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       image_bytes(0, TM) + image_bytes(0, TN));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_update<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             image_bytes(1, TM) + image_bytes(1, TN));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_update<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             image_bytes(2, TM) + image_bytes(2, TN));
+  return e;
+}
 
 int64_t tc_image_bytes(int n, int mode) {
   const int TI = (n + TM - 1) / TM + 1, TJ = (n + TN - 1) / TN + 1;

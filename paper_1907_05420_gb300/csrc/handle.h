@@ -160,12 +160,22 @@ struct Handle {
   cudaEvent_t ev_fa = nullptr, ev_fb = nullptr;  // phase boundaries inside kkt_factor
   cudaEvent_t ev_s0 = nullptr, ev_s1 = nullptr;  // around kkt_solve
   cudaEvent_t ev_done = nullptr;  // end of the handle's last factor/solve (outlives the caller's stream)
+  // CUDA graph of the factor's launch sequence (captured at the first kkt_factor)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t factor_exec = nullptr;
+  bool graph_failed = false;
+  bool capturing = false;
+  int64_t graph_launches = 0;
   int64_t launches = 0;                          // kernels launched since analyze
   kkt_info info{};
 };
 
 constexpr int kDenseNB = 64;
 
+// ---- kernel attributes, set once per device before any launch ----
+cudaError_t dense_prepare();
+cudaError_t dense_tc_prepare();
+cudaError_t schur_tc_prepare();
 // ---- kernel launchers (factor.cu) ----
 cudaError_t launch_scatter_a(Handle& h, cudaStream_t st);
 cudaError_t launch_factor_levels(Handle& h, cudaStream_t st);

@@ -182,14 +182,22 @@ __global__ void __launch_bounds__(128, 1) k_contract_g_tc(const double* __restri
 
 }  // namespace
 
+// Kernel attributes set once (before any launch, outside stream capture).
+cudaError_t schur_tc_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(k_contract_g_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       2 * (GM / 8) * (GK / 8) * 128);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_contract_g_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             2 * (GM / 8) * (GK / 4) * 128);
+  return e;
+}
+
 bool contract_g_tc_supported(const Handle& h) { return h.cpl.k > 0 && h.cpl.k <= GM && h.cpl.nw > 0; }
 
 cudaError_t launch_contract_g_tc(Handle& h, int bf16, cudaStream_t st) {
   const int nchunks = h.g_nchunks, npos = h.g_nchunks_pos;
   const int smem = 2 * (GM / 8) * (GK / (16 / (bf16 ? 2 : 4))) * 128;
-  cudaError_t e = bf16 ? cudaFuncSetAttribute(k_contract_g_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-                       : cudaFuncSetAttribute(k_contract_g_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   if (bf16)
     k_contract_g_tc<1><<<h.N, 128, smem, st>>>(h.W, h.Lx, h.sym.panel_total, h.d.w_dpos, h.d.g_rows, nchunks, npos,
                                            h.cpl.nw, h.cpl.k, h.G, h.dev_err);
