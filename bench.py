@@ -242,38 +242,55 @@ def run_serve(args):
            "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
            "config": {"workload": f"serve: {args.serve_pool} resident patterns from the size mix; "
                                   "Poisson arrivals; every request carries fresh values",
-                      "slots": args.serve_slots, "seconds_per_rate": args.serve_seconds}}
+                      "slots": args.serve_slots, "seconds_per_rate": args.serve_seconds,
+                      "backlog": args.serve_backlog or 4 * args.serve_slots}}
     for prec in args.batch_precs.split(","):
         probs, hs, vals, xs = _mix_problems(args.serve_pool, prec)
         srv = B.KKTServer(slots=args.serve_slots,
                           device_budget_bytes=int(0.8 * torch.cuda.mem_get_info()[0]))
         rng = np.random.default_rng(4242)
         res = {}
+        backlog = args.serve_backlog or 4 * args.serve_slots
         for rate in [float(r) for r in args.rates.split(",")]:
-            lats, ids = [], []
-            t_end = time.perf_counter() + 1.0 + args.serve_seconds
-            t_next = time.perf_counter()
-            t_measure = t_next + 1.0
-            measured = []
+            # Poisson arrivals for 1 s of warm-up plus the measured window; a
+            # request that finds `backlog` requests outstanding is shed (load
+            # shedding keeps the queue, and so the drain after the window, bounded)
+            lats, outstanding = [], {}
+            shed = offered = 0
+            t0 = time.perf_counter()
+            t_measure, t_end = t0 + 1.0, t0 + 1.0 + args.serve_seconds
+            t_next = t0
+
+            def reap(block):
+                for rid in list(outstanding):
+                    got = srv.wait(rid) if block else srv.poll(rid)
+                    if got is None:
+                        continue
+                    in_window = outstanding.pop(rid)
+                    if in_window:
+                        lats.append(got[1])
+
             while time.perf_counter() < t_end:
                 now = time.perf_counter()
                 if now < t_next:
-                    time.sleep(min(t_next - now, 0.001))
+                    time.sleep(min(t_next - now, 0.0005))
+                    continue
+                t_next += rng.exponential(1.0 / rate)
+                in_window = now >= t_measure
+                offered += in_window
+                reap(False)
+                if len(outstanding) >= backlog:
+                    shed += in_window
                     continue
                 k = int(rng.integers(0, len(probs)))
                 a, b, c, r = vals[k]
                 x = torch.empty_like(r)
-                ids.append((srv.submit(hs[k], a, b, c, r, x), now >= t_measure, now))
-                t_next += rng.exponential(1.0 / rate)
-            t_last = time.perf_counter()
-            for rid, in_window, _ in ids:
-                st, lat = srv.wait(rid)
-                if in_window:
-                    lats.append(lat)
-                    measured.append(rid)
+                outstanding[srv.submit(hs[k], a, b, c, r, x)] = in_window
+            reap(True)
             t_done = time.perf_counter()
             n = len(lats)
-            res[str(int(rate))] = {"requests": n, "solves_per_s": n / max(1e-9, (t_done - t_last) + args.serve_seconds),
+            res[str(int(rate))] = {"offered": offered, "served": n, "shed": shed,
+                                   "solves_per_s": n / max(1e-9, t_done - t_measure),
                                    "p50_ms": float(np.percentile(lats, 50)) if n else None,
                                    "p99_ms": float(np.percentile(lats, 99)) if n else None}
         srv.close()
@@ -305,6 +322,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--rates", default="50,100,200,500,1000,2000")
+    ap.add_argument("--serve-backlog", type=int, default=0,
+                    help="requests outstanding before new arrivals are shed (default 4 x slots)")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -95,7 +95,9 @@ typedef struct {
   int32_t max_refine;  /* refinement steps at most (10) */
   double pivot_eps;    /* |d| < pivot_eps * ||A_i||_max is replaced by +-pivot_eps * ||A_i||_max
                           with the expected sign and counted; 0 turns the perturbation off */
-  int32_t use_graphs;  /* capture the factor/solve launch sequences in CUDA graphs */
+  int32_t use_graphs;  /* capture the device work of kkt_factor after the input copies as a CUDA
+                          graph at the handle's first kkt_factor and replay it on later calls (the
+                          solve and its refinement launch directly).  Default 1. */
   int32_t fp64_fallback; /* refactor S in FP64 when refinement stalls in a reduced mode */
   int32_t reduced_contraction; /* KKT_TF32/KKT_BF16 only: also run the Schur contraction
                                   G_i = W_i^T D_i^{-1} W_i on the tensor cores in that precision

@@ -247,6 +247,9 @@ def kkt_batch_factor_solve(handles, a_vals, b_vals, c_vals, rhs, x, streams=8):
     return list(st)
 
 
+KKT_ERR_STATE = 8
+
+
 class KKTServer:
     """Continuous-batching request loop (kkt_server_*)."""
 
@@ -268,6 +271,16 @@ class KKTServer:
     def wait(self, rid):
         st, lat = C.c_int(), C.c_double()
         _check(load().kkt_server_poll(self.s, int(rid), 1, C.byref(st), C.byref(lat)))
+        self._keep.pop(rid, None)
+        return st.value, lat.value
+
+    def poll(self, rid):
+        """(status, latency_ms) if request rid has finished, else None."""
+        st, lat = C.c_int(), C.c_double()
+        r = load().kkt_server_poll(self.s, int(rid), 0, C.byref(st), C.byref(lat))
+        if r == KKT_ERR_STATE:
+            return None
+        _check(r)
         self._keep.pop(rid, None)
         return st.value, lat.value
 
