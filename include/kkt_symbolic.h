@@ -29,7 +29,8 @@ kkt_symbolic* kkt_symbolic_create(int32_t nA, int32_t nP, const int32_t* a_rowpt
  * upd_src, upd_r0, upd_r1, upd_reloff, upd_rel, E, e_t, wpos, sn_wrow, s_key,
  * panel_rend, jlo, jhi, colcount, upd_ntail, stats (n, nsuper, nlevels,
  * panel_total, nnzL, k, nw, tail_sn, tail_col, nw_before_tail), tail_wrow
- * (per tail column its W row, -1 outside the reach).  The dense tail is
+ * (per tail column its W row, -1 outside the reach), wt_ptr / wt_idx (per
+ * supernode the columns of W that are nonzero on it).  The dense tail is
  * chosen as kkt_analyze chooses it with the dense_tail option on. */
 int64_t kkt_symbolic_get(const kkt_symbolic* sym, const char* name, int64_t* out);
 

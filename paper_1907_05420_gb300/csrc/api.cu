@@ -49,7 +49,8 @@ void free_all(Handle* h) {
                   h->d.b_blockptr, h->d.e_t, h->d.e_block, h->d.wpos, h->d.sn_wrow, h->d.w_dpos,
                   h->d.w_col, h->d.reach_lvl_sn, h->d.s_key, h->d.s_ptr, h->d.s_e1, h->d.s_e2,
                   h->d.t_ptr, h->d.t_e, h->d.bt_ptr, h->d.E, h->d.g_rows, h->d.trsv_jlo, h->d.trsv_jhi,
-                  h->d.flvl_sn, h->d.twork, h->d.upd_ntail, h->d.reach_lvl_sn_nt, h->d.tail_sn_list, h->d.tail_wrow, h->Xinv, h->Sdinv, h->wdinv, h->Xtail, h->Tt, h->TY, h->t_imgA, h->t_imgB,
+                  h->d.flvl_sn, h->d.twork, h->d.upd_ntail, h->d.reach_lvl_sn_nt, h->d.tail_sn_list, h->d.tail_wrow, h->d.wt_ptr, h->d.wt_idx,
+                  h->d.g_key, h->d.g_ptr, h->d.g_row, h->Xinv, h->Sdinv, h->wdinv, h->Xtail, h->Tt, h->TY, h->t_imgA, h->t_imgB,
                   h->t_scaleA, h->t_scaleB, h->Lx, h->a_vals, h->b_vals,
                   h->c_vals, h->anorm, h->W, h->G, h->S, h->Ypanel, h->knorm, h->counters, h->r,
                   h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red,
@@ -239,6 +240,22 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   for (int s = S.tail_sn; s < S.nsuper; s++)
     if (C.sn_wrow[s] >= 0) tail_sn_list.push_back(s);  // tail supernodes in the reach of E
   h->tail_reach_sn = (int32_t)tail_sn_list.size();
+  // W solve: per level, the most 32-column chunks of any of its supernodes
+  auto chunks_of = [&](const std::vector<int32_t>& ptr, const std::vector<int32_t>& sn, std::vector<int32_t>& out) {
+    out.assign(S.nlevels, 1);
+    for (int l = 0; l < S.nlevels; l++)
+      for (int q = ptr[l]; q < ptr[l + 1]; q++) {
+        const int s = sn[q], nts = C.wt_ptr[s + 1] - C.wt_ptr[s];
+        out[l] = std::max(out[l], (nts + 31) / 32);
+      }
+  };
+  chunks_of(h->reach_lvl_ptr, C.reach_lvl_sn, h->reach_lvl_chunks);
+  chunks_of(h->reach_lvl_ptr_nt, reach_lvl_sn_nt, h->reach_lvl_chunks_nt);
+  // sparse contraction over the W rows outside the (augmented) tail
+  std::vector<int32_t> g_key, g_row;
+  std::vector<int64_t> g_ptr;
+  g_gather(S, C, h->tail_aug ? S.tail_sn : S.nsuper, g_key, g_ptr, g_row);
+  h->g_nkeys = (int64_t)g_key.size();
 
   // factor work items: 64-row tiles of every supernode outside the dense tail,
   // grouped by level, then those of the tail supernodes; for every (tile,
@@ -385,6 +402,11 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   UP(reach_lvl_sn_nt, reach_lvl_sn_nt);
   UP(tail_sn_list, tail_sn_list);
   UP(tail_wrow, tail_wrow);
+  UP(wt_ptr, C.wt_ptr);
+  UP(wt_idx, C.wt_idx);
+  UP(g_key, g_key);
+  UP(g_ptr, g_ptr);
+  UP(g_row, g_row);
   UP(s_key, C.s_key);
   UP(s_ptr, C.s_ptr);
   UP(s_e1, C.s_e1);
@@ -462,6 +484,8 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   if (e == cudaSuccess)
     e = cudaMemset(h->trsv_flags, 0, sizeof(int) * (size_t)std::max(1, 2 * ((h->nC + kDenseNB - 1) / kDenseNB)));
   if (e == cudaSuccess) e = cudaMemset(h->dev_err, 0, sizeof(int));
+  // W's structurally zero entries are never written: clear it once
+  if (e == cudaSuccess) e = cudaMemset(h->W, 0, sizeof(double) * (size_t)std::max<int64_t>(1, (int64_t)C.nw * C.k * h->N));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->host_red, sizeof(double) * 8);
   for (cudaEvent_t* ev : {&h->ev_f0, &h->ev_f1, &h->ev_fa, &h->ev_fb, &h->ev_s0, &h->ev_s1, &h->ev_done})
     if (e == cudaSuccess) e = cudaEventCreate(ev);

@@ -75,6 +75,11 @@ struct DevSym {
   int32_t* reach_lvl_sn_nt = nullptr;  // reach supernodes outside the tail, by level
   int32_t* tail_sn_list = nullptr;     // the tail supernodes in the reach of E
   int32_t* tail_wrow = nullptr;        // per tail column: its W row (-1 outside the reach)
+  int32_t* wt_ptr = nullptr;           // per supernode: the columns of W on it (wt_idx)
+  int32_t* wt_idx = nullptr;
+  int32_t* g_key = nullptr;            // sparse contraction: entries t1 * k + t2 of G
+  int64_t* g_ptr = nullptr;            // their rows g_row[g_ptr[e] .. g_ptr[e+1])
+  int32_t* g_row = nullptr;
 };
 
 // Counters written by the kernels (device, int64).
@@ -100,6 +105,8 @@ struct Handle {
   int32_t nw_nt = 0;                   // W rows outside the tail (the first ones)
   int32_t tail_reach_sn = 0;           // tail supernodes in the reach of E
   std::vector<int32_t> reach_lvl_ptr_nt;  // reach supernodes outside the tail per level
+  std::vector<int32_t> reach_lvl_chunks, reach_lvl_chunks_nt;  // W solve: 32-column chunks per level
+  int64_t g_nkeys = 0;                 // nonzero entries of the sparse contraction
   int32_t tail_items = 0;              // factor work items of the tail supernodes
 
   // numeric buffers

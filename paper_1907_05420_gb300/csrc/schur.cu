@@ -18,11 +18,14 @@ namespace kkt {
 
 namespace {
 
-// One CTA per (reach supernode, block, chunk of 32 right-hand sides): the
-// columns of W are independent, so chunks spread the narrow top levels of the
-// tree over more SMs.  TAIL_INIT: for a supernode of the augmented tail, only
-// the right-hand side minus the updates from outside the tail (the rows Z the
-// tail factor is augmented with); its triangular solve is the tail factor's.
+// Column t of W is L^{-1} P^T e_{E_t}, nonzero only on the supernodes of the
+// path from E_t's supernode to the root.  One CTA per (reach supernode s,
+// block, chunk of 32 of s's columns T_s): s computes only those columns (its
+// other entries stay zero from the clearing at analysis), and the update from
+// a descendant d touches only d's columns T_d, a subset of T_s.
+// TAIL_INIT: for a supernode of the augmented tail, all k columns of the
+// right-hand side minus the updates from outside the tail (the rows Z the tail
+// factor is augmented with); its triangular solve is the tail factor's.
 constexpr int kWChunk = 32;
 
 template <bool TAIL_INIT>
@@ -30,15 +33,22 @@ __global__ void __launch_bounds__(128) k_w_solve(const int32_t* __restrict__ sn_
                                                  const double* __restrict__ Lx, int64_t pt,
                                                  double* __restrict__ W, int nw, int k) {
   const int s = sn_list[blockIdx.x], b = blockIdx.y;
-  const int t0 = blockIdx.z * kWChunk, nt = min(kWChunk, k - t0);
+  const int32_t* Ts = d.wt_idx + d.wt_ptr[s];
+  const int nts = d.wt_ptr[s + 1] - d.wt_ptr[s];
+  const int c0 = blockIdx.z * kWChunk;
+  if (!TAIL_INIT && c0 >= nts) return;
+  const int nt = TAIL_INIT ? k : min(kWChunk, nts - c0);
+  const int32_t* tc = Ts + c0;                       // this chunk's columns (sorted)
+  const int lo = TAIL_INIT ? 0 : tc[0], hi = TAIL_INIT ? k - 1 : tc[nt - 1];
   const int m = (int)(d.sn_rowptr[s + 1] - d.sn_rowptr[s]);
   const int f = d.sn_first[s], w = d.sn_first[s + 1] - f;
   const int ws = d.sn_wrow[s];
   const double* P = Lx + b * pt + d.sn_valoff[s];
-  double* Wb = W + (int64_t)b * nw * k + t0;
+  double* Wb = W + (int64_t)b * nw * k;
   for (int q = threadIdx.x; q < w * nt; q += blockDim.x) {
-    const int c = q / nt, t = q - c * nt;
-    Wb[(int64_t)(ws + c) * k + t] = d.wpos[t0 + t] == ws + c ? 1.0 : 0.0;
+    const int c = q / nt, jt = q - c * nt;
+    const int t = TAIL_INIT ? jt : tc[jt];
+    Wb[(int64_t)(ws + c) * k + t] = d.wpos[t] == ws + c ? 1.0 : 0.0;
   }
   __syncthreads();
   const int64_t u_end = TAIL_INIT ? d.upd_ptr[s] + d.upd_ntail[s] : d.upd_ptr[s + 1];
@@ -46,14 +56,17 @@ __global__ void __launch_bounds__(128) k_w_solve(const int32_t* __restrict__ sn_
     const int dd = d.upd_src[u];
     const int wrd = d.sn_wrow[dd];
     if (wrd < 0) continue;  // descendant outside the reach: its W rows are zero
+    const int32_t* Td = d.wt_idx + d.wt_ptr[dd];
+    const int ntd = d.wt_ptr[dd + 1] - d.wt_ptr[dd];
     const int r0 = d.upd_r0[u], r1 = d.upd_r1[u];
     const int md = (int)(d.sn_rowptr[dd + 1] - d.sn_rowptr[dd]);
     const int wd = d.sn_first[dd + 1] - d.sn_first[dd];
     const double* Pd = Lx + b * pt + d.sn_valoff[dd];
     const int32_t* Rd = d.sn_rows + d.sn_rowptr[dd];
-    const int total = (r1 - r0) * nt;
+    const int total = (r1 - r0) * ntd;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
-      const int j = r0 + q / nt, t = q % nt;
+      const int j = r0 + q / ntd, t = Td[q % ntd];
+      if (t < lo || t > hi) continue;  // a column of another chunk
       double acc = 0.0;
       for (int kk = 0; kk < wd; kk++) acc += Pd[(int64_t)kk * md + j] * Wb[(int64_t)(wrd + kk) * k + t];
       Wb[(int64_t)(ws + Rd[j] - f) * k + t] -= acc;
@@ -64,10 +77,35 @@ __global__ void __launch_bounds__(128) k_w_solve(const int32_t* __restrict__ sn_
   for (int c = 0; c + 1 < w; c++) {
     const int total = (w - 1 - c) * nt;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
-      const int c2 = c + 1 + q / nt, t = q % nt;
+      const int c2 = c + 1 + q / nt, t = tc[q % nt];
       Wb[(int64_t)(ws + c2) * k + t] -= P[(int64_t)c * m + c2] * Wb[(int64_t)(ws + c) * k + t];
     }
     __syncthreads();
+  }
+}
+
+// G_b = W_b^T D_b^{-1} W_b over the rows outside the tail, by structure: one
+// thread per (nonzero entry t1 >= t2 of G, block) sums its rows in order
+// (every other product is an exact zero).
+__global__ void k_contract_g_sparse(const int32_t* __restrict__ g_key, const int64_t* __restrict__ g_ptr,
+                                    const int32_t* __restrict__ g_row, int64_t nkeys,
+                                    const double* __restrict__ W, const double* __restrict__ wdinv, int nw,
+                                    int k, int N, double* __restrict__ G) {
+  const int64_t total = nkeys * N;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = q / nkeys, e = q - b * nkeys;
+    const int key = g_key[e], t1 = key / k, t2 = key - t1 * k;
+    const double* Wb = W + b * nw * k;
+    const double* db = wdinv + b * nw;
+    double acc = 0.0;
+    for (int64_t r = g_ptr[e]; r < g_ptr[e + 1]; r++) {
+      const int row = g_row[r];
+      acc += Wb[(int64_t)row * k + t1] * db[row] * Wb[(int64_t)row * k + t2];
+    }
+    double* Gb = G + b * k * k;
+    Gb[(int64_t)t1 * k + t2] = acc;
+    Gb[(int64_t)t2 * k + t1] = acc;
   }
 }
 
@@ -185,12 +223,13 @@ __global__ void k_assemble_s(const int64_t* __restrict__ s_key, const int64_t* _
 
 namespace {
 
-cudaError_t w_levels(Handle& h, const std::vector<int32_t>& lvl_ptr, const int32_t* lvl_sn, cudaStream_t st) {
+cudaError_t w_levels(Handle& h, const std::vector<int32_t>& lvl_ptr, const std::vector<int32_t>& lvl_chunks,
+                     const int32_t* lvl_sn, cudaStream_t st) {
   const int k = h.cpl.k;
   for (int l = 0; l < h.sym.nlevels; l++) {
     const int s0 = lvl_ptr[l], s1 = lvl_ptr[l + 1];
     if (s1 == s0) continue;
-    dim3 grid(s1 - s0, h.N, (k + kWChunk - 1) / kWChunk);
+    dim3 grid(s1 - s0, h.N, lvl_chunks[l]);
     k_w_solve<false><<<grid, 128, 0, st>>>(lvl_sn + s0, h.d, h.Lx, h.sym.panel_total, h.W, h.cpl.nw, k);
     h.launches++;
   }
@@ -202,7 +241,7 @@ cudaError_t w_levels(Handle& h, const std::vector<int32_t>& lvl_ptr, const int32
 cudaError_t launch_w_solve(Handle& h, cudaStream_t st) {
   const int k = h.cpl.k;
   if (k == 0 || h.cpl.nw == 0 || h.tail_aug) return cudaSuccess;  // augmented: done before the tail
-  return w_levels(h, h.reach_lvl_ptr, h.d.reach_lvl_sn, st);
+  return w_levels(h, h.reach_lvl_ptr, h.reach_lvl_chunks, h.d.reach_lvl_sn, st);
 }
 
 // Augmented tail: the W rows outside the tail, then the tail's rows Z (the
@@ -210,11 +249,11 @@ cudaError_t launch_w_solve(Handle& h, cudaStream_t st) {
 // factor that completes them.
 cudaError_t launch_w_solve_before_tail(Handle& h, cudaStream_t st) {
   const int k = h.cpl.k;
-  cudaError_t e = w_levels(h, h.reach_lvl_ptr_nt, h.d.reach_lvl_sn_nt, st);
+  cudaError_t e = w_levels(h, h.reach_lvl_ptr_nt, h.reach_lvl_chunks_nt, h.d.reach_lvl_sn_nt, st);
   if (e != cudaSuccess) return e;
   const int nts = h.tail_reach_sn;
   if (nts == 0) return cudaSuccess;
-  dim3 grid(nts, h.N, (k + kWChunk - 1) / kWChunk);
+  dim3 grid(nts, h.N, 1);
   k_w_solve<true><<<grid, 128, 0, st>>>(h.d.tail_sn_list, h.d, h.Lx, h.sym.panel_total, h.W, h.cpl.nw, k);
   h.launches++;
   return cudaGetLastError();
@@ -241,14 +280,12 @@ cudaError_t launch_add_tail_g(Handle& h, cudaStream_t st) {
 cudaError_t launch_contract_g(Handle& h, cudaStream_t st) {
   const int k = h.cpl.k;
   if (k == 0) return cudaSuccess;
-  const int nrows = h.nw_nt;
-  cudaError_t e = cudaSuccess;
-  if (nrows == 0) {
-    e = cudaMemsetAsync(h.G, 0, sizeof(double) * (size_t)h.N * k * k, st);
-  } else {
-    const int T = (k + 31) / 32;
-    dim3 grid(T * (T + 1) / 2, h.N);
-    k_contract_g_f64<<<grid, 256, 0, st>>>(h.W, h.wdinv, h.cpl.nw, nrows, k, h.G);
+  cudaError_t e = cudaMemsetAsync(h.G, 0, sizeof(double) * (size_t)h.N * k * k, st);
+  const int64_t nkeys = (int64_t)h.g_nkeys;
+  if (e == cudaSuccess && nkeys > 0) {
+    const int64_t total = nkeys * h.N;
+    k_contract_g_sparse<<<(int)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, st>>>(
+        h.d.g_key, h.d.g_ptr, h.d.g_row, nkeys, h.W, h.wdinv, h.cpl.nw, k, h.N, h.G);
     h.launches++;
     e = cudaGetLastError();
   }

@@ -505,6 +505,16 @@ std::string analyze_coupling(const Symbolic& S, int32_t N, int32_t nC, const int
     int32_t j = S.iperm[C.E[t]], s = S.col_sn[j];
     C.wpos[t] = C.sn_wrow[s] + (j - S.sn_first[s]);
   }
+  // columns of W per supernode: walk each column's path to the root
+  {
+    std::vector<std::vector<int32_t>> cols(S.nsuper);
+    for (int32_t t = 0; t < C.k; t++)
+      for (int32_t s = S.col_sn[S.iperm[C.E[t]]]; s >= 0; s = S.sn_parent[s]) cols[s].push_back(t);
+    C.wt_ptr.assign(S.nsuper + 1, 0);
+    for (int32_t s = 0; s < S.nsuper; s++) C.wt_ptr[s + 1] = C.wt_ptr[s] + (int32_t)cols[s].size();
+    C.wt_idx.reserve(C.wt_ptr[S.nsuper]);
+    for (int32_t s = 0; s < S.nsuper; s++) C.wt_idx.insert(C.wt_idx.end(), cols[s].begin(), cols[s].end());
+  }
   C.reach_lvl_ptr.assign(S.nlevels + 1, 0);
   for (int32_t s = 0; s < S.nsuper; s++)
     if (in[s]) C.reach_lvl_ptr[S.sn_level[s] + 1]++;
@@ -626,6 +636,34 @@ int32_t tail_w_rows(const Symbolic& S, const Coupling& C, std::vector<int32_t>& 
       wrow_of_tail_col[j - S.tail_col] = C.sn_wrow[s] + (j - S.sn_first[s]);
   }
   return before;
+}
+
+void g_gather(const Symbolic& S, const Coupling& C, int32_t tail_sn, std::vector<int32_t>& g_key,
+              std::vector<int64_t>& g_ptr, std::vector<int32_t>& g_row) {
+  std::vector<std::pair<int32_t, int32_t>> recs;  // (key, W row)
+  for (int32_t s = 0; s < tail_sn; s++) {
+    if (C.sn_wrow[s] < 0) continue;
+    const int32_t* T = C.wt_idx.data() + C.wt_ptr[s];
+    const int32_t nt = C.wt_ptr[s + 1] - C.wt_ptr[s];
+    for (int32_t c = 0; c < S.sn_first[s + 1] - S.sn_first[s]; c++)
+      for (int32_t a = 0; a < nt; a++)
+        for (int32_t b = 0; b <= a; b++) {
+          const int32_t t1 = std::max(T[a], T[b]), t2 = std::min(T[a], T[b]);
+          recs.push_back({t1 * C.k + t2, C.sn_wrow[s] + c});
+        }
+  }
+  std::sort(recs.begin(), recs.end());
+  g_key.clear();
+  g_ptr.assign(1, 0);
+  g_row.clear();
+  for (size_t i = 0; i < recs.size(); i++) {
+    if (i == 0 || recs[i].first != recs[i - 1].first) {
+      if (i > 0) g_ptr.push_back((int64_t)g_row.size());
+      g_key.push_back(recs[i].first);
+    }
+    g_row.push_back(recs[i].second);
+  }
+  if (!recs.empty()) g_ptr.push_back((int64_t)g_row.size());
 }
 
 }  // namespace kkt

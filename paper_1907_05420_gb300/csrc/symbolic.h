@@ -102,7 +102,19 @@ struct Coupling {
   std::vector<int32_t> t_e;          // B entries of that column, block order
   // v_i = M_i x_g: B entries of block i with index t lie in bt_ptr[i*(k+1)+t] ..
   std::vector<int32_t> bt_ptr;       // N * (k + 1)
+  // Column t of W is L^{-1} P^T e_{E_t}: nonzero only on the supernodes of
+  // the elimination-tree path from E_t's supernode to the root.  Per supernode
+  // the columns whose path it is on, sorted (empty outside the reach).
+  std::vector<int32_t> wt_ptr;       // nsuper + 1
+  std::vector<int32_t> wt_idx;
 };
+
+// Gather lists of the contraction G = W^T D^{-1} W over the W rows of the
+// supernodes before `tail_sn`, by structure: entry (t1 >= t2) collects the
+// rows whose supernode has both t1 and t2 among its columns.  Keys t1 * k + t2
+// sorted; rows ascending per key.
+void g_gather(const Symbolic& S, const Coupling& C, int32_t tail_sn, std::vector<int32_t>& g_key,
+              std::vector<int64_t>& g_ptr, std::vector<int32_t>& g_row);
 
 std::string analyze_coupling(const Symbolic& S, int32_t N, int32_t nC, const int32_t* b_blockptr,
                              const int32_t* b_row, const int32_t* b_col, Coupling& out);

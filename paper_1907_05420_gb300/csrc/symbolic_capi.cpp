@@ -72,6 +72,8 @@ int64_t kkt_symbolic_get(const kkt_symbolic* sym, const char* name, int64_t* out
   if (n == "jlo") return copy_out(in->jlo, out);
   if (n == "jhi") return copy_out(in->jhi, out);
   if (n == "colcount") return copy_out(S.colcount, out);
+  if (n == "wt_ptr") return copy_out(C.wt_ptr, out);
+  if (n == "wt_idx") return copy_out(C.wt_idx, out);
   if (n == "upd_ntail") return copy_out(S.upd_ntail, out);
   if (n == "tail_wrow") {
     std::vector<int32_t> tw;

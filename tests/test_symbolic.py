@@ -56,7 +56,7 @@ def analyze(p, hint=True):
     try:
         for name in ("perm partner sn_first sn_rowptr sn_rows sn_valoff sn_parent sn_level a_map "
                      "upd_ptr upd_src upd_r0 upd_r1 upd_reloff upd_rel E e_t wpos sn_wrow s_key "
-                     "panel_rend jlo jhi colcount upd_ntail tail_wrow stats").split():
+                     "panel_rend jlo jhi colcount upd_ntail tail_wrow wt_ptr wt_idx stats").split():
             n = L.kkt_symbolic_get(h, name.encode(), None)
             assert n >= 0, name
             a = np.zeros(n, dtype=np.int64)
@@ -418,3 +418,33 @@ def test_tail_w_rows(name):
     rows = tw[tw >= 0]
     assert np.all(rows >= s["nw_before_tail"]) and len(set(rows.tolist())) == len(rows)
     assert len(rows) == s["nw"] - s["nw_before_tail"]
+
+
+@pytest.mark.parametrize("name", ["aug14", "tiny", "small", "grid30_n24", "storage20"])
+def test_w_column_sets_match_the_structure_of_l_inverse(name):
+    """Column t of W = L^{-1} P^T e_{E_t} is structurally nonzero exactly on the
+    rows reachable from E_t's pivot in the graph of L; a supernode carries
+    column t when one of its columns is reachable.  Checked with the fill
+    pattern from brute-force elimination."""
+    p, s = _case(name)
+    pat = _fill_pattern(p, s["perm"])
+    iperm = np.empty(p.nA, dtype=np.int64)
+    iperm[s["perm"]] = np.arange(p.nA)
+    first = s["sn_first"]
+    col_sn = np.repeat(np.arange(s["nsuper"]), np.diff(first))
+    want = [set() for _ in range(s["nsuper"])]
+    for t, r in enumerate(s["E"].tolist()):
+        seen, stack = set(), [int(iperm[r])]
+        while stack:
+            j = stack.pop()
+            if j in seen:
+                continue
+            seen.add(j)
+            stack.extend(pat[j])
+        for j in seen:
+            want[col_sn[j]].add(t)
+    ptr, idx = s["wt_ptr"], s["wt_idx"]
+    for q in range(s["nsuper"]):
+        got = idx[ptr[q]:ptr[q + 1]].tolist()
+        assert got == sorted(want[q])
+        assert (len(got) > 0) == (s["sn_wrow"][q] >= 0)
