@@ -118,8 +118,14 @@ typedef struct {
                            0: off; 1: trailing updates in FP64 on the CUDA cores; 2: trailing
                            updates in emulated FP64 on the tensor cores (7 base-256 digit
                            slices per operand, as in KKT_F64_EMULATED); -1 (default): 2 in the
-                           KKT_TF32, KKT_BF16 and KKT_F64_EMULATED modes, 0 in KKT_FP64. */
-  int32_t reserved;
+                           KKT_TF32, KKT_BF16 and KKT_F64_EMULATED modes, 1 in KKT_FP64 (all its
+                           arithmetic stays FP64 on the CUDA cores). */
+  int32_t autotune;     /* choose the size of the dense tail by timing: the tail is the longest suffix
+                           whose dense flops are at most r times its sparse flops; with autotune the
+                           distinct tails of r in {1, 1.25, 1.5, 2, 3} are analysed and timed once each
+                           (one kkt_factor on the values hint in every block, B = 0, C = I) and the
+                           fastest is kept.  Needs a_vals_hint; adds those factorizations to
+                           kkt_analyze.  Default 0 (r = 1.5). */
 } kkt_options;
 
 typedef struct {
@@ -146,6 +152,9 @@ typedef struct {
   int32_t dense_tail_cols;      /* columns of the dense tail of each block factor (0 = none) */
   int32_t tail_augmented;       /* 1 if the tail factor also forms the tail's rows of W and its
                                    share of G (the k coupling rows appended to it) */
+  double tail_ratio;            /* cost ratio r the dense tail was chosen with (0 without a tail) */
+  int32_t autotune_candidates;  /* distinct tails timed by the autotuner (0 without autotune) */
+  int32_t reserved_info;
 } kkt_info;
 
 /* Default options: FP64, refine_tol 1e-10, max_refine 10, pivot_eps 1e-20,

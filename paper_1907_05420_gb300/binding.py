@@ -41,7 +41,7 @@ class kkt_options(C.Structure):
     _fields_ = [("prec", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int32),
                 ("pivot_eps", C.c_double), ("use_graphs", C.c_int32),
                 ("fp64_fallback", C.c_int32), ("reduced_contraction", C.c_int32),
-                ("structured_s", C.c_int32), ("dense_tail", C.c_int32), ("reserved", C.c_int32)]
+                ("structured_s", C.c_int32), ("dense_tail", C.c_int32), ("autotune", C.c_int32)]
 
 
 class kkt_info(C.Structure):
@@ -54,7 +54,8 @@ class kkt_info(C.Structure):
                 ("factor_flops", C.c_double), ("device_bytes", C.c_int64),
                 ("ms_block_factor", C.c_double), ("ms_schur_assembly", C.c_double),
                 ("ms_dense_factor", C.c_double), ("ms_solve_device", C.c_double),
-                ("n_launches", C.c_int64), ("dense_tail_cols", C.c_int32), ("tail_augmented", C.c_int32)]
+                ("n_launches", C.c_int64), ("dense_tail_cols", C.c_int32), ("tail_augmented", C.c_int32),
+                ("tail_ratio", C.c_double), ("autotune_candidates", C.c_int32), ("reserved_info", C.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

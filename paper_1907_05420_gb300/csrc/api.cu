@@ -160,11 +160,12 @@ const char* kkt_status_string(kkt_status s) {
 
 const char* kkt_last_error(void) { return g_last_error.c_str(); }
 
-kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handle** out) {
-  if (!pat || !out) {
-    set_error("kkt_analyze: null argument");
-    return KKT_ERR_INVALID;
-  }
+}  // extern "C"
+
+namespace {
+
+// One analysis with the dense tail chosen at cost ratio `tail_ratio`.
+kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double tail_ratio, kkt_handle** out) {
   *out = nullptr;
   if (!pat->a_rowptr || !pat->a_col || !pat->b_blockptr || (pat->c_kind != 0 && pat->c_kind != 1) ||
       pat->N <= 0 || pat->nA <= 0 || pat->nC < 0) {
@@ -203,13 +204,14 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   }
   // dense tail: -1 (default) picks the emulated tail in the reduced-precision
   // modes and none in the plain FP64 mode
-  h->tail_mode = h->opt.dense_tail < 0 ? (h->opt.prec == KKT_FP64 ? 0 : 2) : h->opt.dense_tail;
+  h->tail_mode = h->opt.dense_tail < 0 ? (h->opt.prec == KKT_FP64 ? 1 : 2) : h->opt.dense_tail;
   if (h->tail_mode < 0 || h->tail_mode > 2) {
     set_error("kkt_analyze: dense_tail must be -1, 0, 1 or 2");
     delete h;
     return KKT_ERR_INVALID;
   }
-  if (h->tail_mode) choose_tail(h->sym, h->N, kTailMaxBytes, kTailMinCols);
+  h->tail_ratio = tail_ratio;
+  if (h->tail_mode) choose_tail(h->sym, h->N, kTailMaxBytes, kTailMinCols, tail_ratio);
   else choose_tail(h->sym, h->N, 0, 0);  // no tail fits in 0 bytes
   const Symbolic& S = h->sym;
   const Coupling& C = h->cpl;
@@ -512,6 +514,80 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   return KKT_OK;
 }
 
+// Device time of one kkt_factor (the second of two, after the graph capture
+// of the first) on representative values: every block takes the values hint,
+// B is zero, C the identity.
+double time_factor(kkt_handle* hh, const kkt_pattern* pat) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  const int64_t nA_vals = h->nnzA * h->N, nb = std::max<int64_t>(1, h->nnzB);
+  const int64_t nc = h->c_kind == 0 ? h->nC : (int64_t)h->nC * h->nC;
+  std::vector<double> a((size_t)nA_vals), b((size_t)nb, 0.0), c((size_t)std::max<int64_t>(1, nc), 0.0);
+  for (int i = 0; i < h->N; i++) std::copy(pat->a_vals_hint, pat->a_vals_hint + h->nnzA, a.begin() + i * h->nnzA);
+  for (int64_t q = 0; q < h->nC; q++) c[h->c_kind == 0 ? q : q * h->nC + q] = 1.0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double ms = -1.0;
+  if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+      kkt_factor(hh, a.data(), b.data(), c.data(), 0, nullptr) == KKT_OK && cudaDeviceSynchronize() == cudaSuccess &&
+      cudaEventRecord(e0, nullptr) == cudaSuccess && kkt_factor(hh, a.data(), b.data(), c.data(), 0, nullptr) == KKT_OK &&
+      cudaEventRecord(e1, nullptr) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess) {
+    float f = 0.f;
+    if (cudaEventElapsedTime(&f, e0, e1) == cudaSuccess) ms = f;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  (void)cudaGetLastError();
+  return ms;
+}
+
+}  // namespace
+
+extern "C" {
+
+kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handle** out) {
+  if (!pat || !out) {
+    set_error("kkt_analyze: null argument");
+    return KKT_ERR_INVALID;
+  }
+  *out = nullptr;
+  kkt_options o;
+  kkt_default_options(&o);
+  if (opt) o = *opt;
+  auto t0 = std::chrono::steady_clock::now();
+  kkt_handle* best = nullptr;
+  kkt_status st = analyze_one(pat, &o, kTailRatio, &best);
+  if (st != KKT_OK) return st;
+  // Autotuning of the dense tail: the candidate cost ratios give tails of
+  // different sizes; each distinct one is analysed and timed once on the values
+  // hint, and the fastest factor is kept.
+  if (o.autotune && pat->a_vals_hint && reinterpret_cast<Handle*>(best)->nT > 0) {
+    double best_ms = time_factor(best, pat);
+    std::vector<int32_t> tried = {reinterpret_cast<Handle*>(best)->nT};
+    for (double r : {1.0, 1.25, 2.0, 3.0}) {
+      kkt_handle* cand = nullptr;
+      if (analyze_one(pat, &o, r, &cand) != KKT_OK) continue;
+      const int32_t nT = reinterpret_cast<Handle*>(cand)->nT;
+      if (std::find(tried.begin(), tried.end(), nT) != tried.end()) {
+        kkt_destroy(cand);
+        continue;
+      }
+      tried.push_back(nT);
+      const double ms = time_factor(cand, pat);
+      if (ms > 0.0 && (best_ms <= 0.0 || ms < best_ms)) {
+        kkt_destroy(best);
+        best = cand;
+        best_ms = ms;
+      } else {
+        kkt_destroy(cand);
+      }
+    }
+    Handle* h = reinterpret_cast<Handle*>(best);
+    h->info.autotune_candidates = (int32_t)tried.size();
+    h->info.ms_analyze = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  *out = best;
+  return KKT_OK;
+}
+
 kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals,
                       const double* c_vals, int32_t on_device, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);
@@ -659,6 +735,7 @@ kkt_status kkt_get_info(kkt_handle* hh, kkt_info* info) {
   h->info.device_bytes = h->device_bytes;
   h->info.n_launches = h->launches;
   h->info.dense_tail_cols = h->nT;
+  h->info.tail_ratio = h->nT > 0 ? h->tail_ratio : 0.0;
   h->info.tail_augmented = h->tail_aug ? 1 : 0;
   *info = h->info;
   return KKT_OK;

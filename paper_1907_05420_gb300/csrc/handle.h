@@ -100,6 +100,7 @@ struct Handle {
   std::vector<int32_t> panel_rend;     // structured mode: per 64-wide panel, one past its last nonzero row
   std::vector<int32_t> flvl_ptr;       // supernodes outside the dense tail per level (factor)
   int32_t nT = 0;                      // columns of the dense tail (0 = none)
+  double tail_ratio = 0.0;             // cost ratio the tail was chosen with
   int32_t nTa = 0;                     // order of the tail matrices: nT, plus k augmented rows
   bool tail_aug = false;               // tail augmented by the k coupling rows (Sec. 4.2)
   int32_t nw_nt = 0;                   // W rows outside the tail (the first ones)

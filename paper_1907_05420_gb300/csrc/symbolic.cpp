@@ -600,7 +600,7 @@ void s_envelope(const Coupling& C, int32_t c_kind, int32_t block, std::vector<in
   }
 }
 
-void choose_tail(Symbolic& S, int32_t N, int64_t max_bytes, int32_t min_cols) {
+void choose_tail(Symbolic& S, int32_t N, int64_t max_bytes, int32_t min_cols, double ratio) {
   const int32_t n = S.n;
   S.tail_sn = S.nsuper;
   S.tail_col = n;
@@ -611,7 +611,7 @@ void choose_tail(Symbolic& S, int32_t N, int64_t max_bytes, int32_t min_cols) {
     const double nT = (double)(n - S.sn_first[t]);
     if (nT < min_cols) continue;
     if ((double)N * nT * nT * 8.0 > (double)max_bytes) break;
-    if (nT * nT * nT / 3.0 <= 2.0 * suffix) {
+    if (nT * nT * nT / 3.0 <= ratio * suffix) {
       S.tail_sn = t;
       S.tail_col = S.sn_first[t];
     }

@@ -70,10 +70,11 @@ struct Symbolic {
 };
 
 // Picks the dense tail: the longest suffix of supernodes whose dense factor
-// costs at most twice the exact sparse flops of its columns, has at least
-// min_cols columns, and whose N dense triangles (nT^2 doubles each) fit
+// costs at most `ratio` times the exact sparse flops of its columns, has at
+// least min_cols columns, and whose N dense triangles (nT^2 doubles each) fit
 // max_bytes.  Fills tail_sn, tail_col and upd_ntail.
-void choose_tail(Symbolic& S, int32_t N, int64_t max_bytes, int32_t min_cols);
+constexpr double kTailRatio = 1.5;
+void choose_tail(Symbolic& S, int32_t N, int64_t max_bytes, int32_t min_cols, double ratio = kTailRatio);
 
 // Coupling analysis: B_i (COO per block) against the block factor.
 // With E the sorted union of the rows that carry a nonzero of some B_i

@@ -69,7 +69,7 @@ def test_struct_layouts_match_header(tmp_path):
         "sizeof(kkt_pattern), offsetof(kkt_pattern, a_vals_hint),"
         "sizeof(kkt_options), offsetof(kkt_options, reduced_contraction),"
         "offsetof(kkt_options, dense_tail),"
-        "sizeof(kkt_info), offsetof(kkt_info, n_launches), offsetof(kkt_info, dense_tail_cols));"
+        "sizeof(kkt_info), offsetof(kkt_info, n_launches), offsetof(kkt_info, tail_ratio));"
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -79,5 +79,5 @@ def test_struct_layouts_match_header(tmp_path):
             ctypes.sizeof(binding.kkt_options), binding.kkt_options.reduced_contraction.offset,
             binding.kkt_options.dense_tail.offset,
             ctypes.sizeof(binding.kkt_info), binding.kkt_info.n_launches.offset,
-            binding.kkt_info.dense_tail_cols.offset]
+            binding.kkt_info.tail_ratio.offset]
     assert got == want

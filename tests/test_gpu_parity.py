@@ -177,15 +177,25 @@ def test_dense_tail_modes(name):
         assert info["tail_augmented"] == (1 if mode else 0)
 
 
-@pytest.mark.parametrize("prec", ["tf32", "f64emu"])
-def test_default_tail_in_reduced_modes(prec):
-    """The reduced-precision modes take the emulated tail by default."""
+@pytest.mark.parametrize("prec", ["tf32", "f64emu", "fp64"])
+def test_default_tail(prec):
+    """Every mode takes an augmented dense tail by default (emulated-FP64
+    updates in the reduced modes, FP64 on the CUDA cores in the FP64 mode)."""
     p = make_problem(replace(CONFIGS["grid2383_n96"], n_per=6, name="grid2383_n6"))
     x, info = gpu_solve(p, prec)
-    assert info["dense_tail_cols"] >= 400
+    assert info["dense_tail_cols"] >= 400 and info["tail_augmented"] == 1
+    assert info["tail_ratio"] == 1.5
     assert oracle.backward_error(p, x) <= 1e-10
-    _, info64 = gpu_solve(p, "fp64")
-    assert info64["dense_tail_cols"] == 0
+
+
+def test_autotuned_tail():
+    """The autotuner times the distinct tails of its candidate ratios and keeps
+    one of them; the solution is as accurate."""
+    p = make_problem(replace(CONFIGS["grid2383_n96"], n_per=6, name="grid2383_n6"))
+    x, info = gpu_solve(p, "tf32", autotune=1)
+    assert info["autotune_candidates"] >= 2
+    assert info["tail_ratio"] in (1.0, 1.25, 1.5, 2.0, 3.0)
+    assert oracle.backward_error(p, x) <= 1e-10
 
 
 @pytest.mark.parametrize("prec", ["fp64", "tf32"])
