@@ -325,6 +325,8 @@ def main():
     ap.add_argument("--serve-backlog", type=int, default=0,
                     help="requests outstanding before new arrivals are shed (default 4 x slots)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the dense-tail autotuning at analysis (it times a few factorizations)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -370,7 +372,8 @@ def main():
         row envelope (the structured Schur factor)."""
         prec, _, extra = mode.partition("+")
         h = B.kkt_analyze(prob, B.kkt_default_options(prec, reduced_contraction=int(extra == "tcg"),
-                                                     structured_s=int(extra == "band")))
+                                                     structured_s=int(extra == "band"),
+                                                     autotune=0 if args.no_autotune else 1))
         info0 = B.kkt_get_info(h)
 
         def step_device():
