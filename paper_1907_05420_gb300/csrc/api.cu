@@ -64,6 +64,10 @@ void free_all(Handle* h) {
     if (ev) cudaEventDestroy(ev);
   if (h->factor_exec) cudaGraphExecDestroy(h->factor_exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side_stream) cudaStreamDestroy(h->side_stream);
+  if (h->hi_stream) cudaStreamDestroy(h->hi_stream);
+  if (h->ev_main) cudaEventDestroy(h->ev_main);
+  if (h->ev_side) cudaEventDestroy(h->ev_side);
 }
 
 // An event record that becomes a node of the graph while the factor is captured.
@@ -113,7 +117,7 @@ void capture_factor(Handle& h) {
     e = e1 != cudaSuccess ? e1 : e2;
   }
   h.capturing = false;
-  if (e == cudaSuccess && g) e = cudaGraphInstantiate(&h.factor_exec, g, 0);
+  if (e == cudaSuccess && g) e = cudaGraphInstantiate(&h.factor_exec, g, cudaGraphInstantiateFlagUseNodePriority);
   if (g) cudaGraphDestroy(g);
   h.graph_launches = h.launches - l0;
   h.launches = l0;
@@ -492,6 +496,15 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   for (cudaEvent_t* ev : {&h->ev_f0, &h->ev_f1, &h->ev_fa, &h->ev_fb, &h->ev_s0, &h->ev_s1, &h->ev_done})
     if (e == cudaSuccess) e = cudaEventCreate(ev);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->hi_stream, cudaStreamNonBlocking, hi);
+    h->prio_hi = hi;
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming);
   if (e == cudaSuccess) e = dense_prepare();
   if (e == cudaSuccess) e = dense_tc_prepare();
   if (e == cudaSuccess) e = schur_tc_prepare();

@@ -255,6 +255,24 @@ __global__ void __launch_bounds__(256) k_dense_panel_w(T* __restrict__ S0, T* __
   }
 }
 
+// A launch with a scheduling priority (a launch attribute, so that it also
+// holds for the kernel node when the launch is captured in a graph).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                               int prio, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = prio;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Rows below the diagonal block of nb matrices.  A thread per row issues the
 // fewest instructions (no idle lanes) but its dependency chain is long; a
 // warp per row has a 64-step chain.  FP32 takes a thread per row from 2048
@@ -263,21 +281,24 @@ __global__ void __launch_bounds__(256) k_dense_panel_w(T* __restrict__ S0, T* __
 // warps) to keep every sub-partition's FP64 pipe busy.
 template <class T>
 inline void launch_dense_panel(T* S, T* Y, int n, int k0, int kb, int rend, int nb, int64_t bstride,
-                               int64_t ystride, cudaStream_t st) {
+                               int64_t ystride, cudaStream_t st, int prio = 0) {
   const int m = rend - k0 - kb;
   if (m <= 0) return;
   if constexpr (sizeof(T) == 4) {
     if (m > 2048) {
-      k_dense_panel_t<T, 128><<<dim3((m + 127) / 128, nb), 128, 0, st>>>(S, Y, n, k0, kb, rend, bstride, ystride);
+      launch_prio(k_dense_panel_t<T, 128>, dim3((m + 127) / 128, nb), dim3(128), 0, st, prio, S, Y, n, k0, kb,
+                  rend, bstride, ystride);
       return;
     }
   } else {
     if ((int64_t)m * nb >= 32768) {
-      k_dense_panel_t<T, 32><<<dim3((m + 31) / 32, nb), 32, 0, st>>>(S, Y, n, k0, kb, rend, bstride, ystride);
+      launch_prio(k_dense_panel_t<T, 32>, dim3((m + 31) / 32, nb), dim3(32), 0, st, prio, S, Y, n, k0, kb, rend,
+                  bstride, ystride);
       return;
     }
   }
-  k_dense_panel_w<T><<<dim3((m + 7) / 8, nb), 256, 0, st>>>(S, Y, n, k0, kb, rend, bstride, ystride);
+  launch_prio(k_dense_panel_w<T>, dim3((m + 7) / 8, nb), dim3(256), 0, st, prio, S, Y, n, k0, kb, rend, bstride,
+              ystride);
 }
 
 // Trailing update of matrix blockIdx.y on the lower 64 x 64 tiles below the

@@ -217,22 +217,30 @@ __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S0, cons
   }
 }
 
-// tile list: (I, J) with J <= 2I + 1 (tiles that hold part of the lower triangle)
-__device__ __forceinline__ void tile_of(int t, int TJ, int& I, int& J) {
-  // rows of the list: I = 0 has min(2, TJ) tiles, I has min(2I+2, TJ)
+// tile list: (I, J) with J <= 2I + 1 (tiles that hold part of the lower
+// triangle).  jmode 0: all of them; 1: the first tile column (J = 0, the next
+// panel's columns); 2: the others (J >= 1).
+__device__ __forceinline__ void tile_of(int t, int TJ, int jmode, int& I, int& J) {
+  if (jmode == 1) {
+    I = t;
+    J = 0;
+    return;
+  }
+  // row I of the list has min(2I+2, TJ) tiles, one fewer without J = 0
+  const int skip = jmode == 2 ? 1 : 0;
   int i = 0;
   for (;;) {
-    const int cnt = min(2 * i + 2, TJ);
+    const int cnt = min(2 * i + 2, TJ) - skip;
     if (t < cnt) break;
     t -= cnt;
     i++;
   }
   I = i;
-  J = t;
+  J = t + skip;
 }
 
 template <int MODE, class T>
-__global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n, int k0, int kb, int m, int TJ,
+__global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n, int k0, int kb, int m, int TJ, int jmode,
                                                       const uint8_t* __restrict__ imgA0,
                                                       const uint8_t* __restrict__ imgB0,
                                                       const double* __restrict__ scaleA0,
@@ -259,7 +267,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n,
   __shared__ int s_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int I, J;
-  tile_of(blockIdx.x, TJ, I, J);
+  tile_of(blockIdx.x, TJ, jmode, I, J);
   const int base = k0 + kb;
 
   if (tid == 0) {
@@ -439,34 +447,77 @@ __global__ void k_dense_diag_scale_f(const float* __restrict__ S, double* __rest
 // One blocked LDL^T of nb matrices of order n (matrix b at S + b * ts.s):
 // diagonal block and panel on the CUDA cores, trailing update on the tensor
 // cores.  rend: per 64-wide panel, one past its last nonzero row (or null).
+//
+// Lookahead: the update of step k is split into its first tile column (the
+// next panel's 64 columns) and the rest, so that the next diagonal block and
+// panel run while the rest of the update does.  The critical chain (diagonal
+// block, panel, slicing, first tile column) runs on the handle's high-priority
+// stream, whose blocks the scheduler dispatches ahead of the rest's waiting
+// blocks on the side stream.  The next step's slicing waits for the rest (it
+// overwrites the operand images the rest reads); the caller's stream joins
+// both at the end.
 template <int MODE, class T>
 cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int npiv, int nb, const TcStrides& ts, const PivotRule& rule,
                       const int32_t* rend_of_panel, unsigned long long* counters, uint8_t* imgA,
-                      uint8_t* imgB, double* scaleA, double* scaleB, cudaStream_t st) {
+                      uint8_t* imgB, double* scaleA, double* scaleB, cudaStream_t caller) {
   constexpr int A_BYTES = image_bytes(MODE, TM), B_BYTES = image_bytes(MODE, TN);
   const int smem = A_BYTES + B_BYTES;
-  for (int k0 = 0; k0 < npiv; k0 += TK) {
+  cudaStream_t side = h.side_stream;
+  cudaStream_t st = caller;
+  const int prio = side ? h.prio_hi : 0;  // the critical chain's launches outrank the rest of the update
+  bool side_busy = false;
+  cudaError_t e = cudaSuccess;
+  if (side && h.hi_stream) {  // fork the critical chain onto the high-priority stream
+    e = cudaEventRecord(h.ev_main, caller);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h.hi_stream, h.ev_main, 0);
+    if (e != cudaSuccess) return e;
+    st = h.hi_stream;
+  }
+  for (int k0 = 0; k0 < npiv && e == cudaSuccess; k0 += TK) {
     const int kb = std::min(TK, npiv - k0);
-    k_dense_diag_t<T><<<nb, 256, 0, st>>>(S, n, k0, kb, ts.s, rule, counters);
+    launch_prio(k_dense_diag_t<T>, dim3(nb), dim3(256), 0, st, prio, S, n, k0, kb, ts.s, rule, counters);
     h.launches++;
     // rows below the envelope of the panel's columns stay zero (no pivoting)
     const int rend = rend_of_panel ? rend_of_panel[k0 / TK] : n;
     const int m = rend - k0 - kb;
     if (m <= 0) continue;
-    launch_dense_panel<T>(S, Y, n, k0, kb, rend, nb, ts.s, ts.y, st);
+    launch_dense_panel<T>(S, Y, n, k0, kb, rend, nb, ts.s, ts.y, st, prio);
     h.launches++;
+    if (side_busy) {
+      e = cudaStreamWaitEvent(st, h.ev_side, 0);
+      side_busy = false;
+      if (e != cudaSuccess) break;
+    }
     const int TI = (m + TM - 1) / TM, TJ = (m + TN - 1) / TN;
     const int mpadA = TI * TM, mpadB = TJ * TN;
     const int sgrid = std::max(1, std::min((mpadA + mpadB + 255) / 256, 152 * 8 / nb));
-    k_tc_slice<MODE, T><<<dim3(sgrid, nb), 256, 0, st>>>(S, Y, n, k0, kb, m, imgA, imgB, scaleA, scaleB, mpadA,
-                                                         mpadB, ts);
+    launch_prio(k_tc_slice<MODE, T>, dim3(sgrid, nb), dim3(256), 0, st, prio, S, Y, n, k0, kb, m, imgA, imgB,
+                scaleA, scaleB, mpadA, mpadB, ts);
     int tiles = 0;
     for (int I = 0; I < TI; I++) tiles += std::min(2 * I + 2, TJ);
-    k_tc_update<MODE, T><<<dim3(tiles, nb), 128, smem, st>>>(S, n, k0, kb, m, TJ, imgA, imgB, scaleA, scaleB,
-                                                             h.dev_err, ts);
     h.launches += 2;
+    if (!side || TJ < 2) {
+      k_tc_update<MODE, T><<<dim3(tiles, nb), 128, smem, st>>>(S, n, k0, kb, m, TJ, 0, imgA, imgB, scaleA, scaleB,
+                                                               h.dev_err, ts);
+      continue;
+    }
+    e = cudaEventRecord(h.ev_main, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, h.ev_main, 0);
+    if (e != cudaSuccess) break;
+    k_tc_update<MODE, T><<<dim3(tiles - TI, nb), 128, smem, side>>>(S, n, k0, kb, m, TJ, 2, imgA, imgB, scaleA,
+                                                                      scaleB, h.dev_err, ts);
+    e = cudaEventRecord(h.ev_side, side);
+    side_busy = true;
+    launch_prio(k_tc_update<MODE, T>, dim3(TI, nb), dim3(128), smem, st, prio, S, n, k0, kb, m, TJ, 1, imgA, imgB,
+                scaleA, scaleB, h.dev_err, ts);
+    h.launches++;
   }
-  return cudaGetLastError();
+  if (side_busy && e == cudaSuccess) e = cudaStreamWaitEvent(caller, h.ev_side, 0);
+  if (st != caller && e == cudaSuccess) {  // join the high-priority chain
+    e = cudaEventRecord(h.ev_main, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, h.ev_main, 0);
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace

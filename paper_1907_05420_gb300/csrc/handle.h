@@ -170,6 +170,10 @@ struct Handle {
   cudaEvent_t ev_done = nullptr;  // end of the handle's last factor/solve (outlives the caller's stream)
   // CUDA graph of the factor's launch sequence (captured at the first kkt_factor)
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side_stream = nullptr;  // second stream of the dense factors' lookahead
+  cudaStream_t hi_stream = nullptr;    // high-priority stream of the lookahead's critical chain
+  int prio_hi = 0;                     // its priority (also set on the chain's launches)
+  cudaEvent_t ev_main = nullptr, ev_side = nullptr;
   cudaGraphExec_t factor_exec = nullptr;
   bool graph_failed = false;
   bool capturing = false;
