@@ -22,6 +22,7 @@
 // Every entry is written by one thread in a fixed order: the result does not
 // depend on scheduling.
 #include "handle.h"
+#include "pivot.cuh"
 
 namespace kkt {
 
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(256) k_panel_factor(const int32_t* __restrict_
   const int f = d.sn_first[s], w = d.sn_first[s + 1] - f;
   double* P = Lx + b * pt + d.sn_valoff[s];
   const double thr = pivot_eps * anorm[b];
-  __shared__ double dsh;
+  __shared__ double dsh, dinv_sh;
   __shared__ int cnt[4];
   if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
   for (int c = 0; c < w; c++) {
@@ -153,11 +154,12 @@ __global__ void __launch_bounds__(256) k_panel_factor(const int32_t* __restrict_
       P[(int64_t)c * m + c] = dv;
       cnt[dv > 0.0 ? 0 : (dv < 0.0 ? 1 : 2)]++;
       dsh = dv;
+      dinv_sh = pivot_recip(dv);
     }
     __syncthreads();
-    const double dv = dsh;
+    const double dv = dsh, di = dinv_sh;
     double* colc = P + (int64_t)c * m;
-    for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) colc[r] = colc[r] / dv;
+    for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) colc[r] = colc[r] * di;
     __syncthreads();
     for (int c2 = c + 1; c2 < w; c2++) {
       const double l2 = colc[c2] * dv;
