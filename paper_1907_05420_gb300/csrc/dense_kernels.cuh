@@ -164,6 +164,21 @@ __global__ void __launch_bounds__(256, 1) k_dense_diag_t(T* __restrict__ S0, int
   }
 }
 
+// TF32 operand images of the trailing update, written by the panel kernels
+// themselves (FP32 only): the shared-memory layout of the tensor-core update's
+// 128-row A blocks (Y) and 64-row B blocks (L21), K-major 8-row x 16-byte core
+// matrices, 16 cores along K.  Rows are counted from the first trailing row;
+// columns at or past kb are zero.  A null A skips the images.
+struct Tf32Images {
+  uint8_t* A = nullptr;
+  uint8_t* B = nullptr;
+};
+
+__device__ __forceinline__ int64_t tf32_img_off(int rho, int c, int rows_blk) {
+  const int blk = rho / rows_blk, rr = rho - blk * rows_blk;
+  return (int64_t)blk * (rows_blk / 8) * 16 * 128 + ((rr >> 3) * 16 + (c >> 2)) * 128 + (rr & 7) * 16 + (c & 3) * 4;
+}
+
 // Rows k0+kb .. rend-1 of matrix blockIdx.y, one thread per row (ROWS rows
 // per CTA): solve y L11^T = a with y in registers and L11 in shared memory
 // (every thread of a warp reads the same L11 entry), then Y = y and
@@ -171,7 +186,7 @@ __global__ void __launch_bounds__(256, 1) k_dense_diag_t(T* __restrict__ S0, int
 template <class T, int ROWS>
 __global__ void __launch_bounds__(ROWS) k_dense_panel_t(T* __restrict__ S0, T* __restrict__ Y0, int n,
                                                         int k0, int kb, int rend, int64_t bstride,
-                                                        int64_t ystride) {
+                                                        int64_t ystride, Tf32Images img) {
   __shared__ T L11[kPanelW][kPanelW];  // [j][c], zero outside the strict lower triangle
   __shared__ T dinv[kPanelW];
   T* S = S0 + (int64_t)blockIdx.y * bstride;
@@ -202,6 +217,25 @@ __global__ void __launch_bounds__(ROWS) k_dense_panel_t(T* __restrict__ S0, T* _
       Y[row + (int64_t)c * n] = y[c];
       S[row + (int64_t)(k0 + c) * n] = y[c] * dinv[c];
     }
+  if constexpr (sizeof(T) == 4) {
+    if (img.A) {
+      const int rho = row - (k0 + kb);
+#pragma unroll
+      for (int kq = 0; kq < kPanelW / 4; kq++) {
+        float4 a, l;
+        a.x = y[4 * kq];
+        a.y = y[4 * kq + 1];
+        a.z = y[4 * kq + 2];
+        a.w = y[4 * kq + 3];
+        l.x = y[4 * kq] * dinv[4 * kq];
+        l.y = y[4 * kq + 1] * dinv[4 * kq + 1];
+        l.z = y[4 * kq + 2] * dinv[4 * kq + 2];
+        l.w = y[4 * kq + 3] * dinv[4 * kq + 3];
+        *reinterpret_cast<float4*>(img.A + tf32_img_off(rho, 4 * kq, 128)) = a;
+        *reinterpret_cast<float4*>(img.B + tf32_img_off(rho, 4 * kq, 64)) = l;
+      }
+    }
+  }
 }
 
 // The same solve with one warp per row: lane l holds y_l and y_{l+32}, and
@@ -210,7 +244,8 @@ __global__ void __launch_bounds__(ROWS) k_dense_panel_t(T* __restrict__ S0, T* _
 // for few rows (and in FP64, whose dependent multiply-add latency is long).
 template <class T>
 __global__ void __launch_bounds__(256) k_dense_panel_w(T* __restrict__ S0, T* __restrict__ Y0, int n, int k0,
-                                                       int kb, int rend, int64_t bstride, int64_t ystride) {
+                                                       int kb, int rend, int64_t bstride, int64_t ystride,
+                                                       Tf32Images img) {
   __shared__ T L11[kPanelW][kPanelW + 1];
   __shared__ T dinv[kPanelW];
   T* S = S0 + (int64_t)blockIdx.y * bstride;
@@ -238,6 +273,16 @@ __global__ void __launch_bounds__(256) k_dense_panel_w(T* __restrict__ S0, T* __
   if (lane + 32 < kb) {
     Y[row + (int64_t)(lane + 32) * n] = y1;
     S[row + (int64_t)(k0 + lane + 32) * n] = y1 * dinv[lane + 32];
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (img.A) {
+      const int rho = row - (k0 + kb);
+      const float l0 = lane < kb ? y0 * dinv[lane] : 0.f, l1 = lane + 32 < kb ? y1 * dinv[lane + 32] : 0.f;
+      *reinterpret_cast<float*>(img.A + tf32_img_off(rho, lane, 128)) = y0;
+      *reinterpret_cast<float*>(img.A + tf32_img_off(rho, lane + 32, 128)) = y1;
+      *reinterpret_cast<float*>(img.B + tf32_img_off(rho, lane, 64)) = l0;
+      *reinterpret_cast<float*>(img.B + tf32_img_off(rho, lane + 32, 64)) = l1;
+    }
   }
 }
 
@@ -267,24 +312,24 @@ inline cudaError_t launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, 
 // warps) to keep every sub-partition's FP64 pipe busy.
 template <class T>
 inline void launch_dense_panel(T* S, T* Y, int n, int k0, int kb, int rend, int nb, int64_t bstride,
-                               int64_t ystride, cudaStream_t st, int prio = 0) {
+                               int64_t ystride, cudaStream_t st, int prio = 0, Tf32Images img = Tf32Images{}) {
   const int m = rend - k0 - kb;
   if (m <= 0) return;
   if constexpr (sizeof(T) == 4) {
     if (m > 2048) {
       launch_prio(k_dense_panel_t<T, 128>, dim3((m + 127) / 128, nb), dim3(128), 0, st, prio, S, Y, n, k0, kb,
-                  rend, bstride, ystride);
+                  rend, bstride, ystride, img);
       return;
     }
   } else {
     if ((int64_t)m * nb >= 32768) {
       launch_prio(k_dense_panel_t<T, 32>, dim3((m + 31) / 32, nb), dim3(32), 0, st, prio, S, Y, n, k0, kb, rend,
-                  bstride, ystride);
+                  bstride, ystride, img);
       return;
     }
   }
   launch_prio(k_dense_panel_w<T>, dim3((m + 7) / 8, nb), dim3(256), 0, st, prio, S, Y, n, k0, kb, rend, bstride,
-              ystride);
+              ystride, img);
 }
 
 // Trailing update of matrix blockIdx.y on the lower 64 x 64 tiles below the

@@ -481,7 +481,21 @@ cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int npiv, int nb, const TcSt
     const int rend = rend_of_panel ? rend_of_panel[k0 / TK] : n;
     const int m = rend - k0 - kb;
     if (m <= 0) continue;
-    launch_dense_panel<T>(S, Y, n, k0, kb, rend, nb, ts.s, ts.y, st, prio);
+    // TF32 (one matrix): the panel kernel writes the update's operand images
+    // itself, so it waits for the previous update's rest, which reads them
+    constexpr bool fused = MODE == 0;
+    const bool fuse = fused && nb == 1;
+    if (side_busy && fuse) {
+      e = cudaStreamWaitEvent(st, h.ev_side, 0);
+      side_busy = false;
+      if (e != cudaSuccess) break;
+    }
+    Tf32Images img;
+    if (fuse) {
+      img.A = imgA;
+      img.B = imgB;
+    }
+    launch_dense_panel<T>(S, Y, n, k0, kb, rend, nb, ts.s, ts.y, st, prio, img);
     h.launches++;
     if (side_busy) {
       e = cudaStreamWaitEvent(st, h.ev_side, 0);
@@ -490,12 +504,15 @@ cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int npiv, int nb, const TcSt
     }
     const int TI = (m + TM - 1) / TM, TJ = (m + TN - 1) / TN;
     const int mpadA = TI * TM, mpadB = TJ * TN;
-    const int sgrid = std::max(1, std::min((mpadA + mpadB + 255) / 256, 152 * 8 / nb));
-    launch_prio(k_tc_slice<MODE, T>, dim3(sgrid, nb), dim3(256), 0, st, prio, S, Y, n, k0, kb, m, imgA, imgB,
-                scaleA, scaleB, mpadA, mpadB, ts);
+    if (!fuse) {
+      const int sgrid = std::max(1, std::min((mpadA + mpadB + 255) / 256, 152 * 8 / nb));
+      launch_prio(k_tc_slice<MODE, T>, dim3(sgrid, nb), dim3(256), 0, st, prio, S, Y, n, k0, kb, m, imgA, imgB,
+                  scaleA, scaleB, mpadA, mpadB, ts);
+      h.launches++;
+    }
     int tiles = 0;
     for (int I = 0; I < TI; I++) tiles += std::min(2 * I + 2, TJ);
-    h.launches += 2;
+    h.launches++;
     if (!side || TJ < 2) {
       k_tc_update<MODE, T><<<dim3(tiles, nb), 128, smem, st>>>(S, n, k0, kb, m, TJ, 0, imgA, imgB, scaleA, scaleB,
                                                                h.dev_err, ts);
