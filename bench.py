@@ -373,7 +373,8 @@ def main():
         prec, _, extra = mode.partition("+")
         h = B.kkt_analyze(prob, B.kkt_default_options(prec, reduced_contraction=int(extra == "tcg"),
                                                      structured_s=int(extra == "band"),
-                                                     autotune=0 if args.no_autotune else 1))
+                                                     autotune=0 if args.no_autotune else 1,
+                                                     early_solve=1))
         info0 = B.kkt_get_info(h)
 
         def step_device():

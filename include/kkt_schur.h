@@ -126,6 +126,13 @@ typedef struct {
                            (one kkt_factor on the values hint in every block, B = 0, C = I) and the
                            fastest is kept.  Needs a_vals_hint; adds those factorizations to
                            kkt_analyze.  Default 0 (r = 1.5). */
+  int32_t early_solve;  /* the first application of kkt_solve after a kkt_factor starts its front half
+                           (forward block solves, right-hand-side reduction), which needs only the
+                           block factors, as soon as that factor's Schur assembly has finished, on a
+                           stream of the handle, while the dense factor of S still runs.  The
+                           right-hand side is then read on that stream: a right-hand side on the
+                           device must be complete when kkt_factor is called.  Default 0. */
+  int32_t reserved;
 } kkt_options;
 
 typedef struct {

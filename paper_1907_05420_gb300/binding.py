@@ -41,7 +41,8 @@ class kkt_options(C.Structure):
     _fields_ = [("prec", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int32),
                 ("pivot_eps", C.c_double), ("use_graphs", C.c_int32),
                 ("fp64_fallback", C.c_int32), ("reduced_contraction", C.c_int32),
-                ("structured_s", C.c_int32), ("dense_tail", C.c_int32), ("autotune", C.c_int32)]
+                ("structured_s", C.c_int32), ("dense_tail", C.c_int32), ("autotune", C.c_int32),
+                ("early_solve", C.c_int32), ("reserved", C.c_int32)]
 
 
 class kkt_info(C.Structure):

@@ -65,6 +65,8 @@ void free_all(Handle* h) {
   if (h->factor_exec) cudaGraphExecDestroy(h->factor_exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->side_stream) cudaStreamDestroy(h->side_stream);
+  if (h->early_stream) cudaStreamDestroy(h->early_stream);
+  if (h->ev_early) cudaEventDestroy(h->ev_early);
   if (h->hi_stream) cudaStreamDestroy(h->hi_stream);
   if (h->ev_main) cudaEventDestroy(h->ev_main);
   if (h->ev_side) cudaEventDestroy(h->ev_side);
@@ -497,6 +499,8 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
     if (e == cudaSuccess) e = cudaEventCreate(ev);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->early_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_early, cudaEventDisableTiming);
   if (e == cudaSuccess) {
     int lo = 0, hi = 0;
     e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
@@ -628,6 +632,7 @@ kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals
     KKT_CUDA(enqueue_factor(*h, st));
   }
   h->info.fell_back_fp64 = 0;
+  h->schur_pending = true;
   KKT_CUDA(cudaEventRecord(h->ev_f1, st));
   KKT_CUDA(cudaEventRecord(h->ev_done, st));
   h->factored = true;
@@ -656,9 +661,22 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
   for (int32_t q = 0; q < nrhs; q++) {
     const double* rq = rhs + q * nK;
     double* xq = x + q * nK;
-    KKT_CUDA(cudaMemcpyAsync(h->rhs, rq, sizeof(double) * nK,
-                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    KKT_CUDA(launch_apply_inverse(*h, h->rhs, h->x, st));
+    if (q == 0 && h->opt.early_solve && h->schur_pending) {
+      // the front half needs only the block factors and W: it starts when the
+      // preceding factor's Schur assembly ends, beside the dense factor of S
+      KKT_CUDA(cudaStreamWaitEvent(h->early_stream, h->ev_fb, 0));
+      KKT_CUDA(cudaMemcpyAsync(h->rhs, rq, sizeof(double) * nK,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->early_stream));
+      KKT_CUDA(launch_apply_front(*h, h->rhs, h->early_stream));
+      KKT_CUDA(cudaEventRecord(h->ev_early, h->early_stream));
+      KKT_CUDA(cudaStreamWaitEvent(st, h->ev_early, 0));
+      KKT_CUDA(launch_apply_back(*h, h->x, st));
+    } else {
+      KKT_CUDA(cudaMemcpyAsync(h->rhs, rq, sizeof(double) * nK,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+      KKT_CUDA(launch_apply_inverse(*h, h->rhs, h->x, st));
+    }
+    h->schur_pending = false;
     int steps = 0;
     double eta = INFINITY, eta_prev = INFINITY;
     for (;;) {

@@ -172,6 +172,9 @@ struct Handle {
   cudaStream_t cap_stream = nullptr;
   cudaStream_t side_stream = nullptr;  // second stream of the dense factors' lookahead
   cudaStream_t hi_stream = nullptr;    // high-priority stream of the lookahead's critical chain
+  cudaStream_t early_stream = nullptr; // kkt_solve's front half, overlapping the factor of S
+  cudaEvent_t ev_early = nullptr;
+  bool schur_pending = false;          // ev_fb marks the Schur assembly of a factor not yet solved with
   int prio_hi = 0;                     // its priority (also set on the chain's launches)
   cudaEvent_t ev_main = nullptr, ev_side = nullptr;
   cudaGraphExec_t factor_exec = nullptr;
@@ -220,6 +223,8 @@ cudaError_t launch_dense_diag_panel_f64(Handle& h, int k0, int kb, int rend, uns
 int64_t tc_image_bytes(int n, int mode);
 // ---- (solve.cu) ----
 cudaError_t launch_apply_inverse(Handle& h, const double* rhs, double* out, cudaStream_t st);
+cudaError_t launch_apply_front(Handle& h, const double* rhs, cudaStream_t st);
+cudaError_t launch_apply_back(Handle& h, double* out, cudaStream_t st);
 cudaError_t launch_residual(Handle& h, const double* rhs, const double* x, double* rho,
                             cudaStream_t st);
 cudaError_t launch_knorm(Handle& h, cudaStream_t st);

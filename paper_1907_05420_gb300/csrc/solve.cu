@@ -417,7 +417,10 @@ inline int grid_for(int64_t n, int bs = 256) {
 
 }  // namespace
 
-cudaError_t launch_apply_inverse(Handle& h, const double* r, double* out, cudaStream_t st) {
+// The application is split where it first needs the factor of S: the front
+// (forward block solves and right-hand-side reduction) needs only the block
+// factors and W; the back does the rest.
+cudaError_t launch_apply_front(Handle& h, const double* r, cudaStream_t st) {
   const int nA = h.nA, N = h.N, k = h.cpl.k, nw = h.cpl.nw;
   const int64_t pt = h.sym.panel_total;
   const int64_t nb = (int64_t)nA * N;
@@ -460,6 +463,18 @@ cudaError_t launch_apply_inverse(Handle& h, const double* r, double* out, cudaSt
                                                    h.b_vals, h.u, k, h.nC, h.tg);
     h.launches++;
   }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_back(Handle& h, double* out, cudaStream_t st) {
+  const int nA = h.nA, N = h.N, k = h.cpl.k, nw = h.cpl.nw;
+  const int64_t pt = h.sym.panel_total;
+  const int64_t nb = (int64_t)nA * N;
+  const bool tail = h.nT > 0;
+  const std::vector<int32_t>& lptr = tail ? h.flvl_ptr : h.lvl_ptr;
+  const int32_t* lsn = tail ? h.d.flvl_sn : h.d.lvl_sn;
+  if (h.nC > 0) {
     cudaError_t e = h.s_factor == 1 ? launch_dense_solve_f32(h, h.tg, h.xg, st)
                                     : launch_dense_solve(h, h.tg, h.xg, st);
     if (e != cudaSuccess) return e;
@@ -500,6 +515,11 @@ cudaError_t launch_apply_inverse(Handle& h, const double* r, double* out, cudaSt
   if (h.nC > 0)
     cudaMemcpyAsync(out + nb, h.xg, sizeof(double) * h.nC, cudaMemcpyDeviceToDevice, st);
   return cudaGetLastError();
+}
+
+cudaError_t launch_apply_inverse(Handle& h, const double* r, double* out, cudaStream_t st) {
+  cudaError_t e = launch_apply_front(h, r, st);
+  return e != cudaSuccess ? e : launch_apply_back(h, out, st);
 }
 
 cudaError_t launch_residual(Handle& h, const double* r, const double* x, double* rho, cudaStream_t st) {

@@ -229,3 +229,17 @@ def test_graph_replay_matches_direct_launches(prec):
     for prob, x in zip((p, q), out[1][0][:2]):
         assert oracle.backward_error(prob, x) <= 1e-10
     del torch
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32"])
+def test_early_solve_matches(prec):
+    """With early_solve the first application's front half runs on another
+    stream beside the dense factor of S: the same kernels in the same order
+    per stream, so bitwise the same solution."""
+    _torch()
+    p = make_problem(replace(CONFIGS["grid2383_n96"], n_per=6, name="grid2383_n6"))
+    x0, _ = gpu_solve(p, prec, early_solve=0)
+    x1, _ = gpu_solve(p, prec, early_solve=1)
+    assert np.array_equal(x0, x1)
+    x2, _ = gpu_solve(p, prec, early_solve=1, device_arrays=True)
+    assert np.array_equal(x0, x2)
