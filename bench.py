@@ -538,6 +538,9 @@ def main():
         "roofline": roofline, "phases": phase_report, "fp64_peak_gflops_measured": fp64_gflops,
         "e2e": e2e, "clocks": clk, "gpu_launches": int(launches), "wall_s_timed": t_wall,
         "analyze_ms": info0["ms_analyze"], "refine_steps_last": steps_ir[-1],
+        "dense_tail": {"cols": info0["dense_tail_cols"], "ratio": info0["tail_ratio"],
+                       "augmented": bool(info0["tail_augmented"]),
+                       "autotune_candidates": info0["autotune_candidates"]},
         "fell_back_fp64": main_run["fallback"][-1], "other_precisions": legs,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -271,8 +271,8 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   std::vector<int32_t> fwork, twork, frange, flvl_sn;
   auto add_items = [&](int s, std::vector<int32_t>& items) {
     int m = (int)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]);
-    for (int lo = 0; lo < m; lo += 64) {
-      const int hi = std::min(m, lo + 64);
+    for (int lo = 0; lo < m; lo += kFactorTileRows) {
+      const int hi = std::min(m, lo + kFactorTileRows);
       items.push_back(s);
       items.push_back(lo);
       items.push_back(hi);

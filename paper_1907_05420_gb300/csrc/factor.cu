@@ -73,7 +73,7 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int v) {
 // NONTAIL: apply only the updates from descendants outside the dense tail
 // (the leading upd_ntail[s] entries of s's list); used for the tail supernodes,
 // whose updates among themselves the dense tail factor performs.
-constexpr int kTileRows = 64;
+constexpr int kTileRows = kFactorTileRows;
 
 template <bool NONTAIL>
 __global__ void __launch_bounds__(256) k_factor_update(const int32_t* __restrict__ work,

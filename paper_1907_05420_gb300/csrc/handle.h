@@ -186,6 +186,7 @@ struct Handle {
 };
 
 constexpr int kDenseNB = 64;
+constexpr int kFactorTileRows = 64;  // rows of a work item of the supernodal update (factor.cu)
 
 // ---- kernel attributes, set once per device before any launch ----
 cudaError_t dense_prepare();
