@@ -112,8 +112,9 @@ typedef struct {
                            whose rows are all tail columns) as one dense lower triangle per block
                            with the blocked dense kernels of the factor of S, instead of
                            supernode by supernode.  Chosen at analysis: the longest suffix whose
-                           dense flops are at most twice its exact sparse flops and whose N
-                           triangles fit 24 GB.  The same static-pivot rule applies; the
+                           dense flops are at most r times its exact sparse flops (r: tail_ratio,
+                           else 1.5, else the autotuner's) and whose N triangles fit 24 GiB
+                           (mode 1) or 96 GiB (mode 2).  The same static-pivot rule applies; the
                            factor is scattered back into the supernodal panels.
                            0: off; 1: trailing updates in FP64 on the CUDA cores; 2: trailing
                            updates in emulated FP64 on the tensor cores (7 base-256 digit
@@ -124,8 +125,9 @@ typedef struct {
                            whose dense flops are at most r times its sparse flops; with autotune the
                            distinct tails of r in {1, 1.25, 1.5, 2, 3} are analysed and timed once each
                            (one kkt_factor on the values hint in every block, B = 0, C = I) and the
-                           fastest is kept.  Needs a_vals_hint; adds those factorizations to
-                           kkt_analyze.  Default 0 (r = 1.5). */
+                           fastest is kept.  The candidates share the first analysis (ordering,
+                           supernodes, reach).  Needs a_vals_hint; adds those factorizations to
+                           kkt_analyze; ignored when tail_ratio is set.  Default 0 (r = 1.5). */
   int32_t early_solve;  /* the first application of kkt_solve after a kkt_factor starts its front half
                            (forward block solves, right-hand-side reduction), which needs only the
                            block factors, as soon as that factor's Schur assembly has finished, on a
@@ -133,6 +135,8 @@ typedef struct {
                            right-hand side is then read on that stream: a right-hand side on the
                            device must be complete when kkt_factor is called.  Default 0. */
   int32_t reserved;
+  double tail_ratio;    /* the cost ratio r of the dense tail (above); 0, the default, takes 1.5 or,
+                           with autotune, the autotuner's choice.  Negative values are rejected. */
 } kkt_options;
 
 typedef struct {

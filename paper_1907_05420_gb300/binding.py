@@ -42,7 +42,7 @@ class kkt_options(C.Structure):
                 ("pivot_eps", C.c_double), ("use_graphs", C.c_int32),
                 ("fp64_fallback", C.c_int32), ("reduced_contraction", C.c_int32),
                 ("structured_s", C.c_int32), ("dense_tail", C.c_int32), ("autotune", C.c_int32),
-                ("early_solve", C.c_int32), ("reserved", C.c_int32)]
+                ("early_solve", C.c_int32), ("reserved", C.c_int32), ("tail_ratio", C.c_double)]
 
 
 class kkt_info(C.Structure):

@@ -170,8 +170,12 @@ const char* kkt_last_error(void) { return g_last_error.c_str(); }
 
 namespace {
 
-// One analysis with the dense tail chosen at cost ratio `tail_ratio`.
-kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double tail_ratio, kkt_handle** out) {
+// One analysis with the dense tail chosen at cost ratio `tail_ratio`.  With
+// `sym0` and `cpl0`, the ordering, supernodes and coupling reach are copied
+// from an earlier analysis of the same pattern instead of being recomputed
+// (they do not depend on the tail).
+kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double tail_ratio, const Symbolic* sym0,
+                       const Coupling* cpl0, kkt_handle** out) {
   *out = nullptr;
   if (!pat->a_rowptr || !pat->a_col || !pat->b_blockptr || (pat->c_kind != 0 && pat->c_kind != 1) ||
       pat->N <= 0 || pat->nA <= 0 || pat->nC < 0) {
@@ -199,10 +203,16 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   h->nC = pat->nC;
   h->c_kind = pat->c_kind;
 
-  std::string err = analyze_pattern(pat->nA, pat->nP, pat->a_rowptr, pat->a_col, pat->a_vals_hint,
-                                    pat->a_vals_hint ? 1 : 0, h->sym);
-  if (err.empty())
-    err = analyze_coupling(h->sym, pat->N, pat->nC, pat->b_blockptr, pat->b_row, pat->b_col, h->cpl);
+  std::string err;
+  if (sym0 && cpl0) {
+    h->sym = *sym0;
+    h->cpl = *cpl0;
+  } else {
+    err = analyze_pattern(pat->nA, pat->nP, pat->a_rowptr, pat->a_col, pat->a_vals_hint,
+                          pat->a_vals_hint ? 1 : 0, h->sym);
+    if (err.empty())
+      err = analyze_coupling(h->sym, pat->N, pat->nC, pat->b_blockptr, pat->b_row, pat->b_col, h->cpl);
+  }
   if (!err.empty()) {
     set_error("kkt_analyze: " + err);
     delete h;
@@ -217,7 +227,8 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
     return KKT_ERR_INVALID;
   }
   h->tail_ratio = tail_ratio;
-  if (h->tail_mode) choose_tail(h->sym, h->N, kTailMaxBytes, kTailMinCols, tail_ratio);
+  if (h->tail_mode)
+    choose_tail(h->sym, h->N, h->tail_mode == 2 ? kTailMaxBytesTC : kTailMaxBytes, kTailMinCols, tail_ratio);
   else choose_tail(h->sym, h->N, 0, 0);  // no tail fits in 0 bytes
   const Symbolic& S = h->sym;
   const Coupling& C = h->cpl;
@@ -570,18 +581,25 @@ kkt_status kkt_analyze(const kkt_pattern* pat, const kkt_options* opt, kkt_handl
   kkt_default_options(&o);
   if (opt) o = *opt;
   auto t0 = std::chrono::steady_clock::now();
+  if (!(o.tail_ratio >= 0.0)) {
+    set_error("kkt_analyze: tail_ratio must be >= 0");
+    return KKT_ERR_INVALID;
+  }
   kkt_handle* best = nullptr;
-  kkt_status st = analyze_one(pat, &o, kTailRatio, &best);
+  kkt_status st = analyze_one(pat, &o, o.tail_ratio > 0.0 ? o.tail_ratio : kTailRatio, nullptr, nullptr, &best);
   if (st != KKT_OK) return st;
   // Autotuning of the dense tail: the candidate cost ratios give tails of
-  // different sizes; each distinct one is analysed and timed once on the values
-  // hint, and the fastest factor is kept.
-  if (o.autotune && pat->a_vals_hint && reinterpret_cast<Handle*>(best)->nT > 0) {
+  // different sizes; each distinct one is set up (on a copy of the first
+  // analysis) and timed once on the values hint, and the fastest factor is kept.
+  if (o.autotune && o.tail_ratio == 0.0 && pat->a_vals_hint && reinterpret_cast<Handle*>(best)->nT > 0) {
     double best_ms = time_factor(best, pat);
     std::vector<int32_t> tried = {reinterpret_cast<Handle*>(best)->nT};
+    // the first analysis, kept while `best` may be replaced
+    const Symbolic sym0 = reinterpret_cast<Handle*>(best)->sym;
+    const Coupling cpl0 = reinterpret_cast<Handle*>(best)->cpl;
     for (double r : {1.0, 1.25, 2.0, 3.0}) {
       kkt_handle* cand = nullptr;
-      if (analyze_one(pat, &o, r, &cand) != KKT_OK) continue;
+      if (analyze_one(pat, &o, r, &sym0, &cpl0, &cand) != KKT_OK) continue;
       const int32_t nT = reinterpret_cast<Handle*>(cand)->nT;
       if (std::find(tried.begin(), tried.end(), nT) != tried.end()) {
         kkt_destroy(cand);

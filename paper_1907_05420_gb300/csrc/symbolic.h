@@ -16,9 +16,13 @@ namespace kkt {
 constexpr int kMaxSnWidth = 32;
 
 // Dense tail limits: at least this many columns, and at most this many bytes
-// for the N dense triangles held at once.
+// for the N dense triangles held at once.  A tail whose updates run in FP64 on
+// the CUDA cores gains nothing from growing past the supernodal work it
+// replaces (both run at the FP64 rate), so its cap is smaller; a tail updated
+// on the tensor cores may take the whole dense top of a large grid's tree.
 constexpr int32_t kTailMinCols = 16;
-constexpr int64_t kTailMaxBytes = int64_t(24) << 30;
+constexpr int64_t kTailMaxBytes = int64_t(24) << 30;    // FP64 CUDA-core tail
+constexpr int64_t kTailMaxBytesTC = int64_t(96) << 30;  // emulated-FP64 tensor-core tail
 
 struct Symbolic {
   int32_t n = 0;   // block size nA

@@ -65,10 +65,10 @@ def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "kkt_schur.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(kkt_pattern), offsetof(kkt_pattern, a_vals_hint),"
         "sizeof(kkt_options), offsetof(kkt_options, reduced_contraction),"
-        "offsetof(kkt_options, dense_tail),"
+        "offsetof(kkt_options, dense_tail), offsetof(kkt_options, tail_ratio),"
         "sizeof(kkt_info), offsetof(kkt_info, n_launches), offsetof(kkt_info, tail_ratio));"
         "return 0;}\n")
     exe = tmp_path / "layout"
@@ -77,7 +77,7 @@ def test_struct_layouts_match_header(tmp_path):
                                           check=True).stdout.split()]
     want = [ctypes.sizeof(binding.kkt_pattern), binding.kkt_pattern.a_vals_hint.offset,
             ctypes.sizeof(binding.kkt_options), binding.kkt_options.reduced_contraction.offset,
-            binding.kkt_options.dense_tail.offset,
+            binding.kkt_options.dense_tail.offset, binding.kkt_options.tail_ratio.offset,
             ctypes.sizeof(binding.kkt_info), binding.kkt_info.n_launches.offset,
             binding.kkt_info.tail_ratio.offset]
     assert got == want

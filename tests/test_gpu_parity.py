@@ -198,6 +198,25 @@ def test_autotuned_tail():
     assert oracle.backward_error(p, x) <= 1e-10
 
 
+def test_explicit_tail_ratio():
+    """A set tail_ratio fixes the cost ratio (the autotuner is skipped); a larger
+    ratio gives a tail at least as long, and the CPU inspection library, which
+    runs the same rule, reports the same tail for the FP64 mode."""
+    from test_symbolic import analyze
+
+    p = make_problem(replace(CONFIGS["grid2383_n96"], n_per=6, name="grid2383_n6"))
+    cols = []
+    for r in (1.0, 3.0):
+        x, info = gpu_solve(p, "tf32", tail_ratio=r, autotune=1)
+        assert info["tail_ratio"] == r and info["autotune_candidates"] == 0
+        assert oracle.backward_error(p, x) <= 1e-10
+        cols.append(info["dense_tail_cols"])
+    assert cols[1] >= cols[0] > 0
+    _, info = gpu_solve(p, "fp64")
+    a = analyze(p)
+    assert info["dense_tail_cols"] == a["n"] - a["tail_col"]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "tf32"])
 def test_graph_replay_matches_direct_launches(prec):
     """The factor's launch sequence is captured once as a CUDA graph and
