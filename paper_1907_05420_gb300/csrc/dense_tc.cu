@@ -20,9 +20,12 @@
 //   k_tc_slice:  writes the tile images of the update operands (the exact
 //                shared-memory layout of one 128-row A block or 64-row B block,
 //                all digit slices contiguous) and the row scales;
-//   k_tc_update: one CTA per 128 x 64 lower tile of the trailing matrix; the
-//                images arrive by bulk copy, one thread issues the MMAs, four
-//                warps drain tensor memory and update S.
+//   k_tc_update: (TF32, BF16) one CTA per 128 x 64 lower tile of the trailing
+//                matrix; the images arrive by bulk copy, one thread issues the
+//                MMAs, four warps drain tensor memory and update S;
+//   k_tc_update_emu: (emulated FP64) one CTA per run of up to 8 tiles of a tile
+//                row, with loads, products and the read-modify-write of S
+//                overlapped across the run (below).
 //
 // Shared-memory operand layout (K-major, no swizzle): an 8-row x 16-byte core
 // matrix is 128 contiguous bytes; cores are ordered K-fastest, so the
@@ -99,6 +102,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
 // The 7 base-256 digits of u = v / 2^e in (-1, 1), truncated toward zero:
 // q = trunc(|u| 2^56), and digit s is byte 6 - s of q with the sign of v.
 // Computed on the raw bits with integer operations only (FP64 instructions
@@ -106,15 +118,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 // and E the biased exponent (a subnormal has E = 0, no implicit bit and
 // exponent -1074), so q is m shifted by E - 1075 + 56 - e; |v| < 2^e bounds q
 // below 2^56.
-__device__ __forceinline__ void digits7(double v, int e, float out[kEmuSlices]) {
-  const long long b = __double_as_longlong(v);
+// Returns q; the sign of v is the sign bit of b.
+__device__ __forceinline__ unsigned long long digits7(double v, int e, long long& b) {
+  b = __double_as_longlong(v);
   const int E = (int)((b >> 52) & 0x7FF);
   const unsigned long long m = (unsigned long long)(b & 0xFFFFFFFFFFFFFll) | (E ? (1ull << 52) : 0ull);
   const int sh = (E ? E : 1) - 1075 + 56 - e;
-  const unsigned long long a = sh >= 0 ? (sh < 64 ? m << sh : 0ull) : (sh > -64 ? m >> (-sh) : 0ull);
-  const float sg = b < 0 ? -1.f : 1.f;
-#pragma unroll
-  for (int s = 0; s < kEmuSlices; s++) out[s] = sg * (float)((a >> (8 * (kEmuSlices - 1 - s))) & 0xFFull);
+  return sh >= 0 ? (sh < 64 ? m << sh : 0ull) : (sh > -64 ? m >> (-sh) : 0ull);
 }
 
 // Biased exponent field of a double (0 for zero and subnormals).
@@ -148,6 +158,12 @@ __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S0, cons
   constexpr ModeCfg cfg = mode_cfg(MODE);
   constexpr int KG = kgroups_of(MODE);
   constexpr int kpc = 16 / cfg.esz;  // elements per 16-byte core row
+  __shared__ uint32_t bf16_of_byte[256];
+  if (MODE == 2) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+      bf16_of_byte[i] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)i));
+    __syncthreads();
+  }
   const int base = k0 + kb;
   const int total = mpadA + mpadB;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
@@ -183,20 +199,26 @@ __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S0, cons
     for (int kq = 0; kq < KG; kq++) {
       // one 16-byte core row: elements kq*kpc .. kq*kpc+kpc-1
       if (MODE == 2) {
-        float dig[kpc][kEmuSlices];
+        // BF16 bit patterns of the signed digits, from the table of the 256
+        // byte values (no conversion instructions)
+        uint32_t packed[kEmuSlices][4];
 #pragma unroll
         for (int e = 0; e < kpc; e++) {
           const int c = kq * kpc + e;  // columns >= kb (a ragged panel) are zero
           double v = (live && c < kb) ? (double)src[(int64_t)(base + rho) + (col0 + c) * n] : 0.0;
-          digits7(v, e_exp, dig[e]);
+          long long vb;
+          const unsigned long long a = digits7(v, e_exp, vb);
+          const uint32_t sgn = vb < 0 ? 0x8000u : 0u;
+#pragma unroll
+          for (int s = 0; s < kEmuSlices; s++) {
+            const uint32_t h = bf16_of_byte[(a >> (8 * (kEmuSlices - 1 - s))) & 0xFFull] | sgn;
+            packed[s][e >> 1] = (e & 1) ? (packed[s][e >> 1] | (h << 16)) : h;
+          }
         }
 #pragma unroll
         for (int s = 0; s < kEmuSlices; s++) {
-          __align__(16) __nv_bfloat16 h[8];
-#pragma unroll
-          for (int e = 0; e < 8; e++) h[e] = __float2bfloat16_rn(dig[e][s]);
           uint8_t* dst = blk_img + (int64_t)s * slice_bytes(MODE, rows_blk) + (g * KG + kq) * 128 + r8 * 16;
-          *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+          *reinterpret_cast<uint4*>(dst) = make_uint4(packed[s][0], packed[s][1], packed[s][2], packed[s][3]);
         }
       } else if (MODE == 1) {
         __align__(16) __nv_bfloat16 h[8];
@@ -250,8 +272,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n,
   T* S = S0 + bb * ts.s;
   const uint8_t* imgA = imgA0 + bb * ts.img_a;
   const uint8_t* imgB = imgB0 + bb * ts.img_b;
-  const double* scaleA = scaleA0 + bb * ts.scale;
-  const double* scaleB = scaleB0 + bb * ts.scale;
+  static_assert(MODE != 2, "the emulated-FP64 update is k_tc_update_emu");
+  (void)scaleA0;
+  (void)scaleB0;
   constexpr ModeCfg cfg = mode_cfg(MODE);
   constexpr int KG = kgroups_of(MODE);
   constexpr int A_BYTES = image_bytes(MODE, TM), B_BYTES = image_bytes(MODE, TN);
@@ -359,70 +382,23 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n,
   if (ok) {
     const int rho = I * TM + warp * 32 + lane;  // this thread's tile row
     const int row = base + rho;
-    const double sa = (MODE == 2 && rho < m) ? scaleA[rho] : 1.0;
     for (int cc = 0; cc < TN / 32; cc++) {
       uint32_t r[32];
-      if (MODE == 2) {
-        // levels 0-3 hold exact integers below 2^24: combine them exactly in
-        // int64, V = ((a0 256 + a1) 256 + a2) 256 + a3 (|V| < 2^47); levels 4-6
-        // are below 2^-32 of the product and are combined in FP32,
-        // c = a4 + a5/256 + a6/65536.  Then
-        //   (Y L^T)_ij = 2^{e_i+f_j} 2^-40 (V + c / 256) = 2^{e_i+f_j-56} W,
-        //   W = V 2^16 + round(256 c)   (|W| < 2^63),
-        // applied as cur - W p with p = 2^{e_i-56} 2^{f_j} (exact powers of two).
-        long long V[32];
-        float cf[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), r);
+      if (rho < m) {
+        // all loads of the 32 columns first, then the stores: 32 loads in flight
+        T cur[32];
 #pragma unroll
         for (int j = 0; j < 32; j++) {
-          V[j] = 0;
-          cf[j] = 0.f;
+          const int cj = J * TN + cc * 32 + j;
+          const int col = base + cj;
+          cur[j] = (cj < m && row >= col) ? S[(int64_t)row + (int64_t)col * n] : T(0);
         }
 #pragma unroll
-        for (int d = 0; d < kEmuLevels; d++) {
-          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * TN + cc * 32), r);
-#pragma unroll
-          for (int j = 0; j < 32; j++) {
-            const float fv = __uint_as_float(r[j]);
-            if (d < 4) V[j] = V[j] * 256 + (long long)__float2int_rn(fv);
-            else cf[j] += fv * (d == 4 ? 1.f : (d == 5 ? 0.00390625f : 0.0000152587890625f));
-          }
-        }
-        if (rho < m) {
-          const double pa = sa * 0x1p-56;
-          // all loads of the 32 columns first, then the stores: 32 loads in flight
-          T cur[32];
-#pragma unroll
-          for (int j = 0; j < 32; j++) {
-            const int cj = J * TN + cc * 32 + j;  // trailing column index
-            const int col = base + cj;
-            cur[j] = (cj < m && row >= col) ? S[(int64_t)row + (int64_t)col * n] : T(0);
-          }
-#pragma unroll
-          for (int j = 0; j < 32; j++) {
-            const int cj = J * TN + cc * 32 + j;
-            const int col = base + cj;
-            if (cj < m && row >= col) {
-              const long long W = V[j] * 65536 + (long long)__float2int_rn(cf[j] * 256.f);
-              S[(int64_t)row + (int64_t)col * n] = (T)fma(-(double)W, pa * scaleB[cj], (double)cur[j]);
-            }
-          }
-        }
-      } else {
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), r);
-        if (rho < m) {
-          T cur[32];
-#pragma unroll
-          for (int j = 0; j < 32; j++) {
-            const int cj = J * TN + cc * 32 + j;
-            const int col = base + cj;
-            cur[j] = (cj < m && row >= col) ? S[(int64_t)row + (int64_t)col * n] : T(0);
-          }
-#pragma unroll
-          for (int j = 0; j < 32; j++) {
-            const int cj = J * TN + cc * 32 + j;
-            const int col = base + cj;
-            if (cj < m && row >= col) S[(int64_t)row + (int64_t)col * n] = cur[j] - (T)__uint_as_float(r[j]);
-          }
+        for (int j = 0; j < 32; j++) {
+          const int cj = J * TN + cc * 32 + j;
+          const int col = base + cj;
+          if (cj < m && row >= col) S[(int64_t)row + (int64_t)col * n] = cur[j] - (T)__uint_as_float(r[j]);
         }
       }
     }
@@ -432,16 +408,360 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n,
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
+// ---- Emulated-FP64 update, pipelined over a run of tiles ----
+//
+// One CTA per task: up to kEmuRun consecutive tiles (I, J) of one tile row I.
+// The A image of the row (7 digit slices of 128 rows, 112 KB) is loaded once;
+// the B images (56 KB) go through two shared-memory buffers; the 28 digit
+// products of each tile accumulate in tensor memory (7 levels x 64 columns).
+// Warps with fixed roles:
+//   warp 0 (one lane): bulk copies of A and of the B images, ahead by one;
+//   warp 1 (one lane): tensor-memory allocation and the MMAs of each tile,
+//                      started once the epilogue has drained the previous one;
+//   warps 2-9:         the epilogue, one tile row and 32 columns per thread
+//                      (warp w reads tensor-memory lanes 32 (w mod 4) ...):
+//                      the 7 levels are read and folded into registers first,
+//                      tensor memory is handed back, and only then is S read,
+//                      updated and written, so that the next tile's products
+//                      run during this tile's global read-modify-write.
+// The scaled product W 2^{e_i+f_j-56} is built as an FP64 bit pattern with
+// integer operations (W rounded once, exponents added), and the levels are
+// read out of FP32 without conversion instructions, which on this GPU share
+// the narrow FP64 pipe; one FP64 addition per entry is left.
+// Every wait is bounded: a timeout sets *err, makes the other roles stop, lets
+// the copies and products in flight finish (bounded again) and frees tensor
+// memory before the CTA exits.
+constexpr int kEmuRun = 8;          // tiles per task at most
+// Epilogue warps: 8 (two per tensor-memory lane quadrant, 32 columns per
+// thread).  With 10 warps a thread has 168 registers; 4 epilogue warps of 64
+// columns (255 registers) left one warp per scheduler and ran 1.7x slower.
+constexpr int kEpiWarps = 8;
+constexpr int kEpiCols = TN * 4 / kEpiWarps;     // tile columns per epilogue thread
+constexpr int kEmuThreads = 64 + 32 * kEpiWarps;  // producer, MMA issuer, epilogue
+// A image and two B buffers (229,376 bytes)
+__host__ __device__ constexpr int emu_smem_bytes() { return image_bytes(2, TM) + 2 * image_bytes(2, TN); }
+
+// tasks of tile row I for jmode (0: all tiles, 1: J = 0, 2: J >= 1)
+__host__ __device__ __forceinline__ void emu_row_range(int I, int TJ, int jmode, int& jlo, int& jhi) {
+  const int cnt = min(2 * I + 2, TJ);
+  jlo = jmode == 2 ? 1 : 0;
+  jhi = jmode == 1 ? 1 : cnt;
+}
+
+__host__ __device__ __forceinline__ int emu_row_tasks(int I, int TJ, int jmode) {
+  int jlo, jhi;
+  emu_row_range(I, TJ, jmode, jlo, jhi);
+  return jhi > jlo ? (jhi - jlo + kEmuRun - 1) / kEmuRun : 0;
+}
+
+// Conversions without the conversion instructions, which share this GPU's
+// narrow FP64 pipe: FP32 additions of M = 1.5 * 2^23 put a rounded integer
+// |k| < 2^22 into the low significand bits of M + k, read back with an integer
+// subtraction.
+constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;     // bit pattern of kMagic
+
+// x an integer-valued FP32 number, |x| < 2^30: x exactly as int32
+// (x = 256 hi + lo with hi = rn(x / 256) and |lo| <= 128, both exact).
+__device__ __forceinline__ int exact_f2i(float x) {
+  const float r = fmaf(x, 0.00390625f, kMagic);
+  const float hi = r - kMagic;
+  const float lo = fmaf(-256.0f, hi, x);
+  return (__float_as_int(r) - kMagicBits) * 256 + (__float_as_int(lo + kMagic) - kMagicBits);
+}
+
+// round-to-nearest-even of an FP32 x, |x| < 2^37, as int64
+// (x = 65536 hi + lo with hi = rn(x / 65536), lo exact, |lo| <= 2^15).
+__device__ __forceinline__ long long round_f2ll(float x) {
+  const float r = fmaf(x, 0x1p-16f, kMagic);
+  const float hi = r - kMagic;
+  const float lo = fmaf(-65536.0f, hi, x);
+  return (long long)(__float_as_int(r) - kMagicBits) * 65536 + (__float_as_int(lo + kMagic) - kMagicBits);
+}
+
+// Exponent e of a positive power of two 2^e (normal or subnormal).
+__device__ __forceinline__ int pow2_exponent(double s) {
+  const long long b = __double_as_longlong(s);
+  const int E = (int)((b >> 52) & 0x7FF);
+  return E ? E - 1023 : (63 - __clzll(b)) - 1074;
+}
+
+// -RN(W 2^eoff) as an FP64 bit pattern, built with integer operations for
+// every W (|W| < 2^63) and eoff: a normal result keeps the top 53 bits of |W|
+// (round to nearest even, the carry may bump the exponent), a subnormal one the
+// bits down to 2^-1074, and a result beyond the largest finite value is an
+// infinity.  One rounding of the exact value, as fma(-W, 2^eoff, 0) would do.
+__device__ __forceinline__ double neg_scaled(long long W, int eoff) {
+  const unsigned long long sgn = W < 0 ? 0ull : (1ull << 63);  // sign of -W
+  const unsigned long long a = W < 0 ? (unsigned long long)(-W) : (unsigned long long)W;
+  const int lz = __clzll(a | 1ull);  // a = 0 handled below
+  const unsigned long long x = a << lz;  // leading one at bit 63
+  const int be = (63 - lz) + eoff + 1023;  // biased exponent of a normal result
+  const int drop = be >= 1 ? 11 : min(64, 12 - be);  // low bits of x rounded off
+  unsigned long long mant = drop < 64 ? x >> drop : 0ull;
+  const unsigned long long rem = drop < 64 ? x & ((1ull << drop) - 1ull) : x;
+  const unsigned long long half = 1ull << (drop - 1);
+  if (rem > half || (rem == half && (mant & 1ull))) mant++;
+  unsigned long long bits = be >= 1 ? ((unsigned long long)(be - 1) << 52) + mant : mant;
+  if (12 - be > 64) bits = 0ull;  // below half the smallest subnormal
+  if (be >= 2047) bits = 0x7FF0000000000000ull;
+  return __longlong_as_double((long long)(a == 0 ? 0ull : (sgn | bits)));
+}
+
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitBudget) return false;
+  }
+}
+
+__device__ __forceinline__ void bulk_load(uint8_t* dst, const uint8_t* src, int bytes, uint32_t bar) {
+  for (int off = 0; off < bytes; off += 16384) {
+    const uint32_t sz = (uint32_t)min(16384, bytes - off);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst + off)),
+                 "l"(src + off), "r"(sz), "r"(bar)
+                 : "memory");
+  }
+}
+
+__global__ void __launch_bounds__(kEmuThreads, 1)
+    k_tc_update_emu(double* __restrict__ S0, int n, int k0, int kb, int m, int TI, int TJ, int jmode,
+                    const uint8_t* __restrict__ imgA0, const uint8_t* __restrict__ imgB0,
+                    const double* __restrict__ scaleA0, const double* __restrict__ scaleB0, int* err,
+                    TcStrides ts) {
+  constexpr ModeCfg cfg = mode_cfg(2);
+  constexpr int KG = kgroups_of(2);
+  constexpr int A_BYTES = image_bytes(2, TM), B_BYTES = image_bytes(2, TN);
+  constexpr int A_SLICE = slice_bytes(2, TM), B_SLICE = slice_bytes(2, TN);
+  constexpr uint32_t TMEM_COLS = 512;  // 7 levels x 64 columns
+  constexpr int MMA_K_BYTES = 32;
+  constexpr int KSTEPS = TK * cfg.esz / MMA_K_BYTES;
+  static_assert(cfg.levels * TN <= (int)TMEM_COLS, "levels must fit tensor memory");
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + A_BYTES;  // two buffers of B_BYTES
+  __shared__ __align__(8) uint64_t bar_a, bar_bfull[2], bar_bempty[2], bar_tfull, bar_tempty;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_abort;
+
+  const int64_t bb = blockIdx.y;
+  double* S = S0 + bb * ts.s;
+  const uint8_t* imgA = imgA0 + bb * ts.img_a;
+  const uint8_t* imgB = imgB0 + bb * ts.img_b;
+  const double* scaleA = scaleA0 + bb * ts.scale;
+  const double* scaleB = scaleB0 + bb * ts.scale;
+  // task -> tile row I and its run of tiles [j0, j1)
+  int I = 0, t = blockIdx.x;
+  for (;;) {
+    const int c = emu_row_tasks(I, TJ, jmode);
+    if (t < c || I + 1 >= TI) break;
+    t -= c;
+    I++;
+  }
+  int jlo, jhi;
+  emu_row_range(I, TJ, jmode, jlo, jhi);
+  const int j0 = jlo + t * kEmuRun, j1 = min(j0 + kEmuRun, jhi);
+  const int ntile = max(0, j1 - j0);
+  const int base = k0 + kb;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_a)));
+    for (int s = 0; s < 2; s++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_bfull[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_bempty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_tfull)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_tempty)), "r"(kEpiWarps));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0 && ntile > 0) {
+      // producer
+      const uint32_t ba = smem_u32(&bar_a);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ba), "r"((uint32_t)A_BYTES)
+                   : "memory");
+      bulk_load(sA, imgA + (int64_t)I * A_BYTES, A_BYTES, ba);
+      int armed[2] = {0, 0};  // loads issued per B buffer
+      for (int u = 0; u < ntile; u++) {
+        const int s = u & 1;
+        if (u >= 2 && !mbar_wait_ab(smem_u32(&bar_bempty[s]), (uint32_t)(((u >> 1) - 1) & 1), &s_abort)) {
+          if (!s_abort) atomicExch(err, 4);
+          s_abort = 1;
+          break;
+        }
+        const uint32_t bf = smem_u32(&bar_bfull[s]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bf), "r"((uint32_t)B_BYTES)
+                     : "memory");
+        bulk_load(sB + s * B_BYTES, imgB + (int64_t)(j0 + u) * B_BYTES, B_BYTES, bf);
+        armed[s]++;
+      }
+      // the copies issued must land before the CTA's shared memory goes away
+      volatile int never = 0;
+      mbar_wait_ab(ba, 0u, &never);
+      for (int s = 0; s < 2; s++)
+        if (armed[s] > 0) mbar_wait_ab(smem_u32(&bar_bfull[s]), (uint32_t)((armed[s] - 1) & 1), &never);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && ntile > 0) {
+      // MMA issuer
+      int issued = 0;
+      if (!mbar_wait_ab(smem_u32(&bar_a), 0u, &s_abort)) {
+        if (!s_abort) atomicExch(err, 5);
+        s_abort = 1;
+      } else {
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                               ((uint32_t)(TM >> 4) << 24);
+        for (int u = 0; u < ntile; u++) {
+          const int s = u & 1;
+          if (!mbar_wait_ab(smem_u32(&bar_bfull[s]), (uint32_t)((u >> 1) & 1), &s_abort) ||
+              (u >= 1 && !mbar_wait_ab(smem_u32(&bar_tempty), (uint32_t)((u - 1) & 1), &s_abort))) {
+            if (!s_abort) atomicExch(err, 6);
+            s_abort = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint8_t* bS = sB + s * B_BYTES;
+          for (int d = 0; d < cfg.levels; d++) {
+            const uint32_t dtm = tmem + (uint32_t)(d * TN);
+            bool first = true;
+            for (int sa = 0; sa < cfg.slices; sa++) {
+              const int sb = d - sa;
+              if (sb < 0 || sb >= cfg.slices) continue;
+              for (int ks = 0; ks < KSTEPS; ks++) {
+                const uint64_t ad = umma_desc(smem_u32(sA + sa * A_SLICE + ks * MMA_K_BYTES * 8), 128, KG * 128);
+                const uint64_t bd = umma_desc(smem_u32(bS + sb * B_SLICE + ks * MMA_K_BYTES * 8), 128, KG * 128);
+                const uint32_t acc = first ? 0u : 1u;
+                first = false;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
+                    "p;\n}" ::"r"(dtm),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+              }
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&bar_bempty[s]))
+                       : "memory");
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&bar_tfull))
+                       : "memory");
+          issued++;
+        }
+      }
+      // products in flight must finish before tensor memory is freed
+      volatile int never = 0;
+      if (issued > 0) mbar_wait_ab(smem_u32(&bar_tfull), (uint32_t)((issued - 1) & 1), &never);
+    }
+  } else {
+    // epilogue: tile row rho = I*128 + 32 (warp mod 4) + lane, columns
+    // cbase .. cbase + kEpiCols - 1 of each tile
+    const int q = warp & 3, cbase = ((warp - 2) >> 2) * kEpiCols;
+    const int rho = I * TM + q * 32 + lane;
+    const int row = base + rho;
+    const bool live_row = rho < m;
+    const int ea = pow2_exponent(live_row ? scaleA[rho] : 1.0) - 56;
+    for (int u = 0; u < ntile; u++) {
+      const int J = j0 + u;
+      const int cj0 = J * TN + cbase;
+      // exponents of this lane's column scales, shared across the warp below
+      int ebl[kEpiCols / 32];
+#pragma unroll
+      for (int g = 0; g < kEpiCols / 32; g++)
+        ebl[g] = pow2_exponent(cj0 + g * 32 + lane < m ? scaleB[cj0 + g * 32 + lane] : 1.0);
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait_ab(smem_u32(&bar_tfull), (uint32_t)(u & 1), &s_abort);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) {
+        if (lane == 0) {
+          if (!s_abort) atomicExch(err, 7);
+          s_abort = 1;
+        }
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      // two halves of 16 columns: fold the 7 levels, then
+      // W = V 2^16 + round(256 c) and nd = -W 2^{e_i + f_j - 56}
+      double nd[kEpiCols];
+#pragma unroll
+      for (int hh = 0; hh < kEpiCols / 16; hh++) {
+        long long V[16];
+        float cf[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          V[j] = 0;
+          cf[j] = 0.f;
+        }
+#pragma unroll
+        for (int d = 0; d < kEmuLevels; d++) {
+          uint32_t r[16];
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * TN + cbase + hh * 16), r);
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            const float fv = __uint_as_float(r[j]);
+            if (d < 4) V[j] = V[j] * 256 + exact_f2i(fv);  // levels 0-3: exact integers below 2^24
+            else cf[j] += fv * (d == 4 ? 1.f : (d == 5 ? 0.00390625f : 0.0000152587890625f));
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          const long long W = V[j] * 65536 + round_f2ll(cf[j] * 256.f);  // 256 c can pass 2^31
+          const int eb = __shfl_sync(0xffffffffu, ebl[(hh * 16 + j) >> 5], (hh * 16 + j) & 31);
+          nd[hh * 16 + j] = neg_scaled(W, ea + eb);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_tempty)) : "memory");
+      if (live_row) {
+        // two halves of 16 columns: 16 loads in flight per thread, then the stores
+#pragma unroll
+        for (int hh = 0; hh < kEpiCols / 16; hh++) {
+          double cur[16];
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            const int cj = cj0 + hh * 16 + j, col = base + cj;
+            cur[j] = (cj < m && row >= col) ? S[(int64_t)row + (int64_t)col * n] : 0.0;
+          }
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            const int cj = cj0 + hh * 16 + j, col = base + cj;
+            if (cj < m && row >= col) S[(int64_t)row + (int64_t)col * n] = cur[j] + nd[hh * 16 + j];
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
 // ---- FP32 panel kernels for the TF32 / BF16 modes (same steps as the FP64 ones in dense.cu) ----
 
 __global__ void k_to_f32(const double* __restrict__ S, float* __restrict__ S32, int64_t n2) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n2; q += (int64_t)gridDim.x * blockDim.x)
     S32[q] = (float)S[q];
-}
-
-__global__ void k_dense_diag_scale_f(const float* __restrict__ S, double* __restrict__ x, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    x[i] /= (double)S[i + (int64_t)i * n];
 }
 
 // One blocked LDL^T of nb matrices of order n (matrix b at S + b * ts.s):
@@ -512,22 +832,33 @@ cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int npiv, int nb, const TcSt
     }
     int tiles = 0;
     for (int I = 0; I < TI; I++) tiles += std::min(2 * I + 2, TJ);
-    h.launches++;
+    // one launch of the update over the tiles of jmode (0 all, 1 J = 0, 2 J >= 1)
+    auto update = [&](int jmode, cudaStream_t us, int uprio) -> cudaError_t {
+      h.launches++;
+      if constexpr (MODE == 2) {
+        int tasks = 0;
+        for (int I = 0; I < TI; I++) tasks += emu_row_tasks(I, TJ, jmode);
+        return launch_prio(k_tc_update_emu, dim3(tasks, nb), dim3(kEmuThreads), emu_smem_bytes(), us, uprio,
+                           (double*)S, n, k0, kb, m, TI, TJ, jmode, (const uint8_t*)imgA, (const uint8_t*)imgB,
+                           (const double*)scaleA, (const double*)scaleB, h.dev_err, ts);
+      } else {
+        const int cnt = jmode == 0 ? tiles : (jmode == 1 ? TI : tiles - TI);
+        return launch_prio(k_tc_update<MODE, T>, dim3(cnt, nb), dim3(128), smem, us, uprio, S, n, k0, kb, m, TJ,
+                           jmode, (const uint8_t*)imgA, (const uint8_t*)imgB, (const double*)scaleA,
+                           (const double*)scaleB, h.dev_err, ts);
+      }
+    };
     if (!side || TJ < 2) {
-      k_tc_update<MODE, T><<<dim3(tiles, nb), 128, smem, st>>>(S, n, k0, kb, m, TJ, 0, imgA, imgB, scaleA, scaleB,
-                                                               h.dev_err, ts);
+      e = update(0, st, 0);
       continue;
     }
     e = cudaEventRecord(h.ev_main, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(side, h.ev_main, 0);
     if (e != cudaSuccess) break;
-    k_tc_update<MODE, T><<<dim3(tiles - TI, nb), 128, smem, side>>>(S, n, k0, kb, m, TJ, 2, imgA, imgB, scaleA,
-                                                                      scaleB, h.dev_err, ts);
-    e = cudaEventRecord(h.ev_side, side);
+    e = update(2, side, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(h.ev_side, side);
     side_busy = true;
-    launch_prio(k_tc_update<MODE, T>, dim3(TI, nb), dim3(128), smem, st, prio, S, n, k0, kb, m, TJ, 1, imgA, imgB,
-                scaleA, scaleB, h.dev_err, ts);
-    h.launches++;
+    if (e == cudaSuccess) e = update(1, st, prio);
   }
   if (side_busy && e == cudaSuccess) e = cudaStreamWaitEvent(caller, h.ev_side, 0);
   if (st != caller && e == cudaSuccess) {  // join the high-priority chain
@@ -547,8 +878,7 @@ cudaError_t dense_tc_prepare() {
     e = cudaFuncSetAttribute(k_tc_update<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              image_bytes(1, TM) + image_bytes(1, TN));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_tc_update<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             image_bytes(2, TM) + image_bytes(2, TN));
+    e = cudaFuncSetAttribute(k_tc_update_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, emu_smem_bytes());
   return e;
 }
 
