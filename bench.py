@@ -36,6 +36,18 @@ WORKLOAD_DESC = ("grid2383_n96: synthetic 2,383-bus grid, 2,900 lines, 327 gener
 L2_FLUSH_BYTES = 256 << 20
 
 
+def workload_desc(name):
+    """The config.workload string: the named instance and its sizes."""
+    if name == WORKLOAD:
+        return WORKLOAD_DESC
+    from gen import CONFIGS
+
+    g = CONFIGS[name]
+    return (f"{name}: synthetic {g.n_bus:,}-bus grid, {g.n_line:,} lines, {g.n_gen:,} generators, "
+            f"{g.n_stor:,} storage units, N={g.n_per} periods; blocks nA={g.n_a:,}; "
+            f"S {g.n_c:,} x {g.n_c:,}")
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -157,7 +169,7 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "precision": "fp64", "parallelism": "none (host)"},
+        "config": {"workload": workload_desc(args.workload), "precision": "fp64", "parallelism": "none (host)"},
         "latency_ms": {"p50": 1e3 * statistics.median(times),
                        "p99": 1e3 * max(times) if len(times) < 100 else
                        1e3 * sorted(times)[int(0.99 * len(times))]},
@@ -530,7 +542,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "f64+tf32", "bf16": "f64+bf16", "f64emu": "f64+bf16x7"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "precision": args.prec,
+        "config": {"workload": workload_desc(args.workload), "precision": args.prec,
                    "l2": "256 MB buffer written before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
