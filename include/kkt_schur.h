@@ -192,6 +192,54 @@ kkt_status kkt_analyze(const kkt_pattern* pattern, const kkt_options* opt, kkt_h
 kkt_status kkt_factor(kkt_handle* h, const double* a_vals, const double* b_vals,
                       const double* c_vals, int32_t on_device, void* stream);
 
+/* ---- inertia correction (Sec. 2, inertia correction and curvature detection) ----
+ * The IPM needs K with inertia (N*nP + nC, N*(nA - nP), 0): positive pivots for
+ * the primal rows of every block and for the coupling variables, negative ones
+ * for the multipliers.  When the factor shows another inertia, the diagonal is
+ * shifted, K + diag(dw I on the primal rows of every A_i and on C, -dc I on the
+ * dual rows), and refactored with growing dw until the inertia is right.  The
+ * trial values follow the usual interior-point rule (the paper names the rule,
+ * not its constants; these are the defaults below):
+ *   first trial after the unshifted factor: dw = delta_w_init, or, once a call
+ *     on this handle has succeeded with dw > 0, max(delta_w_min, shrink * last dw);
+ *   dc = delta_c when a pivot of a block factor was zero or replaced under
+ *     pivot_eps (a singular or nearly singular Jacobian), else 0;
+ *   next trials: dw *= grow_first while no call on the handle has needed a
+ *     shift, dw *= grow afterwards; give up when dw > delta_w_max or after
+ *     max_trials factorizations (KKT_ERR_INERTIA; the handle then holds the
+ *     last trial's factor).
+ * The inertia of S counts: in KKT_TF32 / KKT_BF16 mode a factor of S with the
+ * wrong count is first redone FP64-accurately (as the refinement fallback
+ * does), since its reduced-precision pivot signs can be wrong on an
+ * ill-conditioned S. */
+typedef struct {
+  double delta_w_init; /* 1e-4 */
+  double delta_w_min;  /* 1e-20 */
+  double delta_w_max;  /* 1e40 */
+  double grow_first;   /* 100 */
+  double grow;         /* 8 */
+  double shrink;       /* 1/3 */
+  double delta_c;      /* 1e-8 */
+  int32_t max_trials;  /* 40 */
+  int32_t reserved;
+} kkt_inertia_options;
+
+typedef struct {
+  double delta_w, delta_c; /* the shifts of the factor the handle holds */
+  int32_t trials;          /* factorizations done (1: the unshifted factor was right) */
+  int32_t reserved;
+} kkt_inertia_result;
+
+void kkt_default_inertia_options(kkt_inertia_options* opt);
+
+/* kkt_factor with inertia correction (above).  Arguments as kkt_factor, plus
+ * opt (NULL: defaults) and result (may be NULL).  Synchronizes `stream` after
+ * every trial (the inertia is read on the host).  kkt_solve afterwards solves
+ * the shifted system, whose matrix the refinement's residual also uses. */
+kkt_status kkt_factor_inertia(kkt_handle* h, const double* a_vals, const double* b_vals,
+                              const double* c_vals, int32_t on_device, void* stream,
+                              const kkt_inertia_options* opt, kkt_inertia_result* result);
+
 /* Solve K x = rhs for nrhs right-hand sides (stacked, each N*nA + nC long)
  * with the current factorization, refined in FP64 to opt.refine_tol.
  * rhs and x: host (on_device 0) or device (1) arrays.  Returns

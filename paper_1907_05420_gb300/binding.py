@@ -62,11 +62,22 @@ class kkt_info(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class kkt_inertia_options(C.Structure):
+    _fields_ = [("delta_w_init", C.c_double), ("delta_w_min", C.c_double), ("delta_w_max", C.c_double),
+                ("grow_first", C.c_double), ("grow", C.c_double), ("shrink", C.c_double),
+                ("delta_c", C.c_double), ("max_trials", C.c_int32), ("reserved", C.c_int32)]
+
+
+class kkt_inertia_result(C.Structure):
+    _fields_ = [("delta_w", C.c_double), ("delta_c", C.c_double), ("trials", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 # every symbol the header declares
 EXPORTS = ["kkt_default_options", "kkt_analyze", "kkt_factor", "kkt_solve", "kkt_get_info",
            "kkt_destroy", "kkt_status_string", "kkt_last_error", "kkt_measure_fp64_peak",
            "kkt_solve_noalloc", "kkt_batch_factor_solve", "kkt_server_create", "kkt_server_submit",
-           "kkt_server_poll", "kkt_server_destroy"]
+           "kkt_server_poll", "kkt_server_destroy", "kkt_default_inertia_options", "kkt_factor_inertia"]
 
 _lib = None
 
@@ -120,6 +131,11 @@ def load(build_if_missing: bool = True):
     L.kkt_server_poll.restype = C.c_int
     L.kkt_server_destroy.argtypes = [C.c_void_p]
     L.kkt_server_destroy.restype = C.c_int
+    L.kkt_default_inertia_options.argtypes = [C.POINTER(kkt_inertia_options)]
+    L.kkt_default_inertia_options.restype = None
+    L.kkt_factor_inertia.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                     C.POINTER(kkt_inertia_options), C.POINTER(kkt_inertia_result)]
+    L.kkt_factor_inertia.restype = C.c_int
     _lib = L
     return L
 
@@ -203,6 +219,30 @@ def kkt_factor(h, a_vals, b_vals, c_vals, stream=None):
     if len({da, db, dc}) != 1:
         raise ValueError("a_vals, b_vals and c_vals must all be host or all device arrays")
     return _check(load().kkt_factor(h, pa, pb, pc, da, _stream_ptr(stream)))
+
+
+def kkt_default_inertia_options(**kw) -> kkt_inertia_options:
+    opt = kkt_inertia_options()
+    load().kkt_default_inertia_options(C.byref(opt))
+    for k, v in kw.items():
+        setattr(opt, k, v)
+    return opt
+
+
+def kkt_factor_inertia(h, a_vals, b_vals, c_vals, opt: kkt_inertia_options | None = None, stream=None,
+                       allow_wrong_inertia=False) -> dict:
+    """kkt_factor with inertia correction; returns the shifts of the factor
+    the handle holds and the number of factorizations (include/kkt_schur.h)."""
+    pa, da = _ptr(a_vals)
+    pb, db = _ptr(b_vals)
+    pc, dc = _ptr(c_vals)
+    if len({da, db, dc}) != 1:
+        raise ValueError("a_vals, b_vals and c_vals must all be host or all device arrays")
+    res = kkt_inertia_result()
+    st = load().kkt_factor_inertia(h, pa, pb, pc, da, _stream_ptr(stream),
+                                   C.byref(opt) if opt is not None else None, C.byref(res))
+    _check(st, (5,) if allow_wrong_inertia else ())
+    return {"status": st, "delta_w": res.delta_w, "delta_c": res.delta_c, "trials": res.trials}
 
 
 def kkt_solve(h, rhs, x, nrhs=1, stream=None, allow_not_converged=False):

@@ -44,7 +44,7 @@ kkt_status cuda_status(cudaError_t e, const char* what) {
 void free_all(Handle* h) {
   void* ptrs[] = {h->d.sn_first, h->d.sn_rowptr, h->d.sn_rows, h->d.sn_valoff, h->d.upd_ptr,
                   h->d.upd_src, h->d.upd_r0, h->d.upd_r1, h->d.upd_reloff, h->d.upd_rel,
-                  h->d.lvl_sn, h->d.perm, h->d.a_map, h->d.col_primal, h->d.col_dpos, h->d.fwork, h->d.frange,
+                  h->d.lvl_sn, h->d.perm, h->d.a_map, h->d.col_primal, h->d.col_dpos, h->d.diag_pos, h->d.fwork, h->d.frange,
                   h->d.full_rowptr, h->d.full_col, h->d.full_src, h->d.b_row, h->d.b_col,
                   h->d.b_blockptr, h->d.e_t, h->d.e_block, h->d.wpos, h->d.sn_wrow, h->d.w_dpos,
                   h->d.w_col, h->d.reach_lvl_sn, h->d.s_key, h->d.s_ptr, h->d.s_e1, h->d.s_e2,
@@ -246,6 +246,16 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   h->nTa = h->nT + (h->tail_aug ? C.k : 0);
   h->nnzA = pat->a_rowptr[n];
   h->nnzB = nnzB;
+  // position of every row's diagonal entry (the inertia-correction shift)
+  std::vector<int32_t> diag_pos(n, -1);
+  for (int32_t r = 0; r < n; r++)
+    for (int32_t p = pat->a_rowptr[r]; p < pat->a_rowptr[r + 1]; p++)
+      if (pat->a_col[p] == r) diag_pos[r] = p;
+  if (std::find(diag_pos.begin(), diag_pos.end(), -1) != diag_pos.end()) {
+    set_error("kkt_analyze: a row of A has no diagonal entry");
+    delete h;
+    return KKT_ERR_INVALID;
+  }
   h->lvl_ptr = S.lvl_ptr;
   h->reach_lvl_ptr = C.reach_lvl_ptr;
   // reach supernodes outside the tail, by level (the W solve before the tail)
@@ -400,6 +410,7 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   UP(a_map, S.a_map);
   UP(col_primal, col_primal);
   UP(col_dpos, col_dpos);
+  UP(diag_pos, diag_pos);
   UP(fwork, fwork);
   UP(frange, frange);
   UP(flvl_sn, flvl_sn);
@@ -567,6 +578,54 @@ double time_factor(kkt_handle* hh, const kkt_pattern* pat) {
   return ms;
 }
 
+// The factor of the input values with the inertia-correction shift (dw, dc)
+// applied to the device copy (none when both are 0).
+kkt_status factor_values(Handle* h, const double* a_vals, const double* b_vals, const double* c_vals,
+                         int32_t on_device, cudaStream_t st, double dw, double dc) {
+  h->stream = st;
+  (void)cudaGetLastError();  // drop a stale non-sticky error left by an unrelated call
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const int64_t nc_vals = h->c_kind == 0 ? (int64_t)h->nC : (int64_t)h->nC * h->nC;
+  KKT_CUDA(cudaEventRecord(h->ev_f0, st));
+  KKT_CUDA(cudaMemcpyAsync(h->a_vals, a_vals, sizeof(double) * h->nnzA * h->N, kind, st));
+  if (h->nnzB > 0) KKT_CUDA(cudaMemcpyAsync(h->b_vals, b_vals, sizeof(double) * h->nnzB, kind, st));
+  if (nc_vals > 0) KKT_CUDA(cudaMemcpyAsync(h->c_vals, c_vals, sizeof(double) * nc_vals, kind, st));
+  if (dw != 0.0 || dc != 0.0) KKT_CUDA(launch_shift_diag(*h, dw, dc, st));
+  h->g_reduced = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && h->opt.reduced_contraction &&
+                 contract_g_tc_supported(*h);
+  h->s_factor = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) ? 1 : 0;
+  if (h->opt.use_graphs && !h->graph_failed && !h->factor_exec) capture_factor(*h);
+  if (h->factor_exec) {
+    KKT_CUDA(cudaGraphLaunch(h->factor_exec, st));
+    h->launches += h->graph_launches;
+  } else {
+    KKT_CUDA(enqueue_factor(*h, st));
+  }
+  h->info.fell_back_fp64 = 0;
+  h->schur_pending = true;
+  KKT_CUDA(cudaEventRecord(h->ev_f1, st));
+  KKT_CUDA(cudaEventRecord(h->ev_done, st));
+  h->factored = true;
+  h->timed_factor = true;
+  return KKT_OK;
+}
+
+// The factor of S redone FP64-accurately (emulated FP64 on the tensor cores)
+// after a reduced-precision one, from an FP64 contraction if G was reduced.
+kkt_status refactor_s_fp64(Handle* h, cudaStream_t st) {
+  KKT_CUDA(cudaMemsetAsync(h->counters + kNumCounters, 0, sizeof(unsigned long long) * kNumCounters, st));
+  if (h->g_reduced) {
+    // S was assembled from a reduced-precision contraction: rebuild it in FP64
+    KKT_CUDA(launch_contract_g(*h, st));
+    KKT_CUDA(launch_assemble_s(*h, st));
+    h->g_reduced = false;
+  }
+  KKT_CUDA(launch_dense_ldlt_tc(*h, KKT_F64_EMULATED, h->counters + kNumCounters, st));
+  h->s_factor = 0;
+  h->info.fell_back_fp64 = 1;
+  return KKT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -630,33 +689,100 @@ kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals
     set_error("kkt_factor: null argument");
     return KKT_ERR_INVALID;
   }
-  cudaStream_t st = (cudaStream_t)stream;
-  h->stream = st;
-  (void)cudaGetLastError();  // drop a stale non-sticky error left by an unrelated call
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  const int64_t nc_vals = h->c_kind == 0 ? (int64_t)h->nC : (int64_t)h->nC * h->nC;
-  KKT_CUDA(cudaEventRecord(h->ev_f0, st));
-  KKT_CUDA(cudaMemcpyAsync(h->a_vals, a_vals, sizeof(double) * h->nnzA * h->N, kind, st));
-  if (h->nnzB > 0) KKT_CUDA(cudaMemcpyAsync(h->b_vals, b_vals, sizeof(double) * h->nnzB, kind, st));
-  if (nc_vals > 0) KKT_CUDA(cudaMemcpyAsync(h->c_vals, c_vals, sizeof(double) * nc_vals, kind, st));
-  h->g_reduced = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && h->opt.reduced_contraction &&
-                 contract_g_tc_supported(*h);
-  h->s_factor = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) ? 1 : 0;
-  if (h->opt.use_graphs && !h->graph_failed && !h->factor_exec) capture_factor(*h);
-  if (h->factor_exec) {
-    KKT_CUDA(cudaGraphLaunch(h->factor_exec, st));
-    h->launches += h->graph_launches;
-  } else {
-    KKT_CUDA(enqueue_factor(*h, st));
-  }
-  h->info.fell_back_fp64 = 0;
-  h->schur_pending = true;
-  KKT_CUDA(cudaEventRecord(h->ev_f1, st));
-  KKT_CUDA(cudaEventRecord(h->ev_done, st));
-  h->factored = true;
-  h->timed_factor = true;
-  return KKT_OK;
+  return factor_values(h, a_vals, b_vals, c_vals, on_device, (cudaStream_t)stream, 0.0, 0.0);
 }
+
+void kkt_default_inertia_options(kkt_inertia_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->delta_w_init = 1e-4;
+  opt->delta_w_min = 1e-20;
+  opt->delta_w_max = 1e40;
+  opt->grow_first = 100.0;
+  opt->grow = 8.0;
+  opt->shrink = 1.0 / 3.0;
+  opt->delta_c = 1e-8;
+  opt->max_trials = 40;
+}
+
+kkt_status kkt_factor_inertia(kkt_handle* hh, const double* a_vals, const double* b_vals, const double* c_vals,
+                              int32_t on_device, void* stream, const kkt_inertia_options* opt,
+                              kkt_inertia_result* result) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !a_vals || (h->nnzB > 0 && !b_vals) || (h->nC > 0 && !c_vals)) {
+    set_error("kkt_factor_inertia: null argument");
+    return KKT_ERR_INVALID;
+  }
+  kkt_inertia_options o;
+  kkt_default_inertia_options(&o);
+  if (opt) o = *opt;
+  if (!(o.delta_w_init > 0.0) || !(o.delta_w_min > 0.0) || !(o.delta_w_max >= o.delta_w_init) ||
+      !(o.grow_first > 1.0) || !(o.grow > 1.0) || !(o.shrink > 0.0 && o.shrink < 1.0) || !(o.delta_c >= 0.0) ||
+      o.max_trials < 1) {
+    set_error("kkt_factor_inertia: invalid options");
+    return KKT_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // expected pivot signs: blocks (N*nP, N*nD, 0), S (nC, 0, 0)
+  const uint64_t pos_blk = (uint64_t)h->N * h->nP, neg_blk = (uint64_t)h->N * (h->nA - h->nP);
+  unsigned long long c[2 * kNumCounters];
+  int dev_err = 0;
+  auto read_counts = [&]() -> kkt_status {
+    KKT_CUDA(cudaMemcpyAsync(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost, st));
+    KKT_CUDA(cudaMemcpyAsync(&dev_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KKT_CUDA(cudaStreamSynchronize(st));
+    if (dev_err != 0) {
+      set_error("kkt_factor_inertia: a bounded device wait ran out");
+      return KKT_ERR_TIMEOUT;
+    }
+    return KKT_OK;
+  };
+  double dw = 0.0, dc = 0.0;
+  int32_t trials = 0;
+  kkt_status status = KKT_ERR_INERTIA;
+  for (;;) {
+    kkt_status fs = factor_values(h, a_vals, b_vals, c_vals, on_device, st, dw, dc);
+    if (fs == KKT_OK) fs = read_counts();
+    if (fs != KKT_OK) return fs;
+    trials++;
+    const bool blocks_ok =
+        c[kPos] == pos_blk && c[kNeg] == neg_blk && c[kZero] == 0 && c[kPerturbed] == 0;
+    auto s_right = [&]() {
+      return c[kNumCounters + kPos] == (uint64_t)h->nC && c[kNumCounters + kNeg] == 0 &&
+             c[kNumCounters + kZero] == 0;
+    };
+    bool s_ok = s_right();
+    if (blocks_ok && !s_ok && h->s_factor == 1) {
+      // reduced-precision pivot signs of S are not reliable: recount them on
+      // an FP64-accurate factor before shifting
+      fs = refactor_s_fp64(h, st);
+      if (fs == KKT_OK) fs = read_counts();
+      if (fs != KKT_OK) return fs;
+      s_ok = s_right();
+    }
+    if (blocks_ok && s_ok) {
+      status = KKT_OK;
+      break;
+    }
+    if (trials >= o.max_trials) break;
+    if (c[kZero] > 0 || c[kPerturbed] > 0) dc = o.delta_c;
+    double next;
+    if (dw == 0.0) next = h->last_delta_w > 0.0 ? std::max(o.delta_w_min, o.shrink * h->last_delta_w) : o.delta_w_init;
+    else next = dw * (h->last_delta_w > 0.0 ? o.grow : o.grow_first);
+    if (next > o.delta_w_max) break;
+    dw = next;
+  }
+  if (status == KKT_OK && dw > 0.0) h->last_delta_w = dw;
+  if (result) {
+    result->delta_w = dw;
+    result->delta_c = dc;
+    result->trials = trials;
+    result->reserved = 0;
+  }
+  if (status != KKT_OK) set_error("kkt_factor_inertia: no shift within the limits gave the expected inertia");
+  return status;
+}
+
 
 kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs, int32_t on_device,
                      void* stream) {
@@ -717,16 +843,8 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
         if (h->s_factor == 1 && h->opt.fp64_fallback) {
           // refinement with the FP32 factor of S stalls: refactor S (still the
           // assembled FP64 matrix) FP64-accurately and restart from its solve
-          KKT_CUDA(cudaMemsetAsync(h->counters + kNumCounters, 0, sizeof(unsigned long long) * kNumCounters, st));
-          if (h->g_reduced) {
-            // S was assembled from a reduced-precision contraction: rebuild it in FP64
-            KKT_CUDA(launch_contract_g(*h, st));
-            KKT_CUDA(launch_assemble_s(*h, st));
-            h->g_reduced = false;
-          }
-          KKT_CUDA(launch_dense_ldlt_tc(*h, KKT_F64_EMULATED, h->counters + kNumCounters, st));
-          h->s_factor = 0;
-          h->info.fell_back_fp64 = 1;
+          const kkt_status rs = refactor_s_fp64(h, st);
+          if (rs != KKT_OK) return rs;
           KKT_CUDA(launch_apply_inverse(*h, h->rhs, h->x, st));
           eta_prev = INFINITY;
           steps++;

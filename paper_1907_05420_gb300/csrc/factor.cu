@@ -39,6 +39,26 @@ __global__ void k_scatter_a(const double* __restrict__ a_vals, int64_t nnzA,
   }
 }
 
+// Inertia-correction shift of the copied values: +dw on the diagonal of the
+// primal rows of every block, -dc on the dual rows, +dw on C's diagonal (the
+// coupling variables are primal).  One thread per (block, row) or C entry.
+__global__ void k_shift_diag(double* __restrict__ a_vals, int64_t nnzA, const int32_t* __restrict__ diag_pos,
+                             int nA, int nP, int N, double* __restrict__ c_vals, int nC, int c_kind, double dw,
+                             double dc) {
+  const int64_t na = (int64_t)N * nA;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < na + nC;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    if (q < na) {
+      const int64_t b = q / nA;
+      const int r = (int)(q - b * nA);
+      a_vals[b * nnzA + diag_pos[r]] += r < nP ? dw : -dc;
+    } else {
+      const int64_t i = q - na;
+      c_vals[c_kind == 0 ? i : i * nC + i] += dw;
+    }
+  }
+}
+
 // max |a| of each block (threshold base of the pivot perturbation)
 __global__ void k_block_absmax(const double* __restrict__ a_vals, int64_t nnzA,
                                double* __restrict__ anorm) {
@@ -53,16 +73,6 @@ __global__ void k_block_absmax(const double* __restrict__ a_vals, int64_t nnzA,
     __syncthreads();
   }
   if (threadIdx.x == 0) anorm[blockIdx.x] = red[0];
-}
-
-__device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int v) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (a[mid] < v) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
 }
 
 // One CTA per (64-row tile of supernode s, block).  The tile's update is
@@ -172,6 +182,16 @@ __global__ void __launch_bounds__(256) k_panel_factor(const int32_t* __restrict_
 }
 
 }  // namespace
+
+cudaError_t launch_shift_diag(Handle& h, double dw, double dc, cudaStream_t st) {
+  const int64_t total = (int64_t)h.N * h.nA + h.nC;
+  if (total == 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+  k_shift_diag<<<grid, 256, 0, st>>>(h.a_vals, h.nnzA, h.d.diag_pos, h.nA, h.nP, h.N, h.c_vals, h.nC, h.c_kind,
+                                     dw, dc);
+  h.launches++;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_scatter_a(Handle& h, cudaStream_t st) {
   const int64_t pt = h.sym.panel_total;

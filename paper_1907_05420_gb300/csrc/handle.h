@@ -40,6 +40,7 @@ struct DevSym {
   int64_t* a_map = nullptr;
   int32_t* col_primal = nullptr;   // per column (elimination order): 1 if primal
   int64_t* col_dpos = nullptr;     // per column: panel position of its pivot
+  int32_t* diag_pos = nullptr;     // per row of A (pattern order): position of its diagonal entry
   // factor update work items: (supernode, first panel row, last panel row)
   int32_t* fwork = nullptr;        // 4 ints per item: s, lo, hi, offset into frange
   int32_t* frange = nullptr;       // per (item, update of s): rows [ia, ib) of d inside the tile
@@ -101,6 +102,7 @@ struct Handle {
   std::vector<int32_t> flvl_ptr;       // supernodes outside the dense tail per level (factor)
   int32_t nT = 0;                      // columns of the dense tail (0 = none)
   double tail_ratio = 0.0;             // cost ratio the tail was chosen with
+  double last_delta_w = 0.0;           // inertia correction: the last successful shift > 0 (0: none yet)
   int32_t nTa = 0;                     // order of the tail matrices: nT, plus k augmented rows
   bool tail_aug = false;               // tail augmented by the k coupling rows (Sec. 4.2)
   int32_t nw_nt = 0;                   // W rows outside the tail (the first ones)
@@ -193,6 +195,8 @@ cudaError_t dense_prepare();
 cudaError_t dense_tc_prepare();
 cudaError_t schur_tc_prepare();
 // ---- kernel launchers (factor.cu) ----
+// a_vals[i][diag(r)] += dw for primal rows r, -= dc for dual rows; C's diagonal += dw
+cudaError_t launch_shift_diag(Handle& h, double dw, double dc, cudaStream_t st);
 cudaError_t launch_scatter_a(Handle& h, cudaStream_t st);
 cudaError_t launch_factor_levels(Handle& h, cudaStream_t st);
 // ---- (tail.cu) ----

@@ -65,11 +65,13 @@ def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "kkt_schur.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(kkt_pattern), offsetof(kkt_pattern, a_vals_hint),"
         "sizeof(kkt_options), offsetof(kkt_options, reduced_contraction),"
         "offsetof(kkt_options, dense_tail), offsetof(kkt_options, tail_ratio),"
-        "sizeof(kkt_info), offsetof(kkt_info, n_launches), offsetof(kkt_info, tail_ratio));"
+        "sizeof(kkt_info), offsetof(kkt_info, n_launches), offsetof(kkt_info, tail_ratio),"
+        "sizeof(kkt_inertia_options), offsetof(kkt_inertia_options, max_trials),"
+        "sizeof(kkt_inertia_result), offsetof(kkt_inertia_result, trials));"
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -79,5 +81,7 @@ def test_struct_layouts_match_header(tmp_path):
             ctypes.sizeof(binding.kkt_options), binding.kkt_options.reduced_contraction.offset,
             binding.kkt_options.dense_tail.offset, binding.kkt_options.tail_ratio.offset,
             ctypes.sizeof(binding.kkt_info), binding.kkt_info.n_launches.offset,
-            binding.kkt_info.tail_ratio.offset]
+            binding.kkt_info.tail_ratio.offset,
+            ctypes.sizeof(binding.kkt_inertia_options), binding.kkt_inertia_options.max_trials.offset,
+            ctypes.sizeof(binding.kkt_inertia_result), binding.kkt_inertia_result.trials.offset]
     assert got == want
