@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["api.cu", "factor.cu", "tail.cu", "schur.cu", "dense.cu", "solve.cu", "probe.cu", "noalloc.cu", "dense_tc.cu",
       "schur_tc.cu"]
 CPP = ["symbolic.cpp", "serve.cpp"]
-HEADERS = ["handle.h", "symbolic.h", "dense_kernels.cuh", "pivot.cuh"]
+HEADERS = ["handle.h", "symbolic.h", "dense_kernels.cuh", "pivot.cuh", "emu_arith.cuh"]
 
 
 def _nvcc() -> str:

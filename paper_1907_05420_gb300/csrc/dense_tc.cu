@@ -34,6 +34,7 @@
 #include <cuda_bf16.h>
 
 #include "dense_kernels.cuh"
+#include "emu_arith.cuh"
 
 namespace kkt {
 
@@ -42,7 +43,6 @@ namespace {
 constexpr int TM = 128;       // rows of an A block (MMA M)
 constexpr int TN = 64;        // rows of a B block (MMA N)
 constexpr int TK = kDenseNB;  // panel width = reduction length
-constexpr int kEmuSlices = 7;
 constexpr int kEmuLevels = 7;
 constexpr long long kWaitBudget = 4000000000LL;  // cycles (~2 s)
 
@@ -111,26 +111,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
-// The 7 base-256 digits of u = v / 2^e in (-1, 1), truncated toward zero:
-// q = trunc(|u| 2^56), and digit s is byte 6 - s of q with the sign of v.
-// Computed on the raw bits with integer operations only (FP64 instructions
-// are scarce on this GPU): |v| = m 2^(E - 1075) with m the 53-bit significand
-// and E the biased exponent (a subnormal has E = 0, no implicit bit and
-// exponent -1074), so q is m shifted by E - 1075 + 56 - e; |v| < 2^e bounds q
-// below 2^56.
-// Returns q; the sign of v is the sign bit of b.
-__device__ __forceinline__ unsigned long long digits7(double v, int e, long long& b) {
-  b = __double_as_longlong(v);
-  const int E = (int)((b >> 52) & 0x7FF);
-  const unsigned long long m = (unsigned long long)(b & 0xFFFFFFFFFFFFFll) | (E ? (1ull << 52) : 0ull);
-  const int sh = (E ? E : 1) - 1075 + 56 - e;
-  return sh >= 0 ? (sh < 64 ? m << sh : 0ull) : (sh > -64 ? m >> (-sh) : 0ull);
-}
-
-// Biased exponent field of a double (0 for zero and subnormals).
-__device__ __forceinline__ int exp_field(double v) {
-  return (int)((__double_as_longlong(v) >> 52) & 0x7FF);
-}
 
 
 // Images of the operands of one panel step.  Rows rho in [0, m) are trailing
@@ -161,7 +141,7 @@ __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S0, cons
   __shared__ uint32_t bf16_of_byte[256];
   if (MODE == 2) {
     for (int i = threadIdx.x; i < 256; i += blockDim.x)
-      bf16_of_byte[i] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)i));
+      bf16_of_byte[i] = bf16_bits_of_byte((uint32_t)i);
     __syncthreads();
   }
   const int base = k0 + kb;
@@ -452,60 +432,6 @@ __host__ __device__ __forceinline__ int emu_row_tasks(int I, int TJ, int jmode) 
   int jlo, jhi;
   emu_row_range(I, TJ, jmode, jlo, jhi);
   return jhi > jlo ? (jhi - jlo + kEmuRun - 1) / kEmuRun : 0;
-}
-
-// Conversions without the conversion instructions, which share this GPU's
-// narrow FP64 pipe: FP32 additions of M = 1.5 * 2^23 put a rounded integer
-// |k| < 2^22 into the low significand bits of M + k, read back with an integer
-// subtraction.
-constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23
-constexpr int kMagicBits = 0x4B400000;     // bit pattern of kMagic
-
-// x an integer-valued FP32 number, |x| < 2^30: x exactly as int32
-// (x = 256 hi + lo with hi = rn(x / 256) and |lo| <= 128, both exact).
-__device__ __forceinline__ int exact_f2i(float x) {
-  const float r = fmaf(x, 0.00390625f, kMagic);
-  const float hi = r - kMagic;
-  const float lo = fmaf(-256.0f, hi, x);
-  return (__float_as_int(r) - kMagicBits) * 256 + (__float_as_int(lo + kMagic) - kMagicBits);
-}
-
-// round-to-nearest-even of an FP32 x, |x| < 2^37, as int64
-// (x = 65536 hi + lo with hi = rn(x / 65536), lo exact, |lo| <= 2^15).
-__device__ __forceinline__ long long round_f2ll(float x) {
-  const float r = fmaf(x, 0x1p-16f, kMagic);
-  const float hi = r - kMagic;
-  const float lo = fmaf(-65536.0f, hi, x);
-  return (long long)(__float_as_int(r) - kMagicBits) * 65536 + (__float_as_int(lo + kMagic) - kMagicBits);
-}
-
-// Exponent e of a positive power of two 2^e (normal or subnormal).
-__device__ __forceinline__ int pow2_exponent(double s) {
-  const long long b = __double_as_longlong(s);
-  const int E = (int)((b >> 52) & 0x7FF);
-  return E ? E - 1023 : (63 - __clzll(b)) - 1074;
-}
-
-// -RN(W 2^eoff) as an FP64 bit pattern, built with integer operations for
-// every W (|W| < 2^63) and eoff: a normal result keeps the top 53 bits of |W|
-// (round to nearest even, the carry may bump the exponent), a subnormal one the
-// bits down to 2^-1074, and a result beyond the largest finite value is an
-// infinity.  One rounding of the exact value, as fma(-W, 2^eoff, 0) would do.
-__device__ __forceinline__ double neg_scaled(long long W, int eoff) {
-  const unsigned long long sgn = W < 0 ? 0ull : (1ull << 63);  // sign of -W
-  const unsigned long long a = W < 0 ? (unsigned long long)(-W) : (unsigned long long)W;
-  const int lz = __clzll(a | 1ull);  // a = 0 handled below
-  const unsigned long long x = a << lz;  // leading one at bit 63
-  const int be = (63 - lz) + eoff + 1023;  // biased exponent of a normal result
-  const int drop = be >= 1 ? 11 : min(64, 12 - be);  // low bits of x rounded off
-  unsigned long long mant = drop < 64 ? x >> drop : 0ull;
-  const unsigned long long rem = drop < 64 ? x & ((1ull << drop) - 1ull) : x;
-  const unsigned long long half = 1ull << (drop - 1);
-  if (rem > half || (rem == half && (mant & 1ull))) mant++;
-  unsigned long long bits = be >= 1 ? ((unsigned long long)(be - 1) << 52) + mant : mant;
-  if (12 - be > 64) bits = 0ull;  // below half the smallest subnormal
-  if (be >= 2047) bits = 0x7FF0000000000000ull;
-  return __longlong_as_double((long long)(a == 0 ? 0ull : (sgn | bits)));
 }
 
 __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
