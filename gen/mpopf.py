@@ -91,6 +91,8 @@ CONFIGS = {
     "grid30_n24": GridSpec(30, 40, 6, 3, 24, 1e-6, 1e6, 1907, "grid30_n24"),
     "grid2383_n96": GridSpec(2383, 2900, 327, 100, 96, 1e-8, 1e8, 2383, "grid2383_n96"),
     "grid9241_n168": GridSpec(9241, 16049, 1445, 400, 168, 1e-8, 1e8, 9241, "grid9241_n168"),
+    # the same grid over 8 periods: a few GB on the device, for kernel profiles
+    "grid9241_n8": GridSpec(9241, 16049, 1445, 400, 8, 1e-8, 1e8, 9241, "grid9241_n8"),
 }
 
 
