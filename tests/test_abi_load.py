@@ -54,6 +54,17 @@ def test_status_strings_without_gpu():
     assert lib.kkt_status_string(6) == b"refinement did not converge"
     opt = binding.kkt_default_options()
     assert opt.refine_tol == 1e-10 and opt.max_refine == 10 and opt.prec == 0
+    assert opt.tail_ratio == 0.0 and opt.dense_tail == -1 and opt.use_graphs == 1
+
+
+def test_inertia_defaults_without_gpu():
+    """The documented trial constants of the inertia correction."""
+    from paper_1907_05420_gb300 import binding
+
+    o = binding.kkt_default_inertia_options()
+    assert (o.delta_w_init, o.delta_w_min, o.delta_w_max) == (1e-4, 1e-20, 1e40)
+    assert (o.grow_first, o.grow, o.delta_c, o.max_trials) == (100.0, 8.0, 1e-8, 40)
+    assert o.shrink == 1.0 / 3.0
 
 
 def test_struct_layouts_match_header(tmp_path):
