@@ -176,12 +176,25 @@ def _topology(rng, nb, nl):
     return np.array(edges, dtype=np.int64)
 
 
-def make_problem(spec: GridSpec, *, zero_b: bool = False) -> KKTProblem:
+def make_problem(spec: GridSpec, *, zero_b: bool = False, coupling: str = "adjacent") -> KKTProblem:
     """Build the seeded instance described by ``spec``.
 
     zero_b=True keeps B's pattern but sets its values to zero (a special case
     in which the arrowhead system decouples).
+
+    coupling="adjacent" (default): the coupling variables are the states of
+    charge, C is a positive diagonal and B_i couples adjacent periods through
+    the storage dynamics rows of A_i (S is SPD and block-tridiagonal).
+    coupling="paper": the coupling of Sec. 4.1 (eq. B12N): the coupling
+    variables are the multipliers of the cumulative energy constraints, one
+    per storage unit and period, C = 0, A_i has no dynamics rows, and B_i
+    puts period i's charge and discharge into the energy constraints of every
+    period m >= i (coefficients eta_c and -1/eta_d), so S is dense and
+    negative definite and K's inertia is (N nP, N nD + nC, 0).
     """
+    if coupling not in ("adjacent", "paper"):
+        raise ValueError("coupling must be 'adjacent' or 'paper'")
+    paper = coupling == "paper"
     rng = np.random.Generator(np.random.PCG64(spec.seed))
     nb, ng, ns, N = spec.n_bus, spec.n_gen, spec.n_stor, spec.n_per
     edges = _topology(rng, nb, spec.n_line)
@@ -194,7 +207,7 @@ def make_problem(spec: GridSpec, *, zero_b: bool = False) -> KKTProblem:
     sto_bus = rng.choice(nb, size=ns, replace=False)
 
     nP = spec.n_primal
-    nA = spec.n_a
+    nA = spec.n_a - (ns if paper else 0)
     th = lambda k: k                      # noqa: E731
     vv = lambda k: nb + k                 # noqa: E731
     PG = 2 * nb
@@ -231,8 +244,9 @@ def make_problem(spec: GridSpec, *, zero_b: bool = False) -> KKTProblem:
     si = np.arange(ns)
     add(Prow(sto_bus), PD + si, np.ones(ns))
     add(Prow(sto_bus), PC + si, -np.ones(ns))
-    add(DYN + si, PC + si, -ETA_C * np.ones(ns))
-    add(DYN + si, PD + si, (1.0 / ETA_D) * np.ones(ns))
+    if not paper:
+        add(DYN + si, PC + si, -ETA_C * np.ones(ns))
+        add(DYN + si, PD + si, (1.0 / ETA_D) * np.ones(ns))
     # diagonal present everywhere: zero placeholder on primal (barrier added
     # per period), dual regularisation on the multipliers
     add(np.arange(nP), np.arange(nP), np.zeros(nP))
@@ -265,24 +279,39 @@ def make_problem(spec: GridSpec, *, zero_b: bool = False) -> KKTProblem:
     a_vals = np.broadcast_to(a_const, (N, nnz)).copy()
     a_vals[:, bar_pos] += barrier
 
-    # B_i: dynamics row s couples eps_{i,s} (+1) and eps_{i-1,s} (-1)
     bp, br, bc, bv = [0], [], [], []
-    for i in range(N):
-        for s in range(ns):
-            if i > 0:
+    if paper:
+        # B_i: p_dis then p_chg of unit s (rows sorted) into the energy
+        # constraints of unit s in periods m >= i
+        for i in range(N):
+            for row, coef in sorted([(PD + s, -1.0 / ETA_D) for s in range(ns)] +
+                                    [(PC + s, ETA_C) for s in range(ns)]):
+                s = row - PD if row < PC else row - PC
+                for m in range(i, N):
+                    br.append(row)
+                    bc.append(m * ns + s)
+                    bv.append(coef)
+            bp.append(len(br))
+    else:
+        # B_i: dynamics row s couples eps_{i,s} (+1) and eps_{i-1,s} (-1)
+        for i in range(N):
+            for s in range(ns):
+                if i > 0:
+                    br.append(DYN + s)
+                    bc.append((i - 1) * ns + s)
+                    bv.append(-1.0)
                 br.append(DYN + s)
-                bc.append((i - 1) * ns + s)
-                bv.append(-1.0)
-            br.append(DYN + s)
-            bc.append(i * ns + s)
-            bv.append(1.0)
-        bp.append(len(br))
+                bc.append(i * ns + s)
+                bv.append(1.0)
+            bp.append(len(br))
     b_vals = np.array(bv, dtype=np.float64)
     if zero_b:
         b_vals[:] = 0.0
 
     nC = N * ns
     c_vals = _loguniform(rng, spec.bar_lo, spec.bar_hi, nC)
+    if paper:
+        c_vals[:] = 0.0  # drawn all the same, so the right-hand side's draws do not move
     rhs = rng.standard_normal(N * nA + nC)
 
     return KKTProblem(

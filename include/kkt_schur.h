@@ -195,15 +195,17 @@ kkt_status kkt_factor(kkt_handle* h, const double* a_vals, const double* b_vals,
 /* ---- inertia correction (Sec. 2, inertia correction and curvature detection) ----
  * The IPM needs K with inertia (N*nP + nC, N*(nA - nP), 0): positive pivots for
  * the primal rows of every block and for the coupling variables, negative ones
- * for the multipliers.  When the factor shows another inertia, the diagonal is
+ * for the multipliers (coupling_dual below: the coupling variables count as
+ * multipliers).  When the factor shows another inertia, the diagonal is
  * shifted, K + diag(dw I on the primal rows of every A_i and on C, -dc I on the
  * dual rows), and refactored with growing dw until the inertia is right.  The
  * trial values follow the usual interior-point rule (the paper names the rule,
  * not its constants; these are the defaults below):
  *   first trial after the unshifted factor: dw = delta_w_init, or, once a call
  *     on this handle has succeeded with dw > 0, max(delta_w_min, shrink * last dw);
- *   dc = delta_c when a pivot of a block factor was zero or replaced under
- *     pivot_eps (a singular or nearly singular Jacobian), else 0;
+ *   dc = delta_c when a pivot of a block factor or of S was zero, or a block
+ *     pivot was replaced under pivot_eps (a singular or nearly singular
+ *     Jacobian), else 0;
  *   next trials: dw *= grow_first while no call on the handle has needed a
  *     shift, dw *= grow afterwards; give up when dw > delta_w_max or after
  *     max_trials factorizations (KKT_ERR_INERTIA; the handle then holds the
@@ -221,7 +223,10 @@ typedef struct {
   double shrink;       /* 1/3 */
   double delta_c;      /* 1e-8 */
   int32_t max_trials;  /* 40 */
-  int32_t reserved;
+  int32_t coupling_dual; /* 0 (default): the coupling variables are primal (expected inertia
+                            (N*nP + nC, N*nD, 0), C shifted by +dw); 1: they are multipliers, as
+                            in the paper's own MPOPF coupling (expected (N*nP, N*nD + nC, 0), C
+                            shifted by -dc) */
 } kkt_inertia_options;
 
 typedef struct {

@@ -65,7 +65,7 @@ class kkt_info(C.Structure):
 class kkt_inertia_options(C.Structure):
     _fields_ = [("delta_w_init", C.c_double), ("delta_w_min", C.c_double), ("delta_w_max", C.c_double),
                 ("grow_first", C.c_double), ("grow", C.c_double), ("shrink", C.c_double),
-                ("delta_c", C.c_double), ("max_trials", C.c_int32), ("reserved", C.c_int32)]
+                ("delta_c", C.c_double), ("max_trials", C.c_int32), ("coupling_dual", C.c_int32)]
 
 
 class kkt_inertia_result(C.Structure):

@@ -578,10 +578,10 @@ double time_factor(kkt_handle* hh, const kkt_pattern* pat) {
   return ms;
 }
 
-// The factor of the input values with the inertia-correction shift (dw, dc)
-// applied to the device copy (none when both are 0).
+// The factor of the input values with the inertia-correction shift (dw, dc;
+// dcs on C's diagonal) applied to the device copy (none when dw and dc are 0).
 kkt_status factor_values(Handle* h, const double* a_vals, const double* b_vals, const double* c_vals,
-                         int32_t on_device, cudaStream_t st, double dw, double dc) {
+                         int32_t on_device, cudaStream_t st, double dw, double dc, double dcs) {
   h->stream = st;
   (void)cudaGetLastError();  // drop a stale non-sticky error left by an unrelated call
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -590,7 +590,7 @@ kkt_status factor_values(Handle* h, const double* a_vals, const double* b_vals, 
   KKT_CUDA(cudaMemcpyAsync(h->a_vals, a_vals, sizeof(double) * h->nnzA * h->N, kind, st));
   if (h->nnzB > 0) KKT_CUDA(cudaMemcpyAsync(h->b_vals, b_vals, sizeof(double) * h->nnzB, kind, st));
   if (nc_vals > 0) KKT_CUDA(cudaMemcpyAsync(h->c_vals, c_vals, sizeof(double) * nc_vals, kind, st));
-  if (dw != 0.0 || dc != 0.0) KKT_CUDA(launch_shift_diag(*h, dw, dc, st));
+  if (dw != 0.0 || dc != 0.0) KKT_CUDA(launch_shift_diag(*h, dw, dc, dcs, st));
   h->g_reduced = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && h->opt.reduced_contraction &&
                  contract_g_tc_supported(*h);
   h->s_factor = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) ? 1 : 0;
@@ -689,7 +689,7 @@ kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals
     set_error("kkt_factor: null argument");
     return KKT_ERR_INVALID;
   }
-  return factor_values(h, a_vals, b_vals, c_vals, on_device, (cudaStream_t)stream, 0.0, 0.0);
+  return factor_values(h, a_vals, b_vals, c_vals, on_device, (cudaStream_t)stream, 0.0, 0.0, 0.0);
 }
 
 void kkt_default_inertia_options(kkt_inertia_options* opt) {
@@ -718,13 +718,15 @@ kkt_status kkt_factor_inertia(kkt_handle* hh, const double* a_vals, const double
   if (opt) o = *opt;
   if (!(o.delta_w_init > 0.0) || !(o.delta_w_min > 0.0) || !(o.delta_w_max >= o.delta_w_init) ||
       !(o.grow_first > 1.0) || !(o.grow > 1.0) || !(o.shrink > 0.0 && o.shrink < 1.0) || !(o.delta_c >= 0.0) ||
-      o.max_trials < 1) {
+      o.max_trials < 1 || (o.coupling_dual != 0 && o.coupling_dual != 1)) {
     set_error("kkt_factor_inertia: invalid options");
     return KKT_ERR_INVALID;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  // expected pivot signs: blocks (N*nP, N*nD, 0), S (nC, 0, 0)
+  // expected pivot signs: blocks (N*nP, N*nD, 0); S (nC, 0, 0), or (0, nC, 0)
+  // when the coupling variables are multipliers
   const uint64_t pos_blk = (uint64_t)h->N * h->nP, neg_blk = (uint64_t)h->N * (h->nA - h->nP);
+  const uint64_t pos_s = o.coupling_dual ? 0 : (uint64_t)h->nC, neg_s = o.coupling_dual ? (uint64_t)h->nC : 0;
   unsigned long long c[2 * kNumCounters];
   int dev_err = 0;
   auto read_counts = [&]() -> kkt_status {
@@ -741,15 +743,14 @@ kkt_status kkt_factor_inertia(kkt_handle* hh, const double* a_vals, const double
   int32_t trials = 0;
   kkt_status status = KKT_ERR_INERTIA;
   for (;;) {
-    kkt_status fs = factor_values(h, a_vals, b_vals, c_vals, on_device, st, dw, dc);
+    kkt_status fs = factor_values(h, a_vals, b_vals, c_vals, on_device, st, dw, dc, o.coupling_dual ? -dc : dw);
     if (fs == KKT_OK) fs = read_counts();
     if (fs != KKT_OK) return fs;
     trials++;
     const bool blocks_ok =
         c[kPos] == pos_blk && c[kNeg] == neg_blk && c[kZero] == 0 && c[kPerturbed] == 0;
     auto s_right = [&]() {
-      return c[kNumCounters + kPos] == (uint64_t)h->nC && c[kNumCounters + kNeg] == 0 &&
-             c[kNumCounters + kZero] == 0;
+      return c[kNumCounters + kPos] == pos_s && c[kNumCounters + kNeg] == neg_s && c[kNumCounters + kZero] == 0;
     };
     bool s_ok = s_right();
     if (blocks_ok && !s_ok && h->s_factor == 1) {
@@ -765,7 +766,7 @@ kkt_status kkt_factor_inertia(kkt_handle* hh, const double* a_vals, const double
       break;
     }
     if (trials >= o.max_trials) break;
-    if (c[kZero] > 0 || c[kPerturbed] > 0) dc = o.delta_c;
+    if (c[kZero] > 0 || c[kPerturbed] > 0 || c[kNumCounters + kZero] > 0) dc = o.delta_c;  // singular
     double next;
     if (dw == 0.0) next = h->last_delta_w > 0.0 ? std::max(o.delta_w_min, o.shrink * h->last_delta_w) : o.delta_w_init;
     else next = dw * (h->last_delta_w > 0.0 ? o.grow : o.grow_first);

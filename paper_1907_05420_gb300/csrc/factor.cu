@@ -40,11 +40,12 @@ __global__ void k_scatter_a(const double* __restrict__ a_vals, int64_t nnzA,
 }
 
 // Inertia-correction shift of the copied values: +dw on the diagonal of the
-// primal rows of every block, -dc on the dual rows, +dw on C's diagonal (the
-// coupling variables are primal).  One thread per (block, row) or C entry.
+// primal rows of every block, -dc on the dual rows, dcs on C's diagonal (+dw
+// for primal coupling variables, -dc for multipliers).  One thread per
+// (block, row) or C entry.
 __global__ void k_shift_diag(double* __restrict__ a_vals, int64_t nnzA, const int32_t* __restrict__ diag_pos,
                              int nA, int nP, int N, double* __restrict__ c_vals, int nC, int c_kind, double dw,
-                             double dc) {
+                             double dc, double dcs) {
   const int64_t na = (int64_t)N * nA;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < na + nC;
        q += (int64_t)gridDim.x * blockDim.x) {
@@ -54,7 +55,7 @@ __global__ void k_shift_diag(double* __restrict__ a_vals, int64_t nnzA, const in
       a_vals[b * nnzA + diag_pos[r]] += r < nP ? dw : -dc;
     } else {
       const int64_t i = q - na;
-      c_vals[c_kind == 0 ? i : i * nC + i] += dw;
+      c_vals[c_kind == 0 ? i : i * nC + i] += dcs;
     }
   }
 }
@@ -183,12 +184,12 @@ __global__ void __launch_bounds__(256) k_panel_factor(const int32_t* __restrict_
 
 }  // namespace
 
-cudaError_t launch_shift_diag(Handle& h, double dw, double dc, cudaStream_t st) {
+cudaError_t launch_shift_diag(Handle& h, double dw, double dc, double dcs, cudaStream_t st) {
   const int64_t total = (int64_t)h.N * h.nA + h.nC;
   if (total == 0) return cudaSuccess;
   const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
   k_shift_diag<<<grid, 256, 0, st>>>(h.a_vals, h.nnzA, h.d.diag_pos, h.nA, h.nP, h.N, h.c_vals, h.nC, h.c_kind,
-                                     dw, dc);
+                                     dw, dc, dcs);
   h.launches++;
   return cudaGetLastError();
 }

@@ -195,8 +195,8 @@ cudaError_t dense_prepare();
 cudaError_t dense_tc_prepare();
 cudaError_t schur_tc_prepare();
 // ---- kernel launchers (factor.cu) ----
-// a_vals[i][diag(r)] += dw for primal rows r, -= dc for dual rows; C's diagonal += dw
-cudaError_t launch_shift_diag(Handle& h, double dw, double dc, cudaStream_t st);
+// a_vals[i][diag(r)] += dw for primal rows r, -= dc for dual rows; C's diagonal += dcs
+cudaError_t launch_shift_diag(Handle& h, double dw, double dc, double dcs, cudaStream_t st);
 cudaError_t launch_scatter_a(Handle& h, cudaStream_t st);
 cudaError_t launch_factor_levels(Handle& h, cudaStream_t st);
 // ---- (tail.cu) ----

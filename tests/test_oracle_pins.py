@@ -230,3 +230,53 @@ def test_generator_is_deterministic_and_shaped():
     spec = GridSpec(30, 40, 6, 3, 24, 1e-6, 1e6, 1908)
     c = make_problem(spec)
     assert not np.array_equal(a.rhs, c.rhs)
+
+
+# ---- the paper's own MPOPF coupling (Sec. 4.1, eq. B12N; Sec. 4.3) ----
+# Coupling variables are the multipliers of the cumulative energy constraints,
+# C = 0, and B_i feeds period i's storage injections into the constraints of
+# every later period.  The oracle is the same program; these pins check it on
+# that structure against LAPACK and against the block structure Sec. 4.3
+# derives for S.
+
+@pytest.mark.parametrize("name", ["tiny", "small"])
+def test_paper_coupling_matches_dense_lu_and_eigenvalues(name):
+    p = make_problem(CONFIGS[name], coupling="paper")
+    out = oracle.kkt_solve(p)
+    K = dense_K(p)
+    x_lu = np.linalg.solve(K, p.rhs)
+    kappa = np.linalg.cond(K)
+    err = np.max(np.abs(out["x"] - x_lu)) / np.max(np.abs(x_lu))
+    assert err <= max(1e-12, 1e3 * kappa * EPS), (err, kappa)
+    assert oracle.backward_error(p, out["x"]) <= 1e-14
+    # the coupling variables are multipliers now: nC more negative eigenvalues
+    expect = [p.N * p.nP, p.N * (p.nA - p.nP) + p.nC, 0]
+    ev = np.linalg.eigvalsh(K)
+    assert [int((ev > 0).sum()), int((ev < 0).sum()), 0] == expect
+    assert list(out["inertia"]) == expect
+
+
+@pytest.mark.parametrize("name", ["small", "grid30_n24"])
+def test_paper_coupling_schur_structure(name):
+    """S is dense and negative definite, and in every block column the blocks
+    on and below the diagonal are one and the same n_stor x n_stor block (the
+    identical subdiagonal blocks of Sec. 4.3; with the energy constraint of a
+    period taking that period's injections, the diagonal block equals them
+    too), so S is determined by N such blocks."""
+    p = make_problem(CONFIGS[name], coupling="paper")
+    out = oracle.kkt_solve(p, want_S=True)
+    S = out["S"]
+    ns = p.spec.n_stor
+    assert np.all(np.linalg.eigvalsh(0.5 * (S + S.T)) < 0)
+    scale = np.abs(S).max()
+    for j in range(p.N):
+        col = S[:, j * ns:(j + 1) * ns]
+        ref = col[j * ns:(j + 1) * ns]
+        for m in range(j + 1, p.N):
+            assert np.allclose(col[m * ns:(m + 1) * ns], ref, rtol=1e-12, atol=1e-14 * scale)
+    # against the definition evaluated with dense LAPACK solves
+    S_ref = c_dense(p).copy()
+    for i in range(p.N):
+        B = b_dense(p, i)
+        S_ref -= B.T @ np.linalg.solve(block_dense(p, i), B)
+    assert np.allclose(S, S_ref, rtol=1e-8, atol=1e-10 * scale)

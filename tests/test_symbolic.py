@@ -87,6 +87,9 @@ PROBLEMS = {
     "small": lambda: make_problem(CONFIGS["small"]),
     "grid30_n24": lambda: make_problem(CONFIGS["grid30_n24"]),
     "storage20": lambda: make_problem(_storage_spec()),
+    # the paper's cumulative coupling: every period's storage rows reach the
+    # energy constraints of all later periods, so S is dense
+    "paper20": lambda: make_problem(_storage_spec(), coupling="paper"),
 }
 
 
