@@ -34,6 +34,14 @@ struct Graph {
 // Weighted minimum degree on an explicit elimination graph.  The degree of a
 // node is the total weight (number of variables) of its current neighbours.
 // Lazy heap: stale entries are skipped when popped.
+//
+// Once the node taken is adjacent to every remaining node, its elimination
+// leaves a clique.  In a clique of total weight W a node's degree is W - w(v),
+// and each later elimination lowers all of them by the same amount, so the
+// heap would take the rest by decreasing weight, ties by node number; that
+// order is appended directly instead of eliminating the clique node by node
+// (whose merges cost the cube of its size: most of the time on grids with a
+// large dense top separator).
 std::vector<int32_t> weighted_min_degree(Graph& g) {
   const int32_t n = g.n;
   std::vector<int64_t> deg(n, 0);
@@ -46,6 +54,7 @@ std::vector<int32_t> weighted_min_degree(Graph& g) {
   std::vector<int32_t> mark(n, -1), order;
   order.reserve(n);
   std::vector<int32_t> merged;
+  int32_t remaining = n;
   while (!heap.empty()) {
     Key top = heap.top();
     heap.pop();
@@ -53,13 +62,24 @@ std::vector<int32_t> weighted_min_degree(Graph& g) {
     if (gone[p] || top.first.first != deg[p]) continue;
     gone[p] = 1;
     order.push_back(p);
+    remaining--;
+    if ((int32_t)g.adj[p].size() == remaining) {
+      // p is adjacent to all remaining nodes: they form a clique after it
+      std::vector<int32_t> rest(g.adj[p]);
+      std::sort(rest.begin(), rest.end(), [&](int32_t a, int32_t b) {
+        return g.weight[a] != g.weight[b] ? g.weight[a] > g.weight[b] : a < b;
+      });
+      order.insert(order.end(), rest.begin(), rest.end());
+      break;
+    }
     std::vector<int32_t> np;
     np.swap(g.adj[p]);
     for (int32_t u : np) {
-      // adj[u] <- (adj[u] U np) \ {u, p}
+      // adj[u] <- (adj[u] U np) \ {u, p}, and its weight
       std::vector<int32_t>& au = g.adj[u];
       merged.clear();
       merged.reserve(au.size() + np.size());
+      int64_t d = 0;
       size_t a = 0, b = 0;
       while (a < au.size() || b < np.size()) {
         int32_t x;
@@ -68,10 +88,9 @@ std::vector<int32_t> weighted_min_degree(Graph& g) {
         else { x = au[a++]; b++; }
         if (x == u || x == p) continue;
         merged.push_back(x);
+        d += g.weight[x];
       }
-      au.assign(merged.begin(), merged.end());
-      int64_t d = 0;
-      for (int32_t w : au) d += g.weight[w];
+      au.swap(merged);
       deg[u] = d;
       heap.push({{d, g.weight[u]}, u});
     }
