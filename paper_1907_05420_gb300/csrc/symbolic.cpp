@@ -35,15 +35,24 @@ struct Graph {
 // node is the total weight (number of variables) of its current neighbours.
 // Lazy heap: stale entries are skipped when popped.
 //
+// A node's neighbours are a sorted list while few and a bitset once the list
+// would take more bits than the bitset (dense rows near the top of the tree):
+// merging the eliminated node's neighbours into a bitset is a pass over the
+// words they span, and its degree is updated by the weights of the
+// neighbours it gains.  Both forms give the same sets and degrees, so the
+// order is that of plain sorted-list merges.
+//
 // Once the node taken is adjacent to every remaining node, its elimination
 // leaves a clique.  In a clique of total weight W a node's degree is W - w(v),
 // and each later elimination lowers all of them by the same amount, so the
 // heap would take the rest by decreasing weight, ties by node number; that
 // order is appended directly instead of eliminating the clique node by node
-// (whose merges cost the cube of its size: most of the time on grids with a
-// large dense top separator).
+// (whose merges cost the cube of its size).
 std::vector<int32_t> weighted_min_degree(Graph& g) {
   const int32_t n = g.n;
+  const int32_t words = (n + 63) / 64;
+  const size_t dense_at = std::max<size_t>(64, (size_t)n / 32);
+  std::vector<std::vector<uint64_t>> bits(n);  // empty: the sorted list g.adj[v] holds v's neighbours
   std::vector<int64_t> deg(n, 0);
   for (int32_t v = 0; v < n; v++)
     for (int32_t u : g.adj[v]) deg[v] += g.weight[u];
@@ -51,9 +60,10 @@ std::vector<int32_t> weighted_min_degree(Graph& g) {
   std::priority_queue<Key, std::vector<Key>, std::greater<Key>> heap;
   for (int32_t v = 0; v < n; v++) heap.push({{deg[v], g.weight[v]}, v});
   std::vector<char> gone(n, 0);
-  std::vector<int32_t> mark(n, -1), order;
+  std::vector<int32_t> order;
   order.reserve(n);
-  std::vector<int32_t> merged;
+  std::vector<int32_t> merged, np;
+  std::vector<uint64_t> npbits(words, 0);
   int32_t remaining = n;
   while (!heap.empty()) {
     Key top = heap.top();
@@ -63,37 +73,66 @@ std::vector<int32_t> weighted_min_degree(Graph& g) {
     gone[p] = 1;
     order.push_back(p);
     remaining--;
-    if ((int32_t)g.adj[p].size() == remaining) {
+    // p's neighbours, ascending
+    np.clear();
+    if (bits[p].empty()) {
+      np.swap(g.adj[p]);
+    } else {
+      for (int32_t w = 0; w < words; w++)
+        for (uint64_t m = bits[p][w]; m; m &= m - 1) np.push_back(w * 64 + __builtin_ctzll(m));
+      std::vector<uint64_t>().swap(bits[p]);
+    }
+    if ((int32_t)np.size() == remaining) {
       // p is adjacent to all remaining nodes: they form a clique after it
-      std::vector<int32_t> rest(g.adj[p]);
-      std::sort(rest.begin(), rest.end(), [&](int32_t a, int32_t b) {
+      std::sort(np.begin(), np.end(), [&](int32_t a, int32_t b) {
         return g.weight[a] != g.weight[b] ? g.weight[a] > g.weight[b] : a < b;
       });
-      order.insert(order.end(), rest.begin(), rest.end());
+      order.insert(order.end(), np.begin(), np.end());
       break;
     }
-    std::vector<int32_t> np;
-    np.swap(g.adj[p]);
+    if (np.empty()) continue;
+    for (int32_t x : np) npbits[x >> 6] |= 1ull << (x & 63);
+    const int32_t w0 = np.front() >> 6, w1 = np.back() >> 6;
     for (int32_t u : np) {
-      // adj[u] <- (adj[u] U np) \ {u, p}, and its weight
-      std::vector<int32_t>& au = g.adj[u];
-      merged.clear();
-      merged.reserve(au.size() + np.size());
-      int64_t d = 0;
-      size_t a = 0, b = 0;
-      while (a < au.size() || b < np.size()) {
-        int32_t x;
-        if (b >= np.size() || (a < au.size() && au[a] < np[b])) x = au[a++];
-        else if (a >= au.size() || np[b] < au[a]) x = np[b++];
-        else { x = au[a++]; b++; }
-        if (x == u || x == p) continue;
-        merged.push_back(x);
-        d += g.weight[x];
+      // neighbours of u <- (neighbours of u U np) \ {u, p}, and their weight
+      int64_t d;
+      if (bits[u].empty()) {
+        std::vector<int32_t>& au = g.adj[u];
+        merged.clear();
+        merged.reserve(au.size() + np.size());
+        d = 0;
+        size_t a = 0, b = 0;
+        while (a < au.size() || b < np.size()) {
+          int32_t x;
+          if (b >= np.size() || (a < au.size() && au[a] < np[b])) x = au[a++];
+          else if (a >= au.size() || np[b] < au[a]) x = np[b++];
+          else { x = au[a++]; b++; }
+          if (x == u || x == p) continue;
+          merged.push_back(x);
+          d += g.weight[x];
+        }
+        au.swap(merged);
+        if (au.size() > dense_at) {  // switch u to a bitset
+          bits[u].assign(words, 0);
+          for (int32_t x : au) bits[u][x >> 6] |= 1ull << (x & 63);
+          std::vector<int32_t>().swap(au);
+        }
+      } else {
+        uint64_t* bu = bits[u].data();
+        d = deg[u] - g.weight[p];  // p was a neighbour of u
+        bu[p >> 6] &= ~(1ull << (p & 63));
+        for (int32_t w = w0; w <= w1; w++) {
+          uint64_t add = npbits[w] & ~bu[w];
+          if (w == (u >> 6)) add &= ~(1ull << (u & 63));
+          if (!add) continue;
+          bu[w] |= add;
+          for (uint64_t m = add; m; m &= m - 1) d += g.weight[w * 64 + __builtin_ctzll(m)];
+        }
       }
-      au.swap(merged);
       deg[u] = d;
       heap.push({{d, g.weight[u]}, u});
     }
+    for (int32_t x : np) npbits[x >> 6] = 0;
   }
   return order;
 }
