@@ -34,6 +34,14 @@ kkt_symbolic* kkt_symbolic_create(int32_t nA, int32_t nP, const int32_t* a_rowpt
  * chosen as kkt_analyze chooses it with the dense_tail option on. */
 int64_t kkt_symbolic_get(const kkt_symbolic* sym, const char* name, int64_t* out);
 
+/* Re-chooses the dense tail with cost ratio `ratio` and the byte cap
+ * `max_bytes` for the N triangles (kkt_analyze uses 24 GiB for the FP64
+ * CUDA-core tail and 96 GiB for the tensor-core tail; the default ratio is
+ * 1.5), as kkt_analyze's option tail_ratio does; later kkt_symbolic_get calls
+ * see the new tail.  Returns its number of columns, or -1 for a NULL handle or
+ * a ratio <= 0. */
+int32_t kkt_symbolic_choose_tail(kkt_symbolic* sym, double ratio, int64_t max_bytes);
+
 void kkt_symbolic_destroy(kkt_symbolic* sym);
 
 const char* kkt_symbolic_error(void);

@@ -10,6 +10,7 @@ namespace {
 thread_local std::string g_err;
 
 struct Inspect {
+  int32_t N = 0;
   kkt::Symbolic S;
   kkt::Coupling C;
   std::vector<int32_t> panel_rend, jlo, jhi;
@@ -30,6 +31,7 @@ kkt_symbolic* kkt_symbolic_create(int32_t nA, int32_t nP, const int32_t* a_rowpt
                                   const int32_t* b_blockptr, const int32_t* b_row, const int32_t* b_col,
                                   int32_t c_kind) {
   Inspect* in = new Inspect();
+  in->N = N;
   std::string e = kkt::analyze_pattern(nA, nP, a_rowptr, a_col, a_vals_hint, a_vals_hint ? 1 : 0, in->S);
   if (e.empty()) e = kkt::analyze_coupling(in->S, N, nC, b_blockptr, b_row, b_col, in->C);
   if (!e.empty()) {
@@ -88,6 +90,13 @@ int64_t kkt_symbolic_get(const kkt_symbolic* sym, const char* name, int64_t* out
     return copy_out(st, out);
   }
   return -1;
+}
+
+int32_t kkt_symbolic_choose_tail(kkt_symbolic* sym, double ratio, int64_t max_bytes) {
+  Inspect* in = reinterpret_cast<Inspect*>(sym);
+  if (!in || !(ratio > 0.0)) return -1;
+  kkt::choose_tail(in->S, in->N, max_bytes, kkt::kTailMinCols, ratio);
+  return in->S.n - in->S.tail_col;
 }
 
 void kkt_symbolic_destroy(kkt_symbolic* sym) { delete reinterpret_cast<Inspect*>(sym); }

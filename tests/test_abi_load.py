@@ -41,7 +41,8 @@ def test_symbolic_library_exports_its_header():
 
     lib = ctypes.CDLL(lib_build.build_symbolic())
     names = declared_functions(os.path.join(ROOT, "include", "kkt_symbolic.h"))
-    assert names == ["kkt_symbolic_create", "kkt_symbolic_destroy", "kkt_symbolic_error", "kkt_symbolic_get"]
+    assert names == ["kkt_symbolic_choose_tail", "kkt_symbolic_create", "kkt_symbolic_destroy",
+                     "kkt_symbolic_error", "kkt_symbolic_get"]
     for n in names:
         assert hasattr(lib, n), n
 

@@ -31,6 +31,8 @@ def _lib():
     L.kkt_symbolic_destroy.restype = None
     L.kkt_symbolic_error.argtypes = []
     L.kkt_symbolic_error.restype = C.c_char_p
+    L.kkt_symbolic_choose_tail.argtypes = [C.c_void_p, C.c_double, C.c_int64]
+    L.kkt_symbolic_choose_tail.restype = C.c_int32
     return L
 
 
@@ -38,8 +40,10 @@ def _ptr(a, t):
     return a.ctypes.data_as(C.POINTER(t))
 
 
-def analyze(p, hint=True):
-    """All arrays of the analysis of problem p, as a dict of int64 arrays."""
+def analyze(p, hint=True, tails=None):
+    """All arrays of the analysis of problem p, as a dict of int64 arrays.
+    tails: optional list of (ratio, max_bytes); the tail is re-chosen with each
+    and the resulting tail sizes are returned under "tails"."""
     L = _lib()
     rp = np.ascontiguousarray(p.a_rowptr, dtype=np.int32)
     col = np.ascontiguousarray(p.a_col, dtype=np.int32)
@@ -54,6 +58,8 @@ def analyze(p, hint=True):
     assert h, L.kkt_symbolic_error().decode()
     out = {}
     try:
+        if tails:
+            out["tails"] = [int(L.kkt_symbolic_choose_tail(h, float(r), int(b))) for r, b in tails]
         for name in ("perm partner sn_first sn_rowptr sn_rows sn_valoff sn_parent sn_level a_map "
                      "upd_ptr upd_src upd_r0 upd_r1 upd_reloff upd_rel E e_t wpos sn_wrow s_key "
                      "panel_rend jlo jhi colcount upd_ntail tail_wrow wt_ptr wt_idx stats").split():
@@ -206,6 +212,43 @@ def test_dense_tail_is_the_longest_cheap_suffix(name):
     for q in range(ns):
         lst = src[up[q]:up[q + 1]]
         assert np.all(lst[:nt[q]] < t0) and np.all(lst[nt[q]:] >= t0)
+
+
+def _rule_tail(p, s, ratio, cap):
+    """The tail rule evaluated directly: the longest suffix with
+    nT^3/3 <= ratio * sparse flops, nT >= 16 and N nT^2 8 bytes <= cap."""
+    first, ns, n = s["sn_first"], s["nsuper"], p.nA
+    cc = s["colcount"].astype(float)
+    fl = cc * (cc + 3)
+    ok = [t for t in range(ns) if n - first[t] >= 16 and p.N * (n - first[t]) ** 2 * 8 <= cap
+          and (n - first[t]) ** 3 / 3.0 <= ratio * fl[first[t]:].sum()]
+    return n - first[min(ok)] if ok else 0
+
+
+@pytest.mark.parametrize("name", ["aug14", "grid30_n24", "storage20"])
+def test_tail_ratio_and_cap(name):
+    """kkt_symbolic_choose_tail (the tail_ratio option and the per-mode byte
+    caps) follows the rule for every ratio and cap, and a larger ratio or cap
+    never shortens the tail."""
+    p, _ = _case(name)
+    caps = [24 << 30, 96 << 30, p.N * 20 * 20 * 8]
+    grid = [(r, c) for c in caps for r in (1.0, 1.25, 1.5, 2.0, 3.0)]
+    s = analyze(p, tails=grid)
+    for (r, c), nT in zip(grid, s["tails"]):
+        assert nT == _rule_tail(p, s, r, c), (r, c)
+    t = dict(zip(grid, s["tails"]))
+    for c in caps:
+        assert all(t[(a, c)] <= t[(b, c)] for a, b in zip((1.0, 1.25, 1.5, 2.0), (1.25, 1.5, 2.0, 3.0)))
+    assert all(t[(r, caps[2])] <= t[(r, caps[0])] <= t[(r, caps[1])] for r in (1.0, 1.5, 3.0))
+
+
+def test_tail_sizes_of_the_9241_bus_grid():
+    """On the 9,241-bus grid over 168 periods the 24 GiB cap of the FP64 tail
+    binds (4,369 columns), while the 96 GiB cap of the tensor-core tail lets the
+    rule take 7,009 (r = 1.25) or 7,447 (r = 1.5) columns."""
+    p = make_problem(CONFIGS["grid9241_n168"])
+    s = analyze(p, tails=[(1.5, 24 << 30), (1.25, 96 << 30), (1.5, 96 << 30)])
+    assert s["tails"] == [4369, 7009, 7447]
 
 
 def test_dense_tail_present_on_meshed_grids():
