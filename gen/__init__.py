@@ -13,3 +13,4 @@ from .mpopf import (  # noqa: F401
     mix_spec,
     reseed_barrier,
 )
+from .scopf import make_scopf  # noqa: F401

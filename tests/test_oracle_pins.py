@@ -280,3 +280,53 @@ def test_paper_coupling_schur_structure(name):
         B = b_dense(p, i)
         S_ref -= B.T @ np.linalg.solve(block_dense(p, i), B)
     assert np.allclose(S, S_ref, rtol=1e-8, atol=1e-10 * scale)
+
+
+# ---- the SCOPF workload (Sec. 3.1, eq. SCOPF, eq. orderingSCOPF) ----
+# Blocks are scenarios (nominal and line outages); coupling variables are the
+# PV-bus voltages and PV generator powers; C is a dense Hessian block.
+
+SCOPF_CASES = [(GridSpec(9, 12, 3, 0, 1, 1e-4, 1e4, 3, "scopf9"), 2),
+               (GridSpec(14, 20, 5, 0, 1, 1e-4, 1e4, 5, "scopf14"), 4),
+               (GridSpec(30, 41, 6, 0, 1, 1e-6, 1e6, 7, "scopf30"), 8)]
+
+
+@pytest.mark.parametrize("case", range(len(SCOPF_CASES)))
+def test_scopf_matches_dense_lu_and_inertia(case):
+    from gen import make_scopf
+
+    p = make_scopf(*SCOPF_CASES[case])
+    assert p.c_kind == 1
+    out = oracle.kkt_solve(p)
+    K = dense_K(p)
+    x_lu = np.linalg.solve(K, p.rhs)
+    kappa = np.linalg.cond(K)
+    err = np.max(np.abs(out["x"] - x_lu)) / np.max(np.abs(x_lu))
+    assert err <= max(1e-12, 1e3 * kappa * EPS), (err, kappa)
+    assert oracle.backward_error(p, out["x"]) <= 1e-14
+    expect = [p.N * p.nP + p.nC, p.N * (p.nA - p.nP), 0]
+    ev = np.linalg.eigvalsh(K)
+    assert [int((ev > 0).sum()), int((ev < 0).sum()), 0] == expect
+    assert list(out["inertia"]) == expect
+
+
+def test_scopf_schur_complement():
+    """S = C - sum B_c^T A_c^-1 B_c is SPD and equals its definition evaluated
+    with dense LAPACK solves; the contingency blocks differ from the nominal
+    one only in the outaged line's entries."""
+    from gen import make_scopf
+
+    p = make_scopf(*SCOPF_CASES[1])
+    S = oracle.kkt_solve(p, want_S=True)["S"]
+    S_ref = c_dense(p).copy()
+    for i in range(p.N):
+        B = b_dense(p, i)
+        S_ref -= B.T @ np.linalg.solve(block_dense(p, i), B)
+    assert np.allclose(S, S_ref, rtol=1e-8, atol=1e-10 * np.abs(S_ref).max())
+    assert np.all(np.linalg.eigvalsh(0.5 * (S + S.T)) > 0)
+    base = block_dense(p, 0) - np.diag(np.diag(block_dense(p, 0)))
+    for c in range(1, p.N):
+        d = (block_dense(p, c) - np.diag(np.diag(block_dense(p, c)))) - base
+        # one line out: only the theta, v and balance rows of its two buses change
+        rows = np.nonzero(np.any(d != 0, axis=1))[0]
+        assert 0 < len(rows) <= 8 and np.array_equal(d, d.T)

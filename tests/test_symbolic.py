@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gen import CONFIGS, GridSpec, make_problem
+from gen import CONFIGS, GridSpec, make_problem, make_scopf
 
 
 @functools.lru_cache(maxsize=None)
@@ -96,6 +96,8 @@ PROBLEMS = {
     # the paper's cumulative coupling: every period's storage rows reach the
     # energy constraints of all later periods, so S is dense
     "paper20": lambda: make_problem(_storage_spec(), coupling="paper"),
+    # security-constrained: scenario blocks, PV-bus coupling, dense C
+    "scopf14": lambda: make_scopf(GridSpec(14, 20, 5, 0, 1, 1e-4, 1e4, 5, "scopf14"), 4),
 }
 
 
