@@ -411,7 +411,6 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n,
 // Every wait is bounded: a timeout sets *err, makes the other roles stop, lets
 // the copies and products in flight finish (bounded again) and frees tensor
 // memory before the CTA exits.
-constexpr int kEmuRun = 8;          // tiles per task at most
 // Epilogue warps: 8 (two per tensor-memory lane quadrant, 32 columns per
 // thread).  With 10 warps a thread has 168 registers; 4 epilogue warps of 64
 // columns (255 registers) left one warp per scheduler and ran 1.7x slower.
@@ -420,19 +419,6 @@ constexpr int kEpiCols = TN * 4 / kEpiWarps;     // tile columns per epilogue th
 constexpr int kEmuThreads = 64 + 32 * kEpiWarps;  // producer, MMA issuer, epilogue
 // A image and two B buffers (229,376 bytes)
 __host__ __device__ constexpr int emu_smem_bytes() { return image_bytes(2, TM) + 2 * image_bytes(2, TN); }
-
-// tasks of tile row I for jmode (0: all tiles, 1: J = 0, 2: J >= 1)
-__host__ __device__ __forceinline__ void emu_row_range(int I, int TJ, int jmode, int& jlo, int& jhi) {
-  const int cnt = min(2 * I + 2, TJ);
-  jlo = jmode == 2 ? 1 : 0;
-  jhi = jmode == 1 ? 1 : cnt;
-}
-
-__host__ __device__ __forceinline__ int emu_row_tasks(int I, int TJ, int jmode) {
-  int jlo, jhi;
-  emu_row_range(I, TJ, jmode, jlo, jhi);
-  return jhi > jlo ? (jhi - jlo + kEmuRun - 1) / kEmuRun : 0;
-}
 
 __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
   const long long t0 = clock64();
@@ -486,16 +472,8 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
   const double* scaleA = scaleA0 + bb * ts.scale;
   const double* scaleB = scaleB0 + bb * ts.scale;
   // task -> tile row I and its run of tiles [j0, j1)
-  int I = 0, t = blockIdx.x;
-  for (;;) {
-    const int c = emu_row_tasks(I, TJ, jmode);
-    if (t < c || I + 1 >= TI) break;
-    t -= c;
-    I++;
-  }
-  int jlo, jhi;
-  emu_row_range(I, TJ, jmode, jlo, jhi);
-  const int j0 = jlo + t * kEmuRun, j1 = min(j0 + kEmuRun, jhi);
+  int I, j0, j1;
+  emu_task(blockIdx.x, TI, TJ, jmode, I, j0, j1);
   const int ntile = max(0, j1 - j0);
   const int base = k0 + kb;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;

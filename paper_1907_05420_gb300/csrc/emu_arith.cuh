@@ -160,4 +160,38 @@ KKT_HD double neg_scaled(long long W, int eoff) {
   return double_of((long long)(a == 0 ? 0ull : (sgn | bits)));
 }
 
+// ---- tiles of the trailing update (128-row by 64-column tiles) ----
+// Tile (I, J) holds part of the lower triangle when J <= 2I + 1.  A task is a
+// run of at most kEmuRun consecutive tiles of one tile row; jmode 0 takes all
+// tiles, 1 the first tile column (J = 0), 2 the others.
+constexpr int kEmuRun = 8;
+
+// tile columns [jlo, jhi) of tile row I for jmode
+KKT_HD void emu_row_range(int I, int TJ, int jmode, int& jlo, int& jhi) {
+  const int cnt = imin(2 * I + 2, TJ);
+  jlo = jmode == 2 ? 1 : 0;
+  jhi = jmode == 1 ? 1 : cnt;
+}
+
+KKT_HD int emu_row_tasks(int I, int TJ, int jmode) {
+  int jlo, jhi;
+  emu_row_range(I, TJ, jmode, jlo, jhi);
+  return jhi > jlo ? (jhi - jlo + kEmuRun - 1) / kEmuRun : 0;
+}
+
+// task t (of the sum of emu_row_tasks over the TI rows) -> row I, tiles [j0, j1)
+KKT_HD void emu_task(int t, int TI, int TJ, int jmode, int& I, int& j0, int& j1) {
+  I = 0;
+  for (;;) {
+    const int c = emu_row_tasks(I, TJ, jmode);
+    if (t < c || I + 1 >= TI) break;
+    t -= c;
+    I++;
+  }
+  int jlo, jhi;
+  emu_row_range(I, TJ, jmode, jlo, jhi);
+  j0 = jlo + t * kEmuRun;
+  j1 = imin(j0 + kEmuRun, jhi);
+}
+
 }  // namespace kkt

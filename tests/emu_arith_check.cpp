@@ -7,6 +7,8 @@
 //   emu_arith_check digits in out   (float64 v, int64 e)[n] -> (uint64 q, int64 sign)[n]
 //   emu_arith_check pow2   in out   float64[n]          -> int64[n]
 //   emu_arith_check bf16   -  out                       -> uint32[256]
+//   emu_arith_check tasks  in out   (int64 TI, TJ, jmode)[n] -> per triple: count, then
+//                                   count x (I, j0, j1), all int64
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -68,6 +70,24 @@ int main(int argc, char** argv) {
   if (!std::strcmp(mode, "pow2")) {
     std::vector<int64_t> out;
     for (double s : read_all<double>(argv[2])) out.push_back(kkt::pow2_exponent(s));
+    return write_all(argv[3], out) ? 0 : 1;
+  }
+  if (!std::strcmp(mode, "tasks")) {
+    const std::vector<int64_t> in = read_all<int64_t>(argv[2]);
+    std::vector<int64_t> out;
+    for (size_t i = 0; i + 2 < in.size(); i += 3) {
+      const int TI = (int)in[i], TJ = (int)in[i + 1], jmode = (int)in[i + 2];
+      int total = 0;
+      for (int I = 0; I < TI; I++) total += kkt::emu_row_tasks(I, TJ, jmode);
+      out.push_back(total);
+      for (int t = 0; t < total; t++) {
+        int I, j0, j1;
+        kkt::emu_task(t, TI, TJ, jmode, I, j0, j1);
+        out.push_back(I);
+        out.push_back(j0);
+        out.push_back(j1);
+      }
+    }
     return write_all(argv[3], out) ? 0 : 1;
   }
   if (!std::strcmp(mode, "bf16")) {

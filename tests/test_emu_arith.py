@@ -120,3 +120,37 @@ def test_bf16_table(prog):
     got = prog("bf16", None, np.uint32)
     want = np.arange(256, dtype=np.float32).view(np.uint32) >> 16
     assert np.array_equal(got, want)
+
+
+def test_tile_runs_cover_the_lower_triangle_once(prog):
+    """The tasks of the emulated update (runs of at most 8 tiles of one tile
+    row) cover every 128 x 64 tile holding part of the lower triangle exactly
+    once; the first tile column (jmode 1) and the rest (jmode 2) split the
+    full set (jmode 0) between them."""
+    ms = list(range(1, 3000, 37)) + [64, 127, 128, 129, 192, 255, 256, 1024, 7409]
+    trip = []
+    for m in ms:
+        TI, TJ = -(-m // 128), -(-m // 64)
+        for jmode in (0, 1, 2):
+            trip.append((TI, TJ, jmode))
+    out = prog("tasks", np.array(trip, dtype=np.int64), np.int64).tolist()
+    pos = 0
+    sets = {}
+    for TI, TJ, jmode in trip:
+        cnt = out[pos]
+        pos += 1
+        tiles = []
+        for _ in range(cnt):
+            I, j0, j1 = out[pos:pos + 3]
+            pos += 3
+            assert 0 <= I < TI and 0 <= j0 < j1 <= TJ and j1 - j0 <= 8
+            tiles += [(I, J) for J in range(j0, j1)]
+        assert len(tiles) == len(set(tiles))
+        sets[(TI, TJ, jmode)] = set(tiles)
+    assert pos == len(out)
+    for m in ms:
+        TI, TJ = -(-m // 128), -(-m // 64)
+        want = {(I, J) for I in range(TI) for J in range(TJ) if J <= 2 * I + 1}
+        assert sets[(TI, TJ, 0)] == want
+        assert sets[(TI, TJ, 1)] == {t for t in want if t[1] == 0}
+        assert sets[(TI, TJ, 2)] == {t for t in want if t[1] >= 1}
