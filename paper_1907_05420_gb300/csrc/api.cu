@@ -739,11 +739,14 @@ kkt_status kkt_factor_inertia(kkt_handle* hh, const double* a_vals, const double
     }
     return KKT_OK;
   };
-  double dw = 0.0, dc = 0.0;
+  double dw = 0.0, dc = 0.0;          // the next trial's shifts
+  double used_dw = 0.0, used_dc = 0.0;  // those of the factor the handle holds
   int32_t trials = 0;
   kkt_status status = KKT_ERR_INERTIA;
   for (;;) {
     kkt_status fs = factor_values(h, a_vals, b_vals, c_vals, on_device, st, dw, dc, o.coupling_dual ? -dc : dw);
+    used_dw = dw;
+    used_dc = dc;
     if (fs == KKT_OK) fs = read_counts();
     if (fs != KKT_OK) return fs;
     trials++;
@@ -773,10 +776,10 @@ kkt_status kkt_factor_inertia(kkt_handle* hh, const double* a_vals, const double
     if (next > o.delta_w_max) break;
     dw = next;
   }
-  if (status == KKT_OK && dw > 0.0) h->last_delta_w = dw;
+  if (status == KKT_OK && used_dw > 0.0) h->last_delta_w = used_dw;
   if (result) {
-    result->delta_w = dw;
-    result->delta_c = dc;
+    result->delta_w = used_dw;
+    result->delta_c = used_dc;
     result->trials = trials;
     result->reserved = 0;
   }
