@@ -26,3 +26,27 @@ def test_cpu_baseline_sampled_and_scaled_when_large(monkeypatch):
     assert "first 9 of 24 periods" in fields["sample"]
     assert f"x{est(24) / est(9):.1f}" in fields["sample"]
     assert fields["value"] > 0
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference runs the oracle on the host and prints one
+    JSON line with the keys the measurement contract asks for."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1", "--workload", "grid30_n24"],
+                       capture_output=True, text=True, check=True, timeout=600)
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"].startswith("grid30_n24")
