@@ -40,12 +40,9 @@ def workload_desc(name):
     """The config.workload string: the named instance and its sizes."""
     if name == WORKLOAD:
         return WORKLOAD_DESC
-    from gen import CONFIGS
+    from gen import describe_workload
 
-    g = CONFIGS[name]
-    return (f"{name}: synthetic {g.n_bus:,}-bus grid, {g.n_line:,} lines, {g.n_gen:,} generators, "
-            f"{g.n_stor:,} storage units, N={g.n_per} periods; blocks nA={g.n_a:,}; "
-            f"S {g.n_c:,} x {g.n_c:,}")
+    return describe_workload(name)
 
 
 def _peaks():
@@ -189,9 +186,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    from gen import CONFIGS, make_problem
+    from gen import CONFIGS, build_workload, make_problem
 
-    prob = make_problem(CONFIGS[args.workload])
+    prob = build_workload(args.workload)
     small = make_problem(CONFIGS["grid30_n24"])
     for _ in range(args.warmup):  # warm-up on the small instance (loads the library, threads)
         oracle.kkt_solve(small)
@@ -389,7 +386,7 @@ def main():
     import numpy as np
     import torch
 
-    from gen import CONFIGS, make_problem
+    from gen import build_workload
     from paper_1907_05420_gb300 import binding as B
 
     world, rank, local = _dist()
@@ -406,7 +403,7 @@ def main():
 
             dist.barrier()
 
-    prob = make_problem(CONFIGS[args.workload])
+    prob = build_workload(args.workload)
     stream = torch.cuda.current_stream()
     a = torch.from_numpy(np.ascontiguousarray(prob.a_vals)).to(dev)
     b = torch.from_numpy(np.ascontiguousarray(prob.b_vals)).to(dev)

@@ -14,3 +14,4 @@ from .mpopf import (  # noqa: F401
     reseed_barrier,
 )
 from .scopf import make_scopf  # noqa: F401
+from .workloads import build_workload, describe_workload, is_workload  # noqa: F401

@@ -28,7 +28,8 @@ def test_cpu_baseline_sampled_and_scaled_when_large(monkeypatch):
     assert fields["value"] > 0
 
 
-def test_reference_arm_prints_the_contract_line():
+@pytest.mark.parametrize("workload", ["grid30_n24", "grid30_n24_paper", "scopf30_c8"])
+def test_reference_arm_prints_the_contract_line(workload):
     """bench.py --impl reference runs the oracle on the host and prints one
     JSON line with the keys the measurement contract asks for."""
     import json
@@ -38,7 +39,7 @@ def test_reference_arm_prints_the_contract_line():
 
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2",
-                        "--warmup", "1", "--workload", "grid30_n24"],
+                        "--warmup", "1", "--workload", workload],
                        capture_output=True, text=True, check=True, timeout=600)
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
@@ -49,4 +50,4 @@ def test_reference_arm_prints_the_contract_line():
     assert d["impl"] == "reference" and d["steps"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert d["config"]["workload"].startswith("grid30_n24")
+    assert d["config"]["workload"].startswith(workload + ":")
