@@ -322,7 +322,9 @@ kkt_status kkt_server_submit(kkt_server* s, kkt_handle* h, const double* a_vals,
                              int64_t* request_id);
 /* Result of a request: with wait != 0 blocks until it completes; with wait == 0
  * returns KKT_ERR_STATE while it is pending.  *status is the request's status,
- * *latency_ms the time from submit to completion of its solve. */
+ * *latency_ms the time from submit to completion of its solve.  A result is
+ * collected once: an id that is neither queued, running nor finished and
+ * uncollected gives KKT_ERR_INVALID (instead of waiting forever). */
 kkt_status kkt_server_poll(kkt_server* s, int64_t request_id, int32_t wait, kkt_status* status,
                            double* latency_ms);
 /* Drains the queue, joins the workers and frees the streams. */

@@ -100,6 +100,7 @@ struct kkt_server {
   std::deque<Request> queue;
   std::unordered_map<int64_t, Done> done;
   std::unordered_set<kkt_handle*> busy;
+  std::unordered_set<int64_t> running;  // ids taken by a worker, not yet done
   int64_t inflight_bytes = 0;
   int64_t next_id = 1;
   bool stop = false;
@@ -131,6 +132,7 @@ void worker_loop(kkt_server* S, int slot) {
           S->queue.erase(it);
           bytes = reinterpret_cast<Handle*>(req.h)->device_bytes;
           S->busy.insert(req.h);
+          S->running.insert(req.id);
           S->inflight_bytes += bytes;
           break;
         }
@@ -146,6 +148,7 @@ void worker_loop(kkt_server* S, int slot) {
     {
       std::lock_guard<std::mutex> lk(S->mu);
       S->busy.erase(req.h);
+      S->running.erase(req.id);
       S->inflight_bytes -= bytes;
       S->done[req.id] = Done{r, ms};
     }
@@ -218,7 +221,14 @@ extern "C" kkt_status kkt_server_poll(kkt_server* S, int64_t request_id, int32_t
       S->done.erase(it);
       return KKT_OK;
     }
-    if (!wait) return KKT_ERR_STATE;  // not finished yet
+    // not finished: it must be queued or running
+    bool pending = S->running.count(request_id) > 0;
+    for (auto q = S->queue.begin(); !pending && q != S->queue.end(); ++q) pending = q->id == request_id;
+    if (!pending) {
+      set_error("kkt_server_poll: unknown or already collected request");
+      return KKT_ERR_INVALID;
+    }
+    if (!wait) return KKT_ERR_STATE;
     S->cv_done.wait(lk);
   }
 }
