@@ -46,7 +46,9 @@ typedef enum {
   KKT_ERR_INERTIA = 5,       /* inertia differs from (N*nP + nC, N*(nA-nP), 0) */
   KKT_ERR_NOT_CONVERGED = 6, /* refinement did not reach refine_tol */
   KKT_ERR_TIMEOUT = 7,       /* a bounded device wait ran out */
-  KKT_ERR_STATE = 8          /* call out of order (e.g. solve before factor) */
+  KKT_ERR_STATE = 8,         /* call out of order (e.g. solve before factor) */
+  KKT_ERR_NONFINITE = 9      /* a NaN or Inf in the values of K or the right-hand side, or a
+                                solution that is not finite after the FP64 fallback */
 } kkt_status;
 
 /* Arithmetic of the dense factor of S (and of the Schur contraction where
@@ -249,8 +251,12 @@ kkt_status kkt_factor_inertia(kkt_handle* h, const double* a_vals, const double*
  * with the current factorization, refined in FP64 to opt.refine_tol.
  * rhs and x: host (on_device 0) or device (1) arrays.  Returns
  * KKT_ERR_NOT_CONVERGED when refinement stops above refine_tol (x then holds
- * the best iterate).  Synchronizes `stream` (the refinement reads its
- * residual norm on the host). */
+ * the best iterate).  The convergence test sees every NaN and Inf: a
+ * non-finite ||K||_inf or ||rhs||_inf (a NaN or Inf among the values) returns
+ * KKT_ERR_NONFINITE at once; a non-finite iterate first takes the FP64-accurate
+ * refactor of S in the reduced modes and, if it stays non-finite, returns
+ * KKT_ERR_NONFINITE (rel_residual is then NaN).  Synchronizes `stream` (the
+ * refinement reads its residual norm on the host). */
 kkt_status kkt_solve(kkt_handle* h, const double* rhs, double* x, int32_t nrhs, int32_t on_device,
                      void* stream);
 
@@ -274,8 +280,12 @@ const char* kkt_last_error(void);
  * budget, or a latency-critical loop that cannot take the device-wide
  * synchronization an allocation may imply).
  *   rhs, x: device arrays of N*nA + nC doubles (caller-owned; rhs is read,
- *           x is written).  No refinement: x = (factored K)^{-1} rhs, computed
- *           by the same kernels in the same order as kkt_solve's first step.
+ *           x is written).  No refinement: x = (factored K)^{-1} rhs.  The
+ *           call applies the same factorization as kkt_solve with its own
+ *           kernels on the static work vectors (level solves over every
+ *           supernode, a column-by-column solve with the factor of S), so x
+ *           agrees with the first application inside kkt_solve to rounding,
+ *           within the conditioning bound of K, not bit for bit.
  *   Work vectors come from one file-scope device array of 2^21 doubles
  *   (16 MiB) that every GPU loading this library holds until process exit;
  *   systems with N*nA + 2*N*k + 2*nC above that (k: rows of A carrying B's
@@ -287,8 +297,9 @@ const char* kkt_last_error(void);
  *   different handles) race on it and must be serialized by the caller.
  *   Needs an FP64-accurate factor of S (handles in KKT_FP64 or
  *   KKT_F64_EMULATED mode); otherwise returns KKT_ERR_STATE.
- *   Asynchronous with respect to the host; errors of the launches are
- *   returned as KKT_ERR_CUDA. */
+ *   Asynchronous with respect to the host; errors of the launches, and an
+ *   error left pending on this thread by an earlier launch, are returned as
+ *   KKT_ERR_CUDA. */
 kkt_status kkt_solve_noalloc(kkt_handle* h, const double* rhs, double* x, void* stream);
 
 /* ---- batching and serving (no counterpart in the paper; the workload's many

@@ -20,7 +20,7 @@ PRECISIONS = {"fp64": KKT_FP64, "tf32": KKT_TF32, "bf16": KKT_BF16, "f64emu": KK
 STATUS = {
     0: "KKT_OK", 1: "KKT_ERR_INVALID", 2: "KKT_ERR_OOM", 3: "KKT_ERR_CUDA",
     4: "KKT_ERR_ZERO_PIVOT", 5: "KKT_ERR_INERTIA", 6: "KKT_ERR_NOT_CONVERGED",
-    7: "KKT_ERR_TIMEOUT", 8: "KKT_ERR_STATE",
+    7: "KKT_ERR_TIMEOUT", 8: "KKT_ERR_STATE", 9: "KKT_ERR_NONFINITE",
 }
 
 

@@ -160,6 +160,7 @@ const char* kkt_status_string(kkt_status s) {
     case KKT_ERR_NOT_CONVERGED: return "refinement did not converge";
     case KKT_ERR_TIMEOUT: return "device wait timed out";
     case KKT_ERR_STATE: return "call out of order";
+    case KKT_ERR_NONFINITE: return "NaN or Inf in the system or the solution";
   }
   return "unknown status";
 }
@@ -826,6 +827,7 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
     }
     h->schur_pending = false;
     int steps = 0;
+    bool nonfinite = false;
     double eta = INFINITY, eta_prev = INFINITY;
     for (;;) {
       KKT_CUDA(launch_residual(*h, h->rhs, h->x, h->rho, st));
@@ -839,11 +841,20 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
         return KKT_ERR_TIMEOUT;
       }
       const double* hr = h->host_red;
-      eta = hr[0] / (hr[3] * hr[1] + hr[2]);
-      if (!(hr[0] > 0.0)) eta = 0.0;
+      // hr: ||rho||, ||x||, ||r|| (inf-norms that keep NaN) and ||K||_inf
+      if (!std::isfinite(hr[2]) || !std::isfinite(hr[3])) {
+        // a NaN or Inf among the values of K or the right-hand side: no
+        // iterate can meet the test, and eta would be meaningless
+        eta = NAN;
+        nonfinite = true;
+        break;
+      }
+      const bool iterate_finite = std::isfinite(hr[0]) && std::isfinite(hr[1]);
+      eta = iterate_finite ? hr[0] / (hr[3] * hr[1] + hr[2]) : NAN;
+      if (iterate_finite && hr[0] == 0.0) eta = 0.0;  // exact: K x = r in FP64
       if (eta <= h->opt.refine_tol) break;
       const bool stalled = !(eta < 0.5 * eta_prev) || !std::isfinite(eta);
-      if (steps >= h->opt.max_refine || (steps > 0 && stalled)) {
+      if (steps >= h->opt.max_refine || (steps > 0 && stalled) || !iterate_finite) {
         if (h->s_factor == 1 && h->opt.fp64_fallback) {
           // refinement with the FP32 factor of S stalls: refactor S (still the
           // assembled FP64 matrix) FP64-accurately and restart from its solve
@@ -854,6 +865,7 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
           steps++;
           continue;
         }
+        if (!iterate_finite) nonfinite = true;
         break;
       }
       eta_prev = eta;
@@ -865,7 +877,8 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     h->info.refine_steps = steps;
     h->info.rel_residual = eta;
-    if (!(eta <= h->opt.refine_tol)) result = KKT_ERR_NOT_CONVERGED;
+    if (nonfinite) result = KKT_ERR_NONFINITE;
+    else if (!(eta <= h->opt.refine_tol) && result == KKT_OK) result = KKT_ERR_NOT_CONVERGED;
   }
   KKT_CUDA(cudaEventRecord(h->ev_s1, st));
   KKT_CUDA(cudaEventRecord(h->ev_done, st));
@@ -876,7 +889,10 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
   }
   h->info.ms_solve =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  if (result != KKT_OK) set_error("kkt_solve: refinement stopped above refine_tol");
+  if (result == KKT_ERR_NONFINITE)
+    set_error("kkt_solve: NaN or Inf in the values of K, the right-hand side or the solution");
+  else if (result != KKT_OK)
+    set_error("kkt_solve: refinement stopped above refine_tol");
   return result;
 }
 

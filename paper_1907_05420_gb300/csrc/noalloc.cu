@@ -4,11 +4,16 @@
 // that hands all device memory to its own pool up front and runs under that
 // fixed budget, or a latency-critical request loop that cannot accept the
 // device-wide synchronization that cudaMalloc/cudaFree may imply.  This entry
-// point applies the current factorization once (the same kernels, in the same
-// order, as the first application inside kkt_solve, without refinement) and
-// takes every per-call work vector from one file-scope device array instead
-// of the handle or a fresh allocation.  The array is shared by all handles
-// and by every call in the process.
+// point applies the current factorization once, without refinement, and takes
+// every per-call work vector from one file-scope device array instead of the
+// handle or a fresh allocation.  It uses its own kernel sequence on those
+// vectors: the supernodal level solves over every supernode (a dense tail's
+// factor is read from the panels it was scattered back into) and the
+// column-by-column dense solve with the factor of S.  kkt_solve applies the
+// same factorization with other kernels (dense tail solves, blocked solves of
+// S with diagonal-block inverses), so the two agree to rounding, within the
+// conditioning bound of K, not bit for bit.  The array is shared by all
+// handles and by every call in the process.
 #include <mutex>
 
 #include "handle.h"
@@ -99,7 +104,14 @@ extern "C" kkt_status kkt_solve_noalloc(kkt_handle* hh, const double* rhs, doubl
   ws.dot = ws.xg + round_up(h->nC);
   cudaStream_t st = (cudaStream_t)stream;
   h->stream = st;
-  (void)cudaGetLastError();
+  // an error left pending by an earlier launch on this thread would otherwise
+  // be reported as one of ours below: return it as it is
+  const cudaError_t pending = cudaGetLastError();
+  if (pending != cudaSuccess) {
+    set_error(std::string("kkt_solve_noalloc: error pending from an earlier launch: ") +
+              cudaGetErrorString(pending));
+    return KKT_ERR_CUDA;
+  }
   KKT_CUDA(launch_apply_inverse_ws(*h, rhs, x, ws, st));
   KKT_CUDA(cudaEventRecord(h->ev_done, st));
   return KKT_OK;

@@ -328,20 +328,25 @@ __global__ void k_resid_g(const int32_t* __restrict__ t_ptr, const int32_t* __re
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
-  // non-negative doubles order like their bit patterns
+  // non-negative doubles order like their bit patterns; a NaN with a clear
+  // sign bit orders above +Inf, so it survives the maximum
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// red[0] = ||a||_inf, red[1] = ||b||_inf, red[2] = ||c||_inf
+// max(a, b) that keeps a NaN of either argument (fmax drops it), so that a
+// non-finite entry reaches the norm and the convergence test sees it
+__device__ __forceinline__ double max_keep_nan(double a, double b) { return (a > b || a != a) ? a : b; }
+
+// red[0] = ||a||_inf, red[1] = ||b||_inf, red[2] = ||c||_inf; NaN if an entry is NaN
 __global__ void k_norms3(const double* __restrict__ a, const double* __restrict__ b,
                          const double* __restrict__ c, int64_t n, double* __restrict__ red) {
   __shared__ double sh[3][256];
   double m0 = 0, m1 = 0, m2 = 0;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
-    m0 = fmax(m0, fabs(a[q]));
-    m1 = fmax(m1, fabs(b[q]));
-    m2 = fmax(m2, fabs(c[q]));
+    m0 = max_keep_nan(m0, fabs(a[q]));
+    m1 = max_keep_nan(m1, fabs(b[q]));
+    m2 = max_keep_nan(m2, fabs(c[q]));
   }
   sh[0][threadIdx.x] = m0;
   sh[1][threadIdx.x] = m1;
@@ -349,14 +354,14 @@ __global__ void k_norms3(const double* __restrict__ a, const double* __restrict_
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s)
-      for (int k = 0; k < 3; k++) sh[k][threadIdx.x] = fmax(sh[k][threadIdx.x], sh[k][threadIdx.x + s]);
+      for (int k = 0; k < 3; k++) sh[k][threadIdx.x] = max_keep_nan(sh[k][threadIdx.x], sh[k][threadIdx.x + s]);
     __syncthreads();
   }
   if (threadIdx.x == 0)
     for (int k = 0; k < 3; k++) atomic_max_nonneg(&red[k], sh[k][0]);
 }
 
-// ||K||_inf: row sums of |K|
+// ||K||_inf: row sums of |K| (NaN if an entry of A or B is NaN)
 __global__ void k_knorm_blocks(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ src,
                                const double* __restrict__ a_vals, int64_t nnzA,
                                const int32_t* __restrict__ bt_ptr, const int32_t* __restrict__ b_row,
@@ -371,7 +376,7 @@ __global__ void k_knorm_blocks(const int32_t* __restrict__ rowptr, const int32_t
     const double* a = a_vals + b * nnzA;
     double acc = 0.0;
     for (int p = rowptr[row]; p < rowptr[row + 1]; p++) acc += fabs(a[src[p]]);
-    m = fmax(m, acc);
+    m = max_keep_nan(m, acc);
   }
   // rows of E also carry B's entries
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)k * N;
@@ -384,7 +389,7 @@ __global__ void k_knorm_blocks(const int32_t* __restrict__ rowptr, const int32_t
     double acc = 0.0;
     for (int p = rowptr[row]; p < rowptr[row + 1]; p++) acc += fabs(a[src[p]]);
     for (int e = bp[t]; e < bp[t + 1]; e++) acc += fabs(b_vals[e]);
-    m = fmax(m, acc);
+    m = max_keep_nan(m, acc);
   }
   atomic_max_nonneg(out, m);
 }

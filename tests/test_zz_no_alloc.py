@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gen import CONFIGS, make_problem
+from gen import CONFIGS, GridSpec, make_problem
 from tests.kkt_dense import dense_K
 
 pytestmark = pytest.mark.gpu
@@ -33,9 +33,9 @@ def _torch():
     return torch
 
 
-def _factored(p, torch, B):
+def _factored(p, torch, B, opt=None):
     dev = torch.device("cuda:0")
-    h = B.kkt_analyze(p)
+    h = B.kkt_analyze(p, opt)
     a = torch.from_numpy(np.ascontiguousarray(p.a_vals)).to(dev)
     b = torch.from_numpy(np.ascontiguousarray(p.b_vals)).to(dev)
     c = torch.from_numpy(np.ascontiguousarray(p.c_vals)).to(dev)
@@ -71,6 +71,53 @@ def test_noalloc_matches_kkt_solve_on_two_calls(name):
         err = np.max(np.abs(x - x_ref)) / np.max(np.abs(x_ref))
         assert err <= tol, (err, tol)
         assert eta <= 1e-10
+
+
+# Cases where the work-vector path departs most from kkt_solve's kernels: a
+# dense tail whose factor was scattered back into the panels (FP64 and
+# emulated-FP64 updates, augmented by the coupling rows), the envelope-limited
+# factor of S, and the emulated-FP64 factor of S.
+AUG14 = GridSpec(14, 18, 3, 2, 4, 1e-6, 1e6, 102, "aug14")
+CASES = {
+    "aug14_tail_fp64": (AUG14, "fp64", {"dense_tail": 1}),
+    "aug14_tail_emulated": (AUG14, "f64emu", {"dense_tail": 2}),
+    "grid30_structured_s": (CONFIGS["grid30_n24"], "fp64", {"structured_s": 1}),
+    "grid30_f64emu": (CONFIGS["grid30_n24"], "f64emu", {}),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_noalloc_matches_kkt_solve_tail_structured_emulated(case):
+    torch = _torch()
+    from paper_1907_05420_gb300 import binding as B
+
+    spec, prec, kw = CASES[case]
+    p = make_problem(spec)
+    h, r = _factored(p, torch, B, B.kkt_default_options(prec, **kw))
+    try:
+        info = B.kkt_get_info(h)
+        if "dense_tail" in kw:
+            assert info["dense_tail_cols"] > 0 and info["tail_augmented"] == 1
+        x_ref = torch.empty_like(r)
+        B.kkt_solve(h, r, x_ref)
+        outs = []
+        for _ in range(2):
+            x = torch.full_like(r, float("nan"))
+            B.kkt_solve_noalloc(h, r, x)
+            torch.cuda.synchronize()
+            outs.append(x.cpu().numpy())
+    finally:
+        B.kkt_destroy(h)
+    x_ref = x_ref.cpu().numpy()
+    kappa = np.linalg.cond(dense_K(p))
+    eta_ref = oracle.backward_error(p, x_ref)
+    assert np.array_equal(outs[0], outs[1])
+    for x in outs:
+        eta = oracle.backward_error(p, x)
+        assert eta <= 1e-10, eta
+        tol = 10.0 * kappa * max(eta, eta_ref, EPS)
+        err = np.max(np.abs(x - x_ref)) / np.max(np.abs(x_ref))
+        assert err <= tol, (err, tol)
 
 
 def test_noalloc_second_system_reuses_the_shared_array():
