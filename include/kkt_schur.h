@@ -302,6 +302,71 @@ const char* kkt_last_error(void);
  *   KKT_ERR_CUDA. */
 kkt_status kkt_solve_noalloc(kkt_handle* h, const double* rhs, double* x, void* stream);
 
+/* ---- the steps of Algorithm 1 one at a time (Sec. 4.2), for a solve whose
+ * blocks are spread over processes, one GPU each ----
+ * Process p holds a handle analysed for its own blocks i in N_p (its share of
+ * the periods) and the coupling columns they touch, c0 .. c0 + nC_p - 1
+ * (re-indexed from 0); the root holds every coupling column and C, the others
+ * a zero C.  Then (Algorithm 1):
+ *   every p:  kkt_factor_blocks     A_i = L_i D_i L_i^T and S_p = C_p - sum B_i^T A_i^{-1} B_i
+ *   reduce:   the root adds each S_p into the window (c0, c0) of its own S
+ *             (kkt_schur_matrix, kkt_accumulate);
+ *   root:     kkt_factor_schur      S = L_s D_s L_s^T
+ *   every p:  kkt_solve_front       t_p = r_g,p - sum B_i^T A_i^{-1} r_i (r_g,p = 0 off the root)
+ *   reduce:   the root adds each t_p into its t window (kkt_accumulate);
+ *   root:     kkt_solve_coupling    x_g = S^{-1} t;  broadcast x_g
+ *   every p:  kkt_solve_back        x_i = A_i^{-1} (r_i - B_i x_g) with its window of x_g.
+ * FP64 refinement on the distributed K uses kkt_residual (the coupling rows
+ * of each process's residual are its part of r_g - C x_g - sum B_i^T x_i, added
+ * up at the root like t), kkt_abs_rowsums (the rows of |K|, for ||K||_inf) and
+ * kkt_norm_inf.  The collectives are the caller's (torch.distributed in the
+ * Python layer).  All arrays are device arrays of the handle's device, all
+ * calls asynchronous on `stream` except kkt_norm_inf. */
+
+/* kkt_factor without the factor of S: block factors and the assembled S of
+ * the handle's blocks (Algorithm 1: block factorization, local Schur
+ * contributions and their accumulation; eq. SCform).  The Schur contraction
+ * is FP64 in every mode.  kkt_solve needs kkt_factor_schur afterwards. */
+kkt_status kkt_factor_blocks(kkt_handle* h, const double* a_vals, const double* b_vals, const double* c_vals,
+                             int32_t on_device, void* stream);
+/* The handle's S buffer: nC x nC doubles, column-major with leading dimension
+ * *ld = nC, lower triangle (the strictly upper part is zero after
+ * kkt_factor_blocks).  Owned by the handle until kkt_destroy.  After
+ * kkt_factor_schur in the KKT_FP64 and KKT_F64_EMULATED modes it holds the
+ * factor (L strictly below the diagonal, D on it); the TF32 and BF16 modes
+ * factor a copy and keep S. */
+kkt_status kkt_schur_matrix(kkt_handle* h, double** S, int64_t* ld);
+/* Dense LDL^T of the handle's current S in its precision mode (Algorithm 1,
+ * factorization of S; eq. SCsolve); needs kkt_factor_blocks first. */
+kkt_status kkt_factor_schur(kkt_handle* h, void* stream);
+/* The current factor of S as nC x nC doubles (device out; column-major, L
+ * strictly below the diagonal, D on it, the upper part unspecified): the FP32
+ * factor converted in the TF32 and BF16 modes. */
+kkt_status kkt_schur_factor_copy(kkt_handle* h, double* out, void* stream);
+/* dst[i + j ld_dst] += src[i + j ld_src] for i < rows, j < cols (device
+ * arrays; a vector is cols = 1).  The reduce of Algorithm 1 on the root. */
+kkt_status kkt_accumulate(double* dst, int64_t ld_dst, const double* src, int64_t ld_src, int64_t rows,
+                          int64_t cols, void* stream);
+/* Front half of one application: z_i = L_i^{-1} P^T r_i for the handle's
+ * blocks and t = r_g - sum_i B_i^T A_i^{-1} r_i (eq. SCsolve; rhs: N*nA + nC
+ * doubles, t: nC).  Keeps z in the handle for kkt_solve_back. */
+kkt_status kkt_solve_front(kkt_handle* h, const double* rhs, double* t, void* stream);
+/* x_g = S^{-1} t with the current factor of S (t and xg distinct, nC each). */
+kkt_status kkt_solve_coupling(kkt_handle* h, const double* t, double* xg, void* stream);
+/* Back half after kkt_solve_front on the same handle: x_i = A_i^{-1} (r_i -
+ * B_i x_g) for the handle's blocks (eq. SCsolve1); x (N*nA + nC) also gets
+ * xg in its last nC entries. */
+kkt_status kkt_solve_back(kkt_handle* h, const double* xg, double* x, void* stream);
+/* rho = rhs - K x with the handle's values (block rows r_i - A_i x_i - B_i x_g;
+ * coupling rows r_g - C x_g - sum_i B_i^T x_i over the handle's blocks). */
+kkt_status kkt_residual(kkt_handle* h, const double* rhs, const double* x, double* rho, void* stream);
+/* out (N*nA + nC doubles): the absolute row sums of the handle's K; the
+ * coupling rows hold sum |B column| + sum |C row| over the handle's blocks. */
+kkt_status kkt_abs_rowsums(kkt_handle* h, double* out, void* stream);
+/* *out = max |v_i| over n device doubles (NaN if any entry is NaN);
+ * synchronizes `stream`. */
+kkt_status kkt_norm_inf(kkt_handle* h, const double* v, int64_t n, double* out, void* stream);
+
 /* ---- batching and serving (no counterpart in the paper; the workload's many
  * independent systems of different grids and horizons) ---- */
 

@@ -77,7 +77,10 @@ class kkt_inertia_result(C.Structure):
 EXPORTS = ["kkt_default_options", "kkt_analyze", "kkt_factor", "kkt_solve", "kkt_get_info",
            "kkt_destroy", "kkt_status_string", "kkt_last_error", "kkt_measure_fp64_peak",
            "kkt_solve_noalloc", "kkt_batch_factor_solve", "kkt_server_create", "kkt_server_submit",
-           "kkt_server_poll", "kkt_server_destroy", "kkt_default_inertia_options", "kkt_factor_inertia"]
+           "kkt_server_poll", "kkt_server_destroy", "kkt_default_inertia_options", "kkt_factor_inertia",
+           "kkt_factor_blocks", "kkt_schur_matrix", "kkt_factor_schur", "kkt_schur_factor_copy", "kkt_accumulate",
+           "kkt_solve_front", "kkt_solve_coupling", "kkt_solve_back", "kkt_residual", "kkt_abs_rowsums",
+           "kkt_norm_inf"]
 
 _lib = None
 
@@ -136,6 +139,20 @@ def load(build_if_missing: bool = True):
     L.kkt_factor_inertia.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
                                      C.POINTER(kkt_inertia_options), C.POINTER(kkt_inertia_result)]
     L.kkt_factor_inertia.restype = C.c_int
+    vp = C.c_void_p
+    for name, args in (("kkt_factor_blocks", [vp, vp, vp, vp, C.c_int32, vp]),
+                       ("kkt_schur_matrix", [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
+                       ("kkt_factor_schur", [vp, vp]),
+                       ("kkt_schur_factor_copy", [vp, vp, vp]),
+                       ("kkt_accumulate", [vp, C.c_int64, vp, C.c_int64, C.c_int64, C.c_int64, vp]),
+                       ("kkt_solve_front", [vp, vp, vp, vp]),
+                       ("kkt_solve_coupling", [vp, vp, vp, vp]),
+                       ("kkt_solve_back", [vp, vp, vp, vp]),
+                       ("kkt_residual", [vp, vp, vp, vp, vp]),
+                       ("kkt_abs_rowsums", [vp, vp, vp]),
+                       ("kkt_norm_inf", [vp, vp, C.c_int64, C.POINTER(C.c_double), vp])):
+        getattr(L, name).argtypes = args
+        getattr(L, name).restype = C.c_int
     _lib = L
     return L
 
@@ -290,6 +307,75 @@ def kkt_batch_factor_solve(handles, a_vals, b_vals, c_vals, rhs, x, streams=8):
 
 
 KKT_ERR_STATE = 8
+
+
+# ---- the steps of Algorithm 1 one at a time (include/kkt_schur.h) ----
+# Arrays are torch tensors on the handle's device (float64, contiguous).
+
+def _dev(t):
+    p, d = _ptr(t)
+    if t is not None and not d:
+        raise ValueError("device arrays only")
+    return p
+
+
+def kkt_factor_blocks(h, a_vals, b_vals, c_vals, stream=None):
+    pa, da = _ptr(a_vals)
+    pb, db = _ptr(b_vals)
+    pc, dc = _ptr(c_vals)
+    if len({da, db, dc}) != 1:
+        raise ValueError("a_vals, b_vals and c_vals must all be host or all device arrays")
+    return _check(load().kkt_factor_blocks(h, pa, pb, pc, da, _stream_ptr(stream)))
+
+
+def kkt_schur_matrix(h):
+    """(device address, leading dimension) of the handle's S buffer."""
+    ptr, ld = C.c_void_p(), C.c_int64()
+    _check(load().kkt_schur_matrix(h, C.byref(ptr), C.byref(ld)))
+    return ptr.value, ld.value
+
+
+def kkt_factor_schur(h, stream=None):
+    return _check(load().kkt_factor_schur(h, _stream_ptr(stream)))
+
+
+def kkt_schur_factor_copy(h, out, stream=None):
+    return _check(load().kkt_schur_factor_copy(h, _dev(out), _stream_ptr(stream)))
+
+
+def kkt_accumulate(dst_ptr, ld_dst, src, ld_src, rows, cols, stream=None):
+    """dst[i + j ld_dst] += src[i + j ld_src]; dst_ptr an address or a tensor."""
+    if not isinstance(dst_ptr, int):
+        dst_ptr = _dev(dst_ptr)
+    return _check(load().kkt_accumulate(dst_ptr, int(ld_dst), _dev(src), int(ld_src), int(rows), int(cols),
+                                        _stream_ptr(stream)))
+
+
+def kkt_solve_front(h, rhs, t, stream=None):
+    return _check(load().kkt_solve_front(h, _dev(rhs), _dev(t), _stream_ptr(stream)))
+
+
+def kkt_solve_coupling(h, t, xg, stream=None):
+    return _check(load().kkt_solve_coupling(h, _dev(t), _dev(xg), _stream_ptr(stream)))
+
+
+def kkt_solve_back(h, xg, x, stream=None):
+    return _check(load().kkt_solve_back(h, _dev(xg), _dev(x), _stream_ptr(stream)))
+
+
+def kkt_residual(h, rhs, x, rho, stream=None):
+    return _check(load().kkt_residual(h, _dev(rhs), _dev(x), _dev(rho), _stream_ptr(stream)))
+
+
+def kkt_abs_rowsums(h, out, stream=None):
+    return _check(load().kkt_abs_rowsums(h, _dev(out), _stream_ptr(stream)))
+
+
+def kkt_norm_inf(h, v, n=None, stream=None):
+    out = C.c_double()
+    n = v.numel() if n is None else int(n)
+    _check(load().kkt_norm_inf(h, _dev(v), n, C.byref(out), _stream_ptr(stream)))
+    return out.value
 
 
 class KKTServer:

@@ -54,7 +54,7 @@ void free_all(Handle* h) {
                   h->t_scaleA, h->t_scaleB, h->Lx, h->a_vals, h->b_vals,
                   h->c_vals, h->anorm, h->W, h->G, h->S, h->Ypanel, h->knorm, h->counters, h->r,
                   h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red,
-                  h->trsv_flags, h->trsv_ticket, h->dev_err, h->S32, h->Y32, h->tc_imgA,
+                  h->trsv_flags, h->trsv_ticket, h->dev_err, h->S32, h->Y32, h->tw_img, h->tc_imgA,
                   h->tc_imgB, h->tc_scaleA, h->tc_scaleB};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -80,7 +80,7 @@ cudaError_t record(Handle& h, cudaEvent_t ev, cudaStream_t st) {
 // The device work of kkt_factor after the input copies: every launch depends
 // only on the handle's buffers and options, so the sequence is captured once
 // as a CUDA graph and replayed.
-cudaError_t enqueue_factor(Handle& h, cudaStream_t st) {
+cudaError_t enqueue_factor(Handle& h, cudaStream_t st, bool with_s = true) {
   cudaError_t e = cudaMemsetAsync(h.counters, 0, sizeof(unsigned long long) * 2 * kNumCounters, st);
 #define STEP(x) \
   if (e == cudaSuccess) e = (x)
@@ -96,7 +96,9 @@ cudaError_t enqueue_factor(Handle& h, cudaStream_t st) {
   }
   STEP(launch_assemble_s(h, st));
   STEP(record(h, h.ev_fb, st));
-  if (h.opt.prec == KKT_FP64) {
+  if (!with_s) {
+    // the factor of S is left to kkt_factor_schur (a sharded solve reduces S first)
+  } else if (h.opt.prec == KKT_FP64) {
     STEP(launch_dense_ldlt(h, h.counters + kNumCounters, st));
   } else {
     STEP(launch_dense_ldlt_tc(h, h.opt.prec, h.counters + kNumCounters, st));
@@ -498,6 +500,12 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
     AL(S32, float, (int64_t)h->nC * h->nC);
     AL(Y32, float, (int64_t)h->nC * kDenseNB);
   }
+  if (h->opt.prec == KKT_TF32 && tf32_wide_applies(h->nC, h->opt.structured_s != 0)) {
+    h->tw_set_bytes = tf32_wide_set_bytes(h->nC);
+    AL(tw_img, uint8_t, 16 * h->tw_set_bytes);
+    // rows past the trailing matrix are read (and masked) in whole tiles: keep them finite
+    if (e == cudaSuccess) e = cudaMemset(h->tw_img, 0, (size_t)(16 * h->tw_set_bytes));
+  }
   if (h->opt.prec != KKT_FP64 && h->nC > 0) {
     // operand images sized for the largest panel step; the FP64 fallback of the
     // reduced modes uses the emulated path, so size for the larger of the two
@@ -582,7 +590,7 @@ double time_factor(kkt_handle* hh, const kkt_pattern* pat) {
 // The factor of the input values with the inertia-correction shift (dw, dc;
 // dcs on C's diagonal) applied to the device copy (none when dw and dc are 0).
 kkt_status factor_values(Handle* h, const double* a_vals, const double* b_vals, const double* c_vals,
-                         int32_t on_device, cudaStream_t st, double dw, double dc, double dcs) {
+                         int32_t on_device, cudaStream_t st, double dw, double dc, double dcs, bool with_s = true) {
   h->stream = st;
   (void)cudaGetLastError();  // drop a stale non-sticky error left by an unrelated call
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -592,22 +600,26 @@ kkt_status factor_values(Handle* h, const double* a_vals, const double* b_vals, 
   if (h->nnzB > 0) KKT_CUDA(cudaMemcpyAsync(h->b_vals, b_vals, sizeof(double) * h->nnzB, kind, st));
   if (nc_vals > 0) KKT_CUDA(cudaMemcpyAsync(h->c_vals, c_vals, sizeof(double) * nc_vals, kind, st));
   if (dw != 0.0 || dc != 0.0) KKT_CUDA(launch_shift_diag(*h, dw, dc, dcs, st));
-  h->g_reduced = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && h->opt.reduced_contraction &&
+  // the split factor (kkt_factor_blocks) keeps the FP64 contraction: its S may
+  // take other processes' parts, which a fallback could not rebuild
+  h->g_reduced = with_s && (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && h->opt.reduced_contraction &&
                  contract_g_tc_supported(*h);
   h->s_factor = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) ? 1 : 0;
-  if (h->opt.use_graphs && !h->graph_failed && !h->factor_exec) capture_factor(*h);
-  if (h->factor_exec) {
+  if (with_s && h->opt.use_graphs && !h->graph_failed && !h->factor_exec) capture_factor(*h);
+  if (with_s && h->factor_exec) {
     KKT_CUDA(cudaGraphLaunch(h->factor_exec, st));
     h->launches += h->graph_launches;
   } else {
-    KKT_CUDA(enqueue_factor(*h, st));
+    KKT_CUDA(enqueue_factor(*h, st, with_s));
   }
   h->info.fell_back_fp64 = 0;
-  h->schur_pending = true;
+  h->schur_pending = with_s;
   KKT_CUDA(cudaEventRecord(h->ev_f1, st));
   KKT_CUDA(cudaEventRecord(h->ev_done, st));
-  h->factored = true;
-  h->timed_factor = true;
+  h->blocks_factored = true;
+  h->front_done = false;
+  h->factored = with_s;
+  h->timed_factor = with_s;
   return KKT_OK;
 }
 
@@ -691,6 +703,16 @@ kkt_status kkt_factor(kkt_handle* hh, const double* a_vals, const double* b_vals
     return KKT_ERR_INVALID;
   }
   return factor_values(h, a_vals, b_vals, c_vals, on_device, (cudaStream_t)stream, 0.0, 0.0, 0.0);
+}
+
+kkt_status kkt_factor_blocks(kkt_handle* hh, const double* a_vals, const double* b_vals, const double* c_vals,
+                             int32_t on_device, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !a_vals || (h->nnzB > 0 && !b_vals) || (h->nC > 0 && !c_vals)) {
+    set_error("kkt_factor_blocks: null argument");
+    return KKT_ERR_INVALID;
+  }
+  return factor_values(h, a_vals, b_vals, c_vals, on_device, (cudaStream_t)stream, 0.0, 0.0, 0.0, false);
 }
 
 void kkt_default_inertia_options(kkt_inertia_options* opt) {

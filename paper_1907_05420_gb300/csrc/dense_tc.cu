@@ -661,6 +661,267 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
+// ---- TF32 trailing update of a 256-wide outer panel (two-level blocking) ----
+//
+// The TF32 factor of S runs the 64-wide panel steps above inside outer panels
+// of kWideW = 256 columns: the inner steps update only the outer panel's own
+// columns, and the rest of the trailing matrix takes one update with K = 256
+// per outer panel, S22 -= [Y_0 .. Y_3] [L_0 .. L_3]^T, which reads and writes
+// S a quarter as often as four 64-wide updates.  The operands are the images
+// the inner panel kernels wrote (one set per inner step: Y and L21 of the rows
+// below that step, 8-row x 16-byte core matrices, 16 cores along K), read at
+// the row offset of the outer trailing matrix in each set.
+//
+// One CTA per run of up to kWideRun tiles (I, J), J <= I, of one tile row I
+// (tiles of 128 x 128):
+//   warp 0 (one lane): bulk copies: the row's A operand (4 chunks of 128 rows
+//                      x 64 columns, 128 KB, once), then the B chunks of every
+//                      tile through kWideStages shared-memory stages;
+//   warp 1 (one lane): tensor-memory allocation and the MMAs (M = N = 128,
+//                      K = 8 per instruction, 32 per tile) into one of two
+//                      tensor-memory accumulators, so that the products of
+//                      the next tile run during this tile's epilogue;
+//   warps 2-9:         the epilogue, two warps per tensor-memory lane quadrant
+//                      (64 columns per thread): read the accumulator, hand it
+//                      back, read-modify-write the lower-triangle entries of S.
+// Every wait is bounded: a timeout sets *err, makes the other roles stop, lets
+// the copies and products in flight finish (bounded again) and frees tensor
+// memory before the CTA exits.
+constexpr int kWideW = 256;                        // outer panel width (K of the update)
+constexpr int kWideChunks = kWideW / TK;           // 64-column chunks (image sets)
+constexpr int kWideTile = 128;                     // output tile: 128 x 128
+constexpr int kWideChunkBytes = kWideTile / 8 * 16 * 128;  // one chunk of 128 rows (TF32), 32 KB
+constexpr int kWideStages = 3;                     // B chunk stages
+constexpr int kWideRun = 8;                        // tiles per CTA
+constexpr int kWideEpiWarps = 8;
+constexpr int kWideThreads = 64 + 32 * kWideEpiWarps;
+__host__ __device__ constexpr int wide_smem_bytes() {
+  return kWideChunks * kWideChunkBytes + kWideStages * kWideChunkBytes;  // 224 KB
+}
+static_assert(wide_smem_bytes() <= 227 * 1024 - 256, "wide update exceeds shared memory");
+
+// tile columns [jlo, jhi) of tile row I for jmode (0 all J <= I, 1 J < 2, 2 J >= 2)
+__host__ __device__ inline void wide_row_range(int I, int jmode, int& jlo, int& jhi) {
+  jlo = jmode == 2 ? 2 : 0;
+  jhi = jmode == 1 ? (I + 1 < 2 ? I + 1 : 2) : I + 1;
+}
+
+__host__ __device__ inline int wide_row_tasks(int I, int jmode) {
+  int jlo, jhi;
+  wide_row_range(I, jmode, jlo, jhi);
+  return jhi > jlo ? (jhi - jlo + kWideRun - 1) / kWideRun : 0;
+}
+
+__host__ inline int wide_tasks(int TI, int jmode) {
+  int t = 0;
+  for (int I = 0; I < TI; I++) t += wide_row_tasks(I, jmode);
+  return t;
+}
+
+__global__ void __launch_bounds__(kWideThreads, 1)
+    k_tc_update_wide(float* __restrict__ S, int n, int base, int m, int TI, int jmode,
+                     const uint8_t* __restrict__ imgA, const uint8_t* __restrict__ imgB, int64_t set_bytes,
+                     int* err) {
+  constexpr int KG = kgroups_of(0);                 // 16 core matrices along a 64-column chunk
+  constexpr int KSTEPS = TK * 4 / 32;               // 8 MMAs of K = 8 per chunk
+  constexpr uint32_t TMEM_COLS = 2 * kWideTile;     // two 128-column accumulators
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t* sA = smem;                               // kWideChunks chunks of 128 rows
+  uint8_t* sB = smem + kWideChunks * kWideChunkBytes;  // kWideStages stages
+  __shared__ __align__(8) uint64_t bar_a, bar_full[kWideStages], bar_empty[kWideStages], bar_accf[2], bar_acce[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_abort;
+
+  // task -> tile row I and its run [j0, j1)
+  int I = 0, t = blockIdx.x;
+  for (;;) {
+    const int c = wide_row_tasks(I, jmode);
+    if (t < c || I + 1 >= TI) break;
+    t -= c;
+    I++;
+  }
+  int jlo, jhi;
+  wide_row_range(I, jmode, jlo, jhi);
+  const int j0 = jlo + t * kWideRun, j1 = min(j0 + kWideRun, jhi);
+  const int ntile = max(0, j1 - j0);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_a)));
+    for (int q = 0; q < kWideStages; q++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_empty[q])));
+    }
+    for (int q = 0; q < 2; q++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_accf[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_acce[q])), "r"(kWideEpiWarps));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  // image set c holds the rows below inner step c; the outer trailing matrix
+  // starts (kWideChunks - 1 - c) * 64 rows into it
+  auto chunk_src = [&](const uint8_t* img, int c, int row0) -> const uint8_t* {
+    const int64_t rho = (int64_t)(kWideChunks - 1 - c) * TK + row0;
+    return img + (int64_t)c * set_bytes + rho * (KG * 16);
+  };
+
+  if (warp == 0) {
+    if (lane == 0 && ntile > 0) {
+      // producer
+      const uint32_t ba = smem_u32(&bar_a);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ba),
+                   "r"((uint32_t)(kWideChunks * kWideChunkBytes))
+                   : "memory");
+      for (int c = 0; c < kWideChunks; c++)
+        bulk_load(sA + c * kWideChunkBytes, chunk_src(imgA, c, I * kWideTile), kWideChunkBytes, ba);
+      int armed[kWideStages] = {};
+      const int nchunk = ntile * kWideChunks;
+      for (int g = 0; g < nchunk; g++) {
+        const int q = g % kWideStages;
+        if (g >= kWideStages &&
+            !mbar_wait_ab(smem_u32(&bar_empty[q]), (uint32_t)((g / kWideStages - 1) & 1), &s_abort)) {
+          if (!s_abort) atomicExch(err, 8);
+          s_abort = 1;
+          break;
+        }
+        const uint32_t bf = smem_u32(&bar_full[q]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bf), "r"((uint32_t)kWideChunkBytes)
+                     : "memory");
+        const int J = j0 + g / kWideChunks, c = g % kWideChunks;
+        bulk_load(sB + q * kWideChunkBytes, chunk_src(imgB, c, J * kWideTile), kWideChunkBytes, bf);
+        armed[q]++;
+      }
+      // the copies issued must land before the CTA's shared memory goes away
+      volatile int never = 0;
+      mbar_wait_ab(ba, 0u, &never);
+      for (int q = 0; q < kWideStages; q++)
+        if (armed[q] > 0) mbar_wait_ab(smem_u32(&bar_full[q]), (uint32_t)((armed[q] - 1) & 1), &never);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && ntile > 0) {
+      // MMA issuer
+      uint32_t last_bar = 0, last_par = 0;  // the barrier of the last commit and its phase parity
+      if (!mbar_wait_ab(smem_u32(&bar_a), 0u, &s_abort)) {
+        if (!s_abort) atomicExch(err, 9);
+        s_abort = 1;
+      } else {
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kWideTile >> 3) << 17) |
+                               ((uint32_t)(kWideTile >> 4) << 24);
+        bool stop = false;
+        for (int u = 0; u < ntile && !stop; u++) {
+          const int b = u & 1;
+          if (u >= 2 && !mbar_wait_ab(smem_u32(&bar_acce[b]), (uint32_t)(((u >> 1) - 1) & 1), &s_abort)) {
+            if (!s_abort) atomicExch(err, 10);
+            s_abort = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t dtm = tmem + (uint32_t)(b * kWideTile);
+          for (int c = 0; c < kWideChunks; c++) {
+            const int g = u * kWideChunks + c, q = g % kWideStages;
+            if (!mbar_wait_ab(smem_u32(&bar_full[q]), (uint32_t)((g / kWideStages) & 1), &s_abort)) {
+              if (!s_abort) atomicExch(err, 11);
+              s_abort = 1;
+              stop = true;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            for (int ks = 0; ks < KSTEPS; ks++) {
+              const uint64_t ad = umma_desc(smem_u32(sA + c * kWideChunkBytes + ks * 256), 128, KG * 128);
+              const uint64_t bd = umma_desc(smem_u32(sB + q * kWideChunkBytes + ks * 256), 128, KG * 128);
+              const uint32_t acc = (c == 0 && ks == 0) ? 0u : 1u;
+              asm volatile(
+                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, "
+                  "p;\n}" ::"r"(dtm),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bar_empty[q]))
+                         : "memory");
+            last_bar = smem_u32(&bar_empty[q]);
+            last_par = (uint32_t)((g / kWideStages) & 1);
+          }
+          if (stop) break;
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&bar_accf[b]))
+                       : "memory");
+          last_bar = smem_u32(&bar_accf[b]);
+          last_par = (uint32_t)((u >> 1) & 1);
+        }
+        // products in flight must finish before tensor memory is freed: the
+        // last commit covers every MMA issued before it
+        volatile int never = 0;
+        if (last_bar) mbar_wait_ab(last_bar, last_par, &never);
+      }
+    }
+  } else {
+    // epilogue: tile row rho = I*128 + 32 (warp mod 4) + lane, columns
+    // h*64 .. h*64 + 63 of each tile
+    const int qd = warp & 3, h = (warp - 2) >> 2;
+    const int rho = I * kWideTile + qd * 32 + lane;
+    const int row = base + rho;
+    const bool live_row = rho < m;
+    for (int u = 0; u < ntile; u++) {
+      const int b = u & 1, J = j0 + u;
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait_ab(smem_u32(&bar_accf[b]), (uint32_t)((u >> 1) & 1), &s_abort);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) {
+        if (lane == 0) {
+          if (!s_abort) atomicExch(err, 12);
+          s_abort = 1;
+        }
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      uint32_t r0[32], r1[32];
+      const uint32_t ta = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * kWideTile + h * 64);
+      tmem_ld32(ta, r0);
+      tmem_ld32(ta + 32, r1);
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_acce[b])) : "memory");
+      if (live_row) {
+        const int cj0 = J * kWideTile + h * 64;
+        float cur[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+          const int cj = cj0 + j, col = base + cj;
+          cur[j] = (cj < m && row >= col) ? S[(int64_t)row + (int64_t)col * n] : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+          const int cj = cj0 + j, col = base + cj;
+          if (cj < m && row >= col) S[(int64_t)row + (int64_t)col * n] = cur[j] - __uint_as_float(r0[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+          const int cj = cj0 + 32 + j, col = base + cj;
+          cur[j] = (cj < m && row >= col) ? S[(int64_t)row + (int64_t)col * n] : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+          const int cj = cj0 + 32 + j, col = base + cj;
+          if (cj < m && row >= col) S[(int64_t)row + (int64_t)col * n] = cur[j] - __uint_as_float(r1[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
 // ---- FP32 panel kernels for the TF32 / BF16 modes (same steps as the FP64 ones in dense.cu) ----
 
 __global__ void k_to_f32(const double* __restrict__ S, float* __restrict__ S32, int64_t n2) {
@@ -772,6 +1033,91 @@ cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int npiv, int nb, const TcSt
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// The TF32 factor of S with 256-wide outer panels (k_tc_update_wide above).
+// Per outer panel K0: its four 64-wide steps (diagonal block, panel with the
+// operand images in set c of the panel's parity, update of the panel's own
+// remaining columns), then the outer update of the rest, split as in
+// factor_tc: its first two tile columns (the next outer panel's 256 columns)
+// on the high-priority chain, the rest on the side stream, overlapping the
+// next outer panel's steps.  The image sets alternate between two parities, so
+// that the next panel does not overwrite the images the rest still reads.
+cudaError_t factor_tf32_wide(Handle& h, float* S, float* Y, int n, unsigned long long* counters, cudaStream_t caller) {
+  constexpr int B_BYTES = image_bytes(0, TN), A_BYTES = image_bytes(0, TM);
+  cudaStream_t side = h.side_stream;
+  cudaStream_t st = caller;
+  const int prio = side ? h.prio_hi : 0;
+  bool side_busy = false;
+  cudaError_t e = cudaSuccess;
+  if (side && h.hi_stream) {
+    e = cudaEventRecord(h.ev_main, caller);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h.hi_stream, h.ev_main, 0);
+    if (e != cudaSuccess) return e;
+    st = h.hi_stream;
+  }
+  const int64_t sb = h.tw_set_bytes;
+  for (int K0 = 0, j = 0; K0 < n && e == cudaSuccess; K0 += kWideW, j++) {
+    const int Wb = std::min(kWideW, n - K0);
+    uint8_t* setA = h.tw_img + (int64_t)(j & 1) * 2 * kWideChunks * sb;  // [parity][A sets | B sets]
+    uint8_t* setB = setA + kWideChunks * sb;
+    for (int c = 0; c * TK < Wb && e == cudaSuccess; c++) {
+      const int k0 = K0 + c * TK, kb = std::min(TK, n - k0);
+      launch_prio(k_dense_diag_t<float>, dim3(1), dim3(256), 0, st, prio, S, n, k0, kb, (int64_t)0, PivotRule{},
+                  counters);
+      h.launches++;
+      const int m = n - k0 - kb;
+      if (m <= 0) continue;
+      Tf32Images img;
+      img.A = setA + c * sb;
+      img.B = setB + c * sb;
+      launch_dense_panel<float>(S, Y, n, k0, kb, n, 1, 0, 0, st, prio, img);
+      h.launches++;
+      // the rest of this outer panel's columns
+      const int TJl = (K0 + Wb - (k0 + kb) + TN - 1) / TN;
+      if (TJl <= 0) continue;
+      const int TI = (m + TM - 1) / TM;
+      int tiles = 0;
+      for (int I = 0; I < TI; I++) tiles += std::min(2 * I + 2, TJl);
+      e = launch_prio(k_tc_update<0, float>, dim3(tiles), dim3(128), A_BYTES + B_BYTES, st, prio, S, n, k0, kb, m,
+                      TJl, 0, (const uint8_t*)img.A, (const uint8_t*)img.B, (const double*)nullptr,
+                      (const double*)nullptr, h.dev_err, TcStrides{});
+      h.launches++;
+    }
+    const int base = K0 + Wb, m = n - base;
+    if (m <= 0 || e != cudaSuccess) break;
+    // the rest of the previous outer update must be done before this one
+    if (side_busy) {
+      e = cudaStreamWaitEvent(st, h.ev_side, 0);
+      side_busy = false;
+      if (e != cudaSuccess) break;
+    }
+    const int TI = (m + kWideTile - 1) / kWideTile;
+    auto wide = [&](int jmode, cudaStream_t us, int uprio) -> cudaError_t {
+      const int tasks = wide_tasks(TI, jmode);
+      if (tasks == 0) return cudaSuccess;
+      h.launches++;
+      return launch_prio(k_tc_update_wide, dim3(tasks), dim3(kWideThreads), wide_smem_bytes(), us, uprio, S, n, base,
+                         m, TI, jmode, (const uint8_t*)setA, (const uint8_t*)setB, sb, h.dev_err);
+    };
+    if (!side || TI <= 2) {
+      e = wide(0, st, prio);
+      continue;
+    }
+    e = wide(1, st, prio);
+    if (e == cudaSuccess) e = cudaEventRecord(h.ev_main, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, h.ev_main, 0);
+    if (e == cudaSuccess) e = wide(2, side, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(h.ev_side, side);
+    side_busy = e == cudaSuccess;
+  }
+  (void)B_BYTES;
+  if (side_busy && e == cudaSuccess) e = cudaStreamWaitEvent(caller, h.ev_side, 0);
+  if (st != caller && e == cudaSuccess) {
+    e = cudaEventRecord(h.ev_main, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, h.ev_main, 0);
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 }  // namespace
 
 // Kernel attributes set once (before any launch, outside stream capture).
@@ -783,8 +1129,19 @@ cudaError_t dense_tc_prepare() {
                              image_bytes(1, TM) + image_bytes(1, TN));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tc_update_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, emu_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_update_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, wide_smem_bytes());
   return e;
 }
+
+int64_t tf32_wide_set_bytes(int n) {
+  // rows of one image set: the rows below an inner step, read in whole
+  // 128-row tiles from up to 192 rows into the set
+  const int64_t rows = ((int64_t)n + kWideTile - 1) / kWideTile * kWideTile + 2 * kWideW;
+  return rows * (kgroups_of(0) * 16);
+}
+
+bool tf32_wide_applies(int n, bool structured) { return !structured && n >= 2 * kWideW; }
 
 int64_t tc_image_bytes(int n, int mode) {
   const int TI = (n + TM - 1) / TM + 1, TJ = (n + TN - 1) / TN + 1;
@@ -817,7 +1174,9 @@ cudaError_t launch_dense_ldlt_tc(Handle& h, int mode, unsigned long long* counte
   const int64_t n2 = (int64_t)n * n;
   k_to_f32<<<(int)std::min<int64_t>((n2 + 255) / 256, 152 * 32), 256, 0, st>>>(h.S, h.S32, n2);
   h.launches++;
-  if (mode == KKT_TF32)
+  if (mode == KKT_TF32 && h.tw_img && !rend)
+    e = factor_tf32_wide(h, h.S32, h.Y32, n, counters, st);
+  else if (mode == KKT_TF32)
     e = factor_tc<0, float>(h, h.S32, h.Y32, n, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
                             h.tc_scaleA, h.tc_scaleB, st);
   else

@@ -135,6 +135,8 @@ struct Handle {
   double* t_scaleB = nullptr;
   float* S32 = nullptr;       // nC * nC FP32 copy factored in the TF32/BF16 modes
   float* Y32 = nullptr;       // nC * kDenseNB FP32 panel scratch
+  uint8_t* tw_img = nullptr;  // TF32 factor of S with 256-wide outer panels: 2 parities x (4 Y + 4 L21) image sets
+  int64_t tw_set_bytes = 0;   // bytes of one image set
   uint8_t* tc_imgA = nullptr; // tensor-core operand images of one panel step
   uint8_t* tc_imgB = nullptr;
   double* tc_scaleA = nullptr;  // row scales of the emulated FP64 update
@@ -164,6 +166,8 @@ struct Handle {
   int64_t device_bytes = 0;
 
   bool factored = false;
+  bool blocks_factored = false;  // block factors and the assembled S are current (kkt_factor_blocks)
+  bool front_done = false;       // z holds a front half (kkt_solve_front) that kkt_solve_back may finish
   bool timed_factor = false;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_f0 = nullptr, ev_f1 = nullptr;
@@ -226,10 +230,13 @@ int64_t tc_image_bytes_a(int n, int mode);
 cudaError_t launch_dense_diag_panel_f64(Handle& h, int k0, int kb, int rend, unsigned long long* counters,
                                         cudaStream_t st);
 int64_t tc_image_bytes(int n, int mode);
+int64_t tf32_wide_set_bytes(int n);                 // one image set of the 256-wide TF32 factor of S
+bool tf32_wide_applies(int n, bool structured);     // whether that factor is used for S of order n
 // ---- (solve.cu) ----
 cudaError_t launch_apply_inverse(Handle& h, const double* rhs, double* out, cudaStream_t st);
 cudaError_t launch_apply_front(Handle& h, const double* rhs, cudaStream_t st);
-cudaError_t launch_apply_back(Handle& h, double* out, cudaStream_t st);
+cudaError_t launch_apply_back(Handle& h, double* out, cudaStream_t st, bool solve_s = true);
+cudaError_t launch_dense_factor_of(Handle& h, cudaStream_t st);  // (shard.cu) factor of S in the handle's mode
 cudaError_t launch_residual(Handle& h, const double* rhs, const double* x, double* rho,
                             cudaStream_t st);
 cudaError_t launch_knorm(Handle& h, cudaStream_t st);

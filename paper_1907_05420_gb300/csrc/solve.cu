@@ -472,7 +472,7 @@ cudaError_t launch_apply_front(Handle& h, const double* r, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply_back(Handle& h, double* out, cudaStream_t st) {
+cudaError_t launch_apply_back(Handle& h, double* out, cudaStream_t st, bool solve_s) {
   const int nA = h.nA, N = h.N, k = h.cpl.k, nw = h.cpl.nw;
   const int64_t pt = h.sym.panel_total;
   const int64_t nb = (int64_t)nA * N;
@@ -480,8 +480,10 @@ cudaError_t launch_apply_back(Handle& h, double* out, cudaStream_t st) {
   const std::vector<int32_t>& lptr = tail ? h.flvl_ptr : h.lvl_ptr;
   const int32_t* lsn = tail ? h.d.flvl_sn : h.d.lvl_sn;
   if (h.nC > 0) {
-    cudaError_t e = h.s_factor == 1 ? launch_dense_solve_f32(h, h.tg, h.xg, st)
-                                    : launch_dense_solve(h, h.tg, h.xg, st);
+    // without solve_s, h.xg already holds x_g (a sharded solve's broadcast)
+    cudaError_t e = !solve_s ? cudaSuccess
+                             : (h.s_factor == 1 ? launch_dense_solve_f32(h, h.tg, h.xg, st)
+                                                : launch_dense_solve(h, h.tg, h.xg, st));
     if (e != cudaSuccess) return e;
     if (k > 0 && nw > 0) {
       {
