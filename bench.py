@@ -1,14 +1,18 @@
 #!/usr/bin/env python3
-"""KKT solves/s of the Schur-complement solve of a multiperiod storage OPF
-system on GB300.
+"""KKT solves/s and p50/p99 latency of the Schur-complement solve of a
+multiperiod storage OPF system on GB300, mixed precision against FP64.
 
-Workload: the synthetic 2,383-bus grid (2,900 lines, 327 generators, 100
-storage units) over 96 periods; blocks A_i of size 10,486, coupling S of
-size 9,600 (input recipe in gen/mpopf.py).  One step = one KKT solve: the
-numeric factorization (block factors, Schur assembly, dense factor of S) plus
-the solve with FP64 iterative refinement to eta <= 1e-10.
+Default workload (the precision configuration): the synthetic 9,241-bus grid
+(16,049 lines, 1,445 generators, 400 storage units) over 168 periods; blocks
+A_i of order 41,054, coupling S of order 67,200 (input recipe in
+gen/mpopf.py).  One step = one KKT solve: the numeric factorization (block
+factors, Schur assembly, dense factor of S) plus the solve with FP64
+iterative refinement to eta <= 1e-10.  The timed path factors S in TF32 on the
+tensor cores (256-wide outer panels) and the top of every block's elimination
+tree in emulated FP64 on the tensor cores; the legs beside it are the
+FP64-accurate variants and BF16, each with its accuracy.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|tf32|bf16]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   # the CPU oracle, timed on the host
 
 Multi-GPU (torchrun, one rank per GPU): independent replicas, one system per
@@ -17,6 +21,7 @@ rank, no data-path collective; value = solves of all ranks / max rank time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -30,27 +35,39 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "KKT solves/s & p50/p99 latency, mixed-prec vs plain FP64 GPU at resid≤1e-10"
-WORKLOAD = "grid2383_n96"
-WORKLOAD_DESC = ("grid2383_n96: synthetic 2,383-bus grid, 2,900 lines, 327 generators, "
-                 "100 storage units, N=96 periods; blocks nA=10,486; S 9,600 x 9,600")
+WORKLOAD = "grid9241_n168"
 L2_FLUSH_BYTES = 256 << 20
+TIGHT_TOL = 1e-12  # the FP64 paths' level on the 9,241-bus system (eta ~ 5e-13 after one step)
+# TF32 runs at about half the BF16 tensor rate (nominal 1.1 against 2.25 PFLOP/s dense)
+TF32_RATIO = 1.1 / 2.25
+# the emulated-FP64 update issues 28 BF16 digit products per FP64 multiply-add
+EMU_PRODUCTS = 28.0
+# DRAM bytes per launch of the dominant kernel, from an ncu capture of the same
+# kernel code (profiles/); None where no capture of the current kernel exists
+TRAFFIC = {}
 
 
 def workload_desc(name):
     """The config.workload string: the named instance and its sizes."""
-    if name == WORKLOAD:
-        return WORKLOAD_DESC
     from gen import describe_workload
 
     return describe_workload(name)
+
+
+def workload_defaults(name):
+    """Tail ratio and autotuning per workload: the 9,241-bus grids take the
+    ratio the autotuner chose there (r = 1.25; each candidate costs seconds),
+    the others autotune."""
+    if name.startswith("grid9241"):
+        return {"tail_ratio": 1.25, "autotune": 0}
+    return {"tail_ratio": 0.0, "autotune": 1}
 
 
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
-            d = json.load(f)
-        return d, "measured"
+            return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
@@ -118,61 +135,6 @@ def _dist():
     return world, rank, local
 
 
-def cpu_reference_solve(prob, perm=None):
-    """One oracle solve of the workload on the host cores (the CPU baseline).
-
-    The ordering is analysis (once per pattern, like kkt_analyze on the GPU
-    side) and is computed outside the timed region when `perm` is None.
-    """
-    import oracle
-
-    if perm is None:
-        perm = oracle.min_degree(prob.nA, prob.a_rowptr, prob.a_col, prob.nP)
-    t0 = time.perf_counter()
-    out = oracle.kkt_solve(prob, perm)
-    dt = time.perf_counter() - t0
-    return out, dt
-
-
-# CPU work of one bounded oracle sample, in flops (the oracle runs the full
-# 2,383-bus, 96-period solve, 3e11 flops, in about 14 s on 16 Grace cores)
-CPU_SAMPLE_FLOPS = 6e11
-
-
-def cpu_baseline_sample(workload, prob, block_flops):
-    """The oracle timed on a bounded sample of the workload.
-
-    Returns (line fields, oracle output of the full system or None).  A
-    workload whose estimated oracle work, N * block_flops + nC^3 / 3, exceeds
-    CPU_SAMPLE_FLOPS is sampled by its first N' periods (the largest N' within
-    that work) and the rate scaled to the full system by the ratio of the two
-    estimates."""
-    import dataclasses
-
-    import oracle
-    from gen import CONFIGS, make_problem
-
-    ns = prob.nC // prob.N if prob.N else 0
-    est = lambda n: n * block_flops + (n * ns) ** 3 / 3.0  # noqa: E731
-    full = est(prob.N)
-    fields = {"unit": "solves/s", "cores": oracle.max_threads(), "host_cores": host_cores(), "kind": "oracle"}
-    if full <= CPU_SAMPLE_FLOPS or workload not in CONFIGS:
-        out, dt = cpu_reference_solve(prob)
-        fields.update(value=1.0 / dt, sample=f"1 full solve of {workload} (FP64 oracle, OpenMP; "
-                                             "ordering computed once, untimed)")
-        return fields, out
-    fit = [k for k in range(1, prob.N + 1) if est(k) <= CPU_SAMPLE_FLOPS]
-    n = fit[-1] if fit else 1
-    sub = make_problem(dataclasses.replace(CONFIGS[workload], n_per=n, name=f"{workload}_first{n}"))
-    _, dt = cpu_reference_solve(sub)
-    scale = full / est(n)
-    fields.update(value=1.0 / (dt * scale),
-                  sample=f"1 solve of {workload} over its first {n} of {prob.N} periods (FP64 oracle, "
-                         f"OpenMP; {dt:.1f} s), scaled to the full system by its estimated work "
-                         f"N*block_flops + nC^3/3 (x{scale:.1f})")
-    return fields, None
-
-
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -180,8 +142,120 @@ def host_cores():
         return os.cpu_count()
 
 
+# ---------------------------------------------------------------- CPU baseline
+
+def block_flops_host(prob):
+    """Flops of one block factor, sum_j c_j (c_j + 3) over the column counts of
+    the ordering kkt_analyze chooses (the host-only symbolic library; no GPU).
+    It sizes the work of a system for scaling a sampled oracle time."""
+    import numpy as np
+
+    from paper_1907_05420_gb300 import build as lib_build
+
+    L = ctypes.CDLL(lib_build.build_symbolic())
+    L.kkt_symbolic_create.restype = ctypes.c_void_p
+    L.kkt_symbolic_get.restype = ctypes.c_int64
+    L.kkt_symbolic_get.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p]
+    L.kkt_symbolic_destroy.argtypes = [ctypes.c_void_p]
+    rp = np.ascontiguousarray(prob.a_rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(prob.a_col, dtype=np.int32)
+    hint = np.ascontiguousarray(np.asarray(prob.a_vals).reshape(prob.N, -1)[0], dtype=np.float64)
+    zero = np.zeros(2, dtype=np.int32)
+    p = ctypes.c_void_p
+    h = L.kkt_symbolic_create(ctypes.c_int32(prob.nA), ctypes.c_int32(prob.nP), p(rp.ctypes.data),
+                              p(col.ctypes.data), p(hint.ctypes.data), ctypes.c_int32(1), ctypes.c_int32(0),
+                              p(zero.ctypes.data), p(zero.ctypes.data), p(zero.ctypes.data), ctypes.c_int32(0))
+    if not h:
+        raise RuntimeError("symbolic analysis failed")
+    try:
+        n = L.kkt_symbolic_get(h, b"colcount", None)
+        cc = np.zeros(n, dtype=np.int64)
+        L.kkt_symbolic_get(h, b"colcount", p(cc.ctypes.data))
+    finally:
+        L.kkt_symbolic_destroy(h)
+    cc = cc.astype(np.float64)
+    return float(np.sum(cc * (cc + 3.0)))
+
+
+def _est(N, nC, block_flops):
+    """Estimated oracle work of a system: its block factors and the dense factor of S."""
+    return N * block_flops + nC ** 3 / 3.0
+
+
+# oracle work per sample, in estimated flops (the oracle runs the 2,383-bus,
+# 96-period solve, about 3e11 flops, in about 14 s on 16 Grace cores)
+CPU_SAMPLE_FLOPS = 6e11
+# the largest grid whose blocks the oracle's plain minimum-degree ordering
+# handles within seconds (the 9,241-bus blocks do not finish in minutes)
+ORACLE_MAX_BUS = 3000
+
+
+def cpu_sample_plan(workload, prob, block_flops, budget=None):
+    """(sample problem, its description, scale to the full workload) for a
+    bounded oracle run.  The full workload if its estimated work fits the
+    budget; else its first N' periods; else, for grids beyond the oracle's
+    ordering, the same generator recipe on the 2,383-bus grid over N' periods,
+    scaled by the estimated work of the two systems."""
+    import dataclasses
+
+    from gen import CONFIGS, make_problem
+    from gen.workloads import workload_spec
+
+    budget = CPU_SAMPLE_FLOPS if budget is None else budget
+    ns = prob.nC // prob.N if prob.N else 0
+    full = _est(prob.N, prob.nC, block_flops)
+    if full <= budget:
+        return prob, f"1 full solve of {workload}", 1.0
+    kind, spec, _ = workload_spec(workload)
+    if kind == "mpopf" and spec.n_bus <= ORACLE_MAX_BUS:
+        fit = [k for k in range(1, prob.N + 1) if _est(k, k * ns, block_flops) <= budget]
+        n = fit[-1] if fit else 1
+        sub = make_problem(dataclasses.replace(spec, n_per=n, name=f"{workload}_first{n}"))
+        scale = full / _est(n, n * ns, block_flops)
+        return sub, f"1 solve of {workload} over its first {n} of {prob.N} periods", scale
+    base = CONFIGS["grid2383_n96"]
+    one = make_problem(dataclasses.replace(base, n_per=1, name="grid2383_n1"))
+    bf = block_flops_host(one)
+    fit = [k for k in range(1, base.n_per + 1) if _est(k, k * base.n_stor, bf) <= budget]
+    n = fit[-1] if fit else 1
+    sub = make_problem(dataclasses.replace(base, n_per=n, name=f"grid2383_n{n}"))
+    scale = full / _est(n, n * base.n_stor, bf)
+    return sub, (f"1 solve of the same recipe on the 2,383-bus grid over {n} periods (the oracle's "
+                 f"minimum-degree ordering of one {workload} block does not finish in minutes)"), scale
+
+
+def cpu_reference_solve(prob, perm=None):
+    """One oracle solve on the host cores; the ordering is analysis (once per
+    pattern, like kkt_analyze) and is computed outside the timed region."""
+    import oracle
+
+    if perm is None:
+        perm = oracle.min_degree(prob.nA, prob.a_rowptr, prob.a_col, prob.nP)
+    t0 = time.perf_counter()
+    out = oracle.kkt_solve(prob, perm)
+    return out, time.perf_counter() - t0
+
+
+def cpu_baseline_sample(workload, prob, block_flops, budget=None):
+    """The oracle timed on a bounded sample of the workload: (line fields,
+    oracle output of the full system or None)."""
+    import oracle
+
+    sub, desc, scale = cpu_sample_plan(workload, prob, block_flops, budget)
+    out, dt = cpu_reference_solve(sub)
+    fields = {"unit": "solves/s", "cores": oracle.max_threads(), "host_cores": host_cores(), "kind": "oracle",
+              "value": 1.0 / (dt * scale)}
+    if scale == 1.0:
+        fields["sample"] = f"{desc} (FP64 oracle, OpenMP; ordering computed once, untimed; {dt:.1f} s)"
+        return fields, out
+    fields["sample"] = (f"{desc} (FP64 oracle, OpenMP; ordering untimed; {dt:.1f} s), scaled to the full "
+                        f"system by the estimated work N*block_flops + nC^3/3 (x{scale:.1f})")
+    return fields, None
+
+
 def run_reference(args):
-    """--impl reference: the CPU oracle, timed as it stands on the host cores."""
+    """--impl reference: the CPU oracle, timed as it stands on the host cores,
+    one bounded sample of the workload per step, rate scaled to the workload."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
@@ -189,17 +263,22 @@ def run_reference(args):
     from gen import CONFIGS, build_workload, make_problem
 
     prob = build_workload(args.workload)
+    bf = block_flops_host(prob)
+    sub, desc, scale = cpu_sample_plan(args.workload, prob, bf, args.ref_sample_flops)
     small = make_problem(CONFIGS["grid30_n24"])
     for _ in range(args.warmup):  # warm-up on the small instance (loads the library, threads)
         oracle.kkt_solve(small)
-    perm = oracle.min_degree(prob.nA, prob.a_rowptr, prob.a_col, prob.nP)  # analysis, untimed
+    perm = oracle.min_degree(sub.nA, sub.a_rowptr, sub.a_col, sub.nP)  # analysis, untimed
     times = []
     for _ in range(args.steps):
-        _, dt = cpu_reference_solve(prob, perm)
-        times.append(dt)
+        _, dt = cpu_reference_solve(sub, perm)
+        times.append(dt * scale)
     total = sum(times)
     value = args.steps / total
     threads = oracle.max_threads()
+    sample = (f"{args.steps} x {desc}" + (f", each scaled by the estimated work (x{scale:.1f})" if scale != 1.0
+                                          else "") + f"; ordering computed once untimed (warm-up: {args.warmup} "
+              "solves of grid30_n24)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -209,14 +288,14 @@ def run_reference(args):
         "latency_ms": {"p50": 1e3 * statistics.median(times),
                        "p99": 1e3 * max(times) if len(times) < 100 else
                        1e3 * sorted(times)[int(0.99 * len(times))]},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{args.steps} full solves of {args.workload}, ordering computed once "
-                                   f"untimed (warm-up: {args.warmup} solves of grid30_n24)"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
+
+# ------------------------------------------------------------ batching, serving
 
 def _mix_problems(count, prec):
     import numpy as np
@@ -236,7 +315,6 @@ def _mix_problems(count, prec):
 
 def run_batch(args):
     """The 64-instance size mix: one batched call against 64 sequential solves."""
-    import numpy as np
     import torch
 
     import oracle
@@ -289,7 +367,7 @@ def run_serve(args):
     out = {"metric": "KKT solves/s and p50/p99 latency under a Poisson request stream", "unit": "solves/s",
            "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
            "config": {"workload": f"serve: {args.serve_pool} resident patterns from the size mix; "
-                                  "Poisson arrivals; every request carries fresh values",
+                                  "Poisson arrivals",
                       "slots": args.serve_slots, "seconds_per_rate": args.serve_seconds,
                       "backlog": args.serve_backlog or 4 * args.serve_slots}}
     for prec in args.batch_precs.split(","):
@@ -299,10 +377,7 @@ def run_serve(args):
         rng = np.random.default_rng(4242)
         res = {}
         backlog = args.serve_backlog or 4 * args.serve_slots
-        for rate in [float(r) for r in args.rates.split(",")]:
-            # Poisson arrivals for 1 s of warm-up plus the measured window; a
-            # request that finds `backlog` requests outstanding is shed (load
-            # shedding keeps the queue, and so the drain after the window, bounded)
+        for rate in [float(q) for q in args.rates.split(",")]:
             lats, outstanding = [], {}
             shed = offered = 0
             t0 = time.perf_counter()
@@ -314,8 +389,7 @@ def run_serve(args):
                     got = srv.wait(rid) if block else srv.poll(rid)
                     if got is None:
                         continue
-                    in_window = outstanding.pop(rid)
-                    if in_window:
+                    if outstanding.pop(rid):
                         lats.append(got[1])
 
             while time.perf_counter() < t_end:
@@ -330,10 +404,10 @@ def run_serve(args):
                 if len(outstanding) >= backlog:
                     shed += in_window
                     continue
-                k = int(rng.integers(0, len(probs)))
-                a, b, c, r = vals[k]
+                kq = int(rng.integers(0, len(probs)))
+                a, b, c, r = vals[kq]
                 x = torch.empty_like(r)
-                outstanding[srv.submit(hs[k], a, b, c, r, x)] = in_window
+                outstanding[srv.submit(hs[kq], a, b, c, r, x)] = in_window
             reap(True)
             t_done = time.perf_counter()
             n = len(lats)
@@ -350,6 +424,16 @@ def run_serve(args):
     return 0
 
 
+# ------------------------------------------------------------------- main path
+
+def parse_leg(mode):
+    """'prec[+tcg|+band][@tol]' -> (prec, options, refine_tol or None)."""
+    head, _, tol = mode.partition("@")
+    prec, _, extra = head.partition("+")
+    opts = {"reduced_contraction": int(extra == "tcg"), "structured_s": int(extra == "band")}
+    return prec, opts, (float(tol) if tol else None)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -359,22 +443,28 @@ def main():
     ap.add_argument("--prec", default="tf32", choices=["fp64", "tf32", "bf16", "f64emu"],
                     help="arithmetic of the dense factor of S on the timed path (default: the "
                          "mixed path, TF32 tensor cores with FP64 refinement)")
-    ap.add_argument("--legs", default="fp64,f64emu,bf16,tf32+tcg,fp64+band,tf32+band",
-                    help="other precision modes measured beside the timed path ('' for none)")
-    ap.add_argument("--leg-steps", type=int, default=4)
+    ap.add_argument("--legs", default=f"fp64+band,f64emu,tf32@{TIGHT_TOL:g},bf16",
+                    help="other modes measured beside the timed path ('' for none): prec[+tcg|+band][@tol]")
+    ap.add_argument("--leg-steps", type=int, default=2)
+    ap.add_argument("--leg-warmup", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="steps of the end-to-end leg through host buffers (at most --steps)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample-flops", type=float, default=6e10,
+                    help="estimated oracle work of one reference-arm step")
     ap.add_argument("--batch-precs", default="tf32,fp64")
     ap.add_argument("--batch-streams", type=int, default=8)
     ap.add_argument("--serve-pool", type=int, default=32)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--rates", default="50,100,200,500,1000,2000")
+    ap.add_argument("--resolve-frac", type=float, default=0.2)
     ap.add_argument("--serve-backlog", type=int, default=0,
                     help="requests outstanding before new arrivals are shed (default 4 x slots)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true",
-                    help="skip the dense-tail autotuning at analysis (it times a few factorizations)")
+    ap.add_argument("--autotune", type=int, default=-1,
+                    help="dense-tail autotuning at analysis: 1 on, 0 off, -1 the workload's default")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -382,7 +472,24 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    return run_single(args)
 
+
+def _accuracy(B, h, prob, r, x, stream, torch):
+    """eta (device), ||r - Kx||_2 / ||r||_2 from the handle's residual kernel,
+    and the solution on the host."""
+    import numpy as np
+
+    rho = torch.empty_like(x)
+    B.kkt_residual(h, r, x, rho, stream)
+    torch.cuda.synchronize()
+    rh, xh = rho.cpu().numpy(), x.cpu().numpy()
+    info = B.kkt_get_info(h)
+    return {"eta": info["rel_residual"], "resid2": float(np.linalg.norm(rh) / np.linalg.norm(prob.rhs)),
+            "refine_steps": info["refine_steps"], "fell_back_fp64": info["fell_back_fp64"]}, xh
+
+
+def run_single(args):
     import numpy as np
     import torch
 
@@ -403,34 +510,40 @@ def main():
 
             dist.barrier()
 
+    def max_over_ranks(v):
+        if world > 1:
+            import torch.distributed as dist
+
+            t = torch.tensor([v], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return v
+
     prob = build_workload(args.workload)
+    wd = workload_defaults(args.workload)
+    autotune = wd["autotune"] if args.autotune < 0 else args.autotune
     stream = torch.cuda.current_stream()
-    a = torch.from_numpy(np.ascontiguousarray(prob.a_vals)).to(dev)
-    b = torch.from_numpy(np.ascontiguousarray(prob.b_vals)).to(dev)
-    c = torch.from_numpy(np.ascontiguousarray(prob.c_vals)).to(dev)
-    r = torch.from_numpy(np.ascontiguousarray(prob.rhs)).to(dev)
+    up = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(dev)  # noqa: E731
+    a, b, c, r = up(prob.a_vals), up(prob.b_vals), up(prob.c_vals), up(prob.rhs)
     x = torch.empty_like(r)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def time_mode(mode, steps, warmup, sample_clocks=False):
-        """Factor + refined solve of the workload, `steps` timed repetitions.
+    def analyze(mode, time_kernels=0):
+        prec, opts, tol = parse_leg(mode)
+        kw = dict(opts, autotune=autotune, early_solve=1, time_kernels=time_kernels,
+                  tail_ratio=0.0 if autotune else wd["tail_ratio"])
+        if tol is not None:
+            kw["refine_tol"] = tol
+        return B.kkt_analyze(prob, B.kkt_default_options(prec, **kw))
 
-        mode: a precision name; a '+tcg' suffix also runs the Schur contraction on
-        the tensor cores in that precision, '+band' limits the factor of S to its
-        row envelope (the structured Schur factor)."""
-        prec, _, extra = mode.partition("+")
-        h = B.kkt_analyze(prob, B.kkt_default_options(prec, reduced_contraction=int(extra == "tcg"),
-                                                     structured_s=int(extra == "band"),
-                                                     autotune=0 if args.no_autotune else 1,
-                                                     early_solve=1))
-        info0 = B.kkt_get_info(h)
-
-        def step_device():
+    def time_mode(h, steps, warmup, sample_clocks=False, kernel_stats=False):
+        """Factor + refined solve, `steps` timed repetitions with CUDA events."""
+        def step():
             B.kkt_factor(h, a, b, c, stream)
             B.kkt_solve(h, r, x, 1, stream, allow_not_converged=True)
 
         for _ in range(warmup):
-            step_device()
+            step()
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -438,17 +551,17 @@ def main():
         clocks = ClockSampler(local) if sample_clocks else None
         if clocks:
             clocks.start()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         phases = {"a_block_factor": [], "b_schur_assembly": [], "c_dense_factor": [], "d_solve": []}
         etas, steps_ir, fallback = [], [], []
+        kstats = {}
         t_wall0 = time.perf_counter()
         for i in range(steps):
             flush.zero_()
             ev[i][0].record(stream)
-            step_device()
+            step()
             ev[i][1].record(stream)
-            inf = B.kkt_get_info(h)
+            inf = B.kkt_get_info(h)  # synchronizes; the per-step device figures of this step
             phases["a_block_factor"].append(inf["ms_block_factor"])
             phases["b_schur_assembly"].append(inf["ms_schur_assembly"])
             phases["c_dense_factor"].append(inf["ms_dense_factor"])
@@ -456,6 +569,11 @@ def main():
             etas.append(inf["rel_residual"])
             steps_ir.append(inf["refine_steps"])
             fallback.append(inf["fell_back_fp64"])
+            if kernel_stats:
+                for name, st in B.kkt_kernel_stats(h).items():
+                    acc = kstats.setdefault(name, {"launches": 0, "ms_total": 0.0, "flops": 0.0})
+                    for kk in acc:
+                        acc[kk] += st[kk]
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -463,114 +581,147 @@ def main():
         clk = clocks.stop() if clocks else None
         info = B.kkt_get_info(h)
         step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-        total_s = sum(step_ms) / 1e3
-        if world > 1:
-            import torch.distributed as dist
+        return {"info": info, "step_ms": step_ms, "total_s": max_over_ranks(sum(step_ms) / 1e3),
+                "phases": phases, "etas": etas, "steps_ir": steps_ir, "fallback": fallback, "clocks": clk,
+                "launches": info["n_launches"] - launches0, "wall_s": t_wall, "kstats": kstats}
 
-            t = torch.tensor([total_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_s = float(t.item())
-        return {"h": h, "info0": info0, "info": info, "step_ms": step_ms, "total_s": total_s,
-                "phases": phases, "etas": etas, "steps_ir": steps_ir, "fallback": fallback,
-                "clocks": clk, "launches": info["n_launches"] - launches0, "wall_s": t_wall,
-                "x": x.cpu().numpy()}
-
-    main_run = time_mode(args.prec, args.steps, args.warmup, sample_clocks=True)
-    h = main_run["h"]
-    info0, info = main_run["info0"], main_run["info"]
-    step_ms, phases = main_run["step_ms"], main_run["phases"]
-    etas, steps_ir = main_run["etas"], main_run["steps_ir"]
-    clk, launches, t_wall = main_run["clocks"], main_run["launches"], main_run["wall_s"]
+    # ---- the timed path
+    h = analyze(args.prec, time_kernels=1)
+    info0 = B.kkt_get_info(h)
+    main_run = time_mode(h, args.steps, args.warmup, sample_clocks=True, kernel_stats=True)
     value = world * args.steps / main_run["total_s"]
-    x_gpu = main_run["x"]
+    step_ms, phases = main_run["step_ms"], main_run["phases"]
+    acc_main, x_main = _accuracy(B, h, prob, r, x, stream, torch)
+    acc_main.update(eta_max_timed=max(main_run["etas"]), refine_steps_mean=statistics.mean(main_run["steps_ir"]))
 
-    # end to end through the public API with host buffers: H2D of the step's
-    # inputs and D2H of the solution inside the timed region
+    # ---- end to end through the public API with host buffers: H2D of the
+    # step's inputs and D2H of the solution inside the timed region
     e2e = None
     if not args.no_e2e:
+        ksteps = max(1, min(args.steps, args.e2e_steps))
         pin = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).pin_memory()  # noqa: E731
         ha, hb, hc, hr = pin(prob.a_vals), pin(prob.b_vals), pin(prob.c_vals), pin(prob.rhs)
         hx = torch.empty_like(hr).pin_memory()
-        for _ in range(max(1, args.warmup)):
-            B.kkt_factor(h, ha, hb, hc, stream)
-            B.kkt_solve(h, hr, hx, 1, stream, allow_not_converged=True)
+        B.kkt_factor(h, ha, hb, hc, stream)
+        B.kkt_solve(h, hr, hx, 1, stream, allow_not_converged=True)
         torch.cuda.synchronize()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(ksteps):
             flush.zero_()
             B.kkt_factor(h, ha, hb, hc, stream)
             B.kkt_solve(h, hr, hx, 1, stream, allow_not_converged=True)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        e2e_s = e0.elapsed_time(e1) / 1e3
-        if world > 1:
-            import torch.distributed as dist
-
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3)
         h2d = sum(t.numel() * t.element_size() for t in (ha, hb, hc, hr))
-        e2e = {"value": world * args.steps / e2e_s, "unit": "solves/s",
+        e2e = {"value": world * ksteps / e2e_s, "unit": "solves/s", "steps": ksteps,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hx.numel() * 8)}
+        del ha, hb, hc, hr, hx
+    B.kkt_destroy(h)  # every leg below needs the device memory
 
-    legs = {}
+    # ---- the other modes, one handle at a time
+    legs, xs = {}, {}
     for leg in [m for m in args.legs.split(",") if m and m != args.prec]:
-        lr = time_mode(leg, args.leg_steps, 2)
-        B.kkt_destroy(lr["h"])
+        hl = analyze(leg)
+        lr = time_mode(hl, args.leg_steps, args.leg_warmup)
+        acc, xs[leg] = _accuracy(B, hl, prob, r, x, stream, torch)
+        B.kkt_destroy(hl)
         legs[leg] = {"value": world * args.leg_steps / lr["total_s"], "unit": "solves/s",
                      "ms_per_step": statistics.mean(lr["step_ms"]),
                      "latency_ms": {"p50": float(np.percentile(lr["step_ms"], 50)),
                                     "p99": float(np.percentile(lr["step_ms"], 99))},
-                     "residual_eta_max": max(lr["etas"]), "refine_steps": lr["steps_ir"][-1],
-                     "fell_back_fp64": lr["fallback"][-1],
-                     "phases_ms": {kk: statistics.mean(v) for kk, v in lr["phases"].items()},
-                     "_x": lr["x"]}
+                     "accuracy": acc, "phases_ms": {kk: statistics.mean(v) for kk, v in lr["phases"].items()}}
 
-    # roofline of the dominant phase (algorithmic work / measured phase time)
+    # ---- forward errors against the FP64-accurate solutions of this run
+    ref_leg = next((m for m in ("fp64+band", "fp64", "f64emu") if m in xs), None)
+    err = lambda xv, xr: float(np.max(np.abs(xv - xr)) / np.max(np.abs(xr)))  # noqa: E731
+    if ref_leg:
+        acc_main["fwd_err_vs_" + ref_leg] = err(x_main, xs[ref_leg])
+        for leg, xv in xs.items():
+            if leg != ref_leg:
+                legs[leg]["accuracy"]["fwd_err_vs_" + ref_leg] = err(xv, xs[ref_leg])
+
+    # ---- roofline of the dominant kernel (per-launch CUDA events inside the timed region)
     peaks, peak_kind = _peaks()
     fp64_gflops = B.kkt_measure_fp64_peak()
+    ks = main_run["kstats"]
+    timed = {kk: v for kk, v in ks.items() if v["launches"] > 0}
+    dom = max(timed, key=lambda kk: timed[kk]["ms_total"]) if timed else None
+    roofline = None
+    if dom:
+        st = timed[dom]
+        sec = st["ms_total"] / 1e3
+        sustained = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        if dom == "k_tc_update_emu":
+            bound, unit, peak = "tensor", "TFLOP/s", sustained
+            achieved = EMU_PRODUCTS * st["flops"] / sec / 1e12
+            src = (f"bf16_tflops_sustained of {peak_kind} peaks; achieved counts the {EMU_PRODUCTS:.0f} BF16 "
+                   "digit products of every FP64 multiply-add")
+        elif dom in ("k_tc_update_wide", "k_tc_update"):
+            bound, unit, peak = "tensor", "TFLOP/s", sustained * TF32_RATIO
+            achieved = st["flops"] / sec / 1e12
+            src = f"bf16_tflops_sustained of {peak_kind} peaks x {TF32_RATIO:.3f} (TF32 / BF16 nominal)"
+        else:
+            bound, unit, peak = "alu", "TFLOP/s", fp64_gflops / 1e3
+            achieved = st["flops"] / sec / 1e12
+            src = "FP64 FMA throughput measured by kkt_measure_fp64_peak in this run"
+        roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                    "traffic": TRAFFIC.get((args.workload, dom)), "kernel": dom,
+                    "launches_per_step": st["launches"] / args.steps,
+                    "ms_per_launch": st["ms_total"] / st["launches"],
+                    "flops_per_launch": st["flops"] / st["launches"], "peak_source": src}
+    kernels = {}
+    step_total = sum(step_ms)
+    for kk, v in timed.items():
+        kernels[kk] = {"launches_per_step": v["launches"] / args.steps, "ms_per_step": v["ms_total"] / args.steps,
+                       "share_of_step": v["ms_total"] / step_total if step_total else None,
+                       "tflops": v["flops"] / (v["ms_total"] / 1e3) / 1e12 if v["flops"] else None}
+
+    # ---- phases against their bounds (algorithmic work per solve)
+    info = main_run["info"]
     N, nA, nC = prob.N, prob.nA, prob.nC
     k, nw = info["k_coupling_rows"], info["w_rows"]
     mean = {kk: statistics.mean(v) for kk, v in phases.items()}
-    ir = statistics.mean(steps_ir)
+    ir = acc_main["refine_steps_mean"]
+    # algorithmic work per solve (2 flops per multiply-add): (a) reads A and
+    # writes L and D once; (b) the contraction W^T D^-1 W, its symmetric half;
+    # (c) the dense LDL^T of S, n^3/3 multiply-adds; (d) each application reads
+    # the block factors twice and S once
     work = {
-        "a_block_factor": {"flops": N * info["factor_flops"],
-                           "bytes": 8.0 * N * (prob.nnzA + info["nnz_l"] + nA)},
-        "b_schur_assembly": {"flops": N * nw * k * k, "bytes": 8.0 * N * 2 * nw * k},
-        "c_dense_factor": {"flops": nC ** 3 / 3.0, "bytes": 8.0 * nC * nC},
-        "d_solve": {"flops": 0.0,
-                    "bytes": (1 + ir) * (8.0 * N * (2 * info["panel_doubles"] + 2 * nA) + 8.0 * nC * nC)},
+        "a_block_factor": ("hbm", 8.0 * N * (prob.nnzA + info["nnz_l"] + nA)),
+        "b_schur_assembly": ("tensor", float(N) * nw * k * k),
+        "c_dense_factor": ("tensor", 2.0 * nC ** 3 / 3.0),
+        "d_solve": ("hbm", (1 + ir) * (8.0 * N * (2 * info["panel_doubles"] + 2 * nA) + 8.0 * nC * nC)),
     }
-    dom = max(mean, key=mean.get)
-    t_dom = mean[dom] / 1e3
-    if dom == "d_solve":
-        bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
-        achieved = work[dom]["bytes"] / t_dom / 1e9
-        peak_src = f"hbm_gbs of {peak_kind} peaks"
-    elif dom == "c_dense_factor" and args.prec != "fp64":
-        # TF32 runs at half the BF16 rate (nominal 1.1 vs 2.25 PFLOP/s dense); the
-        # emulated FP64 update issues 28 BF16 digit products per FP64 product
-        ratio = {"tf32": 0.5, "bf16": 1.0, "f64emu": 1.0}[args.prec]
-        mult = 28.0 if args.prec == "f64emu" else 1.0
-        bound, peak, unit = "tensor", peaks["bf16_tflops"] * ratio, "TFLOP/s"
-        achieved = mult * work[dom]["flops"] / t_dom / 1e12
-        peak_src = (f"bf16_tflops of {peak_kind} peaks x {ratio} ({args.prec})" +
-                    (", achieved counts the 28 digit products" if mult > 1 else ""))
-    else:
-        bound, peak, unit = "alu", fp64_gflops / 1e3, "TFLOP/s"
-        achieved = work[dom]["flops"] / t_dom / 1e12
-        peak_src = "FP64 FMA throughput measured by kkt_measure_fp64_peak in this run"
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "phase": dom, "peak_source": peak_src}
+    sustained = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    s_peak = sustained * ({"tf32": TF32_RATIO, "bf16": 1.0}.get(args.prec, 1.0))
     phase_report = {}
     for kk, ms in mean.items():
         s = ms / 1e3
-        phase_report[kk] = {"ms": ms, "gflops": work[kk]["flops"] / s / 1e9 if s > 0 else None,
-                            "gbs": work[kk]["bytes"] / s / 1e9 if s > 0 else None,
-                            "hbm_frac": work[kk]["bytes"] / s / 1e9 / peaks["hbm_gbs"] if s > 0 else None}
+        kind, w = work[kk]
+        if s <= 0:
+            phase_report[kk] = {"ms": ms}
+        elif kind == "hbm":
+            phase_report[kk] = {"ms": ms, "bound": "hbm", "bytes": w, "gbs": w / s / 1e9,
+                                "frac": w / s / 1e9 / peaks["hbm_gbs"]}
+        else:
+            phase_report[kk] = {"ms": ms, "bound": "tensor", "flops": w, "tflops": w / s / 1e12,
+                                "frac": w / s / 1e12 / s_peak}
+
+    mixed_vs_fp64 = None
+    if "fp64+band" in legs:
+        fp = legs["fp64+band"]
+        mixed_vs_fp64 = {"fp64_path": "fp64+band (FP64 on the CUDA cores, FP64 tails, banded factor of S)",
+                         "fp64_value": fp["value"], "fp64_eta": fp["accuracy"]["eta"],
+                         "at_1e-10": {"mixed": value, "ratio": value / fp["value"]}}
+        tight = f"tf32@{TIGHT_TOL:g}"
+        if tight in legs:
+            mixed_vs_fp64[f"at_{TIGHT_TOL:g}"] = {
+                "mixed": legs[tight]["value"], "ratio": legs[tight]["value"] / fp["value"],
+                "mixed_eta": legs[tight]["accuracy"]["eta"]}
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
@@ -579,29 +730,26 @@ def main():
         "dtype": {"fp64": "f64", "tf32": "f64+tf32", "bf16": "f64+bf16", "f64emu": "f64+bf16x7"}[args.prec],
         "data": "synthetic",
         "config": {"workload": workload_desc(args.workload), "precision": args.prec,
-                   "l2": "256 MB buffer written before every timed step",
+                   "l2": "256 MB buffer written before every timed step (inputs also exceed L2)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-        "residual_eta_max": max(etas), "refine_steps_mean": ir,
-        "roofline": roofline, "phases": phase_report, "fp64_peak_gflops_measured": fp64_gflops,
-        "e2e": e2e, "clocks": clk, "gpu_launches": int(launches), "wall_s_timed": t_wall,
-        "analyze_ms": info0["ms_analyze"], "refine_steps_last": steps_ir[-1],
+        "accuracy": acc_main, "mixed_vs_fp64": mixed_vs_fp64,
+        "roofline": roofline, "kernels": kernels, "phases": phase_report,
+        "fp64_peak_gflops_measured": fp64_gflops,
+        "e2e": e2e, "clocks": main_run["clocks"], "gpu_launches": int(main_run["launches"]),
+        "wall_s_timed": main_run["wall_s"], "analyze_ms": info0["ms_analyze"],
         "dense_tail": {"cols": info0["dense_tail_cols"], "ratio": info0["tail_ratio"],
                        "augmented": bool(info0["tail_augmented"]),
                        "autotune_candidates": info0["autotune_candidates"]},
-        "fell_back_fp64": main_run["fallback"][-1], "other_precisions": legs,
+        "device_bytes": info0["device_bytes"], "other_precisions": legs,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], out = cpu_baseline_sample(args.workload, prob, info0["factor_flops"])
         if out is not None:
             xo = out["x"]
-            err = lambda xv: float(np.max(np.abs(xv - xo)) / np.max(np.abs(xo)))  # noqa: E731
-            line["error_vs_oracle"] = err(x_gpu)
-            for leg in legs.values():
-                leg["error_vs_oracle"] = err(leg["_x"])
-    for leg in legs.values():
-        leg.pop("_x", None)
-    B.kkt_destroy(h)
+            acc_main["fwd_err_vs_oracle"] = err(x_main, xo)
+            for leg, xv in xs.items():
+                legs[leg]["accuracy"]["fwd_err_vs_oracle"] = err(xv, xo)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -136,7 +136,9 @@ typedef struct {
                            stream of the handle, while the dense factor of S still runs.  The
                            right-hand side is then read on that stream: a right-hand side on the
                            device must be complete when kkt_factor is called.  Default 0. */
-  int32_t reserved;
+  int32_t time_kernels; /* record CUDA events around every launch of the dominant kernel families
+                           (also inside the factor's CUDA graph) and keep each launch's algorithmic
+                           work, for kkt_kernel_stats.  Default 0. */
   double tail_ratio;    /* the cost ratio r of the dense tail (above); 0, the default, takes 1.5 or,
                            with autotune, the autotuner's choice.  Negative values are rejected. */
 } kkt_options;
@@ -405,6 +407,25 @@ kkt_status kkt_server_poll(kkt_server* s, int64_t request_id, int32_t wait, kkt_
                            double* latency_ms);
 /* Drains the queue, joins the workers and frees the streams. */
 kkt_status kkt_server_destroy(kkt_server* s);
+
+/* ---- per-kernel device times (with kkt_options.time_kernels) ----
+ * Families: 0 the emulated-FP64 trailing update (k_tc_update_emu: dense tails
+ * of the block factors, and S in KKT_F64_EMULATED or a fallback), 1 the TF32
+ * update of S with 256-wide outer panels (k_tc_update_wide), 2 the 64-wide
+ * TF32/BF16 update (k_tc_update), 3 the FP64 dense update on the CUDA cores
+ * (k_dense_update: S in KKT_FP64, the FP64 tails), 4 the supernodal updates of
+ * the block factor (k_factor_update), 5 the dense diagonal blocks of the
+ * blocked factors (k_dense_diag_t).  flops: the algorithmic FP64-equivalent
+ * flops of the launches (2 per multiply-add on the entries of the lower
+ * triangle they update; 0 where not counted). */
+typedef struct {
+  int64_t launches;     /* launches of the family in the handle's last factor (and fallback) */
+  double ms_total;      /* sum of their device durations (CUDA events on their streams) */
+  double ms_max;        /* the longest one */
+  double flops;         /* their algorithmic flops */
+} kkt_kernel_stat;
+/* Statistics of family `family` (0..5); synchronizes the handle. */
+kkt_status kkt_kernel_stats(kkt_handle* h, int32_t family, kkt_kernel_stat* out);
 
 /* Measured FP64 FMA throughput of the current device in GFLOP/s (8
  * independent FMA chains per thread, best of 5 launches).  The FP64-bound

@@ -42,7 +42,7 @@ class kkt_options(C.Structure):
                 ("pivot_eps", C.c_double), ("use_graphs", C.c_int32),
                 ("fp64_fallback", C.c_int32), ("reduced_contraction", C.c_int32),
                 ("structured_s", C.c_int32), ("dense_tail", C.c_int32), ("autotune", C.c_int32),
-                ("early_solve", C.c_int32), ("reserved", C.c_int32), ("tail_ratio", C.c_double)]
+                ("early_solve", C.c_int32), ("time_kernels", C.c_int32), ("tail_ratio", C.c_double)]
 
 
 class kkt_info(C.Structure):
@@ -80,7 +80,14 @@ EXPORTS = ["kkt_default_options", "kkt_analyze", "kkt_factor", "kkt_solve", "kkt
            "kkt_server_poll", "kkt_server_destroy", "kkt_default_inertia_options", "kkt_factor_inertia",
            "kkt_factor_blocks", "kkt_schur_matrix", "kkt_factor_schur", "kkt_schur_factor_copy", "kkt_accumulate",
            "kkt_solve_front", "kkt_solve_coupling", "kkt_solve_back", "kkt_residual", "kkt_abs_rowsums",
-           "kkt_norm_inf"]
+           "kkt_norm_inf", "kkt_kernel_stats"]
+
+KERNEL_FAMILIES = ["k_tc_update_emu", "k_tc_update_wide", "k_tc_update", "k_dense_update", "k_factor_update",
+                   "k_dense_diag_t"]
+
+
+class kkt_kernel_stat(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("ms_total", C.c_double), ("ms_max", C.c_double), ("flops", C.c_double)]
 
 _lib = None
 
@@ -153,6 +160,8 @@ def load(build_if_missing: bool = True):
                        ("kkt_norm_inf", [vp, vp, C.c_int64, C.POINTER(C.c_double), vp])):
         getattr(L, name).argtypes = args
         getattr(L, name).restype = C.c_int
+    L.kkt_kernel_stats.argtypes = [vp, C.c_int32, C.POINTER(kkt_kernel_stat)]
+    L.kkt_kernel_stats.restype = C.c_int
     _lib = L
     return L
 
@@ -275,6 +284,16 @@ def kkt_get_info(h) -> dict:
     info = kkt_info()
     _check(load().kkt_get_info(h, C.byref(info)))
     return info.as_dict()
+
+
+def kkt_kernel_stats(h) -> dict:
+    """Per-family device times of the handle's last factor (kkt_options.time_kernels)."""
+    out = {}
+    for f, name in enumerate(KERNEL_FAMILIES):
+        st = kkt_kernel_stat()
+        _check(load().kkt_kernel_stats(h, f, C.byref(st)))
+        out[name] = {"launches": st.launches, "ms_total": st.ms_total, "ms_max": st.ms_max, "flops": st.flops}
+    return out
 
 
 def kkt_solve_noalloc(h, rhs, x, stream=None):

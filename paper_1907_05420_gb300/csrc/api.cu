@@ -15,6 +15,20 @@ namespace kkt {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+int kt_begin(Handle& h, int fam, double flops, cudaStream_t st) {
+  if (!h.opt.time_kernels || 2 * (size_t)(h.kt_used + 1) > h.kt_ev.size()) return -1;
+  const int slot = h.kt_used++;
+  h.kt_fam[slot] = fam;
+  h.kt_flops[slot] = flops;
+  cudaEventRecordWithFlags(h.kt_ev[2 * slot], st, h.capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+  return slot;
+}
+
+void kt_end(Handle& h, int slot, cudaStream_t st) {
+  if (slot < 0) return;
+  cudaEventRecordWithFlags(h.kt_ev[2 * slot + 1], st, h.capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
 namespace {
 
 template <class T>
@@ -62,6 +76,8 @@ void free_all(Handle* h) {
   cudaEvent_t evs[] = {h->ev_f0, h->ev_f1, h->ev_fa, h->ev_fb, h->ev_s0, h->ev_s1, h->ev_done};
   for (cudaEvent_t ev : evs)
     if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : h->kt_ev)
+    if (ev) cudaEventDestroy(ev);
   if (h->factor_exec) cudaGraphExecDestroy(h->factor_exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->side_stream) cudaStreamDestroy(h->side_stream);
@@ -81,6 +97,7 @@ cudaError_t record(Handle& h, cudaEvent_t ev, cudaStream_t st) {
 // only on the handle's buffers and options, so the sequence is captured once
 // as a CUDA graph and replayed.
 cudaError_t enqueue_factor(Handle& h, cudaStream_t st, bool with_s = true) {
+  h.kt_used = 0;
   cudaError_t e = cudaMemsetAsync(h.counters, 0, sizeof(unsigned long long) * 2 * kNumCounters, st);
 #define STEP(x) \
   if (e == cudaSuccess) e = (x)
@@ -540,6 +557,15 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming);
+  if (e == cudaSuccess && h->opt.time_kernels) {
+    // an upper bound on the timed launches of one factor and its fallback
+    const int64_t slots = 8 * ((int64_t)(h->nTa + 63) / 64 + (h->nC + 63) / 64) + 2 * S.nlevels + 64;
+    h->kt_ev.assign(2 * slots, nullptr);
+    h->kt_fam.assign(slots, 0);
+    h->kt_flops.assign(slots, 0.0);
+    for (auto& ev : h->kt_ev)
+      if (e == cudaSuccess) e = cudaEventCreate(&ev);
+  }
   if (e == cudaSuccess) e = dense_prepare();
   if (e == cudaSuccess) e = dense_tc_prepare();
   if (e == cudaSuccess) e = schur_tc_prepare();
@@ -605,10 +631,14 @@ kkt_status factor_values(Handle* h, const double* a_vals, const double* b_vals, 
   h->g_reduced = with_s && (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && h->opt.reduced_contraction &&
                  contract_g_tc_supported(*h);
   h->s_factor = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) ? 1 : 0;
-  if (with_s && h->opt.use_graphs && !h->graph_failed && !h->factor_exec) capture_factor(*h);
+  if (with_s && h->opt.use_graphs && !h->graph_failed && !h->factor_exec) {
+    capture_factor(*h);
+    h->kt_graph_used = h->kt_used;
+  }
   if (with_s && h->factor_exec) {
     KKT_CUDA(cudaGraphLaunch(h->factor_exec, st));
     h->launches += h->graph_launches;
+    h->kt_used = h->kt_graph_used;  // the graph re-records the events of its timed launches
   } else {
     KKT_CUDA(enqueue_factor(*h, st, with_s));
   }
@@ -947,6 +977,26 @@ kkt_status kkt_get_info(kkt_handle* hh, kkt_info* info) {
   h->info.tail_ratio = h->nT > 0 ? h->tail_ratio : 0.0;
   h->info.tail_augmented = h->tail_aug ? 1 : 0;
   *info = h->info;
+  return KKT_OK;
+}
+
+kkt_status kkt_kernel_stats(kkt_handle* hh, int32_t family, kkt_kernel_stat* out) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !out || family < 0 || family >= kNumFamilies) {
+    set_error("kkt_kernel_stats: invalid argument");
+    return KKT_ERR_INVALID;
+  }
+  std::memset(out, 0, sizeof(*out));
+  KKT_CUDA(cudaEventSynchronize(h->ev_done));
+  for (int q = 0; q < h->kt_used; q++) {
+    if (h->kt_fam[q] != family) continue;
+    float ms = 0.f;
+    KKT_CUDA(cudaEventElapsedTime(&ms, h->kt_ev[2 * q], h->kt_ev[2 * q + 1]));
+    out->launches++;
+    out->ms_total += ms;
+    out->ms_max = std::max(out->ms_max, (double)ms);
+    out->flops += h->kt_flops[q];
+  }
   return KKT_OK;
 }
 

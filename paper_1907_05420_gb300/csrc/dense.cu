@@ -261,7 +261,9 @@ cudaError_t launch_dense_ldlt(Handle& h, unsigned long long* counters, cudaStrea
     const int rest = rend - k0 - kb;
     if (rest > 0) {
       const int T = (rest + 63) / 64;
+      const int kt = kt_begin(h, kFamDenseF64, update_flops(rest, 0, rest, kb), st);
       k_dense_update<<<T * (T + 1) / 2, 256, 0, st>>>(h.S, h.Ypanel, n, k0, kb, rend, 0, 0);
+      kt_end(h, kt, st);
       h.launches++;
     }
   }

@@ -960,7 +960,9 @@ cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int npiv, int nb, const TcSt
   }
   for (int k0 = 0; k0 < npiv && e == cudaSuccess; k0 += TK) {
     const int kb = std::min(TK, npiv - k0);
+    const int kd = kt_begin(h, kFamDiag, nb * (2.0 / 3.0) * kb * kb * kb, st);
     launch_prio(k_dense_diag_t<T>, dim3(nb), dim3(256), 0, st, prio, S, n, k0, kb, ts.s, rule, counters);
+    kt_end(h, kd, st);
     h.launches++;
     // rows below the envelope of the panel's columns stay zero (no pivoting)
     const int rend = rend_of_panel ? rend_of_panel[k0 / TK] : n;
@@ -1000,18 +1002,23 @@ cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int npiv, int nb, const TcSt
     // one launch of the update over the tiles of jmode (0 all, 1 J = 0, 2 J >= 1)
     auto update = [&](int jmode, cudaStream_t us, int uprio) -> cudaError_t {
       h.launches++;
+      const int c0 = jmode == 2 ? TN : 0, c1 = jmode == 1 ? TN : m;
+      const int kt = kt_begin(h, MODE == 2 ? kFamEmu : kFamTc, nb * update_flops(m, c0, c1, kb), us);
+      cudaError_t le;
       if constexpr (MODE == 2) {
         int tasks = 0;
         for (int I = 0; I < TI; I++) tasks += emu_row_tasks(I, TJ, jmode);
-        return launch_prio(k_tc_update_emu, dim3(tasks, nb), dim3(kEmuThreads), emu_smem_bytes(), us, uprio,
-                           (double*)S, n, k0, kb, m, TI, TJ, jmode, (const uint8_t*)imgA, (const uint8_t*)imgB,
-                           (const double*)scaleA, (const double*)scaleB, h.dev_err, ts);
+        le = launch_prio(k_tc_update_emu, dim3(tasks, nb), dim3(kEmuThreads), emu_smem_bytes(), us, uprio,
+                         (double*)S, n, k0, kb, m, TI, TJ, jmode, (const uint8_t*)imgA, (const uint8_t*)imgB,
+                         (const double*)scaleA, (const double*)scaleB, h.dev_err, ts);
       } else {
         const int cnt = jmode == 0 ? tiles : (jmode == 1 ? TI : tiles - TI);
-        return launch_prio(k_tc_update<MODE, T>, dim3(cnt, nb), dim3(128), smem, us, uprio, S, n, k0, kb, m, TJ,
-                           jmode, (const uint8_t*)imgA, (const uint8_t*)imgB, (const double*)scaleA,
-                           (const double*)scaleB, h.dev_err, ts);
+        le = launch_prio(k_tc_update<MODE, T>, dim3(cnt, nb), dim3(128), smem, us, uprio, S, n, k0, kb, m, TJ,
+                         jmode, (const uint8_t*)imgA, (const uint8_t*)imgB, (const double*)scaleA,
+                         (const double*)scaleB, h.dev_err, ts);
       }
+      kt_end(h, kt, us);
+      return le;
     };
     if (!side || TJ < 2) {
       e = update(0, st, 0);
@@ -1061,8 +1068,10 @@ cudaError_t factor_tf32_wide(Handle& h, float* S, float* Y, int n, unsigned long
     uint8_t* setB = setA + kWideChunks * sb;
     for (int c = 0; c * TK < Wb && e == cudaSuccess; c++) {
       const int k0 = K0 + c * TK, kb = std::min(TK, n - k0);
+      const int kd = kt_begin(h, kFamDiag, (2.0 / 3.0) * kb * kb * kb, st);
       launch_prio(k_dense_diag_t<float>, dim3(1), dim3(256), 0, st, prio, S, n, k0, kb, (int64_t)0, PivotRule{},
                   counters);
+      kt_end(h, kd, st);
       h.launches++;
       const int m = n - k0 - kb;
       if (m <= 0) continue;
@@ -1077,9 +1086,11 @@ cudaError_t factor_tf32_wide(Handle& h, float* S, float* Y, int n, unsigned long
       const int TI = (m + TM - 1) / TM;
       int tiles = 0;
       for (int I = 0; I < TI; I++) tiles += std::min(2 * I + 2, TJl);
+      const int kt = kt_begin(h, kFamTc, update_flops(m, 0, K0 + Wb - (k0 + kb), kb), st);
       e = launch_prio(k_tc_update<0, float>, dim3(tiles), dim3(128), A_BYTES + B_BYTES, st, prio, S, n, k0, kb, m,
                       TJl, 0, (const uint8_t*)img.A, (const uint8_t*)img.B, (const double*)nullptr,
                       (const double*)nullptr, h.dev_err, TcStrides{});
+      kt_end(h, kt, st);
       h.launches++;
     }
     const int base = K0 + Wb, m = n - base;
@@ -1095,8 +1106,13 @@ cudaError_t factor_tf32_wide(Handle& h, float* S, float* Y, int n, unsigned long
       const int tasks = wide_tasks(TI, jmode);
       if (tasks == 0) return cudaSuccess;
       h.launches++;
-      return launch_prio(k_tc_update_wide, dim3(tasks), dim3(kWideThreads), wide_smem_bytes(), us, uprio, S, n, base,
-                         m, TI, jmode, (const uint8_t*)setA, (const uint8_t*)setB, sb, h.dev_err);
+      const int c0 = jmode == 2 ? 2 * kWideTile : 0, c1 = jmode == 1 ? 2 * kWideTile : m;
+      const int kt = kt_begin(h, kFamWide, update_flops(m, c0, c1, kWideW), us);
+      const cudaError_t le = launch_prio(k_tc_update_wide, dim3(tasks), dim3(kWideThreads), wide_smem_bytes(), us,
+                                         uprio, S, n, base, m, TI, jmode, (const uint8_t*)setA, (const uint8_t*)setB,
+                                         sb, h.dev_err);
+      kt_end(h, kt, us);
+      return le;
     };
     if (!side || TI <= 2) {
       e = wide(0, st, prio);
@@ -1205,7 +1221,9 @@ cudaError_t launch_tail_factor_emulated(Handle& h, cudaStream_t st) {
 cudaError_t launch_dense_diag_panel_f64(Handle& h, int k0, int kb, int rend, unsigned long long* counters,
                                         cudaStream_t st) {
   const int n = h.nC;
+  const int kd = kt_begin(h, kFamDiag, (2.0 / 3.0) * kb * kb * kb, st);
   k_dense_diag_t<double><<<1, 256, 0, st>>>(h.S, n, k0, kb, 0, PivotRule{}, counters);
+  kt_end(h, kd, st);
   h.launches++;
   if (rend - k0 - kb > 0) {
     launch_dense_panel<double>(h.S, h.Ypanel, n, k0, kb, rend, 1, 0, 0, st);

@@ -189,7 +189,30 @@ struct Handle {
   int64_t graph_launches = 0;
   int64_t launches = 0;                          // kernels launched since analyze
   kkt_info info{};
+  // per-launch timing of the dominant kernels (opt.time_kernels): event pairs,
+  // the family and algorithmic flops of each timed launch; kt_used counts the
+  // launches of the current factor (fixed by the graph capture when graphs are on)
+  std::vector<cudaEvent_t> kt_ev;
+  std::vector<int> kt_fam;
+  std::vector<double> kt_flops;
+  int kt_used = 0;
+  int kt_graph_used = 0;  // timed launches inside the factor's graph
 };
+
+enum KernelFamily { kFamEmu = 0, kFamWide, kFamTc, kFamDenseF64, kFamFactorUpd, kFamDiag, kNumFamilies };
+// An event before a timed launch on `st` (returns its slot, -1 when not timing
+// or the pool is full) and one after it.
+int kt_begin(Handle& h, int fam, double flops, cudaStream_t st);
+void kt_end(Handle& h, int slot, cudaStream_t st);
+// algorithmic flops of a trailing update with inner dimension kb over the
+// entries of the lower triangle of an m x m trailing matrix in columns [c0, c1)
+inline double update_flops(int64_t m, int64_t c0, int64_t c1, int64_t kb) {
+  if (c1 > m) c1 = m;
+  if (c0 >= c1) return 0.0;
+  // entries (i, j) with c0 <= j < c1 and j <= i < m
+  const double e = (double)(c1 - c0) * (double)m - 0.5 * ((double)c1 * (c1 - 1) - (double)c0 * (c0 - 1));
+  return 2.0 * (double)kb * e;
+}
 
 constexpr int kDenseNB = 64;
 constexpr int kFactorTileRows = 64;  // rows of a work item of the supernodal update (factor.cu)

@@ -206,13 +206,17 @@ cudaError_t launch_dense_tail(Handle& h, cudaStream_t st) {
   const PivotRule rule{h.anorm, h.opt.pivot_eps, h.d.col_primal + tail_col};
   for (int k0 = 0; h.tail_mode == 1 && k0 < nT; k0 += kPanelW) {
     const int kb = std::min(kPanelW, nT - k0);
+    const int kd = kt_begin(h, kFamDiag, N * (2.0 / 3.0) * kb * kb * kb, st);
     k_dense_diag_t<double><<<N, 256, 0, st>>>(h.Tt, nTa, k0, kb, t2, rule, h.counters);
+    kt_end(h, kd, st);
     h.launches++;
     const int rest = nTa - k0 - kb;
     if (rest > 0) {
       launch_dense_panel<double>(h.Tt, h.TY, nTa, k0, kb, nTa, N, t2, ys, st);
       const int tiles = (rest + 63) / 64;
+      const int kt = kt_begin(h, kFamDenseF64, N * update_flops(rest, 0, rest, kb), st);
       k_dense_update<<<dim3(tiles * (tiles + 1) / 2, N), 256, 0, st>>>(h.Tt, h.TY, nTa, k0, kb, nTa, t2, ys);
+      kt_end(h, kt, st);
       h.launches += 2;
     }
   }

@@ -170,16 +170,39 @@ def test_in_process_shards_match_the_oracle(name, nshards, prec):
         assert err <= 10 * kappa * max(eta, oracle.backward_error(p, ref["x"]), EPS), err
 
 
-@pytest.mark.parametrize("grid", ["grid2383_n96", "grid9241_n168"])
-def test_tf32_wide_factor_matches_the_64_wide_one(grid):
-    """S of the SCOPF workload (dense C, order 652 and 2,888; a mild barrier so
-    that the FP32 factors stay comparable): the factor from 256-wide outer
-    panels is as close to the FP64-accurate factor as the 64-wide one."""
+def _dense_c_system(nC, seed):
+    """One 2 x 2 quasidefinite block, no coupling entries, and a dense SPD C of
+    order nC with eigenvalues log-uniform in [1, 1e3]: S = C, so the factor of
+    S is a plain dense LDL^T of a well-conditioned matrix."""
+    import types
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Q, _ = np.linalg.qr(rng.standard_normal((nC, nC)))
+    C = (Q * np.exp(rng.uniform(0.0, np.log(1e3), nC))) @ Q.T
+    C = 0.5 * (C + C.T)
+    return types.SimpleNamespace(
+        N=1, nA=2, nP=1, nC=nC, nK=2 + nC, c_kind=1,
+        a_rowptr=np.array([0, 1, 3], np.int32), a_col=np.array([0, 0, 1], np.int32),
+        a_vals=np.array([[1.0, 1.0, -1e-8]]), b_blockptr=np.zeros(2, np.int32),
+        b_row=np.zeros(0, np.int32), b_col=np.zeros(0, np.int32), b_vals=np.zeros(0),
+        c_vals=np.ascontiguousarray(C.reshape(-1)), rhs=rng.standard_normal(2 + nC))
+
+
+@pytest.mark.parametrize("case", ["scopf2383", "dense_c_1100", "dense_c_2000"])
+def test_tf32_wide_factor_matches_the_64_wide_one(case):
+    """The factor of S from 256-wide outer panels (TF32, S of order >= 512) is
+    as close to the FP64-accurate factor as the 64-wide one (the structured
+    mode, whose envelope is the whole matrix for a dense C): S of the SCOPF
+    workload (order 652, a mild barrier so that the FP32 factors stay
+    comparable) and dense S of order 1,100 and 2,000 (ragged last panels;
+    tile rows of up to 8 tiles per CTA)."""
     torch = _torch()
     from paper_1907_05420_gb300 import binding as B
 
-    spec = replace(CONFIGS[grid], bar_lo=1e-2, bar_hi=1e2, name=f"{grid}_mild")
-    p = make_scopf(spec, 1 if grid == "grid9241_n168" else 2)
+    if case == "scopf2383":
+        p = make_scopf(replace(CONFIGS["grid2383_n96"], bar_lo=1e-2, bar_hi=1e2, name="scopf2383_mild"), 2)
+    else:
+        p = _dense_c_system(int(case.split("_")[-1]), 7)
     assert p.nC >= 512 and p.c_kind == 1
     a, b, c, r = (_dev(torch, v) for v in (p.a_vals, p.b_vals, p.c_vals, p.rhs))
     F = {}
