@@ -688,12 +688,12 @@ def run_single(args):
     ir = acc_main["refine_steps_mean"]
     # algorithmic work per solve (2 flops per multiply-add): (a) reads A and
     # writes L and D once; (b) the contraction W^T D^-1 W, its symmetric half;
-    # (c) the dense LDL^T of S, n^3/3 multiply-adds; (d) each application reads
-    # the block factors twice and S once
+    # (c) the dense LDL^T of S, n^3/3 flops; (d) each application reads the
+    # block factors twice and S once
     work = {
         "a_block_factor": ("hbm", 8.0 * N * (prob.nnzA + info["nnz_l"] + nA)),
         "b_schur_assembly": ("tensor", float(N) * nw * k * k),
-        "c_dense_factor": ("tensor", 2.0 * nC ** 3 / 3.0),
+        "c_dense_factor": ("tensor", nC ** 3 / 3.0),
         "d_solve": ("hbm", (1 + ir) * (8.0 * N * (2 * info["panel_doubles"] + 2 * nA) + 8.0 * nC * nC)),
     }
     sustained = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])

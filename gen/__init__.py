@@ -14,4 +14,5 @@ from .mpopf import (  # noqa: F401
     reseed_barrier,
 )
 from .scopf import make_scopf  # noqa: F401
+from .ipm import make_ipm_state  # noqa: F401
 from .workloads import build_workload, describe_workload, is_workload  # noqa: F401

@@ -142,6 +142,7 @@ class KKTProblem:
     rhs: np.ndarray
     bar_pos: np.ndarray = field(repr=False, default=None)  # CSR positions of primal diagonals
     a_const: np.ndarray = field(repr=False, default=None)  # block values without the barrier
+    ineq_rows: np.ndarray = field(repr=False, default=None)  # rows of A that are inequality constraints
 
     @property
     def nnzA(self) -> int:
@@ -176,8 +177,17 @@ def _topology(rng, nb, nl):
     return np.array(edges, dtype=np.int64)
 
 
-def make_problem(spec: GridSpec, *, zero_b: bool = False, coupling: str = "adjacent") -> KKTProblem:
+def make_problem(spec: GridSpec, *, zero_b: bool = False, coupling: str = "adjacent",
+                 flow_limits: int = 0) -> KKTProblem:
     """Build the seeded instance described by ``spec``.
+
+    flow_limits=L > 0 appends L inequality rows to every A_i, after the other
+    multiplier rows: the linearised flow limit of line l (l < L), with entries
+    |b_l|, -|b_l| on the angles and g_l, -g_l on the magnitudes of its two
+    buses.  Their multipliers and slacks are those of the slack elimination
+    (Sec. 2, eq. SCOPFslackAtEnd): the rows are listed in ``ineq_rows`` and get
+    the dual regularisation -1e-8 on their diagonal like the other multiplier
+    rows.  L = 0 (the default) draws the same instance as before.
 
     zero_b=True keeps B's pattern but sets its values to zero (a special case
     in which the arrowhead system decouples).
@@ -207,7 +217,10 @@ def make_problem(spec: GridSpec, *, zero_b: bool = False, coupling: str = "adjac
     sto_bus = rng.choice(nb, size=ns, replace=False)
 
     nP = spec.n_primal
-    nA = spec.n_a - (ns if paper else 0)
+    if not 0 <= flow_limits <= spec.n_line:
+        raise ValueError("flow_limits must be between 0 and the number of lines")
+    nA0 = spec.n_a - (ns if paper else 0)
+    nA = nA0 + flow_limits
     th = lambda k: k                      # noqa: E731
     vv = lambda k: nb + k                 # noqa: E731
     PG = 2 * nb
@@ -247,6 +260,13 @@ def make_problem(spec: GridSpec, *, zero_b: bool = False, coupling: str = "adjac
     if not paper:
         add(DYN + si, PC + si, -ETA_C * np.ones(ns))
         add(DYN + si, PD + si, (1.0 / ETA_D) * np.ones(ns))
+    if flow_limits:
+        li = np.arange(flow_limits)
+        fl, tl = f[:flow_limits], t[:flow_limits]
+        add(nA0 + li, th(fl), bmag[:flow_limits])
+        add(nA0 + li, th(tl), -bmag[:flow_limits])
+        add(nA0 + li, vv(fl), g[:flow_limits])
+        add(nA0 + li, vv(tl), -g[:flow_limits])
     # diagonal present everywhere: zero placeholder on primal (barrier added
     # per period), dual regularisation on the multipliers
     add(np.arange(nP), np.arange(nP), np.zeros(nP))
@@ -320,7 +340,7 @@ def make_problem(spec: GridSpec, *, zero_b: bool = False, coupling: str = "adjac
         b_blockptr=np.array(bp, dtype=np.int32),
         b_row=np.array(br, dtype=np.int32), b_col=np.array(bc, dtype=np.int32),
         b_vals=b_vals, c_kind=0, c_vals=c_vals, rhs=rhs,
-        bar_pos=bar_pos, a_const=a_const,
+        bar_pos=bar_pos, a_const=a_const, ineq_rows=np.arange(nA0, nA, dtype=np.int32),
     )
 
 
