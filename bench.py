@@ -463,6 +463,7 @@ def main():
     ap.add_argument("--serve-backlog", type=int, default=0,
                     help="requests outstanding before new arrivals are shed (default 4 x slots)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-slack", action="store_true", help="skip the slack-elimination measurement")
     ap.add_argument("--autotune", type=int, default=-1,
                     help="dense-tail autotuning at analysis: 1 on, 0 off, -1 the workload's default")
     args = ap.parse_args()
@@ -473,6 +474,71 @@ def main():
     if args.workload == "serve":
         return run_serve(args)
     return run_single(args)
+
+
+def slack_timing(args, dev, stream, torch, np, B, reps=20):
+    """The slack elimination (Sec. 2) around one interior-point step on the
+    2,383-bus grid over 96 periods with a flow-limit inequality row for every
+    line (blocks of 13,386 rows): the in-place reduction and the recovery
+    timed alone (CUDA events, `reps` launches each, HBM bytes they must move),
+    and one whole step (reduce, factor, refined TF32 solve, recover)."""
+    from gen import CONFIGS, make_ipm_state, make_problem
+
+    spec = CONFIGS["grid2383_n96"]
+    p = make_problem(spec, flow_limits=spec.n_line)
+    st = make_ipm_state(p, 2383)
+    up = lambda v: torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).to(dev)  # noqa: E731
+    dst = {k: up(getattr(st, k)) for k in B.Slack.FIELDS}
+    h = B.kkt_analyze(p, B.kkt_default_options("tf32", tail_ratio=1.25, early_solve=1))
+    sl = B.Slack(h, p.ineq_rows)
+    try:
+        a_base, c_base, b = up(st.a_base), up(st.c_base), up(p.b_vals)
+        a, c = a_base.clone(), c_base.clone()
+        rhs = torch.empty(p.nK, dtype=torch.float64, device=dev)
+        x = torch.empty_like(rhs)
+        L, N, nP, nA, nC = len(p.ineq_rows), p.N, p.nP, p.nA, p.nC
+        ds, dy = (torch.empty(N * L, dtype=torch.float64, device=dev) for _ in range(2))
+        dz = torch.empty(N * nP + nC, dtype=torch.float64, device=dev)
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        ms_red = timed(lambda: sl.reduce(dst, a, c, a, c, rhs, stream))
+        ms_rec = timed(lambda: sl.recover(dst, x, ds, dz, dy, stream))
+        # bytes each must move: per row of K its diagonal (read + write), its
+        # right-hand side and its state entries; per unknown recovered its inputs and output
+        nx, ni, ne = N * nP + nC, N * L, N * (nA - nP) - N * L
+        red_bytes = 8.0 * (nx * (2 + 1 + 4) + ni * (2 + 1 + 5) + ne * 2)
+        rec_bytes = 8.0 * (nx * 5 + ni * 7)
+
+        def step():
+            a.copy_(a_base)
+            sl.reduce(dst, a, c, a, c, rhs, stream)
+            B.kkt_factor(h, a, b, c, stream)
+            B.kkt_solve(h, rhs, x, 1, stream, allow_not_converged=True)
+            sl.recover(dst, x, ds, dz, dy, stream)
+
+        ms_step = timed(step) if reps else None
+        info = B.kkt_get_info(h)
+        peaks, _ = _peaks()
+        return {"workload": f"grid2383_n96 with {spec.n_line:,} flow-limit rows per period (nA={nA:,})",
+                "reduce_ms": ms_red, "reduce_gbs": red_bytes / ms_red / 1e6,
+                "reduce_hbm_frac": red_bytes / ms_red / 1e6 / peaks["hbm_gbs"],
+                "recover_ms": ms_rec, "recover_gbs": rec_bytes / ms_rec / 1e6,
+                "recover_hbm_frac": rec_bytes / ms_rec / 1e6 / peaks["hbm_gbs"],
+                "ipm_step_ms": ms_step, "ipm_steps_per_s": 1e3 / ms_step if ms_step else None,
+                "eta": info["rel_residual"], "refine_steps": info["refine_steps"]}
+    finally:
+        sl.close()
+        B.kkt_destroy(h)
 
 
 def _accuracy(B, h, prob, r, x, stream, torch):
@@ -635,6 +701,8 @@ def run_single(args):
                                     "p99": float(np.percentile(lr["step_ms"], 99))},
                      "accuracy": acc, "phases_ms": {kk: statistics.mean(v) for kk, v in lr["phases"].items()}}
 
+    slack = None if args.no_slack else slack_timing(args, dev, stream, torch, np, B)
+
     # ---- forward errors against the FP64-accurate solutions of this run
     ref_leg = next((m for m in ("fp64+band", "fp64", "f64emu") if m in xs), None)
     err = lambda xv, xr: float(np.max(np.abs(xv - xr)) / np.max(np.abs(xr)))  # noqa: E731
@@ -741,7 +809,7 @@ def run_single(args):
         "dense_tail": {"cols": info0["dense_tail_cols"], "ratio": info0["tail_ratio"],
                        "augmented": bool(info0["tail_augmented"]),
                        "autotune_candidates": info0["autotune_candidates"]},
-        "device_bytes": info0["device_bytes"], "other_precisions": legs,
+        "device_bytes": info0["device_bytes"], "other_precisions": legs, "slack_elimination": slack,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], out = cpu_baseline_sample(args.workload, prob, info0["factor_flops"])

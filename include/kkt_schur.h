@@ -369,6 +369,46 @@ kkt_status kkt_abs_rowsums(kkt_handle* h, double* out, void* stream);
  * synchronizes `stream`. */
 kkt_status kkt_norm_inf(kkt_handle* h, const double* v, int64_t n, double* out, void* stream);
 
+/* ---- slack elimination around the solve (Sec. 2, eqs. SCOPFhessian,
+ * SCOPFhessianSymmetric, SCOPFslackAtEnd, SCOPFhessianReduced,
+ * SCOPFslackReduction, SCOPFhessianSymmetricRecovery) ----
+ * The barrier method's Newton system in (dx, ds, dlE, dlI, dz, dy) is reduced
+ * to K by eliminating the bound multipliers z, y and the slacks s of the
+ * inequality rows; after the solve the eliminated unknowns are recovered:
+ *   A_i: primal diagonals += z/x; inequality-row diagonals = -(s/y) (-L_s^-1,
+ *        the base value there is replaced); C's diagonal += z_g/x_g;
+ *   rhs: primal rows -(l_a + l_e/x); equality rows -l_c; inequality rows
+ *        -(l_d + (s/y)(l_b + l_f/s));
+ *   ds = (s/y)(dlI - l_b - l_f/s), dz = -(l_e + z dx)/x, dy = -(l_f + y ds)/s.
+ * Every primal variable (the nP primal rows of every block and the nC
+ * coupling variables) has a bound with multiplier z; the inequality rows are
+ * multiplier rows of A.  The elimination assumes s/y well away from 0 and
+ * infinity, as the paper notes.  All arrays are device arrays; the calls are
+ * asynchronous on `stream`; each entry is computed by one thread in the order
+ * written above, with round-to-nearest and no fused multiply-adds. */
+typedef struct kkt_slack kkt_slack;
+typedef struct {
+  const double *x, *z;   /* N*nP + nC: primal variables (blocks, then coupling) and their bound multipliers, > 0 */
+  const double *s, *y;   /* N*n_ineq: slacks of the inequality rows and their bound multipliers, > 0 */
+  const double *la, *le; /* N*nP + nC: residuals l_a (stationarity) and l_e (complementarity of x, z) */
+  const double *lcd;     /* N*(nA - nP): per block the multiplier rows in row order, l_d on the
+                            inequality rows and l_c on the others */
+  const double *lb, *lf; /* N*n_ineq: residuals l_b and l_f (complementarity of s, y) */
+} kkt_ipm_state;
+/* The inequality rows of the handle's pattern: n_ineq increasing rows of A in
+ * [nP, nA), the same in every block (host array, copied). */
+kkt_status kkt_slack_create(kkt_handle* h, int32_t n_ineq, const int32_t* ineq_rows, kkt_slack** out);
+/* a_vals (N*nnzA), c_vals (as kkt_factor) and rhs (N*nA + nC) of the reduced
+ * system from the base values (H and J without the bound terms) and the
+ * state; a_vals may be a_base and c_vals may be c_base (in place). */
+kkt_status kkt_slack_reduce(kkt_slack* sl, const kkt_ipm_state* st, const double* a_base, const double* c_base,
+                            double* a_vals, double* c_vals, double* rhs, void* stream);
+/* ds, dy (N*n_ineq) and dz (N*nP + nC) from the solution dsol of the reduced
+ * system (N*nA + nC). */
+kkt_status kkt_slack_recover(kkt_slack* sl, const kkt_ipm_state* st, const double* dsol, double* ds, double* dz,
+                             double* dy, void* stream);
+kkt_status kkt_slack_destroy(kkt_slack* sl);
+
 /* ---- batching and serving (no counterpart in the paper; the workload's many
  * independent systems of different grids and horizons) ---- */
 

@@ -80,10 +80,15 @@ EXPORTS = ["kkt_default_options", "kkt_analyze", "kkt_factor", "kkt_solve", "kkt
            "kkt_server_poll", "kkt_server_destroy", "kkt_default_inertia_options", "kkt_factor_inertia",
            "kkt_factor_blocks", "kkt_schur_matrix", "kkt_factor_schur", "kkt_schur_factor_copy", "kkt_accumulate",
            "kkt_solve_front", "kkt_solve_coupling", "kkt_solve_back", "kkt_residual", "kkt_abs_rowsums",
-           "kkt_norm_inf", "kkt_kernel_stats"]
+           "kkt_norm_inf", "kkt_kernel_stats", "kkt_slack_create", "kkt_slack_reduce", "kkt_slack_recover",
+           "kkt_slack_destroy"]
 
 KERNEL_FAMILIES = ["k_tc_update_emu", "k_tc_update_wide", "k_tc_update", "k_dense_update", "k_factor_update",
                    "k_dense_diag_t"]
+
+
+class kkt_ipm_state(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("x", "z", "s", "y", "la", "le", "lcd", "lb", "lf")]
 
 
 class kkt_kernel_stat(C.Structure):
@@ -162,6 +167,14 @@ def load(build_if_missing: bool = True):
         getattr(L, name).restype = C.c_int
     L.kkt_kernel_stats.argtypes = [vp, C.c_int32, C.POINTER(kkt_kernel_stat)]
     L.kkt_kernel_stats.restype = C.c_int
+    L.kkt_slack_create.argtypes = [vp, C.c_int32, vp, C.POINTER(C.c_void_p)]
+    L.kkt_slack_create.restype = C.c_int
+    L.kkt_slack_reduce.argtypes = [vp, C.POINTER(kkt_ipm_state), vp, vp, vp, vp, vp, vp]
+    L.kkt_slack_reduce.restype = C.c_int
+    L.kkt_slack_recover.argtypes = [vp, C.POINTER(kkt_ipm_state), vp, vp, vp, vp, vp]
+    L.kkt_slack_recover.restype = C.c_int
+    L.kkt_slack_destroy.argtypes = [vp]
+    L.kkt_slack_destroy.restype = C.c_int
     _lib = L
     return L
 
@@ -294,6 +307,39 @@ def kkt_kernel_stats(h) -> dict:
         _check(load().kkt_kernel_stats(h, f, C.byref(st)))
         out[name] = {"launches": st.launches, "ms_total": st.ms_total, "ms_max": st.ms_max, "flops": st.flops}
     return out
+
+
+class Slack:
+    """Slack elimination around the solve (kkt_slack_*; device tensors)."""
+
+    FIELDS = ("x", "z", "s", "y", "la", "le", "lcd", "lb", "lf")
+
+    def __init__(self, h, ineq_rows):
+        rows = np.ascontiguousarray(ineq_rows, dtype=np.int32)
+        self.sl = C.c_void_p()
+        _check(load().kkt_slack_create(h, int(rows.size), rows.ctypes.data if rows.size else None,
+                                       C.byref(self.sl)))
+
+    def _state(self, st):
+        """st: a mapping or object with device tensors named as kkt_ipm_state's fields."""
+        get = (lambda k: st[k]) if isinstance(st, dict) else (lambda k: getattr(st, k))
+        return kkt_ipm_state(*[_dev(get(k)) if get(k) is not None and get(k).numel() else None
+                               for k in self.FIELDS])
+
+    def reduce(self, st, a_base, c_base, a_vals, c_vals, rhs, stream=None):
+        s = self._state(st)
+        return _check(load().kkt_slack_reduce(self.sl, C.byref(s), _dev(a_base), _dev(c_base), _dev(a_vals),
+                                              _dev(c_vals), _dev(rhs), _stream_ptr(stream)))
+
+    def recover(self, st, dsol, ds, dz, dy, stream=None):
+        s = self._state(st)
+        return _check(load().kkt_slack_recover(self.sl, C.byref(s), _dev(dsol), _dev(ds) if ds.numel() else None,
+                                               _dev(dz), _dev(dy) if dy.numel() else None, _stream_ptr(stream)))
+
+    def close(self):
+        if self.sl:
+            load().kkt_slack_destroy(self.sl)
+            self.sl = C.c_void_p()
 
 
 def kkt_solve_noalloc(h, rhs, x, stream=None):
