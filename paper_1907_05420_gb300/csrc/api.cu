@@ -68,7 +68,8 @@ void free_all(Handle* h) {
                   h->t_scaleA, h->t_scaleB, h->Lx, h->a_vals, h->b_vals,
                   h->c_vals, h->anorm, h->W, h->G, h->S, h->Ypanel, h->knorm, h->counters, h->r,
                   h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red,
-                  h->trsv_flags, h->trsv_ticket, h->dev_err, h->S32, h->Y32, h->tw_img, h->tc_imgA,
+                  h->trsv_flags, h->trsv_ticket, h->dev_err, h->S32, h->Y32, h->tw_img, h->ew_s_Y, h->ew_s_A,
+                  h->ew_s_B, h->ew_s_scale, h->ew_t_Y, h->ew_t_A, h->ew_t_B, h->ew_t_scale, h->tc_imgA,
                   h->tc_imgB, h->tc_scaleA, h->tc_scaleB};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -499,6 +500,12 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
     AL(t_imgB, uint8_t, ib * h->N);
     AL(t_scaleA, double, ((int64_t)h->nTa + 256) * h->N);
     AL(t_scaleB, double, ((int64_t)h->nTa + 256) * h->N);
+    if (emu_wide_applies(h->nT)) {  // 256-wide outer panels of the tails
+      AL(ew_t_Y, double, (int64_t)h->nTa * 256 * h->N);
+      AL(ew_t_A, uint8_t, emu_wide_image_bytes(h->nTa) * h->N);
+      AL(ew_t_B, uint8_t, emu_wide_image_bytes(h->nTa) * h->N);
+      AL(ew_t_scale, double, 2 * ((int64_t)h->nTa + 256) * h->N);
+    }
   }
   AL(knorm, double, 1);
   AL(counters, unsigned long long, 2 * kNumCounters);  // second half: discarded counts
@@ -533,6 +540,12 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
     AL(tc_imgB, uint8_t, itot - ia);
     AL(tc_scaleA, double, (int64_t)h->nC + 256);
     AL(tc_scaleB, double, (int64_t)h->nC + 256);
+    if (emu_wide_applies(h->nC) && !h->opt.structured_s) {  // the emulated factor of S (mode or fallback)
+      AL(ew_s_Y, double, (int64_t)h->nC * 256);
+      AL(ew_s_A, uint8_t, emu_wide_image_bytes(h->nC));
+      AL(ew_s_B, uint8_t, emu_wide_image_bytes(h->nC));
+      AL(ew_s_scale, double, 2 * ((int64_t)h->nC + 256));
+    }
   }
   AL(trsv_ticket, unsigned, 2);
   AL(dev_err, int, 1);

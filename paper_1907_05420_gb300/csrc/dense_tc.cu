@@ -661,6 +661,321 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
+// ---- Emulated-FP64 update of a 256-wide outer panel ----
+//
+// The emulated factors (dense tails of the block factors, S in the emulated
+// mode and the FP64 fallback) also run in outer panels of 256 columns: the
+// 64-wide steps update only the outer panel's own columns, and the rest of the
+// trailing matrix takes one update with K = 256, so that each trailing entry
+// pays one epilogue (levels folded, FP64 bits built, read-modify-write) per
+// 256 columns of K instead of per 64.
+//
+// One 256-wide operand image per outer panel (k_slice_wide): every row of Y
+// (= L D) and of L over the panel's columns is scaled by a power of two 2^e
+// common to the 256 columns, |v| < 2^(e-1), and cut into 7 balanced base-256
+// digits in [-128, 128] (balanced7).  A digit product is then at most 2^14, so
+// the FP32 tensor-memory levels 0..3 of a K = 256 accumulation stay below 2^24
+// and exact, as the 64-wide update's unsigned digits do for K = 64, and the
+// fold and FP64 recombination of the epilogue are the same.  Levels 4..6 round
+// only where their partial sums pass 2^24, which keeps the error of the
+// product within the worst-case rounding of an FP64 dot product of 256 terms.
+//
+// Image layout (per matrix and operand): 64-row blocks; in a block, for each
+// 32-column K chunk (8 of them) and each digit slice (7), the 8 row groups x 4
+// core matrices along K x 128 bytes (4 KB).  One shared-memory stage holds one
+// K chunk of a 128 x 64 tile: A 7 x 8 KB, B 7 x 4 KB.
+constexpr int kEwW = 256;                          // outer panel width
+constexpr int kEwChunk = 32;                       // K per stage
+constexpr int kEwChunks = kEwW / kEwChunk;         // 8
+constexpr int kEwPiece = 4096;                     // one (block, chunk, slice): 8 row groups x 4 x 128 B
+constexpr int kEwBlockBytes = kEwChunks * kEmuSlices * kEwPiece;  // 64 rows: 229,376 bytes
+constexpr int kEwStageA = kEmuSlices * 2 * kEwPiece;  // 128 rows, 57,344 bytes
+constexpr int kEwStageB = kEmuSlices * kEwPiece;      // 64 rows, 28,672 bytes
+constexpr int kEwStages = 2;
+__host__ __device__ constexpr int ew_smem_bytes() { return kEwStages * (kEwStageA + kEwStageB); }  // 168 KB
+
+// rows rho in [0, mpad) of the outer trailing matrix of matrix blockIdx.y:
+// operand A = rows of Y (columns 0..kw-1 of Yw, leading dimension n), operand
+// B = rows of L (columns K0..K0+kw-1 of S); rows >= m and columns >= kw are zero.
+__global__ void __launch_bounds__(128) k_slice_wide(const double* __restrict__ S0, const double* __restrict__ Yw0,
+                                                    int n, int K0, int kw, int base, int m, int mpad,
+                                                    uint8_t* __restrict__ imgA0, uint8_t* __restrict__ imgB0,
+                                                    double* __restrict__ scaleA0, double* __restrict__ scaleB0,
+                                                    int64_t s_stride, int64_t y_stride, int64_t img_stride,
+                                                    int64_t scale_stride) {
+  const int64_t bb = blockIdx.y;
+  __shared__ uint32_t bf16_of_byte[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) bf16_of_byte[i] = bf16_bits_of_byte((uint32_t)i);
+  __syncthreads();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 2 * mpad) return;
+  const bool isA = q < mpad;
+  const int rho = isA ? q : q - mpad;
+  const bool live = rho < m;
+  const double* src = isA ? Yw0 + bb * y_stride : S0 + bb * s_stride + (int64_t)K0 * n;  // column 0 of the operand
+  const int64_t row = (int64_t)base + rho;
+  uint8_t* img = (isA ? imgA0 : imgB0) + bb * img_stride;
+  // e = ilogb(max |v|) + 2, so that |v| < 2^(e-1); rows whose largest entry is
+  // subnormal or zero take the FP64 route
+  int emax = 0;
+  if (live)
+    for (int c = 0; c < kw; c++) emax = max(emax, exp_field(src[row + (int64_t)c * n]));
+  int e_exp;
+  if (emax > 0) {
+    e_exp = emax - 1023 + 2;
+  } else {
+    double amax = 0.0;
+    if (live)
+      for (int c = 0; c < kw; c++) amax = fmax(amax, fabs(src[row + (int64_t)c * n]));
+    e_exp = amax > 0.0 ? ilogb(amax) + 2 : 0;
+  }
+  (isA ? scaleA0 : scaleB0)[bb * scale_stride + rho] = ldexp(1.0, e_exp);
+  const int blk = rho >> 6, rr = rho & 63, g = rr >> 3, r8 = rr & 7;
+  uint8_t* bimg = img + (int64_t)blk * kEwBlockBytes + (g * 4) * 128 + r8 * 16;
+  for (int k = 0; k < kEwChunks; k++) {
+#pragma unroll
+    for (int kq = 0; kq < 4; kq++) {
+      uint32_t packed[kEmuSlices][4];
+#pragma unroll
+      for (int e = 0; e < 8; e++) {
+        const int c = k * kEwChunk + kq * 8 + e;
+        const double v = (live && c < kw) ? src[row + (int64_t)c * n] : 0.0;
+        long long vb;
+        const unsigned long long a = digits7(v, e_exp, vb);
+        int d[kEmuSlices];
+        balanced7(a, d);
+        const uint32_t neg = vb < 0 ? 0x8000u : 0u;
+#pragma unroll
+        for (int sl = 0; sl < kEmuSlices; sl++) {
+          const int t = d[sl];
+          const uint32_t hbits = t == 0 ? 0u : (bf16_of_byte[t < 0 ? -t : t] | ((t < 0 ? 0x8000u : 0u) ^ neg));
+          packed[sl][e >> 1] = (e & 1) ? (packed[sl][e >> 1] | (hbits << 16)) : hbits;
+        }
+      }
+#pragma unroll
+      for (int sl = 0; sl < kEmuSlices; sl++)
+        *reinterpret_cast<uint4*>(bimg + ((int64_t)(k * kEmuSlices + sl)) * kEwPiece + kq * 128) =
+            make_uint4(packed[sl][0], packed[sl][1], packed[sl][2], packed[sl][3]);
+    }
+  }
+}
+
+// The K = 256 emulated update: one CTA per run of up to kEmuRun tiles (I, J)
+// of one tile row I (128 x 64 tiles of the lower triangle, J <= 2I + 1);
+// jmode 1 takes J < 4 (the next outer panel's 256 columns), 2 the rest.
+// Warp roles as in k_tc_update_emu: warp 0 copies the K chunks of A and B of
+// every tile through two shared-memory stages, warp 1 issues the 56 MMAs of
+// each chunk (28 digit pairs x 2 K steps of 16) into 7 tensor-memory levels,
+// warps 2..9 fold the levels of a finished tile, hand tensor memory back and
+// read-modify-write S.  Every wait is bounded, as there.
+__global__ void __launch_bounds__(kEmuThreads, 1)
+    k_tc_update_emu_wide(double* __restrict__ S0, int n, int base, int m, int TI, int TJ, int jmode, int nchunk,
+                         const uint8_t* __restrict__ imgA0, const uint8_t* __restrict__ imgB0,
+                         const double* __restrict__ scaleA0, const double* __restrict__ scaleB0,
+                         int64_t s_stride, int64_t img_stride, int64_t scale_stride, int* err) {
+  constexpr uint32_t TMEM_COLS = 512;  // 7 levels x 64 columns
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bar_full[kEwStages], bar_empty[kEwStages], bar_tfull, bar_tempty;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_abort;
+  const int64_t bb = blockIdx.y;
+  double* S = S0 + bb * s_stride;
+  const uint8_t* imgA = imgA0 + bb * img_stride;
+  const uint8_t* imgB = imgB0 + bb * img_stride;
+  const double* scaleA = scaleA0 + bb * scale_stride;
+  const double* scaleB = scaleB0 + bb * scale_stride;
+  int I, j0, j1;
+  emu_task(blockIdx.x, TI, TJ, jmode, I, j0, j1, 4);
+  const int ntile = max(0, j1 - j0);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    s_abort = 0;
+    for (int st = 0; st < kEwStages; st++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_full[st])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_empty[st])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_tfull)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_tempty)), "r"(kEpiWarps));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const int nsteps = ntile * nchunk;
+
+  if (warp == 0) {
+    if (lane == 0 && ntile > 0) {
+      // producer: chunk g = u * nchunk + k of tile u into stage g & 1
+      int armed[kEwStages] = {0, 0};
+      for (int g = 0; g < nsteps; g++) {
+        const int st = g & 1, u = g / nchunk, k = g - u * nchunk, J = j0 + u;
+        if (g >= kEwStages && !mbar_wait_ab(smem_u32(&bar_empty[st]), (uint32_t)(((g >> 1) - 1) & 1), &s_abort)) {
+          if (!s_abort) atomicExch(err, 13);
+          s_abort = 1;
+          break;
+        }
+        const uint32_t bf = smem_u32(&bar_full[st]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bf),
+                     "r"((uint32_t)(kEwStageA + kEwStageB))
+                     : "memory");
+        uint8_t* sA = smem + st * (kEwStageA + kEwStageB);
+        uint8_t* sB = sA + kEwStageA;
+        for (int sl = 0; sl < kEmuSlices; sl++) {
+          const int64_t piece = ((int64_t)k * kEmuSlices + sl) * kEwPiece;
+          bulk_load(sA + sl * 2 * kEwPiece, imgA + (int64_t)(2 * I) * kEwBlockBytes + piece, kEwPiece, bf);
+          bulk_load(sA + sl * 2 * kEwPiece + kEwPiece, imgA + (int64_t)(2 * I + 1) * kEwBlockBytes + piece, kEwPiece,
+                    bf);
+          bulk_load(sB + sl * kEwPiece, imgB + (int64_t)J * kEwBlockBytes + piece, kEwPiece, bf);
+        }
+        armed[st]++;
+      }
+      volatile int never = 0;
+      for (int st = 0; st < kEwStages; st++)
+        if (armed[st] > 0) mbar_wait_ab(smem_u32(&bar_full[st]), (uint32_t)((armed[st] - 1) & 1), &never);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && ntile > 0) {
+      // MMA issuer
+      uint32_t last_bar = 0, last_par = 0;
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                             ((uint32_t)(TM >> 4) << 24);
+      bool stop = false;
+      for (int u = 0; u < ntile && !stop; u++) {
+        if (u >= 1 && !mbar_wait_ab(smem_u32(&bar_tempty), (uint32_t)((u - 1) & 1), &s_abort)) {
+          if (!s_abort) atomicExch(err, 14);
+          s_abort = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int k = 0; k < nchunk; k++) {
+          const int g = u * nchunk + k, st = g & 1;
+          if (!mbar_wait_ab(smem_u32(&bar_full[st]), (uint32_t)((g >> 1) & 1), &s_abort)) {
+            if (!s_abort) atomicExch(err, 15);
+            s_abort = 1;
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint8_t* sA = smem + st * (kEwStageA + kEwStageB);
+          const uint8_t* sB = sA + kEwStageA;
+          for (int d = 0; d < kEmuLevels; d++) {
+            const uint32_t dtm = tmem + (uint32_t)(d * TN);
+            for (int sa = 0; sa < kEmuSlices; sa++) {
+              const int sb = d - sa;
+              if (sb < 0 || sb >= kEmuSlices) continue;
+              for (int ks = 0; ks < kEwChunk / 16; ks++) {
+                const uint64_t ad = umma_desc(smem_u32(sA + sa * 2 * kEwPiece + ks * 256), 128, 512);
+                const uint64_t bd = umma_desc(smem_u32(sB + sb * kEwPiece + ks * 256), 128, 512);
+                const uint32_t acc = (k == 0 && sa == (d < kEmuSlices ? 0 : d - kEmuSlices + 1) && ks == 0) ? 0u : 1u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
+                    "p;\n}" ::"r"(dtm),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+              }
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&bar_empty[st]))
+                       : "memory");
+          last_bar = smem_u32(&bar_empty[st]);
+          last_par = (uint32_t)((g >> 1) & 1);
+        }
+        if (stop) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&bar_tfull))
+                     : "memory");
+        last_bar = smem_u32(&bar_tfull);
+        last_par = (uint32_t)(u & 1);
+      }
+      volatile int never = 0;
+      if (last_bar) mbar_wait_ab(last_bar, last_par, &never);
+    }
+  } else {
+    // epilogue (as in k_tc_update_emu)
+    const int q = warp & 3, cbase = ((warp - 2) >> 2) * kEpiCols;
+    const int rho = I * TM + q * 32 + lane;
+    const int row = base + rho;
+    const bool live_row = rho < m;
+    const int ea = pow2_exponent(live_row ? scaleA[rho] : 1.0) - 56;
+    for (int u = 0; u < ntile; u++) {
+      const int J = j0 + u;
+      const int cj0 = J * TN + cbase;
+      int ebl[kEpiCols / 32];
+#pragma unroll
+      for (int g2 = 0; g2 < kEpiCols / 32; g2++)
+        ebl[g2] = pow2_exponent(cj0 + g2 * 32 + lane < m ? scaleB[cj0 + g2 * 32 + lane] : 1.0);
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait_ab(smem_u32(&bar_tfull), (uint32_t)(u & 1), &s_abort);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) {
+        if (lane == 0) {
+          if (!s_abort) atomicExch(err, 16);
+          s_abort = 1;
+        }
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      double nd[kEpiCols];
+#pragma unroll
+      for (int hh = 0; hh < kEpiCols / 16; hh++) {
+        long long V[16];
+        float cf[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          V[j] = 0;
+          cf[j] = 0.f;
+        }
+#pragma unroll
+        for (int d = 0; d < kEmuLevels; d++) {
+          uint32_t r[16];
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * TN + cbase + hh * 16), r);
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            const float fv = __uint_as_float(r[j]);
+            if (d < 4) V[j] = V[j] * 256 + exact_f2i(fv);
+            else cf[j] += fv * (d == 4 ? 1.f : (d == 5 ? 0.00390625f : 0.0000152587890625f));
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          const long long W = V[j] * 65536 + round_f2ll(cf[j] * 256.f);
+          const int eb = __shfl_sync(0xffffffffu, ebl[(hh * 16 + j) >> 5], (hh * 16 + j) & 31);
+          nd[hh * 16 + j] = neg_scaled(W, ea + eb);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_tempty)) : "memory");
+      if (live_row) {
+#pragma unroll
+        for (int hh = 0; hh < kEpiCols / 16; hh++) {
+          double cur[16];
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            const int cj = cj0 + hh * 16 + j, col = base + cj;
+            cur[j] = (cj < m && row >= col) ? S[(int64_t)row + (int64_t)col * n] : 0.0;
+          }
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            const int cj = cj0 + hh * 16 + j, col = base + cj;
+            if (cj < m && row >= col) S[(int64_t)row + (int64_t)col * n] = cur[j] + nd[hh * 16 + j];
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
 // ---- TF32 trailing update of a 256-wide outer panel (two-level blocking) ----
 //
 // The TF32 factor of S runs the 64-wide panel steps above inside outer panels
@@ -1040,6 +1355,118 @@ cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int npiv, int nb, const TcSt
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// The emulated-FP64 factor with 256-wide outer panels (k_slice_wide and
+// k_tc_update_emu_wide above), for nb matrices of order n with npiv pivots.
+// Per outer panel K0: its 64-wide steps (diagonal block, panel writing Y into
+// the panel's columns of Yw, per-step images, k_tc_update_emu over the outer
+// panel's own remaining columns); then the 256-wide images and the outer
+// update of the rest: its first four tile columns (the next outer panel's
+// columns) on the high-priority chain, the others on the side stream,
+// overlapping the next outer panel's steps.  The next panel's slicing waits
+// for the side stream (it overwrites the images the rest reads).
+struct EwBuffers {
+  double* Yw = nullptr;   // per matrix: n x 256, leading dimension n
+  int64_t y_stride = 0;
+  uint8_t* A = nullptr;   // per matrix: the 256-wide images of Y and of L
+  uint8_t* B = nullptr;
+  int64_t img_stride = 0;
+  double* sA = nullptr;   // per matrix: row scales
+  double* sB = nullptr;
+  int64_t scale_stride = 0;
+};
+
+cudaError_t factor_emu_wide(Handle& h, double* S, int n, int npiv, int nb, const TcStrides& ts, const PivotRule& rule,
+                            unsigned long long* counters, uint8_t* imgA, uint8_t* imgB, double* scaleA,
+                            double* scaleB, const EwBuffers& ew, cudaStream_t caller) {
+  cudaStream_t side = h.side_stream;
+  cudaStream_t st = caller;
+  const int prio = side ? h.prio_hi : 0;
+  bool side_busy = false;
+  cudaError_t e = cudaSuccess;
+  if (side && h.hi_stream) {
+    e = cudaEventRecord(h.ev_main, caller);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h.hi_stream, h.ev_main, 0);
+    if (e != cudaSuccess) return e;
+    st = h.hi_stream;
+  }
+  TcStrides ti = ts;  // the per-step images, with Y taken from Yw
+  ti.y = ew.y_stride;
+  for (int K0 = 0; K0 < npiv && e == cudaSuccess; K0 += kEwW) {
+    const int Wb = std::min(kEwW, npiv - K0);
+    for (int c = 0; c * TK < Wb && e == cudaSuccess; c++) {
+      const int k0 = K0 + c * TK, kb = std::min(TK, npiv - k0);
+      const int kd = kt_begin(h, kFamDiag, nb * (2.0 / 3.0) * kb * kb * kb, st);
+      launch_prio(k_dense_diag_t<double>, dim3(nb), dim3(256), 0, st, prio, S, n, k0, kb, ts.s, rule, counters);
+      kt_end(h, kd, st);
+      h.launches++;
+      const int m = n - k0 - kb;
+      if (m <= 0) continue;
+      double* Yc = ew.Yw + (int64_t)c * TK * n;
+      launch_dense_panel<double>(S, Yc, n, k0, kb, n, nb, ts.s, ew.y_stride, st, prio);
+      h.launches++;
+      // the outer panel's own remaining columns
+      const int TJl = (K0 + Wb - (k0 + kb) + TN - 1) / TN;
+      if (TJl <= 0) continue;
+      const int TI = (m + TM - 1) / TM, mpadA = TI * TM, mpadB = TJl * TN;
+      const int sgrid = std::max(1, std::min((mpadA + mpadB + 255) / 256, 152 * 8 / nb));
+      launch_prio(k_tc_slice<2, double>, dim3(sgrid, nb), dim3(256), 0, st, prio, (const double*)S,
+                  (const double*)Yc, n, k0, kb, m, imgA, imgB, scaleA, scaleB, mpadA, mpadB, ti);
+      h.launches++;
+      int tasks = 0;
+      for (int I = 0; I < TI; I++) tasks += emu_row_tasks(I, TJl, 0);
+      const int kt = kt_begin(h, kFamEmu, nb * update_flops(m, 0, K0 + Wb - (k0 + kb), kb), st);
+      e = launch_prio(k_tc_update_emu, dim3(tasks, nb), dim3(kEmuThreads), emu_smem_bytes(), st, prio, S, n, k0, kb,
+                      m, TI, TJl, 0, (const uint8_t*)imgA, (const uint8_t*)imgB, (const double*)scaleA,
+                      (const double*)scaleB, h.dev_err, ti);
+      kt_end(h, kt, st);
+      h.launches++;
+    }
+    const int base = K0 + Wb, m = n - base;
+    if (m <= 0 || e != cudaSuccess) break;
+    if (side_busy) {  // the rest of the previous outer update still reads the images
+      e = cudaStreamWaitEvent(st, h.ev_side, 0);
+      side_busy = false;
+      if (e != cudaSuccess) break;
+    }
+    const int TI = (m + TM - 1) / TM, TJ = (m + TN - 1) / TN, mpad = TI * TM;
+    launch_prio(k_slice_wide, dim3((2 * mpad + 127) / 128, nb), dim3(128), 0, st, prio, (const double*)S,
+                (const double*)ew.Yw, n, K0, Wb, base, m, mpad, ew.A, ew.B, ew.sA, ew.sB, ts.s, ew.y_stride,
+                ew.img_stride, ew.scale_stride);
+    h.launches++;
+    const int nchunk = (Wb + kEwChunk - 1) / kEwChunk;
+    auto wide = [&](int jmode, cudaStream_t us, int uprio) -> cudaError_t {
+      int tasks = 0;
+      for (int I = 0; I < TI; I++) tasks += emu_row_tasks(I, TJ, jmode, 4);
+      if (tasks == 0) return cudaSuccess;
+      h.launches++;
+      const int c0 = jmode == 2 ? 4 * TN : 0, c1 = jmode == 1 ? 4 * TN : m;
+      const int kt = kt_begin(h, kFamEmuWide, nb * update_flops(m, c0, c1, Wb), us);
+      const cudaError_t le = launch_prio(k_tc_update_emu_wide, dim3(tasks, nb), dim3(kEmuThreads), ew_smem_bytes(),
+                                         us, uprio, S, n, base, m, TI, TJ, jmode, nchunk, (const uint8_t*)ew.A,
+                                         (const uint8_t*)ew.B, (const double*)ew.sA, (const double*)ew.sB, ts.s,
+                                         ew.img_stride, ew.scale_stride, h.dev_err);
+      kt_end(h, kt, us);
+      return le;
+    };
+    if (!side || TJ <= 4) {
+      e = wide(0, st, prio);
+      continue;
+    }
+    e = wide(1, st, prio);
+    if (e == cudaSuccess) e = cudaEventRecord(h.ev_main, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, h.ev_main, 0);
+    if (e == cudaSuccess) e = wide(2, side, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(h.ev_side, side);
+    side_busy = e == cudaSuccess;
+  }
+  if (side_busy && e == cudaSuccess) e = cudaStreamWaitEvent(caller, h.ev_side, 0);
+  if (st != caller && e == cudaSuccess) {
+    e = cudaEventRecord(h.ev_main, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, h.ev_main, 0);
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 // The TF32 factor of S with 256-wide outer panels (k_tc_update_wide above).
 // Per outer panel K0: its four 64-wide steps (diagonal block, panel with the
 // operand images in set c of the panel's parity, update of the panel's own
@@ -1147,8 +1574,18 @@ cudaError_t dense_tc_prepare() {
     e = cudaFuncSetAttribute(k_tc_update_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, emu_smem_bytes());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tc_update_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, wide_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_update_emu_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, ew_smem_bytes());
   return e;
 }
+
+int64_t emu_wide_image_bytes(int n) {
+  // 64-row blocks of the largest outer trailing matrix, in whole 128-row tiles
+  const int64_t rows = ((int64_t)n + TM - 1) / TM * TM + TM;
+  return rows / 64 * kEwBlockBytes;
+}
+
+bool emu_wide_applies(int npiv) { return npiv >= 2 * kEwW; }
 
 int64_t tf32_wide_set_bytes(int n) {
   // rows of one image set: the rows below an inner step, read in whole
@@ -1183,8 +1620,20 @@ cudaError_t launch_dense_ldlt_tc(Handle& h, int mode, unsigned long long* counte
   const TcStrides one{};
   cudaError_t e;
   if (mode == KKT_F64_EMULATED) {
-    e = factor_tc<2, double>(h, h.S, h.Ypanel, n, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
-                             h.tc_scaleA, h.tc_scaleB, st);
+    if (h.ew_s_A && !rend) {
+      EwBuffers ew;
+      ew.Yw = h.ew_s_Y;
+      ew.y_stride = (int64_t)n * kEwW;
+      ew.A = h.ew_s_A;
+      ew.B = h.ew_s_B;
+      ew.sA = h.ew_s_scale;
+      ew.sB = h.ew_s_scale + (n + 2 * TM);
+      e = factor_emu_wide(h, h.S, n, n, 1, one, PivotRule{}, counters, h.tc_imgA, h.tc_imgB, h.tc_scaleA, h.tc_scaleB,
+                          ew, st);
+    } else {
+      e = factor_tc<2, double>(h, h.S, h.Ypanel, n, n, 1, one, PivotRule{}, rend, counters, h.tc_imgA, h.tc_imgB,
+                               h.tc_scaleA, h.tc_scaleB, st);
+    }
     return e != cudaSuccess ? e : launch_diag_inverse(h, false, st);
   }
   const int64_t n2 = (int64_t)n * n;
@@ -1212,6 +1661,19 @@ cudaError_t launch_tail_factor_emulated(Handle& h, cudaStream_t st) {
   ts.img_b = tc_image_bytes(nTa, KKT_F64_EMULATED) - ts.img_a;
   ts.scale = (int64_t)nTa + 256;
   const PivotRule rule{h.anorm, h.opt.pivot_eps, h.d.col_primal + h.sym.tail_col};
+  if (h.ew_t_A) {
+    EwBuffers ew;
+    ew.Yw = h.ew_t_Y;
+    ew.y_stride = (int64_t)nTa * kEwW;
+    ew.A = h.ew_t_A;
+    ew.B = h.ew_t_B;
+    ew.img_stride = emu_wide_image_bytes(nTa);
+    ew.sA = h.ew_t_scale;
+    ew.sB = h.ew_t_scale + (nTa + 2 * TM);
+    ew.scale_stride = 2 * ((int64_t)nTa + 2 * TM);
+    return factor_emu_wide(h, h.Tt, nTa, h.nT, h.N, ts, rule, h.counters, h.t_imgA, h.t_imgB, h.t_scaleA,
+                           h.t_scaleB, ew, st);
+  }
   return factor_tc<2, double>(h, h.Tt, h.TY, nTa, h.nT, h.N, ts, rule, nullptr, h.counters, h.t_imgA,
                               h.t_imgB, h.t_scaleA, h.t_scaleB, st);
 }

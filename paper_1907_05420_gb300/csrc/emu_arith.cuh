@@ -98,6 +98,24 @@ KKT_HD unsigned long long digits7(double v, int e, long long& b) {
   return sh >= 0 ? (sh < 64 ? m << sh : 0ull) : (sh > -64 ? m >> (-sh) : 0ull);
 }
 
+// The 7 base-256 digits of q < 2^55 rebalanced into [-128, 128]: q =
+// sum_s d_s 256^(6 - s) with d_s in [-128, 127] for s >= 1 and d_0 in
+// [0, 128] (a digit of 128 or more borrows 256 from itself and carries one
+// into the next more significant digit; q < 2^55 keeps the top digit at most
+// 127 + 1).  Every digit product is then at most 2^14 in magnitude.
+KKT_HD void balanced7(unsigned long long q, int (&d)[kEmuSlices]) {
+  int carry = 0;
+  for (int s = kEmuSlices - 1; s >= 0; s--) {
+    int t = (int)((q >> (8 * (kEmuSlices - 1 - s))) & 0xFFull) + carry;
+    carry = 0;
+    if (s > 0 && t >= 128) {
+      t -= 256;
+      carry = 1;
+    }
+    d[s] = t;
+  }
+}
+
 // Biased exponent field of a double (0 for zero and subnormals).
 KKT_HD int exp_field(double v) { return (int)((bits_of(v) >> 52) & 0x7FF); }
 
@@ -163,33 +181,34 @@ KKT_HD double neg_scaled(long long W, int eoff) {
 // ---- tiles of the trailing update (128-row by 64-column tiles) ----
 // Tile (I, J) holds part of the lower triangle when J <= 2I + 1.  A task is a
 // run of at most kEmuRun consecutive tiles of one tile row; jmode 0 takes all
-// tiles, 1 the first tile column (J = 0), 2 the others.
+// tiles, 1 the first jsplit tile columns (J < jsplit: the next panel's
+// columns), 2 the others.
 constexpr int kEmuRun = 8;
 
 // tile columns [jlo, jhi) of tile row I for jmode
-KKT_HD void emu_row_range(int I, int TJ, int jmode, int& jlo, int& jhi) {
+KKT_HD void emu_row_range(int I, int TJ, int jmode, int& jlo, int& jhi, int jsplit = 1) {
   const int cnt = imin(2 * I + 2, TJ);
-  jlo = jmode == 2 ? 1 : 0;
-  jhi = jmode == 1 ? 1 : cnt;
+  jlo = jmode == 2 ? jsplit : 0;
+  jhi = jmode == 1 ? imin(jsplit, cnt) : cnt;
 }
 
-KKT_HD int emu_row_tasks(int I, int TJ, int jmode) {
+KKT_HD int emu_row_tasks(int I, int TJ, int jmode, int jsplit = 1) {
   int jlo, jhi;
-  emu_row_range(I, TJ, jmode, jlo, jhi);
+  emu_row_range(I, TJ, jmode, jlo, jhi, jsplit);
   return jhi > jlo ? (jhi - jlo + kEmuRun - 1) / kEmuRun : 0;
 }
 
 // task t (of the sum of emu_row_tasks over the TI rows) -> row I, tiles [j0, j1)
-KKT_HD void emu_task(int t, int TI, int TJ, int jmode, int& I, int& j0, int& j1) {
+KKT_HD void emu_task(int t, int TI, int TJ, int jmode, int& I, int& j0, int& j1, int jsplit = 1) {
   I = 0;
   for (;;) {
-    const int c = emu_row_tasks(I, TJ, jmode);
+    const int c = emu_row_tasks(I, TJ, jmode, jsplit);
     if (t < c || I + 1 >= TI) break;
     t -= c;
     I++;
   }
   int jlo, jhi;
-  emu_row_range(I, TJ, jmode, jlo, jhi);
+  emu_row_range(I, TJ, jmode, jlo, jhi, jsplit);
   j0 = jlo + t * kEmuRun;
   j1 = imin(j0 + kEmuRun, jhi);
 }

@@ -136,6 +136,14 @@ struct Handle {
   float* S32 = nullptr;       // nC * nC FP32 copy factored in the TF32/BF16 modes
   float* Y32 = nullptr;       // nC * kDenseNB FP32 panel scratch
   uint8_t* tw_img = nullptr;  // TF32 factor of S with 256-wide outer panels: 2 parities x (4 Y + 4 L21) image sets
+  // emulated-FP64 factors with 256-wide outer panels: Y of the outer panel,
+  // its 256-wide operand images and row scales (for S, and per block for the tails)
+  double* ew_s_Y = nullptr;
+  uint8_t *ew_s_A = nullptr, *ew_s_B = nullptr;
+  double* ew_s_scale = nullptr;
+  double* ew_t_Y = nullptr;
+  uint8_t *ew_t_A = nullptr, *ew_t_B = nullptr;
+  double* ew_t_scale = nullptr;
   int64_t tw_set_bytes = 0;   // bytes of one image set
   uint8_t* tc_imgA = nullptr; // tensor-core operand images of one panel step
   uint8_t* tc_imgB = nullptr;
@@ -199,7 +207,7 @@ struct Handle {
   int kt_graph_used = 0;  // timed launches inside the factor's graph
 };
 
-enum KernelFamily { kFamEmu = 0, kFamWide, kFamTc, kFamDenseF64, kFamFactorUpd, kFamDiag, kNumFamilies };
+enum KernelFamily { kFamEmu = 0, kFamWide, kFamTc, kFamDenseF64, kFamFactorUpd, kFamDiag, kFamEmuWide, kNumFamilies };
 // An event before a timed launch on `st` (returns its slot, -1 when not timing
 // or the pool is full) and one after it.
 int kt_begin(Handle& h, int fam, double flops, cudaStream_t st);
@@ -254,6 +262,8 @@ cudaError_t launch_dense_diag_panel_f64(Handle& h, int k0, int kb, int rend, uns
                                         cudaStream_t st);
 int64_t tc_image_bytes(int n, int mode);
 int64_t tf32_wide_set_bytes(int n);                 // one image set of the 256-wide TF32 factor of S
+int64_t emu_wide_image_bytes(int n);                // one operand image of the 256-wide emulated update, order n
+bool emu_wide_applies(int npiv);                    // whether the emulated factors take 256-wide outer panels
 bool tf32_wide_applies(int n, bool structured);     // whether that factor is used for S of order n
 // ---- (solve.cu) ----
 cudaError_t launch_apply_inverse(Handle& h, const double* rhs, double* out, cudaStream_t st);

@@ -6,8 +6,9 @@
 //   emu_arith_check neg    in out   (int64 W, int64 e)[n] -> float64[n]
 //   emu_arith_check digits in out   (float64 v, int64 e)[n] -> (uint64 q, int64 sign)[n]
 //   emu_arith_check pow2   in out   float64[n]          -> int64[n]
+//   emu_arith_check balanced in out int64 q[n] (q < 2^55) -> int64 d[n][7]
 //   emu_arith_check bf16   -  out                       -> uint32[256]
-//   emu_arith_check tasks  in out   (int64 TI, TJ, jmode)[n] -> per triple: count, then
+//   emu_arith_check tasks  in out   (int64 TI, TJ, jmode, jsplit)[n] -> per entry: count, then
 //                                   count x (I, j0, j1), all int64
 #include <cstdio>
 #include <cstring>
@@ -67,6 +68,15 @@ int main(int argc, char** argv) {
     }
     return write_all(argv[3], out) ? 0 : 1;
   }
+  if (!std::strcmp(mode, "balanced")) {
+    std::vector<int64_t> out;
+    for (int64_t q : read_all<int64_t>(argv[2])) {
+      int d[kkt::kEmuSlices];
+      kkt::balanced7((unsigned long long)q, d);
+      for (int s = 0; s < kkt::kEmuSlices; s++) out.push_back(d[s]);
+    }
+    return write_all(argv[3], out) ? 0 : 1;
+  }
   if (!std::strcmp(mode, "pow2")) {
     std::vector<int64_t> out;
     for (double s : read_all<double>(argv[2])) out.push_back(kkt::pow2_exponent(s));
@@ -75,14 +85,14 @@ int main(int argc, char** argv) {
   if (!std::strcmp(mode, "tasks")) {
     const std::vector<int64_t> in = read_all<int64_t>(argv[2]);
     std::vector<int64_t> out;
-    for (size_t i = 0; i + 2 < in.size(); i += 3) {
-      const int TI = (int)in[i], TJ = (int)in[i + 1], jmode = (int)in[i + 2];
+    for (size_t i = 0; i + 3 < in.size(); i += 4) {
+      const int TI = (int)in[i], TJ = (int)in[i + 1], jmode = (int)in[i + 2], jsplit = (int)in[i + 3];
       int total = 0;
-      for (int I = 0; I < TI; I++) total += kkt::emu_row_tasks(I, TJ, jmode);
+      for (int I = 0; I < TI; I++) total += kkt::emu_row_tasks(I, TJ, jmode, jsplit);
       out.push_back(total);
       for (int t = 0; t < total; t++) {
         int I, j0, j1;
-        kkt::emu_task(t, TI, TJ, jmode, I, j0, j1);
+        kkt::emu_task(t, TI, TJ, jmode, I, j0, j1, jsplit);
         out.push_back(I);
         out.push_back(j0);
         out.push_back(j1);

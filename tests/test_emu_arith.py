@@ -122,21 +122,22 @@ def test_bf16_table(prog):
     assert np.array_equal(got, want)
 
 
-def test_tile_runs_cover_the_lower_triangle_once(prog):
+@pytest.mark.parametrize("jsplit", [1, 4])
+def test_tile_runs_cover_the_lower_triangle_once(prog, jsplit):
     """The tasks of the emulated update (runs of at most 8 tiles of one tile
     row) cover every 128 x 64 tile holding part of the lower triangle exactly
-    once; the first tile column (jmode 1) and the rest (jmode 2) split the
-    full set (jmode 0) between them."""
+    once; the first jsplit tile columns (jmode 1: the next panel's 64 or 256
+    columns) and the rest (jmode 2) split the full set (jmode 0) between them."""
     ms = list(range(1, 3000, 37)) + [64, 127, 128, 129, 192, 255, 256, 1024, 7409]
     trip = []
     for m in ms:
         TI, TJ = -(-m // 128), -(-m // 64)
         for jmode in (0, 1, 2):
-            trip.append((TI, TJ, jmode))
+            trip.append((TI, TJ, jmode, jsplit))
     out = prog("tasks", np.array(trip, dtype=np.int64), np.int64).tolist()
     pos = 0
     sets = {}
-    for TI, TJ, jmode in trip:
+    for TI, TJ, jmode, _ in trip:
         cnt = out[pos]
         pos += 1
         tiles = []
@@ -152,5 +153,26 @@ def test_tile_runs_cover_the_lower_triangle_once(prog):
         TI, TJ = -(-m // 128), -(-m // 64)
         want = {(I, J) for I in range(TI) for J in range(TJ) if J <= 2 * I + 1}
         assert sets[(TI, TJ, 0)] == want
-        assert sets[(TI, TJ, 1)] == {t for t in want if t[1] == 0}
-        assert sets[(TI, TJ, 2)] == {t for t in want if t[1] >= 1}
+        assert sets[(TI, TJ, 1)] == {t for t in want if t[1] < jsplit}
+        assert sets[(TI, TJ, 2)] == {t for t in want if t[1] >= jsplit}
+
+
+def test_balanced_digits(prog):
+    """q < 2^55 rebalanced into 7 base-256 digits: the digits add up to q
+    exactly, the lower six lie in [-128, 127] and the top one in [0, 128], so
+    every product of two digits is at most 2^14 and 4 K = 256-term sums of
+    them stay at most 2^24 (exact in FP32)."""
+    rng = np.random.default_rng(6)
+    q = np.concatenate([rng.integers(0, 2**55, 200_000, dtype=np.int64),
+                        np.array([0, 1, 127, 128, 255, 256, 2**55 - 1, 2**55 - 2**48, 0x7F7F7F7F7F7F7F,
+                                  0x7F80808080808080 >> 8, 0x80808080808080 >> 1], dtype=np.int64)])
+    q = q[q < 2**55]
+    d = prog("balanced", q, np.int64).reshape(-1, 7)
+    w = np.array([256 ** (6 - s) for s in range(7)], dtype=object)
+    assert all(sum(int(x) * int(y) for x, y in zip(row, w)) == int(v) for row, v in zip(d[:5000], q[:5000]))
+    # all rows: compare in two exact int64 halves
+    lo = d[:, 4:] @ np.array([65536, 256, 1], dtype=np.int64)
+    hi = d[:, :4] @ np.array([2**24, 2**16, 2**8, 1], dtype=np.int64)
+    assert np.array_equal(hi * 2**24 + lo, q)
+    assert d[:, 1:].min() >= -128 and d[:, 1:].max() <= 127
+    assert d[:, 0].min() >= 0 and d[:, 0].max() <= 128

@@ -229,3 +229,35 @@ def test_tf32_wide_factor_matches_the_64_wide_one(case):
         x, info = xs[key]
         assert oracle.backward_error(p, x) <= 1e-10
         assert info["fell_back_fp64"] == 0, key
+
+
+@pytest.mark.parametrize("case", ["dense_c_1100", "dense_c_2000"])
+def test_emulated_wide_factor_matches_fp64(case):
+    """The emulated-FP64 factor of S with 256-wide outer panels (balanced
+    digits, K = 256 per epilogue) against the FP64 factor on the CUDA cores
+    and the 64-wide emulated factor (structured mode, full envelope), on a
+    well-conditioned dense S: all three are FP64-accurate, so they agree to a
+    few units of FP64 rounding times the growth of the factorization."""
+    torch = _torch()
+    from paper_1907_05420_gb300 import binding as B
+
+    p = _dense_c_system(int(case.split("_")[-1]), 11)
+    a, b, c, r = (_dev(torch, v) for v in (p.a_vals, p.b_vals, p.c_vals, p.rhs))
+    F = {}
+    for key, prec, st in (("wide", "f64emu", 0), ("w64", "f64emu", 1), ("f64", "fp64", 0)):
+        h = B.kkt_analyze(p, B.kkt_default_options(prec, structured_s=st))
+        try:
+            B.kkt_factor(h, a, b, c)
+            out = torch.empty(p.nC * p.nC, dtype=torch.float64, device="cuda:0")
+            B.kkt_schur_factor_copy(h, out)
+            x = torch.empty_like(r)
+            B.kkt_solve(h, r, x)
+            F[key] = np.tril(out.cpu().numpy().reshape(p.nC, p.nC).T)
+            assert oracle.backward_error(p, x.cpu().numpy()) <= 1e-14
+            info = B.kkt_get_info(h)
+            assert [info["n_pos"], info["n_neg"], info["n_zero"]] == [p.nP + p.nC, p.nA - p.nP, 0]
+        finally:
+            B.kkt_destroy(h)
+    scale = np.max(np.abs(F["f64"]))
+    assert np.max(np.abs(F["wide"] - F["f64"])) <= 1e-11 * scale
+    assert np.max(np.abs(F["wide"] - F["w64"])) <= 1e-11 * scale
