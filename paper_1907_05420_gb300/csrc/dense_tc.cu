@@ -446,7 +446,7 @@ __device__ __forceinline__ void bulk_load(uint8_t* dst, const uint8_t* src, int 
 }
 
 __global__ void __launch_bounds__(kEmuThreads, 1)
-    k_tc_update_emu(double* __restrict__ S0, int n, int k0, int kb, int m, int TI, int TJ, int jmode,
+    k_tc_update_emu(double* __restrict__ S0, int n, int k0, int kb, int m, int mcol, int TI, int TJ, int jmode,
                     const uint8_t* __restrict__ imgA0, const uint8_t* __restrict__ imgB0,
                     const double* __restrict__ scaleA0, const double* __restrict__ scaleB0, int* err,
                     TcStrides ts) {
@@ -645,12 +645,12 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
 #pragma unroll
           for (int j = 0; j < 16; j++) {
             const int cj = cj0 + hh * 16 + j, col = base + cj;
-            cur[j] = (cj < m && row >= col) ? S[(int64_t)row + (int64_t)col * n] : 0.0;
+            cur[j] = (cj < mcol && row >= col) ? S[(int64_t)row + (int64_t)col * n] : 0.0;
           }
 #pragma unroll
           for (int j = 0; j < 16; j++) {
             const int cj = cj0 + hh * 16 + j, col = base + cj;
-            if (cj < m && row >= col) S[(int64_t)row + (int64_t)col * n] = cur[j] + nd[hh * 16 + j];
+            if (cj < mcol && row >= col) S[(int64_t)row + (int64_t)col * n] = cur[j] + nd[hh * 16 + j];
           }
         }
       }
@@ -1324,7 +1324,7 @@ cudaError_t factor_tc(Handle& h, T* S, T* Y, int n, int npiv, int nb, const TcSt
         int tasks = 0;
         for (int I = 0; I < TI; I++) tasks += emu_row_tasks(I, TJ, jmode);
         le = launch_prio(k_tc_update_emu, dim3(tasks, nb), dim3(kEmuThreads), emu_smem_bytes(), us, uprio,
-                         (double*)S, n, k0, kb, m, TI, TJ, jmode, (const uint8_t*)imgA, (const uint8_t*)imgB,
+                         (double*)S, n, k0, kb, m, m, TI, TJ, jmode, (const uint8_t*)imgA, (const uint8_t*)imgB,
                          (const double*)scaleA, (const double*)scaleB, h.dev_err, ts);
       } else {
         const int cnt = jmode == 0 ? tiles : (jmode == 1 ? TI : tiles - TI);
@@ -1415,8 +1415,9 @@ cudaError_t factor_emu_wide(Handle& h, double* S, int n, int npiv, int nb, const
       int tasks = 0;
       for (int I = 0; I < TI; I++) tasks += emu_row_tasks(I, TJl, 0);
       const int kt = kt_begin(h, kFamEmu, nb * update_flops(m, 0, K0 + Wb - (k0 + kb), kb), st);
+      // columns past the outer panel (the augmented rows of a tail) belong to the outer update
       e = launch_prio(k_tc_update_emu, dim3(tasks, nb), dim3(kEmuThreads), emu_smem_bytes(), st, prio, S, n, k0, kb,
-                      m, TI, TJl, 0, (const uint8_t*)imgA, (const uint8_t*)imgB, (const double*)scaleA,
+                      m, K0 + Wb - (k0 + kb), TI, TJl, 0, (const uint8_t*)imgA, (const uint8_t*)imgB, (const double*)scaleA,
                       (const double*)scaleB, h.dev_err, ti);
       kt_end(h, kt, st);
       h.launches++;
