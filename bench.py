@@ -723,7 +723,7 @@ def run_single(args):
         st = timed[dom]
         sec = st["ms_total"] / 1e3
         sustained = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-        if dom == "k_tc_update_emu":
+        if dom in ("k_tc_update_emu", "k_tc_update_emu_wide"):
             bound, unit, peak = "tensor", "TFLOP/s", sustained
             achieved = EMU_PRODUCTS * st["flops"] / sec / 1e12
             src = (f"bf16_tflops_sustained of {peak_kind} peaks; achieved counts the {EMU_PRODUCTS:.0f} BF16 "

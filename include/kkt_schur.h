@@ -455,16 +455,17 @@ kkt_status kkt_server_destroy(kkt_server* s);
  * TF32/BF16 update (k_tc_update), 3 the FP64 dense update on the CUDA cores
  * (k_dense_update: S in KKT_FP64, the FP64 tails), 4 the supernodal updates of
  * the block factor (k_factor_update), 5 the dense diagonal blocks of the
- * blocked factors (k_dense_diag_t).  flops: the algorithmic FP64-equivalent
- * flops of the launches (2 per multiply-add on the entries of the lower
- * triangle they update; 0 where not counted). */
+ * blocked factors (k_dense_diag_t), 6 the emulated-FP64 update with K = 256
+ * of the 256-wide outer panels (k_tc_update_emu_wide).  flops: the
+ * algorithmic FP64-equivalent flops of the launches (2 per multiply-add on the
+ * entries of the lower triangle they update). */
 typedef struct {
   int64_t launches;     /* launches of the family in the handle's last factor (and fallback) */
   double ms_total;      /* sum of their device durations (CUDA events on their streams) */
   double ms_max;        /* the longest one */
   double flops;         /* their algorithmic flops */
 } kkt_kernel_stat;
-/* Statistics of family `family` (0..5); synchronizes the handle. */
+/* Statistics of family `family` (0..6); synchronizes the handle. */
 kkt_status kkt_kernel_stats(kkt_handle* h, int32_t family, kkt_kernel_stat* out);
 
 /* Measured FP64 FMA throughput of the current device in GFLOP/s (8

@@ -311,6 +311,18 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   // grouped by level, then those of the tail supernodes; for every (tile,
   // update) the rows [ia, ib) of the descendant that land in the tile
   std::vector<int32_t> fwork, twork, frange, flvl_sn;
+  // algorithmic flops of the updates of each work item: descendant d adds w_d
+  // multiply-adds to every target entry (row i, column j) of the tile with
+  // i >= j, i one of d's rows in the tile ([ia, ib)), j one in s's columns ([r0, r1))
+  double item_flops = 0.0;
+  auto pair_flops = [&](int64_t ia, int64_t ib, int64_t r0, int64_t r1, int64_t wd) {
+    double cnt = 0.0;
+    const int64_t a = std::max(ia, r0), z = std::min(ib, r1);  // i in [r0, r1): i - r0 + 1 targets
+    if (z > a) cnt += 0.5 * (double)(z - a) * (double)((a - r0 + 1) + (z - r0));
+    const int64_t a2 = std::max(ia, r1);  // i >= r1: all r1 - r0 targets
+    if (ib > a2) cnt += (double)(ib - a2) * (double)(r1 - r0);
+    return 2.0 * (double)wd * cnt;
+  };
   auto add_items = [&](int s, std::vector<int32_t>& items) {
     int m = (int)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]);
     for (int lo = 0; lo < m; lo += kFactorTileRows) {
@@ -326,22 +338,32 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
         const int32_t ib = S.upd_r0[u] + (int32_t)(std::lower_bound(rel, rel + nrel, hi) - rel);
         frange.push_back(ia);
         frange.push_back(ib);
+        const int dd = S.upd_src[u];
+        // the tail's own updates among its supernodes run in the dense tail factor
+        const bool counted = !(s >= S.tail_sn && u - S.upd_ptr[s] >= S.upd_ntail[s]);
+        if (counted)
+          item_flops += pair_flops(ia, ib, S.upd_r0[u], S.upd_r1[u], S.sn_first[dd + 1] - S.sn_first[dd]);
       }
     }
   };
   h->fwork_lvl_ptr.assign(S.nlevels + 1, 0);
   h->flvl_ptr.assign(S.nlevels + 1, 0);
+  h->fupd_flops.assign(S.nlevels, 0.0);
   for (int l = 0; l < S.nlevels; l++) {
+    item_flops = 0.0;
     for (int q = S.lvl_ptr[l]; q < S.lvl_ptr[l + 1]; q++) {
       const int s = S.lvl_sn[q];
       if (s >= S.tail_sn) continue;
       flvl_sn.push_back(s);
       add_items(s, fwork);
     }
+    h->fupd_flops[l] = item_flops;
     h->fwork_lvl_ptr[l + 1] = (int32_t)(fwork.size() / 4);
     h->flvl_ptr[l + 1] = (int32_t)flvl_sn.size();
   }
+  item_flops = 0.0;
   for (int s = S.tail_sn; s < S.nsuper; s++) add_items(s, twork);
+  h->tupd_flops = item_flops;
   h->tail_items = (int32_t)(twork.size() / 4);
   // per-column pivot position and primal flag
   std::vector<int64_t> col_dpos(n);

@@ -218,7 +218,7 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
     const int w0 = h.fwork_lvl_ptr[l], w1 = h.fwork_lvl_ptr[l + 1];
     if (l > 0 && w1 > w0) {
       dim3 grid(w1 - w0, h.N);
-      const int kt = kt_begin(h, kFamFactorUpd, 0.0, st);
+      const int kt = kt_begin(h, kFamFactorUpd, h.N * h.fupd_flops[l], st);
       k_factor_update<false><<<grid, 256, 0, st>>>(h.d.fwork + 4 * w0, h.d.frange, h.d, h.Lx, pt);
       kt_end(h, kt, st);
       h.launches++;
@@ -241,7 +241,7 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
     }
     if (h.tail_items > 0) {
       dim3 grid(h.tail_items, h.N);
-      const int kt = kt_begin(h, kFamFactorUpd, 0.0, st);
+      const int kt = kt_begin(h, kFamFactorUpd, h.N * h.tupd_flops, st);
       k_factor_update<true><<<grid, 256, 0, st>>>(h.d.twork, h.d.frange, h.d, h.Lx, pt);
       kt_end(h, kt, st);
       h.launches++;

@@ -111,6 +111,8 @@ struct Handle {
   std::vector<int32_t> reach_lvl_chunks, reach_lvl_chunks_nt;  // W solve: 32-column chunks per level
   int64_t g_nkeys = 0;                 // nonzero entries of the sparse contraction
   int32_t tail_items = 0;              // factor work items of the tail supernodes
+  std::vector<double> fupd_flops;      // algorithmic flops of one block's supernodal updates, per level
+  double tupd_flops = 0.0;             // and of the tail's updates from outside it
 
   // numeric buffers
   double* Lx = nullptr;       // N * panel_total
