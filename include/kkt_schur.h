@@ -141,6 +141,14 @@ typedef struct {
                            work, for kkt_kernel_stats.  Default 0. */
   double tail_ratio;    /* the cost ratio r of the dense tail (above); 0, the default, takes 1.5 or,
                            with autotune, the autotuner's choice.  Negative values are rejected. */
+  int32_t refine_mode;  /* 0 (default): iterative refinement, x += K~^{-1}(r - Kx) while the backward
+                           error falls at least by half per step; 1: GMRES refinement (FP64 GMRES on K,
+                           right-preconditioned by the factorization K~, restarted every gmres_restart
+                           iterations), which converges where the plain iteration stalls on a
+                           reduced-precision factor of an ill-conditioned S.  Both stop at refine_tol,
+                           count one step per application of K~^{-1} (at most max_refine) and, in the
+                           TF32/BF16 modes, refactor S FP64-accurately when they stop short. */
+  int32_t gmres_restart; /* Krylov vectors per GMRES cycle (default 8) */
 } kkt_options;
 
 typedef struct {

@@ -70,7 +70,7 @@ void free_all(Handle* h) {
                   h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red,
                   h->trsv_flags, h->trsv_ticket, h->dev_err, h->S32, h->Y32, h->tw_img, h->ew_s_Y, h->ew_s_A,
                   h->ew_s_B, h->ew_s_scale, h->ew_t_Y, h->ew_t_A, h->ew_t_B, h->ew_t_scale, h->tc_imgA,
-                  h->tc_imgB, h->tc_scaleA, h->tc_scaleB};
+                  h->tc_imgB, h->tc_scaleA, h->tc_scaleB, h->gm_V, h->gm_Z};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->host_red) cudaFreeHost(h->host_red);
@@ -167,6 +167,7 @@ void kkt_default_options(kkt_options* opt) {
   opt->use_graphs = 1;
   opt->fp64_fallback = 1;
   opt->dense_tail = -1;
+  opt->gmres_restart = 8;
 }
 
 const char* kkt_status_string(kkt_status s) {
@@ -215,6 +216,11 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   if (opt) h->opt = *opt;
   if (h->opt.prec < KKT_FP64 || h->opt.prec > KKT_F64_EMULATED) {
     set_error("kkt_analyze: unknown precision mode");
+    delete h;
+    return KKT_ERR_INVALID;
+  }
+  if ((h->opt.refine_mode != 0 && h->opt.refine_mode != 1) || h->opt.gmres_restart < 1 || h->opt.gmres_restart > 64) {
+    set_error("kkt_analyze: refine_mode must be 0 or 1 and gmres_restart in [1, 64]");
     delete h;
     return KKT_ERR_INVALID;
   }
@@ -540,7 +546,12 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   AL(dx, double, nK);
   AL(rho, double, nK);
   AL(rhs, double, nK);
-  AL(red, double, 128);
+  AL(red, double, 1024);
+  if (h->opt.refine_mode == 1) {
+    const int m = std::max(1, h->opt.gmres_restart);
+    AL(gm_V, double, (int64_t)(m + 1) * nK);
+    AL(gm_Z, double, (int64_t)m * nK);
+  }
   AL(trsv_flags, int, 2 * ((h->nC + kDenseNB - 1) / kDenseNB));
   if (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) {
     AL(S32, float, (int64_t)h->nC * h->nC);
@@ -701,6 +712,84 @@ kkt_status refactor_s_fp64(Handle* h, cudaStream_t st) {
   KKT_CUDA(launch_dense_ldlt_tc(*h, KKT_F64_EMULATED, h->counters + kNumCounters, st));
   h->s_factor = 0;
   h->info.fell_back_fp64 = 1;
+  return KKT_OK;
+}
+
+// One cycle of GMRES refinement (right preconditioning by the factorization
+// K~): from the residual rho = r - K x in h->rho, up to `budget` Krylov steps
+// z_j = K~^{-1} v_j, w = K z_j, modified Gram-Schmidt against v_0..v_j, Givens
+// rotations on the Hessenberg column; stops once the residual estimate |g_{j+1}|
+// (a 2-norm, so a bound on the infinity norm) is below `target`.  Then x +=
+// sum_j y_j z_j with H y = g solved on the host.  `its` receives the steps taken.
+kkt_status gmres_cycle(Handle* h, cudaStream_t st, double target, int budget, int& its) {
+  const int64_t nK = (int64_t)h->N * h->nA + h->nC;
+  const int m = std::min(budget, std::max(1, h->opt.gmres_restart));
+  double* V = h->gm_V;
+  double* Z = h->gm_Z;
+  its = 0;
+  auto dot = [&](const double* a, const double* b, double& out) -> kkt_status {
+    KKT_CUDA(launch_dot(*h, a, b, nK, h->red + 8, st));
+    KKT_CUDA(cudaMemcpyAsync(h->host_red + 6, h->red + 8, sizeof(double), cudaMemcpyDeviceToHost, st));
+    KKT_CUDA(cudaStreamSynchronize(st));
+    out = h->host_red[6];
+    return KKT_OK;
+  };
+  double beta2 = 0.0;
+  kkt_status ks = dot(h->rho, h->rho, beta2);
+  if (ks != KKT_OK) return ks;
+  const double beta = std::sqrt(beta2);
+  if (!(beta > 0.0) || !std::isfinite(beta)) return KKT_OK;
+  KKT_CUDA(launch_scale_into(*h, V, 1.0 / beta, h->rho, nK, st));
+  KKT_CUDA(cudaMemsetAsync(h->dx, 0, sizeof(double) * (size_t)nK, st));  // zero right-hand side for K z
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0);
+  auto Hc = [&](int i, int j) -> double& { return H[(size_t)j * (m + 1) + i]; };
+  g[0] = beta;
+  int k = 0;
+  for (int j = 0; j < m; j++) {
+    double* vj = V + (size_t)j * nK;
+    double* zj = Z + (size_t)j * nK;
+    double* u = V + (size_t)(j + 1) * nK;
+    KKT_CUDA(launch_apply_inverse(*h, vj, zj, st));
+    KKT_CUDA(launch_residual(*h, h->dx, zj, u, st));  // u = -K z_j
+    for (int i = 0; i <= j; i++) {
+      double d = 0.0;
+      ks = dot(u, V + (size_t)i * nK, d);
+      if (ks != KKT_OK) return ks;
+      Hc(i, j) = -d;  // (K z_j, v_i)
+      KKT_CUDA(launch_axpby(*h, u, -d, V + (size_t)i * nK, nK, st));  // u = -(w - sum h_ij v_i)
+    }
+    double hn2 = 0.0;
+    ks = dot(u, u, hn2);
+    if (ks != KKT_OK) return ks;
+    const double hn = std::sqrt(hn2);
+    Hc(j + 1, j) = hn;
+    k = j + 1;
+    its = k;
+    if (!std::isfinite(hn)) break;
+    if (hn > 0.0) KKT_CUDA(launch_scale_into(*h, u, -1.0 / hn, u, nK, st));
+    for (int i = 0; i < j; i++) {  // earlier rotations on the new column
+      const double t = cs[i] * Hc(i, j) + sn[i] * Hc(i + 1, j);
+      Hc(i + 1, j) = -sn[i] * Hc(i, j) + cs[i] * Hc(i + 1, j);
+      Hc(i, j) = t;
+    }
+    const double r = std::hypot(Hc(j, j), Hc(j + 1, j));
+    cs[j] = r > 0.0 ? Hc(j, j) / r : 1.0;
+    sn[j] = r > 0.0 ? Hc(j + 1, j) / r : 0.0;
+    Hc(j, j) = r;
+    Hc(j + 1, j) = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    if (std::fabs(g[j + 1]) <= target || hn == 0.0) break;
+  }
+  // back substitution R y = g, then x += Z y
+  std::vector<double> y(k, 0.0);
+  for (int i = k - 1; i >= 0; i--) {
+    double t = g[i];
+    for (int l = i + 1; l < k; l++) t -= Hc(i, l) * y[l];
+    y[i] = Hc(i, i) != 0.0 ? t / Hc(i, i) : 0.0;
+  }
+  for (int i = 0; i < k; i++)
+    if (y[i] != 0.0 && std::isfinite(y[i])) KKT_CUDA(launch_axpby(*h, h->x, y[i], Z + (size_t)i * nK, nK, st));
   return KKT_OK;
 }
 
@@ -956,6 +1045,16 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
         break;
       }
       eta_prev = eta;
+      if (h->opt.refine_mode == 1) {
+        // a cycle aims at the residual whose eta is half the target
+        int its = 0;
+        const kkt_status gs =
+            gmres_cycle(h, st, 0.5 * h->opt.refine_tol * (hr[3] * hr[1] + hr[2]), h->opt.max_refine - steps, its);
+        if (gs != KKT_OK) return gs;
+        if (its == 0) break;
+        steps += its;
+        continue;
+      }
       KKT_CUDA(launch_apply_inverse(*h, h->rho, h->dx, st));
       KKT_CUDA(launch_axpy(*h, h->x, h->dx, nK, st));
       steps++;

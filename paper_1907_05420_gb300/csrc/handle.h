@@ -167,7 +167,9 @@ struct Handle {
   double* dx = nullptr;       // nK correction
   double* rho = nullptr;      // nK residual
   double* rhs = nullptr;      // nK original right-hand side
-  double* red = nullptr;      // reduction scratch (norms)
+  double* red = nullptr;      // reduction scratch (norms; [16, 528) the dot products' partial sums)
+  double* gm_V = nullptr;     // GMRES refinement: gmres_restart + 1 Krylov vectors of nK
+  double* gm_Z = nullptr;     // and their preconditioned images (gmres_restart vectors)
   double* host_red = nullptr; // pinned
   int* trsv_flags = nullptr;  // 2 * ceil(nC/64): block-ready epochs of the dense triangular solves
   unsigned* trsv_ticket = nullptr;  // 2 tickets (forward, backward)
@@ -278,6 +280,10 @@ cudaError_t launch_knorm(Handle& h, cudaStream_t st);
 cudaError_t launch_axpy(Handle& h, double* y, const double* x, int64_t n, cudaStream_t st);
 cudaError_t launch_norms(Handle& h, const double* rho, const double* x, const double* rhs,
                          cudaStream_t st);
+// GMRES refinement: deterministic dot product into device *out (scratch red[16..16+512)), y += a x, y = a x
+cudaError_t launch_dot(Handle& h, const double* a, const double* b, int64_t n, double* out, cudaStream_t st);
+cudaError_t launch_axpby(Handle& h, double* y, double a, const double* x, int64_t n, cudaStream_t st);
+cudaError_t launch_scale_into(Handle& h, double* y, double a, const double* x, int64_t n, cudaStream_t st);
 
 // Solve work vectors supplied by the caller instead of the handle.
 struct SolveWorkspace {

@@ -416,6 +416,49 @@ __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, int
     y[q] += x[q];
 }
 
+// Deterministic dot products (a fixed reduction order for a given n): each
+// of kDotBlocks CTAs sums a strided part of the vectors in a fixed order and
+// reduces it by a tree; one CTA adds the partial sums by a tree.
+constexpr int kDotBlocks = 512;
+
+__global__ void __launch_bounds__(256) k_dot_partial(const double* __restrict__ a, const double* __restrict__ b,
+                                                     int64_t n, double* __restrict__ partial) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    acc += a[q] * b[q];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kDotBlocks) k_dot_final(const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double sh[kDotBlocks];
+  sh[threadIdx.x] = partial[threadIdx.x];
+  __syncthreads();
+  for (int s = kDotBlocks / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+// y += a x
+__global__ void k_axpby(double* __restrict__ y, double a, const double* __restrict__ x, int64_t n) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    y[q] += a * x[q];
+}
+
+// y = a x
+__global__ void k_scale_into(double* __restrict__ y, double a, const double* __restrict__ x, int64_t n) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    y[q] = a * x[q];
+}
+
 inline int grid_for(int64_t n, int bs = 256) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((n + bs - 1) / bs, 152 * 16));
 }
@@ -589,6 +632,25 @@ cudaError_t launch_norms(Handle& h, const double* rho, const double* x, const do
     k_norms3<<<grid_for(nK), 256, 0, st>>>(rho, x, rhs, nK, h.red);
     h.launches++;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(Handle& h, const double* a, const double* b, int64_t n, double* out, cudaStream_t st) {
+  k_dot_partial<<<kDotBlocks, 256, 0, st>>>(a, b, n, h.red + 16);
+  k_dot_final<<<1, kDotBlocks, 0, st>>>(h.red + 16, out);
+  h.launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(Handle& h, double* y, double a, const double* x, int64_t n, cudaStream_t st) {
+  k_axpby<<<grid_for(n), 256, 0, st>>>(y, a, x, n);
+  h.launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_into(Handle& h, double* y, double a, const double* x, int64_t n, cudaStream_t st) {
+  k_scale_into<<<grid_for(n), 256, 0, st>>>(y, a, x, n);
+  h.launches++;
   return cudaGetLastError();
 }
 
