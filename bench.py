@@ -462,6 +462,8 @@ def main():
     ap.add_argument("--resolve-frac", type=float, default=0.2)
     ap.add_argument("--serve-backlog", type=int, default=0,
                     help="requests outstanding before new arrivals are shed (default 4 x slots)")
+    ap.add_argument("--refine-mode", type=int, default=1, choices=[0, 1],
+                    help="FP64 refinement on K: 0 iterative refinement, 1 GMRES preconditioned by the factorization")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-slack", action="store_true", help="skip the slack-elimination measurement")
     ap.add_argument("--autotune", type=int, default=-1,
@@ -597,7 +599,7 @@ def run_single(args):
     def analyze(mode, time_kernels=0):
         prec, opts, tol = parse_leg(mode)
         kw = dict(opts, autotune=autotune, early_solve=1, time_kernels=time_kernels,
-                  tail_ratio=0.0 if autotune else wd["tail_ratio"])
+                  tail_ratio=0.0 if autotune else wd["tail_ratio"], refine_mode=args.refine_mode)
         if tol is not None:
             kw["refine_tol"] = tol
         return B.kkt_analyze(prob, B.kkt_default_options(prec, **kw))
@@ -798,6 +800,7 @@ def run_single(args):
         "dtype": {"fp64": "f64", "tf32": "f64+tf32", "bf16": "f64+bf16", "f64emu": "f64+bf16x7"}[args.prec],
         "data": "synthetic",
         "config": {"workload": workload_desc(args.workload), "precision": args.prec,
+                   "refinement": ["iterative", "gmres"][args.refine_mode],
                    "l2": "256 MB buffer written before every timed step (inputs also exceed L2)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},

@@ -1046,10 +1046,11 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
       }
       eta_prev = eta;
       if (h->opt.refine_mode == 1) {
-        // a cycle aims at the residual whose eta is half the target
+        // a cycle aims at the residual whose eta is the target (its 2-norm
+        // estimate bounds the infinity norm the test uses)
         int its = 0;
         const kkt_status gs =
-            gmres_cycle(h, st, 0.5 * h->opt.refine_tol * (hr[3] * hr[1] + hr[2]), h->opt.max_refine - steps, its);
+            gmres_cycle(h, st, h->opt.refine_tol * (hr[3] * hr[1] + hr[2]), h->opt.max_refine - steps, its);
         if (gs != KKT_OK) return gs;
         if (its == 0) break;
         steps += its;

@@ -87,3 +87,31 @@ def test_structured_s_equals_dense(prec):
             assert np.array_equal(xd, xs)
             assert [infd["n_pos"], infd["n_neg"]] == [infs["n_pos"], infs["n_neg"]]
         assert oracle.backward_error(p, xs) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("name", ["small", "grid30_n24"])
+def test_gmres_refinement_matches_oracle(name, prec):
+    """GMRES refinement (refine_mode 1) meets the same parity bar as the plain
+    iteration: eta <= 1e-10 and the oracle's solution within 10 kappa max(eta, eps)."""
+    p = make_problem(CONFIGS[name])
+    x, info = gpu_solve(p, prec, refine_mode=1)
+    check_against_oracle(p, x, info, np.linalg.cond(dense_K(p)), inertia=bool(info["fell_back_fp64"]))
+
+
+def test_gmres_refinement_reaches_a_tight_tolerance_without_fallback():
+    """On the 2,383-bus grid over 6 periods the plain iteration with the TF32
+    factor of S stalls above 1e-13 and falls back to the FP64-accurate factor;
+    GMRES refinement with the same factor reaches it (8 applications measured),
+    and two solves give bitwise the same solution."""
+    p = make_problem(replace(CONFIGS["grid2383_n96"], n_per=6))
+    xs = []
+    for _ in range(2):
+        x, info = gpu_solve(p, "tf32", refine_mode=1, refine_tol=1e-13, max_refine=12)
+        assert info["fell_back_fp64"] == 0
+        assert info["rel_residual"] <= 1e-13
+        assert oracle.backward_error(p, x) <= 1e-13
+        xs.append(x)
+    assert np.array_equal(xs[0], xs[1])
+    x0, info0 = gpu_solve(p, "tf32", refine_mode=0, refine_tol=1e-13, max_refine=12)
+    assert info0["fell_back_fp64"] == 1 and oracle.backward_error(p, x0) <= 1e-13
