@@ -357,31 +357,45 @@ def run_batch(args):
     return 0
 
 
-def run_serve(args):
-    """Poisson request stream over the size mix; p50/p99 latency and solves/s per rate."""
+def serve_sweep(args, precs, rates, seconds, pool=64):
+    """A Poisson stream of KKT solve requests over the 64-instance size mix
+    (configs[3]'s recipe) through the server's pattern cache: each request
+    names a mix pattern; with probability resolve_frac it re-solves a pattern
+    already seen with fresh barrier diagonals and right-hand side, else it
+    solves the instance as drawn.  A pattern is analysed at its first request
+    (inside that request's latency) and stays resident; admission of a new
+    pattern is by free device memory.  Latency: submit to completion of the
+    refined solve; requests arriving while `backlog` are outstanding are shed.
+    Returns per precision and rate: offered, served, shed, solves/s, p50/p99."""
     import numpy as np
     import torch
 
+    from gen import make_problem, mix_spec, reseed_barrier
     from paper_1907_05420_gb300 import binding as B
 
-    out = {"metric": "KKT solves/s and p50/p99 latency under a Poisson request stream", "unit": "solves/s",
-           "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-           "config": {"workload": f"serve: {args.serve_pool} resident patterns from the size mix; "
-                                  "Poisson arrivals",
-                      "slots": args.serve_slots, "seconds_per_rate": args.serve_seconds,
-                      "backlog": args.serve_backlog or 4 * args.serve_slots}}
-    for prec in args.batch_precs.split(","):
-        probs, hs, vals, xs = _mix_problems(args.serve_pool, prec)
-        srv = B.KKTServer(slots=args.serve_slots,
-                          device_budget_bytes=int(0.8 * torch.cuda.mem_get_info()[0]))
+    dev = torch.device("cuda:0")
+    up = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(dev)  # noqa: E731
+    probs = [make_problem(mix_spec(k)) for k in range(pool)]
+    fresh = [reseed_barrier(p, 4242 + k) for k, p in enumerate(probs)]
+    vals = [[(up(q.a_vals), up(q.b_vals), up(q.c_vals), up(q.rhs)) for q in (p, f)] for p, f in zip(probs, fresh)]
+    pats = [B.make_pattern(p) for p in probs]
+    backlog = args.serve_backlog or 4 * args.serve_slots
+    out = {"workload": f"{pool}-instance size mix (118-3,000 buses, N in {{12,24,48,96}}); Poisson arrivals; "
+                       f"{int(100 * args.resolve_frac)}% re-solves of a seen pattern with fresh barrier diagonals; "
+                       "patterns analysed at first request, resident after, admitted by free HBM",
+           "slots": args.serve_slots, "seconds_per_rate": seconds, "backlog": backlog,
+           "refinement": ["iterative", "gmres"][args.refine_mode]}
+    for prec in precs:
+        srv = B.KKTServer(slots=args.serve_slots)
+        srv.set_cache(B.kkt_default_options(prec, refine_mode=args.refine_mode), reserve_bytes=8 << 30)
         rng = np.random.default_rng(4242)
+        seen = set()
         res = {}
-        backlog = args.serve_backlog or 4 * args.serve_slots
-        for rate in [float(q) for q in args.rates.split(",")]:
+        for rate in rates:
             lats, outstanding = [], {}
             shed = offered = 0
             t0 = time.perf_counter()
-            t_measure, t_end = t0 + 1.0, t0 + 1.0 + args.serve_seconds
+            t_measure, t_end = t0 + 0.5, t0 + 0.5 + seconds
             t_next = t0
 
             def reap(block):
@@ -389,8 +403,9 @@ def run_serve(args):
                     got = srv.wait(rid) if block else srv.poll(rid)
                     if got is None:
                         continue
-                    if outstanding.pop(rid):
-                        lats.append(got[1])
+                    st, lat = got
+                    if outstanding.pop(rid) and st in (0, 6):
+                        lats.append(lat)
 
             while time.perf_counter() < t_end:
                 now = time.perf_counter()
@@ -404,10 +419,14 @@ def run_serve(args):
                 if len(outstanding) >= backlog:
                     shed += in_window
                     continue
-                kq = int(rng.integers(0, len(probs)))
-                a, b, c, r = vals[kq]
+                if seen and rng.random() < args.resolve_frac:
+                    k, v = int(rng.choice(sorted(seen))), 1
+                else:
+                    k, v = int(rng.integers(0, pool)), 0
+                seen.add(k)
+                a, b, c, r = vals[k][v]
                 x = torch.empty_like(r)
-                outstanding[srv.submit(hs[kq], a, b, c, r, x)] = in_window
+                outstanding[srv.submit_pattern(k, probs[k], a, b, c, r, x, pattern=pats[k])] = in_window
             reap(True)
             t_done = time.perf_counter()
             n = len(lats)
@@ -415,12 +434,21 @@ def run_serve(args):
                                    "solves_per_s": n / max(1e-9, t_done - t_measure),
                                    "p50_ms": float(np.percentile(lats, 50)) if n else None,
                                    "p99_ms": float(np.percentile(lats, 99)) if n else None}
+        res["cache"] = srv.cache_info()
         srv.close()
-        for h in hs:
-            B.kkt_destroy(h)
         out[prec] = res
-    out["value"] = max(v["solves_per_s"] for v in out[args.batch_precs.split(",")[0]].values())
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def run_serve(args):
+    """Poisson request stream over the size mix; p50/p99 latency and solves/s per rate."""
+    rates = [float(q) for q in args.rates.split(",")]
+    sw = serve_sweep(args, args.batch_precs.split(","), rates, args.serve_seconds)
+    first = sw[args.batch_precs.split(",")[0]]
+    line = {"metric": "KKT solves/s and p50/p99 latency under a Poisson request stream", "unit": "solves/s",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "config": {"workload": sw["workload"]},
+            "value": max(v["solves_per_s"] for k, v in first.items() if k != "cache"), "serving": sw}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -466,6 +494,9 @@ def main():
                     help="FP64 refinement on K: 0 iterative refinement, 1 GMRES preconditioned by the factorization")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-slack", action="store_true", help="skip the slack-elimination measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving sweep of the default run")
+    ap.add_argument("--serve-seconds-default", type=float, default=2.0,
+                    help="measured seconds per rate of the serving sweep inside the default run")
     ap.add_argument("--autotune", type=int, default=-1,
                     help="dense-tail autotuning at analysis: 1 on, 0 off, -1 the workload's default")
     args = ap.parse_args()
@@ -704,6 +735,10 @@ def run_single(args):
                      "accuracy": acc, "phases_ms": {kk: statistics.mean(v) for kk, v in lr["phases"].items()}}
 
     slack = None if args.no_slack else slack_timing(args, dev, stream, torch, np, B)
+    serving = None
+    if not args.no_serve and world == 1:
+        serving = serve_sweep(args, ["tf32", "fp64"], [float(q) for q in args.rates.split(",")],
+                              args.serve_seconds_default)
 
     # ---- forward errors against the FP64-accurate solutions of this run
     ref_leg = next((m for m in ("fp64+band", "fp64", "f64emu") if m in xs), None)
@@ -813,6 +848,7 @@ def run_single(args):
                        "augmented": bool(info0["tail_augmented"]),
                        "autotune_candidates": info0["autotune_candidates"]},
         "device_bytes": info0["device_bytes"], "other_precisions": legs, "slack_elimination": slack,
+        "serving": serving,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], out = cpu_baseline_sample(args.workload, prob, info0["factor_flops"])

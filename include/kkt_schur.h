@@ -453,8 +453,26 @@ kkt_status kkt_server_submit(kkt_server* s, kkt_handle* h, const double* a_vals,
  * uncollected gives KKT_ERR_INVALID (instead of waiting forever). */
 kkt_status kkt_server_poll(kkt_server* s, int64_t request_id, int32_t wait, kkt_status* status,
                            double* latency_ms);
-/* Drains the queue, joins the workers and frees the streams. */
+/* Drains the queue, joins the workers and frees the streams (and the cached handles). */
 kkt_status kkt_server_destroy(kkt_server* s);
+/* A pattern cache: requests submitted with kkt_server_submit_pattern name a
+ * pattern by a caller-chosen key >= 0; the server analyses the pattern (with
+ * options opt, NULL for the defaults) at the first request on the key, inside
+ * that request's latency, and keeps the handle resident for later requests on
+ * the key.  Admission of a new pattern is by free device memory: before an
+ * analysis, while cudaMemGetInfo reports less than reserve_bytes free, the
+ * idle resident handle used least recently is destroyed; an analysis that
+ * still runs out of memory evicts one more and retries, and fails with
+ * KKT_ERR_OOM once none is left.  Call before the first pattern request. */
+kkt_status kkt_server_set_cache(kkt_server* s, const kkt_options* opt, int64_t reserve_bytes);
+/* Queue one KKT solve of the pattern `key` (the pattern's arrays and the
+ * values must stay valid until the request completes; the pattern is read only
+ * at the key's first request or after an eviction). */
+kkt_status kkt_server_submit_pattern(kkt_server* s, int64_t key, const kkt_pattern* pat, const double* a_vals,
+                                     const double* b_vals, const double* c_vals, const double* rhs, double* x,
+                                     int32_t on_device, int64_t* request_id);
+/* Resident patterns, analyses done and handles evicted so far. */
+kkt_status kkt_server_cache_info(kkt_server* s, int64_t* resident, int64_t* analyses, int64_t* evictions);
 
 /* ---- per-kernel device times (with kkt_options.time_kernels) ----
  * Families: 0 the emulated-FP64 trailing update (k_tc_update_emu: dense tails

@@ -82,7 +82,7 @@ EXPORTS = ["kkt_default_options", "kkt_analyze", "kkt_factor", "kkt_solve", "kkt
            "kkt_factor_blocks", "kkt_schur_matrix", "kkt_factor_schur", "kkt_schur_factor_copy", "kkt_accumulate",
            "kkt_solve_front", "kkt_solve_coupling", "kkt_solve_back", "kkt_residual", "kkt_abs_rowsums",
            "kkt_norm_inf", "kkt_kernel_stats", "kkt_slack_create", "kkt_slack_reduce", "kkt_slack_recover",
-           "kkt_slack_destroy"]
+           "kkt_slack_destroy", "kkt_server_set_cache", "kkt_server_submit_pattern", "kkt_server_cache_info"]
 
 KERNEL_FAMILIES = ["k_tc_update_emu", "k_tc_update_wide", "k_tc_update", "k_dense_update", "k_factor_update",
                    "k_dense_diag_t", "k_tc_update_emu_wide"]
@@ -176,6 +176,13 @@ def load(build_if_missing: bool = True):
     L.kkt_slack_recover.restype = C.c_int
     L.kkt_slack_destroy.argtypes = [vp]
     L.kkt_slack_destroy.restype = C.c_int
+    L.kkt_server_set_cache.argtypes = [vp, C.POINTER(kkt_options), C.c_int64]
+    L.kkt_server_set_cache.restype = C.c_int
+    L.kkt_server_submit_pattern.argtypes = [vp, C.c_int64, C.POINTER(kkt_pattern), vp, vp, vp, vp, vp, C.c_int32,
+                                            C.POINTER(C.c_int64)]
+    L.kkt_server_submit_pattern.restype = C.c_int
+    L.kkt_server_cache_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.kkt_server_cache_info.restype = C.c_int
     _lib = L
     return L
 
@@ -224,12 +231,9 @@ def kkt_default_options(prec="fp64", **kw) -> kkt_options:
     return opt
 
 
-def kkt_analyze(prob, opt: kkt_options | None = None, hint=True):
-    """Analyze the pattern of `prob` (any object with the KKTProblem fields).
-
-    Returns an opaque handle (int).  Host arrays are read during the call only.
-    """
-    L = load()
+def make_pattern(prob, hint=True):
+    """(kkt_pattern, the arrays it points to) of `prob`; keep both alive while
+    the pattern may be read."""
     keep = {
         "a_rowptr": np.ascontiguousarray(prob.a_rowptr, dtype=np.int32),
         "a_col": np.ascontiguousarray(prob.a_col, dtype=np.int32),
@@ -245,10 +249,22 @@ def kkt_analyze(prob, opt: kkt_options | None = None, hint=True):
                       keep["b_blockptr"].ctypes.data, keep["b_row"].ctypes.data,
                       keep["b_col"].ctypes.data, int(prob.c_kind),
                       hint_arr.ctypes.data if hint_arr is not None else None)
+    keep["hint"] = hint_arr
+    return pat, keep
+
+
+def kkt_analyze(prob, opt: kkt_options | None = None, hint=True):
+    """Analyze the pattern of `prob` (any object with the KKTProblem fields).
+
+    Returns an opaque handle (int).  Host arrays are read during the call only.
+    """
+    L = load()
+    pat, keep = make_pattern(prob, hint)
     if opt is None:
         opt = kkt_default_options()
     h = C.c_void_p()
     _check(L.kkt_analyze(C.byref(pat), C.byref(opt), C.byref(h)))
+    del keep
     return h.value
 
 
@@ -461,6 +477,29 @@ class KKTServer:
         _check(load().kkt_server_submit(self.s, h, *[p for p, _ in ptrs], dev.pop(), C.byref(rid)))
         self._keep[rid.value] = (a_vals, b_vals, c_vals, rhs, x)
         return rid.value
+
+    def set_cache(self, opt: kkt_options | None = None, reserve_bytes=0):
+        """Pattern cache with admission by free device memory (kkt_server_set_cache)."""
+        _check(load().kkt_server_set_cache(self.s, C.byref(opt) if opt is not None else None, int(reserve_bytes)))
+
+    def submit_pattern(self, key, prob, a_vals, b_vals, c_vals, rhs, x, pattern=None):
+        """Queue a solve of cached pattern `key` (prob's pattern; `pattern` may
+        pass a (kkt_pattern, arrays) pair from make_pattern to reuse it)."""
+        pat, keep = pattern if pattern is not None else make_pattern(prob)
+        ptrs = [_ptr(v) for v in (a_vals, b_vals, c_vals, rhs, x)]
+        dev = {d for _, d in ptrs}
+        if len(dev) > 1:
+            raise ValueError("all arrays must be host arrays or all device arrays")
+        rid = C.c_int64()
+        _check(load().kkt_server_submit_pattern(self.s, int(key), C.byref(pat), *[p for p, _ in ptrs], dev.pop(),
+                                                C.byref(rid)))
+        self._keep[rid.value] = (pat, keep, a_vals, b_vals, c_vals, rhs, x)
+        return rid.value
+
+    def cache_info(self):
+        res, an, ev = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(load().kkt_server_cache_info(self.s, C.byref(res), C.byref(an), C.byref(ev)))
+        return {"resident": res.value, "analyses": an.value, "evictions": ev.value}
 
     def wait(self, rid):
         st, lat = C.c_int(), C.c_double()

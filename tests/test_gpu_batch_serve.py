@@ -116,3 +116,49 @@ def test_server_budget_below_one_handle_still_progresses():
             B.kkt_destroy(h)
     for p, x in zip(probs, xs):
         assert oracle.backward_error(p, x) <= 1e-10
+
+
+@pytest.mark.parametrize("reserve", ["none", "all"])
+def test_server_pattern_cache_equals_alone(reserve):
+    """Requests that name patterns: the server analyses each key at its first
+    request and re-solves later requests on the resident handle.  With no
+    reserve nothing is evicted; with a reserve larger than the device every new
+    analysis first evicts the idle handles, so repeated keys are analysed
+    again.  Either way each result is bitwise the standalone solve."""
+    _torch()
+    from paper_1907_05420_gb300 import binding as B
+
+    base = _mix(4, seed0=1700)
+    reqs = []
+    for rep in range(2):
+        for i, p in enumerate(base):
+            reqs.append((i, p if rep == 0 else reseed_barrier(p, 300 + i)))
+    srv = B.KKTServer(slots=3)
+    srv.set_cache(B.kkt_default_options("tf32"), 0 if reserve == "none" else 1 << 62)
+    pats = [B.make_pattern(p) for p in base]
+    try:
+        outs, ids = [], []
+        for i, p in reqs:
+            x = np.empty(p.nK)
+            outs.append(x)
+            ids.append(srv.submit_pattern(i, p, np.ascontiguousarray(p.a_vals), p.b_vals, p.c_vals,
+                                          np.ascontiguousarray(p.rhs), x, pattern=pats[i]))
+        for rid in ids:
+            assert srv.wait(rid)[0] == 0
+        info = srv.cache_info()
+    finally:
+        srv.close()
+    if reserve == "none":
+        assert info["analyses"] == len(base) and info["evictions"] == 0 and info["resident"] == len(base)
+    else:
+        assert info["evictions"] > 0 and info["analyses"] >= len(base)
+    alone = []
+    for i, p in reqs:
+        h = B.kkt_analyze(base[i], B.kkt_default_options("tf32"))
+        try:
+            alone.append(_alone(B, h, p))
+        finally:
+            B.kkt_destroy(h)
+    for (i, p), xs, xa in zip(reqs, outs, alone):
+        assert np.array_equal(xs, xa)
+        assert oracle.backward_error(p, xs) <= 1e-10
