@@ -178,7 +178,7 @@ def _topology(rng, nb, nl):
 
 
 def make_problem(spec: GridSpec, *, zero_b: bool = False, coupling: str = "adjacent",
-                 flow_limits: int = 0) -> KKTProblem:
+                 flow_limits: int = 0, own_period_scale: float = 1.0) -> KKTProblem:
     """Build the seeded instance described by ``spec``.
 
     flow_limits=L > 0 appends L inequality rows to every A_i, after the other
@@ -201,6 +201,11 @@ def make_problem(spec: GridSpec, *, zero_b: bool = False, coupling: str = "adjac
     puts period i's charge and discharge into the energy constraints of every
     period m >= i (coefficients eta_c and -1/eta_d), so S is dense and
     negative definite and K's inertia is (N nP, N nD + nC, 0).
+    own_period_scale (paper coupling only) multiplies the coefficient of
+    period i's charging power in period i's own energy constraint, so that
+    the block of B_i for its own period (the paper's C_1) differs from the one
+    repeated for the later periods (C_0) and is not a multiple of it; 1.0
+    (the default) keeps them equal.
     """
     if coupling not in ("adjacent", "paper"):
         raise ValueError("coupling must be 'adjacent' or 'paper'")
@@ -310,7 +315,7 @@ def make_problem(spec: GridSpec, *, zero_b: bool = False, coupling: str = "adjac
                 for m in range(i, N):
                     br.append(row)
                     bc.append(m * ns + s)
-                    bv.append(coef)
+                    bv.append(coef * own_period_scale if (m == i and row >= PC) else coef)
             bp.append(len(br))
     else:
         # B_i: dynamics row s couples eps_{i,s} (+1) and eps_{i-1,s} (-1)

@@ -10,6 +10,7 @@ the paper defines:
                              (minimum degree on the explicit elimination graph);
 * ``ldlt_dense``          -- A = P L D L^T P^T, 1x1 pivots (block factorization, Algorithm 1);
 * ``sparse_solve``        -- A^{-1} b from that factor;
+* ``sparse_solve_multi``  -- A^{-1} B for several columns, one factorization;
 * ``dense_ldlt``          -- S = L_s D_s L_s^T, no pivoting (dense factor of S, Algorithm 1);
 * ``kkt_solve``           -- eqs. SCform, SCsolve, SCsolve1 in sequence,
                              S by one full solve per nonzero column of B_i
@@ -57,6 +58,8 @@ def lib():
         L.orc_ldlt_dense.restype = C.c_int
         L.orc_sparse_solve.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _i32p, _f64p, _f64p]
         L.orc_sparse_solve.restype = C.c_int
+        L.orc_sparse_solve_multi.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _i32p, C.c_int32, _f64p, _f64p]
+        L.orc_sparse_solve_multi.restype = C.c_int
         L.orc_dense_ldlt.argtypes = [C.c_int64, _f64p, _i64p]
         L.orc_dense_ldlt.restype = C.c_int
         L.orc_dense_ldlt_solve.argtypes = [C.c_int64, _f64p, _f64p]
@@ -128,6 +131,16 @@ def sparse_solve(n, rowptr, col, vals, perm, b):
     x = np.empty(n)
     _check(lib().orc_sparse_solve(n, _i32(rowptr), _i32(col), _f64(vals), _i32(perm), _f64(b), x))
     return x
+
+
+def sparse_solve_multi(n, rowptr, col, vals, perm, B):
+    """X = A^{-1} B for the columns of the n x m array B (one factorization)."""
+    Bc = np.asfortranarray(np.asarray(B, dtype=np.float64).reshape(n, -1))
+    m = Bc.shape[1]
+    flat = np.ascontiguousarray(Bc.T).reshape(-1)
+    X = np.empty(n * m)
+    _check(lib().orc_sparse_solve_multi(n, _i32(rowptr), _i32(col), _f64(vals), _i32(perm), m, flat, X))
+    return X.reshape(m, n).T.copy()
 
 
 def dense_ldlt(S):

@@ -429,6 +429,30 @@ int orc_sparse_solve(int32_t n, const int32_t *rowptr, const int32_t *col, const
   return rc;
 }
 
+/* X = A^{-1} B for nrhs right-hand sides (column j of B and X at j * n): one
+   factorization, then the solve of algorithm 1's local systems per column. */
+int orc_sparse_solve_multi(int32_t n, const int32_t *rowptr, const int32_t *col, const double *vals,
+                           const int32_t *perm, int32_t nrhs, const double *B, double *X) {
+  orc_symbolic s;
+  orc_numeric f;
+  if (nrhs < 0) return ORC_ERR_INVALID;
+  int rc = sym_analyze(n, rowptr, col, perm, &s);
+  if (rc) return rc;
+  rc = num_alloc(&s, &f);
+  if (!rc) rc = num_factor(&s, vals, &f);
+  if (!rc) {
+    double *w = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!w) rc = ORC_ERR_NOMEM;
+    else {
+      for (int32_t j = 0; j < nrhs; j++) num_solve(&s, &f, B + (size_t)j * n, X + (size_t)j * n, w);
+      free(w);
+    }
+  }
+  num_free(&f);
+  sym_free(&s);
+  return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* 4. dense LDL^T of S (Crout form), in place, row-major full storage   */
 /* ------------------------------------------------------------------ */
