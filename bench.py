@@ -43,8 +43,12 @@ TF32_RATIO = 1.1 / 2.25
 # the emulated-FP64 update issues 28 BF16 digit products per FP64 multiply-add
 EMU_PRODUCTS = 28.0
 # DRAM bytes per launch of the dominant kernel, from an ncu capture of the same
-# kernel code (profiles/); None where no capture of the current kernel exists
-TRAFFIC = {}
+# kernel code (profiles/); None where no capture of the current kernel exists.
+# k_tc_update_emu_wide on the 9,241-bus grid: all 56 launches of one factor of
+# the 8-period system read 25.99 GB and wrote 14.85 GB; every launch updates the
+# same tail in each of its blocks (each tail, 439 MB, exceeds L2), so a launch
+# over 168 blocks moves 168 / 8 times as much: 40.84 GB * 21 / 56 per launch.
+TRAFFIC = {("grid9241_n168", "k_tc_update_emu_wide"): 40.839235840e9 * 21 / 56}
 
 
 def workload_desc(name):
