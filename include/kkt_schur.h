@@ -105,11 +105,26 @@ typedef struct {
                                   G_i = W_i^T D_i^{-1} W_i on the tensor cores in that precision
                                   (0, the default: FP64 contraction).  On a stall the fallback then
                                   recomputes G in FP64 and reassembles S before refactoring it. */
-  int32_t structured_s; /* limit the dense factor of S and its solves to S's row envelope
+  int32_t structured_s; /* 0 (default): S dense, factored and solved whole.
+                           1: limit the dense factor of S and its solves to S's row envelope
                            (LDL^T without pivoting creates no fill outside it): the same
                            arithmetic on every entry that can be nonzero, the exact zeros outside
                            skipped.  For the adjacent-period coupling S is block-tridiagonal and
-                           the cost drops from n_C^3/3 to ~ n_C (2 n_stor)^2.  Default 0. */
+                           the cost drops from n_C^3/3 to ~ n_C (2 n_stor)^2.
+                           2: the paper's structured S for its cumulative MPOPF coupling (Sec. 4.3,
+                           eqs. LocalSchurBs, LocalSchurBs3, GlobalSchur): the coupling variables
+                           are ordered by period, n_s = n_C / N per period, block i's coupling
+                           columns of period m are zero for m < i and equal (pattern and values)
+                           for all m > i, and C is diagonal (c_kind 0); kkt_analyze returns
+                           KKT_ERR_INVALID for a pattern without that structure.  S is then
+                           kept as two block vectors (S_d: N diagonal n_s x n_s blocks, S_o: the
+                           block repeated below the diagonal in each block column), assembled
+                           from the N local blocks, factored in FP64 in every precision mode
+                           by N partial LDL^T steps of order 2 n_s (O(N n_s^3) flops) and solved
+                           by two chains of N n_s x n_s products.  The analysis builds no
+                           per-entry gather lists of S.  B's values are checked on the device at
+                           every factor: values that do not repeat make the next kkt_solve
+                           return KKT_ERR_INVALID.  Default 0. */
   int32_t dense_tail;   /* factor the top of the elimination tree (a suffix of the supernodes,
                            whose rows are all tail columns) as one dense lower triangle per block
                            with the blocked dense kernels of the factor of S, instead of
@@ -177,7 +192,7 @@ typedef struct {
                                    share of G (the k coupling rows appended to it) */
   double tail_ratio;            /* cost ratio r the dense tail was chosen with (0 without a tail) */
   int32_t autotune_candidates;  /* distinct tails timed by the autotuner (0 without autotune) */
-  int32_t reserved_info;
+  int32_t schur_block;          /* n_s of the structured S (structured_s = 2), else 0 */
 } kkt_info;
 
 /* Default options: FP64, refine_tol 1e-10, max_refine 10, pivot_eps 1e-20,
@@ -306,7 +321,8 @@ const char* kkt_last_error(void);
  *   contents: calls whose kernels overlap on the GPU (different streams,
  *   different handles) race on it and must be serialized by the caller.
  *   Needs an FP64-accurate factor of S (handles in KKT_FP64 or
- *   KKT_F64_EMULATED mode); otherwise returns KKT_ERR_STATE.
+ *   KKT_F64_EMULATED mode, or with structured_s = 2); otherwise returns
+ *   KKT_ERR_STATE.
  *   Asynchronous with respect to the host; errors of the launches, and an
  *   error left pending on this thread by an earlier launch, are returned as
  *   KKT_ERR_CUDA. */
@@ -331,7 +347,11 @@ kkt_status kkt_solve_noalloc(kkt_handle* h, const double* rhs, double* x, void* 
  * up at the root like t), kkt_abs_rowsums (the rows of |K|, for ||K||_inf) and
  * kkt_norm_inf.  The collectives are the caller's (torch.distributed in the
  * Python layer).  All arrays are device arrays of the handle's device, all
- * calls asynchronous on `stream` except kkt_norm_inf. */
+ * calls asynchronous on `stream` except kkt_norm_inf.  A handle with the
+ * structured S (structured_s = 2) has no dense S: kkt_factor_blocks,
+ * kkt_schur_matrix, kkt_factor_schur and kkt_schur_factor_copy return
+ * KKT_ERR_INVALID for it; kkt_solve_front, kkt_solve_coupling and
+ * kkt_solve_back work after kkt_factor. */
 
 /* kkt_factor without the factor of S: block factors and the assembled S of
  * the handle's blocks (Algorithm 1: block factorization, local Schur
@@ -353,6 +373,14 @@ kkt_status kkt_factor_schur(kkt_handle* h, void* stream);
  * strictly below the diagonal, D on it, the upper part unspecified): the FP32
  * factor converted in the TF32 and BF16 modes. */
 kkt_status kkt_schur_factor_copy(kkt_handle* h, double* out, void* stream);
+/* The structured S (structured_s = 2; Sec. 4.3, eq. GlobalSchur) of the last
+ * kkt_factor: its diagonal blocks S_d[0..N-1] into Sd and its subdiagonal
+ * blocks S_o[0..N-2] (the block repeated in every row below the diagonal of
+ * block column j) into So; each block n_s x n_s column-major, the blocks one
+ * after another (device arrays, N n_s^2 and (N-1) n_s^2 doubles).
+ * KKT_ERR_STATE before a kkt_factor, KKT_ERR_INVALID for a handle without the
+ * structured S. */
+kkt_status kkt_schur_blocks(kkt_handle* h, double* Sd, double* So, void* stream);
 /* dst[i + j ld_dst] += src[i + j ld_src] for i < rows, j < cols (device
  * arrays; a vector is cols = 1).  The reduce of Algorithm 1 on the root. */
 kkt_status kkt_accumulate(double* dst, int64_t ld_dst, const double* src, int64_t ld_src, int64_t rows,

@@ -57,7 +57,7 @@ class kkt_info(C.Structure):
                 ("ms_block_factor", C.c_double), ("ms_schur_assembly", C.c_double),
                 ("ms_dense_factor", C.c_double), ("ms_solve_device", C.c_double),
                 ("n_launches", C.c_int64), ("dense_tail_cols", C.c_int32), ("tail_augmented", C.c_int32),
-                ("tail_ratio", C.c_double), ("autotune_candidates", C.c_int32), ("reserved_info", C.c_int32)]
+                ("tail_ratio", C.c_double), ("autotune_candidates", C.c_int32), ("schur_block", C.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -82,7 +82,8 @@ EXPORTS = ["kkt_default_options", "kkt_analyze", "kkt_factor", "kkt_solve", "kkt
            "kkt_factor_blocks", "kkt_schur_matrix", "kkt_factor_schur", "kkt_schur_factor_copy", "kkt_accumulate",
            "kkt_solve_front", "kkt_solve_coupling", "kkt_solve_back", "kkt_residual", "kkt_abs_rowsums",
            "kkt_norm_inf", "kkt_kernel_stats", "kkt_slack_create", "kkt_slack_reduce", "kkt_slack_recover",
-           "kkt_slack_destroy", "kkt_server_set_cache", "kkt_server_submit_pattern", "kkt_server_cache_info"]
+           "kkt_slack_destroy", "kkt_server_set_cache", "kkt_server_submit_pattern", "kkt_server_cache_info",
+           "kkt_schur_blocks"]
 
 KERNEL_FAMILIES = ["k_tc_update_emu", "k_tc_update_wide", "k_tc_update", "k_dense_update", "k_factor_update",
                    "k_dense_diag_t", "k_tc_update_emu_wide"]
@@ -157,6 +158,7 @@ def load(build_if_missing: bool = True):
                        ("kkt_schur_matrix", [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
                        ("kkt_factor_schur", [vp, vp]),
                        ("kkt_schur_factor_copy", [vp, vp, vp]),
+                       ("kkt_schur_blocks", [vp, vp, vp, vp]),
                        ("kkt_accumulate", [vp, C.c_int64, vp, C.c_int64, C.c_int64, C.c_int64, vp]),
                        ("kkt_solve_front", [vp, vp, vp, vp]),
                        ("kkt_solve_coupling", [vp, vp, vp, vp]),
@@ -423,6 +425,12 @@ def kkt_factor_schur(h, stream=None):
 
 def kkt_schur_factor_copy(h, out, stream=None):
     return _check(load().kkt_schur_factor_copy(h, _dev(out), _stream_ptr(stream)))
+
+
+def kkt_schur_blocks(h, Sd, So, stream=None):
+    """The structured S (structured_s = 2): S_d (N x ns x ns) into Sd and S_o
+    ((N-1) x ns x ns) into So, device tensors, each block column-major."""
+    return _check(load().kkt_schur_blocks(h, _dev(Sd), _dev(So) if So is not None else None, _stream_ptr(stream)))
 
 
 def kkt_accumulate(dst_ptr, ld_dst, src, ld_src, rows, cols, stream=None):

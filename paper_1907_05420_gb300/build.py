@@ -15,7 +15,7 @@ LIB = os.path.join(OUT_DIR, "libkkt_schur.so")
 SYM_LIB = os.path.join(OUT_DIR, "libkkt_symbolic.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["api.cu", "factor.cu", "tail.cu", "schur.cu", "dense.cu", "solve.cu", "probe.cu", "noalloc.cu", "dense_tc.cu",
-      "schur_tc.cu", "shard.cu", "slack.cu"]
+      "schur_tc.cu", "shard.cu", "slack.cu", "cumulative.cu"]
 CPP = ["symbolic.cpp", "serve.cpp"]
 HEADERS = ["handle.h", "symbolic.h", "dense_kernels.cuh", "pivot.cuh", "emu_arith.cuh"]
 

@@ -70,7 +70,10 @@ void free_all(Handle* h) {
                   h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red,
                   h->trsv_flags, h->trsv_ticket, h->dev_err, h->S32, h->Y32, h->tw_img, h->ew_s_Y, h->ew_s_A,
                   h->ew_s_B, h->ew_s_scale, h->ew_t_Y, h->ew_t_A, h->ew_t_B, h->ew_t_scale, h->tc_imgA,
-                  h->tc_imgB, h->tc_scaleA, h->tc_scaleB, h->gm_V, h->gm_Z};
+                  h->tc_imgB, h->tc_scaleA, h->tc_scaleB, h->gm_V, h->gm_Z, h->d.cum_y_ptr, h->d.cum_y_t,
+                  h->d.cum_y_e, h->d.cum_z_ptr, h->d.cum_z_t, h->d.cum_z_e, h->d.cum_check, h->cum_err,
+                  h->cum_H, h->cum_Sd, h->cum_So, h->cum_Q, h->cum_QY, h->cum_Linv, h->cum_M, h->cum_Mt,
+                  h->cum_D};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->host_red) cudaFreeHost(h->host_red);
@@ -112,10 +115,16 @@ cudaError_t enqueue_factor(Handle& h, cudaStream_t st, bool with_s = true) {
   } else {
     STEP(launch_contract_g(h, st));
   }
-  STEP(launch_assemble_s(h, st));
+  if (h.cum) {
+    STEP(launch_cum_assemble(h, st));
+  } else {
+    STEP(launch_assemble_s(h, st));
+  }
   STEP(record(h, h.ev_fb, st));
   if (!with_s) {
     // the factor of S is left to kkt_factor_schur (a sharded solve reduces S first)
+  } else if (h.cum) {
+    STEP(launch_cum_factor(h, h.counters + kNumCounters, st));  // FP64 in every mode
   } else if (h.opt.prec == KKT_FP64) {
     STEP(launch_dense_ldlt(h, h.counters + kNumCounters, st));
   } else {
@@ -219,6 +228,11 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
     delete h;
     return KKT_ERR_INVALID;
   }
+  if (h->opt.structured_s < 0 || h->opt.structured_s > 2) {
+    set_error("kkt_analyze: structured_s must be 0, 1 or 2");
+    delete h;
+    return KKT_ERR_INVALID;
+  }
   if ((h->opt.refine_mode != 0 && h->opt.refine_mode != 1) || h->opt.gmres_restart < 1 || h->opt.gmres_restart > 64) {
     set_error("kkt_analyze: refine_mode must be 0 or 1 and gmres_restart in [1, 64]");
     delete h;
@@ -238,7 +252,15 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
     err = analyze_pattern(pat->nA, pat->nP, pat->a_rowptr, pat->a_col, pat->a_vals_hint,
                           pat->a_vals_hint ? 1 : 0, h->sym);
     if (err.empty())
-      err = analyze_coupling(h->sym, pat->N, pat->nC, pat->b_blockptr, pat->b_row, pat->b_col, h->cpl);
+      err = analyze_coupling(h->sym, pat->N, pat->nC, pat->b_blockptr, pat->b_row, pat->b_col, h->cpl,
+                             h->opt.structured_s != 2);
+  }
+  CumPattern cum;
+  if (err.empty() && h->opt.structured_s == 2 && pat->nC > 0) {
+    err = analyze_cumulative(pat, h->cpl, cum);
+    h->cum = err.empty();
+    h->cum_ns = cum.ns;
+    h->cum_npairs = (int64_t)cum.check.size() / 2;
   }
   if (!err.empty()) {
     set_error("kkt_analyze: " + err);
@@ -411,7 +433,7 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   }
   // row envelope of S for the structured mode
   std::vector<int32_t> trsv_jlo, trsv_jhi;
-  if (h->opt.structured_s && h->nC > 0) s_envelope(C, h->c_kind, kDenseNB, h->panel_rend, trsv_jlo, trsv_jhi);
+  if (h->opt.structured_s == 1 && h->nC > 0) s_envelope(C, h->c_kind, kDenseNB, h->panel_rend, trsv_jlo, trsv_jhi);
   // symmetric full CSR of A with source positions
   std::vector<int32_t> full_rowptr(n + 1, 0), full_col, full_src;
   for (int r = 0; r < n; r++)
@@ -499,6 +521,15 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
     UP(trsv_jlo, trsv_jlo);
     UP(trsv_jhi, trsv_jhi);
   }
+  if (h->cum) {
+    UP(cum_y_ptr, cum.y_ptr);
+    UP(cum_y_t, cum.y_t);
+    UP(cum_y_e, cum.y_e);
+    UP(cum_z_ptr, cum.z_ptr);
+    UP(cum_z_t, cum.z_t);
+    UP(cum_z_e, cum.z_e);
+    UP(cum_check, cum.check);
+  }
 #undef UP
   const int64_t nK = (int64_t)h->N * n + h->nC;
   const int64_t k = C.k;
@@ -512,9 +543,28 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   AL(W, double, (int64_t)C.nw * k * h->N);
   AL(G, double, k * k * h->N);
   AL(wdinv, double, (int64_t)C.nw * h->N);
-  AL(S, double, (int64_t)h->nC * h->nC);
-  AL(Ypanel, double, (int64_t)h->nC * kDenseNB);
-  AL(Xinv, double, (int64_t)((h->nC + kDenseNB - 1) / kDenseNB) * kDenseNB * kDenseNB);
+  // the dense S and its factor's buffers (none with the structured S)
+  const int64_t nCd = h->cum ? 0 : h->nC;
+  AL(S, double, nCd * nCd);
+  AL(Ypanel, double, nCd * kDenseNB);
+  AL(Xinv, double, (int64_t)((nCd + kDenseNB - 1) / kDenseNB) * kDenseNB * kDenseNB);
+  if (h->cum) {
+    const int64_t ns = h->cum_ns, nn = ns * ns;
+    AL(cum_err, int, 1);
+    AL(cum_H, double, 3 * nn * h->N);
+    AL(cum_Sd, double, nn * h->N);
+    AL(cum_So, double, nn * h->N);
+    AL(cum_Q, double, 4 * nn * h->N);
+    AL(cum_QY, double, 2 * ns * kDenseNB);
+    AL(cum_Linv, double, nn * h->N);
+    AL(cum_M, double, nn * h->N);
+    AL(cum_Mt, double, nn * h->N);
+    AL(cum_D, double, ns * h->N);
+    // the last period has no M_j: it stays zero; the flag starts clear
+    if (e == cudaSuccess) e = cudaMemset(h->cum_M, 0, sizeof(double) * (size_t)(nn * h->N));
+    if (e == cudaSuccess) e = cudaMemset(h->cum_Mt, 0, sizeof(double) * (size_t)(nn * h->N));
+    if (e == cudaSuccess) e = cudaMemset(h->cum_err, 0, sizeof(int));
+  }
   AL(Sdinv, double, h->nC);
   if (h->nT > 0) {
     AL(Xtail, double, (int64_t)((h->nT + kDenseNB - 1) / kDenseNB) * kDenseNB * kDenseNB * h->N);
@@ -553,17 +603,17 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
     AL(gm_Z, double, (int64_t)m * nK);
   }
   AL(trsv_flags, int, 2 * ((h->nC + kDenseNB - 1) / kDenseNB));
-  if (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) {
+  if ((h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && !h->cum) {
     AL(S32, float, (int64_t)h->nC * h->nC);
     AL(Y32, float, (int64_t)h->nC * kDenseNB);
   }
-  if (h->opt.prec == KKT_TF32 && tf32_wide_applies(h->nC, h->opt.structured_s != 0)) {
+  if (h->opt.prec == KKT_TF32 && !h->cum && tf32_wide_applies(h->nC, h->opt.structured_s != 0)) {
     h->tw_set_bytes = tf32_wide_set_bytes(h->nC);
     AL(tw_img, uint8_t, 16 * h->tw_set_bytes);
     // rows past the trailing matrix are read (and masked) in whole tiles: keep them finite
     if (e == cudaSuccess) e = cudaMemset(h->tw_img, 0, (size_t)(16 * h->tw_set_bytes));
   }
-  if (h->opt.prec != KKT_FP64 && h->nC > 0) {
+  if (h->opt.prec != KKT_FP64 && h->nC > 0 && !h->cum) {
     // operand images sized for the largest panel step; the FP64 fallback of the
     // reduced modes uses the emulated path, so size for the larger of the two
     const int mode_img = KKT_F64_EMULATED;
@@ -615,6 +665,7 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   if (e == cudaSuccess) e = dense_prepare();
   if (e == cudaSuccess) e = dense_tc_prepare();
   if (e == cudaSuccess) e = schur_tc_prepare();
+  if (e == cudaSuccess && h->cum) e = cum_prepare();
   if (e != cudaSuccess) {
     kkt_status st = cuda_status(e, "kkt_analyze");
     free_all(h);
@@ -628,6 +679,7 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   h->info.k_coupling_rows = C.k;
   h->info.w_rows = C.nw;
   h->info.factor_flops = S.flops;
+  h->info.schur_block = h->cum ? h->cum_ns : 0;
   h->info.ms_analyze =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = reinterpret_cast<kkt_handle*>(h);
@@ -676,7 +728,7 @@ kkt_status factor_values(Handle* h, const double* a_vals, const double* b_vals, 
   // take other processes' parts, which a fallback could not rebuild
   h->g_reduced = with_s && (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && h->opt.reduced_contraction &&
                  contract_g_tc_supported(*h);
-  h->s_factor = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) ? 1 : 0;
+  h->s_factor = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && !h->cum ? 1 : 0;
   if (with_s && h->opt.use_graphs && !h->graph_failed && !h->factor_exec) {
     capture_factor(*h);
     h->kt_graph_used = h->kt_used;
@@ -866,6 +918,10 @@ kkt_status kkt_factor_blocks(kkt_handle* hh, const double* a_vals, const double*
     set_error("kkt_factor_blocks: null argument");
     return KKT_ERR_INVALID;
   }
+  if (h->cum) {
+    set_error("kkt_factor_blocks: the structured S (structured_s = 2) has no dense S to reduce");
+    return KKT_ERR_INVALID;
+  }
   return factor_values(h, a_vals, b_vals, c_vals, on_device, (cudaStream_t)stream, 0.0, 0.0, 0.0, false);
 }
 
@@ -905,14 +961,19 @@ kkt_status kkt_factor_inertia(kkt_handle* hh, const double* a_vals, const double
   const uint64_t pos_blk = (uint64_t)h->N * h->nP, neg_blk = (uint64_t)h->N * (h->nA - h->nP);
   const uint64_t pos_s = o.coupling_dual ? 0 : (uint64_t)h->nC, neg_s = o.coupling_dual ? (uint64_t)h->nC : 0;
   unsigned long long c[2 * kNumCounters];
-  int dev_err = 0;
+  int dev_err = 0, cum_err = 0;
   auto read_counts = [&]() -> kkt_status {
     KKT_CUDA(cudaMemcpyAsync(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost, st));
     KKT_CUDA(cudaMemcpyAsync(&dev_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (h->cum) KKT_CUDA(cudaMemcpyAsync(&cum_err, h->cum_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     KKT_CUDA(cudaStreamSynchronize(st));
     if (dev_err != 0) {
       set_error("kkt_factor_inertia: a bounded device wait ran out");
       return KKT_ERR_TIMEOUT;
+    }
+    if (cum_err != 0) {
+      set_error("kkt_factor_inertia: B's values do not repeat over the later periods (structured_s = 2)");
+      return KKT_ERR_INVALID;
     }
     return KKT_OK;
   };
@@ -1011,10 +1072,15 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
       KKT_CUDA(cudaMemcpyAsync(h->host_red, h->red, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
       KKT_CUDA(cudaMemcpyAsync(h->host_red + 3, h->knorm, sizeof(double), cudaMemcpyDeviceToHost, st));
       KKT_CUDA(cudaMemcpyAsync(h->host_red + 4, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      if (h->cum) KKT_CUDA(cudaMemcpyAsync(h->host_red + 5, h->cum_err, sizeof(int), cudaMemcpyDeviceToHost, st));
       KKT_CUDA(cudaStreamSynchronize(st));
       if (*reinterpret_cast<int*>(h->host_red + 4) != 0) {
         set_error("kkt_solve: a bounded device wait ran out");
         return KKT_ERR_TIMEOUT;
+      }
+      if (h->cum && *reinterpret_cast<int*>(h->host_red + 5) != 0) {
+        set_error("kkt_solve: B's values do not repeat over the later periods (structured_s = 2)");
+        return KKT_ERR_INVALID;
       }
       const double* hr = h->host_red;
       // hr: ||rho||, ||x||, ||r|| (inf-norms that keep NaN) and ||K||_inf

@@ -81,6 +81,16 @@ struct DevSym {
   int32_t* g_key = nullptr;            // sparse contraction: entries t1 * k + t2 of G
   int64_t* g_ptr = nullptr;            // their rows g_row[g_ptr[e] .. g_ptr[e+1])
   int32_t* g_row = nullptr;
+  // structured S of the cumulative coupling: per block and storage unit the
+  // (index into E, B entry) lists of its own period's columns (y) and of the
+  // later periods' (z); pairs of B entries that must hold equal values
+  int32_t* cum_y_ptr = nullptr;
+  int32_t* cum_y_t = nullptr;
+  int32_t* cum_y_e = nullptr;
+  int32_t* cum_z_ptr = nullptr;
+  int32_t* cum_z_t = nullptr;
+  int32_t* cum_z_e = nullptr;
+  int32_t* cum_check = nullptr;
 };
 
 // Counters written by the kernels (device, int64).
@@ -174,6 +184,21 @@ struct Handle {
   int* trsv_flags = nullptr;  // 2 * ceil(nC/64): block-ready epochs of the dense triangular solves
   unsigned* trsv_ticket = nullptr;  // 2 tickets (forward, backward)
   int* dev_err = nullptr;     // set when a bounded device wait runs out
+  // structured S of the cumulative coupling (structured_s = 2, cumulative.cu):
+  // ns x ns blocks, column-major, N of each unless noted
+  bool cum = false;
+  int32_t cum_ns = 0;          // coupling variables per period
+  int64_t cum_npairs = 0;      // B entries whose values must repeat
+  int* cum_err = nullptr;      // set by the factor when they do not
+  double* cum_H = nullptr;     // 3 per block: Y^T G Y, Z^T G Y, Z^T G Z
+  double* cum_Sd = nullptr;    // S_d (eq. GlobalSchur)
+  double* cum_So = nullptr;    // S_o (the last unused)
+  double* cum_Q = nullptr;     // N x (2ns)^2: the augmented matrix of each period, factored in place
+  double* cum_QY = nullptr;    // 2ns x 64: panel scratch of its factor
+  double* cum_Linv = nullptr;  // L_j^{-1}
+  double* cum_M = nullptr;     // M_j = L21_j L_j^{-1} (the last zero)
+  double* cum_Mt = nullptr;    // M_j^T
+  double* cum_D = nullptr;     // N x ns: the pivots
   int trsv_epoch = 0;
   int64_t device_bytes = 0;
 
@@ -284,6 +309,22 @@ cudaError_t launch_norms(Handle& h, const double* rho, const double* x, const do
 cudaError_t launch_dot(Handle& h, const double* a, const double* b, int64_t n, double* out, cudaStream_t st);
 cudaError_t launch_axpby(Handle& h, double* y, double a, const double* x, int64_t n, cudaStream_t st);
 cudaError_t launch_scale_into(Handle& h, double* y, double a, const double* x, int64_t n, cudaStream_t st);
+
+// ---- (cumulative.cu) structured S of the cumulative coupling ----
+constexpr int kCumMaxStor = 4096;            // coupling variables per period at most
+constexpr int kCumInverseSmem = 200 * 1024;  // dynamic shared memory of its inverse kernel
+struct CumPattern {
+  int32_t ns = 0;
+  std::vector<int32_t> y_ptr, y_t, y_e;  // per block: ns + 1 offsets; (E index, B entry) per entry
+  std::vector<int32_t> z_ptr, z_t, z_e;
+  std::vector<int32_t> check;            // pairs (entry, entry it must equal)
+};
+// Checks that B has the cumulative structure and builds the lists ("" on success).
+std::string analyze_cumulative(const kkt_pattern* pat, const Coupling& C, CumPattern& out);
+cudaError_t cum_prepare();
+cudaError_t launch_cum_assemble(Handle& h, cudaStream_t st);   // S_d, S_o from G and B
+cudaError_t launch_cum_factor(Handle& h, unsigned long long* counters, cudaStream_t st);
+cudaError_t launch_cum_solve(Handle& h, const double* t, double* x, cudaStream_t st);
 
 // Solve work vectors supplied by the caller instead of the handle.
 struct SolveWorkspace {

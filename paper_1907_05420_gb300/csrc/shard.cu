@@ -134,6 +134,10 @@ kkt_status kkt_schur_matrix(kkt_handle* hh, double** S, int64_t* ld) {
     set_error("kkt_schur_matrix: null argument");
     return KKT_ERR_INVALID;
   }
+  if (h->cum) {
+    set_error("kkt_schur_matrix: the structured S (structured_s = 2) has no dense S");
+    return KKT_ERR_INVALID;
+  }
   *S = h->S;
   *ld = h->nC;
   return KKT_OK;
@@ -143,6 +147,10 @@ kkt_status kkt_factor_schur(kkt_handle* hh, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) {
     set_error("kkt_factor_schur: null handle");
+    return KKT_ERR_INVALID;
+  }
+  if (h->cum) {
+    set_error("kkt_factor_schur: the structured S (structured_s = 2) is factored by kkt_factor");
     return KKT_ERR_INVALID;
   }
   kkt_status s = need(h->blocks_factored, "kkt_factor_schur: no block factorization (kkt_factor_blocks first)");
@@ -163,6 +171,10 @@ kkt_status kkt_schur_factor_copy(kkt_handle* hh, double* out, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || (!out && h->nC > 0)) {
     set_error("kkt_schur_factor_copy: null argument");
+    return KKT_ERR_INVALID;
+  }
+  if (h->cum) {
+    set_error("kkt_schur_factor_copy: the structured S (structured_s = 2) has no dense factor");
     return KKT_ERR_INVALID;
   }
   kkt_status s = need(h->factored, "kkt_schur_factor_copy: S is not factored");
@@ -222,7 +234,8 @@ kkt_status kkt_solve_coupling(kkt_handle* hh, const double* t, double* xg, void*
   h->stream = st;
   (void)cudaGetLastError();
   if (h->nC > 0)
-    KKT_CUDA(h->s_factor == 1 ? launch_dense_solve_f32(*h, t, xg, st) : launch_dense_solve(*h, t, xg, st));
+    KKT_CUDA(h->cum ? launch_cum_solve(*h, t, xg, st)
+                    : h->s_factor == 1 ? launch_dense_solve_f32(*h, t, xg, st) : launch_dense_solve(*h, t, xg, st));
   KKT_CUDA(cudaEventRecord(h->ev_done, st));
   return KKT_OK;
 }

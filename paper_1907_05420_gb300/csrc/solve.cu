@@ -525,8 +525,9 @@ cudaError_t launch_apply_back(Handle& h, double* out, cudaStream_t st, bool solv
   if (h.nC > 0) {
     // without solve_s, h.xg already holds x_g (a sharded solve's broadcast)
     cudaError_t e = !solve_s ? cudaSuccess
-                             : (h.s_factor == 1 ? launch_dense_solve_f32(h, h.tg, h.xg, st)
-                                                : launch_dense_solve(h, h.tg, h.xg, st));
+                    : h.cum     ? launch_cum_solve(h, h.tg, h.xg, st)
+                    : (h.s_factor == 1 ? launch_dense_solve_f32(h, h.tg, h.xg, st)
+                                       : launch_dense_solve(h, h.tg, h.xg, st));
     if (e != cudaSuccess) return e;
     if (k > 0 && nw > 0) {
       {
@@ -679,7 +680,7 @@ cudaError_t launch_apply_inverse_ws(Handle& h, const double* r, double* out,
     k_reduce_t<<<(h.nC + 255) / 256, 256, 0, st>>>(r + nb, h.d.t_ptr, h.d.t_e, h.d.e_t, h.d.e_block,
                                                    h.b_vals, ws.u, k, h.nC, ws.tg);
     h.launches++;
-    cudaError_t e = launch_dense_solve_ws(h, ws.tg, ws.xg, ws.dot, st);
+    cudaError_t e = h.cum ? launch_cum_solve(h, ws.tg, ws.xg, st) : launch_dense_solve_ws(h, ws.tg, ws.xg, ws.dot, st);
     if (e != cudaSuccess) return e;
     if (k > 0 && nw > 0) {
       k_mx<<<(k * N + 255) / 256, 256, 0, st>>>(h.d.bt_ptr, h.d.b_col, h.b_vals, ws.xg, k, N, ws.v);

@@ -513,7 +513,7 @@ std::string analyze_pattern(int32_t n, int32_t nP, const int32_t* rowptr, const 
 }
 
 std::string analyze_coupling(const Symbolic& S, int32_t N, int32_t nC, const int32_t* b_blockptr,
-                             const int32_t* b_row, const int32_t* b_col, Coupling& C) {
+                             const int32_t* b_row, const int32_t* b_col, Coupling& C, bool s_records) {
   C = Coupling();
   C.N = N;
   C.nC = nC;
@@ -589,7 +589,7 @@ std::string analyze_coupling(const Symbolic& S, int32_t N, int32_t nC, const int
     int32_t e1, e2;
   };
   std::vector<Rec> recs;
-  for (int32_t i = 0; i < N; i++)
+  for (int32_t i = 0; s_records && i < N; i++)
     for (int32_t e1 = b_blockptr[i]; e1 < b_blockptr[i + 1]; e1++)
       for (int32_t e2 = b_blockptr[i]; e2 < b_blockptr[i + 1]; e2++)
         if (b_col[e1] >= b_col[e2]) recs.push_back({(int64_t)b_col[e1] * nC + b_col[e2], e1, e2});

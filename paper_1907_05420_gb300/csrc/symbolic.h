@@ -121,8 +121,11 @@ struct Coupling {
 void g_gather(const Symbolic& S, const Coupling& C, int32_t tail_sn, std::vector<int32_t>& g_key,
               std::vector<int64_t>& g_ptr, std::vector<int32_t>& g_row);
 
+// s_records = false leaves the gather records of S empty (the structured S of
+// the cumulative coupling does without them).
 std::string analyze_coupling(const Symbolic& S, int32_t N, int32_t nC, const int32_t* b_blockptr,
-                             const int32_t* b_row, const int32_t* b_col, Coupling& out);
+                             const int32_t* b_row, const int32_t* b_col, Coupling& out,
+                             bool s_records = true);
 
 // Row envelope of S = C - sum_i M_i^T G_i M_i (the structured factor): for each
 // 64-wide panel p, one past the last row that can be nonzero in its columns

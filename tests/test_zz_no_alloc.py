@@ -76,13 +76,15 @@ def test_noalloc_matches_kkt_solve_on_two_calls(name):
 # Cases where the work-vector path departs most from kkt_solve's kernels: a
 # dense tail whose factor was scattered back into the panels (FP64 and
 # emulated-FP64 updates, augmented by the coupling rows), the envelope-limited
-# factor of S, and the emulated-FP64 factor of S.
+# factor of S, the emulated-FP64 factor of S, and the structured S of the
+# paper's cumulative coupling (FP64 in the TF32 mode too).
 AUG14 = GridSpec(14, 18, 3, 2, 4, 1e-6, 1e6, 102, "aug14")
 CASES = {
     "aug14_tail_fp64": (AUG14, "fp64", {"dense_tail": 1}),
     "aug14_tail_emulated": (AUG14, "f64emu", {"dense_tail": 2}),
     "grid30_structured_s": (CONFIGS["grid30_n24"], "fp64", {"structured_s": 1}),
     "grid30_f64emu": (CONFIGS["grid30_n24"], "f64emu", {}),
+    "grid30_paper_structured_tf32": (CONFIGS["grid30_n24"], "tf32", {"structured_s": 2}),
 }
 
 
@@ -92,7 +94,7 @@ def test_noalloc_matches_kkt_solve_tail_structured_emulated(case):
     from paper_1907_05420_gb300 import binding as B
 
     spec, prec, kw = CASES[case]
-    p = make_problem(spec)
+    p = make_problem(spec, coupling="paper") if kw.get("structured_s") == 2 else make_problem(spec)
     h, r = _factored(p, torch, B, B.kkt_default_options(prec, **kw))
     try:
         info = B.kkt_get_info(h)
