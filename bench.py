@@ -499,6 +499,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-slack", action="store_true", help="skip the slack-elimination measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sweep of the default run")
+    ap.add_argument("--no-paper", action="store_true",
+                    help="skip the structured-S leg on the paper's cumulative coupling")
     ap.add_argument("--serve-seconds-default", type=float, default=2.0,
                     help="measured seconds per rate of the serving sweep inside the default run")
     ap.add_argument("--autotune", type=int, default=-1,
@@ -576,6 +578,71 @@ def slack_timing(args, dev, stream, torch, np, B, reps=20):
     finally:
         sl.close()
         B.kkt_destroy(h)
+
+
+def structured_paper_timing(args, dev, stream, torch, np, B, steps=5, warmup=2):
+    """The paper's own MPOPF coupling on the 2,383-bus grid over 96 periods
+    (n_C = 9,600: 100 storage multipliers per period, Sec. 4.1 eq. B12N) with
+    the structured S of Sec. 4.3 (structured_s = 2): factor + refined solve per
+    step, device-resident inputs, FP64 and TF32 block tails.  The dense-S
+    analysis of this pattern would need one gather record per pair of B
+    entries of a block (reported), far beyond host memory."""
+    from gen import CONFIGS, make_problem
+
+    p = make_problem(CONFIGS["grid2383_n96"], coupling="paper")
+    N, nC = p.N, p.nC
+    ns = nC // N
+    up = lambda v: torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).to(dev)  # noqa: E731
+    a, b, c, r = up(p.a_vals), up(p.b_vals), up(p.c_vals), up(p.rhs)
+    x = torch.empty_like(r)
+    bp = np.asarray(p.b_blockptr, dtype=np.int64)
+    records = int(np.sum((bp[1:] - bp[:-1]) ** 2))
+    # partial LDL^T of order 2 n_s with n_s pivots per period (the last: n_s of order n_s)
+    chain_flops = (N - 1) * 7.0 * ns ** 3 / 3.0 + ns ** 3 / 3.0
+    fp64_gflops = B.kkt_measure_fp64_peak()
+    out = {"workload": f"grid2383_n96_paper: the 2,383-bus grid over 96 periods with the paper's cumulative "
+                       f"coupling (C = 0), n_C = {nC:,} ({ns} per period), blocks nA={p.nA:,}",
+           "dense_s_gather_records": records, "dense_s_factor_flops": nC ** 3 / 3.0,
+           "dense_s_factor_ms_at_fp64_peak": nC ** 3 / 3.0 / (fp64_gflops * 1e6),
+           "structured_factor_flops": chain_flops}
+    for prec in ("fp64", "tf32"):
+        t0 = time.perf_counter()
+        h = B.kkt_analyze(p, B.kkt_default_options(prec, structured_s=2, refine_mode=args.refine_mode))
+        ana_ms = (time.perf_counter() - t0) * 1e3
+        try:
+            def step():
+                B.kkt_factor(h, a, b, c, stream)
+                B.kkt_solve(h, r, x, 1, stream)
+
+            for _ in range(warmup):
+                step()
+            torch.cuda.synchronize()
+            ms, ph = [], {"a_block_factor": [], "b_schur_assembly": [], "c_structured_factor": [], "d_solve": []}
+            for _ in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                info = B.kkt_get_info(h)
+                ph["a_block_factor"].append(info["ms_block_factor"])
+                ph["b_schur_assembly"].append(info["ms_schur_assembly"])
+                ph["c_structured_factor"].append(info["ms_dense_factor"])
+                ph["d_solve"].append(info["ms_solve_device"])
+            expect = [N * p.nP, N * (p.nA - p.nP) + nC, 0]
+            cms = statistics.mean(ph["c_structured_factor"])
+            out[prec] = {"value": 1e3 / statistics.mean(ms), "unit": "solves/s", "ms_per_step": statistics.mean(ms),
+                         "analyze_ms": ana_ms, "phases_ms": {k: statistics.mean(v) for k, v in ph.items()},
+                         "structured_factor": {"bound": "alu", "gflops": chain_flops / cms / 1e6,
+                                               "frac_of_fp64_peak": chain_flops / cms / 1e6 / fp64_gflops},
+                         "eta": info["rel_residual"], "refine_steps": info["refine_steps"],
+                         "fell_back_fp64": info["fell_back_fp64"],
+                         "inertia_ok": [info["n_pos"], info["n_neg"], info["n_zero"]] == expect,
+                         "device_bytes": info["device_bytes"]}
+        finally:
+            B.kkt_destroy(h)
+    return out
 
 
 def _accuracy(B, h, prob, r, x, stream, torch):
@@ -739,6 +806,7 @@ def run_single(args):
                      "accuracy": acc, "phases_ms": {kk: statistics.mean(v) for kk, v in lr["phases"].items()}}
 
     slack = None if args.no_slack else slack_timing(args, dev, stream, torch, np, B)
+    paper = None if args.no_paper else structured_paper_timing(args, dev, stream, torch, np, B)
     serving = None
     if not args.no_serve and world == 1:
         serving = serve_sweep(args, ["tf32", "fp64"], [float(q) for q in args.rates.split(",")],
@@ -852,7 +920,7 @@ def run_single(args):
                        "augmented": bool(info0["tail_augmented"]),
                        "autotune_candidates": info0["autotune_candidates"]},
         "device_bytes": info0["device_bytes"], "other_precisions": legs, "slack_elimination": slack,
-        "serving": serving,
+        "structured_paper": paper, "serving": serving,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], out = cpu_baseline_sample(args.workload, prob, info0["factor_flops"])

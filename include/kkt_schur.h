@@ -527,6 +527,13 @@ kkt_status kkt_kernel_stats(kkt_handle* h, int32_t family, kkt_kernel_stat* out)
  * phases report their roofline fraction against it. */
 kkt_status kkt_measure_fp64_peak(double* gflops);
 
+/* Diagnostic: for n device doubles d, recip[i] = the reciprocal the factor
+ * kernels take of a pivot d[i] (an FP32 seed and two FP64 Newton-Raphson
+ * steps; CUDA's division for |d| outside [1e-36, 1e36]) and quotient[i] =
+ * 1.0 / d[i] by CUDA's FP64 division, so that tests can bound the
+ * difference.  Device arrays; asynchronous on `stream`. */
+kkt_status kkt_probe_pivot_reciprocal(const double* d, int64_t n, double* recip, double* quotient, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,7 +83,7 @@ EXPORTS = ["kkt_default_options", "kkt_analyze", "kkt_factor", "kkt_solve", "kkt
            "kkt_solve_front", "kkt_solve_coupling", "kkt_solve_back", "kkt_residual", "kkt_abs_rowsums",
            "kkt_norm_inf", "kkt_kernel_stats", "kkt_slack_create", "kkt_slack_reduce", "kkt_slack_recover",
            "kkt_slack_destroy", "kkt_server_set_cache", "kkt_server_submit_pattern", "kkt_server_cache_info",
-           "kkt_schur_blocks"]
+           "kkt_schur_blocks", "kkt_probe_pivot_reciprocal"]
 
 KERNEL_FAMILIES = ["k_tc_update_emu", "k_tc_update_wide", "k_tc_update", "k_dense_update", "k_factor_update",
                    "k_dense_diag_t", "k_tc_update_emu_wide"]
@@ -159,6 +159,7 @@ def load(build_if_missing: bool = True):
                        ("kkt_factor_schur", [vp, vp]),
                        ("kkt_schur_factor_copy", [vp, vp, vp]),
                        ("kkt_schur_blocks", [vp, vp, vp, vp]),
+                       ("kkt_probe_pivot_reciprocal", [vp, C.c_int64, vp, vp, vp]),
                        ("kkt_accumulate", [vp, C.c_int64, vp, C.c_int64, C.c_int64, C.c_int64, vp]),
                        ("kkt_solve_front", [vp, vp, vp, vp]),
                        ("kkt_solve_coupling", [vp, vp, vp, vp]),
@@ -431,6 +432,12 @@ def kkt_schur_blocks(h, Sd, So, stream=None):
     """The structured S (structured_s = 2): S_d (N x ns x ns) into Sd and S_o
     ((N-1) x ns x ns) into So, device tensors, each block column-major."""
     return _check(load().kkt_schur_blocks(h, _dev(Sd), _dev(So) if So is not None else None, _stream_ptr(stream)))
+
+
+def kkt_probe_pivot_reciprocal(d, recip, quotient, stream=None):
+    """recip = the factor kernels' pivot reciprocal of d, quotient = 1.0 / d (device tensors)."""
+    return _check(load().kkt_probe_pivot_reciprocal(_dev(d), int(d.numel()), _dev(recip), _dev(quotient),
+                                                    _stream_ptr(stream)))
 
 
 def kkt_accumulate(dst_ptr, ld_dst, src, ld_src, rows, cols, stream=None):

@@ -144,6 +144,37 @@ __global__ void k_cum_build(const double* __restrict__ Sd, const double* __restr
   }
 }
 
+// Trailing update of one period's partial factor, A[i][j] -= sum_c Y[i][c]
+// L[j][c] for base <= j <= i < rend: a 16 x 16 tile of the lower triangle per
+// CTA, one entry per thread.  The trailing matrices here are small (2 n_s
+// rows), so small tiles spread each update over many SMs.
+constexpr int kCumTile = 16;
+constexpr int kCumPanel = 32;  // pivot columns per panel of the period factors
+
+__global__ void __launch_bounds__(kCumTile * kCumTile) k_cum_update(double* __restrict__ S, const double* __restrict__ Y,
+                                                                   int n, int k0, int kb, int rend) {
+  const int base = k0 + kb;
+  int tile = blockIdx.x, ti = 0;
+  while (tile > ti) {
+    tile -= ti + 1;
+    ti++;
+  }
+  const int i0 = base + ti * kCumTile, j0 = base + tile * kCumTile;
+  __shared__ double Ys[kCumPanel][kCumTile + 1];
+  __shared__ double Ls[kCumPanel][kCumTile + 1];
+  const int tx = threadIdx.x % kCumTile, ty = threadIdx.x / kCumTile;
+  for (int q = threadIdx.x; q < kb * kCumTile; q += blockDim.x) {
+    const int c = q / kCumTile, r = q % kCumTile;
+    Ys[c][r] = i0 + r < rend ? Y[(i0 + r) + (int64_t)c * n] : 0.0;
+    Ls[c][r] = j0 + r < rend ? S[(j0 + r) + (int64_t)(k0 + c) * n] : 0.0;
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int c = 0; c < kb; c++) acc += Ys[c][ty] * Ls[c][tx];
+  const int i = i0 + ty, j = j0 + tx;
+  if (i < rend && j <= i) S[i + (int64_t)j * n] -= acc;
+}
+
 // Z L_j = [I; L21_j] for the rows of Z: rows < ns give Linv_j = L_j^{-1}, the
 // others M_j = L21_j L_j^{-1} (stored also transposed); D_j is copied out.
 // One thread per row of Z, its row in shared memory; the columns are swept
@@ -391,8 +422,8 @@ cudaError_t launch_cum_factor(Handle& h, unsigned long long* counters, cudaStrea
     k_cum_build<<<grid_of(q2), 256, 0, st>>>(h.cum_Sd, h.cum_So, j ? Q - q2 : nullptr, Q, ns, j, last);
     h.launches++;
     const int rend = last ? ns : n2;
-    for (int k0 = 0; k0 < ns; k0 += kPanelW) {
-      const int kb = std::min(kPanelW, ns - k0);
+    for (int k0 = 0; k0 < ns; k0 += kCumPanel) {
+      const int kb = std::min(kCumPanel, ns - k0);
       const int kd = kt_begin(h, kFamDiag, (2.0 / 3.0) * kb * kb * kb, st);
       k_dense_diag_t<double><<<1, 256, 0, st>>>(Q, n2, k0, kb, 0, PivotRule{}, counters);
       kt_end(h, kd, st);
@@ -400,9 +431,9 @@ cudaError_t launch_cum_factor(Handle& h, unsigned long long* counters, cudaStrea
       const int rest = rend - k0 - kb;
       if (rest > 0) {
         launch_dense_panel<double>(Q, h.cum_QY, n2, k0, kb, rend, 1, 0, 0, st);
-        const int tiles = (rest + 63) / 64;
+        const int tiles = (rest + kCumTile - 1) / kCumTile;
         const int kt = kt_begin(h, kFamDenseF64, update_flops(rest, 0, rest, kb), st);
-        k_dense_update<<<tiles * (tiles + 1) / 2, 256, 0, st>>>(Q, h.cum_QY, n2, k0, kb, rend, 0, 0);
+        k_cum_update<<<tiles * (tiles + 1) / 2, kCumTile * kCumTile, 0, st>>>(Q, h.cum_QY, n2, k0, kb, rend);
         kt_end(h, kt, st);
         h.launches += 2;
       }

@@ -1,10 +1,14 @@
 // FP64 FMA throughput of the current device: the denominator of the roofline
 // of the FP64-bound phases (block factor, FP64 Schur contraction, FP64 dense
 // factor).  Each thread runs 8 independent FMA chains, so the FP64 pipe, not
-// latency, limits the rate.
+// latency, limits the rate.  Also the pivot reciprocal of the factor kernels
+// beside CUDA's own FP64 division, for the tests.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "handle.h"
+#include "pivot.cuh"
 
 namespace kkt {
 namespace {
@@ -23,8 +27,30 @@ __global__ void __launch_bounds__(256) k_fp64_fma(double* out, int iters, double
   if (s == 12345.678) out[0] = s;  // keeps the chains alive
 }
 
+__global__ void k_recip_pair(const double* __restrict__ d, int64_t n, double* __restrict__ recip,
+                             double* __restrict__ quot) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    recip[q] = pivot_recip(d[q]);
+    quot[q] = 1.0 / d[q];
+  }
+}
+
 }  // namespace
 }  // namespace kkt
+
+extern "C" kkt_status kkt_probe_pivot_reciprocal(const double* d, int64_t n, double* recip, double* quotient,
+                                                 void* stream) {
+  using namespace kkt;
+  if (n < 0 || (n > 0 && (!d || !recip || !quotient))) {
+    set_error("kkt_probe_pivot_reciprocal: invalid argument");
+    return KKT_ERR_INVALID;
+  }
+  if (n == 0) return KKT_OK;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  k_recip_pair<<<grid, 256, 0, (cudaStream_t)stream>>>(d, n, recip, quotient);
+  KKT_CUDA(cudaGetLastError());
+  return KKT_OK;
+}
 
 extern "C" kkt_status kkt_measure_fp64_peak(double* gflops) {
   using namespace kkt;
