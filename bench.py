@@ -389,9 +389,12 @@ def serve_sweep(args, precs, rates, seconds, pool=64):
                        "patterns analysed at first request, resident after, admitted by free HBM",
            "slots": args.serve_slots, "seconds_per_rate": seconds, "backlog": backlog,
            "refinement": ["iterative", "gmres"][args.refine_mode]}
-    for prec in precs:
+    for mode in precs:
+        prec, opts, tol = parse_leg(mode)
+        if tol is not None:
+            opts["refine_tol"] = tol
         srv = B.KKTServer(slots=args.serve_slots)
-        srv.set_cache(B.kkt_default_options(prec, refine_mode=args.refine_mode), reserve_bytes=8 << 30)
+        srv.set_cache(B.kkt_default_options(prec, refine_mode=args.refine_mode, **opts), reserve_bytes=8 << 30)
         rng = np.random.default_rng(4242)
         seen = set()
         res = {}
@@ -440,7 +443,7 @@ def serve_sweep(args, precs, rates, seconds, pool=64):
                                    "p99_ms": float(np.percentile(lats, 99)) if n else None}
         res["cache"] = srv.cache_info()
         srv.close()
-        out[prec] = res
+        out[mode] = res
     return out
 
 
@@ -486,6 +489,9 @@ def main():
     ap.add_argument("--ref-sample-flops", type=float, default=6e10,
                     help="estimated oracle work of one reference-arm step")
     ap.add_argument("--batch-precs", default="tf32,fp64")
+    ap.add_argument("--serve-modes", default="tf32,tf32+band,fp64+band",
+                    help="modes of the serving sweep in the default run: prec[+band][@tol] (the mix uses the "
+                         "adjacent coupling, whose S is banded: +band is its envelope-limited factor)")
     ap.add_argument("--batch-streams", type=int, default=8)
     ap.add_argument("--serve-pool", type=int, default=32)
     ap.add_argument("--serve-slots", type=int, default=8)
@@ -809,7 +815,7 @@ def run_single(args):
     paper = None if args.no_paper else structured_paper_timing(args, dev, stream, torch, np, B)
     serving = None
     if not args.no_serve and world == 1:
-        serving = serve_sweep(args, ["tf32", "fp64"], [float(q) for q in args.rates.split(",")],
+        serving = serve_sweep(args, args.serve_modes.split(","), [float(q) for q in args.rates.split(",")],
                               args.serve_seconds_default)
 
     # ---- forward errors against the FP64-accurate solutions of this run
