@@ -94,7 +94,8 @@ typedef struct {
 typedef struct {
   kkt_precision prec;  /* arithmetic of the Schur contraction and the factor of S */
   double refine_tol;   /* target normwise backward error of the refined solution (1e-10) */
-  int32_t max_refine;  /* refinement steps at most (10) */
+  int32_t max_refine;  /* refinement steps at most (10); after an FP64 fallback the refinement on the
+                          FP64-accurate factor has max_refine steps of its own */
   double pivot_eps;    /* |d| < pivot_eps * ||A_i||_max is replaced by +-pivot_eps * ||A_i||_max
                           with the expected sign and counted; 0 turns the perturbation off */
   int32_t use_graphs;  /* capture the device work of kkt_factor after the input copies as a CUDA

@@ -1063,7 +1063,7 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
       KKT_CUDA(launch_apply_inverse(*h, h->rhs, h->x, st));
     }
     h->schur_pending = false;
-    int steps = 0;
+    int steps = 0, before_fallback = 0;  // steps of this refinement, of the one before the FP64 fallback
     bool nonfinite = false;
     double eta = INFINITY, eta_prev = INFINITY;
     for (;;) {
@@ -1104,7 +1104,9 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
           if (rs != KKT_OK) return rs;
           KKT_CUDA(launch_apply_inverse(*h, h->rhs, h->x, st));
           eta_prev = INFINITY;
-          steps++;
+          // the refinement starts over on the FP64-accurate factor, with its own budget
+          before_fallback += steps + 1;
+          steps = 0;
           continue;
         }
         if (!iterate_finite) nonfinite = true;
@@ -1128,7 +1130,7 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
     }
     KKT_CUDA(cudaMemcpyAsync(xq, h->x, sizeof(double) * nK,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    h->info.refine_steps = steps;
+    h->info.refine_steps = before_fallback + steps;
     h->info.rel_residual = eta;
     if (nonfinite) result = KKT_ERR_NONFINITE;
     else if (!(eta <= h->opt.refine_tol) && result == KKT_OK) result = KKT_ERR_NOT_CONVERGED;

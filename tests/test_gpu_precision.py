@@ -115,3 +115,15 @@ def test_gmres_refinement_reaches_a_tight_tolerance_without_fallback():
     assert np.array_equal(xs[0], xs[1])
     x0, info0 = gpu_solve(p, "tf32", refine_mode=0, refine_tol=1e-13, max_refine=12)
     assert info0["fell_back_fp64"] == 1 and oracle.backward_error(p, x0) <= 1e-13
+
+
+def test_refinement_after_the_fallback_has_its_own_budget():
+    """BF16 GMRES that uses the whole step budget falls back to the
+    FP64-accurate factor of S; the refinement on that factor then has
+    max_refine steps of its own, so the solve still meets the tolerance (on the
+    9,241-bus system it had none left and stopped at 5.6e-9)."""
+    p = make_problem(replace(CONFIGS["grid2383_n96"], n_per=6))
+    x, info = gpu_solve(p, "bf16", refine_mode=1, max_refine=2, refine_tol=1e-13)
+    assert info["fell_back_fp64"] == 1
+    assert oracle.backward_error(p, x) <= 1e-13
+    assert info["refine_steps"] <= 2 + 1 + 2
