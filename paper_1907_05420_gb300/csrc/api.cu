@@ -336,8 +336,9 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   h->g_nkeys = (int64_t)g_key.size();
 
   // factor work items: 64-row tiles of every supernode outside the dense tail,
-  // grouped by level, then those of the tail supernodes; for every (tile,
-  // update) the rows [ia, ib) of the descendant that land in the tile
+  // grouped by level, then those of the tail supernodes; per item the updates
+  // that meet the tile, as (update index within s's list, rows [ia, ib) of the
+  // descendant that land in the tile), from the item's offset to the next item's
   std::vector<int32_t> fwork, twork, frange, flvl_sn;
   // algorithmic flops of the updates of each work item: descendant d adds w_d
   // multiply-adds to every target entry (row i, column j) of the tile with
@@ -358,19 +359,21 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
       items.push_back(s);
       items.push_back(lo);
       items.push_back(hi);
-      items.push_back((int32_t)(frange.size() / 2));
+      items.push_back((int32_t)(frange.size() / 3));
       for (int64_t u = S.upd_ptr[s]; u < S.upd_ptr[s + 1]; u++) {
         const int32_t* rel = S.upd_rel.data() + S.upd_reloff[u];
         const int64_t nrel = S.upd_reloff[u + 1] - S.upd_reloff[u];
         const int32_t ia = S.upd_r0[u] + (int32_t)(std::lower_bound(rel, rel + nrel, lo) - rel);
         const int32_t ib = S.upd_r0[u] + (int32_t)(std::lower_bound(rel, rel + nrel, hi) - rel);
-        frange.push_back(ia);
-        frange.push_back(ib);
         const int dd = S.upd_src[u];
         // the tail's own updates among its supernodes run in the dense tail factor
         const bool counted = !(s >= S.tail_sn && u - S.upd_ptr[s] >= S.upd_ntail[s]);
-        if (counted)
+        if (counted && ia < ib) {
+          frange.push_back((int32_t)(u - S.upd_ptr[s]));
+          frange.push_back(ia);
+          frange.push_back(ib);
           item_flops += pair_flops(ia, ib, S.upd_r0[u], S.upd_r1[u], S.sn_first[dd + 1] - S.sn_first[dd]);
+        }
       }
     }
   };
@@ -389,10 +392,16 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
     h->fwork_lvl_ptr[l + 1] = (int32_t)(fwork.size() / 4);
     h->flvl_ptr[l + 1] = (int32_t)flvl_sn.size();
   }
+  // a closing item after each list gives its last item the end of its updates
+  const auto close_items = [&](std::vector<int32_t>& items) {
+    items.insert(items.end(), {0, 0, 0, (int32_t)(frange.size() / 3)});
+  };
+  close_items(fwork);
   item_flops = 0.0;
   for (int s = S.tail_sn; s < S.nsuper; s++) add_items(s, twork);
   h->tupd_flops = item_flops;
   h->tail_items = (int32_t)(twork.size() / 4);
+  close_items(twork);
   // per-column pivot position and primal flag
   std::vector<int64_t> col_dpos(n);
   std::vector<int32_t> col_primal(n);

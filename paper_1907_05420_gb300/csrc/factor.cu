@@ -17,7 +17,7 @@
 //     pivot_eps*max|A_i| is replaced by the expected-sign value and counted).
 // The top of the tree (the dense tail, a suffix of the supernodes) is left out
 // of the level loop: once the rest is factored, its updates from outside the
-// tail are applied (k_factor_update<true>) and the tail is factored as one
+// tail are applied (k_factor_update over the tail's lists) and the tail is factored as one
 // dense triangle per block (tail.cu).
 // Every entry is written by one thread in a fixed order: the result does not
 // depend on scheduling.
@@ -77,16 +77,15 @@ __global__ void k_block_absmax(const double* __restrict__ a_vals, int64_t nnzA,
 }
 
 // One CTA per (64-row tile of supernode s, block).  The tile's update is
-// accumulated in shared memory over all descendants d (in update order) and
-// subtracted from the panel once.  For each update the rows of d that land in
-// the tile ([ia, ib), precomputed per tile) and the rows that land in s's
-// columns ([r0, r1)) are staged in shared memory, the latter pre-multiplied by D_d.
-// NONTAIL: apply only the updates from descendants outside the dense tail
-// (the leading upd_ntail[s] entries of s's list); used for the tail supernodes,
-// whose updates among themselves the dense tail factor performs.
+// accumulated in shared memory over the descendants d that meet the tile (in
+// update order) and subtracted from the panel once.  For each update the rows
+// of d that land in the tile ([ia, ib), listed per tile at analysis with only
+// the updates that meet it) and the rows that land in s's columns ([r0, r1))
+// are staged in shared memory, the latter pre-multiplied by D_d.  For the tail
+// supernodes the lists hold only the updates from descendants outside the
+// dense tail; their updates among themselves are the dense tail factor's.
 constexpr int kTileRows = kFactorTileRows;
 
-template <bool NONTAIL>
 __global__ void __launch_bounds__(256) k_factor_update(const int32_t* __restrict__ work,
                                                        const int32_t* __restrict__ frange, DevSym d,
                                                        double* __restrict__ Lx, int64_t pt) {
@@ -96,16 +95,16 @@ __global__ void __launch_bounds__(256) k_factor_update(const int32_t* __restrict
   __shared__ int rs[kTileRows], tc[kMaxSnWidth];
   const int item = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
   const int s = work[4 * item], lo = work[4 * item + 1], hi = work[4 * item + 2];
-  const int roff = work[4 * item + 3];
+  const int p0 = work[4 * item + 3], p1 = work[4 * item + 7];  // this item's updates, to the next item's
   const int ms = (int)(d.sn_rowptr[s + 1] - d.sn_rowptr[s]);
   const int f = d.sn_first[s], ws = d.sn_first[s + 1] - f;
   const int nrow = hi - lo;
   double* P = Lx + b * pt + d.sn_valoff[s];
   for (int q = tid; q < kTileRows * (kMaxSnWidth + 1); q += blockDim.x) (&acc[0][0])[q] = 0.0;
-  const int64_t u0 = d.upd_ptr[s], u1 = NONTAIL ? u0 + d.upd_ntail[s] : d.upd_ptr[s + 1];
-  for (int64_t u = u0; u < u1; u++) {
-    const int ia = frange[2 * (roff + (u - u0))], ib = frange[2 * (roff + (u - u0)) + 1];
-    if (ia >= ib) continue;  // no row of this descendant falls in the tile
+  const int64_t u0 = d.upd_ptr[s];
+  for (int p = p0; p < p1; p++) {
+    const int64_t u = u0 + frange[3 * p];
+    const int ia = frange[3 * p + 1], ib = frange[3 * p + 2];
     const int dd = d.upd_src[u];
     const int r0 = d.upd_r0[u], r1 = d.upd_r1[u];
     const int md = (int)(d.sn_rowptr[dd + 1] - d.sn_rowptr[dd]);
@@ -219,7 +218,7 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
     if (l > 0 && w1 > w0) {
       dim3 grid(w1 - w0, h.N);
       const int kt = kt_begin(h, kFamFactorUpd, h.N * h.fupd_flops[l], st);
-      k_factor_update<false><<<grid, 256, 0, st>>>(h.d.fwork + 4 * w0, h.d.frange, h.d, h.Lx, pt);
+      k_factor_update<<<grid, 256, 0, st>>>(h.d.fwork + 4 * w0, h.d.frange, h.d, h.Lx, pt);
       kt_end(h, kt, st);
       h.launches++;
     }
@@ -242,7 +241,7 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
     if (h.tail_items > 0) {
       dim3 grid(h.tail_items, h.N);
       const int kt = kt_begin(h, kFamFactorUpd, h.N * h.tupd_flops, st);
-      k_factor_update<true><<<grid, 256, 0, st>>>(h.d.twork, h.d.frange, h.d, h.Lx, pt);
+      k_factor_update<<<grid, 256, 0, st>>>(h.d.twork, h.d.frange, h.d, h.Lx, pt);
       kt_end(h, kt, st);
       h.launches++;
     }

@@ -42,8 +42,8 @@ struct DevSym {
   int64_t* col_dpos = nullptr;     // per column: panel position of its pivot
   int32_t* diag_pos = nullptr;     // per row of A (pattern order): position of its diagonal entry
   // factor update work items: (supernode, first panel row, last panel row)
-  int32_t* fwork = nullptr;        // 4 ints per item: s, lo, hi, offset into frange
-  int32_t* frange = nullptr;       // per (item, update of s): rows [ia, ib) of d inside the tile
+  int32_t* fwork = nullptr;        // 4 ints per item: s, lo, hi, its first update in frange (a closing item ends the list)
+  int32_t* frange = nullptr;       // per item, the updates of s that meet the tile: (index in s's list, ia, ib)
   // symmetric full CSR of A for the residual: entry p reads a_vals[full_src[p]]
   int32_t* full_rowptr = nullptr;
   int32_t* full_col = nullptr;
