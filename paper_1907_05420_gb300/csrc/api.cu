@@ -58,7 +58,7 @@ kkt_status cuda_status(cudaError_t e, const char* what) {
 void free_all(Handle* h) {
   void* ptrs[] = {h->d.sn_first, h->d.sn_rowptr, h->d.sn_rows, h->d.sn_valoff, h->d.upd_ptr,
                   h->d.upd_src, h->d.upd_r0, h->d.upd_r1, h->d.upd_reloff, h->d.upd_rel,
-                  h->d.lvl_sn, h->d.perm, h->d.a_map, h->d.col_primal, h->d.col_dpos, h->d.diag_pos, h->d.fwork, h->d.frange,
+                  h->d.lvl_sn, h->d.perm, h->d.a_map, h->d.col_primal, h->d.col_dpos, h->d.diag_pos, h->d.fwork, h->d.fpairs,
                   h->d.full_rowptr, h->d.full_col, h->d.full_src, h->d.b_row, h->d.b_col,
                   h->d.b_blockptr, h->d.e_t, h->d.e_block, h->d.wpos, h->d.sn_wrow, h->d.w_dpos,
                   h->d.w_col, h->d.reach_lvl_sn, h->d.s_key, h->d.s_ptr, h->d.s_e1, h->d.s_e2,
@@ -339,7 +339,8 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   // grouped by level, then those of the tail supernodes; per item the updates
   // that meet the tile, as (update index within s's list, rows [ia, ib) of the
   // descendant that land in the tile), from the item's offset to the next item's
-  std::vector<int32_t> fwork, twork, frange, flvl_sn;
+  std::vector<int32_t> fwork, twork, flvl_sn;
+  std::vector<UpdPair> fpairs;
   // algorithmic flops of the updates of each work item: descendant d adds w_d
   // multiply-adds to every target entry (row i, column j) of the tile with
   // i >= j, i one of d's rows in the tile ([ia, ib)), j one in s's columns ([r0, r1))
@@ -359,7 +360,7 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
       items.push_back(s);
       items.push_back(lo);
       items.push_back(hi);
-      items.push_back((int32_t)(frange.size() / 3));
+      items.push_back((int32_t)fpairs.size());
       for (int64_t u = S.upd_ptr[s]; u < S.upd_ptr[s + 1]; u++) {
         const int32_t* rel = S.upd_rel.data() + S.upd_reloff[u];
         const int64_t nrel = S.upd_reloff[u + 1] - S.upd_reloff[u];
@@ -369,9 +370,17 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
         // the tail's own updates among its supernodes run in the dense tail factor
         const bool counted = !(s >= S.tail_sn && u - S.upd_ptr[s] >= S.upd_ntail[s]);
         if (counted && ia < ib) {
-          frange.push_back((int32_t)(u - S.upd_ptr[s]));
-          frange.push_back(ia);
-          frange.push_back(ib);
+          UpdPair pr;
+          pr.rel = S.upd_reloff[u];
+          pr.val = S.sn_valoff[dd];
+          pr.rows = S.sn_rowptr[dd];
+          pr.ia = ia;
+          pr.ib = ib;
+          pr.r0 = S.upd_r0[u];
+          pr.r1 = S.upd_r1[u];
+          pr.md = (int32_t)(S.sn_rowptr[dd + 1] - S.sn_rowptr[dd]);
+          pr.wd = S.sn_first[dd + 1] - S.sn_first[dd];
+          fpairs.push_back(pr);
           item_flops += pair_flops(ia, ib, S.upd_r0[u], S.upd_r1[u], S.sn_first[dd + 1] - S.sn_first[dd]);
         }
       }
@@ -394,7 +403,7 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   }
   // a closing item after each list gives its last item the end of its updates
   const auto close_items = [&](std::vector<int32_t>& items) {
-    items.insert(items.end(), {0, 0, 0, (int32_t)(frange.size() / 3)});
+    items.insert(items.end(), {0, 0, 0, (int32_t)fpairs.size()});
   };
   close_items(fwork);
   item_flops = 0.0;
@@ -492,7 +501,7 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   UP(col_dpos, col_dpos);
   UP(diag_pos, diag_pos);
   UP(fwork, fwork);
-  UP(frange, frange);
+  UP(fpairs, fpairs);
   UP(flvl_sn, flvl_sn);
   UP(twork, twork);
   UP(upd_ntail, S.upd_ntail);

@@ -87,7 +87,7 @@ __global__ void k_block_absmax(const double* __restrict__ a_vals, int64_t nnzA,
 constexpr int kTileRows = kFactorTileRows;
 
 __global__ void __launch_bounds__(256) k_factor_update(const int32_t* __restrict__ work,
-                                                       const int32_t* __restrict__ frange, DevSym d,
+                                                       const UpdPair* __restrict__ pairs, DevSym d,
                                                        double* __restrict__ Lx, int64_t pt) {
   __shared__ double acc[kTileRows][kMaxSnWidth + 1];
   __shared__ double Li[kTileRows][kMaxSnWidth + 1];
@@ -99,35 +99,33 @@ __global__ void __launch_bounds__(256) k_factor_update(const int32_t* __restrict
   const int ms = (int)(d.sn_rowptr[s + 1] - d.sn_rowptr[s]);
   const int f = d.sn_first[s], ws = d.sn_first[s + 1] - f;
   const int nrow = hi - lo;
+  const double* Lb = Lx + b * pt;
   double* P = Lx + b * pt + d.sn_valoff[s];
   for (int q = tid; q < kTileRows * (kMaxSnWidth + 1); q += blockDim.x) (&acc[0][0])[q] = 0.0;
-  const int64_t u0 = d.upd_ptr[s];
+  UpdPair Rn{};  // the next update's record, loaded during this one's products
+  if (p0 < p1) Rn = pairs[p0];
   for (int p = p0; p < p1; p++) {
-    const int64_t u = u0 + frange[3 * p];
-    const int ia = frange[3 * p + 1], ib = frange[3 * p + 2];
-    const int dd = d.upd_src[u];
-    const int r0 = d.upd_r0[u], r1 = d.upd_r1[u];
-    const int md = (int)(d.sn_rowptr[dd + 1] - d.sn_rowptr[dd]);
-    const int wd = d.sn_first[dd + 1] - d.sn_first[dd];
-    const double* Pd = Lx + b * pt + d.sn_valoff[dd];
-    const int32_t* Rd = d.sn_rows + d.sn_rowptr[dd];
-    const int32_t* rel = d.upd_rel + d.upd_reloff[u];
-    const int ni = ib - ia, nj = r1 - r0;
+    const UpdPair R = Rn;
+    const int ni = R.ib - R.ia, nj = R.r1 - R.r0, wd = R.wd, md = R.md;
+    const double* Pd = Lb + R.val;
+    const int32_t* Rd = d.sn_rows + R.rows;
+    const int32_t* rel = d.upd_rel + R.rel;
     __syncthreads();  // the previous update's reads of Li/Lj are done
     for (int q = tid; q < ni * wd; q += blockDim.x) {
       const int i = q % ni, kk = q / ni;
-      Li[i][kk] = Pd[(int64_t)kk * md + ia + i];
+      Li[i][kk] = Pd[(int64_t)kk * md + R.ia + i];
     }
     for (int q = tid; q < nj * wd; q += blockDim.x) {
       const int j = q % nj, kk = q / nj;
-      Lj[j][kk] = Pd[(int64_t)kk * md + r0 + j] * Pd[(int64_t)kk * md + kk];
+      Lj[j][kk] = Pd[(int64_t)kk * md + R.r0 + j] * Pd[(int64_t)kk * md + kk];
     }
-    for (int q = tid; q < ni; q += blockDim.x) rs[q] = rel[ia + q - r0] - lo;
-    for (int q = tid; q < nj; q += blockDim.x) tc[q] = Rd[r0 + q] - f;
+    for (int q = tid; q < ni; q += blockDim.x) rs[q] = rel[R.ia + q - R.r0] - lo;
+    for (int q = tid; q < nj; q += blockDim.x) tc[q] = Rd[R.r0 + q] - f;
     __syncthreads();
+    if (p + 1 < p1) Rn = pairs[p + 1];
     for (int q = tid; q < ni * nj; q += blockDim.x) {
       const int i = q % ni, j = q / ni;
-      if (ia + i < r0 + j) continue;  // above the diagonal of the target
+      if (R.ia + i < R.r0 + j) continue;  // above the diagonal of the target
       double sum = 0.0;
       for (int kk = 0; kk < wd; kk++) sum += Li[i][kk] * Lj[j][kk];
       acc[rs[i]][tc[j]] += sum;
@@ -218,7 +216,7 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
     if (l > 0 && w1 > w0) {
       dim3 grid(w1 - w0, h.N);
       const int kt = kt_begin(h, kFamFactorUpd, h.N * h.fupd_flops[l], st);
-      k_factor_update<<<grid, 256, 0, st>>>(h.d.fwork + 4 * w0, h.d.frange, h.d, h.Lx, pt);
+      k_factor_update<<<grid, 256, 0, st>>>(h.d.fwork + 4 * w0, h.d.fpairs, h.d, h.Lx, pt);
       kt_end(h, kt, st);
       h.launches++;
     }
@@ -241,7 +239,7 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
     if (h.tail_items > 0) {
       dim3 grid(h.tail_items, h.N);
       const int kt = kt_begin(h, kFamFactorUpd, h.N * h.tupd_flops, st);
-      k_factor_update<<<grid, 256, 0, st>>>(h.d.twork, h.d.frange, h.d, h.Lx, pt);
+      k_factor_update<<<grid, 256, 0, st>>>(h.d.twork, h.d.fpairs, h.d, h.Lx, pt);
       kt_end(h, kt, st);
       h.launches++;
     }

@@ -23,6 +23,19 @@ void set_error(const std::string& msg);
     }                                                                               \
   } while (0)
 
+// One update of a factor work item (a 64-row tile of supernode s) by a
+// descendant d that meets the tile, with everything the update kernel reads
+// about d, so that one load gives it.
+struct UpdPair {
+  int64_t rel;   // offset of the update's relative row map in upd_rel
+  int64_t val;   // offset of d's panel in a block's factor
+  int64_t rows;  // offset of d's row list in sn_rows
+  int32_t ia, ib;  // d's rows [ia, ib) land in the tile
+  int32_t r0, r1;  // d's rows [r0, r1) are columns of s
+  int32_t md, wd;  // rows and columns of d's panel
+};
+static_assert(sizeof(UpdPair) == 48, "UpdPair layout");
+
 // Device copies of the symbolic structures.
 struct DevSym {
   int32_t* sn_first = nullptr;
@@ -42,8 +55,8 @@ struct DevSym {
   int64_t* col_dpos = nullptr;     // per column: panel position of its pivot
   int32_t* diag_pos = nullptr;     // per row of A (pattern order): position of its diagonal entry
   // factor update work items: (supernode, first panel row, last panel row)
-  int32_t* fwork = nullptr;        // 4 ints per item: s, lo, hi, its first update in frange (a closing item ends the list)
-  int32_t* frange = nullptr;       // per item, the updates of s that meet the tile: (index in s's list, ia, ib)
+  int32_t* fwork = nullptr;        // 4 ints per item: s, lo, hi, its first update in fpairs (a closing item ends the list)
+  UpdPair* fpairs = nullptr;       // per item, the updates of s that meet the tile
   // symmetric full CSR of A for the residual: entry p reads a_vals[full_src[p]]
   int32_t* full_rowptr = nullptr;
   int32_t* full_col = nullptr;
