@@ -136,12 +136,19 @@ __global__ void __launch_bounds__(256) k_diag_inverse(const T* __restrict__ L0, 
 // L y = b in place (unit lower L, column-major n x n, leading dimension n).
 // One CTA per 64-row block, taken in ticket order; block t adds the products
 // of the finished blocks j < t (each awaited on its flag), then applies X_t.
+// For an FP32 factor (the TF32 and BF16 modes) the products of each 64 x 64
+// block are formed in FP32 (x_j rounded to FP32, 16 FMAs per thread) and added
+// to the FP64 row sums once per block: the FP32 factor's own error is some
+// 1e-4 relative, far above the 1e-7 of these products, and the conversions
+// and FMAs stay off this GPU's narrow FP64 pipe.  The FP64 factor keeps FP64
+// products.
 template <class T>
 __global__ void __launch_bounds__(256) k_trsv_lower(const T* __restrict__ L, int n, double* x,
                                                     int* flags, unsigned* ticket, int epoch, int* err,
                                                     const int* __restrict__ jlo, const double* __restrict__ X) {
   __shared__ int s_blk, s_ok;
   __shared__ double yj[64];
+  __shared__ T yjt[64];  // x_j in the factor's type, for the products
   __shared__ double part[4][64];
   __shared__ double Xs[64][65];
   const int tid = threadIdx.x;
@@ -158,12 +165,19 @@ __global__ void __launch_bounds__(256) k_trsv_lower(const T* __restrict__ L, int
     if (tid == 0 && !wait_flag(flags + j, epoch, err)) s_ok = 0;
     __syncthreads();
     if (!s_ok) break;
-    if (tid < 64) yj[tid] = __ldcg(x + j * 64 + tid);
+    if (tid < 64) yjt[tid] = (T)__ldcg(x + j * 64 + tid);
     __syncthreads();
     if (r < rows) {
       const T* col = L + (int64_t)(r0 + r) + (int64_t)(j * 64 + pid * 16) * n;
+      if constexpr (sizeof(T) == 8) {
 #pragma unroll 4
-      for (int c = 0; c < 16; c++) acc += (double)col[(int64_t)c * n] * yj[pid * 16 + c];
+        for (int c = 0; c < 16; c++) acc += col[(int64_t)c * n] * yjt[pid * 16 + c];
+      } else {
+        T a = T(0);
+#pragma unroll 4
+        for (int c = 0; c < 16; c++) a += col[(int64_t)c * n] * yjt[pid * 16 + c];
+        acc += (double)a;
+      }
     }
     __syncthreads();
   }
@@ -196,6 +210,7 @@ __global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ L, int
                                                     const double* __restrict__ dinv) {
   __shared__ int s_blk, s_ok;
   __shared__ double xj[64];
+  __shared__ T xjt[64];  // x_j in the factor's type, for the products
   __shared__ double accs[64];
   __shared__ double part[4][64];
   __shared__ double Xs[64][65];
@@ -214,18 +229,18 @@ __global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ L, int
     __syncthreads();
     if (!s_ok) break;
     const int c0 = j * 64, cols = min(64, n - c0);
-    if (tid < 64) xj[tid] = tid < cols ? __ldcg(x + c0 + tid) : 0.0;
+    if (tid < 64) xjt[tid] = tid < cols ? (T)__ldcg(x + c0 + tid) : T(0);
     __syncthreads();
     // warp w handles rows 8w..8w+7 of this block; lanes run along the column
     for (int rr = warp * 8; rr < warp * 8 + 8; rr++) {
       if (rr >= rows) break;
       const T* col = L + (int64_t)(r0 + rr) * n + c0;
-      double v = 0.0;
-      if (lane < cols) v += (double)col[lane] * xj[lane];
-      if (lane + 32 < cols) v += (double)col[lane + 32] * xj[lane + 32];
+      T v = T(0);
+      if (lane < cols) v += col[lane] * xjt[lane];
+      if (lane + 32 < cols) v += col[lane + 32] * xjt[lane + 32];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) accs[rr] += v;
+      if (lane == 0) accs[rr] += (double)v;
     }
     __syncthreads();
   }

@@ -28,9 +28,13 @@
 // the augmented rows become W_T^T D_T^{-1} with W_T = L_T^{-1} Z, and the
 // trailing k x k block becomes -W_T^T D_T^{-1} W_T, the tail's share of G.  So
 // the tail's W solve and contraction run inside the tail factor.
+#include <cooperative_groups.h>
+
 #include "dense_kernels.cuh"
 
 namespace kkt {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -117,17 +121,33 @@ __global__ void __launch_bounds__(256) k_tail_fgather(DevSym d, const double* __
   }
 }
 
-// Dense triangular solves of the tails, one CTA per block, in 64-row steps
-// with the diagonal-block inverses X_t.  Forward (L_T y = z): y_t = X_t z_t,
-// then the rows below take z_i -= L_it y_t.  Backward (L_T^T x = y): x_t =
-// X_t^T y_t, then the rows above take y_i -= L_ti^T x_t.  zt points at the
-// tail's first entry of block 0 (blocks nA apart).
+// Dense triangular solves of the tails in 64-row steps with the
+// diagonal-block inverses X_t.  Forward (L_T y = z): y_t = X_t z_t, then the
+// rows below take z_i -= L_it y_t.  Backward (L_T^T x = y): x_t = X_t^T y_t,
+// then the rows above take y_i -= L_ti^T x_t.  zt points at the tail's first
+// entry of block 0 (blocks nA apart).
+//
+// A cluster of kTrsvCluster CTAs per block: the 64-row blocks of the tail are
+// owned cyclically (block u by CTA u mod kTrsvCluster), each CTA updates only
+// its own rows, and the CTAs meet at one hardware cluster barrier per step,
+// after which the owner's z_t is complete; every CTA reads it from L2 and
+// forms X_t z_t itself.  The owner keeps that solution block and stores it
+// after the next barrier, when every CTA has read z_t.  The FP64 work of a tail
+// thus spreads over several SMs, and a batch of N tails over N x kTrsvCluster
+// CTAs, which also evens out N tails on 152 SMs.
+constexpr int kTrsvCluster = 4;
+
 template <bool FORWARD>
-__global__ void __launch_bounds__(256) k_tail_trsv(const double* __restrict__ T, int nT, int nTa,
-                                                   const double* __restrict__ X, double* __restrict__ zt, int nA) {
+__global__ void __cluster_dims__(kTrsvCluster, 1, 1) __launch_bounds__(256)
+    k_tail_trsv(const double* __restrict__ T, int nT, int nTa, const double* __restrict__ X,
+                double* __restrict__ zt, int nA) {
   __shared__ double v[64];
+  __shared__ double pend[64];  // the solution of the block this CTA owns, stored a step later
   __shared__ double part[4][64];
-  const int b = blockIdx.x, tid = threadIdx.x, r = tid & 63, pid = tid >> 6;
+  cg::cluster_group cluster = cg::this_cluster();
+  int pend_r0 = -1, pend_rows = 0;
+  const int q = (int)cluster.block_rank();
+  const int b = blockIdx.x / kTrsvCluster, tid = threadIdx.x, r = tid & 63, pid = tid >> 6;
   const int nbT = (nT + 63) / 64;
   const double* Tb = T + (int64_t)b * nTa * nTa;
   const double* Xb = X + (int64_t)b * nbT * 4096;
@@ -135,7 +155,10 @@ __global__ void __launch_bounds__(256) k_tail_trsv(const double* __restrict__ T,
   for (int step = 0; step < nbT; step++) {
     const int t = FORWARD ? step : nbT - 1 - step;
     const int r0 = t * 64, rows = min(64, nT - r0);
-    if (tid < 64) v[tid] = tid < rows ? z[r0 + tid] : 0.0;
+    cluster.sync();  // the owner's updates of z_t (its own rows) are done and visible
+    if (pend_r0 >= 0 && tid < pend_rows) z[pend_r0 + tid] = pend[tid];  // every CTA has read that block
+    pend_r0 = -1;
+    if (tid < 64) v[tid] = tid < rows ? __ldcg(z + r0 + tid) : 0.0;
     __syncthreads();
     // X_t v (forward) or X_t^T v (backward), 4 partial sums per output
     double acc = 0.0;
@@ -148,24 +171,31 @@ __global__ void __launch_bounds__(256) k_tail_trsv(const double* __restrict__ T,
     if (tid < 64) {
       const double y = part[0][tid] + part[1][tid] + part[2][tid] + part[3][tid];
       v[tid] = y;
-      if (tid < rows) z[r0 + tid] = y;
+      pend[tid] = y;
+    }
+    if (t % kTrsvCluster == q) {
+      pend_r0 = r0;
+      pend_rows = rows;
     }
     __syncthreads();
-    if (FORWARD) {
-      for (int i = r0 + 64 + tid; i < nT; i += blockDim.x) {
-        double a = 0.0;
+    // this CTA's rows after (forward) or before (backward) block t: its blocks
+    // u = q, q + kTrsvCluster, ... four at a time over the 256 threads
+    const int ub = FORWARD ? t + 1 : 0, ue = FORWARD ? nbT : t;
+    const int u0 = ub + ((q - ub) % kTrsvCluster + kTrsvCluster) % kTrsvCluster;
+    for (int u = u0 + (tid >> 6) * kTrsvCluster; u < ue; u += 4 * kTrsvCluster) {
+      const int i = u * 64 + r;
+      if (i >= nT) continue;
+      double a = 0.0;
+      if (FORWARD) {
         for (int c = 0; c < rows; c++) a += Tb[(int64_t)i + (int64_t)(r0 + c) * nTa] * v[c];
-        z[i] -= a;
-      }
-    } else {
-      for (int i = tid; i < r0; i += blockDim.x) {
-        double a = 0.0;
+      } else {
         for (int c = 0; c < rows; c++) a += Tb[(int64_t)(r0 + c) + (int64_t)i * nTa] * v[c];
-        z[i] -= a;
       }
+      z[i] -= a;
     }
-    __syncthreads();
   }
+  cluster.sync();
+  if (pend_r0 >= 0 && tid < pend_rows) z[pend_r0 + tid] = pend[tid];
 }
 
 }  // namespace
@@ -173,13 +203,13 @@ __global__ void __launch_bounds__(256) k_tail_trsv(const double* __restrict__ T,
 cudaError_t launch_tail_fsolve(Handle& h, double* z, cudaStream_t st) {
   const int nts = h.sym.nsuper - h.sym.tail_sn;
   k_tail_fgather<<<dim3(nts, h.N), 256, 0, st>>>(h.d, h.Lx, h.sym.panel_total, z, h.nA, h.sym.tail_sn);
-  k_tail_trsv<true><<<h.N, 256, 0, st>>>(h.Tt, h.nT, h.nTa, h.Xtail, z + h.sym.tail_col, h.nA);
+  k_tail_trsv<true><<<h.N * kTrsvCluster, 256, 0, st>>>(h.Tt, h.nT, h.nTa, h.Xtail, z + h.sym.tail_col, h.nA);
   h.launches += 2;
   return cudaGetLastError();
 }
 
 cudaError_t launch_tail_bsolve(Handle& h, double* z, cudaStream_t st) {
-  k_tail_trsv<false><<<h.N, 256, 0, st>>>(h.Tt, h.nT, h.nTa, h.Xtail, z + h.sym.tail_col, h.nA);
+  k_tail_trsv<false><<<h.N * kTrsvCluster, 256, 0, st>>>(h.Tt, h.nT, h.nTa, h.Xtail, z + h.sym.tail_col, h.nA);
   h.launches++;
   return cudaGetLastError();
 }
