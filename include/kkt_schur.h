@@ -165,6 +165,14 @@ typedef struct {
                            count one step per application of K~^{-1} (at most max_refine) and, in the
                            TF32/BF16 modes, refactor S FP64-accurately when they stop short. */
   int32_t gmres_restart; /* Krylov vectors per GMRES cycle (default 8) */
+  int32_t device_refine; /* refine_mode 0 only: run kkt_solve's application of the factorization and its
+                            refinement loop as one CUDA graph whose loop is a device-side conditional
+                            (WHILE) node: a one-thread kernel evaluates the convergence test, and the host
+                            reads the outcome once, after the loop, instead of a residual norm per step.
+                            The arithmetic is kkt_solve's own, step for step, so the solution is the same
+                            bit for bit.  When the loop stops above refine_tol in the TF32/BF16 modes,
+                            the FP64 fallback and its refinement run as without this option.  Not used for
+                            the first solve after a factor with early_solve.  Default 0. */
 } kkt_options;
 
 typedef struct {

@@ -43,7 +43,8 @@ class kkt_options(C.Structure):
                 ("fp64_fallback", C.c_int32), ("reduced_contraction", C.c_int32),
                 ("structured_s", C.c_int32), ("dense_tail", C.c_int32), ("autotune", C.c_int32),
                 ("early_solve", C.c_int32), ("time_kernels", C.c_int32), ("tail_ratio", C.c_double),
-                ("refine_mode", C.c_int32), ("gmres_restart", C.c_int32)]
+                ("refine_mode", C.c_int32), ("gmres_restart", C.c_int32),
+                ("device_refine", C.c_int32)]
 
 
 class kkt_info(C.Structure):

@@ -72,7 +72,7 @@ void free_all(Handle* h) {
                   h->ew_s_B, h->ew_s_scale, h->ew_t_Y, h->ew_t_A, h->ew_t_B, h->ew_t_scale, h->tc_imgA,
                   h->tc_imgB, h->tc_scaleA, h->tc_scaleB, h->gm_V, h->gm_Z, h->d.cum_y_ptr, h->d.cum_y_t,
                   h->d.cum_y_e, h->d.cum_z_ptr, h->d.cum_z_t, h->d.cum_z_e, h->d.cum_check, h->cum_err,
-                  h->cum_H, h->cum_Sd, h->cum_So, h->cum_Q, h->cum_QY, h->cum_Linv, h->cum_M, h->cum_Mt,
+                  h->rstate, h->cum_H, h->cum_Sd, h->cum_So, h->cum_Q, h->cum_QY, h->cum_Linv, h->cum_M, h->cum_Mt,
                   h->cum_D};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -83,6 +83,8 @@ void free_all(Handle* h) {
   for (cudaEvent_t ev : h->kt_ev)
     if (ev) cudaEventDestroy(ev);
   if (h->factor_exec) cudaGraphExecDestroy(h->factor_exec);
+  for (cudaGraphExec_t ex : h->solve_exec)
+    if (ex) cudaGraphExecDestroy(ex);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->side_stream) cudaStreamDestroy(h->side_stream);
   if (h->early_stream) cudaStreamDestroy(h->early_stream);
@@ -135,6 +137,51 @@ cudaError_t enqueue_factor(Handle& h, cudaStream_t st, bool with_s = true) {
   return e;
 }
 
+// The convergence test of the refinement on the device (device_refine): the
+// same test as kkt_solve's loop, from the norms of this step's residual, and
+// the decision whether the loop's body runs again (the body applies the
+// factorization to the residual, adds the correction and recomputes the
+// residual and its norms).  st: eta, eta_prev, steps, outcome (0 converged or
+// still running, 1 stopped above the tolerance, 2 a non-finite iterate, 3 a
+// non-finite K or right-hand side).
+__global__ void k_refine_decide(const double* __restrict__ red, const double* __restrict__ knorm, double tol,
+                                int max_steps, double* __restrict__ st, cudaGraphConditionalHandle loop,
+                                int first) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (first) {
+    st[1] = INFINITY;
+    st[2] = 0.0;
+  }
+  const double r0 = red[0], r1 = red[1], r2 = red[2], kn = knorm[0];
+  unsigned int again = 0;
+  double eta, outcome;
+  if (!isfinite(r2) || !isfinite(kn)) {
+    eta = NAN;
+    outcome = 3.0;  // a NaN or Inf in K or the right-hand side: no iterate can meet the test
+  } else {
+    const bool finite_x = isfinite(r0) && isfinite(r1);
+    eta = finite_x ? r0 / (kn * r1 + r2) : NAN;
+    if (finite_x && r0 == 0.0) eta = 0.0;
+    const double steps = st[2];
+    if (eta <= tol) {
+      outcome = 0.0;
+    } else {
+      const bool stalled = !(eta < 0.5 * st[1]) || !isfinite(eta);
+      if (steps >= (double)max_steps || (steps > 0.0 && stalled) || !finite_x) {
+        outcome = finite_x ? 1.0 : 2.0;
+      } else {
+        outcome = 0.0;
+        again = 1;
+        st[1] = eta;
+        st[2] = steps + 1.0;
+      }
+    }
+  }
+  st[0] = eta;
+  st[3] = outcome;
+  cudaGraphSetConditional(loop, again);
+}
+
 // Captures enqueue_factor into h.factor_exec; on any failure the handle keeps
 // launching directly.
 void capture_factor(Handle& h) {
@@ -177,6 +224,7 @@ void kkt_default_options(kkt_options* opt) {
   opt->fp64_fallback = 1;
   opt->dense_tail = -1;
   opt->gmres_restart = 8;
+  opt->device_refine = 0;
 }
 
 const char* kkt_status_string(kkt_status s) {
@@ -230,6 +278,11 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   }
   if (h->opt.structured_s < 0 || h->opt.structured_s > 2) {
     set_error("kkt_analyze: structured_s must be 0, 1 or 2");
+    delete h;
+    return KKT_ERR_INVALID;
+  }
+  if (h->opt.device_refine != 0 && (h->opt.device_refine != 1 || h->opt.refine_mode != 0)) {
+    set_error("kkt_analyze: device_refine must be 0, or 1 with refine_mode 0");
     delete h;
     return KKT_ERR_INVALID;
   }
@@ -615,6 +668,7 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   AL(rho, double, nK);
   AL(rhs, double, nK);
   AL(red, double, 1024);
+  AL(rstate, double, 4);
   if (h->opt.refine_mode == 1) {
     const int m = std::max(1, h->opt.gmres_restart);
     AL(gm_V, double, (int64_t)(m + 1) * nK);
@@ -783,6 +837,78 @@ kkt_status refactor_s_fp64(Handle* h, cudaStream_t st) {
   h->s_factor = 0;
   h->info.fell_back_fp64 = 1;
   return KKT_OK;
+}
+
+// The solve graph of device_refine: apply the factorization to h->rhs into
+// h->x, residual, norms and the test; then a WHILE node whose body is one
+// refinement step (apply to the residual, x += dx, residual, norms, test).
+// The application depends on the kind of factor of S the handle holds
+// (h.s_factor), so there is one graph per kind.  On any failure the handle
+// keeps the host loop for that kind.
+void build_solve_graph(Handle& h) {
+  const int sf = h.s_factor;
+  const int64_t nK = (int64_t)h.N * h.nA + h.nC;
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle loop{};
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&loop, g, 0, cudaGraphCondAssignDefault);
+  const int64_t l0 = h.launches;
+  h.solve_capturing = true;
+  auto capture_into = [&](cudaGraph_t target, bool prologue) -> cudaError_t {
+    cudaError_t c = cudaStreamBeginCaptureToGraph(h.cap_stream, target, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+    if (c != cudaSuccess) return c;
+    cudaError_t w;
+    if (prologue) {
+      w = launch_apply_inverse(h, h.rhs, h.x, h.cap_stream);
+    } else {
+      w = launch_apply_inverse(h, h.rho, h.dx, h.cap_stream);
+      if (w == cudaSuccess) w = launch_axpy(h, h.x, h.dx, nK, h.cap_stream);
+    }
+    if (w == cudaSuccess) w = launch_residual(h, h.rhs, h.x, h.rho, h.cap_stream);
+    if (w == cudaSuccess) w = launch_norms(h, h.rho, h.x, h.rhs, h.cap_stream);
+    if (w == cudaSuccess) {
+      k_refine_decide<<<1, 32, 0, h.cap_stream>>>(h.red, h.knorm, h.opt.refine_tol, h.opt.max_refine, h.rstate,
+                                                   loop, prologue ? 1 : 0);
+      w = cudaGetLastError();
+    }
+    cudaGraph_t out = nullptr;
+    c = cudaStreamEndCapture(h.cap_stream, &out);
+    return w != cudaSuccess ? w : c;
+  };
+  if (e == cudaSuccess) e = capture_into(g, true);
+  // the loop node after every leaf of the prologue
+  std::vector<cudaGraphNode_t> leaves;
+  if (e == cudaSuccess) {
+    size_t nn = 0;
+    e = cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+    for (size_t i = 0; e == cudaSuccess && i < nn; i++) {
+      size_t nd = 0;
+      e = cudaGraphNodeGetDependentNodes(nodes[i], nullptr, nullptr, &nd);
+      if (e == cudaSuccess && nd == 0) leaves.push_back(nodes[i]);
+    }
+  }
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = loop;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t wnode = nullptr;
+    e = cudaGraphAddNode(&wnode, g, leaves.data(), nullptr, leaves.size(), &np);
+    if (e == cudaSuccess) e = capture_into(np.conditional.phGraph_out[0], false);
+  }
+  h.solve_capturing = false;
+  h.launches = l0;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h.solve_exec[sf], g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess || !h.solve_exec[sf]) {
+    h.solve_graph_failed[sf] = true;
+    h.solve_exec[sf] = nullptr;
+    (void)cudaGetLastError();
+  }
 }
 
 // One cycle of GMRES refinement (right preconditioning by the factorization
@@ -1065,7 +1191,49 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
   for (int32_t q = 0; q < nrhs; q++) {
     const double* rq = rhs + q * nK;
     double* xq = x + q * nK;
-    if (q == 0 && h->opt.early_solve && h->schur_pending) {
+    const bool early = q == 0 && h->opt.early_solve && h->schur_pending;
+    const int sf = h->s_factor;
+    if (h->opt.device_refine && !early && !h->solve_exec[sf] && !h->solve_graph_failed[sf]) build_solve_graph(*h);
+    const bool on_graph = h->opt.device_refine && !early && h->solve_exec[sf];
+    int steps = 0, before_fallback = 0;  // steps of this refinement, of the one before the FP64 fallback
+    bool nonfinite = false, host_loop = true;
+    double eta = INFINITY, eta_prev = INFINITY;
+    if (on_graph) {
+      // the application and the refinement loop on the device; one read of the outcome
+      KKT_CUDA(cudaMemcpyAsync(h->rhs, rq, sizeof(double) * nK,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+      KKT_CUDA(cudaGraphLaunch(h->solve_exec[sf], st));
+      KKT_CUDA(cudaMemcpyAsync(h->host_red, h->rstate, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+      KKT_CUDA(cudaMemcpyAsync(h->host_red + 4, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      if (h->cum) KKT_CUDA(cudaMemcpyAsync(h->host_red + 5, h->cum_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      KKT_CUDA(cudaStreamSynchronize(st));
+      if (*reinterpret_cast<int*>(h->host_red + 4) != 0) {
+        set_error("kkt_solve: a bounded device wait ran out");
+        return KKT_ERR_TIMEOUT;
+      }
+      if (h->cum && *reinterpret_cast<int*>(h->host_red + 5) != 0) {
+        set_error("kkt_solve: B's values do not repeat over the later periods (structured_s = 2)");
+        return KKT_ERR_INVALID;
+      }
+      eta = h->host_red[0];
+      steps = (int)h->host_red[2];
+      const int outcome = (int)h->host_red[3];
+      host_loop = false;
+      if (outcome == 3) {
+        nonfinite = true;  // a NaN or Inf among the values of K or the right-hand side
+      } else if (outcome != 0 && h->s_factor == 1 && h->opt.fp64_fallback) {
+        // stopped above the tolerance with the FP32 factor of S: the fallback
+        // and its refinement run on the host, as without device_refine
+        const kkt_status rs = refactor_s_fp64(h, st);
+        if (rs != KKT_OK) return rs;
+        KKT_CUDA(launch_apply_inverse(*h, h->rhs, h->x, st));
+        before_fallback = steps + 1;
+        steps = 0;
+        host_loop = true;
+      } else if (outcome == 2) {
+        nonfinite = true;
+      }
+    } else if (early) {
       // the front half needs only the block factors and W: it starts when the
       // preceding factor's Schur assembly ends, beside the dense factor of S
       KKT_CUDA(cudaStreamWaitEvent(h->early_stream, h->ev_fb, 0));
@@ -1081,10 +1249,7 @@ kkt_status kkt_solve(kkt_handle* hh, const double* rhs, double* x, int32_t nrhs,
       KKT_CUDA(launch_apply_inverse(*h, h->rhs, h->x, st));
     }
     h->schur_pending = false;
-    int steps = 0, before_fallback = 0;  // steps of this refinement, of the one before the FP64 fallback
-    bool nonfinite = false;
-    double eta = INFINITY, eta_prev = INFINITY;
-    for (;;) {
+    while (host_loop) {
       KKT_CUDA(launch_residual(*h, h->rhs, h->x, h->rho, st));
       KKT_CUDA(launch_norms(*h, h->rho, h->x, h->rhs, st));
       KKT_CUDA(cudaMemcpyAsync(h->host_red, h->red, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));

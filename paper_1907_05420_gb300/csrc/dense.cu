@@ -265,6 +265,25 @@ __global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ L, int
 
 }  // namespace
 
+// The epochs the two triangular solves of one application wait for (a block's
+// flag holds the epoch of the last solve that finished it; a wait ends once it
+// is at least the solve's own).  Launched directly, each solve takes new,
+// growing ones, starting above kGraphEpoch; inside the solve graph, whose
+// launches replay their captured arguments, the flags are cleared first and
+// the fixed kGraphEpoch is used, which leaves flags below every later direct
+// epoch.
+constexpr int kGraphEpoch = 1;
+
+static cudaError_t trsv_epochs(Handle& h, int nb, int& ep_f, int& ep_b, cudaStream_t st) {
+  if (h.solve_capturing) {
+    ep_f = ep_b = kGraphEpoch;
+    return cudaMemsetAsync(h.trsv_flags, 0, sizeof(int) * 2 * (size_t)nb, st);
+  }
+  ep_f = ++h.trsv_epoch;
+  ep_b = ++h.trsv_epoch;
+  return cudaSuccess;
+}
+
 cudaError_t launch_dense_ldlt(Handle& h, unsigned long long* counters, cudaStream_t st) {
   const int n = h.nC;
   for (int k0 = 0; k0 < n; k0 += NB) {
@@ -294,7 +313,9 @@ cudaError_t launch_dense_solve(Handle& h, const double* t, double* x, cudaStream
   if (e == cudaSuccess) e = cudaMemsetAsync(h.trsv_ticket, 0, sizeof(unsigned) * 2, st);
   if (e != cudaSuccess) return e;
   // flags hold the epoch of the last solve that finished each block; two per solve
-  const int ep_f = ++h.trsv_epoch, ep_b = ++h.trsv_epoch;
+  int ep_f, ep_b;
+  e = trsv_epochs(h, nb, ep_f, ep_b, st);
+  if (e != cudaSuccess) return e;
   k_trsv_lower<double><<<nb, 256, 0, st>>>(h.S, n, x, h.trsv_flags, h.trsv_ticket, ep_f, h.dev_err,
                                            h.d.trsv_jlo, h.Xinv);
   k_trsv_upper<double><<<nb, 256, 0, st>>>(h.S, n, x, h.trsv_flags + nb, h.trsv_ticket + 1, ep_b,
@@ -372,7 +393,9 @@ cudaError_t launch_dense_solve_f32(Handle& h, const double* t, double* x, cudaSt
   cudaError_t e = cudaMemcpyAsync(x, t, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h.trsv_ticket, 0, sizeof(unsigned) * 2, st);
   if (e != cudaSuccess) return e;
-  const int ep_f = ++h.trsv_epoch, ep_b = ++h.trsv_epoch;
+  int ep_f, ep_b;
+  e = trsv_epochs(h, nb, ep_f, ep_b, st);
+  if (e != cudaSuccess) return e;
   k_trsv_lower<float><<<nb, 256, 0, st>>>(h.S32, n, x, h.trsv_flags, h.trsv_ticket, ep_f, h.dev_err,
                                           h.d.trsv_jlo, h.Xinv);
   k_trsv_upper<float><<<nb, 256, 0, st>>>(h.S32, n, x, h.trsv_flags + nb, h.trsv_ticket + 1, ep_b,

@@ -197,6 +197,14 @@ struct Handle {
   int* trsv_flags = nullptr;  // 2 * ceil(nC/64): block-ready epochs of the dense triangular solves
   unsigned* trsv_ticket = nullptr;  // 2 tickets (forward, backward)
   int* dev_err = nullptr;     // set when a bounded device wait runs out
+  // device-side refinement (opt.device_refine): the solve graph and its loop state
+  // (eta, eta_prev, steps, outcome: 0 converged, 1 stopped above the tolerance, 2 not finite)
+  // one graph per kind of factor of S (s_factor: the FP32 one of the TF32/BF16
+  // modes, or the FP64-accurate one, also after a fallback), built at first use
+  cudaGraphExec_t solve_exec[2] = {nullptr, nullptr};
+  bool solve_graph_failed[2] = {false, false};
+  bool solve_capturing = false;  // the dense triangular solves clear their flags instead of advancing an epoch
+  double* rstate = nullptr;
   // structured S of the cumulative coupling (structured_s = 2, cumulative.cu):
   // ns x ns blocks, column-major, N of each unless noted
   bool cum = false;
@@ -212,7 +220,7 @@ struct Handle {
   double* cum_M = nullptr;     // M_j = L21_j L_j^{-1} (the last zero)
   double* cum_Mt = nullptr;    // M_j^T
   double* cum_D = nullptr;     // N x ns: the pivots
-  int trsv_epoch = 0;
+  int trsv_epoch = 1;          // the last epoch of a direct triangular solve of S (graph solves use 1)
   int64_t device_bytes = 0;
 
   bool factored = false;

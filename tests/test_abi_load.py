@@ -56,7 +56,7 @@ def test_status_strings_without_gpu():
     opt = binding.kkt_default_options()
     assert opt.refine_tol == 1e-10 and opt.max_refine == 10 and opt.prec == 0
     assert opt.tail_ratio == 0.0 and opt.dense_tail == -1 and opt.use_graphs == 1
-    assert opt.refine_mode == 0 and opt.gmres_restart == 8
+    assert opt.refine_mode == 0 and opt.gmres_restart == 8 and opt.device_refine == 0
 
 
 def test_inertia_defaults_without_gpu():
@@ -82,7 +82,7 @@ def test_struct_layouts_match_header(tmp_path):
         "sizeof(kkt_pattern), offsetof(kkt_pattern, a_vals_hint),"
         "sizeof(kkt_options), offsetof(kkt_options, reduced_contraction),"
         "offsetof(kkt_options, dense_tail), offsetof(kkt_options, tail_ratio),"
-        "offsetof(kkt_options, gmres_restart),"
+        "offsetof(kkt_options, device_refine),"
         "sizeof(kkt_info), offsetof(kkt_info, n_launches), offsetof(kkt_info, tail_ratio),"
         "sizeof(kkt_inertia_options), offsetof(kkt_inertia_options, max_trials),"
         "sizeof(kkt_inertia_result), offsetof(kkt_inertia_result, trials));"
@@ -94,7 +94,7 @@ def test_struct_layouts_match_header(tmp_path):
     want = [ctypes.sizeof(binding.kkt_pattern), binding.kkt_pattern.a_vals_hint.offset,
             ctypes.sizeof(binding.kkt_options), binding.kkt_options.reduced_contraction.offset,
             binding.kkt_options.dense_tail.offset, binding.kkt_options.tail_ratio.offset,
-            binding.kkt_options.gmres_restart.offset,
+            binding.kkt_options.device_refine.offset,
             ctypes.sizeof(binding.kkt_info), binding.kkt_info.n_launches.offset,
             binding.kkt_info.tail_ratio.offset,
             ctypes.sizeof(binding.kkt_inertia_options), binding.kkt_inertia_options.max_trials.offset,
