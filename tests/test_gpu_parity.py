@@ -262,3 +262,29 @@ def test_early_solve_matches(prec):
     assert np.array_equal(x0, x1)
     x2, _ = gpu_solve(p, prec, early_solve=1, device_arrays=True)
     assert np.array_equal(x0, x2)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_full_size_2383_bus_96_periods_reduced_modes(prec):
+    """The reduced-precision factors of S at full size: eta by the oracle's
+    residual after GMRES refinement to 1e-12, and the inertia of K from
+    kkt_factor_inertia, which recounts the pivot signs of S on an
+    FP64-accurate factor when the reduced-precision ones disagree (one TF32
+    pivot sign of this S is wrong)."""
+    torch = _torch()
+    from paper_1907_05420_gb300 import binding as B
+
+    p = make_problem(CONFIGS["grid2383_n96"])
+    h = B.kkt_analyze(p, B.kkt_default_options(prec, refine_mode=1, refine_tol=1e-12, max_refine=20))
+    try:
+        res = B.kkt_factor_inertia(h, np.ascontiguousarray(p.a_vals), np.ascontiguousarray(p.b_vals),
+                                   np.ascontiguousarray(p.c_vals))
+        assert res["trials"] == 1 and res["delta_w"] == 0.0
+        info = B.kkt_get_info(h)
+        assert [info["n_pos"], info["n_neg"], info["n_zero"]] == expected_inertia(p)
+        x = np.empty(p.nK)
+        B.kkt_solve(h, np.ascontiguousarray(p.rhs), x)
+        assert oracle.backward_error(p, x) <= 1e-12
+    finally:
+        B.kkt_destroy(h)
+    del torch
