@@ -120,9 +120,10 @@ typedef struct {
                            KKT_ERR_INVALID for a pattern without that structure.  S is then
                            kept as two block vectors (S_d: N diagonal n_s x n_s blocks, S_o: the
                            block repeated below the diagonal in each block column), assembled
-                           from the N local blocks, factored in FP64 in every precision mode
-                           by N partial LDL^T steps of order 2 n_s (O(N n_s^3) flops) and solved
-                           by two chains of N n_s x n_s products.  The analysis builds no
+                           from the N local blocks, factored by N partial LDL^T steps of order
+                           2 n_s (O(N n_s^3) flops; FP32 in the TF32/BF16 modes, with FP64
+                           refinement on K and the FP64 steps as the fallback, FP64 otherwise) and
+                           solved by two chains of N n_s x n_s products.  The analysis builds no
                            per-entry gather lists of S.  B's values are checked on the device at
                            every factor: values that do not repeat make the next kkt_solve
                            return KKT_ERR_INVALID.  Default 0. */
@@ -330,8 +331,7 @@ const char* kkt_last_error(void);
  *   contents: calls whose kernels overlap on the GPU (different streams,
  *   different handles) race on it and must be serialized by the caller.
  *   Needs an FP64-accurate factor of S (handles in KKT_FP64 or
- *   KKT_F64_EMULATED mode, or with structured_s = 2); otherwise returns
- *   KKT_ERR_STATE.
+ *   KKT_F64_EMULATED mode); otherwise returns KKT_ERR_STATE.
  *   Asynchronous with respect to the host; errors of the launches, and an
  *   error left pending on this thread by an earlier launch, are returned as
  *   KKT_ERR_CUDA. */

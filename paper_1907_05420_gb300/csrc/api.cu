@@ -72,7 +72,7 @@ void free_all(Handle* h) {
                   h->ew_s_B, h->ew_s_scale, h->ew_t_Y, h->ew_t_A, h->ew_t_B, h->ew_t_scale, h->tc_imgA,
                   h->tc_imgB, h->tc_scaleA, h->tc_scaleB, h->gm_V, h->gm_Z, h->d.cum_y_ptr, h->d.cum_y_t,
                   h->d.cum_y_e, h->d.cum_z_ptr, h->d.cum_z_t, h->d.cum_z_e, h->d.cum_check, h->cum_err,
-                  h->rstate, h->cum_H, h->cum_Sd, h->cum_So, h->cum_Q, h->cum_QY, h->cum_Linv, h->cum_M, h->cum_Mt,
+                  h->rstate, h->cum_Q32, h->cum_QY32, h->cum_Linv32, h->cum_M32, h->cum_Mt32, h->cum_D32, h->cum_H, h->cum_Sd, h->cum_So, h->cum_Q, h->cum_QY, h->cum_Linv, h->cum_M, h->cum_Mt,
                   h->cum_D};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -126,7 +126,7 @@ cudaError_t enqueue_factor(Handle& h, cudaStream_t st, bool with_s = true) {
   if (!with_s) {
     // the factor of S is left to kkt_factor_schur (a sharded solve reduces S first)
   } else if (h.cum) {
-    STEP(launch_cum_factor(h, h.counters + kNumCounters, st));  // FP64 in every mode
+    STEP(launch_cum_factor(h, h.counters + kNumCounters, st, h.opt.prec == KKT_TF32 || h.opt.prec == KKT_BF16));
   } else if (h.opt.prec == KKT_FP64) {
     STEP(launch_dense_ldlt(h, h.counters + kNumCounters, st));
   } else {
@@ -635,6 +635,16 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
     if (e == cudaSuccess) e = cudaMemset(h->cum_M, 0, sizeof(double) * (size_t)(nn * h->N));
     if (e == cudaSuccess) e = cudaMemset(h->cum_Mt, 0, sizeof(double) * (size_t)(nn * h->N));
     if (e == cudaSuccess) e = cudaMemset(h->cum_err, 0, sizeof(int));
+    if (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) {
+      AL(cum_Q32, float, 4 * nn * h->N);
+      AL(cum_QY32, float, 2 * ns * kDenseNB);
+      AL(cum_Linv32, float, nn * h->N);
+      AL(cum_M32, float, nn * h->N);
+      AL(cum_Mt32, float, nn * h->N);
+      AL(cum_D32, float, ns * h->N);
+      if (e == cudaSuccess) e = cudaMemset(h->cum_M32, 0, sizeof(float) * (size_t)(nn * h->N));
+      if (e == cudaSuccess) e = cudaMemset(h->cum_Mt32, 0, sizeof(float) * (size_t)(nn * h->N));
+    }
   }
   AL(Sdinv, double, h->nC);
   if (h->nT > 0) {
@@ -800,7 +810,7 @@ kkt_status factor_values(Handle* h, const double* a_vals, const double* b_vals, 
   // take other processes' parts, which a fallback could not rebuild
   h->g_reduced = with_s && (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && h->opt.reduced_contraction &&
                  contract_g_tc_supported(*h);
-  h->s_factor = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) && !h->cum ? 1 : 0;
+  h->s_factor = (h->opt.prec == KKT_TF32 || h->opt.prec == KKT_BF16) ? 1 : 0;
   if (with_s && h->opt.use_graphs && !h->graph_failed && !h->factor_exec) {
     capture_factor(*h);
     h->kt_graph_used = h->kt_used;
@@ -830,10 +840,14 @@ kkt_status refactor_s_fp64(Handle* h, cudaStream_t st) {
   if (h->g_reduced) {
     // S was assembled from a reduced-precision contraction: rebuild it in FP64
     KKT_CUDA(launch_contract_g(*h, st));
-    KKT_CUDA(launch_assemble_s(*h, st));
+    KKT_CUDA(h->cum ? launch_cum_assemble(*h, st) : launch_assemble_s(*h, st));
     h->g_reduced = false;
   }
-  KKT_CUDA(launch_dense_ldlt_tc(*h, KKT_F64_EMULATED, h->counters + kNumCounters, st));
+  if (h->cum) {
+    KKT_CUDA(launch_cum_factor(*h, h->counters + kNumCounters, st, false));  // the FP64 period steps
+  } else {
+    KKT_CUDA(launch_dense_ldlt_tc(*h, KKT_F64_EMULATED, h->counters + kNumCounters, st));
+  }
   h->s_factor = 0;
   h->info.fell_back_fp64 = 1;
   return KKT_OK;

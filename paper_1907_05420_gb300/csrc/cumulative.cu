@@ -25,6 +25,9 @@
 // which leaves L_j, D_j (Delta_j = S_d[j] - U_j = L_j D_j L_j^T, U_j = -V_j)
 // and L21_j (the block in every row m > j) in its first ns columns.  These N
 // steps are the only sequential part (N ns^3 7/3 flops instead of nC^3/3).
+// In the TF32 and BF16 modes these steps, the inversion and the solve's
+// products run in FP32 (like the dense factor of S there), with FP64
+// refinement on K and the FP64 steps as the fallback.
 // Then, for all periods at once, Z L_j = [I; L21_j] gives Linv_j = L_j^{-1}
 // and M_j = L21_j L_j^{-1}, and a solve S x = t is two chains of one ns x ns
 // matrix-vector product per period,
@@ -118,8 +121,10 @@ __global__ void k_cum_prefix(const double* __restrict__ H, const double* __restr
 
 // Q_j (column-major, leading dimension 2ns, lower triangle) from S_d[j],
 // S_o[j] and the trailing block V of Q_{j-1}; the last period has no rows below.
+// T: the type of the period factors (FP32 in the TF32 and BF16 modes).
+template <class T>
 __global__ void k_cum_build(const double* __restrict__ Sd, const double* __restrict__ So,
-                            const double* __restrict__ Qprev, double* __restrict__ Q, int ns, int j, int last) {
+                            const T* __restrict__ Qprev, T* __restrict__ Q, int ns, int j, int last) {
   const int n2 = 2 * ns;
   const int64_t nn = (int64_t)ns * ns, total = (int64_t)n2 * n2;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
@@ -128,7 +133,7 @@ __global__ void k_cum_build(const double* __restrict__ Sd, const double* __restr
     auto V = [&](int r1, int c1) -> double {
       if (!Qprev) return 0.0;
       const int hi = max(r1, c1), lo = min(r1, c1);
-      return Qprev[(ns + hi) + (int64_t)(ns + lo) * n2];
+      return (double)Qprev[(ns + hi) + (int64_t)(ns + lo) * n2];
     };
     double v;
     if (c < ns && r < ns) {
@@ -140,7 +145,7 @@ __global__ void k_cum_build(const double* __restrict__ Sd, const double* __restr
     } else {
       v = V(r - ns, c - ns);
     }
-    Q[q] = v;
+    Q[q] = (T)v;
   }
 }
 
@@ -151,8 +156,9 @@ __global__ void k_cum_build(const double* __restrict__ Sd, const double* __restr
 constexpr int kCumTile = 16;
 constexpr int kCumPanel = 32;  // pivot columns per panel of the period factors
 
-__global__ void __launch_bounds__(kCumTile * kCumTile) k_cum_update(double* __restrict__ S, const double* __restrict__ Y,
-                                                                   int n, int k0, int kb, int rend) {
+template <class T>
+__global__ void __launch_bounds__(kCumTile * kCumTile) k_cum_update(T* __restrict__ S, const T* __restrict__ Y, int n,
+                                                                   int k0, int kb, int rend) {
   const int base = k0 + kb;
   int tile = blockIdx.x, ti = 0;
   while (tile > ti) {
@@ -160,16 +166,16 @@ __global__ void __launch_bounds__(kCumTile * kCumTile) k_cum_update(double* __re
     ti++;
   }
   const int i0 = base + ti * kCumTile, j0 = base + tile * kCumTile;
-  __shared__ double Ys[kCumPanel][kCumTile + 1];
-  __shared__ double Ls[kCumPanel][kCumTile + 1];
+  __shared__ T Ys[kCumPanel][kCumTile + 1];
+  __shared__ T Ls[kCumPanel][kCumTile + 1];
   const int tx = threadIdx.x % kCumTile, ty = threadIdx.x / kCumTile;
   for (int q = threadIdx.x; q < kb * kCumTile; q += blockDim.x) {
     const int c = q / kCumTile, r = q % kCumTile;
-    Ys[c][r] = i0 + r < rend ? Y[(i0 + r) + (int64_t)c * n] : 0.0;
-    Ls[c][r] = j0 + r < rend ? S[(j0 + r) + (int64_t)(k0 + c) * n] : 0.0;
+    Ys[c][r] = i0 + r < rend ? Y[(i0 + r) + (int64_t)c * n] : T(0);
+    Ls[c][r] = j0 + r < rend ? S[(j0 + r) + (int64_t)(k0 + c) * n] : T(0);
   }
   __syncthreads();
-  double acc = 0.0;
+  T acc = T(0);
   for (int c = 0; c < kb; c++) acc += Ys[c][ty] * Ls[c][tx];
   const int i = i0 + ty, j = j0 + tx;
   if (i < rend && j <= i) S[i + (int64_t)j * n] -= acc;
@@ -179,22 +185,23 @@ __global__ void __launch_bounds__(kCumTile * kCumTile) k_cum_update(double* __re
 // others M_j = L21_j L_j^{-1} (stored also transposed); D_j is copied out.
 // One thread per row of Z, its row in shared memory; the columns are swept
 // from the last, z_c = b_c - sum_{k>c} z_k L(k, c).
-__global__ void k_cum_inverse(const double* __restrict__ Qall, int ns, int N, int rows_per_cta, int ld,
-                              double* __restrict__ Linv, double* __restrict__ M, double* __restrict__ Mt,
-                              double* __restrict__ D) {
-  extern __shared__ double zs[];  // rows_per_cta x ld
+template <class T>
+__global__ void k_cum_inverse(const T* __restrict__ Qall, int ns, int N, int rows_per_cta, int ld,
+                              T* __restrict__ Linv, T* __restrict__ M, T* __restrict__ Mt, T* __restrict__ D) {
+  extern __shared__ __align__(16) unsigned char zraw[];
+  T* zs = reinterpret_cast<T*>(zraw);  // rows_per_cta x ld
   const int j = blockIdx.y;
   const int n2 = 2 * ns;
   const int rows = j + 1 < N ? n2 : ns;
   const int r = blockIdx.x * rows_per_cta + threadIdx.x;
   if (threadIdx.x >= rows_per_cta || r >= rows) return;  // no barrier below: each thread works alone
-  const double* Q = Qall + (int64_t)j * n2 * n2;
-  double* z = zs + (int64_t)threadIdx.x * ld;
+  const T* Q = Qall + (int64_t)j * n2 * n2;
+  T* z = zs + (int64_t)threadIdx.x * ld;
   const int64_t nn = (int64_t)ns * ns;
   const int cstart = r < ns ? r : ns - 1;  // L^{-1} is lower triangular
-  for (int c = cstart + 1; c < ns; c++) z[c] = 0.0;
+  for (int c = cstart + 1; c < ns; c++) z[c] = T(0);
   for (int c = cstart; c >= 0; c--) {
-    double v = r < ns ? (r == c ? 1.0 : 0.0) : Q[r + (int64_t)c * n2];
+    T v = r < ns ? (r == c ? T(1) : T(0)) : Q[r + (int64_t)c * n2];
     for (int kk = c + 1; kk <= cstart; kk++) v -= z[kk] * Q[kk + (int64_t)c * n2];
     z[c] = v;
   }
@@ -214,18 +221,19 @@ __global__ void k_cum_inverse(const double* __restrict__ Qall, int ns, int N, in
 // tpr threads per row (a power of two, 32 at most), each a stride of the
 // columns, reduced with shuffles.  Every thread runs the same number of
 // iterations, so whole warps take part in the shuffles.
-__device__ __forceinline__ void rows_matvec(const double* __restrict__ A, const double* v, int ns, int r0, int r1,
-                                            int tpr, double* out) {
+template <class T>
+__device__ __forceinline__ void rows_matvec(const T* __restrict__ A, const T* v, int ns, int r0, int r1, int tpr,
+                                            double* out) {
   const int tid = threadIdx.x, part = tid % tpr, per_it = kCumThreads / tpr;
   const int iters = (r1 - r0 + per_it - 1) / per_it;
   for (int it = 0; it < iters; it++) {
     const int a = r0 + it * per_it + tid / tpr;
     const bool live = a < r1;
-    double s = 0.0;
+    T s = T(0);
     if (live)
       for (int c = part; c < ns; c += tpr) s += A[a + (int64_t)c * ns] * v[c];
     for (int off = tpr / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (live && part == 0) out[a - r0] = s;
+    if (live && part == 0) out[a - r0] = (double)s;
   }
 }
 
@@ -233,13 +241,16 @@ __device__ __forceinline__ void rows_matvec(const double* __restrict__ A, const 
 // cluster of kCumCluster CTAs; CTA `rank` owns rows [r0, r1) of the vectors.
 //   forward:  x_j := w_j = t_j - R_j, R += M_j w_j
 //   backward: x_j := a_j - Mt_j Q, Q += x_j (x holds a_j on entry)
-template <bool FORWARD>
+// The running sums and x stay FP64; with an FP32 factor (T float) the
+// exchanged vector and the products are FP32, each product row added to the
+// FP64 sum.
+template <bool FORWARD, class T>
 __global__ void __cluster_dims__(kCumCluster, 1, 1) __launch_bounds__(kCumThreads)
-    k_cum_chain(const double* __restrict__ Mall, int ns, int N, int tpr, double* __restrict__ x) {
-  extern __shared__ double sm[];
-  double* vbuf = sm;             // 2 x ns: the exchanged vector, double-buffered
-  double* state = sm + 2 * ns;   // own rows of R (forward) or Q (backward)
-  double* part = state + ns;     // own rows of the product
+    k_cum_chain(const T* __restrict__ Mall, int ns, int N, int tpr, double* __restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* state = reinterpret_cast<double*>(smraw);  // own rows of R (forward) or Q (backward)
+  double* part = state + ns;                          // own rows of the product
+  T* vbuf = reinterpret_cast<T*>(part + ns);          // 2 x ns: the exchanged vector, double-buffered
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int per = (ns + kCumCluster - 1) / kCumCluster;
@@ -249,18 +260,18 @@ __global__ void __cluster_dims__(kCumCluster, 1, 1) __launch_bounds__(kCumThread
   cluster.sync();  // every CTA of the cluster runs before any writes into its shared memory
   for (int s = 0; s < N; s++) {
     const int j = FORWARD ? s : N - 1 - s;
-    double* vb = vbuf + (s & 1) * ns;
+    T* vb = vbuf + (s & 1) * ns;
     double* xj = x + (int64_t)j * ns;
     if (FORWARD) {
       // w_j = t_j - R_j on own rows, to every CTA's buffer
       for (int a = threadIdx.x; a < r1 - r0; a += blockDim.x) {
         const double w = xj[r0 + a] - state[a];
         xj[r0 + a] = w;
-        for (int q = 0; q < kCumCluster; q++) cluster.map_shared_rank(vb, q)[r0 + a] = w;
+        for (int q = 0; q < kCumCluster; q++) cluster.map_shared_rank(vb, q)[r0 + a] = (T)w;
       }
     } else {
       for (int a = threadIdx.x; a < r1 - r0; a += blockDim.x)
-        for (int q = 0; q < kCumCluster; q++) cluster.map_shared_rank(vb, q)[r0 + a] = state[a];
+        for (int q = 0; q < kCumCluster; q++) cluster.map_shared_rank(vb, q)[r0 + a] = (T)state[a];
     }
     cluster.sync();  // the full vector is in vb on every CTA
     if (FORWARD && j == N - 1) break;
@@ -280,29 +291,30 @@ __global__ void __cluster_dims__(kCumCluster, 1, 1) __launch_bounds__(kCumThread
   cluster.sync();  // no CTA leaves while another may still write into its buffer
 }
 
-// a_j = Linv_j^T D_j^{-1} Linv_j w_j for every period (one CTA each), in place in x.
-__global__ void __launch_bounds__(kCumThreads) k_cum_diag(const double* __restrict__ Linv,
-                                                          const double* __restrict__ D, int ns,
-                                                          double* __restrict__ x) {
-  extern __shared__ double sm[];
-  double* w = sm;       // ns
-  double* z = sm + ns;  // ns
+// a_j = Linv_j^T D_j^{-1} Linv_j w_j for every period (one CTA each), in place
+// in x (in the factor's type T).
+template <class T>
+__global__ void __launch_bounds__(kCumThreads) k_cum_diag(const T* __restrict__ Linv, const T* __restrict__ D,
+                                                          int ns, double* __restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* w = reinterpret_cast<T*>(smraw);  // ns
+  T* z = w + ns;                       // ns
   const int j = blockIdx.x;
   const int64_t nn = (int64_t)ns * ns;
-  const double* Lj = Linv + (int64_t)j * nn;
+  const T* Lj = Linv + (int64_t)j * nn;
   double* xj = x + (int64_t)j * ns;
-  for (int a = threadIdx.x; a < ns; a += blockDim.x) w[a] = xj[a];
+  for (int a = threadIdx.x; a < ns; a += blockDim.x) w[a] = (T)xj[a];
   __syncthreads();
   for (int a = threadIdx.x; a < ns; a += blockDim.x) {  // y = Linv w (lower), z = y / d
-    double s = 0.0;
+    T s = T(0);
     for (int c = 0; c <= a; c++) s += Lj[a + (int64_t)c * ns] * w[c];
     z[a] = s / D[(int64_t)j * ns + a];
   }
   __syncthreads();
   for (int c = threadIdx.x; c < ns; c += blockDim.x) {  // a = Linv^T z
-    double s = 0.0;
+    T s = T(0);
     for (int a = c; a < ns; a++) s += Lj[a + (int64_t)c * ns] * z[a];
-    xj[c] = s;
+    xj[c] = (double)s;
   }
 }
 
@@ -384,13 +396,23 @@ int cum_inverse_rows(int ns) {
 }
 
 cudaError_t cum_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_cum_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, kCumInverseSmem);
   const int chain = (4 * kCumMaxStor) * 8;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cum_chain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, chain);
+  cudaError_t e = cudaFuncSetAttribute(k_cum_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kCumInverseSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_cum_chain<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, chain);
+    e = cudaFuncSetAttribute(k_cum_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCumInverseSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_cum_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kCumMaxStor * 8);
+    e = cudaFuncSetAttribute(k_cum_chain<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, chain);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cum_chain<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, chain);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cum_chain<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, chain);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cum_chain<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, chain);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cum_diag<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kCumMaxStor * 8);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cum_diag<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kCumMaxStor * 8);
   return e;
 }
 
@@ -413,53 +435,75 @@ cudaError_t launch_cum_assemble(Handle& h, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_cum_factor(Handle& h, unsigned long long* counters, cudaStream_t st) {
+namespace {
+
+// The N period steps and the batched inversion in type T, on the buffers of
+// that type (Q, its panel scratch, L^{-1}, M, M^T, D).
+template <class T>
+cudaError_t cum_factor_in(Handle& h, unsigned long long* counters, cudaStream_t st, T* Qall, T* QY, T* Linv, T* M,
+                          T* Mt, T* D) {
   const int ns = h.cum_ns, N = h.N, n2 = 2 * ns;
   const int64_t q2 = (int64_t)n2 * n2;
   for (int j = 0; j < N; j++) {
-    double* Q = h.cum_Q + (int64_t)j * q2;
+    T* Q = Qall + (int64_t)j * q2;
     const int last = j + 1 == N;
-    k_cum_build<<<grid_of(q2), 256, 0, st>>>(h.cum_Sd, h.cum_So, j ? Q - q2 : nullptr, Q, ns, j, last);
+    k_cum_build<T><<<grid_of(q2), 256, 0, st>>>(h.cum_Sd, h.cum_So, j ? Q - q2 : nullptr, Q, ns, j, last);
     h.launches++;
     const int rend = last ? ns : n2;
     for (int k0 = 0; k0 < ns; k0 += kCumPanel) {
       const int kb = std::min(kCumPanel, ns - k0);
       const int kd = kt_begin(h, kFamDiag, (2.0 / 3.0) * kb * kb * kb, st);
-      k_dense_diag_t<double><<<1, 256, 0, st>>>(Q, n2, k0, kb, 0, PivotRule{}, counters);
+      k_dense_diag_t<T><<<1, 256, 0, st>>>(Q, n2, k0, kb, 0, PivotRule{}, counters);
       kt_end(h, kd, st);
       h.launches++;
       const int rest = rend - k0 - kb;
       if (rest > 0) {
-        launch_dense_panel<double>(Q, h.cum_QY, n2, k0, kb, rend, 1, 0, 0, st);
+        launch_dense_panel<T>(Q, QY, n2, k0, kb, rend, 1, 0, 0, st);
         const int tiles = (rest + kCumTile - 1) / kCumTile;
         const int kt = kt_begin(h, kFamDenseF64, update_flops(rest, 0, rest, kb), st);
-        k_cum_update<<<tiles * (tiles + 1) / 2, kCumTile * kCumTile, 0, st>>>(Q, h.cum_QY, n2, k0, kb, rend);
+        k_cum_update<T><<<tiles * (tiles + 1) / 2, kCumTile * kCumTile, 0, st>>>(Q, QY, n2, k0, kb, rend);
         kt_end(h, kt, st);
         h.launches += 2;
       }
     }
   }
   const int rows = cum_inverse_rows(ns), ld = ns % 2 ? ns : ns + 1;
-  k_cum_inverse<<<dim3((n2 + rows - 1) / rows, N), rows, (size_t)rows * ld * sizeof(double), st>>>(
-      h.cum_Q, ns, N, rows, ld, h.cum_Linv, h.cum_M, h.cum_Mt, h.cum_D);
+  k_cum_inverse<T><<<dim3((n2 + rows - 1) / rows, N), rows, (size_t)rows * ld * sizeof(T), st>>>(Qall, ns, N, rows,
+                                                                                                ld, Linv, M, Mt, D);
   h.launches++;
   return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t cum_solve_in(Handle& h, double* x, cudaStream_t st, const T* Linv, const T* M, const T* Mt,
+                         const T* D) {
+  const int ns = h.cum_ns, N = h.N;
+  const int tpr = threads_per_row(ns);
+  const size_t chain_smem = (size_t)2 * ns * sizeof(double) + (size_t)2 * ns * sizeof(T);
+  k_cum_chain<true, T><<<kCumCluster, kCumThreads, chain_smem, st>>>(M, ns, N, tpr, x);
+  k_cum_diag<T><<<N, kCumThreads, (size_t)2 * ns * sizeof(T), st>>>(Linv, D, ns, x);
+  k_cum_chain<false, T><<<kCumCluster, kCumThreads, chain_smem, st>>>(Mt, ns, N, tpr, x);
+  h.launches += 3;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_cum_factor(Handle& h, unsigned long long* counters, cudaStream_t st, bool f32) {
+  if (f32)
+    return cum_factor_in<float>(h, counters, st, h.cum_Q32, h.cum_QY32, h.cum_Linv32, h.cum_M32, h.cum_Mt32,
+                                h.cum_D32);
+  return cum_factor_in<double>(h, counters, st, h.cum_Q, h.cum_QY, h.cum_Linv, h.cum_M, h.cum_Mt, h.cum_D);
 }
 
 // ---- solve: x = S^{-1} t (x and t may be the same array) ----
 
 cudaError_t launch_cum_solve(Handle& h, const double* t, double* x, cudaStream_t st) {
-  const int ns = h.cum_ns, N = h.N;
   cudaError_t e = cudaSuccess;
   if (x != t) e = cudaMemcpyAsync(x, t, sizeof(double) * (size_t)h.nC, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
-  const int tpr = threads_per_row(ns);
-  const size_t chain_smem = (size_t)4 * ns * sizeof(double);
-  k_cum_chain<true><<<kCumCluster, kCumThreads, chain_smem, st>>>(h.cum_M, ns, N, tpr, x);
-  k_cum_diag<<<N, kCumThreads, (size_t)2 * ns * sizeof(double), st>>>(h.cum_Linv, h.cum_D, ns, x);
-  k_cum_chain<false><<<kCumCluster, kCumThreads, chain_smem, st>>>(h.cum_Mt, ns, N, tpr, x);
-  h.launches += 3;
-  return cudaGetLastError();
+  if (h.s_factor == 1) return cum_solve_in<float>(h, x, st, h.cum_Linv32, h.cum_M32, h.cum_Mt32, h.cum_D32);
+  return cum_solve_in<double>(h, x, st, h.cum_Linv, h.cum_M, h.cum_Mt, h.cum_D);
 }
 
 }  // namespace kkt

@@ -220,6 +220,9 @@ struct Handle {
   double* cum_M = nullptr;     // M_j = L21_j L_j^{-1} (the last zero)
   double* cum_Mt = nullptr;    // M_j^T
   double* cum_D = nullptr;     // N x ns: the pivots
+  // FP32 copies of the period factors in the TF32/BF16 modes (the FP64 ones are the fallback)
+  float *cum_Q32 = nullptr, *cum_QY32 = nullptr, *cum_Linv32 = nullptr, *cum_M32 = nullptr, *cum_Mt32 = nullptr;
+  float* cum_D32 = nullptr;
   int trsv_epoch = 1;          // the last epoch of a direct triangular solve of S (graph solves use 1)
   int64_t device_bytes = 0;
 
@@ -344,7 +347,8 @@ struct CumPattern {
 std::string analyze_cumulative(const kkt_pattern* pat, const Coupling& C, CumPattern& out);
 cudaError_t cum_prepare();
 cudaError_t launch_cum_assemble(Handle& h, cudaStream_t st);   // S_d, S_o from G and B
-cudaError_t launch_cum_factor(Handle& h, unsigned long long* counters, cudaStream_t st);
+// the period steps in FP32 (f32: the TF32/BF16 modes) or FP64
+cudaError_t launch_cum_factor(Handle& h, unsigned long long* counters, cudaStream_t st, bool f32);
 cudaError_t launch_cum_solve(Handle& h, const double* t, double* x, cudaStream_t st);
 
 // Solve work vectors supplied by the caller instead of the handle.

@@ -77,14 +77,14 @@ def test_noalloc_matches_kkt_solve_on_two_calls(name):
 # dense tail whose factor was scattered back into the panels (FP64 and
 # emulated-FP64 updates, augmented by the coupling rows), the envelope-limited
 # factor of S, the emulated-FP64 factor of S, and the structured S of the
-# paper's cumulative coupling (FP64 in the TF32 mode too).
+# paper's cumulative coupling.
 AUG14 = GridSpec(14, 18, 3, 2, 4, 1e-6, 1e6, 102, "aug14")
 CASES = {
     "aug14_tail_fp64": (AUG14, "fp64", {"dense_tail": 1}),
     "aug14_tail_emulated": (AUG14, "f64emu", {"dense_tail": 2}),
     "grid30_structured_s": (CONFIGS["grid30_n24"], "fp64", {"structured_s": 1}),
     "grid30_f64emu": (CONFIGS["grid30_n24"], "f64emu", {}),
-    "grid30_paper_structured_tf32": (CONFIGS["grid30_n24"], "tf32", {"structured_s": 2}),
+    "grid30_paper_structured": (CONFIGS["grid30_n24"], "f64emu", {"structured_s": 2}),
 }
 
 
