@@ -44,6 +44,7 @@ constexpr int TM = 128;       // rows of an A block (MMA M)
 constexpr int TN = 64;        // rows of a B block (MMA N)
 constexpr int TK = kDenseNB;  // panel width = reduction length
 constexpr int kEmuLevels = 7;
+static_assert(kEmuLevels == kEmuSlices, "level d holds the digit pairs sa + sb = d, 0 <= sa, sb <= d");
 constexpr long long kWaitBudget = 4000000000LL;  // cycles (~2 s)
 
 struct ModeCfg {
@@ -74,6 +75,17 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
   d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;  // descriptor version of the fifth-generation tensor core
   return d;                // base offset 0, no swizzle
+}
+
+// The descriptor of the operand at byte offset off from the one desc
+// describes: shared-memory addresses stay below 256 KB, so the 14-bit address
+// field (address / 16) takes off / 16 without a carry into the other fields.
+__device__ __forceinline__ uint64_t umma_desc_at(uint64_t desc, uint32_t off) { return desc + (uint64_t)(off >> 4); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtm),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
@@ -400,10 +412,12 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(T* __restrict__ S0, int n,
 //                      started once the epilogue has drained the previous one;
 //   warps 2-9:         the epilogue, one tile row and 32 columns per thread
 //                      (warp w reads tensor-memory lanes 32 (w mod 4) ...):
-//                      the 7 levels are read and folded into registers first,
-//                      tensor memory is handed back, and only then is S read,
+//                      the 7 levels are read and folded into one integer W
+//                      per entry first, tensor memory is handed back, and only
+//                      then are the FP64 bit patterns built and S read,
 //                      updated and written, so that the next tile's products
-//                      run during this tile's global read-modify-write.
+//                      run during this tile's bit building and global
+//                      read-modify-write.
 // The scaled product W 2^{e_i+f_j-56} is built as an FP64 bit pattern with
 // integer operations (W rounded once, exponents added), and the levels are
 // read out of FP32 without conversion instructions, which on this GPU share
@@ -442,6 +456,62 @@ __device__ __forceinline__ void bulk_load(uint8_t* dst, const uint8_t* src, int 
                      smem_u32(dst + off)),
                  "l"(src + off), "r"(sz), "r"(bar)
                  : "memory");
+  }
+}
+
+// The epilogue's read-out of tensor memory: the 7 levels of this thread's
+// kEpiCols columns (16-column loads) folded into W = V 2^16 + round(256 c),
+// V the exact integer of levels 0-3 and c the FP32 sum of levels 4-6.  Only
+// this part holds tensor memory; the FP64 bit patterns are built after it is
+// handed back.
+__device__ __forceinline__ void emu_fold(uint32_t taddr, long long (&W)[kEpiCols]) {
+#pragma unroll
+  for (int hh = 0; hh < kEpiCols / 16; hh++) {
+    long long V[16];
+    float cf[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+      V[j] = 0;
+      cf[j] = 0.f;
+    }
+#pragma unroll
+    for (int d = 0; d < kEmuLevels; d++) {
+      uint32_t r[16];
+      tmem_ld16(taddr + (uint32_t)(d * TN + hh * 16), r);
+#pragma unroll
+      for (int j = 0; j < 16; j++) {
+        const float fv = __uint_as_float(r[j]);
+        if (d < 4) V[j] = V[j] * 256 + exact_f2i(fv);  // levels 0-3: exact integers below 2^24
+        else cf[j] += fv * (d == 4 ? 1.f : (d == 5 ? 0.00390625f : 0.0000152587890625f));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 16; j++) W[hh * 16 + j] = V[j] * 65536 + round_f2ll(cf[j] * 256.f);  // 256 c can pass 2^31
+  }
+}
+
+// S[row, col] += -W 2^{e_i + f_j - 56} for the thread's columns col = base +
+// cj, cj = cj0 .. cj0 + kEpiCols - 1, that lie below mcol and on or below the
+// diagonal; 16 loads of S in flight per thread.  Lane l's ebl is the exponent
+// f_j of column cj0 + l; every lane of the warp takes part (the exponents go
+// through shuffles).
+__device__ __forceinline__ void emu_apply(double* __restrict__ S, int n, int row, bool live_row, int base, int cj0,
+                                          int mcol, int ea, int ebl, const long long (&W)[kEpiCols]) {
+#pragma unroll
+  for (int hh = 0; hh < kEpiCols / 16; hh++) {
+    double cur[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+      const int cj = cj0 + hh * 16 + j, col = base + cj;
+      cur[j] = (live_row && cj < mcol && row >= col) ? S[(int64_t)row + (int64_t)col * n] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+      const int c = hh * 16 + j, cj = cj0 + c, col = base + cj;
+      const int eb = __shfl_sync(0xffffffffu, ebl, c);
+      const double nd = neg_scaled(W[c], ea + eb);
+      if (live_row && cj < mcol && row >= col) S[(int64_t)row + (int64_t)col * n] = cur[j] + nd;
+    }
   }
 }
 
@@ -545,24 +615,19 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint8_t* bS = sB + s * B_BYTES;
-          for (int d = 0; d < cfg.levels; d++) {
+          const uint64_t a0 = umma_desc(smem_u32(sA), 128, KG * 128);
+          const uint64_t b0 = umma_desc(smem_u32(sB + s * B_BYTES), 128, KG * 128);
+          // level d takes the digit pairs sa + sb = d
+#pragma unroll
+          for (int d = 0; d < kEmuLevels; d++) {
             const uint32_t dtm = tmem + (uint32_t)(d * TN);
-            bool first = true;
-            for (int sa = 0; sa < cfg.slices; sa++) {
-              const int sb = d - sa;
-              if (sb < 0 || sb >= cfg.slices) continue;
-              for (int ks = 0; ks < KSTEPS; ks++) {
-                const uint64_t ad = umma_desc(smem_u32(sA + sa * A_SLICE + ks * MMA_K_BYTES * 8), 128, KG * 128);
-                const uint64_t bd = umma_desc(smem_u32(bS + sb * B_SLICE + ks * MMA_K_BYTES * 8), 128, KG * 128);
-                const uint32_t acc = first ? 0u : 1u;
-                first = false;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
-                    "p;\n}" ::"r"(dtm),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-              }
-            }
+#pragma unroll
+            for (int sa = 0; sa <= d; sa++)
+#pragma unroll
+              for (int ks = 0; ks < KSTEPS; ks++)
+                mma_bf16(dtm, umma_desc_at(a0, sa * A_SLICE + ks * MMA_K_BYTES * 8),
+                         umma_desc_at(b0, (d - sa) * B_SLICE + ks * MMA_K_BYTES * 8), idesc,
+                         (sa == 0 && ks == 0) ? 0u : 1u);
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            smem_u32(&bar_bempty[s]))
@@ -604,56 +669,12 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      // two halves of 16 columns: fold the 7 levels, then
-      // W = V 2^16 + round(256 c) and nd = -W 2^{e_i + f_j - 56}
-      double nd[kEpiCols];
-#pragma unroll
-      for (int hh = 0; hh < kEpiCols / 16; hh++) {
-        long long V[16];
-        float cf[16];
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-          V[j] = 0;
-          cf[j] = 0.f;
-        }
-#pragma unroll
-        for (int d = 0; d < kEmuLevels; d++) {
-          uint32_t r[16];
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * TN + cbase + hh * 16), r);
-#pragma unroll
-          for (int j = 0; j < 16; j++) {
-            const float fv = __uint_as_float(r[j]);
-            if (d < 4) V[j] = V[j] * 256 + exact_f2i(fv);  // levels 0-3: exact integers below 2^24
-            else cf[j] += fv * (d == 4 ? 1.f : (d == 5 ? 0.00390625f : 0.0000152587890625f));
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-          const long long W = V[j] * 65536 + round_f2ll(cf[j] * 256.f);  // 256 c can pass 2^31
-          const int eb = __shfl_sync(0xffffffffu, ebl[(hh * 16 + j) >> 5], (hh * 16 + j) & 31);
-          nd[hh * 16 + j] = neg_scaled(W, ea + eb);
-        }
-      }
+      long long W[kEpiCols];
+      emu_fold(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cbase, W);
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_tempty)) : "memory");
-      if (live_row) {
-        // two halves of 16 columns: 16 loads in flight per thread, then the stores
-#pragma unroll
-        for (int hh = 0; hh < kEpiCols / 16; hh++) {
-          double cur[16];
-#pragma unroll
-          for (int j = 0; j < 16; j++) {
-            const int cj = cj0 + hh * 16 + j, col = base + cj;
-            cur[j] = (cj < mcol && row >= col) ? S[(int64_t)row + (int64_t)col * n] : 0.0;
-          }
-#pragma unroll
-          for (int j = 0; j < 16; j++) {
-            const int cj = cj0 + hh * 16 + j, col = base + cj;
-            if (cj < mcol && row >= col) S[(int64_t)row + (int64_t)col * n] = cur[j] + nd[hh * 16 + j];
-          }
-        }
-      }
+      emu_apply(S, n, row, live_row, base, cj0, mcol, ea, ebl[0], W);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -864,22 +885,19 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint8_t* sA = smem + st * (kEwStageA + kEwStageB);
-          const uint8_t* sB = sA + kEwStageA;
+          const uint64_t a0 = umma_desc(smem_u32(sA), 128, 512);
+          const uint64_t b0 = umma_desc(smem_u32(sA + kEwStageA), 128, 512);
+          // level d takes the digit pairs sa + sb = d
+#pragma unroll
           for (int d = 0; d < kEmuLevels; d++) {
             const uint32_t dtm = tmem + (uint32_t)(d * TN);
-            for (int sa = 0; sa < kEmuSlices; sa++) {
-              const int sb = d - sa;
-              if (sb < 0 || sb >= kEmuSlices) continue;
-              for (int ks = 0; ks < kEwChunk / 16; ks++) {
-                const uint64_t ad = umma_desc(smem_u32(sA + sa * 2 * kEwPiece + ks * 256), 128, 512);
-                const uint64_t bd = umma_desc(smem_u32(sB + sb * kEwPiece + ks * 256), 128, 512);
-                const uint32_t acc = (k == 0 && sa == (d < kEmuSlices ? 0 : d - kEmuSlices + 1) && ks == 0) ? 0u : 1u;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
-                    "p;\n}" ::"r"(dtm),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-              }
-            }
+#pragma unroll
+            for (int sa = 0; sa <= d; sa++)
+#pragma unroll
+              for (int ks = 0; ks < kEwChunk / 16; ks++)
+                mma_bf16(dtm, umma_desc_at(a0, sa * 2 * kEwPiece + ks * 256),
+                         umma_desc_at(b0, (d - sa) * kEwPiece + ks * 256), idesc,
+                         (k == 0 && sa == 0 && ks == 0) ? 0u : 1u);
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            smem_u32(&bar_empty[st]))
@@ -922,53 +940,12 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      double nd[kEpiCols];
-#pragma unroll
-      for (int hh = 0; hh < kEpiCols / 16; hh++) {
-        long long V[16];
-        float cf[16];
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-          V[j] = 0;
-          cf[j] = 0.f;
-        }
-#pragma unroll
-        for (int d = 0; d < kEmuLevels; d++) {
-          uint32_t r[16];
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * TN + cbase + hh * 16), r);
-#pragma unroll
-          for (int j = 0; j < 16; j++) {
-            const float fv = __uint_as_float(r[j]);
-            if (d < 4) V[j] = V[j] * 256 + exact_f2i(fv);
-            else cf[j] += fv * (d == 4 ? 1.f : (d == 5 ? 0.00390625f : 0.0000152587890625f));
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-          const long long W = V[j] * 65536 + round_f2ll(cf[j] * 256.f);
-          const int eb = __shfl_sync(0xffffffffu, ebl[(hh * 16 + j) >> 5], (hh * 16 + j) & 31);
-          nd[hh * 16 + j] = neg_scaled(W, ea + eb);
-        }
-      }
+      long long W[kEpiCols];
+      emu_fold(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cbase, W);
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_tempty)) : "memory");
-      if (live_row) {
-#pragma unroll
-        for (int hh = 0; hh < kEpiCols / 16; hh++) {
-          double cur[16];
-#pragma unroll
-          for (int j = 0; j < 16; j++) {
-            const int cj = cj0 + hh * 16 + j, col = base + cj;
-            cur[j] = (cj < m && row >= col) ? S[(int64_t)row + (int64_t)col * n] : 0.0;
-          }
-#pragma unroll
-          for (int j = 0; j < 16; j++) {
-            const int cj = cj0 + hh * 16 + j, col = base + cj;
-            if (cj < m && row >= col) S[(int64_t)row + (int64_t)col * n] = cur[j] + nd[hh * 16 + j];
-          }
-        }
-      }
+      emu_apply(S, n, row, live_row, base, cj0, m, ea, ebl[0], W);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
