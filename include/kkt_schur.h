@@ -519,16 +519,19 @@ kkt_status kkt_server_cache_info(kkt_server* s, int64_t* resident, int64_t* anal
  * (k_dense_update: S in KKT_FP64, the FP64 tails), 4 the supernodal updates of
  * the block factor (k_factor_update), 5 the dense diagonal blocks of the
  * blocked factors (k_dense_diag_t), 6 the emulated-FP64 update with K = 256
- * of the 256-wide outer panels (k_tc_update_emu_wide).  flops: the
+ * of the 256-wide outer panels (k_tc_update_emu_wide), 7 the emulated-FP64
+ * panels of those factors (k_tc_panel_emu, timed with the two launches that
+ * form its operands: W = L11^{-1} and the digit image of A21).  flops: the
  * algorithmic FP64-equivalent flops of the launches (2 per multiply-add on the
- * entries of the lower triangle they update). */
+ * entries of the lower triangle they update; for a panel, 2 per multiply-add
+ * of the row solves it replaces). */
 typedef struct {
   int64_t launches;     /* launches of the family in the handle's last factor (and fallback) */
   double ms_total;      /* sum of their device durations (CUDA events on their streams) */
   double ms_max;        /* the longest one */
   double flops;         /* their algorithmic flops */
 } kkt_kernel_stat;
-/* Statistics of family `family` (0..6); synchronizes the handle. */
+/* Statistics of family `family` (0..7); synchronizes the handle. */
 kkt_status kkt_kernel_stats(kkt_handle* h, int32_t family, kkt_kernel_stat* out);
 
 /* Measured FP64 FMA throughput of the current device in GFLOP/s (8

@@ -87,7 +87,7 @@ EXPORTS = ["kkt_default_options", "kkt_analyze", "kkt_factor", "kkt_solve", "kkt
            "kkt_schur_blocks", "kkt_probe_pivot_reciprocal"]
 
 KERNEL_FAMILIES = ["k_tc_update_emu", "k_tc_update_wide", "k_tc_update", "k_dense_update", "k_factor_update",
-                   "k_dense_diag_t", "k_tc_update_emu_wide"]
+                   "k_dense_diag_t", "k_tc_update_emu_wide", "k_tc_panel_emu"]
 
 
 class kkt_ipm_state(C.Structure):

@@ -134,6 +134,30 @@ struct TcStrides {
   int64_t s = 0, y = 0, img_a = 0, img_b = 0, scale = 0;
 };
 
+// One 16-byte core-matrix row of each of the 7 digit slices: the BF16 digits
+// (unsigned base-256 digits of |v| 2^-e, with the sign of v) of 8 consecutive
+// K entries, stored at dst + s * slice_stride for slice s.  table holds the
+// BF16 bit patterns of the 256 byte values (no conversion instructions).
+__device__ __forceinline__ void emu_store_core_row(const double (&v)[8], int e_exp, const uint32_t* table,
+                                                   uint8_t* dst, int slice_stride) {
+  uint32_t packed[kEmuSlices][4];
+#pragma unroll
+  for (int e = 0; e < 8; e++) {
+    long long vb;
+    const unsigned long long a = digits7(v[e], e_exp, vb);
+    const uint32_t sgn = vb < 0 ? 0x8000u : 0u;
+#pragma unroll
+    for (int s = 0; s < kEmuSlices; s++) {
+      const uint32_t h = table[(a >> (8 * (kEmuSlices - 1 - s))) & 0xFFull] | sgn;
+      packed[s][e >> 1] = (e & 1) ? (packed[s][e >> 1] | (h << 16)) : h;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < kEmuSlices; s++)
+    *reinterpret_cast<uint4*>(dst + (int64_t)s * slice_stride) =
+        make_uint4(packed[s][0], packed[s][1], packed[s][2], packed[s][3]);
+}
+
 template <int MODE, class T>
 __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S0, const T* __restrict__ Y0,
                                                   int n, int k0, int kb, int m, uint8_t* __restrict__ imgA0,
@@ -193,25 +217,14 @@ __global__ void __launch_bounds__(256) k_tc_slice(const T* __restrict__ S0, cons
       if (MODE == 2) {
         // BF16 bit patterns of the signed digits, from the table of the 256
         // byte values (no conversion instructions)
-        uint32_t packed[kEmuSlices][4];
+        double v[8] = {};
 #pragma unroll
         for (int e = 0; e < kpc; e++) {
           const int c = kq * kpc + e;  // columns >= kb (a ragged panel) are zero
-          double v = (live && c < kb) ? (double)src[(int64_t)(base + rho) + (col0 + c) * n] : 0.0;
-          long long vb;
-          const unsigned long long a = digits7(v, e_exp, vb);
-          const uint32_t sgn = vb < 0 ? 0x8000u : 0u;
-#pragma unroll
-          for (int s = 0; s < kEmuSlices; s++) {
-            const uint32_t h = bf16_of_byte[(a >> (8 * (kEmuSlices - 1 - s))) & 0xFFull] | sgn;
-            packed[s][e >> 1] = (e & 1) ? (packed[s][e >> 1] | (h << 16)) : h;
-          }
+          v[e] = (live && c < kb) ? (double)src[(int64_t)(base + rho) + (col0 + c) * n] : 0.0;
         }
-#pragma unroll
-        for (int s = 0; s < kEmuSlices; s++) {
-          uint8_t* dst = blk_img + (int64_t)s * slice_bytes(MODE, rows_blk) + (g * KG + kq) * 128 + r8 * 16;
-          *reinterpret_cast<uint4*>(dst) = make_uint4(packed[s][0], packed[s][1], packed[s][2], packed[s][3]);
-        }
+        emu_store_core_row(v, e_exp, bf16_of_byte, blk_img + (g * KG + kq) * 128 + r8 * 16,
+                           slice_bytes(MODE, rows_blk));
       } else if (MODE == 1) {
         __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
@@ -680,6 +693,199 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// ---- Emulated-FP64 panel of a 64-column step ----
+//
+// The panel of a step, Y = A21 L11^{-T} and L21 = Y D1^{-1} (the rows below
+// the diagonal block), as a product on the tensor cores instead of one
+// substitution per row on the FP64 pipe: W = L11^{-1} is formed per matrix
+// in FP64 (k_panel_inverse_slice, 64 x 64, W[i][j] by the same substitution
+// that k_dense_panel_t runs for a row, with the unit vector e_j as the row),
+// and Y = A21 W^T is one 64-column product with K = 64 in the format of the
+// 64-wide emulated update (7 BF16 digit slices, 7 exact tensor-memory levels,
+// the same fold), written instead of accumulated (k_tc_panel_emu).  The
+// rounding differs from the substitution's: the product is within the
+// rounding of an FP64 dot product of W's rows, W within that of the
+// substitution, so the panel's residual A21 - Y L11^T grows with the
+// condition of L11 (unit lower triangular, well conditioned for the
+// diagonal blocks of these quasidefinite matrices).
+
+// W = L11^{-1} of matrix blockIdx.x (the kb x kb unit lower triangle at
+// (k0, k0) after k_dense_diag_t) and the digit image of its rows, the B
+// operand of k_tc_panel_emu: row i of B is row i of W (K index = column),
+// rows and columns >= kb zero, the row scales in scaleB[0..63].
+__global__ void __launch_bounds__(256) k_panel_inverse_slice(const double* __restrict__ S0, int n, int k0, int kb,
+                                                             uint8_t* __restrict__ imgB0,
+                                                             double* __restrict__ scaleB0, TcStrides ts) {
+  constexpr int KG = kgroups_of(2);
+  __shared__ double M[TK][TK + 1];  // L11 by rows, then W by rows
+  __shared__ uint32_t bf16_of_byte[256];
+  const int64_t bb = blockIdx.x;
+  const double* S = S0 + bb * ts.s;
+  uint8_t* imgB = imgB0 + bb * ts.img_b;
+  double* scaleB = scaleB0 + bb * ts.scale;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) bf16_of_byte[i] = bf16_bits_of_byte((uint32_t)i);
+  for (int q = threadIdx.x; q < TK * TK; q += blockDim.x) {
+    const int c = q / TK, j = q - c * TK;
+    M[j][c] = (j > c && j < kb) ? S[(int64_t)(k0 + j) + (int64_t)(k0 + c) * n] : 0.0;
+  }
+  __syncthreads();
+  // column jc of W: w L11^T = e_jc solved as a row, subtracted in increasing c
+  const int jc = threadIdx.x;
+  double w[TK];
+  if (jc < TK) {
+#pragma unroll
+    for (int c = 0; c < TK; c++) w[c] = (c == jc && c < kb) ? 1.0 : 0.0;
+#pragma unroll
+    for (int j = 1; j < TK; j++) {
+      double acc = w[j];
+#pragma unroll
+      for (int c = 0; c < j; c++) acc -= w[c] * M[j][c];
+      w[j] = acc;
+    }
+  }
+  __syncthreads();  // every read of L11 is done
+  if (jc < TK) {
+#pragma unroll
+    for (int i = 0; i < TK; i++) M[i][jc] = w[i];
+  }
+  __syncthreads();
+  // the digit image: 64 rows x 8 core rows of K, two per thread
+  for (int q = threadIdx.x; q < TK * KG; q += blockDim.x) {
+    const int i = q / KG, kq = q - i * KG;
+    int emax = 0;
+    double amax = 0.0;
+    for (int c = 0; c < TK; c++) {
+      emax = max(emax, exp_field(M[i][c]));
+      amax = fmax(amax, fabs(M[i][c]));
+    }
+    // |w| < 2^e; rows whose largest entry is subnormal (or zero) take ilogb
+    const int e_exp = emax > 0 ? emax - 1023 + 1 : (amax > 0.0 ? ilogb(amax) + 1 : 0);
+    if (kq == 0) scaleB[i] = ldexp(1.0, e_exp);
+    double v[8];
+#pragma unroll
+    for (int e = 0; e < 8; e++) v[e] = M[i][kq * 8 + e];
+    emu_store_core_row(v, e_exp, bf16_of_byte, imgB + ((i / 8) * KG + kq) * 128 + (i % 8) * 16,
+                       slice_bytes(2, TN));
+  }
+}
+
+// Y = A21 W^T for the 128-row tile blockIdx.x of matrix blockIdx.y: the A
+// image of the tile (k_tc_slice of A21) and the B image of W are copied once,
+// thread 0 issues the 112 MMAs (28 digit pairs x 4 K steps of 16) into the 7
+// levels, and 8 warps (two per tensor-memory lane quadrant, 32 columns each)
+// fold the levels and write Y (leading dimension n) and L21 = Y D1^{-1} into
+// the panel's columns of S.  Both waits are bounded (a timeout sets *err).
+__host__ __device__ constexpr int panel_emu_smem_bytes() { return image_bytes(2, TM) + image_bytes(2, TN); }
+
+__global__ void __launch_bounds__(256, 1) k_tc_panel_emu(double* __restrict__ S0, double* __restrict__ Y0, int n,
+                                                         int k0, int kb, int m, const uint8_t* __restrict__ imgA0,
+                                                         const uint8_t* __restrict__ imgB0,
+                                                         const double* __restrict__ scaleA0,
+                                                         const double* __restrict__ scaleB0, int* err,
+                                                         TcStrides ts) {
+  constexpr int KG = kgroups_of(2);
+  constexpr int A_BYTES = image_bytes(2, TM), B_BYTES = image_bytes(2, TN);
+  constexpr int A_SLICE = slice_bytes(2, TM), B_SLICE = slice_bytes(2, TN);
+  constexpr uint32_t TMEM_COLS = 512;  // 7 levels x 64 columns
+  constexpr int KSTEPS = TK * 2 / 32;  // MMAs of K = 16 per level and digit pair
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + A_BYTES;
+  __shared__ __align__(8) uint64_t bar_load, bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_ok;
+  __shared__ double dinv[TK];
+  const int64_t bb = blockIdx.y;
+  const int I = blockIdx.x;
+  double* S = S0 + bb * ts.s;
+  double* Y = Y0 + bb * ts.y;
+  const uint8_t* imgA = imgA0 + bb * ts.img_a + (int64_t)I * A_BYTES;
+  const uint8_t* imgB = imgB0 + bb * ts.img_b;
+  const double* scaleA = scaleA0 + bb * ts.scale;
+  const double* scaleB = scaleB0 + bb * ts.scale;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int base = k0 + kb;
+
+  if (tid == 0) {
+    s_ok = 1;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_load)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (tid < TK) dinv[tid] = tid < kb ? 1.0 / S[(int64_t)(k0 + tid) + (int64_t)(k0 + tid) * n] : 0.0;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+
+  if (tid == 0) {
+    const uint32_t bl = smem_u32(&bar_load);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bl), "r"((uint32_t)(A_BYTES + B_BYTES))
+                 : "memory");
+    bulk_load(sA, imgA, A_BYTES, bl);
+    bulk_load(sB, imgB, B_BYTES, bl);
+    if (!mbar_wait(bl, 0)) {
+      atomicExch(err, 17);
+      s_ok = 0;
+      mbar_wait(bl, 0);  // give copies still in flight a second bounded window before exit
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                             ((uint32_t)(TM >> 4) << 24);
+      const uint64_t a0 = umma_desc(smem_u32(sA), 128, KG * 128);
+      const uint64_t b0 = umma_desc(smem_u32(sB), 128, KG * 128);
+#pragma unroll
+      for (int d = 0; d < kEmuLevels; d++) {
+#pragma unroll
+        for (int sa = 0; sa <= d; sa++)
+#pragma unroll
+          for (int ks = 0; ks < KSTEPS; ks++)
+            mma_bf16(tmem + (uint32_t)(d * TN), umma_desc_at(a0, sa * A_SLICE + ks * 256),
+                     umma_desc_at(b0, (d - sa) * B_SLICE + ks * 256), idesc, (sa == 0 && ks == 0) ? 0u : 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&bar_mma))
+                   : "memory");
+    }
+  }
+  __syncthreads();
+  bool ok = s_ok != 0;
+  if (ok && !mbar_wait(smem_u32(&bar_mma), 0)) {
+    if (tid == 0) atomicExch(err, 18);
+    ok = false;
+    mbar_wait(smem_u32(&bar_mma), 0);  // second bounded window before tensor memory is freed
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    const int q = warp & 3, cbase = (warp >> 2) * kEpiCols;
+    const int rho = I * TM + q * 32 + lane;
+    const int row = base + rho;
+    const bool live_row = rho < m;
+    const int ea = pow2_exponent(live_row ? scaleA[rho] : 1.0) - 56;
+    const int ebl = pow2_exponent(cbase + lane < kb ? scaleB[cbase + lane] : 1.0);
+    long long W[kEpiCols];
+    emu_fold(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cbase, W);
+#pragma unroll
+    for (int c = 0; c < kEpiCols; c++) {
+      const int j = cbase + c;
+      const int eb = __shfl_sync(0xffffffffu, ebl, c);
+      const double y = -neg_scaled(W[c], ea + eb);
+      if (live_row && j < kb) {
+        Y[(int64_t)row + (int64_t)j * n] = y;
+        S[(int64_t)row + (int64_t)(k0 + j) * n] = y * dinv[j];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
 // ---- Emulated-FP64 update of a 256-wide outer panel ----
@@ -1379,8 +1585,25 @@ cudaError_t factor_emu_wide(Handle& h, double* S, int n, int npiv, int nb, const
       const int m = n - k0 - kb;
       if (m <= 0) continue;
       double* Yc = ew.Yw + (int64_t)c * TK * n;
-      launch_dense_panel<double>(S, Yc, n, k0, kb, n, nb, ts.s, ew.y_stride, st, prio);
-      h.launches++;
+      {
+        // the panel as a product: W = L11^{-1}, the digit image of A21 (rows
+        // below the diagonal block, columns k0 .. k0 + kb of S), Y = A21 W^T
+        const int TIp = (m + TM - 1) / TM;
+        TcStrides tp = ti;  // A21 read in place: its "Y" is S from column k0 on
+        tp.y = ts.s;
+        const int kp = kt_begin(h, kFamPanelEmu, nb * (double)m * kb * (kb - 1), st);
+        launch_prio(k_panel_inverse_slice, dim3(nb), dim3(256), 0, st, prio, (const double*)S, n, k0, kb, imgB,
+                    scaleB, ti);
+        const int pgrid = std::max(1, std::min((TIp * TM + 255) / 256, 152 * 8 / nb));
+        launch_prio(k_tc_slice<2, double>, dim3(pgrid, nb), dim3(256), 0, st, prio, (const double*)S,
+                    (const double*)(S + (int64_t)k0 * n), n, k0, kb, m, imgA, imgB, scaleA, scaleB, TIp * TM, 0, tp);
+        e = launch_prio(k_tc_panel_emu, dim3(TIp, nb), dim3(256), panel_emu_smem_bytes(), st, prio, S, Yc, n, k0, kb,
+                        m, (const uint8_t*)imgA, (const uint8_t*)imgB, (const double*)scaleA, (const double*)scaleB,
+                        h.dev_err, ti);
+        kt_end(h, kp, st);
+        h.launches += 3;
+        if (e != cudaSuccess) break;
+      }
       // the outer panel's own remaining columns
       const int TJl = (K0 + Wb - (k0 + kb) + TN - 1) / TN;
       if (TJl <= 0) continue;
@@ -1554,6 +1777,8 @@ cudaError_t dense_tc_prepare() {
     e = cudaFuncSetAttribute(k_tc_update_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, wide_smem_bytes());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tc_update_emu_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, ew_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_panel_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, panel_emu_smem_bytes());
   return e;
 }
 

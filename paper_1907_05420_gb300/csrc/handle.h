@@ -260,7 +260,9 @@ struct Handle {
   int kt_graph_used = 0;  // timed launches inside the factor's graph
 };
 
-enum KernelFamily { kFamEmu = 0, kFamWide, kFamTc, kFamDenseF64, kFamFactorUpd, kFamDiag, kFamEmuWide, kNumFamilies };
+enum KernelFamily {
+  kFamEmu = 0, kFamWide, kFamTc, kFamDenseF64, kFamFactorUpd, kFamDiag, kFamEmuWide, kFamPanelEmu, kNumFamilies
+};
 // An event before a timed launch on `st` (returns its slot, -1 when not timing
 // or the pool is full) and one after it.
 int kt_begin(Handle& h, int fam, double flops, cudaStream_t st);
