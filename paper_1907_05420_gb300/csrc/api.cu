@@ -388,7 +388,7 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
   g_gather(S, C, h->tail_aug ? S.tail_sn : S.nsuper, g_key, g_ptr, g_row);
   h->g_nkeys = (int64_t)g_key.size();
 
-  // factor work items: 64-row tiles of every supernode outside the dense tail,
+  // factor work items: 32-row tiles of every supernode outside the dense tail,
   // grouped by level, then those of the tail supernodes; per item the updates
   // that meet the tile, as (update index within s's list, rows [ia, ib) of the
   // descendant that land in the tile), from the item's offset to the next item's

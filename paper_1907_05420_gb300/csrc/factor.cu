@@ -11,7 +11,7 @@
 // elimination tree.  Per level two launches:
 //   k_factor_update: left-looking updates of every supernode s of the level
 //     from its descendants d,  P_s[rel(i), j - f_s] -= sum_k L_d[i,k] D_d[k] L_d[j,k],
-//     one CTA per (64-row tile of s, block) so that the wide supernodes at the
+//     one CTA per (32-row tile of s, block) so that the wide supernodes at the
 //     top of the tree spread over many SMs;
 //   k_panel_factor: dense LDL^T of the panel (1x1 pivots; a pivot below
 //     pivot_eps*max|A_i| is replaced by the expected-sign value and counted).
@@ -76,7 +76,7 @@ __global__ void k_block_absmax(const double* __restrict__ a_vals, int64_t nnzA,
   if (threadIdx.x == 0) anorm[blockIdx.x] = red[0];
 }
 
-// One CTA per (64-row tile of supernode s, block).  The tile's update is
+// One CTA per (32-row tile of supernode s, block; 128 threads).  The tile's update is
 // accumulated in shared memory over the descendants d that meet the tile (in
 // update order) and subtracted from the panel once.  For each update the rows
 // of d that land in the tile ([ia, ib), listed per tile at analysis with only
@@ -85,8 +85,9 @@ __global__ void k_block_absmax(const double* __restrict__ a_vals, int64_t nnzA,
 // supernodes the lists hold only the updates from descendants outside the
 // dense tail; their updates among themselves are the dense tail factor's.
 constexpr int kTileRows = kFactorTileRows;
+constexpr int kFactorThreads = 128;
 
-__global__ void __launch_bounds__(256) k_factor_update(const int32_t* __restrict__ work,
+__global__ void __launch_bounds__(kFactorThreads) k_factor_update(const int32_t* __restrict__ work,
                                                        const UpdPair* __restrict__ pairs, DevSym d,
                                                        double* __restrict__ Lx, int64_t pt) {
   __shared__ double acc[kTileRows][kMaxSnWidth + 1];
@@ -216,7 +217,7 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
     if (l > 0 && w1 > w0) {
       dim3 grid(w1 - w0, h.N);
       const int kt = kt_begin(h, kFamFactorUpd, h.N * h.fupd_flops[l], st);
-      k_factor_update<<<grid, 256, 0, st>>>(h.d.fwork + 4 * w0, h.d.fpairs, h.d, h.Lx, pt);
+      k_factor_update<<<grid, kFactorThreads, 0, st>>>(h.d.fwork + 4 * w0, h.d.fpairs, h.d, h.Lx, pt);
       kt_end(h, kt, st);
       h.launches++;
     }
@@ -239,7 +240,7 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
     if (h.tail_items > 0) {
       dim3 grid(h.tail_items, h.N);
       const int kt = kt_begin(h, kFamFactorUpd, h.N * h.tupd_flops, st);
-      k_factor_update<<<grid, 256, 0, st>>>(h.d.twork, h.d.fpairs, h.d, h.Lx, pt);
+      k_factor_update<<<grid, kFactorThreads, 0, st>>>(h.d.twork, h.d.fpairs, h.d, h.Lx, pt);
       kt_end(h, kt, st);
       h.launches++;
     }

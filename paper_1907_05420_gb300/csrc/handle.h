@@ -23,7 +23,7 @@ void set_error(const std::string& msg);
     }                                                                               \
   } while (0)
 
-// One update of a factor work item (a 64-row tile of supernode s) by a
+// One update of a factor work item (a 32-row tile of supernode s) by a
 // descendant d that meets the tile, with everything the update kernel reads
 // about d, so that one load gives it.
 struct UpdPair {
@@ -278,7 +278,7 @@ inline double update_flops(int64_t m, int64_t c0, int64_t c1, int64_t kb) {
 }
 
 constexpr int kDenseNB = 64;
-constexpr int kFactorTileRows = 64;  // rows of a work item of the supernodal update (factor.cu)
+constexpr int kFactorTileRows = 32;  // rows of a work item of the supernodal update (factor.cu)
 
 // ---- kernel attributes, set once per device before any launch ----
 cudaError_t dense_prepare();
