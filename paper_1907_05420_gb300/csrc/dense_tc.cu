@@ -472,6 +472,23 @@ __device__ __forceinline__ void bulk_load(uint8_t* dst, const uint8_t* src, int 
   }
 }
 
+// The S entries an epilogue thread will read and write for one tile (its row,
+// columns base + cj0 .. base + cj0 + COLS - 1 below mcol and on or below the
+// diagonal) prefetched into L2 while the tile's products run: for the 32 rows
+// of a warp one prefetch per column covers whole cache lines, and the
+// read-modify-write after the products then waits on L2 instead of DRAM.
+template <class T, int COLS>
+__device__ __forceinline__ void prefetch_tile_row(const T* S, int n, int row, bool live_row, int base, int cj0,
+                                                  int mcol) {
+  if (!live_row) return;
+#pragma unroll 8
+  for (int j = 0; j < COLS; j++) {
+    const int cj = cj0 + j, col = base + cj;
+    if (cj < mcol && row >= col)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(S + (int64_t)row + (int64_t)col * n));
+  }
+}
+
 // The epilogue's read-out of tensor memory: the 7 levels of this thread's
 // kEpiCols columns (16-column loads) folded into W = V 2^16 + round(256 c),
 // V the exact integer of levels 0-3 and c the FP32 sum of levels 4-6.  Only
@@ -671,6 +688,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
 #pragma unroll
       for (int g = 0; g < kEpiCols / 32; g++)
         ebl[g] = pow2_exponent(cj0 + g * 32 + lane < m ? scaleB[cj0 + g * 32 + lane] : 1.0);
+      prefetch_tile_row<double, kEpiCols>(S, n, row, live_row, base, cj0, mcol);
       bool ok = true;
       if (lane == 0) ok = mbar_wait_ab(smem_u32(&bar_tfull), (uint32_t)(u & 1), &s_abort);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
@@ -1135,6 +1153,7 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
 #pragma unroll
       for (int g2 = 0; g2 < kEpiCols / 32; g2++)
         ebl[g2] = pow2_exponent(cj0 + g2 * 32 + lane < m ? scaleB[cj0 + g2 * 32 + lane] : 1.0);
+      prefetch_tile_row<double, kEpiCols>(S, n, row, live_row, base, cj0, m);
       bool ok = true;
       if (lane == 0) ok = mbar_wait_ab(smem_u32(&bar_tfull), (uint32_t)(u & 1), &s_abort);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
@@ -1371,6 +1390,7 @@ __global__ void __launch_bounds__(kWideThreads, 1)
     const bool live_row = rho < m;
     for (int u = 0; u < ntile; u++) {
       const int b = u & 1, J = j0 + u;
+      prefetch_tile_row<float, 64>(S, n, row, live_row, base, J * kWideTile + h * 64, m);
       bool ok = true;
       if (lane == 0) ok = mbar_wait_ab(smem_u32(&bar_accf[b]), (uint32_t)((u >> 1) & 1), &s_abort);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
