@@ -48,7 +48,7 @@ EMU_PRODUCTS = 28.0
 # the 8-period system read 25.99 GB and wrote 14.85 GB; every launch updates the
 # same tail in each of its blocks (each tail, 439 MB, exceeds L2), so a launch
 # over 168 blocks moves 168 / 8 times as much: 40.84 GB * 21 / 56 per launch.
-TRAFFIC = {("grid9241_n168", "k_tc_update_emu_wide"): 40.839235840e9 * 21 / 56}
+TRAFFIC = {("grid9241_n168", "k_tc_update_emu_wide"): 40.395244032e9 * 21 / 56}
 
 
 def workload_desc(name):
