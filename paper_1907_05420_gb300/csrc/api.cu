@@ -65,7 +65,7 @@ void free_all(Handle* h) {
                   h->d.t_ptr, h->d.t_e, h->d.bt_ptr, h->d.E, h->d.g_rows, h->d.trsv_jlo, h->d.trsv_jhi,
                   h->d.flvl_sn, h->d.twork, h->d.upd_ntail, h->d.reach_lvl_sn_nt, h->d.tail_sn_list, h->d.tail_wrow, h->d.wt_ptr, h->d.wt_idx,
                   h->d.g_key, h->d.g_ptr, h->d.g_row, h->Xinv, h->Sdinv, h->wdinv, h->Xtail, h->Tt, h->TY, h->t_imgA, h->t_imgB,
-                  h->t_scaleA, h->t_scaleB, h->Lx, h->a_vals, h->b_vals,
+                  h->t_scaleA, h->t_scaleB, h->Lx, h->LDx, h->a_vals, h->b_vals,
                   h->c_vals, h->anorm, h->W, h->G, h->S, h->Ypanel, h->knorm, h->counters, h->r,
                   h->z, h->u, h->v, h->tg, h->xg, h->x, h->dx, h->rho, h->rhs, h->red,
                   h->trsv_flags, h->trsv_ticket, h->dev_err, h->S32, h->Y32, h->tw_img, h->ew_s_Y, h->ew_s_A,
@@ -607,6 +607,8 @@ kkt_status analyze_one(const kkt_pattern* pat, const kkt_options* opt, double ta
 #define AL(dst, T, cnt) \
   if (e == cudaSuccess) e = dalloc<T>(&h->dst, cnt, by)
   AL(Lx, double, S.panel_total * h->N);
+  h->ld_total = std::max<int64_t>(1, S.sn_valoff[S.tail_sn]);
+  AL(LDx, double, h->ld_total * h->N);
   AL(a_vals, double, h->nnzA * h->N);
   AL(b_vals, double, nnzB);
   AL(c_vals, double, h->c_kind == 0 ? (int64_t)h->nC : (int64_t)h->nC * h->nC);

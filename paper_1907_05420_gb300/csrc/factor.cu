@@ -89,7 +89,8 @@ constexpr int kFactorThreads = 128;
 
 __global__ void __launch_bounds__(kFactorThreads) k_factor_update(const int32_t* __restrict__ work,
                                                        const UpdPair* __restrict__ pairs, DevSym d,
-                                                       double* __restrict__ Lx, int64_t pt) {
+                                                       double* __restrict__ Lx, int64_t pt,
+                                                       const double* __restrict__ LDx, int64_t ldt) {
   __shared__ double acc[kTileRows][kMaxSnWidth + 1];
   __shared__ double Li[kTileRows][kMaxSnWidth + 1];
   __shared__ double Lj[kMaxSnWidth][kMaxSnWidth + 1];
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_update(const int32_t*
   const int f = d.sn_first[s], ws = d.sn_first[s + 1] - f;
   const int nrow = hi - lo;
   const double* Lb = Lx + b * pt;
+  const double* LDb = LDx + b * ldt;
   double* P = Lx + b * pt + d.sn_valoff[s];
   for (int q = tid; q < kTileRows * (kMaxSnWidth + 1); q += blockDim.x) (&acc[0][0])[q] = 0.0;
   UpdPair Rn{};  // the next update's record, loaded during this one's products
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_update(const int32_t*
     const UpdPair R = Rn;
     const int ni = R.ib - R.ia, nj = R.r1 - R.r0, wd = R.wd, md = R.md;
     const double* Pd = Lb + R.val;
+    const double* PDd = LDb + R.val;  // the same panel's L D (descendants lie outside the tail)
     const int32_t* Rd = d.sn_rows + R.rows;
     const int32_t* rel = d.upd_rel + R.rel;
     __syncthreads();  // the previous update's reads of Li/Lj are done
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_update(const int32_t*
     }
     for (int q = tid; q < nj * wd; q += blockDim.x) {
       const int j = q % nj, kk = q / nj;
-      Lj[j][kk] = Pd[(int64_t)kk * md + R.r0 + j] * Pd[(int64_t)kk * md + kk];
+      Lj[j][kk] = PDd[(int64_t)kk * md + R.r0 + j];
     }
     for (int q = tid; q < ni; q += blockDim.x) rs[q] = rel[R.ia + q - R.r0] - lo;
     for (int q = tid; q < nj; q += blockDim.x) tc[q] = Rd[R.r0 + q] - f;
@@ -141,6 +144,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_update(const int32_t*
 
 __global__ void __launch_bounds__(256) k_panel_factor(const int32_t* __restrict__ lvl_sn, DevSym d,
                                                       double* __restrict__ Lx, int64_t pt,
+                                                      double* __restrict__ LDx, int64_t ldt,
                                                       const double* __restrict__ anorm,
                                                       double pivot_eps,
                                                       unsigned long long* __restrict__ counters) {
@@ -178,6 +182,13 @@ __global__ void __launch_bounds__(256) k_panel_factor(const int32_t* __restrict_
     __syncthreads();
   }
   if (threadIdx.x < 4 && cnt[threadIdx.x]) atomicAdd(&counters[threadIdx.x], (unsigned long long)cnt[threadIdx.x]);
+  // L D of the panel for the updates of its ancestors: column c's entries
+  // times d_c, the product the updates would otherwise form per target tile
+  double* PD = LDx + b * ldt + d.sn_valoff[s];
+  for (int c = 0; c < w; c++) {
+    const double dv = P[(int64_t)c * m + c];
+    for (int r = threadIdx.x; r < m; r += blockDim.x) PD[(int64_t)c * m + r] = P[(int64_t)c * m + r] * dv;
+  }
 }
 
 }  // namespace
@@ -217,14 +228,16 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
     if (l > 0 && w1 > w0) {
       dim3 grid(w1 - w0, h.N);
       const int kt = kt_begin(h, kFamFactorUpd, h.N * h.fupd_flops[l], st);
-      k_factor_update<<<grid, kFactorThreads, 0, st>>>(h.d.fwork + 4 * w0, h.d.fpairs, h.d, h.Lx, pt);
+      k_factor_update<<<grid, kFactorThreads, 0, st>>>(h.d.fwork + 4 * w0, h.d.fpairs, h.d, h.Lx, pt, h.LDx,
+                                                        h.ld_total);
       kt_end(h, kt, st);
       h.launches++;
     }
     const int s0 = h.flvl_ptr[l], s1 = h.flvl_ptr[l + 1];
     if (s1 > s0) {
       dim3 grid2(s1 - s0, h.N);
-      k_panel_factor<<<grid2, 256, 0, st>>>(h.d.flvl_sn + s0, h.d, h.Lx, pt, h.anorm, h.opt.pivot_eps,
+      k_panel_factor<<<grid2, 256, 0, st>>>(h.d.flvl_sn + s0, h.d, h.Lx, pt, h.LDx, h.ld_total, h.anorm,
+                                            h.opt.pivot_eps,
                                             h.counters);
       h.launches++;
     }
@@ -240,7 +253,7 @@ cudaError_t launch_factor_levels(Handle& h, cudaStream_t st) {
     if (h.tail_items > 0) {
       dim3 grid(h.tail_items, h.N);
       const int kt = kt_begin(h, kFamFactorUpd, h.N * h.tupd_flops, st);
-      k_factor_update<<<grid, kFactorThreads, 0, st>>>(h.d.twork, h.d.fpairs, h.d, h.Lx, pt);
+      k_factor_update<<<grid, kFactorThreads, 0, st>>>(h.d.twork, h.d.fpairs, h.d, h.Lx, pt, h.LDx, h.ld_total);
       kt_end(h, kt, st);
       h.launches++;
     }

@@ -139,6 +139,8 @@ struct Handle {
 
   // numeric buffers
   double* Lx = nullptr;       // N * panel_total
+  double* LDx = nullptr;      // N * ld_total: L D of the panels outside the dense tail
+  int64_t ld_total = 0;       // entries of those panels per block (sn_valoff[tail_sn])
   double* a_vals = nullptr;   // N * nnzA (FP64 copy for the residual)
   double* b_vals = nullptr;   // nnzB
   double* c_vals = nullptr;   // nC or nC*nC
