@@ -718,16 +718,16 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
 // The panel of a step, Y = A21 L11^{-T} and L21 = Y D1^{-1} (the rows below
 // the diagonal block), as a product on the tensor cores instead of one
 // substitution per row on the FP64 pipe: W = L11^{-1} is formed per matrix
-// in FP64 (k_panel_inverse_slice, 64 x 64, W[i][j] by the same substitution
-// that k_dense_panel_t runs for a row, with the unit vector e_j as the row),
-// and Y = A21 W^T is one 64-column product with K = 64 in the format of the
+// in FP64 (k_panel_inverse_slice, 64 x 64: column j of W by the substitution
+// that k_dense_panel_t runs for a row, applied to the unit vector e_j), and
+// Y = A21 W^T is one 64-column product with K = 64 in the format of the
 // 64-wide emulated update (7 BF16 digit slices, 7 exact tensor-memory levels,
 // the same fold), written instead of accumulated (k_tc_panel_emu).  The
 // rounding differs from the substitution's: the product is within the
-// rounding of an FP64 dot product of W's rows, W within that of the
+// rounding of an FP64 dot product with W's rows, W within that of the
 // substitution, so the panel's residual A21 - Y L11^T grows with the
-// condition of L11 (unit lower triangular, well conditioned for the
-// diagonal blocks of these quasidefinite matrices).
+// condition of the unit lower triangle L11, which the diagonal blocks of
+// these quasidefinite matrices keep small.
 
 // W = L11^{-1} of matrix blockIdx.x (the kb x kb unit lower triangle at
 // (k0, k0) after k_dense_diag_t) and the digit image of its rows, the B
