@@ -520,8 +520,8 @@ kkt_status kkt_server_cache_info(kkt_server* s, int64_t* resident, int64_t* anal
  * the block factor (k_factor_update), 5 the dense diagonal blocks of the
  * blocked factors (k_dense_diag_t), 6 the emulated-FP64 update with K = 256
  * of the 256-wide outer panels (k_tc_update_emu_wide), 7 the emulated-FP64
- * panels of those factors (k_tc_panel_emu, timed with the two launches that
- * form its operands: W = L11^{-1} and the digit image of A21).  flops: the
+ * panels of those factors (k_tc_panel_emu, timed with the launch that forms
+ * its operands: W = L11^{-1} and the digit images of W and A21).  flops: the
  * algorithmic FP64-equivalent flops of the launches (2 per multiply-add on the
  * entries of the lower triangle they update; for a panel, 2 per multiply-add
  * of the row solves it replaces). */

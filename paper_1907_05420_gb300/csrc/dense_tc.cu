@@ -719,7 +719,8 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
 // the diagonal block), as a product on the tensor cores instead of one
 // substitution per row on the FP64 pipe: W = L11^{-1} is formed per matrix
 // in FP64 (k_panel_inverse_slice, 64 x 64: column j of W by the substitution
-// that k_dense_panel_t runs for a row, applied to the unit vector e_j), and
+// that k_dense_panel_t runs for a row, applied to the unit vector e_j; the
+// same launch slices the rows of A21 into digits), and
 // Y = A21 W^T is one 64-column product with K = 64 in the format of the
 // 64-wide emulated update (7 BF16 digit slices, 7 exact tensor-memory levels,
 // the same fold), written instead of accumulated (k_tc_panel_emu).  The
@@ -729,21 +730,63 @@ __global__ void __launch_bounds__(kEmuThreads, 1)
 // condition of the unit lower triangle L11, which the diagonal blocks of
 // these quasidefinite matrices keep small.
 
-// W = L11^{-1} of matrix blockIdx.x (the kb x kb unit lower triangle at
-// (k0, k0) after k_dense_diag_t) and the digit image of its rows, the B
-// operand of k_tc_panel_emu: row i of B is row i of W (K index = column),
-// rows and columns >= kb zero, the row scales in scaleB[0..63].
+// The two operands of k_tc_panel_emu for matrix blockIdx.y, in one launch.
+// CTA 0: W = L11^{-1} (the kb x kb unit lower triangle at (k0, k0) after
+// k_dense_diag_t) and the digit image of its rows, the B operand: row i of B
+// is row i of W (K index = column), rows and columns >= kb zero, the row
+// scales in scaleB[0..63].  CTAs 1..: the digit image of the rows of A21
+// (columns k0 .. k0 + kb of the rows below the diagonal block, rows >= m
+// zero), the A operand, with the row scales and layout of k_tc_slice.
 __global__ void __launch_bounds__(256) k_panel_inverse_slice(const double* __restrict__ S0, int n, int k0, int kb,
+                                                             int m, int mpadA, uint8_t* __restrict__ imgA0,
                                                              uint8_t* __restrict__ imgB0,
+                                                             double* __restrict__ scaleA0,
                                                              double* __restrict__ scaleB0, TcStrides ts) {
   constexpr int KG = kgroups_of(2);
   __shared__ double M[TK][TK + 1];  // L11 by rows, then W by rows
   __shared__ uint32_t bf16_of_byte[256];
-  const int64_t bb = blockIdx.x;
+  const int64_t bb = blockIdx.y;
   const double* S = S0 + bb * ts.s;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) bf16_of_byte[i] = bf16_bits_of_byte((uint32_t)i);
+  __syncthreads();
+  if (blockIdx.x > 0) {
+    uint8_t* imgA = imgA0 + bb * ts.img_a;
+    double* scaleA = scaleA0 + bb * ts.scale;
+    for (int rho = (blockIdx.x - 1) * blockDim.x + threadIdx.x; rho < mpadA;
+         rho += (gridDim.x - 1) * blockDim.x) {
+      const bool live = rho < m;
+      const double* src = S + (int64_t)(k0 + kb + rho) + (int64_t)k0 * n;  // column c at src[c n]
+      // e = ilogb(max |v|) + 1 from the largest exponent field; rows whose
+      // largest entry is subnormal (or zero) take the FP64 route
+      int emax = 0;
+      if (live)
+        for (int c = 0; c < kb; c++) emax = max(emax, exp_field(src[(int64_t)c * n]));
+      int e_exp;
+      if (emax > 0) {
+        e_exp = emax - 1023 + 1;  // |v| < 2^e
+      } else {
+        double amax = 0.0;
+        if (live)
+          for (int c = 0; c < kb; c++) amax = fmax(amax, fabs(src[(int64_t)c * n]));
+        e_exp = amax > 0.0 ? ilogb(amax) + 1 : 0;
+      }
+      scaleA[rho] = ldexp(1.0, e_exp);
+      const int rr = rho % TM;
+      uint8_t* blk_img = imgA + (int64_t)(rho / TM) * image_bytes(2, TM) + (rr / 8) * KG * 128 + (rr % 8) * 16;
+      for (int kq = 0; kq < KG; kq++) {
+        double v[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+          const int c = kq * 8 + e;
+          v[e] = (live && c < kb) ? src[(int64_t)c * n] : 0.0;
+        }
+        emu_store_core_row(v, e_exp, bf16_of_byte, blk_img + kq * 128, slice_bytes(2, TM));
+      }
+    }
+    return;
+  }
   uint8_t* imgB = imgB0 + bb * ts.img_b;
   double* scaleB = scaleB0 + bb * ts.scale;
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) bf16_of_byte[i] = bf16_bits_of_byte((uint32_t)i);
   for (int q = threadIdx.x; q < TK * TK; q += blockDim.x) {
     const int c = q / TK, j = q - c * TK;
     M[j][c] = (j > c && j < kb) ? S[(int64_t)(k0 + j) + (int64_t)(k0 + c) * n] : 0.0;
@@ -790,7 +833,7 @@ __global__ void __launch_bounds__(256) k_panel_inverse_slice(const double* __res
 }
 
 // Y = A21 W^T for the 128-row tile blockIdx.x of matrix blockIdx.y: the A
-// image of the tile (k_tc_slice of A21) and the B image of W are copied once,
+// image of the tile and the B image of W (k_panel_inverse_slice) are copied once,
 // thread 0 issues the 112 MMAs (28 digit pairs x 4 K steps of 16) into the 7
 // levels, and 8 warps (two per tensor-memory lane quadrant, 32 columns each)
 // fold the levels and write Y (leading dimension n) and L21 = Y D1^{-1} into
@@ -1609,19 +1652,15 @@ cudaError_t factor_emu_wide(Handle& h, double* S, int n, int npiv, int nb, const
         // the panel as a product: W = L11^{-1}, the digit image of A21 (rows
         // below the diagonal block, columns k0 .. k0 + kb of S), Y = A21 W^T
         const int TIp = (m + TM - 1) / TM;
-        TcStrides tp = ti;  // A21 read in place: its "Y" is S from column k0 on
-        tp.y = ts.s;
         const int kp = kt_begin(h, kFamPanelEmu, nb * (double)m * kb * (kb - 1), st);
-        launch_prio(k_panel_inverse_slice, dim3(nb), dim3(256), 0, st, prio, (const double*)S, n, k0, kb, imgB,
-                    scaleB, ti);
         const int pgrid = std::max(1, std::min((TIp * TM + 255) / 256, 152 * 8 / nb));
-        launch_prio(k_tc_slice<2, double>, dim3(pgrid, nb), dim3(256), 0, st, prio, (const double*)S,
-                    (const double*)(S + (int64_t)k0 * n), n, k0, kb, m, imgA, imgB, scaleA, scaleB, TIp * TM, 0, tp);
+        launch_prio(k_panel_inverse_slice, dim3(1 + pgrid, nb), dim3(256), 0, st, prio, (const double*)S, n, k0, kb,
+                    m, TIp * TM, imgA, imgB, scaleA, scaleB, ti);
         e = launch_prio(k_tc_panel_emu, dim3(TIp, nb), dim3(256), panel_emu_smem_bytes(), st, prio, S, Yc, n, k0, kb,
                         m, (const uint8_t*)imgA, (const uint8_t*)imgB, (const double*)scaleA, (const double*)scaleB,
                         h.dev_err, ti);
         kt_end(h, kp, st);
-        h.launches += 3;
+        h.launches += 2;
         if (e != cudaSuccess) break;
       }
       // the outer panel's own remaining columns
