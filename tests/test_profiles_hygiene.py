@@ -1,8 +1,8 @@
 """The committed profiling evidence: every ncu command the repository documents
-(the summaries under profiles/ and the capture commands in the design doc) leaves
-the GPU clocks alone (--clock-control none), every summary gives the command
-that made it, and profiles/ holds text only (the raw reports stay out of the
-repository)."""
+(the summaries under profiles/ and the capture commands of the design notes at
+the repository root) leaves the GPU clocks alone (--clock-control none), every
+summary gives the command that made it, and profiles/ holds text only (the raw
+reports stay out of the repository)."""
 import pathlib
 
 ROOT = pathlib.Path(__file__).resolve().parents[1]
@@ -30,7 +30,8 @@ def _summaries():
 
 
 def test_every_documented_ncu_command_keeps_the_clocks():
-    cmds = [(f.name, c) for f in _summaries() + [ROOT / "DESIGN.md"] for c in _ncu_commands(f.read_text())]
+    notes = ROOT / "DESIGN.md"
+    cmds = [(f.name, c) for f in _summaries() + [notes] for c in _ncu_commands(f.read_text())]
     assert cmds
     for name, cmd in cmds:
         assert "--clock-control none" in cmd, (name, cmd)
