@@ -100,3 +100,25 @@ def test_struct_layouts_match_header(tmp_path):
             ctypes.sizeof(binding.kkt_inertia_options), binding.kkt_inertia_options.max_trials.offset,
             ctypes.sizeof(binding.kkt_inertia_result), binding.kkt_inertia_result.trials.offset]
     assert got == want
+
+
+def test_kernel_families_agree_with_the_header():
+    """kkt_kernel_stats' families: the binding's names, the header's documented
+    range and the library's family enumeration have the same count, in the
+    header's order (each documented family names its kernel)."""
+    from paper_1907_05420_gb300 import binding
+
+    enum = open(os.path.join(ROOT, "paper_1907_05420_gb300", "csrc", "handle.h")).read()
+    body = re.search(r"enum KernelFamily \{(.*?)\};", enum, flags=re.S).group(1)
+    members = [m.strip().split("=")[0].strip() for m in body.split(",") if m.strip()]
+    assert members[-1] == "kNumFamilies"
+    count = len(members) - 1
+    assert len(binding.KERNEL_FAMILIES) == count
+    header = open(HEADER).read()
+    assert f"(0..{count - 1})" in header
+    doc = header[header.index("Families:"):header.index("typedef struct", header.index("Families:"))]
+    for f, name in enumerate(binding.KERNEL_FAMILIES):
+        # "<f> the ... (name" or "<f> the ... (name, ...": each number precedes its kernel's name
+        pos_f = re.search(rf"\b{f} (the|an?) ", doc)
+        assert pos_f, (f, name)
+        assert name in doc[pos_f.start():], (f, name)
